@@ -1,0 +1,1849 @@
+// Plain FP64 CPU oracle for arXiv 1812.05540 (two-stage fixed-stress / CPR
+// preconditioner for multiphase poromechanics).
+//
+// TEST INFRASTRUCTURE ONLY: the product (the CUDA library and its binding)
+// never includes, links or calls this file.  It is deliberately slow and
+// literal: every routine restates one passage of the paper (cited inline) in
+// the order the paper states it, with no blocking, fusion or reordering.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (see __init__.py).
+// -ffp-contract=off keeps every a*b+c as two roundings so that the integer
+// decisions taken from floating point (strength of connection, aggregation)
+// are reproducible on x86 and Arm hosts.
+#include "oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <vector>
+
+namespace {
+
+typedef std::vector<double> vec;
+const double kMilliDarcy = 9.869233e-16;  // m^2
+const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: splitmix64 (S. Vigna), used as a pure
+// function of a 64-bit counter so that any lattice point can be drawn alone.
+// ---------------------------------------------------------------------------
+inline uint64_t sm64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+inline uint64_t lattice(int64_t i, int64_t j, int64_t k) {
+  const int64_t off = int64_t(1) << 17;
+  return uint64_t(i + off) | (uint64_t(j + off) << 18) | (uint64_t(k + off) << 36);
+}
+inline uint64_t rbits(uint64_t seed, int field, int sub, uint64_t idx) {
+  return sm64(sm64(seed) ^ (uint64_t(field) << 55) ^ (uint64_t(sub) << 54) ^ idx);
+}
+inline double unif(uint64_t seed, int field, int sub, uint64_t idx) {
+  return double(rbits(seed, field, sub, idx) >> 11) * 0x1.0p-53;
+}
+// Box-Muller from two independent uniforms of the same counter
+inline double gauss(uint64_t seed, int field, uint64_t idx) {
+  double u0 = unif(seed, field, 0, idx), u1 = unif(seed, field, 1, idx);
+  return std::sqrt(-2.0 * std::log(1.0 - u0)) * std::cos(2.0 * kPi * u1);
+}
+enum { F_E = 1, F_NU = 2, F_KAPPA = 3, F_PHI = 4, F_SW = 5, F_DP = 6, F_ELAYER = 7,
+       F_CHANNEL = 8, F_RHS = 9 };
+
+// Unit-variance Gaussian random field on the cells: white noise on the integer
+// lattice (padded by the kernel radius) convolved separably with
+// exp(-(d/L)^2/2), |d| <= 3L, then divided by the kernel's L2 norm.
+vec correlated_field(uint64_t seed, int field, int nx, int ny, int nz, int Lx, int Ly, int Lz) {
+  int R[3] = {3 * Lx, 3 * Ly, 3 * Lz};
+  int L[3] = {Lx, Ly, Lz};
+  std::vector<vec> w(3);
+  double norm = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    double s2 = 0.0;
+    for (int d = -R[a]; d <= R[a]; ++d) {
+      double t = double(d) / double(L[a]);
+      w[a].push_back(std::exp(-0.5 * t * t));
+      s2 += w[a].back() * w[a].back();
+    }
+    norm *= std::sqrt(s2);
+  }
+  int px = nx + 2 * R[0], py = ny + 2 * R[1], pz = nz + 2 * R[2];
+  vec W(size_t(px) * py * pz);
+  for (int k = 0; k < pz; ++k)
+    for (int j = 0; j < py; ++j)
+      for (int i = 0; i < px; ++i)
+        W[(size_t(k) * py + j) * px + i] = gauss(seed, field, lattice(i - R[0], j - R[1], k - R[2]));
+  // x pass: output i in [0,nx), padded j,k
+  vec X(size_t(nx) * py * pz, 0.0);
+  for (int k = 0; k < pz; ++k)
+    for (int j = 0; j < py; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double s = 0.0;
+        for (int d = -R[0]; d <= R[0]; ++d)
+          s += w[0][d + R[0]] * W[(size_t(k) * py + j) * px + (i + R[0] - d)];
+        X[(size_t(k) * py + j) * nx + i] = s;
+      }
+  vec Y(size_t(nx) * ny * pz, 0.0);
+  for (int k = 0; k < pz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double s = 0.0;
+        for (int d = -R[1]; d <= R[1]; ++d)
+          s += w[1][d + R[1]] * X[(size_t(k) * py + (j + R[1] - d)) * nx + i];
+        Y[(size_t(k) * ny + j) * nx + i] = s;
+      }
+  vec Z(size_t(nx) * ny * nz, 0.0);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double s = 0.0;
+        for (int d = -R[2]; d <= R[2]; ++d)
+          s += w[2][d + R[2]] * Y[(size_t(k + R[2] - d) * ny + j) * nx + i];
+        Z[(size_t(k) * ny + j) * nx + i] = s / norm;
+      }
+  return Z;
+}
+
+// ---------------------------------------------------------------------------
+// Cell fields and the linearisation state (§6 constitutive models; the
+// synthetic statistics stand in for the paper's staircase / SPE10 inputs).
+// ---------------------------------------------------------------------------
+struct Fields {
+  int nx, ny, nz;
+  vec E, nu, kh, kv, phi0, sw, p;
+};
+
+Fields make_fields(const or_gen_params& gp) {
+  Fields f;
+  f.nx = gp.nx; f.ny = gp.ny; f.nz = gp.nz;
+  int nx = gp.nx, ny = gp.ny, nz = gp.nz;
+  size_t nc = size_t(nx) * ny * nz;
+  f.E.resize(nc); f.nu.resize(nc); f.kh.resize(nc); f.kv.resize(nc);
+  f.phi0.resize(nc); f.sw.resize(nc); f.p.resize(nc);
+  uint64_t sd = gp.seed;
+  vec ghat = correlated_field(sd, F_DP, nx, ny, nz, 10, 10, 3);
+  vec ksm, swsm;
+  if (gp.field_kind == OR_FIELDS_LAYERED || gp.field_kind == OR_FIELDS_CHANNELS) {
+    ksm = correlated_field(sd, F_KAPPA, nx, ny, nz, 20, 20, 2);
+    swsm = correlated_field(sd, F_SW, nx, ny, nz, 10, 10, 3);
+  }
+  // channel geometry (channelised lower layers)
+  int n_low = (nz * 50 + 42) / 85;
+  struct Ch { double x0, A, lam, ph, halfw, logk; int k0, thick; };
+  std::vector<Ch> ch;
+  if (gp.field_kind == OR_FIELDS_CHANNELS) {
+    for (int c = 0; c < 12; ++c) {
+      Ch q;
+      q.x0 = double(nx) * unif(sd, F_CHANNEL, 0, lattice(c, 0, 0));
+      q.A = 5.0 + 10.0 * unif(sd, F_CHANNEL, 0, lattice(c, 1, 0));
+      q.lam = 40.0 + 70.0 * unif(sd, F_CHANNEL, 0, lattice(c, 2, 0));
+      q.ph = 2.0 * kPi * unif(sd, F_CHANNEL, 0, lattice(c, 3, 0));
+      int width = 4 + int(std::floor(5.0 * unif(sd, F_CHANNEL, 0, lattice(c, 4, 0))));
+      q.halfw = 0.5 * width;
+      q.thick = 5 + int(std::floor(6.0 * unif(sd, F_CHANNEL, 0, lattice(c, 5, 0))));
+      int room = n_low - q.thick + 1;
+      q.k0 = room > 0 ? int(std::floor(double(room) * unif(sd, F_CHANNEL, 0, lattice(c, 6, 0)))) : 0;
+      q.logk = std::log(1e3) + std::log(10.0) * unif(sd, F_CHANNEL, 0, lattice(c, 7, 0));
+      ch.push_back(q);
+    }
+  }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t c = (size_t(k) * ny + j) * nx + i;
+        uint64_t L = lattice(i, j, k);
+        double E, nu, kh, kv, phi, sw;
+        switch (gp.field_kind) {
+          case OR_FIELDS_LOGNORMAL: {
+            E = std::exp(std::log(1e10) - 0.5 * 0.25 + 0.5 * gauss(sd, F_E, L));
+            nu = 0.2 + 0.1 * unif(sd, F_NU, 0, L);
+            kh = std::exp(std::log(100.0 * kMilliDarcy) - 0.5 + gauss(sd, F_KAPPA, L));
+            kv = kh;
+            phi = 0.15 + 0.1 * unif(sd, F_PHI, 0, L);
+            sw = 0.2 + 0.6 * unif(sd, F_SW, 0, L);
+            break;
+          }
+          case OR_FIELDS_LAYERED:
+          case OR_FIELDS_CHANNELS: {
+            if (gp.field_kind == OR_FIELDS_LAYERED) {
+              E = std::exp(std::log(1e9) + std::log(50.0) * unif(sd, F_ELAYER, 0, lattice(0, 0, k)));
+              kh = 100.0 * kMilliDarcy * std::exp(2.0 * ksm[c]);
+            } else {
+              E = std::exp(std::log(0.5e9) + std::log(100.0) * unif(sd, F_E, 0, L));
+              if (k < n_low) {
+                double best = std::log(1e-2);
+                for (const Ch& q : ch) {
+                  if (k < q.k0 || k >= q.k0 + q.thick) continue;
+                  double xc = q.x0 + q.A * std::sin(2.0 * kPi * (j + 0.5) / q.lam + q.ph);
+                  if (std::fabs((i + 0.5) - xc) <= q.halfw) best = std::max(best, q.logk);
+                }
+                kh = std::exp(best) * kMilliDarcy;
+              } else {
+                kh = 100.0 * kMilliDarcy * std::exp(2.5 * ksm[c]);
+              }
+            }
+            kv = 0.1 * kh;
+            nu = 0.2 + 0.1 * unif(sd, F_NU, 0, L);
+            phi = 0.15 + 0.1 * unif(sd, F_PHI, 0, L);
+            sw = 0.2 + 0.6 * (0.5 * std::erfc(-swsm[c] / std::sqrt(2.0)));
+            break;
+          }
+          default: {
+            E = gp.E0; nu = gp.nu0; kh = gp.kappa0; kv = gp.kappa0; phi = gp.phi0; sw = gp.sw0;
+          }
+        }
+        f.E[c] = E; f.nu[c] = nu; f.kh[c] = kh; f.kv[c] = kv; f.phi0[c] = phi; f.sw[c] = sw;
+        double g = (gp.flags & OR_GRAVITY) ? gp.grav : 0.0;
+        double zc = (k + 0.5) * gp.h, ztop = nz * gp.h;
+        f.p[c] = gp.p_ref + gp.rho_w0 * g * (ztop - zc) + gp.dp_amp * std::tanh(ghat[c]);
+      }
+  return f;
+}
+
+// Constitutive quantities of one cell at state (s, p, mean volumetric strain).
+struct Mat {
+  double lam, G, Kdr, dphidp, phi, rw, rnw, rs, drho_deps, drho_dp, drho_ds;
+  double krw, krnw, dkrw, dkrnw;  // relative permeabilities and d/ds
+};
+
+void relperm(const or_gen_params& gp, double s, double* krw, double* krnw, double* dkrw, double* dkrnw) {
+  double den = 1.0 - gp.s_wr - gp.s_nwr;
+  double sh = (s - gp.s_wr) / den;
+  bool inside = sh > 0.0 && sh < 1.0;
+  sh = std::min(1.0, std::max(0.0, sh));
+  double n = gp.corey;
+  if (n == 2.0) {
+    *krw = sh * sh; *krnw = (1.0 - sh) * (1.0 - sh);
+    *dkrw = inside ? 2.0 * sh / den : 0.0;
+    *dkrnw = inside ? -2.0 * (1.0 - sh) / den : 0.0;
+  } else if (n == 1.0) {
+    *krw = sh; *krnw = 1.0 - sh;
+    *dkrw = inside ? 1.0 / den : 0.0;
+    *dkrnw = inside ? -1.0 / den : 0.0;
+  } else {
+    *krw = std::pow(sh, n); *krnw = std::pow(1.0 - sh, n);
+    *dkrw = inside ? n * std::pow(sh, n - 1.0) / den : 0.0;
+    *dkrnw = inside ? -n * std::pow(1.0 - sh, n - 1.0) / den : 0.0;
+  }
+}
+
+// Eq. (4) porosity law, §6 density law, §2 mixture density and App. B
+// derivatives of the mixture density.
+Mat material(const or_gen_params& gp, double E, double nu, double phi0, double s, double p,
+             double epsv_mean) {
+  Mat m;
+  double b = gp.biot;
+  m.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  m.G = E / (2.0 * (1.0 + nu));
+  m.Kdr = E / (3.0 * (1.0 - 2.0 * nu));
+  m.dphidp = (b - phi0) * (1.0 - b) / m.Kdr;
+  double dp = p - gp.p_ref;
+  m.phi = phi0 + b * epsv_mean + m.dphidp * dp;
+  m.rw = gp.rho_w0 * (1.0 + gp.c_w * dp);
+  m.rnw = gp.rho_nw0 * (1.0 + gp.c_nw * dp);
+  m.rs = gp.rho_s0 * (1.0 + gp.c_r * dp);
+  double B = -m.rs + s * m.rw + (1.0 - s) * m.rnw;
+  m.drho_deps = B * b;
+  m.drho_dp = B * m.dphidp + (1.0 - m.phi) * gp.rho_s0 * gp.c_r + s * m.phi * gp.rho_w0 * gp.c_w +
+              (1.0 - s) * m.phi * gp.rho_nw0 * gp.c_nw;
+  m.drho_ds = m.phi * (m.rw - m.rnw);
+  relperm(gp, s, &m.krw, &m.krnw, &m.dkrw, &m.dkrnw);
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Q1 reference integrals on a cube of edge h, 2x2x2 Gauss (exact here).
+// Local node a = (ax, ay, az) with ax = a&1, ay = (a>>1)&1, az = (a>>2)&1.
+// ---------------------------------------------------------------------------
+struct RefInt {
+  double G[8][8][3][3], IN[8], IdN[8][3], INdN[8][8][3];
+  double gp_N[8][8], gp_dN[8][8][3], gp_w;  // [gauss pt][node]
+};
+RefInt ref_integrals(double h) {
+  RefInt R;
+  std::memset(&R, 0, sizeof(R));
+  double g[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+  R.gp_w = h * h * h / 8.0;
+  for (int q = 0; q < 8; ++q) {
+    double xi[3] = {g[q & 1], g[(q >> 1) & 1], g[(q >> 2) & 1]};
+    for (int a = 0; a < 8; ++a) {
+      int ad[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+      double f[3], df[3];
+      for (int d = 0; d < 3; ++d) {
+        f[d] = ad[d] ? xi[d] : 1.0 - xi[d];
+        df[d] = (ad[d] ? 1.0 : -1.0) / h;
+      }
+      R.gp_N[q][a] = f[0] * f[1] * f[2];
+      R.gp_dN[q][a][0] = df[0] * f[1] * f[2];
+      R.gp_dN[q][a][1] = f[0] * df[1] * f[2];
+      R.gp_dN[q][a][2] = f[0] * f[1] * df[2];
+    }
+  }
+  for (int q = 0; q < 8; ++q)
+    for (int a = 0; a < 8; ++a) {
+      R.IN[a] += R.gp_w * R.gp_N[q][a];
+      for (int d = 0; d < 3; ++d) R.IdN[a][d] += R.gp_w * R.gp_dN[q][a][d];
+      for (int b = 0; b < 8; ++b)
+        for (int d = 0; d < 3; ++d) {
+          R.INdN[a][b][d] += R.gp_w * R.gp_N[q][a] * R.gp_dN[q][b][d];
+          for (int e = 0; e < 3; ++e) R.G[a][b][d][e] += R.gp_w * R.gp_dN[q][a][d] * R.gp_dN[q][b][e];
+        }
+    }
+  return R;
+}
+
+// ---------------------------------------------------------------------------
+// Block sparse storage and the structured patterns of §3 (Q1 nodes, P0 cells)
+// ---------------------------------------------------------------------------
+struct BSR {
+  int64_t nbr = 0, nbc = 0;
+  int br = 1, bc = 1;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  vec v;
+  int64_t find(int64_t i, int64_t j) const {
+    auto b = ci.begin() + rp[i], e = ci.begin() + rp[i + 1];
+    auto it = std::lower_bound(b, e, int32_t(j));
+    if (it == e || *it != j) return -1;
+    return it - ci.begin();
+  }
+};
+
+struct Grid {
+  int nx, ny, nz;
+  double h;
+  int64_t nn() const { return int64_t(nx + 1) * (ny + 1) * (nz + 1); }
+  int64_t ncell() const { return int64_t(nx) * ny * nz; }
+  int64_t node(int i, int j, int k) const { return i + int64_t(nx + 1) * (j + int64_t(ny + 1) * k); }
+  int64_t cell(int i, int j, int k) const { return i + int64_t(nx) * (j + int64_t(ny) * k); }
+};
+
+BSR pattern_uu(const Grid& g) {
+  BSR A; A.nbr = A.nbc = g.nn(); A.br = A.bc = 3;
+  A.rp.push_back(0);
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i) {
+        for (int dk = -1; dk <= 1; ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              int a = i + di, b = j + dj, c = k + dk;
+              if (a < 0 || b < 0 || c < 0 || a > g.nx || b > g.ny || c > g.nz) continue;
+              A.ci.push_back(int32_t(g.node(a, b, c)));
+            }
+        A.rp.push_back(int64_t(A.ci.size()));
+      }
+  A.v.assign(A.ci.size() * 9, 0.0);
+  return A;
+}
+BSR pattern_uf(const Grid& g) {
+  BSR A; A.nbr = g.nn(); A.nbc = g.ncell(); A.br = 3; A.bc = 2;
+  A.rp.push_back(0);
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i) {
+        for (int dk = -1; dk <= 0; ++dk)
+          for (int dj = -1; dj <= 0; ++dj)
+            for (int di = -1; di <= 0; ++di) {
+              int a = i + di, b = j + dj, c = k + dk;
+              if (a < 0 || b < 0 || c < 0 || a >= g.nx || b >= g.ny || c >= g.nz) continue;
+              A.ci.push_back(int32_t(g.cell(a, b, c)));
+            }
+        A.rp.push_back(int64_t(A.ci.size()));
+      }
+  A.v.assign(A.ci.size() * 6, 0.0);
+  return A;
+}
+BSR pattern_fu(const Grid& g) {
+  BSR A; A.nbr = g.ncell(); A.nbc = g.nn(); A.br = 2; A.bc = 3;
+  A.rp.push_back(0);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        for (int dk = 0; dk <= 1; ++dk)
+          for (int dj = 0; dj <= 1; ++dj)
+            for (int di = 0; di <= 1; ++di) A.ci.push_back(int32_t(g.node(i + di, j + dj, k + dk)));
+        A.rp.push_back(int64_t(A.ci.size()));
+      }
+  A.v.assign(A.ci.size() * 6, 0.0);
+  return A;
+}
+BSR pattern_ff(const Grid& g) {
+  BSR A; A.nbr = A.nbc = g.ncell(); A.br = A.bc = 2;
+  A.rp.push_back(0);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        if (k > 0) A.ci.push_back(int32_t(g.cell(i, j, k - 1)));
+        if (j > 0) A.ci.push_back(int32_t(g.cell(i, j - 1, k)));
+        if (i > 0) A.ci.push_back(int32_t(g.cell(i - 1, j, k)));
+        A.ci.push_back(int32_t(g.cell(i, j, k)));
+        if (i + 1 < g.nx) A.ci.push_back(int32_t(g.cell(i + 1, j, k)));
+        if (j + 1 < g.ny) A.ci.push_back(int32_t(g.cell(i, j + 1, k)));
+        if (k + 1 < g.nz) A.ci.push_back(int32_t(g.cell(i, j, k + 1)));
+        A.rp.push_back(int64_t(A.ci.size()));
+      }
+  A.v.assign(A.ci.size() * 4, 0.0);
+  return A;
+}
+
+// Extra boundary conditions used only by the Terzaghi column.
+struct ExtraBC {
+  bool active = false;
+  std::vector<uint8_t> dir_u;  // per displacement dof
+  double sigma_top = 0.0;      // compressive load on the top face
+  bool top_drained = false;    // Dirichlet flow face on top of the top cells
+  double p_top = 0.0, s_top = 0.0;
+};
+
+struct State {  // linearisation point
+  vec u;        // nodal displacement, 3 per node
+  vec s, p;     // per cell
+};
+
+// mean volumetric strain of each element from nodal u (Q1, Gauss average)
+vec mean_epsv(const Grid& g, const RefInt& R, const vec& u) {
+  vec ev(g.ncell(), 0.0);
+  if (u.empty()) return ev;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        double s = 0.0;
+        for (int a = 0; a < 8; ++a) {
+          int64_t I = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+          for (int d = 0; d < 3; ++d) s += R.IdN[a][d] * u[3 * I + d];
+        }
+        ev[g.cell(i, j, k)] = s / (g.h * g.h * g.h);
+      }
+  return ev;
+}
+
+struct Jac {
+  BSR uu, uf, fu, ff;
+  vec dfs;
+  std::vector<uint8_t> dir;
+  double alpha_u = 1.0, alpha_f = 1.0;
+};
+
+// Two-point flux of phase l across one interior face K|L (Eq. (8), Eq. (12),
+// App. A transmissibility) and its derivatives (App. B, face Jacobian).
+struct FaceFlux {
+  double F, dF_dsK, dF_dsL, dF_dpK, dF_dpL;
+};
+FaceFlux face_flux(const or_gen_params& gp, double Ups, double dz, double g, int phase,
+                   double sK, double pK, double sL, double pL, bool boundaryL) {
+  double rho0 = phase == 0 ? gp.rho_w0 : gp.rho_nw0;
+  double c = phase == 0 ? gp.c_w : gp.c_nw;
+  double mu = phase == 0 ? gp.mu_w : gp.mu_nw;
+  double rK = rho0 * (1.0 + c * (pK - gp.p_ref));
+  double rL = rho0 * (1.0 + c * (pL - gp.p_ref));
+  double satK = phase == 0 ? sK : 1.0 - sK;
+  double satL = phase == 0 ? sL : 1.0 - sL;
+  // Eq. (12): face density
+  double varrho, dvK, dvL;
+  if (satK > 0.0 && satL > 0.0) { varrho = 0.5 * (rK + rL); dvK = 0.5 * rho0 * c; dvL = 0.5 * rho0 * c; }
+  else if (satK > 0.0) { varrho = rK; dvK = rho0 * c; dvL = 0.0; }
+  else if (satL > 0.0) { varrho = rL; dvK = 0.0; dvL = rho0 * c; }
+  else { varrho = 0.0; dvK = dvL = 0.0; }
+  (void)boundaryL;
+  double Phi = Ups * ((pL - pK) + varrho * g * dz);
+  bool upL = Phi > 0.0;  // ties: K upstream
+  double sU = upL ? sL : sK, pU = upL ? pL : pK;
+  double krw, krnw, dkrw, dkrnw;
+  relperm(gp, sU, &krw, &krnw, &dkrw, &dkrnw);
+  double kr = phase == 0 ? krw : krnw, dkr = phase == 0 ? dkrw : dkrnw;
+  double rU = rho0 * (1.0 + c * (pU - gp.p_ref));
+  double lamU = kr / mu;
+  FaceFlux f;
+  f.F = rU * lamU * Phi;
+  double dF_dsU = rU / mu * Phi * dkr;
+  f.dF_dsK = upL ? 0.0 : dF_dsU;
+  f.dF_dsL = upL ? dF_dsU : 0.0;
+  double drU = rho0 * c;
+  f.dF_dpK = (upL ? 0.0 : drU * lamU * Phi) + rU * lamU * Ups * (-1.0 + dvK * g * dz);
+  f.dF_dpL = (upL ? drU * lamU * Phi : 0.0) + rU * lamU * Ups * (1.0 + dvL * g * dz);
+  return f;
+}
+
+// Jacobian blocks of App. B at the given state, before scaling and Dirichlet.
+void assemble(const or_gen_params& gp, const Grid& g, const Fields& F, const State& st,
+              const ExtraBC& bc, Jac& J) {
+  RefInt R = ref_integrals(g.h);
+  J.uu = pattern_uu(g); J.uf = pattern_uf(g); J.fu = pattern_fu(g); J.ff = pattern_ff(g);
+  int64_t nc = g.ncell();
+  J.dfs.assign(2 * nc, 0.0);
+  double grav = (gp.flags & OR_GRAVITY) ? gp.grav : 0.0;
+  vec ev = mean_epsv(g, R, st.u);
+  double V = g.h * g.h * g.h;
+  bool coupling = (gp.flags & OR_COUPLING) != 0;
+  // element loop: mechanics and coupling blocks (App. B, element blocks)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        int64_t c = g.cell(i, j, k);
+        double s = st.s[c];
+        Mat m = material(gp, F.E[c], F.nu[c], F.phi0[c], s, st.p[c], ev[c]);
+        double b = gp.biot;
+        int64_t nodes[8];
+        for (int a = 0; a < 8; ++a) nodes[a] = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+        for (int a = 0; a < 8; ++a) {
+          for (int bb = 0; bb < 8; ++bb) {
+            int64_t pos = J.uu.find(nodes[a], nodes[bb]);
+            double* blk = &J.uu.v[pos * 9];
+            double trG = R.G[a][bb][0][0] + R.G[a][bb][1][1] + R.G[a][bb][2][2];
+            for (int d = 0; d < 3; ++d)
+              for (int e = 0; e < 3; ++e) {
+                // int grad^s eta_i : C_dr : grad^s eta_j
+                double kel = m.lam * R.G[a][bb][d][e] + m.G * R.G[a][bb][e][d] + (d == e ? m.G * trG : 0.0);
+                // - int eta_i . (drho/deps_v g) div eta_j, g = (0,0,-grav)
+                double gd = d == 2 ? -grav : 0.0;
+                double kg = -m.drho_deps * gd * R.INdN[a][bb][e];
+                blk[d * 3 + e] += kel + kg;
+              }
+          }
+          // A_us, A_up (node a, cell c): 3x2 block, columns (s, p)
+          int64_t pos = J.uf.find(nodes[a], c);
+          double* blk = &J.uf.v[pos * 6];
+          for (int d = 0; d < 3; ++d) {
+            double gd = d == 2 ? -grav : 0.0;
+            double us = -R.IN[a] * m.drho_ds * gd;
+            double up = -b * R.IdN[a][d] - R.IN[a] * m.drho_dp * gd;
+            if (coupling) { blk[d * 2 + 0] += us; blk[d * 2 + 1] += up; }
+          }
+          // A_su, A_pu (cell c, node a): 2x3 block
+          int64_t pos2 = J.fu.find(c, nodes[a]);
+          double* blk2 = &J.fu.v[pos2 * 6];
+          for (int e = 0; e < 3; ++e) {
+            double su = s * m.rw * b * R.IdN[a][e];
+            double pu = (1.0 - s) * m.rnw * b * R.IdN[a][e];
+            if (coupling) { blk2[0 * 3 + e] += su; blk2[1 * 3 + e] += pu; }
+          }
+        }
+        // accumulation (App. B element blocks A_ss, A_sp, A_ps, A_pp; no wells)
+        if (gp.flags & OR_ACCUM) {
+          int64_t pos = J.ff.find(c, c);
+          double* blk = &J.ff.v[pos * 4];
+          blk[0] += V * m.phi * m.rw;
+          blk[1] += V * (s * m.rw * m.dphidp + m.phi * s * gp.rho_w0 * gp.c_w);
+          blk[2] += -V * m.phi * m.rnw;
+          blk[3] += V * ((1.0 - s) * m.rnw * m.dphidp + m.phi * (1.0 - s) * gp.rho_nw0 * gp.c_nw);
+        }
+        // §5.1 fixed-stress diagonals
+        J.dfs[2 * c + 0] = V * b * b / m.Kdr * s * m.rw;
+        J.dfs[2 * c + 1] = V * b * b / m.Kdr * (1.0 - s) * m.rnw;
+      }
+  // face loop: TPFA Jacobian (App. B face blocks, with the Jacobian's sign:
+  // row K gets -dt dF, row L gets +dt dF)
+  if (gp.flags & OR_FLUX) {
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          int64_t K = g.cell(i, j, k);
+          for (int dir = 0; dir < 3; ++dir) {
+            int a = i + (dir == 0), b2 = j + (dir == 1), c2 = k + (dir == 2);
+            if (a >= g.nx || b2 >= g.ny || c2 >= g.nz) continue;
+            int64_t L = g.cell(a, b2, c2);
+            double kK = dir == 2 ? F.kv[K] : F.kh[K];
+            double kL = dir == 2 ? F.kv[L] : F.kh[L];
+            double area = g.h * g.h;
+            double UK = area * kK / (0.5 * g.h), UL = area * kL / (0.5 * g.h);
+            double Ups = UK * UL / (UK + UL);
+            double dz = dir == 2 ? g.h : 0.0;
+            int64_t pKK = J.ff.find(K, K), pKL = J.ff.find(K, L), pLK = J.ff.find(L, K), pLL = J.ff.find(L, L);
+            for (int ph = 0; ph < 2; ++ph) {
+              FaceFlux f = face_flux(gp, Ups, dz, grav, ph, st.s[K], st.p[K], st.s[L], st.p[L], false);
+              double dsK = (gp.flags & OR_FLUX_SAT) ? f.dF_dsK : 0.0;
+              double dsL = (gp.flags & OR_FLUX_SAT) ? f.dF_dsL : 0.0;
+              double dt = gp.dt;
+              J.ff.v[pKK * 4 + ph * 2 + 0] += -dt * dsK;
+              J.ff.v[pKK * 4 + ph * 2 + 1] += -dt * f.dF_dpK;
+              J.ff.v[pKL * 4 + ph * 2 + 0] += -dt * dsL;
+              J.ff.v[pKL * 4 + ph * 2 + 1] += -dt * f.dF_dpL;
+              J.ff.v[pLK * 4 + ph * 2 + 0] += dt * dsK;
+              J.ff.v[pLK * 4 + ph * 2 + 1] += dt * f.dF_dpK;
+              J.ff.v[pLL * 4 + ph * 2 + 0] += dt * dsL;
+              J.ff.v[pLL * 4 + ph * 2 + 1] += dt * f.dF_dpL;
+            }
+          }
+        }
+    if (bc.active && bc.top_drained) {
+      // Dirichlet flow face on top of each top cell: Upsilon^f = Upsilon^{f,K}
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          int64_t K = g.cell(i, j, g.nz - 1);
+          double Ups = g.h * g.h * F.kv[K] / (0.5 * g.h);
+          int64_t pKK = J.ff.find(K, K);
+          for (int ph = 0; ph < 2; ++ph) {
+            // the face plays the role of L; jump of psi is -psi_K
+            FaceFlux f = face_flux(gp, Ups, 0.5 * g.h, grav, ph, st.s[K], st.p[K], bc.s_top, bc.p_top, true);
+            double dsK = (gp.flags & OR_FLUX_SAT) ? f.dF_dsK : 0.0;
+            J.ff.v[pKK * 4 + ph * 2 + 0] += -gp.dt * dsK;
+            J.ff.v[pKK * 4 + ph * 2 + 1] += -gp.dt * f.dF_dpK;
+          }
+        }
+    }
+  }
+  // Dirichlet dofs
+  int64_t nu = 3 * g.nn();
+  J.dir.assign(nu, 0);
+  if (bc.active) {
+    J.dir = bc.dir_u;
+  } else if (gp.flags & OR_DIRICHLET) {
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i) {
+        int64_t I = g.node(i, j, 0);
+        for (int d = 0; d < 3; ++d) J.dir[3 * I + d] = 1;
+      }
+  }
+}
+
+// Dirichlet elimination (zero rows and columns of the constrained dofs),
+// block-row scaling (§4 remark) and unit diagonal for constrained dofs.
+void finalize(const or_gen_params& gp, const Grid& g, Jac& J, bool scale) {
+  int64_t nn = g.nn(), nc = g.ncell();
+  for (int64_t I = 0; I < nn; ++I)
+    for (int64_t q = J.uu.rp[I]; q < J.uu.rp[I + 1]; ++q) {
+      int64_t Jn = J.uu.ci[q];
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e)
+          if (J.dir[3 * I + d] || J.dir[3 * Jn + e]) J.uu.v[q * 9 + d * 3 + e] = 0.0;
+    }
+  for (int64_t I = 0; I < nn; ++I)
+    for (int64_t q = J.uf.rp[I]; q < J.uf.rp[I + 1]; ++q)
+      for (int d = 0; d < 3; ++d)
+        if (J.dir[3 * I + d]) { J.uf.v[q * 6 + d * 2] = 0.0; J.uf.v[q * 6 + d * 2 + 1] = 0.0; }
+  for (int64_t c = 0; c < nc; ++c)
+    for (int64_t q = J.fu.rp[c]; q < J.fu.rp[c + 1]; ++q) {
+      int64_t I = J.fu.ci[q];
+      for (int e = 0; e < 3; ++e)
+        if (J.dir[3 * I + e]) { J.fu.v[q * 6 + e] = 0.0; J.fu.v[q * 6 + 3 + e] = 0.0; }
+    }
+  J.alpha_u = 1.0; J.alpha_f = 1.0;
+  if (scale) {
+    const double pcol = 1e6;  // pressure unknown in MPa
+    for (size_t q = 0; q < J.uf.ci.size(); ++q)
+      for (int d = 0; d < 3; ++d) J.uf.v[q * 6 + d * 2 + 1] *= pcol;
+    for (size_t q = 0; q < J.ff.ci.size(); ++q) { J.ff.v[q * 4 + 1] *= pcol; J.ff.v[q * 4 + 3] *= pcol; }
+    for (int64_t c = 0; c < nc; ++c) { J.dfs[2 * c] *= pcol; J.dfs[2 * c + 1] *= pcol; }
+    double su = 0.0; int64_t cnt = 0;
+    for (int64_t I = 0; I < nn; ++I) {
+      int64_t q = J.uu.find(I, I);
+      for (int d = 0; d < 3; ++d)
+        if (!J.dir[3 * I + d]) { su += J.uu.v[q * 9 + d * 4]; ++cnt; }
+    }
+    J.alpha_u = cnt ? su / double(cnt) : 1.0;
+    double sf = 0.0;
+    for (int64_t c = 0; c < nc; ++c) sf += std::fabs(J.ff.v[J.ff.find(c, c) * 4 + 3]);
+    J.alpha_f = sf / double(nc);
+    for (double& x : J.uu.v) x /= J.alpha_u;
+    for (double& x : J.uf.v) x /= J.alpha_u;
+    for (double& x : J.fu.v) x /= J.alpha_f;
+    for (double& x : J.ff.v) x /= J.alpha_f;
+    for (double& x : J.dfs) x /= J.alpha_f;
+  }
+  for (int64_t I = 0; I < nn; ++I) {
+    int64_t q = J.uu.find(I, I);
+    for (int d = 0; d < 3; ++d)
+      if (J.dir[3 * I + d]) J.uu.v[q * 9 + d * 4] = 1.0;
+  }
+}
+
+template <class T>
+T* dup(const std::vector<T>& v) {
+  T* p = (T*)std::malloc(std::max<size_t>(1, v.size()) * sizeof(T));
+  if (!v.empty()) std::memcpy(p, v.data(), v.size() * sizeof(T));
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting (textbook Doolittle, row-major)
+// ---------------------------------------------------------------------------
+struct DenseLU {
+  int64_t n = 0;
+  vec a;
+  std::vector<int64_t> piv;
+  bool ok = false;
+  void factor(int64_t n_, vec m) {
+    n = n_; a = std::move(m); piv.resize(n);
+    ok = true;
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t p = k;
+      double best = std::fabs(a[k * n + k]);
+      for (int64_t i = k + 1; i < n; ++i)
+        if (std::fabs(a[i * n + k]) > best) { best = std::fabs(a[i * n + k]); p = i; }
+      piv[k] = p;
+      if (best == 0.0) { ok = false; continue; }
+      if (p != k)
+        for (int64_t j = 0; j < n; ++j) std::swap(a[k * n + j], a[p * n + j]);
+      for (int64_t i = k + 1; i < n; ++i) {
+        double l = a[i * n + k] / a[k * n + k];
+        a[i * n + k] = l;
+        if (l == 0.0) continue;
+        for (int64_t j = k + 1; j < n; ++j) a[i * n + j] -= l * a[k * n + j];
+      }
+    }
+  }
+  void solve(const double* b, double* x) const {
+    vec y(b, b + n);
+    for (int64_t k = 0; k < n; ++k) std::swap(y[k], y[piv[k]]);
+    for (int64_t i = 0; i < n; ++i) {
+      double s = y[i];
+      for (int64_t j = 0; j < i; ++j) s -= a[i * n + j] * y[j];
+      y[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int64_t j = i + 1; j < n; ++j) s -= a[i * n + j] * y[j];
+      y[i] = s / a[i * n + i];
+    }
+    for (int64_t i = 0; i < n; ++i) x[i] = y[i];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Scalar CSR with nc values per entry (shared pattern for the three SDC
+// displacement components of §5.2)
+// ---------------------------------------------------------------------------
+struct CSR {
+  int64_t n = 0, m = 0;
+  int nc = 1;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  vec v;  // v[e*nc + comp]
+  int64_t nnz() const { return int64_t(ci.size()); }
+  int64_t find(int64_t i, int64_t j) const {
+    auto b = ci.begin() + rp[i], e = ci.begin() + rp[i + 1];
+    auto it = std::lower_bound(b, e, int32_t(j));
+    if (it == e || *it != j) return -1;
+    return it - ci.begin();
+  }
+};
+
+void csr_spmv(const CSR& A, int comp, const double* x, double* y) {
+  for (int64_t i = 0; i < A.n; ++i) {
+    double s = 0.0;
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) s += A.v[q * A.nc + comp] * x[A.ci[q]];
+    y[i] = s;
+  }
+}
+
+// transpose; entries of each output row appear in ascending input-row order
+CSR transpose(const CSR& A) {
+  CSR T; T.n = A.m; T.m = A.n; T.nc = A.nc;
+  T.rp.assign(T.n + 1, 0);
+  for (int32_t c : A.ci) T.rp[c + 1]++;
+  for (int64_t i = 0; i < T.n; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size()); T.v.resize(A.v.size());
+  std::vector<int64_t> fill(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+      int64_t pos = fill[A.ci[q]]++;
+      T.ci[pos] = int32_t(i);
+      for (int c = 0; c < A.nc; ++c) T.v[pos * A.nc + c] = A.v[q * A.nc + c];
+    }
+  return T;
+}
+
+// C = X Y (row-wise Gustavson).  For each output entry the products are added
+// in ascending order of the inner index k, starting from 0.
+CSR spgemm(const CSR& X, const CSR& Y) {
+  CSR C; C.n = X.n; C.m = Y.m; C.nc = X.nc;
+  C.rp.assign(C.n + 1, 0);
+  std::vector<int64_t> mark(Y.m, -1);
+  vec acc(size_t(Y.m) * X.nc, 0.0);
+  std::vector<int32_t> cols;
+  for (int64_t i = 0; i < X.n; ++i) {
+    cols.clear();
+    for (int64_t q = X.rp[i]; q < X.rp[i + 1]; ++q) {
+      int64_t k = X.ci[q];
+      for (int64_t r = Y.rp[k]; r < Y.rp[k + 1]; ++r) {
+        int64_t j = Y.ci[r];
+        if (mark[j] != i) {
+          mark[j] = i;
+          cols.push_back(int32_t(j));
+          for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = 0.0;
+        }
+        for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = acc[j * X.nc + c] + X.v[q * X.nc + c] * Y.v[r * X.nc + c];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t j : cols) {
+      C.ci.push_back(j);
+      for (int c = 0; c < X.nc; ++c) C.v.push_back(acc[j * X.nc + c]);
+    }
+    C.rp[i + 1] = int64_t(C.ci.size());
+  }
+  return C;
+}
+
+// ---------------------------------------------------------------------------
+// Smoothed-aggregation AMG (the amg(.) of §5.2 and §5.3; the paper uses Hypre
+// BoomerAMG, this restates a deterministic smoothed aggregation)
+// ---------------------------------------------------------------------------
+struct Level {
+  CSR A, P, R;
+  std::vector<int32_t> agg;
+  int64_t nagg = 0;
+  vec dl1;  // n*nc, l1 row norms
+  vec dg;   // n*nc, diagonal
+  vec lam;  // nc, Gershgorin bound of rho(D^{-1}A)
+  std::vector<uint8_t> root;  // distance-2 MIS roots
+  std::vector<DenseLU> lu;  // coarsest only, per component
+};
+struct AMG {
+  int nc = 1;
+  std::vector<Level> L;
+};
+
+// node-level strength value: sum over components of |a_ij|
+inline double abar(const CSR& A, int64_t q) {
+  double s = 0.0;
+  for (int c = 0; c < A.nc; ++c) s = s + std::fabs(A.v[q * A.nc + c]);
+  return s;
+}
+
+inline int64_t mis_key(int64_t i, int level) {
+  uint64_t h = sm64((uint64_t(level) << 32) | uint64_t(i));
+  return (int64_t(h >> 33) << 32) | i;
+}
+
+// Strength graph, distance-2 maximal independent set, aggregates.
+void aggregate(Level& lev, double theta, int level) {
+  const CSR& A = lev.A;
+  int64_t n = A.n;
+  vec dg(n, 0.0);
+  std::vector<uint8_t> excluded(n, 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+      if (A.ci[q] == i) dg[i] = abar(A, q);
+      else
+        for (int c = 0; c < A.nc; ++c)
+          if (A.v[q * A.nc + c] != 0.0) excluded[i] = 0;
+    }
+  // symmetric strength graph: edge i~j if max(abar_ij, abar_ji) >= theta*sqrt(abar_ii*abar_jj)
+  std::vector<uint8_t> strong(A.nnz(), 0);
+  vec wgt(A.nnz(), 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (excluded[i]) continue;
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+      int64_t j = A.ci[q];
+      if (j == i || excluded[j]) continue;
+      int64_t qt = A.find(j, i);
+      double aij = abar(A, q), aji = qt >= 0 ? abar(A, qt) : 0.0;
+      double t = std::max(aij, aji);
+      double den = std::sqrt(dg[i] * dg[j]);
+      if (t >= theta * den && t > 0.0) { strong[q] = 1; wgt[q] = t / den; }
+    }
+  }
+  // synchronous distance-2 MIS rounds: 0 undecided, 1 root, 2 covered, 3 excluded
+  std::vector<uint8_t> st(n, 0);
+  for (int64_t i = 0; i < n; ++i) if (excluded[i]) st[i] = 3;
+  std::vector<int64_t> m1(n), m2(n);
+  std::vector<uint8_t> nr(n), c1(n);
+  for (;;) {
+    bool any = false;
+    for (int64_t i = 0; i < n; ++i) if (st[i] == 0) { any = true; break; }
+    if (!any) break;
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t m = st[i] == 0 ? mis_key(i, level) : -1;
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (strong[q] && st[A.ci[q]] == 0) m = std::max(m, mis_key(A.ci[q], level));
+      m1[i] = m;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t m = m1[i];
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (strong[q]) m = std::max(m, m1[A.ci[q]]);
+      m2[i] = m;
+    }
+    for (int64_t i = 0; i < n; ++i) nr[i] = (st[i] == 0 && m2[i] == mis_key(i, level));
+    for (int64_t i = 0; i < n; ++i) if (nr[i]) st[i] = 1;
+    for (int64_t i = 0; i < n; ++i) {
+      uint8_t c = nr[i];
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (strong[q] && nr[A.ci[q]]) c = 1;
+      c1[i] = c;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      if (st[i] != 0) continue;
+      uint8_t c = c1[i];
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (strong[q] && c1[A.ci[q]]) c = 1;
+      if (c) st[i] = 2;
+    }
+  }
+  lev.agg.assign(n, -1);
+  lev.root.assign(n, 0);
+  for (int64_t i = 0; i < n; ++i) lev.root[i] = st[i] == 1;
+  int64_t na = 0;
+  for (int64_t i = 0; i < n; ++i) if (st[i] == 1) lev.agg[i] = int32_t(na++);
+  lev.nagg = na;
+  // phase 1: strong neighbours of a root join it
+  std::vector<int32_t> ph1 = lev.agg;
+  for (int64_t i = 0; i < n; ++i) {
+    if (st[i] != 2) continue;
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+      if (strong[q] && st[A.ci[q]] == 1) { ph1[i] = lev.agg[A.ci[q]]; break; }
+  }
+  // phase 2: leftovers join the aggregate of their strongest phase-1 neighbour
+  lev.agg = ph1;
+  for (int64_t i = 0; i < n; ++i) {
+    if (st[i] != 2 || ph1[i] >= 0) continue;
+    double bw = -1.0; int32_t ba = -1;
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+      if (!strong[q]) continue;
+      int32_t a = ph1[A.ci[q]];
+      if (a < 0) continue;
+      if (wgt[q] > bw || (wgt[q] == bw && a < ba)) { bw = wgt[q]; ba = a; }
+    }
+    lev.agg[i] = ba;
+  }
+}
+
+// Gershgorin bound lambda_hat = max_i sum_j |a_ij| / |a_ii| per component
+vec gershgorin(const CSR& A) {
+  vec lam(A.nc, 0.0);
+  for (int c = 0; c < A.nc; ++c)
+    for (int64_t i = 0; i < A.n; ++i) {
+      double s = 0.0, d = 0.0;
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+        s = s + std::fabs(A.v[q * A.nc + c]);
+        if (A.ci[q] == i) d = A.v[q * A.nc + c];
+      }
+      lam[c] = std::max(lam[c], s / std::fabs(d));
+    }
+  return lam;
+}
+
+// P = (I - omega D^{-1} A) P_tent, omega = (4/3)/lambda_hat (Gershgorin)
+CSR smoothed_prolongator(const Level& lev) {
+  const CSR& A = lev.A;
+  int nc = A.nc;
+  int64_t n = A.n;
+  vec lam = gershgorin(A), omega(nc);
+  for (int c = 0; c < nc; ++c) omega[c] = (4.0 / 3.0) / lam[c];
+  CSR P; P.n = n; P.m = lev.nagg; P.nc = nc; P.rp.assign(n + 1, 0);
+  std::vector<int32_t> aggs;
+  for (int64_t i = 0; i < n; ++i) {
+    if (lev.agg[i] >= 0) {
+      aggs.clear();
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (lev.agg[A.ci[q]] >= 0) aggs.push_back(lev.agg[A.ci[q]]);
+      std::sort(aggs.begin(), aggs.end());
+      aggs.erase(std::unique(aggs.begin(), aggs.end()), aggs.end());
+      int64_t qd = A.find(i, i);
+      for (int32_t a : aggs) {
+        P.ci.push_back(a);
+        for (int c = 0; c < nc; ++c) {
+          double S = 0.0;
+          for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+            if (lev.agg[A.ci[q]] == a) S = S + A.v[q * nc + c];
+          double coef = omega[c] / A.v[qd * nc + c];
+          double delta = a == lev.agg[i] ? 1.0 : 0.0;
+          P.v.push_back(delta - coef * S);
+        }
+      }
+    }
+    P.rp[i + 1] = int64_t(P.ci.size());
+  }
+  return P;
+}
+
+vec l1_diag(const CSR& A) {
+  vec d(A.n * A.nc, 0.0);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int c = 0; c < A.nc; ++c) {
+      double s = 0.0;
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) s = s + std::fabs(A.v[q * A.nc + c]);
+      d[i * A.nc + c] = s;
+    }
+  return d;
+}
+
+bool build_amg(AMG& H, CSR A0, double theta0, int coarse_max, int max_levels) {
+  H.nc = A0.nc;
+  H.L.clear();
+  H.L.emplace_back();
+  H.L[0].A = std::move(A0);
+  double theta = theta0;
+  for (int l = 0;; ++l) {
+    Level& lev = H.L[l];
+    bool coarsest = lev.A.n <= coarse_max || l + 1 >= max_levels;
+    if (!coarsest) {
+      aggregate(lev, theta, l);
+      if (lev.nagg == 0 || double(lev.A.n) / double(lev.nagg) < 1.2) coarsest = true;
+    }
+    if (coarsest) {
+      if (lev.A.n > 12000) return false;
+      lev.agg.clear(); lev.nagg = 0;
+      lev.lu.resize(H.nc);
+      for (int c = 0; c < H.nc; ++c) {
+        int64_t n = lev.A.n;
+        vec d(size_t(n) * n, 0.0);
+        for (int64_t i = 0; i < n; ++i)
+          for (int64_t q = lev.A.rp[i]; q < lev.A.rp[i + 1]; ++q) d[i * n + lev.A.ci[q]] = lev.A.v[q * H.nc + c];
+        lev.lu[c].factor(n, std::move(d));
+      }
+      break;
+    }
+    lev.P = smoothed_prolongator(lev);
+    lev.R = transpose(lev.P);
+    lev.dl1 = l1_diag(lev.A);
+    lev.lam = gershgorin(lev.A);
+    lev.dg.assign(lev.A.n * H.nc, 0.0);
+    for (int64_t i = 0; i < lev.A.n; ++i) {
+      int64_t q = lev.A.find(i, i);
+      for (int c = 0; c < H.nc; ++c) lev.dg[i * H.nc + c] = lev.A.v[q * H.nc + c];
+    }
+    CSR AP = spgemm(lev.A, lev.P);
+    CSR Ac = spgemm(lev.R, AP);
+    H.L.emplace_back();
+    H.L[l + 1].A = std::move(Ac);
+    theta *= 0.5;
+  }
+  return true;
+}
+
+struct Smooth {
+  int kind, pre, post, degree;
+  double ratio;
+};
+
+// Chebyshev smoother on D^{-1}A over [lambda_hat/ratio, lambda_hat]
+// (three-term recurrence of Adams, Brezina, Hu, Tuminaro 2003)
+void chebyshev(const Level& lev, int nc, int c, const vec& b, vec& x, int degree, double ratio, bool zero) {
+  int64_t n = lev.A.n;
+  double lmax = lev.lam[c], lmin = lmax / ratio;
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  double sigma = theta / delta, rho = 1.0 / sigma;
+  vec r(n), d(n), Ax(n);
+  if (zero) {
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] / lev.dg[i * nc + c];
+  } else {
+    csr_spmv(lev.A, c, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i * nc + c];
+  }
+  for (int64_t i = 0; i < n; ++i) d[i] = r[i] / theta;
+  for (int k = 0; k < degree; ++k) {
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + d[i];
+    if (k == degree - 1) break;
+    csr_spmv(lev.A, c, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i * nc + c];
+    double rn = 1.0 / (2.0 * sigma - rho);
+    for (int64_t i = 0; i < n; ++i) d[i] = rn * rho * d[i] + 2.0 * rn / delta * r[i];
+    rho = rn;
+  }
+}
+
+void l1_jacobi(const Level& lev, int nc, int c, const vec& b, vec& x, int sweeps) {
+  int64_t n = lev.A.n;
+  vec Ax(n);
+  for (int it = 0; it < sweeps; ++it) {
+    csr_spmv(lev.A, c, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + (b[i] - Ax[i]) / lev.dl1[i * nc + c];
+  }
+}
+
+// V-cycle: pre-smoothing from x = 0, coarse correction x += P V(R r), post-smoothing
+void vcycle(const AMG& H, int l, int c, const vec& b, vec& x, const Smooth& sm) {
+  const Level& lev = H.L[l];
+  int64_t n = lev.A.n;
+  x.assign(n, 0.0);
+  if (lev.lu.size()) { lev.lu[c].solve(b.data(), x.data()); return; }
+  if (sm.kind == 0) l1_jacobi(lev, H.nc, c, b, x, sm.pre);
+  else chebyshev(lev, H.nc, c, b, x, sm.degree, sm.ratio, true);
+  vec Ax(n);
+  csr_spmv(lev.A, c, x.data(), Ax.data());
+  vec r(n);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - Ax[i];
+  vec bc(lev.R.n), xc;
+  csr_spmv(lev.R, c, r.data(), bc.data());
+  vcycle(H, l + 1, c, bc, xc, sm);
+  vec Pe(n);
+  csr_spmv(lev.P, c, xc.data(), Pe.data());
+  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + Pe[i];
+  if (sm.kind == 0) l1_jacobi(lev, H.nc, c, b, x, sm.post);
+  else chebyshev(lev, H.nc, c, b, x, sm.degree, sm.ratio, false);
+}
+
+inline void mul22(const double* a, const double* b, double* c) {
+  double c0 = a[0] * b[0] + a[1] * b[2], c1 = a[0] * b[1] + a[1] * b[3];
+  double c2 = a[2] * b[0] + a[3] * b[2], c3 = a[2] * b[1] + a[3] * b[3];
+  c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
+}
+inline void inv22(const double* a, double* r) {
+  double det = a[0] * a[3] - a[1] * a[2];
+  r[0] = a[3] / det; r[1] = -a[1] / det; r[2] = -a[2] / det; r[3] = a[0] / det;
+}
+
+BSR to_bsr(const or_system* s, int which) {
+  BSR A;
+  if (which == 0) { A.nbr = s->n_nodes; A.nbc = s->n_nodes; A.br = 3; A.bc = 3; }
+  if (which == 1) { A.nbr = s->n_nodes; A.nbc = s->n_cells; A.br = 3; A.bc = 2; }
+  if (which == 2) { A.nbr = s->n_cells; A.nbc = s->n_nodes; A.br = 2; A.bc = 3; }
+  if (which == 3) { A.nbr = s->n_cells; A.nbc = s->n_cells; A.br = 2; A.bc = 2; }
+  const int64_t* rp = which == 0 ? s->uu_rp : which == 1 ? s->uf_rp : which == 2 ? s->fu_rp : s->ff_rp;
+  const int32_t* ci = which == 0 ? s->uu_ci : which == 1 ? s->uf_ci : which == 2 ? s->fu_ci : s->ff_ci;
+  const double* v = which == 0 ? s->uu_v : which == 1 ? s->uf_v : which == 2 ? s->fu_v : s->ff_v;
+  A.rp.assign(rp, rp + A.nbr + 1);
+  A.ci.assign(ci, ci + A.rp[A.nbr]);
+  A.v.assign(v, v + A.rp[A.nbr] * A.br * A.bc);
+  return A;
+}
+
+void bsr_dense(const BSR& A, vec& d, int64_t r0, int64_t c0, int64_t ld) {
+  for (int64_t I = 0; I < A.nbr; ++I)
+    for (int64_t q = A.rp[I]; q < A.rp[I + 1]; ++q)
+      for (int a = 0; a < A.br; ++a)
+        for (int b = 0; b < A.bc; ++b)
+          d[(r0 + I * A.br + a) * ld + c0 + int64_t(A.ci[q]) * A.bc + b] = A.v[(q * A.br + a) * A.bc + b];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Preconditioner state
+// ---------------------------------------------------------------------------
+static Smooth smooth_of(const or_prec_params& pp) {
+  Smooth s;
+  s.kind = pp.smoother; s.pre = pp.pre; s.post = pp.post; s.degree = pp.cheb_degree; s.ratio = pp.cheb_ratio;
+  return s;
+}
+
+struct or_prec {
+  const or_system* s = nullptr;
+  or_prec_params pp;
+  BSR A_fu, A_ff, Sff;  // Sff = S_ff^(FS), §5.1
+  vec dss, dps;         // quasi-IMPES diagonals, §5.3
+  CSR spp;
+  AMG amg_u, amg_p;
+  BSR ilu;              // L (unit, strictly lower) and U (upper) blocks in the S_ff pattern
+  vec dinv;             // inv(U_ii)
+  DenseLU lu_uu, lu_flow, lu_local, lu_pp, lu_full;
+};
+
+extern "C" {
+
+uint64_t or_splitmix64(uint64_t state) { return sm64(state); }
+
+void or_correlated_field(uint64_t seed, int field, int nx, int ny, int nz, int Lx, int Ly, int Lz, double* out) {
+  vec f = correlated_field(seed, field, nx, ny, nz, Lx, Ly, Lz);
+  std::memcpy(out, f.data(), f.size() * sizeof(double));
+}
+
+void or_default_params(or_gen_params* gp, int config) {
+  std::memset(gp, 0, sizeof(*gp));
+  gp->h = 10.0;
+  gp->seed = 1000 + config;
+  gp->field_kind = config == 0 ? OR_FIELDS_LOGNORMAL : config == 2 ? OR_FIELDS_CHANNELS : OR_FIELDS_LAYERED;
+  if (config == 0) { gp->nx = 8; gp->ny = 8; gp->nz = 4; }
+  else if (config == 1) { gp->nx = 64; gp->ny = 64; gp->nz = 32; }
+  else if (config == 2) { gp->nx = 60; gp->ny = 220; gp->nz = 85; }
+  else { gp->nx = 16; gp->ny = 16; gp->nz = 8; }
+  gp->flags = OR_ALL;
+  gp->dt = 86400.0;
+  gp->biot = 0.8;
+  gp->c_w = gp->c_nw = gp->c_r = 1e-9;
+  gp->mu_w = 1e-3; gp->mu_nw = 5e-3;
+  gp->rho_w0 = 1035.0; gp->rho_nw0 = 863.0; gp->rho_s0 = 2650.0;
+  gp->s_wr = 0.2; gp->s_nwr = 0.2;
+  gp->grav = 9.81;
+  gp->p_ref = 20e6;
+  gp->dp_amp = 5e6;
+  gp->corey = 2.0;
+  gp->E0 = 1e10; gp->nu0 = 0.25; gp->kappa0 = 100.0 * kMilliDarcy; gp->phi0 = 0.2; gp->sw0 = 0.5;
+}
+
+int or_generate(const or_gen_params* gp, or_system** out) {
+  if (gp->nx < 1 || gp->ny < 1 || gp->nz < 1) return 1;
+  Grid g{gp->nx, gp->ny, gp->nz, gp->h};
+  Fields F = make_fields(*gp);
+  State st;
+  st.s = F.sw; st.p = F.p;
+  Jac J;
+  ExtraBC bc;
+  assemble(*gp, g, F, st, bc, J);
+  finalize(*gp, g, J, (gp->flags & OR_SCALE) != 0);
+  or_system* s = (or_system*)std::calloc(1, sizeof(or_system));
+  s->nx = g.nx; s->ny = g.ny; s->nz = g.nz; s->h = g.h;
+  s->n_nodes = g.nn(); s->n_cells = g.ncell();
+  s->n_u = 3 * s->n_nodes; s->n_f = 2 * s->n_cells; s->n = s->n_u + s->n_f;
+  s->nnzb_uu = J.uu.ci.size(); s->nnzb_uf = J.uf.ci.size(); s->nnzb_fu = J.fu.ci.size(); s->nnzb_ff = J.ff.ci.size();
+  s->uu_rp = dup(J.uu.rp); s->uu_ci = dup(J.uu.ci); s->uu_v = dup(J.uu.v);
+  s->uf_rp = dup(J.uf.rp); s->uf_ci = dup(J.uf.ci); s->uf_v = dup(J.uf.v);
+  s->fu_rp = dup(J.fu.rp); s->fu_ci = dup(J.fu.ci); s->fu_v = dup(J.fu.v);
+  s->ff_rp = dup(J.ff.rp); s->ff_ci = dup(J.ff.ci); s->ff_v = dup(J.ff.v);
+  s->d_fs = dup(J.dfs);
+  s->dirichlet = dup(J.dir);
+  vec rhs(s->n, 0.0);
+  for (int64_t r = 0; r < s->n; ++r) {
+    if (r < s->n_u && J.dir[r]) continue;
+    rhs[r] = 2.0 * unif(gp->seed, F_RHS, 0, uint64_t(r)) - 1.0;
+  }
+  s->rhs = dup(rhs);
+  s->alpha_u = J.alpha_u; s->alpha_f = J.alpha_f;
+  s->E = dup(F.E); s->nu = dup(F.nu); s->kh = dup(F.kh); s->kv = dup(F.kv);
+  s->phi0 = dup(F.phi0); s->sw = dup(F.sw); s->p = dup(F.p);
+  *out = s;
+  return 0;
+}
+
+void or_system_free(or_system* s) {
+  if (!s) return;
+  void* ptrs[] = {s->uu_rp, s->uu_ci, s->uu_v, s->uf_rp, s->uf_ci, s->uf_v, s->fu_rp, s->fu_ci, s->fu_v,
+                  s->ff_rp, s->ff_ci, s->ff_v, s->d_fs, s->dirichlet, s->rhs, s->E, s->nu, s->kh, s->kv,
+                  s->phi0, s->sw, s->p};
+  for (void* p : ptrs) std::free(p);
+  std::free(s);
+}
+
+void or_spmv(const or_system* s, const double* x, double* y) {
+  const double* xu = x;
+  const double* xf = x + s->n_u;
+  for (int64_t I = 0; I < s->n_nodes; ++I) {
+    double acc[3] = {0, 0, 0};
+    for (int64_t q = s->uu_rp[I]; q < s->uu_rp[I + 1]; ++q)
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) acc[d] += s->uu_v[q * 9 + d * 3 + e] * xu[3 * int64_t(s->uu_ci[q]) + e];
+    for (int64_t q = s->uf_rp[I]; q < s->uf_rp[I + 1]; ++q)
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 2; ++e) acc[d] += s->uf_v[q * 6 + d * 2 + e] * xf[2 * int64_t(s->uf_ci[q]) + e];
+    for (int d = 0; d < 3; ++d) y[3 * I + d] = acc[d];
+  }
+  for (int64_t c = 0; c < s->n_cells; ++c) {
+    double acc[2] = {0, 0};
+    for (int64_t q = s->fu_rp[c]; q < s->fu_rp[c + 1]; ++q)
+      for (int a = 0; a < 2; ++a)
+        for (int e = 0; e < 3; ++e) acc[a] += s->fu_v[q * 6 + a * 3 + e] * xu[3 * int64_t(s->fu_ci[q]) + e];
+    for (int64_t q = s->ff_rp[c]; q < s->ff_rp[c + 1]; ++q)
+      for (int a = 0; a < 2; ++a)
+        for (int e = 0; e < 2; ++e) acc[a] += s->ff_v[q * 4 + a * 2 + e] * xf[2 * int64_t(s->ff_ci[q]) + e];
+    y[s->n_u + 2 * c] = acc[0];
+    y[s->n_u + 2 * c + 1] = acc[1];
+  }
+}
+
+void or_ref_integrals(double h, double* G, double* IN, double* IdN, double* INdN) {
+  RefInt R = ref_integrals(h);
+  std::memcpy(G, R.G, sizeof(R.G));
+  std::memcpy(IN, R.IN, sizeof(R.IN));
+  std::memcpy(IdN, R.IdN, sizeof(R.IdN));
+  std::memcpy(INdN, R.INdN, sizeof(R.INdN));
+}
+
+}  // extern "C"
+
+namespace {
+// Residual of the discrete weak form, Eq. (5a)-(5c) with the App. B element and
+// face contributions, at x_n = (u, s, p); the previous level is `prev`.  The
+// face term carries the sign under which its derivative is the App. B face
+// Jacobian (Dt sum_f [[psi]] F).
+void residual(const or_gen_params& gp, const Grid& g, const Fields& F, const State& prev, const State& x,
+              const ExtraBC& bc, vec& r) {
+  RefInt R = ref_integrals(g.h);
+  int64_t nn = g.nn(), nc = g.ncell();
+  r.assign(3 * nn + 2 * nc, 0.0);
+  double grav = (gp.flags & OR_GRAVITY) ? gp.grav : 0.0;
+  double V = g.h * g.h * g.h;
+  double b = gp.biot;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        int64_t c = g.cell(i, j, k);
+        int64_t nodes[8];
+        for (int a = 0; a < 8; ++a) nodes[a] = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+        Mat m0 = material(gp, F.E[c], F.nu[c], F.phi0[c], x.s[c], x.p[c], 0.0);
+        double s = x.s[c], p = x.p[c];
+        double int_ev = 0.0;
+        for (int q = 0; q < 8; ++q) {
+          double gu[3][3] = {{0}};
+          for (int a = 0; a < 8; ++a)
+            for (int d = 0; d < 3; ++d)
+              for (int e = 0; e < 3; ++e) gu[d][e] += x.u[3 * nodes[a] + d] * R.gp_dN[q][a][e];
+          double ev = gu[0][0] + gu[1][1] + gu[2][2];
+          int_ev += R.gp_w * ev;
+          double sig[3][3];
+          for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e)
+              sig[d][e] = m0.lam * ev * (d == e) + m0.G * (gu[d][e] + gu[e][d]);
+          double phi = F.phi0[c] + b * ev + m0.dphidp * (p - gp.p_ref);
+          double rho = (1.0 - phi) * m0.rs + phi * (s * m0.rw + (1.0 - s) * m0.rnw);
+          for (int a = 0; a < 8; ++a)
+            for (int d = 0; d < 3; ++d) {
+              double v = 0.0;
+              for (int e = 0; e < 3; ++e) v += sig[d][e] * R.gp_dN[q][a][e];
+              v -= R.gp_dN[q][a][d] * b * p;
+              double gd = d == 2 ? -grav : 0.0;
+              v -= R.gp_N[q][a] * rho * gd;
+              r[3 * nodes[a] + d] += R.gp_w * v;
+            }
+        }
+        if (gp.flags & OR_ACCUM) {
+          // int_K phi rho_l s_l, phi linear in the pointwise volumetric strain
+          double phiV = V * (F.phi0[c] + m0.dphidp * (p - gp.p_ref)) + b * int_ev;
+          Mat mp = material(gp, F.E[c], F.nu[c], F.phi0[c], prev.s[c], prev.p[c], 0.0);
+          double int_evp = 0.0;  // int_K eps_v of the previous displacement
+          for (int a = 0; a < 8; ++a)
+            for (int d = 0; d < 3; ++d) int_evp += R.IdN[a][d] * prev.u[3 * nodes[a] + d];
+          double phiVp = V * (F.phi0[c] + mp.dphidp * (prev.p[c] - gp.p_ref)) + b * int_evp;
+          r[3 * nn + 2 * c] += phiV * m0.rw * s - phiVp * mp.rw * prev.s[c];
+          r[3 * nn + 2 * c + 1] += phiV * m0.rnw * (1.0 - s) - phiVp * mp.rnw * (1.0 - prev.s[c]);
+        }
+      }
+  if (bc.active && bc.sigma_top != 0.0) {
+    // - int eta . tbar, tbar = (0,0,-sigma) on the top face: +sigma h^2/4 per node
+    // each top face contributes sigma * h^2/4 to each of its four nodes
+    for (int j = 0; j <= g.ny; ++j)
+      for (int i = 0; i <= g.nx; ++i) {
+        double fx = (i == 0 || i == g.nx) ? 1.0 : 2.0, fy = (j == 0 || j == g.ny) ? 1.0 : 2.0;
+        r[3 * g.node(i, j, g.nz) + 2] += bc.sigma_top * g.h * g.h / 4.0 * fx * fy;
+      }
+  }
+  if (gp.flags & OR_FLUX) {
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          int64_t K = g.cell(i, j, k);
+          for (int dir = 0; dir < 3; ++dir) {
+            int a = i + (dir == 0), b2 = j + (dir == 1), c2 = k + (dir == 2);
+            if (a >= g.nx || b2 >= g.ny || c2 >= g.nz) continue;
+            int64_t L = g.cell(a, b2, c2);
+            double kK = dir == 2 ? F.kv[K] : F.kh[K], kL = dir == 2 ? F.kv[L] : F.kh[L];
+            double UK = g.h * g.h * kK / (0.5 * g.h), UL = g.h * g.h * kL / (0.5 * g.h);
+            double Ups = UK * UL / (UK + UL);
+            double dz = dir == 2 ? g.h : 0.0;
+            for (int ph = 0; ph < 2; ++ph) {
+              FaceFlux f = face_flux(gp, Ups, dz, grav, ph, x.s[K], x.p[K], x.s[L], x.p[L], false);
+              r[3 * nn + 2 * K + ph] += -gp.dt * f.F;
+              r[3 * nn + 2 * L + ph] += gp.dt * f.F;
+            }
+          }
+        }
+    if (bc.active && bc.top_drained)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          int64_t K = g.cell(i, j, g.nz - 1);
+          double Ups = g.h * g.h * F.kv[K] / (0.5 * g.h);
+          for (int ph = 0; ph < 2; ++ph) {
+            FaceFlux f = face_flux(gp, Ups, 0.5 * g.h, grav, ph, x.s[K], x.p[K], bc.s_top, bc.p_top, true);
+            r[3 * nn + 2 * K + ph] += -gp.dt * f.F;
+          }
+        }
+  }
+}
+
+void full_dense(const or_system* s, vec& d) {
+  int64_t n = s->n;
+  d.assign(size_t(n) * n, 0.0);
+  bsr_dense(to_bsr(s, 0), d, 0, 0, n);
+  bsr_dense(to_bsr(s, 1), d, 0, s->n_u, n);
+  bsr_dense(to_bsr(s, 2), d, s->n_u, 0, n);
+  bsr_dense(to_bsr(s, 3), d, s->n_u, s->n_u, n);
+}
+
+typedef std::function<void(const double*, double*)> Op;
+
+// Flexible GMRES(m), right preconditioned (§4), modified Gram-Schmidt,
+// Givens rotations, restart from the current iterate, x0 = 0.
+void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, double tol, int m, int maxit,
+            or_stats* st) {
+  std::memset(st, 0, sizeof(*st));
+  double bn = 0.0;
+  for (int64_t i = 0; i < n; ++i) bn += b[i] * b[i];
+  bn = std::sqrt(bn);
+  for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  if (bn == 0.0) { st->converged = 1; return; }
+  vec r(b, b + n), w(n);
+  int total = 0;
+  for (;;) {
+    double beta = 0.0;
+    for (int64_t i = 0; i < n; ++i) beta += r[i] * r[i];
+    beta = std::sqrt(beta);
+    std::vector<vec> V, Z;
+    V.emplace_back(n);
+    for (int64_t i = 0; i < n; ++i) V[0][i] = r[i] / beta;
+    vec H(size_t(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+    g[0] = beta;
+    int jend = -1;
+    bool brk = false;
+    for (int j = 0; j < m; ++j) {
+      Z.emplace_back(n);
+      M(V[j].data(), Z[j].data());
+      A(Z[j].data(), w.data());
+      for (int i = 0; i <= j; ++i) {
+        double h = 0.0;
+        for (int64_t e = 0; e < n; ++e) h += w[e] * V[i][e];
+        H[i * m + j] = h;
+        for (int64_t e = 0; e < n; ++e) w[e] -= h * V[i][e];
+      }
+      double hn = 0.0;
+      for (int64_t e = 0; e < n; ++e) hn += w[e] * w[e];
+      hn = std::sqrt(hn);
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[j * m + j], c = H[(j + 1) * m + j];
+      double rr = std::hypot(a, c);
+      cs[j] = a / rr; sn[j] = c / rr;
+      H[j * m + j] = rr; H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      st->est_relres = std::fabs(g[j + 1]) / bn;
+      jend = j;
+      if (!(hn > 1e-300)) brk = true;
+      if (st->est_relres <= tol || brk || total >= maxit || j == m - 1) break;
+      V.emplace_back(n);
+      for (int64_t e = 0; e < n; ++e) V[j + 1][e] = w[e] / hn;
+    }
+    vec y(jend + 1);
+    for (int i = jend; i >= 0; --i) {
+      double s = g[i];
+      for (int k2 = i + 1; k2 <= jend; ++k2) s -= H[i * m + k2] * y[k2];
+      y[i] = s / H[i * m + i];
+    }
+    for (int i = 0; i <= jend; ++i)
+      for (int64_t e = 0; e < n; ++e) x[e] += y[i] * Z[i][e];
+    A(x, w.data());
+    double rn = 0.0;
+    for (int64_t e = 0; e < n; ++e) { r[e] = b[e] - w[e]; rn += r[e] * r[e]; }
+    st->true_relres = std::sqrt(rn) / bn;
+    st->iters = total;
+    if (std::isnan(st->true_relres)) return;
+    if (st->true_relres <= tol) { st->converged = 1; return; }
+    if (brk) { st->breakdown = 1; return; }
+    if (total >= maxit) return;
+    st->restarts++;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int or_residual(const or_gen_params* gp, const double* dx, double* r) {
+  Grid g{gp->nx, gp->ny, gp->nz, gp->h};
+  Fields F = make_fields(*gp);
+  State prev;
+  prev.u.assign(3 * g.nn(), 0.0); prev.s = F.sw; prev.p = F.p;
+  State x = prev;
+  int64_t nu = 3 * g.nn();
+  for (int64_t i = 0; i < nu; ++i) x.u[i] += dx[i];
+  for (int64_t c = 0; c < g.ncell(); ++c) { x.s[c] += dx[nu + 2 * c]; x.p[c] += dx[nu + 2 * c + 1]; }
+  vec rv;
+  ExtraBC bc;
+  residual(*gp, g, F, prev, x, bc, rv);
+  std::memcpy(r, rv.data(), rv.size() * sizeof(double));
+  return 0;
+}
+
+void or_default_prec_params(or_prec_params* pp) {
+  std::memset(pp, 0, sizeof(*pp));
+  pp->theta_u = 0.08; pp->theta_p = 0.08;
+  pp->coarse_max_u = 500; pp->coarse_max_p = 500;
+  pp->max_levels = 25;
+  pp->pre = 1; pp->post = 1;
+  pp->smoother = 1; pp->cheb_degree = 2; pp->cheb_ratio = 20.0;
+}
+
+int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
+  or_prec* P = new or_prec();
+  P->s = s; P->pp = *pp;
+  int64_t nc = s->n_cells, nn = s->n_nodes;
+  P->A_fu = to_bsr(s, 2);
+  P->A_ff = to_bsr(s, 3);
+  BSR Auu = to_bsr(s, 0);
+  // §5.1, fixed-stress Schur approximation: S_ff^(FS) = A_ff + blockdiag([[0, D_sp],[0, D_pp]])
+  P->Sff = P->A_ff;
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t q = P->Sff.find(c, c);
+    P->Sff.v[q * 4 + 1] = P->Sff.v[q * 4 + 1] + s->d_fs[2 * c];
+    P->Sff.v[q * 4 + 3] = P->Sff.v[q * 4 + 3] + s->d_fs[2 * c + 1];
+  }
+  // §5.3 quasi-IMPES: D_ss = diagm(A_ss), D_ps = diagm(A_ps);
+  // S_pp = A_pp^(FS) - D_ps D_ss^{-1} A_sp^(FS)
+  P->dss.resize(nc); P->dps.resize(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t q = P->A_ff.find(c, c);
+    P->dss[c] = P->A_ff.v[q * 4 + 0];
+    P->dps[c] = P->A_ff.v[q * 4 + 2];
+  }
+  P->spp.n = P->spp.m = nc; P->spp.nc = 1;
+  P->spp.rp = P->Sff.rp; P->spp.ci = P->Sff.ci;
+  P->spp.v.resize(P->Sff.ci.size());
+  for (int64_t c = 0; c < nc; ++c) {
+    double ratio = P->dps[c] / P->dss[c];
+    for (int64_t q = P->Sff.rp[c]; q < P->Sff.rp[c + 1]; ++q)
+      P->spp.v[q] = P->Sff.v[q * 4 + 3] - ratio * P->Sff.v[q * 4 + 1];
+  }
+  // §5.2: M_uu = amg(A_uu^(SDC)), three displacement components, shared aggregates
+  if (pp->mech_mode == OR_MECH_AMG) {
+    CSR A0; A0.n = A0.m = nn; A0.nc = 3; A0.rp = Auu.rp; A0.ci = Auu.ci;
+    A0.v.resize(Auu.ci.size() * 3);
+    for (size_t q = 0; q < Auu.ci.size(); ++q)
+      for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = Auu.v[q * 9 + d * 4];
+    if (!build_amg(P->amg_u, std::move(A0), pp->theta_u, pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
+  } else {
+    vec d(size_t(s->n_u) * s->n_u, 0.0);
+    bsr_dense(Auu, d, 0, 0, s->n_u);
+    P->lu_uu.factor(s->n_u, std::move(d));
+  }
+  if (pp->press_mode == OR_PRESS_AMG) {
+    if (!build_amg(P->amg_p, P->spp, pp->theta_p, pp->coarse_max_p, pp->max_levels)) { delete P; return 2; }
+  } else {
+    vec d(size_t(nc) * nc, 0.0);
+    for (int64_t i = 0; i < nc; ++i)
+      for (int64_t q = P->spp.rp[i]; q < P->spp.rp[i + 1]; ++q) d[i * nc + P->spp.ci[q]] = P->spp.v[q];
+    P->lu_pp.factor(nc, std::move(d));
+  }
+  // §5.3 option 2: block ILU(0) of the interleaved S_ff^(FS), natural cell order (IKJ)
+  P->ilu = P->Sff;
+  P->dinv.assign(4 * nc, 0.0);
+  for (int64_t i = 0; i < nc; ++i) {
+    for (int64_t qk = P->ilu.rp[i]; qk < P->ilu.rp[i + 1]; ++qk) {
+      int64_t k = P->ilu.ci[qk];
+      if (k >= i) break;
+      double L[4];
+      mul22(&P->ilu.v[qk * 4], &P->dinv[4 * k], L);
+      std::memcpy(&P->ilu.v[qk * 4], L, sizeof(L));
+      for (int64_t qj = qk + 1; qj < P->ilu.rp[i + 1]; ++qj) {
+        int64_t jj = P->ilu.ci[qj];
+        int64_t qkj = P->ilu.find(k, jj);
+        if (qkj < 0) continue;
+        double t[4];
+        mul22(L, &P->ilu.v[qkj * 4], t);
+        for (int e = 0; e < 4; ++e) P->ilu.v[qj * 4 + e] -= t[e];
+      }
+    }
+    inv22(&P->ilu.v[P->ilu.find(i, i) * 4], &P->dinv[4 * i]);
+  }
+  if (pp->flow_mode == OR_FLOW_EXACT_FS || pp->local_mode == OR_LOCAL_EXACT) {
+    vec d(size_t(s->n_f) * s->n_f, 0.0);
+    bsr_dense(P->Sff, d, 0, 0, s->n_f);
+    if (pp->flow_mode == OR_FLOW_EXACT_FS) P->lu_flow.factor(s->n_f, d);
+    if (pp->local_mode == OR_LOCAL_EXACT) P->lu_local.factor(s->n_f, d);
+  }
+  if (pp->flow_mode == OR_FLOW_EXACT_SCHUR) {
+    // S_ff = A_ff - A_fu A_uu^{-1} A_uf (Eq. (LU) of §5.1), dense
+    int64_t nu = s->n_u, nf = s->n_f;
+    vec duu(size_t(nu) * nu, 0.0), duf(size_t(nu) * nf, 0.0), dfu(size_t(nf) * nu, 0.0), dff(size_t(nf) * nf, 0.0);
+    bsr_dense(Auu, duu, 0, 0, nu);
+    bsr_dense(to_bsr(s, 1), duf, 0, 0, nf);
+    bsr_dense(P->A_fu, dfu, 0, 0, nu);
+    bsr_dense(P->A_ff, dff, 0, 0, nf);
+    DenseLU lu; lu.factor(nu, duu);
+    vec col(nu), xs(nu);
+    for (int64_t j = 0; j < nf; ++j) {
+      for (int64_t i = 0; i < nu; ++i) col[i] = duf[i * nf + j];
+      lu.solve(col.data(), xs.data());
+      for (int64_t i = 0; i < nf; ++i) {
+        double t = 0.0;
+        for (int64_t k = 0; k < nu; ++k) t += dfu[i * nu + k] * xs[k];
+        dff[i * nf + j] -= t;
+      }
+    }
+    P->lu_flow.factor(nf, std::move(dff));
+  }
+  if (pp->full_exact) {
+    vec d; full_dense(s, d);
+    P->lu_full.factor(s->n, std::move(d));
+  }
+  *out = P;
+  return 0;
+}
+
+void or_prec_free(or_prec* p) { delete p; }
+
+int or_ilu_apply(const or_prec* P, const double* w, double* dz) {
+  int64_t nc = P->s->n_cells;
+  vec y(2 * nc);
+  for (int64_t i = 0; i < nc; ++i) {
+    double a0 = w[2 * i], a1 = w[2 * i + 1];
+    for (int64_t q = P->ilu.rp[i]; q < P->ilu.rp[i + 1]; ++q) {
+      int64_t k = P->ilu.ci[q];
+      if (k >= i) break;
+      const double* L = &P->ilu.v[q * 4];
+      a0 -= L[0] * y[2 * k] + L[1] * y[2 * k + 1];
+      a1 -= L[2] * y[2 * k] + L[3] * y[2 * k + 1];
+    }
+    y[2 * i] = a0; y[2 * i + 1] = a1;
+  }
+  for (int64_t i = nc - 1; i >= 0; --i) {
+    double a0 = y[2 * i], a1 = y[2 * i + 1];
+    for (int64_t q = P->ilu.rp[i]; q < P->ilu.rp[i + 1]; ++q) {
+      int64_t j = P->ilu.ci[q];
+      if (j <= i) continue;
+      const double* U = &P->ilu.v[q * 4];
+      a0 -= U[0] * dz[2 * j] + U[1] * dz[2 * j + 1];
+      a1 -= U[2] * dz[2 * j] + U[3] * dz[2 * j + 1];
+    }
+    const double* D = &P->dinv[4 * i];
+    dz[2 * i] = D[0] * a0 + D[1] * a1;
+    dz[2 * i + 1] = D[2] * a0 + D[3] * a1;
+  }
+  return 0;
+}
+
+// Algorithm 1: z = M^{-1} v
+void or_prec_apply(or_prec* P, const double* v, double* z) {
+  const or_system* s = P->s;
+  int64_t nn = s->n_nodes, nc = s->n_cells, nu = s->n_u, nf = s->n_f;
+  if (P->pp.full_exact) { P->lu_full.solve(v, z); return; }
+  // step 1: z_u = M_uu^{-1} v_u
+  vec zu(nu);
+  if (P->pp.mech_mode == OR_MECH_AMG) {
+    for (int c = 0; c < 3; ++c) {
+      vec b(nn), x;
+      for (int64_t I = 0; I < nn; ++I) b[I] = v[3 * I + c];
+      vcycle(P->amg_u, 0, c, b, x, smooth_of(P->pp));
+      for (int64_t I = 0; I < nn; ++I) zu[3 * I + c] = x[I];
+    }
+  } else {
+    P->lu_uu.solve(v, zu.data());
+  }
+  // step 2: y_f = v_f - A_fu z_u
+  vec yf(nf);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int a = 0; a < 2; ++a) {
+      double acc = 0.0;
+      for (int64_t q = P->A_fu.rp[c]; q < P->A_fu.rp[c + 1]; ++q)
+        for (int e = 0; e < 3; ++e) acc += P->A_fu.v[q * 6 + a * 3 + e] * zu[3 * int64_t(P->A_fu.ci[q]) + e];
+      yf[2 * c + a] = v[nu + 2 * c + a] - acc;
+    }
+  vec zf(nf);
+  if (P->pp.flow_mode != OR_FLOW_CPR) {
+    P->lu_flow.solve(yf.data(), zf.data());
+  } else {
+    // step 3: z_s = D_ss^{-1} y_s
+    vec zs(nc), wp(nc), zp(nc);
+    for (int64_t c = 0; c < nc; ++c) zs[c] = yf[2 * c] / P->dss[c];
+    // step 4: w_p = y_p - A_ps z_s (complete A_ps)
+    for (int64_t c = 0; c < nc; ++c) {
+      double acc = 0.0;
+      for (int64_t q = P->A_ff.rp[c]; q < P->A_ff.rp[c + 1]; ++q) acc += P->A_ff.v[q * 4 + 2] * zs[P->A_ff.ci[q]];
+      wp[c] = yf[2 * c + 1] - acc;
+    }
+    // step 5: z_p = M_pp^{-1} w_p
+    if (P->pp.press_mode == OR_PRESS_AMG) {
+      vec x;
+      vcycle(P->amg_p, 0, 0, wp, x, smooth_of(P->pp));
+      zp = x;
+    } else {
+      P->lu_pp.solve(wp.data(), zp.data());
+    }
+    for (int64_t c = 0; c < nc; ++c) { zf[2 * c] = zs[c]; zf[2 * c + 1] = zp[c]; }
+    // step 6: w_f = y_f - S_ff^(FS) z_f
+    vec wf(nf);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int a = 0; a < 2; ++a) {
+        double acc = 0.0;
+        for (int64_t q = P->Sff.rp[c]; q < P->Sff.rp[c + 1]; ++q)
+          for (int e = 0; e < 2; ++e) acc += P->Sff.v[q * 4 + a * 2 + e] * zf[2 * int64_t(P->Sff.ci[q]) + e];
+        wf[2 * c + a] = yf[2 * c + a] - acc;
+      }
+    // step 7: dz_f = M_L^{-1} w_f
+    vec dz(nf);
+    if (P->pp.local_mode == OR_LOCAL_ILU0) or_ilu_apply(P, wf.data(), dz.data());
+    else P->lu_local.solve(wf.data(), dz.data());
+    // step 8: z_f += dz_f
+    for (int64_t e = 0; e < nf; ++e) zf[e] += dz[e];
+  }
+  for (int64_t e = 0; e < nu; ++e) z[e] = zu[e];
+  for (int64_t e = 0; e < nf; ++e) z[nu + e] = zf[e];
+}
+
+static const AMG* pick(const or_prec* p, int which) { return which == 0 ? &p->amg_u : &p->amg_p; }
+
+int or_amg_nlevels(const or_prec* p, int which) { return int(pick(p, which)->L.size()); }
+int64_t or_amg_level_n(const or_prec* p, int which, int level) { return pick(p, which)->L[level].A.n; }
+int64_t or_amg_level_nnz(const or_prec* p, int which, int level) { return pick(p, which)->L[level].A.nnz(); }
+int or_amg_level_matrix(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v) {
+  const CSR& A = pick(p, which)->L[level].A;
+  std::memcpy(rp, A.rp.data(), A.rp.size() * sizeof(int64_t));
+  std::memcpy(ci, A.ci.data(), A.ci.size() * sizeof(int32_t));
+  std::memcpy(v, A.v.data(), A.v.size() * sizeof(double));
+  return 0;
+}
+int64_t or_amg_aggregates(const or_prec* p, int which, int level, int32_t* agg) {
+  const Level& L = pick(p, which)->L[level];
+  if (!L.agg.empty()) std::memcpy(agg, L.agg.data(), L.agg.size() * sizeof(int32_t));
+  return L.nagg;
+}
+int64_t or_amg_roots(const or_prec* p, int which, int level, uint8_t* root) {
+  const Level& L = pick(p, which)->L[level];
+  if (!L.root.empty()) std::memcpy(root, L.root.data(), L.root.size());
+  return int64_t(L.root.size());
+}
+int64_t or_amg_p_nnz(const or_prec* p, int which, int level) { return pick(p, which)->L[level].P.nnz(); }
+int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v) {
+  const CSR& A = pick(p, which)->L[level].P;
+  std::memcpy(rp, A.rp.data(), A.rp.size() * sizeof(int64_t));
+  std::memcpy(ci, A.ci.data(), A.ci.size() * sizeof(int32_t));
+  std::memcpy(v, A.v.data(), A.v.size() * sizeof(double));
+  return 0;
+}
+int or_amg_vcycle(const or_prec* p, int which, int comp, const double* b, double* x) {
+  const AMG* H = pick(p, which);
+  vec bb(b, b + H->L[0].A.n), xx;
+  vcycle(*H, 0, comp, bb, xx, smooth_of(p->pp));
+  std::memcpy(x, xx.data(), xx.size() * sizeof(double));
+  return 0;
+}
+int64_t or_spp_nnz(const or_prec* p) { return p->spp.nnz(); }
+int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v) {
+  std::memcpy(rp, p->spp.rp.data(), p->spp.rp.size() * sizeof(int64_t));
+  std::memcpy(ci, p->spp.ci.data(), p->spp.ci.size() * sizeof(int32_t));
+  std::memcpy(v, p->spp.v.data(), p->spp.v.size() * sizeof(double));
+  return 0;
+}
+int or_ilu_dinv(const or_prec* p, double* dinv) {
+  std::memcpy(dinv, p->dinv.data(), p->dinv.size() * sizeof(double));
+  return 0;
+}
+
+int or_fgmres(const or_system* s, or_prec* p, const double* b, double* x, double tol, int restart, int max_iters,
+              or_stats* st) {
+  Op A = [s](const double* in, double* out) { or_spmv(s, in, out); };
+  Op M = [p](const double* in, double* out) { or_prec_apply(p, in, out); };
+  fgmres(s->n, A, M, b, x, tol, restart, max_iters, st);
+  return st->converged ? 0 : 4;
+}
+
+int or_fgmres_diag(int64_t n, const double* diag, const double* b, double* x, double tol, int restart,
+                   int max_iters, or_stats* st) {
+  Op A = [n, diag](const double* in, double* out) { for (int64_t i = 0; i < n; ++i) out[i] = diag[i] * in[i]; };
+  Op M = [n](const double* in, double* out) { for (int64_t i = 0; i < n; ++i) out[i] = in[i]; };
+  fgmres(n, A, M, b, x, tol, restart, max_iters, st);
+  return st->converged ? 0 : 4;
+}
+
+int or_dense_solve(const or_system* s, const double* b, double* x) {
+  if (s->n > 6000) return 1;
+  vec d; full_dense(s, d);
+  DenseLU lu; lu.factor(s->n, std::move(d));
+  if (!lu.ok) return 3;
+  lu.solve(b, x);
+  return 0;
+}
+
+int or_lu_solve(int64_t n, double* a, const double* b, double* x) {
+  DenseLU lu; lu.factor(n, vec(a, a + size_t(n) * n));
+  if (!lu.ok) return 3;
+  lu.solve(b, x);
+  return 0;
+}
+
+// Terzaghi column: homogeneous medium, identical phases, Corey exponent 1,
+// no gravity, incompressible fluids, drained top, rollers, fixed base.
+int or_terzaghi(const or_terzaghi_params* tp, double* tout, double* pout, double* p0out, double* cvout,
+                double* newton_ratio) {
+  or_gen_params gp;
+  or_default_params(&gp, 0);
+  gp.nx = 1; gp.ny = 1; gp.nz = tp->nz; gp.h = tp->h;
+  gp.field_kind = OR_FIELDS_HOMOGENEOUS;
+  gp.flags = OR_ACCUM | OR_FLUX | OR_FLUX_SAT | OR_COUPLING;
+  gp.biot = tp->biot;
+  gp.c_w = gp.c_nw = gp.c_r = 0.0;
+  gp.mu_w = gp.mu_nw = tp->mu;
+  gp.rho_w0 = gp.rho_nw0 = tp->rho0;
+  gp.s_wr = gp.s_nwr = 0.0;
+  gp.corey = 1.0;
+  gp.p_ref = 0.0; gp.dp_amp = 0.0;
+  gp.E0 = tp->E; gp.nu0 = tp->nu; gp.kappa0 = tp->kappa; gp.phi0 = tp->phi0; gp.sw0 = 0.5;
+  Grid g{1, 1, tp->nz, tp->h};
+  Fields F = make_fields(gp);
+  ExtraBC bc;
+  bc.active = true;
+  bc.dir_u.assign(3 * g.nn(), 0);
+  for (int k = 0; k <= g.nz; ++k)
+    for (int j = 0; j <= 1; ++j)
+      for (int i = 0; i <= 1; ++i) {
+        int64_t I = g.node(i, j, k);
+        bc.dir_u[3 * I + 0] = 1; bc.dir_u[3 * I + 1] = 1;
+        if (k == 0) bc.dir_u[3 * I + 2] = 1;
+      }
+  bc.sigma_top = tp->sigma0;
+  bc.top_drained = true;
+  bc.p_top = 0.0; bc.s_top = 0.5;
+  int64_t nu = 3 * g.nn(), nc = g.ncell(), n = nu + 2 * nc;
+  State prev;
+  prev.u.assign(nu, 0.0); prev.s.assign(nc, 0.5); prev.p.assign(nc, 0.0);
+  double worst = 0.0, first_rn = -1.0;
+  auto step = [&](double dt, State& x) {
+    or_gen_params q = gp;
+    q.dt = dt;
+    x = prev;
+    for (int it = 0; it < 4; ++it) {
+      vec r;
+      residual(q, g, F, prev, x, bc, r);
+      Jac J;
+      assemble(q, g, F, x, bc, J);
+      finalize(q, g, J, false);
+      for (int64_t i = 0; i < nu; ++i) if (bc.dir_u[i]) r[i] = 0.0;
+      double rn = 0.0;
+      for (double v : r) rn += v * v;
+      rn = std::sqrt(rn);
+      or_system tmp;
+      std::memset(&tmp, 0, sizeof(tmp));
+      tmp.n_nodes = g.nn(); tmp.n_cells = nc; tmp.n_u = nu; tmp.n_f = 2 * nc; tmp.n = n;
+      tmp.uu_rp = J.uu.rp.data(); tmp.uu_ci = J.uu.ci.data(); tmp.uu_v = J.uu.v.data();
+      tmp.uf_rp = J.uf.rp.data(); tmp.uf_ci = J.uf.ci.data(); tmp.uf_v = J.uf.v.data();
+      tmp.fu_rp = J.fu.rp.data(); tmp.fu_ci = J.fu.ci.data(); tmp.fu_v = J.fu.v.data();
+      tmp.ff_rp = J.ff.rp.data(); tmp.ff_ci = J.ff.ci.data(); tmp.ff_v = J.ff.v.data();
+      vec d; full_dense(&tmp, d);
+      DenseLU lu; lu.factor(n, std::move(d));
+      vec mr(n), dx(n);
+      for (int64_t i = 0; i < n; ++i) mr[i] = -r[i];
+      lu.solve(mr.data(), dx.data());
+      for (int64_t i = 0; i < nu; ++i) x.u[i] += dx[i];
+      for (int64_t c = 0; c < nc; ++c) { x.s[c] += dx[nu + 2 * c]; x.p[c] += dx[nu + 2 * c + 1]; }
+      vec r2;
+      residual(q, g, F, prev, x, bc, r2);
+      for (int64_t i = 0; i < nu; ++i) if (bc.dir_u[i]) r2[i] = 0.0;
+      double rn2 = 0.0;
+      for (double v : r2) rn2 += v * v;
+      rn2 = std::sqrt(rn2);
+      // one-step Newton contraction, on steps whose starting residual is well above round-off
+      if (it == 0 && rn > 0.0) {
+        if (first_rn < 0.0) first_rn = rn;
+        if (rn >= 1e-3 * first_rn) worst = std::max(worst, rn2 / rn);
+      }
+      if (rn2 <= 1e-13 * rn) break;
+    }
+  };
+  // undrained loading: no drainage during the instantaneous step
+  State x;
+  {
+    or_gen_params saved = gp;
+    gp.flags = OR_ACCUM | OR_COUPLING;
+    step(1.0, x);
+    gp = saved;
+    first_rn = -1.0;
+  }
+  double p0 = 0.0;
+  for (int64_t c = 0; c < nc; ++c) p0 += x.p[c];
+  *p0out = p0 / double(nc);
+  prev = x;
+  Mat m = material(gp, tp->E, tp->nu, tp->phi0, 0.5, 0.0, 0.0);
+  double Kv = m.Kdr + 4.0 * m.G / 3.0;
+  double S = m.dphidp;
+  *cvout = (tp->kappa / tp->mu) / (S + tp->biot * tp->biot / Kv);
+  for (int n_ = 0; n_ < tp->nsteps; ++n_) {
+    step(tp->dt, x);
+    prev = x;
+    tout[n_] = (n_ + 1) * tp->dt;
+    for (int64_t c = 0; c < nc; ++c) pout[int64_t(n_) * nc + c] = x.p[c];
+  }
+  *newton_ratio = worst;
+  return 0;
+}
+
+}  // extern "C"
