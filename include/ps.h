@@ -1,0 +1,196 @@
+/*
+ * ps.h -- C ABI of the GB300 solver for one linearised fully-implicit
+ * multiphase-poromechanics Jacobian (White, Castelletto, Klevtsov, Bui,
+ * Osei-Kuffuor, Tchelepi, "A two-stage preconditioner for multiphase
+ * poromechanics in reservoir simulation", arXiv 1812.05540).
+ *
+ * Problem (§4): solve A dx = b, A = [[A_uu, A_uf], [A_fu, A_ff]] (Eq. (jac_system)
+ * regrouped as in §5.1), with right-preconditioned flexible GMRES under the
+ * block-triangular preconditioner of §5.1 (Eq. (blk_tr_prec)) whose mechanics
+ * stage is an AMG V-cycle on the separate-displacement-component block (§5.2)
+ * and whose flow stage is the CPR two-stage operator of §5.3 (quasi-IMPES
+ * pressure AMG followed by block ILU(0)), applied by Algorithm 1.  The solver
+ * runs in two phases, setup then iterate, as §5.4 describes.
+ *
+ * Unknown ordering: x = [u (3 per node, node-major, components x,y,z);
+ * f (2 per cell, interleaved (s, p))] -- the interleaved flow ordering of the
+ * permutation P in §5.3.  Node id = i + (nx+1)(j + (ny+1)k), cell id =
+ * i + nx(j + ny k), k = 0 at the bottom.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are device pointers unless ps_params.host_ptrs = 1 (then every
+ *    array in ps_jacobian, rhs and x is a host pointer and the library copies).
+ *  - The caller owns every pointer it passes; the library owns every handle.
+ *  - All device work is enqueued on ps_params.stream (NULL = legacy stream);
+ *    ps_setup and ps_solve synchronise that stream before returning.
+ *  - Functions return ps_status and never abort; no device assert or trap is
+ *    used.  The handle stays valid after PS_ERR_NOT_CONVERGED, PS_ERR_NAN and
+ *    PS_ERR_TIMEOUT.  Not thread-safe per handle.
+ */
+#ifndef PS_H
+#define PS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID = 1,        /* bad argument, shape or pattern */
+  PS_ERR_OOM = 2,            /* device allocation failed */
+  PS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  PS_ERR_NOT_CONVERGED = 4,  /* max_iters reached; x holds the last iterate */
+  PS_ERR_BREAKDOWN = 5,      /* Krylov breakdown before convergence */
+  PS_ERR_NAN = 6,            /* NaN/Inf in the residual or the Hessenberg */
+  PS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  PS_ERR_BUDGET = 8          /* the handle would exceed ps_params.hbm_budget */
+} ps_status;
+
+enum { PS_FP64 = 0, PS_MIXED_FP32 = 1 };     /* preconditioner precision */
+enum { PS_SMOOTH_L1JACOBI = 0, PS_SMOOTH_CHEBYSHEV = 1 };
+enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
+
+/* Cartesian box of nx*ny*nz cubic cells (§6 grids); hx = hy = hz. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double hx, hy, hz;
+} ps_grid;
+
+/* Block-sparse row matrix: n_brow block rows of br x bc row-major FP64 blocks,
+   column indices sorted ascending within each row. */
+typedef struct {
+  int64_t n_brow, n_bcol, nnzb;
+  int32_t br, bc;
+  const int64_t* rowptr; /* n_brow + 1 */
+  const int32_t* colind; /* nnzb */
+  const double* val;     /* nnzb * br * bc */
+} ps_bsr;
+
+/* Jacobian blocks of §5.1 (App. B expressions):
+   A_uu: 3x3, node x node, Q1 27-point pattern;
+   A_uf: 3x2, node x cell, columns (s, p) = [A_us A_up];
+   A_fu: 2x3, cell x node, rows (s, p) = [A_su; A_pu];
+   A_ff: 2x2, cell x cell, TPFA 7-point pattern, [[A_ss A_sp] [A_ps A_pp]]. */
+typedef struct {
+  ps_bsr A_uu, A_uf, A_fu, A_ff;
+  const double* d_fs;         /* 2 per cell: fixed-stress (D_sp, D_pp) of §5.1, scaled like A_ff */
+  const uint8_t* dirichlet_u; /* 3 per node, 1 = constrained (identity row); may be NULL */
+} ps_jacobian;
+
+typedef struct {
+  int32_t precision;          /* PS_FP64 or PS_MIXED_FP32 (FP32 preconditioner, FP64 Krylov) */
+  int32_t restart;            /* FGMRES restart length m (default 100) */
+  int32_t max_iters;          /* total Krylov iterations (default 1000) */
+  int32_t smoother;           /* PS_SMOOTH_* (default Chebyshev) */
+  int32_t pre, post;          /* l1-Jacobi sweeps (default 1, 1) */
+  int32_t cheb_degree;        /* Chebyshev degree (default 2) */
+  double cheb_ratio;          /* Chebyshev interval [lambda/ratio, lambda] (default 20) */
+  double theta_u, theta_p;    /* strength thresholds at level 0, halved per level (0.08) */
+  int32_t coarse_max_u;       /* coarsest mechanics level size in nodes (500) */
+  int32_t coarse_max_p;       /* coarsest pressure level size in cells (500) */
+  int32_t max_levels;         /* (25) */
+  int32_t ilu_mode;           /* PS_ILU_* */
+  int64_t spin_limit;         /* bounded-wait polls before PS_ERR_TIMEOUT */
+  int32_t host_ptrs;          /* 1: jacobian arrays, rhs and x are host pointers */
+  int64_t hbm_budget;         /* bytes the handle may hold; 0 = unlimited */
+  void* stream;               /* cudaStream_t */
+} ps_params;
+
+typedef struct {
+  int32_t iters, restarts;
+  double true_relres, est_relres;  /* ||b - A x|| / ||b|| in FP64, Arnoldi estimate */
+  float ms_setup_u, ms_setup_f, ms_solve;
+  int64_t bytes_model;              /* algorithmic HBM bytes of the solve */
+  int64_t handle_bytes;             /* device bytes held by the handle */
+  int32_t levels_u, levels_p;
+} ps_stats;
+
+typedef struct ps_handle ps_handle;
+
+/* Fill *p with the defaults listed above. */
+void ps_params_default(ps_params* p);
+
+/* Setup phase of §5.4: validates shapes (A_uu rows = nodes, A_ff rows = cells of
+   *grid, 7-point A_ff pattern), copies the FP64 blocks, builds S_ff^(FS) (§5.1),
+   the quasi-IMPES S_pp (§5.3), the mechanics AMG on A_uu^(SDC) (§5.2), the
+   pressure AMG on S_pp, block ILU(0) of S_ff^(FS) and the Krylov workspace.
+   On success *out owns all of it until ps_free.  Errors: PS_ERR_INVALID,
+   PS_ERR_OOM, PS_ERR_BUDGET, PS_ERR_CUDA. */
+ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params,
+                   ps_handle** out);
+
+/* Rebuild the flow stage (S_ff^(FS), S_pp, pressure AMG, ILU(0)) from new A_fu,
+   A_ff and d_fs values with unchanged patterns, keeping the mechanics AMG: the
+   per-Newton flow setup of §5.2/§5.4. */
+ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac);
+
+/* Iteration phase: x = FGMRES(A, M^{-1}, rhs) from x0 = 0 to the true FP64
+   relative residual tol.  rhs, x: n = 3*nodes + 2*cells doubles.
+   PS_ERR_NOT_CONVERGED still fills x and *st (st may be NULL). */
+ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* st);
+
+/* y = A x with the stored FP64 Jacobian (device pointers). */
+ps_status ps_spmv(ps_handle* h, const double* x, double* y);
+
+/* z = M^{-1} v, Algorithm 1 (device pointers, FP64 in and out). */
+ps_status ps_apply_prec(ps_handle* h, const double* v, double* z);
+
+/* Hierarchy inspection for parity checks: which = 0 mechanics, 1 pressure.
+   Returns the level count; level_n/level_nnz/agg are copied to host memory. */
+int32_t ps_amg_nlevels(ps_handle* h, int32_t which);
+ps_status ps_amg_level_info(ps_handle* h, int32_t which, int32_t level, int64_t* n, int64_t* nnz,
+                            int64_t* nagg);
+/* host copies: rowptr[n+1], colind[nnz], val[nnz*ncomp] (ncomp 3 or 1), agg[n] (-1 excluded) */
+ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t* rowptr, int32_t* colind,
+                            double* val, int32_t* agg);
+/* S_pp values in the A_ff pattern and ILU inverse diagonal blocks (host copies) */
+ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv);
+
+/* Frees everything the handle owns (synchronises its stream). */
+void ps_free(ps_handle* h);
+
+/* ---- seeded synthetic Jacobian generator (test input; §6 physics) ---- */
+enum { PS_FIELDS_LOGNORMAL = 0, PS_FIELDS_LAYERED = 1, PS_FIELDS_CHANNELS = 2,
+       PS_FIELDS_HOMOGENEOUS = 3 };
+enum {
+  PS_GEN_GRAVITY = 1 << 0, PS_GEN_DIRICHLET = 1 << 1, PS_GEN_SCALE = 1 << 2,
+  PS_GEN_ACCUM = 1 << 3, PS_GEN_FLUX = 1 << 4, PS_GEN_FLUX_SAT = 1 << 5,
+  PS_GEN_COUPLING = 1 << 6, PS_GEN_ALL = 0x7f
+};
+
+typedef struct {
+  int32_t nx, ny, nz;
+  double h;
+  uint64_t seed;
+  int32_t field_kind;
+  uint32_t flags;
+  double dt, biot, c_w, c_nw, c_r, mu_w, mu_nw, rho_w0, rho_nw0, rho_s0, s_wr, s_nwr, grav, p_ref, dp_amp, corey;
+  double E0, nu0, kappa0, phi0, sw0;
+} ps_gen_params;
+
+/* A generated system: every pointer is device memory owned by the library. */
+typedef struct {
+  ps_jacobian jac;
+  ps_grid grid;
+  double* rhs;
+  int64_t n_nodes, n_cells, n_u, n_f, n;
+  double alpha_u, alpha_f;        /* row scales of §4 (remark on block-row scaling) */
+  double *E, *nu, *kh, *kv, *phi0, *sw, *p;  /* cell fields at the linearisation point */
+} ps_system;
+
+/* Defaults of the synthetic configurations (0: 8x8x4 lognormal, 1: 64x64x32
+   layered, 2: 60x220x85 channelised, 3: 16x16x8 layered). */
+void ps_gen_default(ps_gen_params* gp, int32_t config);
+/* Generates the Jacobian, d_fs and a seeded rhs on the device (stream may be
+   NULL).  *out is owned by the library until ps_system_free. */
+ps_status ps_generate(const ps_gen_params* gp, void* stream, ps_system** out);
+void ps_system_free(ps_system* s);
+
+const char* ps_strerror(ps_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,224 @@
+"""Python binding of libps, the GB300 solver for linearised multiphase
+poromechanics Jacobians under the two-stage preconditioner of arXiv 1812.05540.
+
+Argument marshalling only: every step of the setup and solve runs in the CUDA
+library (include/ps.h).  Device memory is passed as raw pointers
+(``tensor.data_ptr()``); PyTorch is used by callers for allocation and streams.
+Importing this module loads ``_build/libps.so`` and raises if it is missing;
+there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libps.so")
+
+PS_OK, PS_ERR_INVALID, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_NOT_CONVERGED, PS_ERR_BREAKDOWN, PS_ERR_NAN, \
+    PS_ERR_TIMEOUT, PS_ERR_BUDGET = range(9)
+PS_FP64, PS_MIXED_FP32 = 0, 1
+PS_SMOOTH_L1JACOBI, PS_SMOOTH_CHEBYSHEV = 0, 1
+PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
+PS_FIELDS_LOGNORMAL, PS_FIELDS_LAYERED, PS_FIELDS_CHANNELS, PS_FIELDS_HOMOGENEOUS = range(4)
+PS_GEN_GRAVITY, PS_GEN_DIRICHLET, PS_GEN_SCALE, PS_GEN_ACCUM, PS_GEN_FLUX, PS_GEN_FLUX_SAT, PS_GEN_COUPLING = \
+    (1 << i for i in range(7))
+PS_GEN_ALL = 0x7F
+
+
+class ps_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double)]
+
+
+class ps_bsr(C.Structure):
+    _fields_ = [("n_brow", C.c_int64), ("n_bcol", C.c_int64), ("nnzb", C.c_int64), ("br", C.c_int32),
+                ("bc", C.c_int32), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p)]
+
+
+class ps_jacobian(C.Structure):
+    _fields_ = [("A_uu", ps_bsr), ("A_uf", ps_bsr), ("A_fu", ps_bsr), ("A_ff", ps_bsr),
+                ("d_fs", C.c_void_p), ("dirichlet_u", C.c_void_p)]
+
+
+class ps_params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("restart", C.c_int32), ("max_iters", C.c_int32),
+                ("smoother", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32), ("cheb_degree", C.c_int32),
+                ("cheb_ratio", C.c_double), ("theta_u", C.c_double), ("theta_p", C.c_double),
+                ("coarse_max_u", C.c_int32), ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32),
+                ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
+                ("hbm_budget", C.c_int64), ("stream", C.c_void_p)]
+
+
+class ps_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("true_relres", C.c_double),
+                ("est_relres", C.c_double), ("ms_setup_u", C.c_float), ("ms_setup_f", C.c_float),
+                ("ms_solve", C.c_float), ("bytes_model", C.c_int64), ("handle_bytes", C.c_int64),
+                ("levels_u", C.c_int32), ("levels_p", C.c_int32)]
+
+
+class ps_gen_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
+                ("seed", C.c_uint64), ("field_kind", C.c_int32), ("flags", C.c_uint32),
+                ("dt", C.c_double), ("biot", C.c_double), ("c_w", C.c_double), ("c_nw", C.c_double),
+                ("c_r", C.c_double), ("mu_w", C.c_double), ("mu_nw", C.c_double), ("rho_w0", C.c_double),
+                ("rho_nw0", C.c_double), ("rho_s0", C.c_double), ("s_wr", C.c_double), ("s_nwr", C.c_double),
+                ("grav", C.c_double), ("p_ref", C.c_double), ("dp_amp", C.c_double), ("corey", C.c_double),
+                ("E0", C.c_double), ("nu0", C.c_double), ("kappa0", C.c_double), ("phi0", C.c_double),
+                ("sw0", C.c_double)]
+
+
+_PD = C.POINTER(C.c_double)
+
+
+class ps_system(C.Structure):
+    _fields_ = [("jac", ps_jacobian), ("grid", ps_grid), ("rhs", C.c_void_p), ("n_nodes", C.c_int64),
+                ("n_cells", C.c_int64), ("n_u", C.c_int64), ("n_f", C.c_int64), ("n", C.c_int64),
+                ("alpha_u", C.c_double), ("alpha_f", C.c_double),
+                ("E", C.c_void_p), ("nu", C.c_void_p), ("kh", C.c_void_p), ("kv", C.c_void_p),
+                ("phi0", C.c_void_p), ("sw", C.c_void_p), ("p", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libps.so (built in-tree by __graft_entry__.build()); raises when absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libps.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        H = C.c_void_p
+        L.ps_params_default.argtypes = [C.POINTER(ps_params)]
+        L.ps_params_default.restype = None
+        L.ps_setup.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.POINTER(ps_params), C.POINTER(H)]
+        L.ps_setup_flow.argtypes = [H, C.POINTER(ps_jacobian)]
+        L.ps_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ps_stats)]
+        L.ps_spmv.argtypes = [H, C.c_void_p, C.c_void_p]
+        L.ps_apply_prec.argtypes = [H, C.c_void_p, C.c_void_p]
+        L.ps_amg_nlevels.argtypes = [H, C.c_int32]
+        L.ps_amg_nlevels.restype = C.c_int32
+        L.ps_amg_level_info.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int64)]
+        L.ps_amg_level_copy.argtypes = [H, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ps_flow_copy.argtypes = [H, C.c_void_p, C.c_void_p]
+        L.ps_free.argtypes = [H]
+        L.ps_free.restype = None
+        L.ps_gen_default.argtypes = [C.POINTER(ps_gen_params), C.c_int32]
+        L.ps_gen_default.restype = None
+        L.ps_generate.argtypes = [C.POINTER(ps_gen_params), C.c_void_p, C.POINTER(C.POINTER(ps_system))]
+        L.ps_system_free.argtypes = [C.POINTER(ps_system)]
+        L.ps_system_free.restype = None
+        L.ps_strerror.argtypes = [C.c_int]
+        L.ps_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class PsError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s: %s (status %d)" % (what, lib().ps_strerror(status).decode(), status))
+        self.status = status
+
+
+def _check(status, what):
+    if status != PS_OK:
+        raise PsError(status, what)
+
+
+def ps_strerror(status):
+    return lib().ps_strerror(status).decode()
+
+
+def ps_params_default(**kw):
+    p = ps_params()
+    lib().ps_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def ps_gen_default(config=0, **kw):
+    gp = ps_gen_params()
+    lib().ps_gen_default(C.byref(gp), config)
+    for k, v in kw.items():
+        setattr(gp, k, v)
+    return gp
+
+
+def ps_generate(gp, stream=None):
+    """Seeded synthetic Jacobian on the device; returns a ctypes ps_system pointer."""
+    out = C.POINTER(ps_system)()
+    _check(lib().ps_generate(C.byref(gp), stream, C.byref(out)), "ps_generate")
+    return out
+
+
+def ps_system_free(sys_ptr):
+    lib().ps_system_free(sys_ptr)
+
+
+def ps_setup(jac, grid, params):
+    h = C.c_void_p()
+    _check(lib().ps_setup(C.byref(jac), C.byref(grid), C.byref(params), C.byref(h)), "ps_setup")
+    return h
+
+
+def ps_setup_flow(h, jac):
+    _check(lib().ps_setup_flow(h, C.byref(jac)), "ps_setup_flow")
+
+
+def ps_solve(h, rhs_ptr, x_ptr, tol, raise_on_error=True):
+    """Returns (status, ps_stats); raises unless raise_on_error is False."""
+    st = ps_stats()
+    s = lib().ps_solve(h, rhs_ptr, x_ptr, tol, C.byref(st))
+    if raise_on_error:
+        _check(s, "ps_solve")
+    return s, st
+
+
+def ps_spmv(h, x_ptr, y_ptr):
+    _check(lib().ps_spmv(h, x_ptr, y_ptr), "ps_spmv")
+
+
+def ps_apply_prec(h, v_ptr, z_ptr):
+    _check(lib().ps_apply_prec(h, v_ptr, z_ptr), "ps_apply_prec")
+
+
+def ps_free(h):
+    lib().ps_free(h)
+
+
+def ps_amg_nlevels(h, which):
+    return lib().ps_amg_nlevels(h, which)
+
+
+def ps_amg_level_info(h, which, level):
+    n, nnz, nagg = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().ps_amg_level_info(h, which, level, C.byref(n), C.byref(nnz), C.byref(nagg)), "ps_amg_level_info")
+    return n.value, nnz.value, nagg.value
+
+
+def ps_amg_level_copy(h, which, level):
+    """Host copies (numpy) of a level operator and its aggregates."""
+    import numpy as np
+    n, nnz, _ = ps_amg_level_info(h, which, level)
+    nc = 3 if which == 0 else 1
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(max(nnz, 1), np.int32)
+    v = np.empty(max(nnz, 1) * nc)
+    agg = np.empty(n, np.int32)
+    _check(lib().ps_amg_level_copy(h, which, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, agg.ctypes.data),
+           "ps_amg_level_copy")
+    return rp, ci[:nnz], v[:nnz * nc].reshape(nnz, nc), agg
+
+
+def ps_flow_copy(h, nnzb, ncells):
+    import numpy as np
+    spp = np.empty(nnzb)
+    dinv = np.empty(4 * ncells)
+    _check(lib().ps_flow_copy(h, spp.ctypes.data, dinv.ctypes.data), "ps_flow_copy")
+    return spp, dinv
+
+
+def bsr(n_brow, n_bcol, br, bc, rowptr, colind, val, nnzb):
+    """ps_bsr from three pointers (ints)."""
+    return ps_bsr(n_brow, n_bcol, nnzb, br, bc, rowptr, colind, val)

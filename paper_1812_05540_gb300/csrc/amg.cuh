@@ -1,0 +1,85 @@
+// Smoothed-aggregation AMG hierarchy on the device: the amg(.) operator of
+// §5.2 (three SDC displacement components on shared nodal aggregates, nc = 3)
+// and §5.3 (pressure, nc = 1).
+#pragma once
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ps_internal {
+
+struct AmgLevel {
+  int64_t n = 0, nnz = 0;
+  int32_t* rp = nullptr;  // n+1
+  int32_t* ci = nullptr;  // nnz
+  double* v = nullptr;    // nnz*nc, entry-major
+  float* vf = nullptr;    // FP32 copy (mixed precision)
+  double* dg = nullptr;   // diagonal, n*nc
+  float* dgf = nullptr;
+  double* dl1 = nullptr;  // l1 row norms, n*nc
+  float* dl1f = nullptr;
+  double lam[3] = {0, 0, 0};  // Gershgorin bound of rho(D^{-1}A) per component
+  int lanes = 32;             // threads per row in SpMV kernels
+  // transfer to level+1
+  int64_t nagg = 0;
+  int32_t* agg = nullptr;
+  int64_t pnnz = 0;
+  int32_t *prp = nullptr, *pci = nullptr;
+  double* pv = nullptr;
+  float* pvf = nullptr;
+  int plane = 8;
+  int32_t *rrp = nullptr, *rci = nullptr;
+  double* rv = nullptr;
+  float* rvf = nullptr;
+  int rlane = 8;
+  // coarsest level: dense inverse per component (row-major n x n)
+  bool coarsest = false;
+  double* inv = nullptr;
+  float* invf = nullptr;
+  // V-cycle work vectors (n*nc entries of the apply precision): iterate x and
+  // its ping-pong partner t, residual r, Chebyshev direction d, right-hand
+  // side b (written by the finer level's restriction) and result e (read by
+  // the finer level's prolongation)
+  void *x = nullptr, *t = nullptr, *r = nullptr, *d = nullptr, *b = nullptr, *e = nullptr;
+};
+
+struct Amg {
+  int nc = 1;
+  std::vector<AmgLevel> L;
+};
+
+struct AmgParams {
+  double theta;
+  int coarse_max, max_levels;
+  bool mixed;
+};
+
+// Build the hierarchy from the level-0 operator (rp/ci/v are adopted: the
+// arena must own them).  Bit-for-bit deterministic: aggregates and Galerkin
+// operators do not depend on thread scheduling.
+ps_status amg_build(Arena& ar, Amg& H, int nc, int64_t n, int64_t nnz, int32_t* rp, int32_t* ci, double* v,
+                    const AmgParams& prm, cudaStream_t st);
+
+// Smoothing schedule
+struct SmoothParams {
+  int kind;    // PS_SMOOTH_*
+  int pre, post, degree;
+  double ratio;
+};
+
+// x = V-cycle(b) on the level-0 vectors (interleaved nc components), T = float or double
+template <class T>
+ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st);
+// allocate the per-level work vectors for precision T
+template <class T>
+ps_status amg_alloc_work(Arena& ar, Amg& H);
+
+// SpMV lane choice from the mean row length
+inline int lanes_for(double mean_row) {
+  if (mean_row <= 6) return 4;
+  if (mean_row <= 14) return 8;
+  if (mean_row <= 40) return 16;
+  return 32;
+}
+
+}  // namespace ps_internal

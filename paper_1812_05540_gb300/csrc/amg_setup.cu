@@ -1,0 +1,726 @@
+// AMG setup kernels: strength of connection, distance-2 maximal independent
+// set, aggregation, smoothed prolongator, transpose, Galerkin product by a
+// shared-memory SpGEMM, and the dense inverse of the coarsest operator.
+//
+// This translation unit is compiled without floating-point contraction and
+// every floating-point sum is taken in a fixed order (ascending column / inner
+// index), so the aggregates and coarse operators are reproducible bit for bit.
+#include <cmath>
+#include <cstdio>
+
+#include "amg.cuh"
+
+namespace ps_internal {
+namespace {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// MIS priority: (hash(level, i), i), unique per node
+__device__ __forceinline__ int64_t mis_key(int64_t i, int level) {
+  uint64_t h = mix64((uint64_t(level) << 32) | uint64_t(i));
+  return (int64_t(h >> 33) << 32) | i;
+}
+
+template <int NC>
+__device__ __forceinline__ double abar(const double* v, int64_t q) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) s = s + fabs(v[q * NC + c]);
+  return s;
+}
+
+template <int NC>
+__global__ void k_diag_excl(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, double* __restrict__ dgbar, uint8_t* __restrict__ excl,
+                            double* __restrict__ dg) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  uint8_t ex = 1;
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+    if (ci[q] == i) {
+      d = abar<NC>(v, q);
+      for (int c = 0; c < NC; ++c) dg[i * NC + c] = v[int64_t(q) * NC + c];
+    } else {
+      for (int c = 0; c < NC; ++c)
+        if (v[int64_t(q) * NC + c] != 0.0) ex = 0;
+    }
+  }
+  dgbar[i] = d;
+  excl[i] = ex;
+}
+
+__device__ __forceinline__ int32_t find_col(const int32_t* __restrict__ ci, int32_t lo, int32_t hi, int32_t j) {
+  while (lo < hi) {
+    int32_t m = (lo + hi) >> 1;
+    if (ci[m] < j) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+// symmetric strength graph: i~j if max(abar_ij, abar_ji) >= theta sqrt(abar_ii abar_jj)
+template <int NC>
+__global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const double* __restrict__ dgbar,
+                           const uint8_t* __restrict__ excl, double theta, uint8_t* __restrict__ strong,
+                           double* __restrict__ wgt) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+    int32_t j = ci[q];
+    uint8_t s = 0;
+    double w = 0.0;
+    if (!excl[i] && j != i && !excl[j]) {
+      int32_t lo = rp[j], hi = rp[j + 1];
+      int32_t qt = find_col(ci, lo, hi, int32_t(i));
+      double aij = abar<NC>(v, q);
+      double aji = (qt < hi && ci[qt] == i) ? abar<NC>(v, qt) : 0.0;
+      double t = aij > aji ? aij : aji;
+      double den = sqrt(dgbar[i] * dgbar[j]);
+      if (t >= theta * den && t > 0.0) {
+        s = 1;
+        w = t / den;
+      }
+    }
+    strong[q] = s;
+    wgt[q] = w;
+  }
+}
+
+// ---- distance-2 MIS rounds (state: 0 undecided, 1 root, 2 covered, 3 excluded) ----
+__global__ void k_mis_init(int64_t n, const uint8_t* __restrict__ excl, uint8_t* __restrict__ st) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) st[i] = excl[i] ? 3 : 0;
+}
+__global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st, int level,
+                         int64_t* __restrict__ m1) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t m = st[i] == 0 ? mis_key(i, level) : -1;
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+    if (strong[q] && st[ci[q]] == 0) {
+      int64_t k = mis_key(ci[q], level);
+      m = k > m ? k : m;
+    }
+  m1[i] = m;
+}
+__global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const uint8_t* __restrict__ strong, const int64_t* __restrict__ m1, int level,
+                         uint8_t* __restrict__ st, uint8_t* __restrict__ nr) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t m = m1[i];
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+    if (strong[q]) {
+      int64_t k = m1[ci[q]];
+      m = k > m ? k : m;
+    }
+  uint8_t r = (st[i] == 0 && m == mis_key(i, level)) ? 1 : 0;
+  nr[i] = r;
+  if (r) st[i] = 1;
+}
+__global__ void k_mis_c1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const uint8_t* __restrict__ strong, const uint8_t* __restrict__ nr,
+                         uint8_t* __restrict__ c1) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint8_t c = nr[i];
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+    if (strong[q] && nr[ci[q]]) c = 1;
+  c1[i] = c;
+}
+__global__ void k_mis_c2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const uint8_t* __restrict__ strong, const uint8_t* __restrict__ c1,
+                         uint8_t* __restrict__ st, int32_t* __restrict__ undecided) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || st[i] != 0) return;
+  uint8_t c = c1[i];
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+    if (strong[q] && c1[ci[q]]) c = 1;
+  if (c) st[i] = 2;
+  else atomicAdd(undecided, 1);
+}
+
+__global__ void k_is_root(int64_t n, const uint8_t* __restrict__ st, int32_t* __restrict__ f) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = st[i] == 1 ? 1 : 0;
+}
+// phase 1: roots take their id (roots in ascending node order); a strong
+// neighbour of a root joins it (roots are >= 3 apart, so it is unique)
+__global__ void k_agg_phase1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st,
+                             const int32_t* __restrict__ rootscan, int32_t* __restrict__ ph1) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t a = -1;
+  if (st[i] == 1) a = rootscan[i];
+  else if (st[i] == 2) {
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
+      if (strong[q] && st[ci[q]] == 1) { a = rootscan[ci[q]]; break; }
+  }
+  ph1[i] = a;
+}
+// phase 2: leftovers join the aggregate of their strongest phase-1 neighbour
+// (largest weight, then smallest aggregate id)
+__global__ void k_agg_phase2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const uint8_t* __restrict__ strong, const double* __restrict__ wgt,
+                             const uint8_t* __restrict__ st, const int32_t* __restrict__ ph1,
+                             int32_t* __restrict__ agg) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t a = ph1[i];
+  if (st[i] == 2 && a < 0) {
+    double bw = -1.0;
+    int32_t ba = -1;
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+      if (!strong[q]) continue;
+      int32_t aj = ph1[ci[q]];
+      if (aj < 0) continue;
+      if (wgt[q] > bw || (wgt[q] == bw && aj < ba)) { bw = wgt[q]; ba = aj; }
+    }
+    a = ba;
+  }
+  agg[i] = a;
+}
+
+// Gershgorin ratio sum_j |a_ij| / |a_ii| per row and component (component-major output)
+template <int NC>
+__global__ void k_gersh(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const double* __restrict__ v, double* __restrict__ out) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double s = 0.0, d = 0.0;
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+      s = s + fabs(v[int64_t(q) * NC + c]);
+      if (ci[q] == i) d = v[int64_t(q) * NC + c];
+    }
+    out[c * n + i] = s / fabs(d);
+  }
+}
+
+template <int NC>
+__global__ void k_l1(int64_t n, const int32_t* __restrict__ rp, const double* __restrict__ v,
+                     double* __restrict__ out) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    double s = 0.0;
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) s = s + fabs(v[int64_t(q) * NC + c]);
+    out[i * NC + c] = s;
+  }
+}
+
+// ---- smoothed prolongator P = (I - omega D^{-1} A) P_tent, row by row ----
+__device__ __forceinline__ bool first_occurrence(const int32_t* __restrict__ ci, const int32_t* __restrict__ agg,
+                                                 int32_t q0, int32_t q, int32_t a) {
+  for (int32_t t = q0; t < q; ++t)
+    if (agg[ci[t]] == a) return false;
+  return true;
+}
+__global__ void k_p_count(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const int32_t* __restrict__ agg, int32_t* __restrict__ cnt) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t c = 0;
+  if (agg[i] >= 0)
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+      int32_t a = agg[ci[q]];
+      if (a >= 0 && first_occurrence(ci, agg, rp[i], q, a)) ++c;
+    }
+  cnt[i] = c;
+}
+template <int NC>
+__global__ void k_p_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, const int32_t* __restrict__ agg, double w0, double w1,
+                         double w2, const int32_t* __restrict__ prp, int32_t* __restrict__ pci,
+                         double* __restrict__ pv) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || agg[i] < 0) return;
+  const double om[3] = {w0, w1, w2};
+  int32_t q0 = rp[i], q1 = rp[i + 1];
+  int32_t qd = q0;
+  while (ci[qd] != i) ++qd;
+  for (int32_t q = q0; q < q1; ++q) {
+    int32_t a = agg[ci[q]];
+    if (a < 0 || !first_occurrence(ci, agg, q0, q, a)) continue;
+    int32_t rank = 0;
+    for (int32_t t = q0; t < q1; ++t) {
+      int32_t b = agg[ci[t]];
+      if (b >= 0 && b < a && first_occurrence(ci, agg, q0, t, b)) ++rank;
+    }
+    int32_t pos = prp[i] + rank;
+    pci[pos] = a;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double S = 0.0;
+      for (int32_t t = q0; t < q1; ++t)
+        if (agg[ci[t]] == a) S = S + v[int64_t(t) * NC + c];
+      double coef = om[c] / v[int64_t(qd) * NC + c];
+      double delta = a == agg[i] ? 1.0 : 0.0;
+      pv[int64_t(pos) * NC + c] = delta - coef * S;
+    }
+  }
+}
+
+// ---- transpose (R = P^T) with rows sorted by fine index ----
+__global__ void k_col_count(int64_t nnz, const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
+  int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q < nnz) atomicAdd(&cnt[ci[q]], 1);
+}
+template <int NC>
+__global__ void k_transpose_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ v, int32_t* __restrict__ cursor,
+                                 int32_t* __restrict__ tci, double* __restrict__ tv) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+    int32_t pos = atomicAdd(&cursor[ci[q]], 1);
+    tci[pos] = int32_t(i);
+    for (int c = 0; c < NC; ++c) tv[int64_t(pos) * NC + c] = v[int64_t(q) * NC + c];
+  }
+}
+// order each row by column: a warp per row ranks every entry by counting the
+// smaller keys (keys in a row are distinct)
+template <int NC>
+__global__ void k_rank_rows(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci_in,
+                            const double* __restrict__ v_in, int32_t* __restrict__ ci_out,
+                            double* __restrict__ v_out) {
+  int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  int32_t q0 = rp[row], q1 = rp[row + 1];
+  for (int32_t q = q0 + lane; q < q1; q += 32) {
+    int32_t k = ci_in[q];
+    int32_t rank = 0;
+    for (int32_t t = q0; t < q1; ++t) rank += ci_in[t] < k;
+    ci_out[q0 + rank] = k;
+    for (int c = 0; c < NC; ++c) v_out[int64_t(q0 + rank) * NC + c] = v_in[int64_t(q) * NC + c];
+  }
+}
+
+// ---- SpGEMM C = X Y, one warp per row, shared-memory hash + sorted list ----
+constexpr int kHash = 2048;   // hash slots per warp
+constexpr int kUniq = 1024;   // distinct output columns per row
+constexpr int kEmpty = -1;
+
+__device__ __forceinline__ bool hash_insert(int32_t* tab, int32_t key, int* overflow) {
+  uint32_t h = (uint32_t(key) * 2654435761u) & (kHash - 1);
+  for (int probe = 0; probe < kHash; ++probe) {
+    int32_t prev = atomicCAS(&tab[h], kEmpty, key);
+    if (prev == kEmpty) return true;
+    if (prev == key) return false;
+    h = (h + 1) & (kHash - 1);
+  }
+  *overflow = 1;
+  return false;
+}
+
+// collect the distinct columns of row i into tab; returns their count (all lanes)
+__device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                              const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci, int32_t* tab,
+                              int lane, int* overflow) {
+  for (int t = lane; t < kHash; t += 32) tab[t] = kEmpty;
+  __syncwarp();
+  int cnt = 0;
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    int32_t k = xci[q];
+    for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32)
+      if (hash_insert(tab, yci[r], overflow)) ++cnt;
+  }
+  __syncwarp();
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  return cnt;
+}
+
+__global__ void k_spgemm_count(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                               const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                               int32_t* __restrict__ cnt, int* __restrict__ err) {
+  extern __shared__ int32_t smem[];
+  int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (i >= n) return;
+  int32_t* tab = smem + wib * kHash;
+  int ovf = 0;
+  int c = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
+  ovf = __any_sync(0xffffffffu, ovf);
+  if (lane == 0) {
+    cnt[i] = c;
+    if (ovf || c > kUniq) atomicExch(err, 1);
+  }
+}
+
+template <int NC>
+__global__ void k_spgemm_fill(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                              const double* __restrict__ xv, const int32_t* __restrict__ yrp,
+                              const int32_t* __restrict__ yci, const double* __restrict__ yv,
+                              const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cv,
+                              int* __restrict__ err) {
+  extern __shared__ unsigned char sraw[];
+  int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (i >= n) return;
+  size_t per = size_t(kHash) * 4 + size_t(kUniq) * 4 + size_t(kUniq) * NC * 8;
+  unsigned char* base = sraw + per * wib;
+  int32_t* tab = reinterpret_cast<int32_t*>(base);
+  int32_t* list = reinterpret_cast<int32_t*>(base + kHash * 4);
+  double* acc = reinterpret_cast<double*>(base + kHash * 4 + kUniq * 4);
+  int ovf = 0;
+  int u = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
+  if (u > kUniq || __any_sync(0xffffffffu, ovf)) {
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
+  // compact the table into list[0..u)
+  __shared__ int fill_ctr[8];
+  if (lane == 0) fill_ctr[wib] = 0;
+  __syncwarp();
+  for (int t = lane; t < kHash; t += 32) {
+    int32_t key = tab[t];
+    if (key != kEmpty) list[atomicAdd(&fill_ctr[wib], 1)] = key;
+  }
+  __syncwarp();
+  // bitonic sort of list[0..P), P = next power of two >= u, padded with INT_MAX
+  int P = 1;
+  while (P < u) P <<= 1;
+  for (int t = u + lane; t < P; t += 32) list[t] = 0x7fffffff;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < P; t += 32) {
+        int p = t ^ j;
+        if (p > t) {
+          int32_t a = list[t], b = list[p];
+          bool up = (t & k) == 0;
+          if ((a > b) == up) { list[t] = b; list[p] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  for (int t = lane; t < u * NC; t += 32) acc[t] = 0.0;
+  __syncwarp();
+  // numeric: products added in ascending order of the inner index k
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    int32_t k = xci[q];
+    double x[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = xv[int64_t(q) * NC + c];
+    for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32) {
+      int32_t j = yci[r];
+      int lo = 0, hi = u;
+      while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (list[m] < j) lo = m + 1;
+        else hi = m;
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[lo * NC + c] = acc[lo * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+    }
+    __syncwarp();
+  }
+  int32_t o = crp[i];
+  for (int t = lane; t < u; t += 32) {
+    cci[o + t] = list[t];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cv[int64_t(o + t) * NC + c] = acc[t * NC + c];
+  }
+}
+
+// ---- coarsest level: Gauss-Jordan inverse with partial pivoting, per component ----
+// M: [nc][n][n] row-major, I: [nc][n][n]; f: [nc][n] multipliers, piv scratch
+__global__ void k_dense_unpack(int64_t n, int nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, double* __restrict__ M, double* __restrict__ I) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int c = 0; c < nc; ++c) {
+    for (int32_t q = rp[t]; q < rp[t + 1]; ++q) M[(c * n + t) * n + ci[q]] = v[int64_t(q) * nc + c];
+    I[(c * n + t) * n + t] = 1.0;
+  }
+}
+__global__ void k_gj_pivot(int64_t n, int64_t k, double* __restrict__ M, double* __restrict__ I,
+                           double* __restrict__ f) {
+  int c = blockIdx.x;
+  double* A = M + int64_t(c) * n * n;
+  double* B = I + int64_t(c) * n * n;
+  __shared__ double bv[256];
+  __shared__ int64_t bi[256];
+  double best = -1.0;
+  int64_t arg = k;
+  for (int64_t r = k + threadIdx.x; r < n; r += blockDim.x) {
+    double a = fabs(A[r * n + k]);
+    if (a > best) { best = a; arg = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      double o = bv[threadIdx.x + off];
+      int64_t oi = bi[threadIdx.x + off];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  int64_t p = bi[0];
+  if (p != k)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+      t = B[k * n + j]; B[k * n + j] = B[p * n + j]; B[p * n + j] = t;
+    }
+  __syncthreads();
+  double piv = A[k * n + k];
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    A[k * n + j] = A[k * n + j] / piv;
+    B[k * n + j] = B[k * n + j] / piv;
+  }
+  __syncthreads();
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) f[int64_t(c) * n + r] = A[r * n + k];
+}
+__global__ void k_gj_elim(int64_t n, int64_t k, double* __restrict__ M, double* __restrict__ I,
+                          const double* __restrict__ f) {
+  int c = blockIdx.z;
+  int64_t r = int64_t(blockIdx.y);
+  int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r == k || j >= 2 * n) return;
+  double m = f[int64_t(c) * n + r];
+  if (m == 0.0) return;
+  double* A = M + int64_t(c) * n * n;
+  double* B = I + int64_t(c) * n * n;
+  if (j < n) A[r * n + j] = A[r * n + j] - m * A[k * n + j];
+  else B[r * n + j - n] = B[r * n + j - n] - m * B[k * n + j - n];
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = float(a[t]);
+}
+
+template <int NC>
+ps_status spgemm(Arena& ar, int64_t n, const int32_t* xrp, const int32_t* xci, const double* xv, const int32_t* yrp,
+                 const int32_t* yci, const double* yv, int32_t** crp, int32_t** cci, double** cv, int64_t* cnnz,
+                 int* d_err, cudaStream_t st) {
+  int32_t* cnt;
+  PS_TRY(ar.alloc(&cnt, n + 1));
+  PS_TRY(ar.alloc(crp, n + 1));
+  const int wpb_c = 4;
+  size_t sm_c = size_t(wpb_c) * kHash * 4;
+  k_spgemm_count<<<grid_for(n, wpb_c), 32 * wpb_c, sm_c, st>>>(n, xrp, xci, yrp, yci, cnt, d_err);
+  PS_CUDA(cudaGetLastError());
+  int32_t tot = 0;
+  PS_TRY(scan_i32(ar, cnt, *crp, n, &tot, st));
+  int herr = 0;
+  PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  if (herr) return PS_ERR_INVALID;
+  *cnnz = tot;
+  PS_TRY(ar.alloc(cci, size_t(tot) + 1));
+  PS_TRY(ar.alloc(cv, (size_t(tot) + 1) * NC));
+  const int wpb = NC == 3 ? 2 : 4;
+  size_t per = size_t(kHash) * 4 + size_t(kUniq) * 4 + size_t(kUniq) * NC * 8;
+  size_t sm = per * wpb;
+  PS_CUDA(cudaFuncSetAttribute(k_spgemm_fill<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  k_spgemm_fill<NC><<<grid_for(n, wpb), 32 * wpb, sm, st>>>(n, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, d_err);
+  PS_CUDA(cudaGetLastError());
+  ar.release(cnt);
+  return PS_OK;
+}
+
+template <int NC>
+ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, int32_t* ci0, double* v0,
+                     const AmgParams& prm, cudaStream_t st) {
+  H.nc = NC;
+  H.L.clear();
+  H.L.emplace_back();
+  H.L[0].n = n0; H.L[0].nnz = nnz0; H.L[0].rp = rp0; H.L[0].ci = ci0; H.L[0].v = v0;
+  int* d_err;
+  PS_TRY(ar.alloc(&d_err, 4));
+  PS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  double theta = prm.theta;
+  for (int l = 0;; ++l) {
+    AmgLevel& lev = H.L[l];
+    int64_t n = lev.n, nnz = lev.nnz;
+    lev.lanes = lanes_for(double(nnz) / double(n > 0 ? n : 1));
+    double* dgbar;
+    uint8_t* excl;
+    PS_TRY(ar.alloc(&dgbar, n));
+    PS_TRY(ar.alloc(&excl, n));
+    PS_TRY(ar.alloc(&lev.dg, n * NC));
+    k_diag_excl<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, lev.dg);
+    PS_CUDA(cudaGetLastError());
+    bool coarsest = n <= prm.coarse_max || l + 1 >= prm.max_levels;
+    uint8_t *strong = nullptr, *stt = nullptr;
+    double* wgt = nullptr;
+    if (!coarsest) {
+      PS_TRY(ar.alloc(&strong, nnz));
+      PS_TRY(ar.alloc(&wgt, nnz));
+      k_strength<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, theta, strong, wgt);
+      PS_TRY(ar.alloc(&stt, n));
+      int64_t* m1;
+      uint8_t *nr, *c1;
+      int32_t* und;
+      PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, 1));
+      k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, excl, stt);
+      for (int round = 0;; ++round) {
+        PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
+        k_mis_m1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
+        k_mis_m2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
+        k_mis_c1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
+        k_mis_c2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
+        int32_t h_und = 0;
+        PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        if (h_und == 0) break;
+        if (round > 100000) return PS_ERR_INVALID;
+      }
+      int32_t *isr, *rscan, *ph1;
+      PS_TRY(ar.alloc(&isr, n)); PS_TRY(ar.alloc(&rscan, n + 1)); PS_TRY(ar.alloc(&ph1, n));
+      PS_TRY(ar.alloc(&lev.agg, n));
+      k_is_root<<<grid_for(n, 256), 256, 0, st>>>(n, stt, isr);
+      int32_t na = 0;
+      PS_TRY(scan_i32(ar, isr, rscan, n, &na, st));
+      k_agg_phase1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, rscan, ph1);
+      k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, wgt, stt, ph1, lev.agg);
+      PS_CUDA(cudaGetLastError());
+      lev.nagg = na;
+      ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(isr); ar.release(rscan);
+      ar.release(ph1);
+      if (na == 0 || double(n) / double(na) < 1.2) coarsest = true;
+    }
+    if (coarsest) {
+      if (n > 16384) return PS_ERR_INVALID;  // coarsening stalled on a large level
+      lev.coarsest = true;
+      lev.nagg = 0;
+      if (lev.agg) { ar.release(lev.agg); lev.agg = nullptr; }
+      double *M, *f;
+      PS_TRY(ar.alloc(&M, size_t(NC) * n * n));
+      PS_TRY(ar.alloc(&lev.inv, size_t(NC) * n * n));
+      PS_TRY(ar.alloc(&f, size_t(NC) * n));
+      PS_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * NC * n * n, st));
+      PS_CUDA(cudaMemsetAsync(lev.inv, 0, sizeof(double) * NC * n * n, st));
+      k_dense_unpack<<<grid_for(n, 128), 128, 0, st>>>(n, NC, lev.rp, lev.ci, lev.v, M, lev.inv);
+      for (int64_t k = 0; k < n; ++k) {
+        k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
+        dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), NC);
+        k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
+      }
+      PS_CUDA(cudaGetLastError());
+      ar.release(M); ar.release(f);
+      if (prm.mixed) {
+        PS_TRY(ar.alloc(&lev.invf, size_t(NC) * n * n));
+        k_to_f32<<<grid_for(NC * n * n, 256), 256, 0, st>>>(lev.inv, lev.invf, NC * n * n);
+      }
+    }
+    if (strong) ar.release(strong);
+    if (wgt) ar.release(wgt);
+    if (stt) ar.release(stt);
+    ar.release(dgbar); ar.release(excl);
+    if (prm.mixed) {
+      PS_TRY(ar.alloc(&lev.vf, nnz * NC));
+      PS_TRY(ar.alloc(&lev.dgf, n * NC));
+      k_to_f32<<<grid_for(nnz * NC, 256), 256, 0, st>>>(lev.v, lev.vf, nnz * NC);
+      k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dg, lev.dgf, n * NC);
+    }
+    if (lev.coarsest) break;
+    // Gershgorin bound, omega = (4/3) / lambda
+    double* gr;
+    PS_TRY(ar.alloc(&gr, n * NC));
+    k_gersh<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, gr);
+    double* dmax;
+    PS_TRY(ar.alloc(&dmax, NC));
+    for (int c = 0; c < NC; ++c) PS_TRY(max_f64(ar, gr + c * n, n, dmax + c, st));
+    PS_CUDA(cudaMemcpyAsync(lev.lam, dmax, sizeof(double) * NC, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    ar.release(gr); ar.release(dmax);
+    double om[3] = {0, 0, 0};
+    for (int c = 0; c < NC; ++c) om[c] = (4.0 / 3.0) / lev.lam[c];
+    // l1 row norms for the l1-Jacobi smoother
+    PS_TRY(ar.alloc(&lev.dl1, n * NC));
+    k_l1<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.v, lev.dl1);
+    if (prm.mixed) {
+      PS_TRY(ar.alloc(&lev.dl1f, n * NC));
+      k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
+    }
+    // prolongator
+    int32_t* pc;
+    PS_TRY(ar.alloc(&pc, n + 1));
+    PS_TRY(ar.alloc(&lev.prp, n + 1));
+    k_p_count<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.agg, pc);
+    int32_t pnnz = 0;
+    PS_TRY(scan_i32(ar, pc, lev.prp, n, &pnnz, st));
+    lev.pnnz = pnnz;
+    PS_TRY(ar.alloc(&lev.pci, size_t(pnnz) + 1));
+    PS_TRY(ar.alloc(&lev.pv, (size_t(pnnz) + 1) * NC));
+    k_p_fill<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, om[0], om[1], om[2], lev.prp,
+                                                    lev.pci, lev.pv);
+    PS_CUDA(cudaGetLastError());
+    ar.release(pc);
+    lev.plane = lanes_for(double(pnnz) / double(n));
+    // restriction R = P^T
+    int64_t na = lev.nagg;
+    int32_t *ccount, *cursor, *tci;
+    double* tv;
+    PS_TRY(ar.alloc(&ccount, na + 1));
+    PS_TRY(ar.alloc(&lev.rrp, na + 1));
+    PS_TRY(ar.alloc(&cursor, na + 1));
+    PS_TRY(ar.alloc(&tci, size_t(pnnz) + 1));
+    PS_TRY(ar.alloc(&tv, (size_t(pnnz) + 1) * NC));
+    PS_TRY(ar.alloc(&lev.rci, size_t(pnnz) + 1));
+    PS_TRY(ar.alloc(&lev.rv, (size_t(pnnz) + 1) * NC));
+    PS_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (na + 1), st));
+    k_col_count<<<grid_for(pnnz, 256), 256, 0, st>>>(pnnz, lev.pci, ccount);
+    PS_TRY(scan_i32(ar, ccount, lev.rrp, na, nullptr, st));
+    PS_CUDA(cudaMemcpyAsync(cursor, lev.rrp, sizeof(int32_t) * na, cudaMemcpyDeviceToDevice, st));
+    k_transpose_fill<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.prp, lev.pci, lev.pv, cursor, tci, tv);
+    k_rank_rows<NC><<<grid_for(na * 32, 256), 256, 0, st>>>(na, lev.rrp, tci, tv, lev.rci, lev.rv);
+    PS_CUDA(cudaGetLastError());
+    ar.release(ccount); ar.release(cursor); ar.release(tci); ar.release(tv);
+    lev.rlane = lanes_for(double(pnnz) / double(na));
+    if (prm.mixed) {
+      PS_TRY(ar.alloc(&lev.pvf, size_t(pnnz) * NC + 1));
+      PS_TRY(ar.alloc(&lev.rvf, size_t(pnnz) * NC + 1));
+      k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.pv, lev.pvf, pnnz * NC);
+      k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.rv, lev.rvf, pnnz * NC);
+    }
+    // Galerkin product A_c = R (A P)
+    int32_t *aprp, *apci, *crp, *cci;
+    double *apv, *cv;
+    int64_t apnnz = 0, cnnz = 0;
+    PS_TRY(spgemm<NC>(ar, n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci, lev.pv, &aprp, &apci, &apv, &apnnz, d_err, st));
+    PS_TRY(spgemm<NC>(ar, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz, d_err, st));
+    int herr = 0;
+    PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (herr) return PS_ERR_INVALID;
+    ar.release(aprp); ar.release(apci); ar.release(apv);
+    H.L.emplace_back();
+    AmgLevel& nx = H.L.back();
+    nx.n = na; nx.nnz = cnnz; nx.rp = crp; nx.ci = cci; nx.v = cv;
+    theta *= 0.5;
+  }
+  // Gershgorin bounds for the levels that did not compute one (coarsest)
+  ar.release(d_err);
+  return PS_OK;
+}
+
+}  // namespace
+
+ps_status amg_build(Arena& ar, Amg& H, int nc, int64_t n, int64_t nnz, int32_t* rp, int32_t* ci, double* v,
+                    const AmgParams& prm, cudaStream_t st) {
+  if (nc == 3) return build_impl<3>(ar, H, n, nnz, rp, ci, v, prm, st);
+  if (nc == 1) return build_impl<1>(ar, H, n, nnz, rp, ci, v, prm, st);
+  return PS_ERR_INVALID;
+}
+
+}  // namespace ps_internal

@@ -1,0 +1,485 @@
+// C ABI: setup phase, Algorithm 1 and the flexible-GMRES iteration phase.
+#include <cmath>
+#include <cstring>
+
+#include "amg.cuh"
+#include "flow.cuh"
+#include "krylov.cuh"
+
+using namespace ps_internal;
+
+namespace {
+
+__global__ void k_sdc(int64_t nnzb, const double* __restrict__ uu, double* __restrict__ out) {
+  int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= nnzb) return;
+  out[q * 3 + 0] = uu[q * 9 + 0];
+  out[q * 3 + 1] = uu[q * 9 + 4];
+  out[q * 3 + 2] = uu[q * 9 + 8];
+}
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = float(a[t]);
+}
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = double(a[t]);
+}
+__global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = a[t];
+}
+
+}  // namespace
+
+struct ps_handle {
+  Arena ar;   // Jacobian copies, mechanics AMG, Krylov workspace
+  Arena arf;  // flow stage and pressure AMG (rebuilt by ps_setup_flow)
+  cudaStream_t st = 0;
+  ps_params prm;
+  ps_grid grid;
+  int64_t nn = 0, nc = 0, nu = 0, nf = 0, n = 0;
+  bool mixed = false;
+  JacDev J;
+  double* dfs = nullptr;
+  Amg amg_u, amg_p;
+  FlowStage F;
+  FlowWork<float> w32;
+  FlowWork<double> w64;
+  float *vu32 = nullptr, *zu32 = nullptr;
+  double* zu64 = nullptr;
+  // Krylov
+  int m = 100;
+  double *V = nullptr, *Z = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *part = nullptr, *mpart = nullptr;
+  KrylovState K;
+  double* hsc = nullptr;  // pinned: 8 scalars
+  int* hflag = nullptr;   // pinned: 2 flags
+  float ms_setup_u = 0, ms_setup_f = 0;
+  int64_t spmv_part = 0;
+};
+
+namespace {
+
+SmoothParams smooth_params(const ps_params& p) {
+  SmoothParams s;
+  s.kind = p.smoother; s.pre = p.pre; s.post = p.post; s.degree = p.cheb_degree; s.ratio = p.cheb_ratio;
+  return s;
+}
+
+template <class T>
+ps_status alg1(ps_handle* h, const double* v, double* z) {
+  cudaStream_t st = h->st;
+  SmoothParams sp = smooth_params(h->prm);
+  FlowWork<T>* W;
+  if constexpr (sizeof(T) == 4) W = &h->w32;
+  else W = &h->w64;
+  // step 1: z_u = M_uu^{-1} v_u
+  if constexpr (sizeof(T) == 4) {
+    k_d2f<<<grid_for(h->nu, 256), 256, 0, st>>>(v, h->vu32, h->nu);
+    PS_TRY(amg_vcycle<float>(h->amg_u, sp, h->vu32, h->zu32, st));
+    k_f2d<<<grid_for(h->nu, 256), 256, 0, st>>>(h->zu32, z, h->nu);
+    k_d2f<<<grid_for(h->nf, 256), 256, 0, st>>>(v + h->nu, W->vf, h->nf);
+    // steps 2-4
+    alg1_steps_2_4<float>(h->F, *W, h->zu32, st);
+  } else {
+    PS_TRY(amg_vcycle<double>(h->amg_u, sp, v, z, st));
+    PS_CUDA(cudaMemcpyAsync(W->vf, v + h->nu, sizeof(double) * h->nf, cudaMemcpyDeviceToDevice, st));
+    alg1_steps_2_4<double>(h->F, *W, z, st);
+  }
+  // step 5: z_p = M_pp^{-1} w_p
+  PS_TRY(amg_vcycle<T>(h->amg_p, sp, W->wp, W->zp, st));
+  // steps 6-8
+  alg1_steps_6_8<T>(h->F, *W, z + h->nu, h->prm.ilu_mode, st);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+ps_status apply_prec(ps_handle* h, const double* v, double* z) {
+  return h->mixed ? alg1<float>(h, v, z) : alg1<double>(h, v, z);
+}
+
+ps_status copy_in(Arena& ar, const void* src, size_t bytes, void** dst, bool host, cudaStream_t st) {
+  PS_TRY(ar.alloc(dst, bytes));
+  PS_CUDA(cudaMemcpyAsync(*dst, src, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  return PS_OK;
+}
+
+ps_status copy_bsr(ps_handle* h, const ps_bsr& B, int32_t** rp, int32_t** ci, const double** v) {
+  bool host = h->prm.host_ptrs != 0;
+  int64_t* rp64;
+  PS_TRY(copy_in(h->ar, B.rowptr, sizeof(int64_t) * (B.n_brow + 1), (void**)&rp64, host, h->st));
+  PS_TRY(h->ar.alloc(rp, B.n_brow + 1));
+  rowptr_to_i32(rp64, *rp, B.n_brow + 1, h->st);
+  PS_TRY(copy_in(h->ar, B.colind, sizeof(int32_t) * (B.nnzb + 1), (void**)ci, host, h->st));
+  void* vv;
+  PS_TRY(copy_in(h->ar, B.val, sizeof(double) * B.nnzb * B.br * B.bc, &vv, host, h->st));
+  *v = static_cast<const double*>(vv);
+  PS_CUDA(cudaStreamSynchronize(h->st));
+  h->ar.release(rp64);
+  return PS_OK;
+}
+
+bool bsr_ok(const ps_bsr& B, int64_t rows, int64_t cols, int br, int bc) {
+  return B.n_brow == rows && B.n_bcol == cols && B.br == br && B.bc == bc && B.rowptr && B.colind && B.val &&
+         B.nnzb >= 0 && B.nnzb < (int64_t(1) << 31) / 9;
+}
+
+ps_status build_flow(ps_handle* h) {
+  Arena& ar = h->arf;
+  cudaStream_t st = h->st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  FlowStage& F = h->F;
+  F.nx = h->grid.nx; F.ny = h->grid.ny; F.nz = h->grid.nz;
+  F.nc = h->nc; F.nnzb = int64_t(0);
+  int32_t tot = 0;
+  PS_CUDA(cudaMemcpyAsync(&tot, h->J.ff_rp + h->nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  F.nnzb = tot;
+  F.rp = h->J.ff_rp; F.ci = h->J.ff_ci;
+  F.fu_rp = h->J.fu_rp; F.fu_ci = h->J.fu_ci; F.fu_v = h->J.fu_v;
+  PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, h->dfs, h->mixed, st));
+  if (h->mixed) {
+    int64_t nfu = 0;
+    int32_t t2 = 0;
+    PS_CUDA(cudaMemcpyAsync(&t2, h->J.fu_rp + h->nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    nfu = t2;
+    PS_TRY(ar.alloc(&F.fu_vf, nfu * 6 + 1));
+    k_d2f<<<grid_for(nfu * 6, 256), 256, 0, st>>>(h->J.fu_v, F.fu_vf, nfu * 6);
+  }
+  AmgParams ap;
+  ap.theta = h->prm.theta_p; ap.coarse_max = h->prm.coarse_max_p; ap.max_levels = h->prm.max_levels;
+  ap.mixed = h->mixed;
+  PS_TRY(amg_build(ar, h->amg_p, 1, h->nc, F.nnzb, F.rp, F.ci, F.spp, ap, st));
+  if (h->mixed) {
+    PS_TRY(amg_alloc_work<float>(ar, h->amg_p));
+    PS_TRY(flow_alloc_work<float>(ar, F, h->w32));
+  } else {
+    PS_TRY(amg_alloc_work<double>(ar, h->amg_p));
+    PS_TRY(flow_alloc_work<double>(ar, F, h->w64));
+  }
+  cudaEventRecord(e1, st);
+  PS_CUDA(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&h->ms_setup_f, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return PS_OK;
+}
+
+ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
+  cudaStream_t st = h->st;
+  Arena& ar = h->ar;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  JacDev& J = h->J;
+  J.nn = h->nn; J.nc = h->nc;
+  PS_TRY(copy_bsr(h, jac->A_uu, &J.uu_rp, &J.uu_ci, &J.uu_v));
+  PS_TRY(copy_bsr(h, jac->A_uf, &J.uf_rp, &J.uf_ci, &J.uf_v));
+  PS_TRY(copy_bsr(h, jac->A_fu, &J.fu_rp, &J.fu_ci, &J.fu_v));
+  PS_TRY(copy_bsr(h, jac->A_ff, &J.ff_rp, &J.ff_ci, &J.ff_v));
+  PS_TRY(copy_in(ar, jac->d_fs, sizeof(double) * 2 * h->nc, (void**)&h->dfs, h->prm.host_ptrs != 0, st));
+  PS_TRY(flow_check_pattern(ar, h->grid, J.ff_rp, J.ff_ci, st));
+  // §5.2 mechanics: amg(A_uu^(SDC)) on the three diagonal components of each 3x3 block
+  int64_t nnzb = jac->A_uu.nnzb;
+  double* sdc;
+  PS_TRY(ar.alloc(&sdc, nnzb * 3));
+  k_sdc<<<grid_for(nnzb, 256), 256, 0, st>>>(nnzb, J.uu_v, sdc);
+  AmgParams ap;
+  ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
+  ap.mixed = h->mixed;
+  PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
+  if (h->mixed) {
+    PS_TRY(amg_alloc_work<float>(ar, h->amg_u));
+    PS_TRY(ar.alloc(&h->vu32, h->nu));
+    PS_TRY(ar.alloc(&h->zu32, h->nu));
+  } else {
+    PS_TRY(amg_alloc_work<double>(ar, h->amg_u));
+  }
+  cudaEventRecord(e1, st);
+  PS_CUDA(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&h->ms_setup_u, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // §5.3 flow stage
+  PS_TRY(build_flow(h));
+  // Krylov workspace
+  int m = h->m;
+  int64_t n = h->n;
+  PS_TRY(ar.alloc(&h->V, size_t(n) * (m + 1)));
+  PS_TRY(ar.alloc(&h->Z, size_t(n) * m));
+  PS_TRY(ar.alloc(&h->r, n));
+  PS_TRY(ar.alloc(&h->b, n));
+  PS_TRY(ar.alloc(&h->x, n));
+  int64_t gu = ceil_div(h->nn * 32, 256), gf = ceil_div(h->nc * 32, 256);
+  h->spmv_part = kRedBlocks + gu + gf;
+  PS_TRY(ar.alloc(&h->part, h->spmv_part));
+  PS_TRY(ar.alloc(&h->mpart, size_t(m + 2) * kRedBlocks));
+  KrylovState& K = h->K;
+  PS_TRY(ar.alloc(&K.H, size_t(m + 1) * m));
+  PS_TRY(ar.alloc(&K.cs, m)); PS_TRY(ar.alloc(&K.sn, m)); PS_TRY(ar.alloc(&K.g, m + 1));
+  PS_TRY(ar.alloc(&K.h1, m + 2)); PS_TRY(ar.alloc(&K.h2, m + 2)); PS_TRY(ar.alloc(&K.y, m + 1));
+  PS_TRY(ar.alloc(&K.sc, 16)); PS_TRY(ar.alloc(&K.flag, 4));
+  PS_CUDA(cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), st));
+  PS_CUDA(cudaMallocHost(&h->hsc, 16 * sizeof(double)));
+  PS_CUDA(cudaMallocHost(&h->hflag, 4 * sizeof(int)));
+  PS_CUDA(cudaStreamSynchronize(st));
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ps_params_default(ps_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->precision = PS_FP64;
+  p->restart = 100;
+  p->max_iters = 1000;
+  p->smoother = PS_SMOOTH_CHEBYSHEV;
+  p->pre = 1; p->post = 1;
+  p->cheb_degree = 2;
+  p->cheb_ratio = 20.0;
+  p->theta_u = 0.08; p->theta_p = 0.08;
+  p->coarse_max_u = 500; p->coarse_max_p = 500;
+  p->max_levels = 25;
+  p->ilu_mode = PS_ILU_LEVEL_LAUNCH;
+  p->spin_limit = 100000000;
+}
+
+ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params, ps_handle** out) {
+  if (!jac || !grid || !params || !out) return PS_ERR_INVALID;
+  *out = nullptr;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return PS_ERR_INVALID;
+  int64_t nn = int64_t(grid->nx + 1) * (grid->ny + 1) * (grid->nz + 1);
+  int64_t nc = int64_t(grid->nx) * grid->ny * grid->nz;
+  if (!bsr_ok(jac->A_uu, nn, nn, 3, 3) || !bsr_ok(jac->A_uf, nn, nc, 3, 2) || !bsr_ok(jac->A_fu, nc, nn, 2, 3) ||
+      !bsr_ok(jac->A_ff, nc, nc, 2, 2) || !jac->d_fs)
+    return PS_ERR_INVALID;
+  if (params->restart < 1 || params->restart > 120 || params->max_iters < 1) return PS_ERR_INVALID;
+  if (params->precision != PS_FP64 && params->precision != PS_MIXED_FP32) return PS_ERR_INVALID;
+  ps_handle* h = new ps_handle();
+  h->prm = *params;
+  h->grid = *grid;
+  h->st = (cudaStream_t)params->stream;
+  h->ar.stream = h->st;
+  h->arf.stream = h->st;
+  h->ar.budget = params->hbm_budget;
+  h->nn = nn; h->nc = nc; h->nu = 3 * nn; h->nf = 2 * nc; h->n = h->nu + h->nf;
+  h->mixed = params->precision == PS_MIXED_FP32;
+  h->m = params->restart;
+  ps_status s = setup_impl(h, jac);
+  if (s != PS_OK) {
+    ps_free(h);
+    return s;
+  }
+  *out = h;
+  return PS_OK;
+}
+
+ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
+  if (!h || !jac) return PS_ERR_INVALID;
+  if (!bsr_ok(jac->A_fu, h->nc, h->nn, 2, 3) || !bsr_ok(jac->A_ff, h->nc, h->nc, 2, 2) || !jac->d_fs ||
+      jac->A_ff.nnzb != h->F.nnzb)
+    return PS_ERR_INVALID;
+  cudaStream_t st = h->st;
+  bool host = h->prm.host_ptrs != 0;
+  auto kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.fu_v), jac->A_fu.val, sizeof(double) * jac->A_fu.nnzb * 6, kind, st));
+  PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.ff_v), jac->A_ff.val, sizeof(double) * jac->A_ff.nnzb * 4, kind, st));
+  PS_CUDA(cudaMemcpyAsync(h->dfs, jac->d_fs, sizeof(double) * 2 * h->nc, kind, st));
+  h->arf.free_all();
+  h->F = FlowStage();
+  h->amg_p = Amg();
+  h->w32 = FlowWork<float>();
+  h->w64 = FlowWork<double>();
+  return build_flow(h);
+}
+
+ps_status ps_spmv(ps_handle* h, const double* x, double* y) {
+  if (!h || !x || !y) return PS_ERR_INVALID;
+  jac_spmv(h->J, x, y, nullptr, nullptr, h->st);
+  PS_CUDA(cudaGetLastError());
+  PS_CUDA(cudaStreamSynchronize(h->st));
+  return PS_OK;
+}
+
+ps_status ps_apply_prec(ps_handle* h, const double* v, double* z) {
+  if (!h || !v || !z) return PS_ERR_INVALID;
+  PS_TRY(apply_prec(h, v, z));
+  PS_CUDA(cudaStreamSynchronize(h->st));
+  return PS_OK;
+}
+
+ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* stats) {
+  if (!h || !rhs || !x || !(tol > 0.0)) return PS_ERR_INVALID;
+  cudaStream_t st = h->st;
+  int64_t n = h->n;
+  int m = h->m;
+  KrylovState& K = h->K;
+  bool host = h->prm.host_ptrs != 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  double* xk = h->x;
+  fill_zero(xk, n, st);
+  // ||b||
+  multidot(h->V, n, 0, h->b, n, h->mpart, K.sc + 7, 1, nullptr, st);
+  PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  double bn2 = h->hsc[7];
+  ps_stats S;
+  std::memset(&S, 0, sizeof(S));
+  ps_status result = PS_OK;
+  if (!(bn2 > 0.0)) {
+    if (std::isnan(bn2)) result = PS_ERR_NAN;
+  } else {
+    double bnorm = std::sqrt(bn2);
+    double hb[2] = {bn2, bnorm};
+    PS_CUDA(cudaMemcpyAsync(K.sc + 3, &hb[0], sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(K.sc + 7, &hb[1], sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(h->r, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    int total = 0;
+    for (;;) {
+      cycle_start(K, m, st);
+      scale_vec(h->r, h->V, n, K.sc + 4, st);
+      int jend = -1;
+      bool brk = false, nanf = false;
+      for (int j = 0; j < m; ++j) {
+        double* vj = h->V + int64_t(j) * n;
+        double* zj = h->Z + int64_t(j) * n;
+        double* w = h->V + int64_t(j + 1) * n;
+        PS_TRY(apply_prec(h, vj, zj));
+        jac_spmv(h->J, zj, w, nullptr, nullptr, st);
+        // classical Gram-Schmidt with selective reorthogonalisation
+        multidot(h->V, n, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
+        PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        mupdate(h->V, n, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
+        arnoldi_check(K, st);
+        multidot(h->V, n, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
+        mupdate(h->V, n, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
+        arnoldi_finish(K, m, j, st);
+        scale_vec(w, w, n, K.sc + 4, st);
+        ++total;
+        PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaStreamSynchronize(st));
+        double est = h->hsc[5], hn = h->hsc[6];
+        S.est_relres = est;
+        jend = j;
+        if (h->hflag[1]) { nanf = true; break; }
+        if (!(hn > 1e-300 * bnorm)) brk = true;
+        if (est <= tol || brk || total >= h->prm.max_iters) break;
+      }
+      if (nanf) { result = PS_ERR_NAN; break; }
+      hessenberg_solve(K, m, jend, st);
+      maxpy(h->Z, n, jend + 1, K.y, xk, n, st);
+      jac_spmv(h->J, xk, h->r, h->b, h->part, st);
+      finish_sum(h->part, K.sc + 3, st);
+      PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PS_CUDA(cudaStreamSynchronize(st));
+      double rr = std::sqrt(h->hsc[3]) / bnorm;
+      S.true_relres = rr;
+      S.iters = total;
+      if (std::isnan(rr)) { result = PS_ERR_NAN; break; }
+      if (rr <= tol) { result = PS_OK; break; }
+      if (brk) { result = PS_ERR_BREAKDOWN; break; }
+      if (total >= h->prm.max_iters) { result = PS_ERR_NOT_CONVERGED; break; }
+      S.restarts++;
+    }
+  }
+  PS_CUDA(cudaMemcpyAsync(x, xk, sizeof(double) * n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  cudaEventRecord(e1, st);
+  PS_CUDA(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&S.ms_solve, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.ms_setup_u = h->ms_setup_u;
+  S.ms_setup_f = h->ms_setup_f;
+  S.handle_bytes = h->ar.bytes + h->arf.bytes;
+  S.levels_u = int32_t(h->amg_u.L.size());
+  S.levels_p = int32_t(h->amg_p.L.size());
+  if (stats) *stats = S;
+  return result;
+}
+
+int32_t ps_amg_nlevels(ps_handle* h, int32_t which) {
+  if (!h) return 0;
+  return int32_t((which == 0 ? h->amg_u : h->amg_p).L.size());
+}
+
+ps_status ps_amg_level_info(ps_handle* h, int32_t which, int32_t level, int64_t* n, int64_t* nnz, int64_t* nagg) {
+  if (!h) return PS_ERR_INVALID;
+  Amg& A = which == 0 ? h->amg_u : h->amg_p;
+  if (level < 0 || level >= int32_t(A.L.size())) return PS_ERR_INVALID;
+  if (n) *n = A.L[level].n;
+  if (nnz) *nnz = A.L[level].nnz;
+  if (nagg) *nagg = A.L[level].nagg;
+  return PS_OK;
+}
+
+ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t* rowptr, int32_t* colind,
+                            double* val, int32_t* agg) {
+  if (!h) return PS_ERR_INVALID;
+  Amg& A = which == 0 ? h->amg_u : h->amg_p;
+  if (level < 0 || level >= int32_t(A.L.size())) return PS_ERR_INVALID;
+  AmgLevel& L = A.L[level];
+  cudaStream_t st = h->st;
+  if (rowptr) {
+    int64_t* tmp;
+    PS_TRY(h->ar.alloc(&tmp, L.n + 1));
+    k_i32_to_i64<<<grid_for(L.n + 1, 256), 256, 0, st>>>(L.rp, tmp, L.n + 1);
+    PS_CUDA(cudaMemcpyAsync(rowptr, tmp, sizeof(int64_t) * (L.n + 1), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    h->ar.release(tmp);
+  }
+  if (colind) PS_CUDA(cudaMemcpyAsync(colind, L.ci, sizeof(int32_t) * L.nnz, cudaMemcpyDeviceToHost, st));
+  if (val) PS_CUDA(cudaMemcpyAsync(val, L.v, sizeof(double) * L.nnz * A.nc, cudaMemcpyDeviceToHost, st));
+  if (agg) {
+    if (L.agg) PS_CUDA(cudaMemcpyAsync(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, st));
+    else for (int64_t i = 0; i < L.n; ++i) agg[i] = -1;
+  }
+  PS_CUDA(cudaStreamSynchronize(st));
+  return PS_OK;
+}
+
+ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv) {
+  if (!h) return PS_ERR_INVALID;
+  if (spp) PS_CUDA(cudaMemcpyAsync(spp, h->F.spp, sizeof(double) * h->F.nnzb, cudaMemcpyDeviceToHost, h->st));
+  if (dinv) PS_CUDA(cudaMemcpyAsync(dinv, h->F.dinv, sizeof(double) * 4 * h->nc, cudaMemcpyDeviceToHost, h->st));
+  PS_CUDA(cudaStreamSynchronize(h->st));
+  return PS_OK;
+}
+
+void ps_free(ps_handle* h) {
+  if (!h) return;
+  h->arf.free_all();
+  h->ar.free_all();
+  cudaStreamSynchronize(h->st);
+  if (h->hsc) cudaFreeHost(h->hsc);
+  if (h->hflag) cudaFreeHost(h->hflag);
+  delete h;
+}
+
+const char* ps_strerror(ps_status s) {
+  switch (s) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID: return "invalid argument, shape or pattern";
+    case PS_ERR_OOM: return "device out of memory";
+    case PS_ERR_CUDA: return ps_internal::last_error().empty() ? "CUDA error" : ps_internal::last_error().c_str();
+    case PS_ERR_NOT_CONVERGED: return "not converged within max_iters";
+    case PS_ERR_BREAKDOWN: return "Krylov breakdown before convergence";
+    case PS_ERR_NAN: return "NaN or Inf encountered";
+    case PS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PS_ERR_BUDGET: return "HBM budget exceeded";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

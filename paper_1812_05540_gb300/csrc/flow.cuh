@@ -1,0 +1,51 @@
+// Flow stage of the preconditioner: the fixed-stress Schur approximation
+// S_ff^(FS) (§5.1), the quasi-IMPES reduction to S_pp (§5.3) and block ILU(0)
+// of S_ff^(FS) in the interleaved (s, p) ordering (§5.3, option 2).
+#pragma once
+#include "internal.cuh"
+
+namespace ps_internal {
+
+struct FlowStage {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t nc = 0, nnzb = 0;
+  int32_t *rp = nullptr, *ci = nullptr;  // A_ff pattern (7-point), int32
+  int32_t* diagpos = nullptr;            // position of the diagonal block per row
+  double* sff = nullptr;                 // S_ff^(FS) blocks, 4 per entry, FP64
+  double* spp = nullptr;                 // S_pp^(cpr-fs), 1 per entry, FP64
+  double *dss = nullptr, *dps = nullptr; // quasi-IMPES diagonals
+  double* dinv = nullptr;                // inv(U_ii) of block ILU(0), 4 per cell
+  float *sff_f = nullptr, *aps_f = nullptr, *dinv_f = nullptr, *dss_f = nullptr;
+  double* aps = nullptr;                 // A_ps entries (lower-left of each block), FP64
+  // wavefront levels of the natural ordering (level = i + j + k)
+  int nlev = 0;
+  int32_t* lev_cells = nullptr;
+  std::vector<int32_t> lev_off;          // host copy, nlev + 1
+  // A_fu for Algorithm 1 step 2
+  int32_t *fu_rp = nullptr, *fu_ci = nullptr;
+  const double* fu_v = nullptr;
+  float* fu_vf = nullptr;
+};
+
+// Build S_ff^(FS), S_pp, the level lists and the ILU(0) factors from the
+// caller's FP64 A_ff / d_fs (device pointers, already int32 row pointers).
+ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_t* ff_ci, const double* ff_v,
+                     const double* d_fs, bool mixed, cudaStream_t st);
+ps_status flow_check_pattern(Arena& ar, const ps_grid& g, const int32_t* ff_rp, const int32_t* ff_ci,
+                             cudaStream_t st);
+
+// Algorithm 1 steps 2-4 and 6-8 for precision T (pressure V-cycle in between,
+// called by the driver).  v_f, y, z_s, w_p, t, dz are per-cell work vectors.
+template <class T>
+struct FlowWork {
+  T *vf, *y, *zs, *wp, *zp, *t, *dz;
+};
+template <class T>
+ps_status flow_alloc_work(Arena& ar, const FlowStage& F, FlowWork<T>& W);
+template <class T>
+void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaStream_t st);
+// steps 6-8: ILU(0) sweeps; writes z_f (interleaved, FP64) to zout
+template <class T>
+void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int ilu_mode, cudaStream_t st);
+
+}  // namespace ps_internal

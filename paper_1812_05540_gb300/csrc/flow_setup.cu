@@ -1,0 +1,183 @@
+// Flow-stage setup.  Compiled without floating-point contraction: S_pp feeds
+// the pressure aggregation, so its entries are formed with exactly the
+// operations of the reduction formula, in that order.
+#include "flow.cuh"
+
+namespace ps_internal {
+namespace {
+
+__device__ __forceinline__ void mul22(const double* a, const double* b, double* c) {
+  double c0 = a[0] * b[0] + a[1] * b[2], c1 = a[0] * b[1] + a[1] * b[3];
+  double c2 = a[2] * b[0] + a[3] * b[2], c3 = a[2] * b[1] + a[3] * b[3];
+  c[0] = c0; c[1] = c1; c[2] = c2; c[3] = c3;
+}
+__device__ __forceinline__ void inv22(const double* a, double* r) {
+  double det = a[0] * a[3] - a[1] * a[2];
+  r[0] = a[3] / det; r[1] = -a[1] / det; r[2] = -a[2] / det; r[3] = a[0] / det;
+}
+
+// the A_ff pattern must be the 7-point TPFA stencil of the grid in natural order
+__global__ void k_check7(int nx, int ny, int nz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         int* __restrict__ bad) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (c >= nc) return;
+  int i = int(c % nx), j = int((c / nx) % ny), k = int(c / (int64_t(nx) * ny));
+  int64_t nxy = int64_t(nx) * ny;
+  int64_t want[7];
+  int m = 0;
+  if (k > 0) want[m++] = c - nxy;
+  if (j > 0) want[m++] = c - nx;
+  if (i > 0) want[m++] = c - 1;
+  want[m++] = c;
+  if (i + 1 < nx) want[m++] = c + 1;
+  if (j + 1 < ny) want[m++] = c + nx;
+  if (k + 1 < nz) want[m++] = c + nxy;
+  if (rp[c + 1] - rp[c] != m) { atomicExch(bad, 1); return; }
+  for (int t = 0; t < m; ++t)
+    if (ci[rp[c] + t] != want[t]) { atomicExch(bad, 1); return; }
+}
+
+// S_ff^(FS) = A_ff + [[0 D_sp] [0 D_pp]] on the diagonal (§5.1);
+// quasi-IMPES: d_ss = (A_ss)_ii, d_ps = (A_ps)_ii, S_pp = A_pp^(FS) - (d_ps/d_ss) A_sp^(FS) (§5.3)
+__global__ void k_sff_spp(int64_t nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ aff, const double* __restrict__ dfs, double* __restrict__ sff,
+                          double* __restrict__ spp, double* __restrict__ dss, double* __restrict__ dps,
+                          double* __restrict__ aps, int32_t* __restrict__ diagpos) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  int32_t qd = rp[c];
+  while (ci[qd] != c) ++qd;
+  diagpos[c] = qd;
+  double s = aff[int64_t(qd) * 4 + 0], ps = aff[int64_t(qd) * 4 + 2];
+  dss[c] = s;
+  dps[c] = ps;
+  double ratio = ps / s;
+  for (int32_t q = rp[c]; q < rp[c + 1]; ++q) {
+    double b0 = aff[int64_t(q) * 4 + 0], b1 = aff[int64_t(q) * 4 + 1];
+    double b2 = aff[int64_t(q) * 4 + 2], b3 = aff[int64_t(q) * 4 + 3];
+    if (q == qd) {
+      b1 = b1 + dfs[2 * c];
+      b3 = b3 + dfs[2 * c + 1];
+    }
+    sff[int64_t(q) * 4 + 0] = b0; sff[int64_t(q) * 4 + 1] = b1;
+    sff[int64_t(q) * 4 + 2] = b2; sff[int64_t(q) * 4 + 3] = b3;
+    spp[q] = b3 - ratio * b1;
+    aps[q] = b2;
+  }
+}
+
+__global__ void k_level_count(int nx, int ny, int nz, int32_t* __restrict__ cnt) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (c >= nc) return;
+  int i = int(c % nx), j = int((c / nx) % ny), k = int(c / (int64_t(nx) * ny));
+  atomicAdd(&cnt[i + j + k], 1);
+}
+__global__ void k_level_fill(int nx, int ny, int nz, int32_t* __restrict__ cursor, int32_t* __restrict__ cells) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (c >= nc) return;
+  int i = int(c % nx), j = int((c / nx) % ny), k = int(c / (int64_t(nx) * ny));
+  cells[atomicAdd(&cursor[i + j + k], 1)] = int32_t(c);
+}
+
+// Block ILU(0) of S_ff^(FS) in natural order, one wavefront level: with the
+// 7-point stencil no two lower neighbours of a cell are coupled, so the IKJ
+// elimination only updates the diagonal block:
+//   U_ii = S_ii - sum_{k<i} (S_ik inv(U_kk)) S_ki   (k ascending)
+__global__ void k_ilu_factor(const int32_t* __restrict__ cells, int32_t ncell_lev, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, const int32_t* __restrict__ diagpos,
+                             const double* __restrict__ sff, double* __restrict__ dinv) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncell_lev) return;
+  int32_t i = cells[t];
+  int32_t qd = diagpos[i];
+  double D[4] = {sff[int64_t(qd) * 4], sff[int64_t(qd) * 4 + 1], sff[int64_t(qd) * 4 + 2], sff[int64_t(qd) * 4 + 3]};
+  for (int32_t q = rp[i]; q < qd; ++q) {
+    int32_t k = ci[q];
+    double L[4], U[4];
+    mul22(&sff[int64_t(q) * 4], &dinv[int64_t(k) * 4], L);
+    // (k, i) is the upper block of row k
+    int32_t qk = diagpos[k] + 1;
+    while (ci[qk] != i) ++qk;
+    mul22(L, &sff[int64_t(qk) * 4], U);
+    for (int e = 0; e < 4; ++e) D[e] -= U[e];
+  }
+  inv22(D, &dinv[int64_t(i) * 4]);
+}
+
+__global__ void k_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = float(a[t]);
+}
+
+}  // namespace
+
+ps_status flow_check_pattern(Arena& ar, const ps_grid& g, const int32_t* ff_rp, const int32_t* ff_ci,
+                             cudaStream_t st) {
+  int* bad;
+  PS_TRY(ar.alloc(&bad, 1));
+  PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  int64_t nc = int64_t(g.nx) * g.ny * g.nz;
+  k_check7<<<grid_for(nc, 256), 256, 0, st>>>(g.nx, g.ny, g.nz, ff_rp, ff_ci, bad);
+  int h = 0;
+  PS_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  ar.release(bad);
+  return h ? PS_ERR_INVALID : PS_OK;
+}
+
+ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_t* ff_ci, const double* ff_v,
+                     const double* d_fs, bool mixed, cudaStream_t st) {
+  int64_t nc = F.nc, nnzb = F.nnzb;
+  if (!F.sff) {
+    PS_TRY(ar.alloc(&F.sff, nnzb * 4));
+    PS_TRY(ar.alloc(&F.spp, nnzb));
+    PS_TRY(ar.alloc(&F.aps, nnzb));
+    PS_TRY(ar.alloc(&F.dss, nc));
+    PS_TRY(ar.alloc(&F.dps, nc));
+    PS_TRY(ar.alloc(&F.dinv, nc * 4));
+    PS_TRY(ar.alloc(&F.diagpos, nc));
+    if (mixed) {
+      PS_TRY(ar.alloc(&F.sff_f, nnzb * 4));
+      PS_TRY(ar.alloc(&F.aps_f, nnzb));
+      PS_TRY(ar.alloc(&F.dinv_f, nc * 4));
+      PS_TRY(ar.alloc(&F.dss_f, nc));
+    }
+    // wavefront levels
+    F.nlev = F.nx + F.ny + F.nz - 2;
+    int32_t *cnt, *off, *cursor;
+    PS_TRY(ar.alloc(&cnt, F.nlev + 1));
+    PS_TRY(ar.alloc(&off, F.nlev + 1));
+    PS_TRY(ar.alloc(&cursor, F.nlev + 1));
+    PS_TRY(ar.alloc(&F.lev_cells, nc));
+    PS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (F.nlev + 1), st));
+    k_level_count<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cnt);
+    PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
+    PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
+    k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
+    F.lev_off.resize(F.nlev + 1);
+    PS_CUDA(cudaMemcpyAsync(F.lev_off.data(), off, sizeof(int32_t) * (F.nlev + 1), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    ar.release(cnt); ar.release(off); ar.release(cursor);
+  }
+  k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
+                                               F.diagpos);
+  for (int l = 0; l < F.nlev; ++l) {
+    int32_t m = F.lev_off[l + 1] - F.lev_off[l];
+    k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
+                                                   F.dinv);
+  }
+  PS_CUDA(cudaGetLastError());
+  if (mixed) {
+    k_f32<<<grid_for(nnzb * 4, 256), 256, 0, st>>>(F.sff, F.sff_f, nnzb * 4);
+    k_f32<<<grid_for(nnzb, 256), 256, 0, st>>>(F.aps, F.aps_f, nnzb);
+    k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
+    k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
+    PS_CUDA(cudaGetLastError());
+  }
+  return PS_OK;
+}
+
+}  // namespace ps_internal

@@ -1,0 +1,344 @@
+// FP64 Jacobian SpMV and flexible-GMRES kernels.  Every reduction is taken in
+// a fixed order (per-block partial sums, then one block over the partials), so
+// repeated solves give identical iterates.
+#include <cmath>
+
+#include "krylov.cuh"
+
+namespace ps_internal {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Displacement rows: one warp per node.  A_uu row: 27 blocks x 3 rows = up to
+// 81 row segments of 3 doubles; A_uf row: up to 8 blocks x 3 rows of 2 doubles.
+__global__ void __launch_bounds__(256) k_spmv_u(JacDev J, const double* __restrict__ x, double* __restrict__ y,
+                                                const double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[8];
+  int64_t I = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  double r2 = 0.0;
+  if (I < J.nn) {
+    const double* xu = x;
+    const double* xf = x + 3 * J.nn;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    int32_t q0 = J.uu_rp[I], q1 = J.uu_rp[I + 1];
+    int nseg = (q1 - q0) * 3;
+    for (int s = lane; s < nseg; s += 32) {
+      int32_t q = q0 + s / 3;
+      int r = s % 3;
+      int64_t c = J.uu_ci[q];
+      const double* v = J.uu_v + int64_t(q) * 9 + r * 3;
+      double t = v[0] * xu[3 * c] + v[1] * xu[3 * c + 1] + v[2] * xu[3 * c + 2];
+      acc0 += r == 0 ? t : 0.0;
+      acc1 += r == 1 ? t : 0.0;
+      acc2 += r == 2 ? t : 0.0;
+    }
+    int32_t p0 = J.uf_rp[I], p1 = J.uf_rp[I + 1];
+    int mseg = (p1 - p0) * 3;
+    for (int s = lane; s < mseg; s += 32) {
+      int32_t q = p0 + s / 3;
+      int r = s % 3;
+      int64_t c = J.uf_ci[q];
+      const double* v = J.uf_v + int64_t(q) * 6 + r * 2;
+      double t = v[0] * xf[2 * c] + v[1] * xf[2 * c + 1];
+      acc0 += r == 0 ? t : 0.0;
+      acc1 += r == 1 ? t : 0.0;
+      acc2 += r == 2 ? t : 0.0;
+    }
+    acc0 = warp_sum(acc0);
+    acc1 = warp_sum(acc1);
+    acc2 = warp_sum(acc2);
+    if (lane < 3) {
+      double a = lane == 0 ? acc0 : lane == 1 ? acc1 : acc2;
+      if (b) {
+        a = b[3 * I + lane] - a;
+        r2 = a * a;
+      }
+      y[3 * I + lane] = a;
+    }
+  }
+  if (part) {
+    r2 = warp_sum(r2);
+    if (lane == 0) red[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      part[blockIdx.x] = s;
+    }
+  }
+}
+
+// Flow rows: one warp per cell; lanes 0..15 take the 8 A_fu blocks x 2 rows,
+// lanes 16..29 the 7 A_ff blocks x 2 rows.
+__global__ void __launch_bounds__(256) k_spmv_f(JacDev J, const double* __restrict__ x, double* __restrict__ y,
+                                                const double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[8];
+  int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  double r2 = 0.0;
+  if (c < J.nc) {
+    const double* xu = x;
+    const double* xf = x + 3 * J.nn;
+    double a0 = 0.0, a1 = 0.0;
+    if (lane < 16) {
+      int32_t q = J.fu_rp[c] + (lane >> 1);
+      int r = lane & 1;
+      if (q < J.fu_rp[c + 1]) {
+        int64_t J3 = int64_t(J.fu_ci[q]) * 3;
+        const double* v = J.fu_v + int64_t(q) * 6 + r * 3;
+        double t = v[0] * xu[J3] + v[1] * xu[J3 + 1] + v[2] * xu[J3 + 2];
+        if (r == 0) a0 = t; else a1 = t;
+      }
+    } else {
+      int s = lane - 16;
+      int32_t q = J.ff_rp[c] + (s >> 1);
+      int r = s & 1;
+      if (s < 14 && q < J.ff_rp[c + 1]) {
+        int64_t j2 = int64_t(J.ff_ci[q]) * 2;
+        const double* v = J.ff_v + int64_t(q) * 4 + r * 2;
+        double t = v[0] * xf[j2] + v[1] * xf[j2 + 1];
+        if (r == 0) a0 = t; else a1 = t;
+      }
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if (lane < 2) {
+      double a = lane == 0 ? a0 : a1;
+      int64_t o = 3 * J.nn + 2 * c + lane;
+      if (b) {
+        a = b[o] - a;
+        r2 = a * a;
+      }
+      y[o] = a;
+    }
+  }
+  if (part) {
+    r2 = warp_sum(r2);
+    if (lane == 0) red[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      part[blockIdx.x] = s;
+    }
+  }
+}
+
+// fold per-block partials into kRedBlocks slots (fixed mapping)
+__global__ void k_fold(const double* __restrict__ in, int64_t nin, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kRedBlocks) return;
+  double s = 0.0;
+  for (int64_t i = t; i < nin; i += kRedBlocks) s += in[i];
+  out[t] = s;
+}
+
+__global__ void k_finish_sum(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += 256) a += part[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// ---- multi-dot h = V^T w (columns in chunks of 8) ----
+constexpr int kChunk = 8;
+__global__ void __launch_bounds__(256) k_multidot(const double* __restrict__ V, int64_t ldv, int m,
+                                                  const double* __restrict__ w, int64_t n, int with_norm,
+                                                  double* __restrict__ part, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  __shared__ double red[kChunk][8];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int mm = m + (with_norm ? 1 : 0);
+  for (int c0 = 0; c0 < mm; c0 += kChunk) {
+    double acc[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) acc[k] = 0.0;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+      double we = w[e];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k) {
+        int c = c0 + k;
+        if (c < m) acc[k] += V[int64_t(c) * ldv + e] * we;
+        else if (c == m && with_norm) acc[k] += we * we;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      double v = warp_sum(acc[k]);
+      if (lane == 0) red[k][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kChunk && c0 + threadIdx.x < mm) {
+      double s = 0.0;
+      for (int q = 0; q < 8; ++q) s += red[threadIdx.x][q];
+      part[int64_t(c0 + threadIdx.x) * kRedBlocks + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// one warp per column: h[c] = sum of the kRedBlocks partials (fixed order)
+__global__ void k_multidot_final(const double* __restrict__ part, int mm, double* __restrict__ h,
+                                 const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (c >= mm) return;
+  double s = 0.0;
+  for (int i = lane; i < kRedBlocks; i += 32) s += part[int64_t(c) * kRedBlocks + i];
+  s = warp_sum(s);
+  if (lane == 0) h[c] = s;
+}
+
+__global__ void __launch_bounds__(256) k_mupdate(const double* __restrict__ V, int64_t ldv, int m,
+                                                 const double* __restrict__ h, double* __restrict__ w, int64_t n,
+                                                 double* __restrict__ part, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  __shared__ double hs[128];
+  __shared__ double red[8];
+  for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  double r2 = 0.0;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    double s = w[e];
+    for (int c = 0; c < m; ++c) s -= V[int64_t(c) * ldv + e] * hs[c];
+    w[e] = s;
+    r2 += s * s;
+  }
+  r2 = warp_sum(r2);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += red[q];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_maxpy(const double* __restrict__ Z, int64_t ldz, int m, const double* __restrict__ y,
+                        double* __restrict__ x, int64_t n) {
+  __shared__ double ys[128];
+  for (int c = threadIdx.x; c < m; c += blockDim.x) ys[c] = y[c];
+  __syncthreads();
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    double s = x[e];
+    for (int c = 0; c < m; ++c) s += Z[int64_t(c) * ldz + e] * ys[c];
+    x[e] = s;
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                        const double* __restrict__ sc) {
+  double a = *sc;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    y[e] = x[e] * a;
+}
+__global__ void k_zero(double* __restrict__ x, int64_t n) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x)
+    x[e] = 0.0;
+}
+
+// Daniel-Gragg-Kaufman-Stewart test: reorthogonalise when ||w'|| < ||w|| / sqrt(2)
+__global__ void k_arnoldi_check(double* sc, int* flag) {
+  flag[0] = (sc[1] < 0.5 * sc[0]) ? 1 : 0;
+}
+
+// column j of the Hessenberg matrix, Givens rotations, residual estimate
+__global__ void k_arnoldi_finish(double* H, double* cs, double* sn, double* g, const double* h1, const double* h2,
+                                 double* sc, int* flag, int m, int j) {
+  int re = flag[0];
+  double hn2 = re ? sc[2] : sc[1];
+  double hn = sqrt(hn2);
+  double* col = H + int64_t(j) * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + (re ? h2[i] : 0.0);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    double a = col[i], c = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * c;
+    col[i + 1] = -sn[i] * a + cs[i] * c;
+  }
+  double a = col[j], c = col[j + 1];
+  double rr = hypot(a, c);
+  cs[j] = a / rr;
+  sn[j] = c / rr;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  sc[5] = fabs(g[j + 1]) / sc[7];
+  sc[6] = hn;
+  sc[4] = hn > 0.0 ? 1.0 / hn : 0.0;
+  flag[1] = (isnan(sc[5]) || isnan(hn) || isinf(hn)) ? 1 : 0;
+}
+
+__global__ void k_cycle_start(double* g, double* sc, int m) {
+  double beta = sqrt(sc[3]);
+  for (int i = 0; i <= m; ++i) g[i] = 0.0;
+  g[0] = beta;
+  sc[4] = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+__global__ void k_hsolve(const double* H, const double* g, double* y, int m, int k) {
+  for (int i = k; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c <= k; ++c) s -= H[int64_t(c) * (m + 1) + i] * y[c];
+    y[i] = s / H[int64_t(i) * (m + 1) + i];
+  }
+}
+
+constexpr int kVecBlocks = 1216;  // 8 x 152 SMs
+
+}  // namespace
+
+void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, double* part, cudaStream_t st) {
+  int64_t gu = ceil_div(J.nn * 32, 256), gf = ceil_div(J.nc * 32, 256);
+  // partial sums: u blocks first, then f blocks, folded into kRedBlocks slots
+  double* pu = part ? part + kRedBlocks : nullptr;
+  double* pf = part ? part + kRedBlocks + gu : nullptr;
+  k_spmv_u<<<unsigned(gu), 256, 0, st>>>(J, x, y, b, pu);
+  k_spmv_f<<<unsigned(gf), 256, 0, st>>>(J, x, y, b, pf);
+  if (part) k_fold<<<grid_for(kRedBlocks, 256), 256, 0, st>>>(part + kRedBlocks, gu + gf, part);
+}
+
+void multidot(const double* V, int64_t ldv, int m, const double* w, int64_t n, double* part, double* h,
+              int with_norm, const int* gate, cudaStream_t st) {
+  k_multidot<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, w, n, with_norm, part, gate);
+  int mm = m + (with_norm ? 1 : 0);
+  k_multidot_final<<<grid_for(int64_t(mm) * 32, 256), 256, 0, st>>>(part, mm, h, gate);
+}
+
+void mupdate(const double* V, int64_t ldv, int m, const double* h, double* w, int64_t n, double* part,
+             double* norm2, const int* gate, cudaStream_t st) {
+  k_mupdate<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, h, w, n, part, gate);
+  k_finish_sum<<<1, 256, 0, st>>>(part, norm2);
+}
+
+void maxpy(const double* Z, int64_t ldz, int m, const double* y, double* x, int64_t n, cudaStream_t st) {
+  k_maxpy<<<kVecBlocks, 256, 0, st>>>(Z, ldz, m, y, x, n);
+}
+void finish_sum(const double* part, double* out, cudaStream_t st) { k_finish_sum<<<1, 256, 0, st>>>(part, out); }
+void scale_vec(const double* x, double* y, int64_t n, const double* scale, cudaStream_t st) {
+  k_scale<<<kVecBlocks, 256, 0, st>>>(x, y, n, scale);
+}
+void fill_zero(double* x, int64_t n, cudaStream_t st) { k_zero<<<kVecBlocks, 256, 0, st>>>(x, n); }
+
+void arnoldi_check(KrylovState& K, cudaStream_t st) { k_arnoldi_check<<<1, 1, 0, st>>>(K.sc, K.flag); }
+void arnoldi_finish(KrylovState& K, int m, int j, cudaStream_t st) {
+  k_arnoldi_finish<<<1, 1, 0, st>>>(K.H, K.cs, K.sn, K.g, K.h1, K.h2, K.sc, K.flag, m, j);
+}
+void cycle_start(KrylovState& K, int m, cudaStream_t st) { k_cycle_start<<<1, 1, 0, st>>>(K.g, K.sc, m); }
+void hessenberg_solve(KrylovState& K, int m, int k, cudaStream_t st) { k_hsolve<<<1, 1, 0, st>>>(K.H, K.g, K.y, m, k); }
+
+}  // namespace ps_internal

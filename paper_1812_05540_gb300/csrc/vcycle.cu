@@ -1,0 +1,332 @@
+// V-cycle apply of the smoothed-aggregation hierarchy (M_uu^{-1} of §5.2 and
+// M_pp^{-1} of §5.3): Chebyshev or l1-Jacobi smoothing, residual, restriction
+// by R = P^T, coarse correction by P, dense coarsest solve.  Vectors hold nc
+// interleaved components (node-major x,y,z for the SDC mechanics operator).
+#include <utility>
+
+#include "amg.cuh"
+
+namespace ps_internal {
+namespace {
+
+template <class T, int NC, int LANES>
+struct Row {
+  // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum
+  template <class XF>
+  __device__ __forceinline__ static void dot(bool active, int32_t q0, int32_t q1, const int32_t* __restrict__ ci,
+                                             const T* __restrict__ v, XF xf, int sub, T (&s)[NC]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = T(0);
+    if (active)
+      for (int32_t q = q0 + sub; q < q1; q += LANES) {
+        int32_t j = __ldg(ci + q);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] += __ldg(v + int64_t(q) * NC + c) * xf(j, c);
+      }
+#pragma unroll
+    for (int off = LANES / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+  }
+};
+
+#define ROW_SETUP                                                        \
+  int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;         \
+  int64_t i = tid / LANES;                                               \
+  int sub = int(tid % LANES);                                            \
+  bool active = i < n;                                                   \
+  int32_t q0 = active ? rp[i] : 0, q1 = active ? rp[i + 1] : 0;
+
+// Chebyshev from x = 0, first two steps fused:
+// d0 = D^{-1} b / theta; r = D^{-1}(b - A d0); d1 = c1 d0 + c2 r; x = d0 + d1
+template <class T, int NC, int LANES>
+__global__ void k_cheb_pre(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const T* __restrict__ v, const T* __restrict__ dg, const T* __restrict__ b,
+                           T* __restrict__ x, T* __restrict__ dout, double3 inv_theta, double3 c1, double3 c2) {
+  ROW_SETUP
+  const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
+  auto xf = [&](int32_t j, int c) { return (b[int64_t(j) * NC + c] / dg[int64_t(j) * NC + c]) * T(it[c]); };
+  T s[NC];
+  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  if (active && sub == 0) {
+    const double a1[3] = {c1.x, c1.y, c1.z}, a2[3] = {c2.x, c2.y, c2.z};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T bi = b[i * NC + c], di = dg[i * NC + c];
+      T d0 = (bi / di) * T(it[c]);
+      T r = (bi - s[c]) / di;
+      T d1 = T(a1[c]) * d0 + T(a2[c]) * r;
+      x[i * NC + c] = d0 + d1;
+      if (dout) dout[i * NC + c] = d1;
+    }
+  }
+}
+
+// one Chebyshev step from a nonzero x: r = D^{-1}(b - A x); d = c1 d + c2 r; xo = x + d
+// (first == true: d = r / theta, i.e. c1 = 0, c2 = 1/theta)
+template <class T, int NC, int LANES>
+__global__ void k_cheb_step(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const T* __restrict__ v, const T* __restrict__ dg, const T* __restrict__ b,
+                            const T* __restrict__ x, T* __restrict__ xo, T* __restrict__ d, double3 c1, double3 c2,
+                            int first) {
+  ROW_SETUP
+  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  T s[NC];
+  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  if (active && sub == 0) {
+    const double a1[3] = {c1.x, c1.y, c1.z}, a2[3] = {c2.x, c2.y, c2.z};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T r = (b[i * NC + c] - s[c]) / dg[i * NC + c];
+      T dn = first ? T(a2[c]) * r : T(a1[c]) * d[i * NC + c] + T(a2[c]) * r;
+      xo[i * NC + c] = x[i * NC + c] + dn;
+      if (d) d[i * NC + c] = dn;
+    }
+  }
+}
+
+// l1-Jacobi: xo = x + (b - A x) / dl1
+template <class T, int NC, int LANES>
+__global__ void k_l1_step(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const T* __restrict__ v, const T* __restrict__ dl1, const T* __restrict__ b,
+                          const T* __restrict__ x, T* __restrict__ xo) {
+  ROW_SETUP
+  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  T s[NC];
+  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  if (active && sub == 0)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xo[i * NC + c] = x[i * NC + c] + (b[i * NC + c] - s[c]) / dl1[i * NC + c];
+}
+
+template <class T, int NC>
+__global__ void k_l1_first(int64_t n, const T* __restrict__ dl1, const T* __restrict__ b, T* __restrict__ x) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n * NC) x[t] = b[t] / dl1[t];
+}
+
+template <class T, int NC>
+__global__ void k_cheb_first1(int64_t n, const T* __restrict__ dg, const T* __restrict__ b, T* __restrict__ x,
+                              double3 inv_theta) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
+  if (t < n * NC) x[t] = (b[t] / dg[t]) * T(it[t % NC]);
+}
+
+// r = b - A x
+template <class T, int NC, int LANES>
+__global__ void k_resid(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                        const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
+                        T* __restrict__ r) {
+  ROW_SETUP
+  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  T s[NC];
+  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  if (active && sub == 0)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) r[i * NC + c] = b[i * NC + c] - s[c];
+}
+
+// y = M x (restriction with R, or y += P x when add)
+template <class T, int NC, int LANES>
+__global__ void k_spmv(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, int add) {
+  ROW_SETUP
+  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  T s[NC];
+  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  if (active && sub == 0)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) y[i * NC + c] = add ? y[i * NC + c] + s[c] : s[c];
+}
+
+// coarsest: x = inv_c b_c per component, one warp per row
+template <class T, int NC>
+__global__ void k_dense_solve(int64_t n, const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n * NC) return;
+  int c = int(w / n);
+  int64_t i = w % n;
+  const T* row = inv + (int64_t(c) * n + i) * n;
+  T s = T(0);
+  for (int64_t j = lane; j < n; j += 32) s += row[j] * b[j * NC + c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[i * NC + c] = s;
+}
+
+template <class T>
+struct LevelT {
+  const T *v, *dg, *dl1, *pv, *rv, *inv;
+};
+template <class T>
+LevelT<T> view(const AmgLevel& L) {
+  LevelT<T> o;
+  if constexpr (sizeof(T) == 4) {
+    o.v = L.vf; o.dg = L.dgf; o.dl1 = L.dl1f; o.pv = L.pvf; o.rv = L.rvf; o.inv = L.invf;
+  } else {
+    o.v = L.v; o.dg = L.dg; o.dl1 = L.dl1; o.pv = L.pv; o.rv = L.rv; o.inv = L.inv;
+  }
+  return o;
+}
+
+#define DISPATCH_LANES(lanes, KERNEL, ...)                       \
+  switch (lanes) {                                               \
+    case 4: KERNEL<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
+    case 8: KERNEL<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
+    case 16: KERNEL<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(__VA_ARGS__); break; \
+    default: KERNEL<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(__VA_ARGS__); break; \
+  }
+
+struct ChebCoef {
+  double3 inv_theta;
+  double3 c1[8], c2[8];  // step k (k = 1..degree-1)
+  double3 post_c2;       // 1/theta for the first post step
+};
+
+inline ChebCoef cheb_coef(const AmgLevel& L, int nc, const SmoothParams& sp) {
+  ChebCoef cc;
+  double it[3] = {0, 0, 0}, a1[8][3] = {{0}}, a2[8][3] = {{0}};
+  for (int c = 0; c < nc; ++c) {
+    double lmax = L.lam[c], lmin = lmax / sp.ratio;
+    double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    double sigma = theta / delta, rho = 1.0 / sigma;
+    it[c] = 1.0 / theta;
+    for (int k = 1; k < sp.degree && k < 8; ++k) {
+      double rn = 1.0 / (2.0 * sigma - rho);
+      a1[k][c] = rn * rho;
+      a2[k][c] = 2.0 * rn / delta;
+      rho = rn;
+    }
+  }
+  cc.inv_theta = make_double3(it[0], it[1], it[2]);
+  cc.post_c2 = cc.inv_theta;
+  for (int k = 0; k < 8; ++k) {
+    cc.c1[k] = make_double3(a1[k][0], a1[k][1], a1[k][2]);
+    cc.c2[k] = make_double3(a2[k][0], a2[k][1], a2[k][2]);
+  }
+  return cc;
+}
+
+// Smoothing from x = 0; returns the buffer (x or t) that holds the result.
+template <class T, int NC>
+T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, const T* b, T* x, T* t, T* d,
+               cudaStream_t st) {
+  int64_t n = L.n;
+  T* cur = x;
+  T* other = t;
+  if (sp.kind == PS_SMOOTH_CHEBYSHEV) {
+    ChebCoef cc = cheb_coef(L, NC, sp);
+    int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
+    if (deg == 1) {
+      k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, cc.inv_theta);
+      return x;
+    }
+    DISPATCH_LANES(L.lanes, k_cheb_pre, n, L.rp, L.ci, V.v, V.dg, b, x, deg > 2 ? d : nullptr, cc.inv_theta,
+                   cc.c1[1], cc.c2[1]);
+    for (int k = 2; k < deg; ++k) {
+      DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, other, d, cc.c1[k], cc.c2[k], 0);
+      std::swap(cur, other);
+    }
+  } else {
+    k_l1_first<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dl1, b, x);
+    for (int k = 1; k < sp.pre; ++k) {
+      DISPATCH_LANES(L.lanes, k_l1_step, n, L.rp, L.ci, V.v, V.dl1, b, cur, other);
+      std::swap(cur, other);
+    }
+  }
+  return cur;
+}
+
+// Smoothing from the iterate in cur (other is free scratch); result written to out.
+template <class T, int NC>
+void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, const T* b, T* cur, T* other,
+                 T* d, T* out, cudaStream_t st) {
+  int64_t n = L.n;
+  if (sp.kind == PS_SMOOTH_CHEBYSHEV) {
+    ChebCoef cc = cheb_coef(L, NC, sp);
+    int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
+    for (int k = 0; k < deg; ++k) {
+      T* dst = k == deg - 1 ? out : other;
+      if (k == 0)
+        DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, dst, deg > 1 ? d : nullptr,
+                       cc.c1[0], cc.post_c2, 1)
+      else
+        DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, dst, d, cc.c1[k], cc.c2[k], 0)
+      other = cur;
+      cur = dst;
+    }
+  } else {
+    int sweeps = sp.post < 1 ? 1 : sp.post;
+    for (int k = 0; k < sweeps; ++k) {
+      T* dst = k == sweeps - 1 ? out : other;
+      DISPATCH_LANES(L.lanes, k_l1_step, n, L.rp, L.ci, V.v, V.dl1, b, cur, dst);
+      other = cur;
+      cur = dst;
+    }
+  }
+}
+
+template <class T, int NC>
+void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const T* v, const T* x, T* y, int add,
+                cudaStream_t st) {
+  switch (lanes) {
+    case 4: k_spmv<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 8: k_spmv<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 16: k_spmv<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    default: k_spmv<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+  }
+}
+
+template <class T, int NC>
+void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cudaStream_t st) {
+  AmgLevel& L = H.L[l];
+  LevelT<T> V = view<T>(L);
+  int64_t n = L.n;
+  if (L.coarsest) {
+    k_dense_solve<T, NC><<<grid_for(n * NC * 32, 256), 256, 0, st>>>(n, V.inv, b, out);
+    return;
+  }
+  T* x = static_cast<T*>(L.x);
+  T* t = static_cast<T*>(L.t);
+  T* d = static_cast<T*>(L.d);
+  T* r = static_cast<T*>(L.r);
+  AmgLevel& C = H.L[l + 1];
+  T* bc = static_cast<T*>(C.b);
+  T* ec = static_cast<T*>(C.e);
+  T* xs = smooth_zero<T, NC>(L, V, sp, b, x, t, d, st);
+  DISPATCH_LANES(L.lanes, k_resid, n, L.rp, L.ci, V.v, b, xs, r);
+  spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, V.rv, r, bc, 0, st);
+  vcycle_level<T, NC>(H, l + 1, sp, bc, ec, st);
+  spmv_lanes<T, NC>(L.plane, n, L.prp, L.pci, V.pv, ec, xs, 1, st);
+  smooth_post<T, NC>(L, V, sp, b, xs, xs == x ? t : x, d, out, st);
+}
+
+}  // namespace
+
+template <class T>
+ps_status amg_alloc_work(Arena& ar, Amg& H) {
+  for (auto& L : H.L) {
+    size_t m = size_t(L.n) * H.nc + 1;
+    T *x, *t, *r, *d, *b, *e;
+    PS_TRY(ar.alloc(&x, m)); PS_TRY(ar.alloc(&t, m)); PS_TRY(ar.alloc(&r, m)); PS_TRY(ar.alloc(&d, m));
+    PS_TRY(ar.alloc(&b, m)); PS_TRY(ar.alloc(&e, m));
+    L.x = x; L.t = t; L.r = r; L.d = d; L.b = b; L.e = e;
+  }
+  return PS_OK;
+}
+
+template <class T>
+ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st) {
+  if (H.nc == 3) vcycle_level<T, 3>(H, 0, sp, b, x, st);
+  else vcycle_level<T, 1>(H, 0, sp, b, x, st);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+template ps_status amg_alloc_work<float>(Arena&, Amg&);
+template ps_status amg_alloc_work<double>(Arena&, Amg&);
+template ps_status amg_vcycle<float>(Amg&, const SmoothParams&, const float*, float*, cudaStream_t);
+template ps_status amg_vcycle<double>(Amg&, const SmoothParams&, const double*, double*, cudaStream_t);
+
+}  // namespace ps_internal

@@ -1,0 +1,169 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1812_05540_gb300 as ps
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    ps.lib()
+
+
+def _gpu():
+    from tests import _gpu as g
+    return g
+
+
+def _rows_close(a, b, bs, rp, rtol):
+    """|a - b| <= rtol * (max |a| over the block row), per block row."""
+    a = a.reshape(-1, bs)
+    b = b.reshape(-1, bs)
+    nrow = len(rp) - 1
+    rows = np.repeat(np.arange(nrow), np.diff(rp))
+    scale = np.zeros(nrow)
+    np.maximum.at(scale, rows, np.abs(a).max(axis=1))
+    err = np.abs(a - b).max(axis=1)
+    worst = np.max(err / np.maximum(scale[rows], 1e-300))
+    return worst <= rtol, worst
+
+
+GEN_CASES = [(0, {}), (1, dict(nx=24, ny=20, nz=10)), (2, dict(nx=30, ny=44, nz=17)),
+             (0, dict(nx=5, ny=3, nz=2, flags=oracle.OR_ALL & ~oracle.OR_SCALE)),
+             (3, dict(field_kind=oracle.FIELDS_HOMOGENEOUS, nx=4, ny=4, nz=3, dp_amp=0.0))]
+
+
+@pytest.mark.parametrize("cfg,kw", GEN_CASES)
+def test_generator_parity(cfg, kw):
+    # a0: same counter-based fields and App. B formulas on both sides; patterns bit-exact,
+    # values within 1e-13 of the row scale (transcendental functions differ by ulps)
+    g = _gpu()
+    ogp = oracle.default_params(cfg, **kw)
+    osys = oracle.System(ogp)
+    sp = ps.ps_generate(g.gen_params_like(ogp))
+    try:
+        d = g.system_to_numpy(sp)
+    finally:
+        ps.ps_system_free(sp)
+    assert d["n"] == osys.n
+    for name, bs in (("uu", 9), ("uf", 6), ("fu", 6), ("ff", 4)):
+        orp, oci, ov = osys.blocks[name]
+        rp, ci, v = d[name]
+        assert np.array_equal(rp, orp) and np.array_equal(ci, oci), name
+        ok, worst = _rows_close(ov, v, bs, orp, 1e-13)
+        assert ok, (name, worst)
+    assert np.array_equal(d["dirichlet"], osys.dirichlet)
+    assert np.array_equal(d["rhs"], osys.rhs)
+    assert np.allclose(d["d_fs"], osys.d_fs, rtol=1e-13, atol=0)
+    for k in ("E", "nu", "kh", "kv", "phi0", "sw", "p"):
+        assert np.allclose(d[k], osys.fields[k], rtol=1e-13, atol=0), k
+    assert d["alpha_u"] == pytest.approx(osys.alpha_u, rel=1e-14)
+    assert d["alpha_f"] == pytest.approx(osys.alpha_f, rel=1e-14)
+
+
+@pytest.fixture(scope="module")
+def sys1():
+    return oracle.System(oracle.default_params(1, nx=24, ny=20, nz=10))
+
+
+def test_spmv_parity(sys1):
+    # a12: FP64 Jacobian SpMV against the oracle on the same bytes
+    g = _gpu()
+    dev = g.to_device(sys1)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default())
+    try:
+        xs = np.random.default_rng(0).standard_normal(sys1.n)
+        x = torch.from_numpy(xs).cuda()
+        y = torch.empty_like(x)
+        ps.ps_spmv(h, x.data_ptr(), y.data_ptr())
+        ref = sys1.spmv(xs)
+        assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    finally:
+        ps.ps_free(h)
+
+
+@pytest.mark.parametrize("cfg,kw,cm", [(0, {}, 16), (1, dict(nx=24, ny=20, nz=10), 60)])
+def test_hierarchy_parity(cfg, kw, cm):
+    # a1-a5: S_pp bit-exact, aggregates bit-exact at every level (integer work),
+    # Galerkin operators bit-exact (fixed summation order, no contraction), ILU within 1e-13
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm))
+    try:
+        for which in (0, 1):
+            nl = P.nlevels(which)
+            assert ps.ps_amg_nlevels(h, which) == nl
+            for l in range(nl):
+                orp, oci, ov = P.level(which, l)
+                rp, ci, v, agg = ps.ps_amg_level_copy(h, which, l)
+                assert np.array_equal(rp, orp) and np.array_equal(ci, oci), (which, l)
+                assert np.array_equal(v, ov), (which, l, np.abs(v - ov).max())
+                if l < nl - 1:
+                    oagg, ona = P.aggregates(which, l)
+                    assert np.array_equal(agg, oagg), (which, l)
+        rp, ci, spp_o = P.spp()
+        spp, dinv = ps.ps_flow_copy(h, len(ci), osys.n_cells)
+        assert np.array_equal(spp, spp_o)
+        do = P.ilu_dinv()
+        assert np.allclose(dinv, do, rtol=1e-13, atol=1e-13 * np.abs(do).max())
+    finally:
+        ps.ps_free(h)
+
+
+@pytest.mark.parametrize("cm", [16, 500])
+def test_apply_parity_fp64(cm):
+    # Algorithm 1 in FP64 against the oracle's Algorithm 1 on the same vector
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(0))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm))
+    try:
+        for seed in range(3):
+            vs = np.random.default_rng(seed).standard_normal(osys.n)
+            v = torch.from_numpy(vs).cuda()
+            z = torch.empty_like(v)
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            zo = P.apply(vs)
+            assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+    finally:
+        ps.ps_free(h)
+
+
+SOLVE_CASES = [(0, {}, 16), (0, {}, 500), (1, dict(nx=24, ny=20, nz=10), 60), (2, dict(nx=20, ny=44, nz=17), 100),
+               (0, dict(nx=7, ny=3, nz=2), 500)]
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+@pytest.mark.parametrize("cfg,kw,cm", SOLVE_CASES)
+def test_solve_parity(cfg, kw, cm, prec):
+    # true FP64 relres <= 1e-8 (recomputed by the oracle), solution within 1e-6 of the oracle
+    # solved to 1e-12, iterations within 10% (+1) of the oracle's FGMRES at 1e-8
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    xo, sto = P.fgmres(tol=1e-12)
+    _, sto8 = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=cm, coarse_max_p=cm))
+    try:
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    relres = np.linalg.norm(osys.rhs - osys.spmv(xs)) / np.linalg.norm(osys.rhs)
+    assert relres <= 1e-8 and st.true_relres <= 1e-8
+    assert abs(st.true_relres - relres) <= 1e-10
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - sto8.iters) <= max(1, int(0.1 * sto8.iters) + 1), (st.iters, sto8.iters)
