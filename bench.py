@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Time-to-1e-8 per coupled solve of one linearised multiphase-poromechanics
+Jacobian under the two-stage (fixed-stress + CPR) preconditioner.
+
+Workload: the 60x220x85-cell channelised box (5,722,098 DoF; synthetic
+stand-in for the SPE10 Model 2 reservoir grid), generated on the device.
+A step = one setup phase (S_ff^(FS), quasi-IMPES S_pp, mechanics and pressure
+AMG, ILU(0)) + one FGMRES solve to a true FP64 relative residual of 1e-8.
+The headline is the mixed-precision path (FP32 preconditioner, FP64 Krylov);
+the FP64 path is timed beside it.  N GPUs run N independent replicas.
+
+--impl reference times the CPU oracle (plain FP64 restatement) on the host
+cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 per coupled solve (setup + FGMRES), 60x220x85 poromechanics Jacobian"
+WORKLOAD = "60x220x85 channelised/lognormal poromechanics Jacobian, 5,722,098 DoF (SPE10-Model-2-sized, synthetic)"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(config):
+    """Full oracle setup + FGMRES on a slab of the workload (same statistics,
+    nz cut to 1/10), scaled to the full size by the DoF ratio."""
+    import oracle
+    full = oracle.default_params(config)
+    nz = max(2, full.nz // 10)
+    gp = oracle.default_params(config, nz=nz)
+    s = oracle.System(gp)
+    t0 = time.perf_counter()
+    P = oracle.Prec(s)
+    t1 = time.perf_counter()
+    x, st = P.fgmres(tol=TOL)
+    t2 = time.perf_counter()
+    n_full = 3 * (full.nx + 1) * (full.ny + 1) * (full.nz + 1) + 2 * full.nx * full.ny * full.nz
+    scale = n_full / s.n
+    return {"seconds_sample": t2 - t0, "setup_s": t1 - t0, "solve_s": t2 - t1, "iters": st.iters,
+            "relres": st.true_relres, "dof_sample": s.n, "scale": scale, "value": (t2 - t0) * scale,
+            "sample": "oracle setup+FGMRES(1e-8) on the %dx%dx%d slab of the workload (%d DoF, same field "
+                      "statistics), x %.3f DoF ratio to the full %dx%dx%d grid" % (gp.nx, gp.ny, nz, s.n, scale,
+                                                                                    full.nx, full.ny, full.nz)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps would only repeat the sample
+    vals = []
+    info = None
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        info = oracle_sample(args.config)
+        vals.append(info["value"])
+    wall = time.perf_counter() - t0
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(1, args.steps), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": TOL},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": info["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_iters": info["iters"]}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+class _DevArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def dev_to_numpy(ptr, n, dtype):
+    """Host copy of n elements of a device array owned by the library."""
+    import numpy as np
+    import torch
+    ts = {np.float64: "<f8", np.int64: "<i8", np.int32: "<i4"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, n, ts), device="cuda").cpu().numpy().copy()
+
+
+def algorithmic_spmv_bytes(s):
+    j = s.jac
+    b = 0
+    for blk, bs in ((j.A_uu, 9), (j.A_uf, 6), (j.A_fu, 6), (j.A_ff, 4)):
+        b += blk.nnzb * (bs * 8 + 4) + (blk.n_brow + 1) * 4
+    return b + 2 * s.n * 8
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1812_05540_gb300 import _build
+    _build.build()
+    import paper_1812_05540_gb300 as ps
+
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        gp = ps.ps_gen_default(args.config)
+        tg = time.perf_counter()
+        sysp = ps.ps_generate(gp, sptr)
+        gen_s = time.perf_counter() - tg
+        s = sysp.contents
+        n = s.n
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+        def step(prec):
+            p = ps.ps_params_default(precision=prec, stream=sptr)
+            h = ps.ps_setup(s.jac, s.grid, p)
+            try:
+                status, st = ps.ps_solve(h, s.rhs, x.data_ptr(), TOL, raise_on_error=False)
+            finally:
+                ps.ps_free(h)
+            if status != ps.PS_OK:
+                raise RuntimeError("solve failed: %s" % ps.ps_strerror(status))
+            return st
+
+        def barrier():
+            if world > 1:
+                torch.distributed.barrier()
+
+        def timed(prec, steps, clocks=None):
+            stats = []
+            barrier()
+            torch.cuda.synchronize()
+            l0 = ps.ps_launch_count()
+            if clocks:
+                clocks.start()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                stats.append(step(prec))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ck = clocks.stop() if clocks else None
+            launches = ps.ps_launch_count() - l0
+            barrier()
+            t = e0.elapsed_time(e1) / 1000.0
+            if world > 1:
+                tt = torch.tensor([t], device="cuda")
+                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+                t = float(tt.item())
+            return t, stats, launches, ck
+
+        for _ in range(args.warmup):
+            step(ps.PS_MIXED_FP32)
+        step(ps.PS_FP64)
+        clocks = Clocks(local)
+        t_mx, st_mx, launches, ck = timed(ps.PS_MIXED_FP32, args.steps, clocks)
+        t_64, st_64, _, _ = timed(ps.PS_FP64, args.steps)
+        per_mx = t_mx / args.steps
+        per_64 = t_64 / args.steps
+
+        # relres of the last mixed solve, recomputed with the library SpMV
+        step(ps.PS_MIXED_FP32)
+        h = ps.ps_setup(s.jac, s.grid, ps.ps_params_default(stream=sptr))
+        y = torch.empty_like(x)
+        ps.ps_spmv(h, x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        rhs_np = dev_to_numpy(s.rhs, n, np.float64)
+        relres = float(np.linalg.norm(rhs_np - y.cpu().numpy()) / np.linalg.norm(rhs_np))
+
+        # dominant-kernel roofline: the FP64 Jacobian SpMV, timed alone on its stream
+        nb = algorithmic_spmv_bytes(s)
+        xs = torch.randn(n, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ps.ps_spmv(h, xs.data_ptr(), y.data_ptr())
+        times = []
+        for _ in range(20):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ps.ps_spmv(h, xs.data_ptr(), y.data_ptr())
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1000.0)
+        ps.ps_free(h)
+        t_spmv = sorted(times)[len(times) // 2]
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = nb / t_spmv / 1e9
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+        if os.path.exists(tfile):
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        e2e = None
+        if not args.no_e2e:
+            host = {}
+            ptrs = {}
+            def hcopy(ptr, count, dtype, tdtype):
+                t = torch.empty(count, dtype=tdtype, pin_memory=True)
+                src = dev_to_numpy(ptr, count, dtype)
+                t.copy_(torch.from_numpy(src))
+                return t
+            j = s.jac
+            blocks = []
+            h2d = 0
+            for blk, bs in ((j.A_uu, 9), (j.A_uf, 6), (j.A_fu, 6), (j.A_ff, 4)):
+                rp = hcopy(blk.rowptr, blk.n_brow + 1, np.int64, torch.int64)
+                ci = hcopy(blk.colind, blk.nnzb, np.int32, torch.int32)
+                v = hcopy(blk.val, blk.nnzb * bs, np.float64, torch.float64)
+                host[len(host)] = (rp, ci, v)
+                blocks.append(ps.ps_bsr(blk.n_brow, blk.n_bcol, blk.nnzb, blk.br, blk.bc, rp.data_ptr(),
+                                        ci.data_ptr(), v.data_ptr()))
+                h2d += rp.numel() * 8 + ci.numel() * 4 + v.numel() * 8
+            dfs = hcopy(j.d_fs, 2 * s.n_cells, np.float64, torch.float64)
+            rhs_h = hcopy(s.rhs, n, np.float64, torch.float64)
+            x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            h2d += dfs.numel() * 8 + rhs_h.numel() * 8
+            hjac = ps.ps_jacobian(blocks[0], blocks[1], blocks[2], blocks[3], dfs.data_ptr(), None)
+
+            def step_host():
+                p = ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr, host_ptrs=1)
+                hh = ps.ps_setup(hjac, s.grid, p)
+                try:
+                    status, st = ps.ps_solve(hh, rhs_h.data_ptr(), x_h.data_ptr(), TOL, raise_on_error=False)
+                finally:
+                    ps.ps_free(hh)
+                if status != ps.PS_OK:
+                    raise RuntimeError("e2e solve failed: %s" % ps.ps_strerror(status))
+
+            step_host()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step_host()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            te = e0.elapsed_time(e1) / 1000.0
+            if world > 1:
+                tt = torch.tensor([te], device="cuda")
+                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+                te = float(tt.item())
+            e2e = {"value": te / args.steps / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(n * 8)}
+        ps.ps_system_free(sysp)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        info = oracle_sample(args.config)
+        cpu = {"value": info["value"], "unit": "s", "cores": 1, "kind": "oracle", "sample": info["sample"],
+               "oracle_iters": info["iters"]}
+    if rank != 0:
+        return
+    it_mx = [st.iters for st in st_mx]
+    it_64 = [st.iters for st in st_64]
+    line = {
+        "metric": METRIC, "value": per_mx / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * per_mx, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [60, 220, 85], "dof": n, "tol": TOL,
+                   "precision": "mixed: FP32 preconditioner (AMG, ILU), FP64 Jacobian SpMV + FGMRES(100)",
+                   "l2": "inputs larger than L2 (3.7 GB FP64 Jacobian per SpMV)", "replicas": world},
+        "iters_mixed": it_mx, "iters_fp64": it_64,
+        "setup_ms_mixed": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_mx],
+        "solve_ms_mixed": [round(st.ms_solve, 2) for st in st_mx],
+        "fp64": {"value": per_64 / world, "ms_per_step": 1000.0 * per_64,
+                 "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_64],
+                 "solve_ms": [round(st.ms_solve, 2) for st in st_64]},
+        "mixed_speedup_vs_fp64": per_64 / per_mx,
+        "true_relres_mixed": relres, "gen_s": gen_s,
+        "roofline": {"kernel": "FP64 Jacobian SpMV (k_spmv_u + k_spmv_f)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes": nb, "launch_ms": 1000.0 * t_spmv,
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"},
+        "cpu_baseline": cpu,
+        "clocks": ck,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

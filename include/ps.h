@@ -190,6 +190,10 @@ void ps_system_free(ps_system* s);
 
 const char* ps_strerror(ps_status s);
 
+/* Number of CUDA kernels this library has launched in the process so far
+   (monotone counter; differences bracket a region of interest). */
+int64_t ps_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

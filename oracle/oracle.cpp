@@ -793,6 +793,7 @@ struct Level {
   vec dg;   // n*nc, diagonal
   vec lam;  // nc, Gershgorin bound of rho(D^{-1}A)
   std::vector<uint8_t> root;  // distance-2 MIS roots
+  std::vector<uint8_t> excl;  // rows whose off-diagonal entries are all zero
   std::vector<DenseLU> lu;  // coarsest only, per component
 };
 struct AMG {
@@ -840,9 +841,17 @@ void aggregate(Level& lev, double theta, int level) {
       if (t >= theta * den && t > 0.0) { strong[q] = 1; wgt[q] = t / den; }
     }
   }
-  // synchronous distance-2 MIS rounds: 0 undecided, 1 root, 2 covered, 3 excluded
+  // Rows without any strong connection (identity rows included) stay out of the
+  // coarse space: the smoother alone treats them (the isolated-node rule of
+  // smoothed aggregation).  Their prolongator rows still follow (I - w D^{-1} A) P_tent.
+  lev.excl = excluded;
   std::vector<uint8_t> st(n, 0);
-  for (int64_t i = 0; i < n; ++i) if (excluded[i]) st[i] = 3;
+  for (int64_t i = 0; i < n; ++i) {
+    bool any = false;
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) any = any || strong[q];
+    if (excluded[i] || !any) st[i] = 3;
+  }
+  // synchronous distance-2 MIS rounds: 0 undecided, 1 root, 2 covered, 3 not aggregated
   std::vector<int64_t> m1(n), m2(n);
   std::vector<uint8_t> nr(n), c1(n);
   for (;;) {
@@ -930,7 +939,7 @@ CSR smoothed_prolongator(const Level& lev) {
   CSR P; P.n = n; P.m = lev.nagg; P.nc = nc; P.rp.assign(n + 1, 0);
   std::vector<int32_t> aggs;
   for (int64_t i = 0; i < n; ++i) {
-    if (lev.agg[i] >= 0) {
+    if (!lev.excl[i]) {
       aggs.clear();
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
         if (lev.agg[A.ci[q]] >= 0) aggs.push_back(lev.agg[A.ci[q]]);

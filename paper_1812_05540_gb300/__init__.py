@@ -108,6 +108,8 @@ def lib():
         L.ps_generate.argtypes = [C.POINTER(ps_gen_params), C.c_void_p, C.POINTER(C.POINTER(ps_system))]
         L.ps_system_free.argtypes = [C.POINTER(ps_system)]
         L.ps_system_free.restype = None
+        L.ps_launch_count.argtypes = []
+        L.ps_launch_count.restype = C.c_int64
         L.ps_strerror.argtypes = [C.c_int]
         L.ps_strerror.restype = C.c_char_p
         _lib = L
@@ -127,6 +129,10 @@ def _check(status, what):
 
 def ps_strerror(status):
     return lib().ps_strerror(status).decode()
+
+
+def ps_launch_count():
+    return lib().ps_launch_count()
 
 
 def ps_params_default(**kw):

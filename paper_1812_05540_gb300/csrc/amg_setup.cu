@@ -93,9 +93,15 @@ __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int3
 }
 
 // ---- distance-2 MIS rounds (state: 0 undecided, 1 root, 2 covered, 3 excluded) ----
-__global__ void k_mis_init(int64_t n, const uint8_t* __restrict__ excl, uint8_t* __restrict__ st) {
+// rows without a strong connection (identity rows included) are not aggregated:
+// the smoother alone treats them (isolated-node rule of smoothed aggregation)
+__global__ void k_mis_init(int64_t n, const int32_t* __restrict__ rp, const uint8_t* __restrict__ strong,
+                           const uint8_t* __restrict__ excl, uint8_t* __restrict__ st) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < n) st[i] = excl[i] ? 3 : 0;
+  if (i >= n) return;
+  bool any = false;
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) any = any || strong[q];
+  st[i] = (excl[i] || !any) ? 3 : 0;
 }
 __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st, int level,
@@ -227,11 +233,12 @@ __device__ __forceinline__ bool first_occurrence(const int32_t* __restrict__ ci,
   return true;
 }
 __global__ void k_p_count(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                          const int32_t* __restrict__ agg, int32_t* __restrict__ cnt) {
+                          const int32_t* __restrict__ agg, const uint8_t* __restrict__ excl,
+                          int32_t* __restrict__ cnt) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t c = 0;
-  if (agg[i] >= 0)
+  if (!excl[i])
     for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
       int32_t a = agg[ci[q]];
       if (a >= 0 && first_occurrence(ci, agg, rp[i], q, a)) ++c;
@@ -241,10 +248,10 @@ __global__ void k_p_count(int64_t n, const int32_t* __restrict__ rp, const int32
 template <int NC>
 __global__ void k_p_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ v, const int32_t* __restrict__ agg, double w0, double w1,
-                         double w2, const int32_t* __restrict__ prp, int32_t* __restrict__ pci,
-                         double* __restrict__ pv) {
+                         double w2, const uint8_t* __restrict__ excl, const int32_t* __restrict__ prp,
+                         int32_t* __restrict__ pci, double* __restrict__ pv) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n || agg[i] < 0) return;
+  if (i >= n || excl[i]) return;
   const double om[3] = {w0, w1, w2};
   int32_t q0 = rp[i], q1 = rp[i + 1];
   int32_t qd = q0;
@@ -341,9 +348,12 @@ __device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const 
   return cnt;
 }
 
+// rows whose distinct columns exceed the shared-memory capacity are listed in
+// longrows[] and handled by the dense-accumulator kernels below
 __global__ void k_spgemm_count(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
                                const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
-                               int32_t* __restrict__ cnt, int* __restrict__ err) {
+                               int32_t* __restrict__ cnt, uint8_t* __restrict__ islong,
+                               int32_t* __restrict__ longrows, int32_t* __restrict__ nlong) {
   extern __shared__ int32_t smem[];
   int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
@@ -353,8 +363,96 @@ __global__ void k_spgemm_count(int64_t n, const int32_t* __restrict__ xrp, const
   int c = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
   ovf = __any_sync(0xffffffffu, ovf);
   if (lane == 0) {
-    cnt[i] = c;
-    if (ovf || c > kUniq) atomicExch(err, 1);
+    bool lg = ovf || c > kUniq;
+    cnt[i] = lg ? 0 : c;
+    islong[i] = lg ? 1 : 0;
+    if (lg) longrows[atomicAdd(nlong, 1)] = int32_t(i);
+  }
+}
+
+// dense path, one CTA per long row: stamp[j] marks the columns seen for this row
+// (stamps are row id + 1, so the scratch never needs clearing)
+__global__ void k_spgemm_dense_count(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                                     const int32_t* __restrict__ xci, const int32_t* __restrict__ yrp,
+                                     const int32_t* __restrict__ yci, int32_t* __restrict__ stamp, int64_t m,
+                                     int32_t* __restrict__ cnt) {
+  int b = blockIdx.x;
+  if (b >= nrows) return;
+  int32_t i = rows[b];
+  int32_t* mk = stamp + int64_t(b) * m;
+  __shared__ int32_t c;
+  if (threadIdx.x == 0) c = 0;
+  __syncthreads();
+  int32_t tag = i + 1;
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    int32_t k = xci[q];
+    for (int32_t r = yrp[k] + threadIdx.x; r < yrp[k + 1]; r += blockDim.x)
+      if (atomicExch(&mk[yci[r]], tag) != tag) atomicAdd(&c, 1);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt[i] = c;
+}
+
+template <int NC>
+__global__ void k_spgemm_dense_fill(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                                    const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                                    const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                    const double* __restrict__ yv, int32_t* __restrict__ stamp,
+                                    double* __restrict__ acc_all, int64_t m, const int32_t* __restrict__ crp,
+                                    int32_t* __restrict__ cci, double* __restrict__ cv) {
+  int b = blockIdx.x;
+  if (b >= nrows) return;
+  int32_t i = rows[b];
+  int32_t* mk = stamp + int64_t(b) * m;
+  double* acc = acc_all + int64_t(b) * m * NC;
+  // the stamp of the count pass is i + 1; mark this pass with -(i + 1) and zero the accumulators
+  int32_t tag = -(i + 1);
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    int32_t k = xci[q];
+    for (int32_t r = yrp[k] + threadIdx.x; r < yrp[k + 1]; r += blockDim.x) {
+      int32_t j = yci[r];
+      if (atomicExch(&mk[j], tag) != tag)
+        for (int c = 0; c < NC; ++c) acc[int64_t(j) * NC + c] = 0.0;
+    }
+    __syncthreads();
+  }
+  // products in ascending order of the inner index k (distinct j within one Y row)
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    int32_t k = xci[q];
+    double x[NC];
+    for (int c = 0; c < NC; ++c) x[c] = xv[int64_t(q) * NC + c];
+    for (int32_t r = yrp[k] + threadIdx.x; r < yrp[k + 1]; r += blockDim.x) {
+      int32_t j = yci[r];
+      for (int c = 0; c < NC; ++c)
+        acc[int64_t(j) * NC + c] = acc[int64_t(j) * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+    }
+    __syncthreads();
+  }
+  // emit in ascending column order: rank of each marked column by a block scan over j
+  __shared__ int32_t base;
+  if (threadIdx.x == 0) base = crp[i];
+  __syncthreads();
+  for (int64_t j0 = 0; j0 < m; j0 += blockDim.x) {
+    int64_t j = j0 + threadIdx.x;
+    int f = (j < m && mk[j] == tag) ? 1 : 0;
+    // block-wide exclusive scan of f (blockDim.x <= 1024)
+    __shared__ int32_t sc[1024];
+    sc[threadIdx.x] = f;
+    __syncthreads();
+    for (int off = 1; off < blockDim.x; off <<= 1) {
+      int32_t t = threadIdx.x >= off ? sc[threadIdx.x - off] : 0;
+      __syncthreads();
+      sc[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (f) {
+      int32_t pos = base + sc[threadIdx.x] - 1;
+      cci[pos] = int32_t(j);
+      for (int c = 0; c < NC; ++c) cv[int64_t(pos) * NC + c] = acc[j * NC + c];
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) base += sc[threadIdx.x];
+    __syncthreads();
   }
 }
 
@@ -363,7 +461,7 @@ __global__ void k_spgemm_fill(int64_t n, const int32_t* __restrict__ xrp, const 
                               const double* __restrict__ xv, const int32_t* __restrict__ yrp,
                               const int32_t* __restrict__ yci, const double* __restrict__ yv,
                               const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cv,
-                              int* __restrict__ err) {
+                              const uint8_t* __restrict__ islong, int* __restrict__ err) {
   extern __shared__ unsigned char sraw[];
   int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
@@ -374,6 +472,7 @@ __global__ void k_spgemm_fill(int64_t n, const int32_t* __restrict__ xrp, const 
   int32_t* list = reinterpret_cast<int32_t*>(base + kHash * 4);
   double* acc = reinterpret_cast<double*>(base + kHash * 4 + kUniq * 4);
   int ovf = 0;
+  if (islong[i]) return;
   int u = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
   if (u > kUniq || __any_sync(0xffffffffu, ovf)) {
     if (lane == 0) atomicExch(err, 1);
@@ -508,22 +607,44 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
 }
 
 template <int NC>
-ps_status spgemm(Arena& ar, int64_t n, const int32_t* xrp, const int32_t* xci, const double* xv, const int32_t* yrp,
-                 const int32_t* yci, const double* yv, int32_t** crp, int32_t** cci, double** cv, int64_t* cnnz,
-                 int* d_err, cudaStream_t st) {
-  int32_t* cnt;
+ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int32_t* xci, const double* xv,
+                 const int32_t* yrp, const int32_t* yci, const double* yv, int32_t** crp, int32_t** cci, double** cv,
+                 int64_t* cnnz, int* d_err, cudaStream_t st) {
+  int32_t *cnt, *longrows, *nlong;
+  uint8_t* islong;
   PS_TRY(ar.alloc(&cnt, n + 1));
   PS_TRY(ar.alloc(crp, n + 1));
+  PS_TRY(ar.alloc(&islong, n + 1));
+  PS_TRY(ar.alloc(&longrows, n + 1));
+  PS_TRY(ar.alloc(&nlong, 1));
+  PS_CUDA(cudaMemsetAsync(nlong, 0, sizeof(int32_t), st));
   const int wpb_c = 4;
   size_t sm_c = size_t(wpb_c) * kHash * 4;
-  k_spgemm_count<<<grid_for(n, wpb_c), 32 * wpb_c, sm_c, st>>>(n, xrp, xci, yrp, yci, cnt, d_err);
+  PS_TICK(); k_spgemm_count<<<grid_for(n, wpb_c), 32 * wpb_c, sm_c, st>>>(n, xrp, xci, yrp, yci, cnt, islong, longrows,
+                                                                          nlong);
   PS_CUDA(cudaGetLastError());
+  int32_t hl = 0;
+  PS_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  // dense-accumulator batches for the long rows
+  int32_t* stamp = nullptr;
+  double* acc = nullptr;
+  int64_t B = 0;
+  if (hl > 0) {
+    int64_t per = m * (4 + 8 * NC);
+    B = (int64_t(256) << 20) / (per > 0 ? per : 1);
+    if (B < 1) B = 1;
+    if (B > hl) B = hl;
+    PS_TRY(ar.alloc(&stamp, size_t(B) * m + 1));
+    PS_TRY(ar.alloc(&acc, (size_t(B) * m + 1) * NC));
+    PS_CUDA(cudaMemsetAsync(stamp, 0, sizeof(int32_t) * (size_t(B) * m + 1), st));
+    for (int64_t b0 = 0; b0 < hl; b0 += B) {
+      int32_t nb = int32_t(hl - b0 < B ? hl - b0 : B);
+      PS_TICK(); k_spgemm_dense_count<<<nb, 256, 0, st>>>(longrows + b0, nb, xrp, xci, yrp, yci, stamp, m, cnt);
+    }
+  }
   int32_t tot = 0;
   PS_TRY(scan_i32(ar, cnt, *crp, n, &tot, st));
-  int herr = 0;
-  PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PS_CUDA(cudaStreamSynchronize(st));
-  if (herr) return PS_ERR_INVALID;
   *cnnz = tot;
   PS_TRY(ar.alloc(cci, size_t(tot) + 1));
   PS_TRY(ar.alloc(cv, (size_t(tot) + 1) * NC));
@@ -531,9 +652,17 @@ ps_status spgemm(Arena& ar, int64_t n, const int32_t* xrp, const int32_t* xci, c
   size_t per = size_t(kHash) * 4 + size_t(kUniq) * 4 + size_t(kUniq) * NC * 8;
   size_t sm = per * wpb;
   PS_CUDA(cudaFuncSetAttribute(k_spgemm_fill<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  k_spgemm_fill<NC><<<grid_for(n, wpb), 32 * wpb, sm, st>>>(n, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, d_err);
+  PS_TICK(); k_spgemm_fill<NC><<<grid_for(n, wpb), 32 * wpb, sm, st>>>(n, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv,
+                                                                       islong, d_err);
   PS_CUDA(cudaGetLastError());
-  ar.release(cnt);
+  for (int64_t b0 = 0; b0 < hl; b0 += B) {
+    int32_t nb = int32_t(hl - b0 < B ? hl - b0 : B);
+    PS_TICK(); k_spgemm_dense_fill<NC><<<nb, 256, 0, st>>>(longrows + b0, nb, xrp, xci, xv, yrp, yci, yv, stamp, acc, m,
+                                                           *crp, *cci, *cv);
+  }
+  PS_CUDA(cudaGetLastError());
+  if (stamp) { ar.release(stamp); ar.release(acc); }
+  ar.release(cnt); ar.release(islong); ar.release(longrows); ar.release(nlong);
   return PS_OK;
 }
 
@@ -557,7 +686,7 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     PS_TRY(ar.alloc(&dgbar, n));
     PS_TRY(ar.alloc(&excl, n));
     PS_TRY(ar.alloc(&lev.dg, n * NC));
-    k_diag_excl<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, lev.dg);
+    PS_TICK(); k_diag_excl<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, lev.dg);
     PS_CUDA(cudaGetLastError());
     bool coarsest = n <= prm.coarse_max || l + 1 >= prm.max_levels;
     uint8_t *strong = nullptr, *stt = nullptr;
@@ -565,33 +694,36 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     if (!coarsest) {
       PS_TRY(ar.alloc(&strong, nnz));
       PS_TRY(ar.alloc(&wgt, nnz));
-      k_strength<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, theta, strong, wgt);
+      PS_TICK(); k_strength<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, theta, strong, wgt);
       PS_TRY(ar.alloc(&stt, n));
       int64_t* m1;
       uint8_t *nr, *c1;
       int32_t* und;
       PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, 1));
-      k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, excl, stt);
+      PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, strong, excl, stt);
       for (int round = 0;; ++round) {
         PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
-        k_mis_m1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
-        k_mis_m2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
-        k_mis_c1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
-        k_mis_c2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
+        PS_TICK(); k_mis_m1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
+        PS_TICK(); k_mis_m2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
+        PS_TICK(); k_mis_c1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
+        PS_TICK(); k_mis_c2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
         int32_t h_und = 0;
         PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
         if (h_und == 0) break;
-        if (round > 100000) return PS_ERR_INVALID;
+        if (round > 100000) {
+          set_reason("aggregation did not terminate on level %d", l);
+          return PS_ERR_INVALID;
+        }
       }
       int32_t *isr, *rscan, *ph1;
       PS_TRY(ar.alloc(&isr, n)); PS_TRY(ar.alloc(&rscan, n + 1)); PS_TRY(ar.alloc(&ph1, n));
       PS_TRY(ar.alloc(&lev.agg, n));
-      k_is_root<<<grid_for(n, 256), 256, 0, st>>>(n, stt, isr);
+      PS_TICK(); k_is_root<<<grid_for(n, 256), 256, 0, st>>>(n, stt, isr);
       int32_t na = 0;
       PS_TRY(scan_i32(ar, isr, rscan, n, &na, st));
-      k_agg_phase1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, rscan, ph1);
-      k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, wgt, stt, ph1, lev.agg);
+      PS_TICK(); k_agg_phase1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, rscan, ph1);
+      PS_TICK(); k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, wgt, stt, ph1, lev.agg);
       PS_CUDA(cudaGetLastError());
       lev.nagg = na;
       ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(isr); ar.release(rscan);
@@ -599,7 +731,10 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       if (na == 0 || double(n) / double(na) < 1.2) coarsest = true;
     }
     if (coarsest) {
-      if (n > 16384) return PS_ERR_INVALID;  // coarsening stalled on a large level
+      if (n > 16384) {  // coarsening stalled on a large level
+        set_reason("coarsening stalled: level %d has %lld rows (nc=%d)", l, (long long)n, NC);
+        return PS_ERR_INVALID;
+      }
       lev.coarsest = true;
       lev.nagg = 0;
       if (lev.agg) { ar.release(lev.agg); lev.agg = nullptr; }
@@ -609,34 +744,34 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_TRY(ar.alloc(&f, size_t(NC) * n));
       PS_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * NC * n * n, st));
       PS_CUDA(cudaMemsetAsync(lev.inv, 0, sizeof(double) * NC * n * n, st));
-      k_dense_unpack<<<grid_for(n, 128), 128, 0, st>>>(n, NC, lev.rp, lev.ci, lev.v, M, lev.inv);
+      PS_TICK(); k_dense_unpack<<<grid_for(n, 128), 128, 0, st>>>(n, NC, lev.rp, lev.ci, lev.v, M, lev.inv);
       for (int64_t k = 0; k < n; ++k) {
-        k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
+        PS_TICK(); k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
         dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), NC);
-        k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
+        PS_TICK(); k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
       }
       PS_CUDA(cudaGetLastError());
       ar.release(M); ar.release(f);
       if (prm.mixed) {
         PS_TRY(ar.alloc(&lev.invf, size_t(NC) * n * n));
-        k_to_f32<<<grid_for(NC * n * n, 256), 256, 0, st>>>(lev.inv, lev.invf, NC * n * n);
+        PS_TICK(); k_to_f32<<<grid_for(NC * n * n, 256), 256, 0, st>>>(lev.inv, lev.invf, NC * n * n);
       }
     }
     if (strong) ar.release(strong);
     if (wgt) ar.release(wgt);
     if (stt) ar.release(stt);
-    ar.release(dgbar); ar.release(excl);
+    if (coarsest) { ar.release(dgbar); ar.release(excl); }
     if (prm.mixed) {
       PS_TRY(ar.alloc(&lev.vf, nnz * NC));
       PS_TRY(ar.alloc(&lev.dgf, n * NC));
-      k_to_f32<<<grid_for(nnz * NC, 256), 256, 0, st>>>(lev.v, lev.vf, nnz * NC);
-      k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dg, lev.dgf, n * NC);
+      PS_TICK(); k_to_f32<<<grid_for(nnz * NC, 256), 256, 0, st>>>(lev.v, lev.vf, nnz * NC);
+      PS_TICK(); k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dg, lev.dgf, n * NC);
     }
     if (lev.coarsest) break;
     // Gershgorin bound, omega = (4/3) / lambda
     double* gr;
     PS_TRY(ar.alloc(&gr, n * NC));
-    k_gersh<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, gr);
+    PS_TICK(); k_gersh<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, gr);
     double* dmax;
     PS_TRY(ar.alloc(&dmax, NC));
     for (int c = 0; c < NC; ++c) PS_TRY(max_f64(ar, gr + c * n, n, dmax + c, st));
@@ -647,23 +782,23 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     for (int c = 0; c < NC; ++c) om[c] = (4.0 / 3.0) / lev.lam[c];
     // l1 row norms for the l1-Jacobi smoother
     PS_TRY(ar.alloc(&lev.dl1, n * NC));
-    k_l1<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.v, lev.dl1);
+    PS_TICK(); k_l1<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.v, lev.dl1);
     if (prm.mixed) {
       PS_TRY(ar.alloc(&lev.dl1f, n * NC));
-      k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
+      PS_TICK(); k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
     }
     // prolongator
     int32_t* pc;
     PS_TRY(ar.alloc(&pc, n + 1));
     PS_TRY(ar.alloc(&lev.prp, n + 1));
-    k_p_count<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.agg, pc);
+    PS_TICK(); k_p_count<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.agg, excl, pc);
     int32_t pnnz = 0;
     PS_TRY(scan_i32(ar, pc, lev.prp, n, &pnnz, st));
     lev.pnnz = pnnz;
     PS_TRY(ar.alloc(&lev.pci, size_t(pnnz) + 1));
     PS_TRY(ar.alloc(&lev.pv, (size_t(pnnz) + 1) * NC));
-    k_p_fill<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, om[0], om[1], om[2], lev.prp,
-                                                    lev.pci, lev.pv);
+    PS_TICK(); k_p_fill<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, om[0], om[1], om[2], excl,
+                                                    lev.prp, lev.pci, lev.pv);
     PS_CUDA(cudaGetLastError());
     ar.release(pc);
     lev.plane = lanes_for(double(pnnz) / double(n));
@@ -679,31 +814,36 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     PS_TRY(ar.alloc(&lev.rci, size_t(pnnz) + 1));
     PS_TRY(ar.alloc(&lev.rv, (size_t(pnnz) + 1) * NC));
     PS_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (na + 1), st));
-    k_col_count<<<grid_for(pnnz, 256), 256, 0, st>>>(pnnz, lev.pci, ccount);
+    PS_TICK(); k_col_count<<<grid_for(pnnz, 256), 256, 0, st>>>(pnnz, lev.pci, ccount);
     PS_TRY(scan_i32(ar, ccount, lev.rrp, na, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, lev.rrp, sizeof(int32_t) * na, cudaMemcpyDeviceToDevice, st));
-    k_transpose_fill<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.prp, lev.pci, lev.pv, cursor, tci, tv);
-    k_rank_rows<NC><<<grid_for(na * 32, 256), 256, 0, st>>>(na, lev.rrp, tci, tv, lev.rci, lev.rv);
+    PS_TICK(); k_transpose_fill<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.prp, lev.pci, lev.pv, cursor, tci, tv);
+    PS_TICK(); k_rank_rows<NC><<<grid_for(na * 32, 256), 256, 0, st>>>(na, lev.rrp, tci, tv, lev.rci, lev.rv);
     PS_CUDA(cudaGetLastError());
     ar.release(ccount); ar.release(cursor); ar.release(tci); ar.release(tv);
     lev.rlane = lanes_for(double(pnnz) / double(na));
     if (prm.mixed) {
       PS_TRY(ar.alloc(&lev.pvf, size_t(pnnz) * NC + 1));
       PS_TRY(ar.alloc(&lev.rvf, size_t(pnnz) * NC + 1));
-      k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.pv, lev.pvf, pnnz * NC);
-      k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.rv, lev.rvf, pnnz * NC);
+      PS_TICK(); k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.pv, lev.pvf, pnnz * NC);
+      PS_TICK(); k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.rv, lev.rvf, pnnz * NC);
     }
     // Galerkin product A_c = R (A P)
     int32_t *aprp, *apci, *crp, *cci;
     double *apv, *cv;
     int64_t apnnz = 0, cnnz = 0;
-    PS_TRY(spgemm<NC>(ar, n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci, lev.pv, &aprp, &apci, &apv, &apnnz, d_err, st));
-    PS_TRY(spgemm<NC>(ar, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz, d_err, st));
+    PS_TRY(spgemm<NC>(ar, n, na, lev.rp, lev.ci, lev.v, lev.prp, lev.pci, lev.pv, &aprp, &apci, &apv, &apnnz, d_err, st));
+    PS_TRY(spgemm<NC>(ar, na, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz, d_err, st));
     int herr = 0;
     PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
-    if (herr) return PS_ERR_INVALID;
+    if (herr) {
+      set_reason("SpGEMM capacity exceeded on level %d", l);
+      return PS_ERR_INVALID;
+    }
     ar.release(aprp); ar.release(apci); ar.release(apv);
+    ar.release(dgbar);
+    ar.release(excl);
     H.L.emplace_back();
     AmgLevel& nx = H.L.back();
     nx.n = na; nx.nnz = cnnz; nx.rp = crp; nx.ci = cci; nx.v = cv;

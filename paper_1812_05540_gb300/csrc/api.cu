@@ -75,10 +75,10 @@ ps_status alg1(ps_handle* h, const double* v, double* z) {
   else W = &h->w64;
   // step 1: z_u = M_uu^{-1} v_u
   if constexpr (sizeof(T) == 4) {
-    k_d2f<<<grid_for(h->nu, 256), 256, 0, st>>>(v, h->vu32, h->nu);
+    PS_TICK(); k_d2f<<<grid_for(h->nu, 256), 256, 0, st>>>(v, h->vu32, h->nu);
     PS_TRY(amg_vcycle<float>(h->amg_u, sp, h->vu32, h->zu32, st));
-    k_f2d<<<grid_for(h->nu, 256), 256, 0, st>>>(h->zu32, z, h->nu);
-    k_d2f<<<grid_for(h->nf, 256), 256, 0, st>>>(v + h->nu, W->vf, h->nf);
+    PS_TICK(); k_f2d<<<grid_for(h->nu, 256), 256, 0, st>>>(h->zu32, z, h->nu);
+    PS_TICK(); k_d2f<<<grid_for(h->nf, 256), 256, 0, st>>>(v + h->nu, W->vf, h->nf);
     // steps 2-4
     alg1_steps_2_4<float>(h->F, *W, h->zu32, st);
   } else {
@@ -110,7 +110,10 @@ ps_status copy_bsr(ps_handle* h, const ps_bsr& B, int32_t** rp, int32_t** ci, co
   PS_TRY(copy_in(h->ar, B.rowptr, sizeof(int64_t) * (B.n_brow + 1), (void**)&rp64, host, h->st));
   PS_TRY(h->ar.alloc(rp, B.n_brow + 1));
   rowptr_to_i32(rp64, *rp, B.n_brow + 1, h->st);
-  PS_TRY(copy_in(h->ar, B.colind, sizeof(int32_t) * (B.nnzb + 1), (void**)ci, host, h->st));
+  PS_TRY(h->ar.alloc(ci, B.nnzb + 1));
+  if (B.nnzb > 0)
+    PS_CUDA(cudaMemcpyAsync(*ci, B.colind, sizeof(int32_t) * B.nnzb,
+                            host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
   void* vv;
   PS_TRY(copy_in(h->ar, B.val, sizeof(double) * B.nnzb * B.br * B.bc, &vv, host, h->st));
   *v = static_cast<const double*>(vv);
@@ -148,7 +151,7 @@ ps_status build_flow(ps_handle* h) {
     PS_CUDA(cudaStreamSynchronize(st));
     nfu = t2;
     PS_TRY(ar.alloc(&F.fu_vf, nfu * 6 + 1));
-    k_d2f<<<grid_for(nfu * 6, 256), 256, 0, st>>>(h->J.fu_v, F.fu_vf, nfu * 6);
+    PS_TICK(); k_d2f<<<grid_for(nfu * 6, 256), 256, 0, st>>>(h->J.fu_v, F.fu_vf, nfu * 6);
   }
   AmgParams ap;
   ap.theta = h->prm.theta_p; ap.coarse_max = h->prm.coarse_max_p; ap.max_levels = h->prm.max_levels;
@@ -183,12 +186,15 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(copy_bsr(h, jac->A_fu, &J.fu_rp, &J.fu_ci, &J.fu_v));
   PS_TRY(copy_bsr(h, jac->A_ff, &J.ff_rp, &J.ff_ci, &J.ff_v));
   PS_TRY(copy_in(ar, jac->d_fs, sizeof(double) * 2 * h->nc, (void**)&h->dfs, h->prm.host_ptrs != 0, st));
-  PS_TRY(flow_check_pattern(ar, h->grid, J.ff_rp, J.ff_ci, st));
+  if (flow_check_pattern(ar, h->grid, J.ff_rp, J.ff_ci, st) != PS_OK) {
+    set_reason("A_ff is not the 7-point TPFA pattern of the %dx%dx%d grid", h->grid.nx, h->grid.ny, h->grid.nz);
+    return PS_ERR_INVALID;
+  }
   // §5.2 mechanics: amg(A_uu^(SDC)) on the three diagonal components of each 3x3 block
   int64_t nnzb = jac->A_uu.nnzb;
   double* sdc;
   PS_TRY(ar.alloc(&sdc, nnzb * 3));
-  k_sdc<<<grid_for(nnzb, 256), 256, 0, st>>>(nnzb, J.uu_v, sdc);
+  PS_TICK(); k_sdc<<<grid_for(nnzb, 256), 256, 0, st>>>(nnzb, J.uu_v, sdc);
   AmgParams ap;
   ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
   ap.mixed = h->mixed;
@@ -434,7 +440,7 @@ ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t*
   if (rowptr) {
     int64_t* tmp;
     PS_TRY(h->ar.alloc(&tmp, L.n + 1));
-    k_i32_to_i64<<<grid_for(L.n + 1, 256), 256, 0, st>>>(L.rp, tmp, L.n + 1);
+    PS_TICK(); k_i32_to_i64<<<grid_for(L.n + 1, 256), 256, 0, st>>>(L.rp, tmp, L.n + 1);
     PS_CUDA(cudaMemcpyAsync(rowptr, tmp, sizeof(int64_t) * (L.n + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     h->ar.release(tmp);
@@ -470,7 +476,8 @@ void ps_free(ps_handle* h) {
 const char* ps_strerror(ps_status s) {
   switch (s) {
     case PS_OK: return "ok";
-    case PS_ERR_INVALID: return "invalid argument, shape or pattern";
+    case PS_ERR_INVALID:
+      return ps_internal::last_reason().empty() ? "invalid argument, shape or pattern" : ps_internal::last_reason().c_str();
     case PS_ERR_OOM: return "device out of memory";
     case PS_ERR_CUDA: return ps_internal::last_error().empty() ? "CUDA error" : ps_internal::last_error().c_str();
     case PS_ERR_NOT_CONVERGED: return "not converged within max_iters";

@@ -145,8 +145,8 @@ ps_status flow_alloc_work(Arena& ar, const FlowStage& F, FlowWork<T>& W) {
 template <class T>
 void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaStream_t st) {
   FlowView<T> V = fview<T>(F);
-  k_step23<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.fu_rp, F.fu_ci, V.fu, W.vf, zu, V.dss, W.y, W.zs);
-  k_step4<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.rp, F.ci, V.aps, W.y, W.zs, W.wp);
+  PS_TICK(); k_step23<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.fu_rp, F.fu_ci, V.fu, W.vf, zu, V.dss, W.y, W.zs);
+  PS_TICK(); k_step4<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.rp, F.ci, V.aps, W.y, W.zs, W.wp);
 }
 
 template <class T>
@@ -155,12 +155,12 @@ void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int 
   FlowView<T> V = fview<T>(F);
   for (int l = 0; l < F.nlev; ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
-    k_ilu_fwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
+    PS_TICK(); k_ilu_fwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
                                                    V.dinv, W.y, W.zs, W.zp, W.t);
   }
   for (int l = F.nlev - 1; l >= 0; --l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
-    k_ilu_bwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
+    PS_TICK(); k_ilu_bwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
                                                    V.dinv, W.t, W.zs, W.zp, W.dz, zout);
   }
 }

@@ -120,7 +120,7 @@ ps_status flow_check_pattern(Arena& ar, const ps_grid& g, const int32_t* ff_rp, 
   PS_TRY(ar.alloc(&bad, 1));
   PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
   int64_t nc = int64_t(g.nx) * g.ny * g.nz;
-  k_check7<<<grid_for(nc, 256), 256, 0, st>>>(g.nx, g.ny, g.nz, ff_rp, ff_ci, bad);
+  PS_TICK(); k_check7<<<grid_for(nc, 256), 256, 0, st>>>(g.nx, g.ny, g.nz, ff_rp, ff_ci, bad);
   int h = 0;
   PS_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   PS_CUDA(cudaStreamSynchronize(st));
@@ -153,28 +153,28 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(ar.alloc(&cursor, F.nlev + 1));
     PS_TRY(ar.alloc(&F.lev_cells, nc));
     PS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (F.nlev + 1), st));
-    k_level_count<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cnt);
+    PS_TICK(); k_level_count<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cnt);
     PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
-    k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
+    PS_TICK(); k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
     F.lev_off.resize(F.nlev + 1);
     PS_CUDA(cudaMemcpyAsync(F.lev_off.data(), off, sizeof(int32_t) * (F.nlev + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     ar.release(cnt); ar.release(off); ar.release(cursor);
   }
-  k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
+  PS_TICK(); k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
                                                F.diagpos);
   for (int l = 0; l < F.nlev; ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
-    k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
+    PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
                                                    F.dinv);
   }
   PS_CUDA(cudaGetLastError());
   if (mixed) {
-    k_f32<<<grid_for(nnzb * 4, 256), 256, 0, st>>>(F.sff, F.sff_f, nnzb * 4);
-    k_f32<<<grid_for(nnzb, 256), 256, 0, st>>>(F.aps, F.aps_f, nnzb);
-    k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
-    k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
+    PS_TICK(); k_f32<<<grid_for(nnzb * 4, 256), 256, 0, st>>>(F.sff, F.sff_f, nnzb * 4);
+    PS_TICK(); k_f32<<<grid_for(nnzb, 256), 256, 0, st>>>(F.aps, F.aps_f, nnzb);
+    PS_TICK(); k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
+    PS_TICK(); k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
     PS_CUDA(cudaGetLastError());
   }
   return PS_OK;

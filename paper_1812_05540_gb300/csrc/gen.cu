@@ -96,10 +96,10 @@ ps_status correlated(Arena& ar, uint64_t seed, int field, int nx, int ny, int nz
     PS_CUDA(cudaMemcpyAsync(dw[a], hw[a].data(), hw[a].size() * sizeof(double), cudaMemcpyHostToDevice, st));
   }
   int64_t n0 = int64_t(px) * py * pz;
-  k_white<<<grid_for(n0, 256), 256, 0, st>>>(W, px, py, pz, R[0], R[1], R[2], seed, field);
-  k_conv<<<grid_for(int64_t(nx) * py * pz, 256), 256, 0, st>>>(W, X, dw[0], R[0], nx, py, pz, 0, 1.0);
-  k_conv<<<grid_for(int64_t(nx) * ny * pz, 256), 256, 0, st>>>(X, Y, dw[1], R[1], nx, ny, pz, 1, 1.0);
-  k_conv<<<grid_for(int64_t(nx) * ny * nz, 256), 256, 0, st>>>(Y, out, dw[2], R[2], nx, ny, nz, 2, norm);
+  PS_TICK(); k_white<<<grid_for(n0, 256), 256, 0, st>>>(W, px, py, pz, R[0], R[1], R[2], seed, field);
+  PS_TICK(); k_conv<<<grid_for(int64_t(nx) * py * pz, 256), 256, 0, st>>>(W, X, dw[0], R[0], nx, py, pz, 0, 1.0);
+  PS_TICK(); k_conv<<<grid_for(int64_t(nx) * ny * pz, 256), 256, 0, st>>>(X, Y, dw[1], R[1], nx, ny, pz, 1, 1.0);
+  PS_TICK(); k_conv<<<grid_for(int64_t(nx) * ny * nz, 256), 256, 0, st>>>(Y, out, dw[2], R[2], nx, ny, nz, 2, norm);
   PS_CUDA(cudaGetLastError());
   PS_CUDA(cudaStreamSynchronize(st));  // host weight buffers go out of scope
   ar.release(W); ar.release(X); ar.release(Y);
@@ -684,7 +684,7 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
       C.logk = std::log(1e3) + std::log(10.0) * u01(gp->seed, FCHAN, 0, lat3(c, 7, 0));
     }
   }
-  k_fields<<<grid_for(nc, 256), 256, 0, st>>>(fa, ghat, ksm, swsm, E, nu, kh, kv, phi, sw, p);
+  PS_TICK(); k_fields<<<grid_for(nc, 256), 256, 0, st>>>(fa, ghat, ksm, swsm, E, nu, kh, kv, phi, sw, p);
   PS_CUDA(cudaGetLastError());
   o.E = E; o.nu = nu; o.kh = kh; o.kv = kv; o.phi0 = phi; o.sw = sw; o.p = p;
   // material table
@@ -694,7 +694,7 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   P.s_nwr = gp->s_nwr; P.grav = gp->grav; P.p_ref = gp->p_ref; P.corey = gp->corey; P.h = gp->h; P.flags = gp->flags;
   CellMat* M;
   PS_TRY(ar.alloc(&M, nc));
-  k_material<<<grid_for(nc, 256), 256, 0, st>>>(P, nc, E, nu, phi, sw, p, M);
+  PS_TICK(); k_material<<<grid_for(nc, 256), 256, 0, st>>>(P, nc, E, nu, phi, sw, p, M);
   Ref hR;
   build_ref(gp->h, &hR);
   Ref* dR;
@@ -712,12 +712,12 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
     int32_t* ci;
     double* v;
     PS_TRY(ar.alloc(&rp, rows[kind] + 1));
-    k_pattern_count<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], cnt);
+    PS_TICK(); k_pattern_count<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], cnt);
     int64_t nnzb = 0;
     PS_TRY(scan_i64(ar, cnt, rp, rows[kind], &nnzb, st));
     PS_TRY(ar.alloc(&ci, nnzb));
     PS_TRY(ar.alloc(&v, nnzb * br[kind] * bc[kind]));
-    k_pattern_fill<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], rp, ci);
+    PS_TICK(); k_pattern_fill<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], rp, ci);
     B.n_brow = rows[kind]; B.n_bcol = cols[kind]; B.nnzb = nnzb; B.br = br[kind]; B.bc = bc[kind];
     B.rowptr = rp; B.colind = ci; B.val = v;
   }
@@ -728,20 +728,20 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   double* vff = const_cast<double*>(o.jac.A_ff.val);
   double* dfs;
   PS_TRY(ar.alloc(&dfs, 2 * nc));
-  k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, vuu);
-  k_values_uf<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uf.rowptr, o.jac.A_uf.colind, nn, vuf);
-  k_values_fu<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, M, sw, o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, vfu);
-  k_values_ff<<<grid_for(nc, 128), 128, 0, st>>>(g, P, M, sw, p, kh, kv, o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc,
+  PS_TICK(); k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, vuu);
+  PS_TICK(); k_values_uf<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uf.rowptr, o.jac.A_uf.colind, nn, vuf);
+  PS_TICK(); k_values_fu<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, M, sw, o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, vfu);
+  PS_TICK(); k_values_ff<<<grid_for(nc, 128), 128, 0, st>>>(g, P, M, sw, p, kh, kv, o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc,
                                                  vff, dfs);
   PS_CUDA(cudaGetLastError());
   o.jac.d_fs = dfs;
   // Dirichlet elimination (base nodes)
   uint8_t* dir;
   PS_TRY(ar.alloc(&dir, 3 * nn));
-  k_dirichlet_flags<<<grid_for(nn, 256), 256, 0, st>>>(g, nn, dir, (gp->flags & PS_GEN_DIRICHLET) ? 1 : 0);
-  k_zero_uu<<<grid_for(nn, 128), 128, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
-  k_zero_uf<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uf.rowptr, nn, dir, vuf);
-  k_zero_fu<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, dir, vfu);
+  PS_TICK(); k_dirichlet_flags<<<grid_for(nn, 256), 256, 0, st>>>(g, nn, dir, (gp->flags & PS_GEN_DIRICHLET) ? 1 : 0);
+  PS_TICK(); k_zero_uu<<<grid_for(nn, 128), 128, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
+  PS_TICK(); k_zero_uf<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uf.rowptr, nn, dir, vuf);
+  PS_TICK(); k_zero_fu<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, dir, vfu);
   o.jac.dirichlet_u = dir;
   double* alpha;  // [alpha_u, alpha_f]
   PS_TRY(ar.alloc(&alpha, 2));
@@ -750,25 +750,25 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   if (gp->flags & PS_GEN_SCALE) {
     double *dv, *cv, *sums;
     PS_TRY(ar.alloc(&dv, 3 * nn)); PS_TRY(ar.alloc(&cv, 3 * nn)); PS_TRY(ar.alloc(&sums, 3));
-    k_diag_uu<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu, dv, cv);
+    PS_TICK(); k_diag_uu<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu, dv, cv);
     PS_TRY(sum_f64(ar, dv, 3 * nn, sums + 0, st));
     PS_TRY(sum_f64(ar, cv, 3 * nn, sums + 1, st));
-    k_diag_pp<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc, vff, 1e6, dv);
+    PS_TICK(); k_diag_pp<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc, vff, 1e6, dv);
     PS_TRY(sum_f64(ar, dv, nc, sums + 2, st));
-    k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc));
+    PS_TICK(); k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc));
     const double pc = 1e6;
-    k_scale<<<grid_for(o.jac.A_uu.nnzb * 9, 256), 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, 9, 0, pc, alpha, 0);
-    k_scale<<<grid_for(o.jac.A_uf.nnzb * 6, 256), 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, 2, 0x2, pc, alpha, 0);
-    k_scale<<<grid_for(o.jac.A_fu.nnzb * 6, 256), 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, 6, 0, pc, alpha, 1);
-    k_scale<<<grid_for(o.jac.A_ff.nnzb * 4, 256), 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, 2, 0x2, pc, alpha, 1);
-    k_scale<<<grid_for(2 * nc, 256), 256, 0, st>>>(dfs, 2 * nc, 1, 0x1, pc, alpha, 1);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_uu.nnzb * 9, 256), 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, 9, 0, pc, alpha, 0);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_uf.nnzb * 6, 256), 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, 2, 0x2, pc, alpha, 0);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_fu.nnzb * 6, 256), 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, 6, 0, pc, alpha, 1);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_ff.nnzb * 4, 256), 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, 2, 0x2, pc, alpha, 1);
+    PS_TICK(); k_scale<<<grid_for(2 * nc, 256), 256, 0, st>>>(dfs, 2 * nc, 1, 0x1, pc, alpha, 1);
     PS_CUDA(cudaGetLastError());
     ar.release(dv); ar.release(cv); ar.release(sums);
   }
-  k_unit_diag<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
+  PS_TICK(); k_unit_diag<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
   double* rhs;
   PS_TRY(ar.alloc(&rhs, o.n));
-  k_rhs<<<grid_for(o.n, 256), 256, 0, st>>>(gp->seed, o.n, o.n_u, dir, rhs);
+  PS_TICK(); k_rhs<<<grid_for(o.n, 256), 256, 0, st>>>(gp->seed, o.n, o.n_u, dir, rhs);
   PS_CUDA(cudaGetLastError());
   o.rhs = rhs;
   double ha[2];

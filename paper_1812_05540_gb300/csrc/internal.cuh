@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -26,7 +27,14 @@
 
 namespace ps_internal {
 
+// number of kernels launched by this library (for launch accounting)
+extern std::atomic<int64_t> g_launches;
+#define PS_TICK() ps_internal::g_launches.fetch_add(1, std::memory_order_relaxed)
+
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+// reason attached to the next PS_ERR_INVALID / PS_ERR_TIMEOUT returned
+void set_reason(const char* fmt, ...);
+const std::string& last_reason();
 const std::string& last_error();
 
 // Device memory owned by one object; every allocation is stream-ordered from a

@@ -307,38 +307,38 @@ void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, doub
   // partial sums: u blocks first, then f blocks, folded into kRedBlocks slots
   double* pu = part ? part + kRedBlocks : nullptr;
   double* pf = part ? part + kRedBlocks + gu : nullptr;
-  k_spmv_u<<<unsigned(gu), 256, 0, st>>>(J, x, y, b, pu);
-  k_spmv_f<<<unsigned(gf), 256, 0, st>>>(J, x, y, b, pf);
-  if (part) k_fold<<<grid_for(kRedBlocks, 256), 256, 0, st>>>(part + kRedBlocks, gu + gf, part);
+  PS_TICK(); k_spmv_u<<<unsigned(gu), 256, 0, st>>>(J, x, y, b, pu);
+  PS_TICK(); k_spmv_f<<<unsigned(gf), 256, 0, st>>>(J, x, y, b, pf);
+  if (part) { PS_TICK(); k_fold<<<grid_for(kRedBlocks, 256), 256, 0, st>>>(part + kRedBlocks, gu + gf, part); }
 }
 
 void multidot(const double* V, int64_t ldv, int m, const double* w, int64_t n, double* part, double* h,
               int with_norm, const int* gate, cudaStream_t st) {
-  k_multidot<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, w, n, with_norm, part, gate);
+  PS_TICK(); k_multidot<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, w, n, with_norm, part, gate);
   int mm = m + (with_norm ? 1 : 0);
-  k_multidot_final<<<grid_for(int64_t(mm) * 32, 256), 256, 0, st>>>(part, mm, h, gate);
+  PS_TICK(); k_multidot_final<<<grid_for(int64_t(mm) * 32, 256), 256, 0, st>>>(part, mm, h, gate);
 }
 
 void mupdate(const double* V, int64_t ldv, int m, const double* h, double* w, int64_t n, double* part,
              double* norm2, const int* gate, cudaStream_t st) {
-  k_mupdate<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, h, w, n, part, gate);
-  k_finish_sum<<<1, 256, 0, st>>>(part, norm2);
+  PS_TICK(); k_mupdate<<<kRedBlocks, 256, 0, st>>>(V, ldv, m, h, w, n, part, gate);
+  PS_TICK(); k_finish_sum<<<1, 256, 0, st>>>(part, norm2);
 }
 
 void maxpy(const double* Z, int64_t ldz, int m, const double* y, double* x, int64_t n, cudaStream_t st) {
-  k_maxpy<<<kVecBlocks, 256, 0, st>>>(Z, ldz, m, y, x, n);
+  PS_TICK(); k_maxpy<<<kVecBlocks, 256, 0, st>>>(Z, ldz, m, y, x, n);
 }
-void finish_sum(const double* part, double* out, cudaStream_t st) { k_finish_sum<<<1, 256, 0, st>>>(part, out); }
+void finish_sum(const double* part, double* out, cudaStream_t st) { PS_TICK(); k_finish_sum<<<1, 256, 0, st>>>(part, out); }
 void scale_vec(const double* x, double* y, int64_t n, const double* scale, cudaStream_t st) {
-  k_scale<<<kVecBlocks, 256, 0, st>>>(x, y, n, scale);
+  PS_TICK(); k_scale<<<kVecBlocks, 256, 0, st>>>(x, y, n, scale);
 }
-void fill_zero(double* x, int64_t n, cudaStream_t st) { k_zero<<<kVecBlocks, 256, 0, st>>>(x, n); }
+void fill_zero(double* x, int64_t n, cudaStream_t st) { PS_TICK(); k_zero<<<kVecBlocks, 256, 0, st>>>(x, n); }
 
-void arnoldi_check(KrylovState& K, cudaStream_t st) { k_arnoldi_check<<<1, 1, 0, st>>>(K.sc, K.flag); }
+void arnoldi_check(KrylovState& K, cudaStream_t st) { PS_TICK(); k_arnoldi_check<<<1, 1, 0, st>>>(K.sc, K.flag); }
 void arnoldi_finish(KrylovState& K, int m, int j, cudaStream_t st) {
-  k_arnoldi_finish<<<1, 1, 0, st>>>(K.H, K.cs, K.sn, K.g, K.h1, K.h2, K.sc, K.flag, m, j);
+  PS_TICK(); k_arnoldi_finish<<<1, 1, 0, st>>>(K.H, K.cs, K.sn, K.g, K.h1, K.h2, K.sc, K.flag, m, j);
 }
-void cycle_start(KrylovState& K, int m, cudaStream_t st) { k_cycle_start<<<1, 1, 0, st>>>(K.g, K.sc, m); }
-void hessenberg_solve(KrylovState& K, int m, int k, cudaStream_t st) { k_hsolve<<<1, 1, 0, st>>>(K.H, K.g, K.y, m, k); }
+void cycle_start(KrylovState& K, int m, cudaStream_t st) { PS_TICK(); k_cycle_start<<<1, 1, 0, st>>>(K.g, K.sc, m); }
+void hessenberg_solve(KrylovState& K, int m, int k, cudaStream_t st) { PS_TICK(); k_hsolve<<<1, 1, 0, st>>>(K.H, K.g, K.y, m, k); }
 
 }  // namespace ps_internal

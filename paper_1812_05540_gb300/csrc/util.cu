@@ -1,4 +1,5 @@
 // Allocation, error bookkeeping and deterministic scan / reduction kernels.
+#include <cstdarg>
 #include <cstdio>
 #include <mutex>
 
@@ -6,6 +7,7 @@
 
 namespace ps_internal {
 
+std::atomic<int64_t> g_launches{0};
 static std::string g_last_error;
 static std::mutex g_err_mu;
 
@@ -16,6 +18,18 @@ void set_last_error(cudaError_t e, const char* what, const char* file, int line)
   g_last_error = buf;
 }
 const std::string& last_error() { return g_last_error; }
+
+static std::string g_reason;
+void set_reason(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_reason = buf;
+}
+const std::string& last_reason() { return g_reason; }
 
 // One stream-ordered pool per device; freed blocks stay cached in the pool so
 // that repeated setups do not pay for cudaMalloc.
@@ -134,12 +148,12 @@ static ps_status scan_o(Arena& ar, const O* in, O* out, int64_t n, cudaStream_t 
   int64_t nb = ceil_div(n, 1024);
   O* bs = nullptr;
   PS_TRY(ar.alloc(&bs, nb + 1));
-  k_block_scan_o<O><<<unsigned(nb), 1024, 0, st>>>(in, out, bs, n);
+  PS_TICK(); k_block_scan_o<O><<<unsigned(nb), 1024, 0, st>>>(in, out, bs, n);
   if (nb > 1) {
     O* bo = nullptr;
     PS_TRY(ar.alloc(&bo, nb + 1));
     PS_TRY(scan_o<O>(ar, bs, bo, nb, st));
-    k_add_offsets_o<O><<<unsigned(nb), 1024, 0, st>>>(out, bo, n);
+    PS_TICK(); k_add_offsets_o<O><<<unsigned(nb), 1024, 0, st>>>(out, bo, n);
     ar.release(bo);
   }
   ar.release(bs);
@@ -158,9 +172,9 @@ static ps_status scan_impl(Arena& ar, const int32_t* in, O* out, int64_t n, O* t
   O* bo = nullptr;
   PS_TRY(ar.alloc(&bs, nb + 1));
   PS_TRY(ar.alloc(&bo, nb + 1));
-  k_block_scan<O><<<unsigned(nb), 1024, 0, st>>>(in, out, bs, n);
+  PS_TICK(); k_block_scan<O><<<unsigned(nb), 1024, 0, st>>>(in, out, bs, n);
   PS_TRY(scan_o<O>(ar, bs, bo, nb, st));
-  k_add_offsets<O><<<unsigned(nb), 1024, 0, st>>>(out, bo, n, out + n, in);
+  PS_TICK(); k_add_offsets<O><<<unsigned(nb), 1024, 0, st>>>(out, bo, n, out + n, in);
   PS_CUDA(cudaGetLastError());
   ar.release(bs);
   ar.release(bo);
@@ -207,8 +221,8 @@ static ps_status reduce(Arena& ar, const double* x, int64_t n, double* d_out, cu
   const int G = 512;
   double* part = nullptr;
   PS_TRY(ar.alloc(&part, G));
-  k_reduce_partial<OP><<<G, 256, 0, st>>>(x, n, part);
-  k_reduce_partial<OP><<<1, 256, 0, st>>>(part, G, d_out);
+  PS_TICK(); k_reduce_partial<OP><<<G, 256, 0, st>>>(x, n, part);
+  PS_TICK(); k_reduce_partial<OP><<<1, 256, 0, st>>>(part, G, d_out);
   PS_CUDA(cudaGetLastError());
   ar.release(part);
   return PS_OK;
@@ -226,7 +240,9 @@ __global__ void k_rowptr_i32(const int64_t* __restrict__ in, int32_t* __restrict
   if (i < n) out[i] = int32_t(in[i]);
 }
 void rowptr_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t st) {
-  k_rowptr_i32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+  PS_TICK(); k_rowptr_i32<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
 }
 
 }  // namespace ps_internal
+
+extern "C" int64_t ps_launch_count(void) { return ps_internal::g_launches.load(); }

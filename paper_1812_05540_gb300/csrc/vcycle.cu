@@ -172,10 +172,10 @@ LevelT<T> view(const AmgLevel& L) {
 
 #define DISPATCH_LANES(lanes, KERNEL, ...)                       \
   switch (lanes) {                                               \
-    case 4: KERNEL<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
-    case 8: KERNEL<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
-    case 16: KERNEL<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(__VA_ARGS__); break; \
-    default: KERNEL<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(__VA_ARGS__); break; \
+    case 4: PS_TICK(); KERNEL<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
+    case 8: PS_TICK(); KERNEL<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
+    case 16: PS_TICK(); KERNEL<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(__VA_ARGS__); break; \
+    default: PS_TICK(); KERNEL<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(__VA_ARGS__); break; \
   }
 
 struct ChebCoef {
@@ -219,7 +219,7 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
     ChebCoef cc = cheb_coef(L, NC, sp);
     int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
     if (deg == 1) {
-      k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, cc.inv_theta);
+      PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, cc.inv_theta);
       return x;
     }
     DISPATCH_LANES(L.lanes, k_cheb_pre, n, L.rp, L.ci, V.v, V.dg, b, x, deg > 2 ? d : nullptr, cc.inv_theta,
@@ -229,7 +229,7 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
       std::swap(cur, other);
     }
   } else {
-    k_l1_first<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dl1, b, x);
+    PS_TICK(); k_l1_first<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dl1, b, x);
     for (int k = 1; k < sp.pre; ++k) {
       DISPATCH_LANES(L.lanes, k_l1_step, n, L.rp, L.ci, V.v, V.dl1, b, cur, other);
       std::swap(cur, other);
@@ -271,10 +271,10 @@ template <class T, int NC>
 void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const T* v, const T* x, T* y, int add,
                 cudaStream_t st) {
   switch (lanes) {
-    case 4: k_spmv<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 8: k_spmv<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 16: k_spmv<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    default: k_spmv<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 4: PS_TICK(); k_spmv<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 8: PS_TICK(); k_spmv<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 16: PS_TICK(); k_spmv<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    default: PS_TICK(); k_spmv<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
   }
 }
 
@@ -284,7 +284,7 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
   LevelT<T> V = view<T>(L);
   int64_t n = L.n;
   if (L.coarsest) {
-    k_dense_solve<T, NC><<<grid_for(n * NC * 32, 256), 256, 0, st>>>(n, V.inv, b, out);
+    PS_TICK(); k_dense_solve<T, NC><<<grid_for(n * NC * 32, 256), 256, 0, st>>>(n, V.inv, b, out);
     return;
   }
   T* x = static_cast<T*>(L.x);
