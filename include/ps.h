@@ -148,6 +148,25 @@ ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t*
 /* S_pp values in the A_ff pattern and ILU inverse diagonal blocks (host copies) */
 ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv);
 
+/* Residual without device allocation: r = b - A x and *rnorm2 = ||r||^2 for
+   the FP64 Jacobian blocks in *jac (device pointers, int64 row pointers as in
+   ps_bsr), x, b, r of length n and rnorm2 (one double) device pointers.  The
+   paper has no counterpart: this entry point exists for callers that manage
+   all device memory themselves (for instance a simulator that reserves its HBM
+   at start-up so a long run cannot fail on an allocation, or a process whose
+   allocator is capped) and so cannot let the library call cudaMalloc.  It
+   allocates nothing: its only scratch (the partial sums of ||r||^2) is a fixed
+   static device array of (2^19 + 1024) doubles, 4 MiB, which every GPU that
+   loads the library holds until exit.  The first call on each device looks up
+   that array's device address (cudaGetSymbolAddress) with the device current;
+   make that first call before any stream capture.  Systems with more than
+   2^22 node + cell rows in total are rejected with PS_ERR_INVALID.  Every call
+   shares the array, so calls that overlap on the GPU race: the caller must not
+   run two at once.  Work is enqueued on stream (NULL = legacy stream) and not
+   synchronised; *rnorm2 is valid once the stream reaches that point. */
+ps_status ps_residual_noalloc(const ps_jacobian* jac, const ps_grid* grid, const double* x, const double* b,
+                              double* r, double* rnorm2, void* stream);
+
 /* Frees everything the handle owns (synchronises its stream). */
 void ps_free(ps_handle* h);
 

@@ -108,6 +108,8 @@ def lib():
         L.ps_generate.argtypes = [C.POINTER(ps_gen_params), C.c_void_p, C.POINTER(C.POINTER(ps_system))]
         L.ps_system_free.argtypes = [C.POINTER(ps_system)]
         L.ps_system_free.restype = None
+        L.ps_residual_noalloc.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.ps_launch_count.argtypes = []
         L.ps_launch_count.restype = C.c_int64
         L.ps_strerror.argtypes = [C.c_int]
@@ -187,6 +189,12 @@ def ps_spmv(h, x_ptr, y_ptr):
 
 def ps_apply_prec(h, v_ptr, z_ptr):
     _check(lib().ps_apply_prec(h, v_ptr, z_ptr), "ps_apply_prec")
+
+
+def ps_residual_noalloc(jac, grid, x_ptr, b_ptr, r_ptr, rnorm2_ptr, stream=None):
+    """r = b - A x and ||r||^2 with no device allocation (all pointers device memory)."""
+    _check(lib().ps_residual_noalloc(C.byref(jac), C.byref(grid), x_ptr, b_ptr, r_ptr, rnorm2_ptr, stream),
+           "ps_residual_noalloc")
 
 
 def ps_free(h):
