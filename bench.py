@@ -37,6 +37,9 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling only: stop FGMRES after this many iterations (bounded ncu launch lists)")
     return ap.parse_args()
 
 
@@ -191,12 +194,14 @@ def run_ours(args):
 
         def step(prec):
             p = ps.ps_params_default(precision=prec, stream=sptr)
+            if args.profile_iters:
+                p.max_iters = args.profile_iters
             h = ps.ps_setup(s.jac, s.grid, p)
             try:
                 status, st = ps.ps_solve(h, s.rhs, x.data_ptr(), TOL, raise_on_error=False)
             finally:
                 ps.ps_free(h)
-            if status != ps.PS_OK:
+            if status != ps.PS_OK and not (args.profile_iters and status == ps.PS_ERR_NOT_CONVERGED):
                 raise RuntimeError("solve failed: %s" % ps.ps_strerror(status))
             return st
 
@@ -230,10 +235,15 @@ def run_ours(args):
 
         for _ in range(args.warmup):
             step(ps.PS_MIXED_FP32)
-        step(ps.PS_FP64)
+        if not args.no_fp64:
+            step(ps.PS_FP64)
         clocks = Clocks(local)
         t_mx, st_mx, launches, ck = timed(ps.PS_MIXED_FP32, args.steps, clocks)
-        t_64, st_64, _, _ = timed(ps.PS_FP64, args.steps)
+        if args.profile_iters:
+            print(json.dumps({"profile_iters": args.profile_iters, "launches": launches, "seconds": t_mx}))
+            ps.ps_system_free(sysp)
+            return
+        t_64, st_64 = (t_mx, st_mx) if args.no_fp64 else timed(ps.PS_FP64, args.steps)[:2]
         per_mx = t_mx / args.steps
         per_64 = t_64 / args.steps
 
@@ -349,9 +359,16 @@ def run_ours(args):
         "iters_mixed": it_mx, "iters_fp64": it_64,
         "setup_ms_mixed": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_mx],
         "solve_ms_mixed": [round(st.ms_solve, 2) for st in st_mx],
+        "solve_phases_ms_mixed": {"precond": round(st_mx[-1].ms_prec, 1), "spmv": round(st_mx[-1].ms_spmv, 1),
+                                  "gram_schmidt": round(st_mx[-1].ms_orth, 1),
+                                  "reorth_steps": st_mx[-1].reorth,
+                                  "vcycle_u": round(st_mx[-1].ms_vcycle_u, 1), "flow_2_4": round(st_mx[-1].ms_flow24, 1),
+                                  "vcycle_p": round(st_mx[-1].ms_vcycle_p, 1), "ilu": round(st_mx[-1].ms_ilu, 1)},
         "fp64": {"value": per_64 / world, "ms_per_step": 1000.0 * per_64,
                  "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_64],
-                 "solve_ms": [round(st.ms_solve, 2) for st in st_64]},
+                 "solve_ms": [round(st.ms_solve, 2) for st in st_64],
+                 "solve_phases_ms": {"precond": round(st_64[-1].ms_prec, 1), "spmv": round(st_64[-1].ms_spmv, 1),
+                                     "gram_schmidt": round(st_64[-1].ms_orth, 1)}},
         "mixed_speedup_vs_fp64": per_64 / per_mx,
         "true_relres_mixed": relres, "gen_s": gen_s,
         "roofline": {"kernel": "FP64 Jacobian SpMV (k_spmv_u + k_spmv_f)", "bound": "hbm",

@@ -91,11 +91,14 @@ typedef struct {
   int32_t coarse_max_u;       /* coarsest mechanics level size in nodes (500) */
   int32_t coarse_max_p;       /* coarsest pressure level size in cells (500) */
   int32_t max_levels;         /* (25) */
-  int32_t ilu_mode;           /* PS_ILU_* */
-  int64_t spin_limit;         /* bounded-wait polls before PS_ERR_TIMEOUT */
+  int32_t ilu_mode;           /* PS_ILU_PENCIL (default: sync-free wavefront) or PS_ILU_LEVEL_LAUNCH */
+  int64_t spin_limit;         /* polls of a wavefront wait before PS_ERR_TIMEOUT (default 2e6, ~1 s) */
   int32_t host_ptrs;          /* 1: jacobian arrays, rhs and x are host pointers */
   int64_t hbm_budget;         /* bytes the handle may hold; 0 = unlimited */
   void* stream;               /* cudaStream_t */
+  int32_t test_stall_wave;    /* testing only, 0 = off: k > 0 makes wavefront CTA k-1 skip its
+                                 work so that the bounded waits of its consumers run out and
+                                 ps_solve returns PS_ERR_TIMEOUT (no fault, no hang) */
 } ps_params;
 
 typedef struct {
@@ -105,6 +108,10 @@ typedef struct {
   int64_t bytes_model;              /* algorithmic HBM bytes of the solve */
   int64_t handle_bytes;             /* device bytes held by the handle */
   int32_t levels_u, levels_p;
+  float ms_prec, ms_spmv, ms_orth;  /* solve time in Algorithm 1, the Jacobian SpMV and Gram-Schmidt */
+  int32_t reorth;                   /* Arnoldi steps that needed the second Gram-Schmidt pass */
+  float ms_vcycle_u, ms_flow24, ms_vcycle_p, ms_ilu;  /* parts of ms_prec: Algorithm 1 step 1, steps
+                                                          2-4, step 5, steps 6-8 */
 } ps_stats;
 
 typedef struct ps_handle ps_handle;
@@ -125,6 +132,9 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
    A_ff and d_fs values with unchanged patterns, keeping the mechanics AMG: the
    per-Newton flow setup of §5.2/§5.4. */
 ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac);
+
+/* Testing only: set ps_params.test_stall_wave on an existing handle (0 = off). */
+ps_status ps_set_test_stall(ps_handle* h, int32_t wave_cta_plus_one);
 
 /* Iteration phase: x = FGMRES(A, M^{-1}, rhs) from x0 = 0 to the true FP64
    relative residual tol.  rhs, x: n = 3*nodes + 2*cells doubles.

@@ -45,14 +45,16 @@ class ps_params(C.Structure):
                 ("cheb_ratio", C.c_double), ("theta_u", C.c_double), ("theta_p", C.c_double),
                 ("coarse_max_u", C.c_int32), ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32),
                 ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
-                ("hbm_budget", C.c_int64), ("stream", C.c_void_p)]
+                ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32)]
 
 
 class ps_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("true_relres", C.c_double),
                 ("est_relres", C.c_double), ("ms_setup_u", C.c_float), ("ms_setup_f", C.c_float),
                 ("ms_solve", C.c_float), ("bytes_model", C.c_int64), ("handle_bytes", C.c_int64),
-                ("levels_u", C.c_int32), ("levels_p", C.c_int32)]
+                ("levels_u", C.c_int32), ("levels_p", C.c_int32), ("ms_prec", C.c_float), ("ms_spmv", C.c_float),
+                ("ms_orth", C.c_float), ("reorth", C.c_int32), ("ms_vcycle_u", C.c_float),
+                ("ms_flow24", C.c_float), ("ms_vcycle_p", C.c_float), ("ms_ilu", C.c_float)]
 
 
 class ps_gen_params(C.Structure):
@@ -92,6 +94,7 @@ def lib():
         L.ps_params_default.restype = None
         L.ps_setup.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.POINTER(ps_params), C.POINTER(H)]
         L.ps_setup_flow.argtypes = [H, C.POINTER(ps_jacobian)]
+        L.ps_set_test_stall.argtypes = [H, C.c_int32]
         L.ps_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ps_stats)]
         L.ps_spmv.argtypes = [H, C.c_void_p, C.c_void_p]
         L.ps_apply_prec.argtypes = [H, C.c_void_p, C.c_void_p]
@@ -168,6 +171,10 @@ def ps_setup(jac, grid, params):
     h = C.c_void_p()
     _check(lib().ps_setup(C.byref(jac), C.byref(grid), C.byref(params), C.byref(h)), "ps_setup")
     return h
+
+
+def ps_set_test_stall(h, wave_cta_plus_one):
+    _check(lib().ps_set_test_stall(h, wave_cta_plus_one), "ps_set_test_stall")
 
 
 def ps_setup_flow(h, jac):

@@ -225,55 +225,45 @@ __global__ void k_l1(int64_t n, const int32_t* __restrict__ rp, const double* __
   }
 }
 
-// ---- smoothed prolongator P = (I - omega D^{-1} A) P_tent, row by row ----
-__device__ __forceinline__ bool first_occurrence(const int32_t* __restrict__ ci, const int32_t* __restrict__ agg,
-                                                 int32_t q0, int32_t q, int32_t a) {
-  for (int32_t t = q0; t < q; ++t)
-    if (agg[ci[t]] == a) return false;
-  return true;
-}
-__global__ void k_p_count(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                          const int32_t* __restrict__ agg, const uint8_t* __restrict__ excl,
-                          int32_t* __restrict__ cnt) {
+// tentative prolongator P_tent[i, agg(i)] = 1 (one entry per aggregated row)
+__global__ void k_ptent_count(int64_t n, const int32_t* __restrict__ agg, int32_t* __restrict__ cnt) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t c = 0;
-  if (!excl[i])
-    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
-      int32_t a = agg[ci[q]];
-      if (a >= 0 && first_occurrence(ci, agg, rp[i], q, a)) ++c;
-    }
-  cnt[i] = c;
+  if (i < n) cnt[i] = agg[i] >= 0 ? 1 : 0;
 }
 template <int NC>
-__global__ void k_p_fill(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const double* __restrict__ v, const int32_t* __restrict__ agg, double w0, double w1,
-                         double w2, const uint8_t* __restrict__ excl, const int32_t* __restrict__ prp,
-                         int32_t* __restrict__ pci, double* __restrict__ pv) {
+__global__ void k_ptent_fill(int64_t n, const int32_t* __restrict__ agg, const int32_t* __restrict__ rp,
+                             int32_t* __restrict__ ci, double* __restrict__ v) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || agg[i] < 0) return;
+  ci[rp[i]] = agg[i];
+  for (int c = 0; c < NC; ++c) v[int64_t(rp[i]) * NC + c] = 1.0;
+}
+// row lengths of P: those of T = A P_tent, except identity rows, which are empty
+__global__ void k_p_rowlen(int64_t n, const int32_t* __restrict__ trp, const uint8_t* __restrict__ excl,
+                           int32_t* __restrict__ cnt) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = excl[i] ? 0 : trp[i + 1] - trp[i];
+}
+// P_ia = delta(a, agg(i)) - (omega / a_ii) * T_ia, T_ia = sum over the row's
+// columns j of aggregate a of a_ij (ascending j)
+template <int NC>
+__global__ void k_p_finish(int64_t n, const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                           const double* __restrict__ tv, const uint8_t* __restrict__ excl,
+                           const int32_t* __restrict__ agg, const double* __restrict__ dg, double w0, double w1,
+                           double w2, const int32_t* __restrict__ prp, int32_t* __restrict__ pci,
+                           double* __restrict__ pv) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n || excl[i]) return;
   const double om[3] = {w0, w1, w2};
-  int32_t q0 = rp[i], q1 = rp[i + 1];
-  int32_t qd = q0;
-  while (ci[qd] != i) ++qd;
-  for (int32_t q = q0; q < q1; ++q) {
-    int32_t a = agg[ci[q]];
-    if (a < 0 || !first_occurrence(ci, agg, q0, q, a)) continue;
-    int32_t rank = 0;
-    for (int32_t t = q0; t < q1; ++t) {
-      int32_t b = agg[ci[t]];
-      if (b >= 0 && b < a && first_occurrence(ci, agg, q0, t, b)) ++rank;
-    }
-    int32_t pos = prp[i] + rank;
-    pci[pos] = a;
+  int32_t o = prp[i];
+  for (int32_t q = trp[i]; q < trp[i + 1]; ++q, ++o) {
+    int32_t a = tci[q];
+    pci[o] = a;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      double S = 0.0;
-      for (int32_t t = q0; t < q1; ++t)
-        if (agg[ci[t]] == a) S = S + v[int64_t(t) * NC + c];
-      double coef = om[c] / v[int64_t(qd) * NC + c];
+      double coef = om[c] / dg[i * NC + c];
       double delta = a == agg[i] ? 1.0 : 0.0;
-      pv[int64_t(pos) * NC + c] = delta - coef * S;
+      pv[int64_t(o) * NC + c] = delta - coef * tv[int64_t(q) * NC + c];
     }
   }
 }
@@ -787,23 +777,36 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_TRY(ar.alloc(&lev.dl1f, n * NC));
       PS_TICK(); k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
     }
-    // prolongator
-    int32_t* pc;
+    // prolongator: T = A P_tent by the deterministic SpGEMM, then P = P_tent - omega D^{-1} T
+    int64_t na = lev.nagg;
+    int32_t *trp0, *tci0, *pc;
+    double* tv0;
     PS_TRY(ar.alloc(&pc, n + 1));
+    PS_TRY(ar.alloc(&trp0, n + 1));
+    PS_TICK(); k_ptent_count<<<grid_for(n, 256), 256, 0, st>>>(n, lev.agg, pc);
+    int32_t nt = 0;
+    PS_TRY(scan_i32(ar, pc, trp0, n, &nt, st));
+    PS_TRY(ar.alloc(&tci0, size_t(nt) + 1));
+    PS_TRY(ar.alloc(&tv0, (size_t(nt) + 1) * NC));
+    PS_TICK(); k_ptent_fill<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.agg, trp0, tci0, tv0);
+    int32_t *Trp, *Tci;
+    double* Tv;
+    int64_t Tnnz = 0;
+    PS_TRY(spgemm<NC>(ar, n, na, lev.rp, lev.ci, lev.v, trp0, tci0, tv0, &Trp, &Tci, &Tv, &Tnnz, d_err, st));
+    ar.release(trp0); ar.release(tci0); ar.release(tv0);
     PS_TRY(ar.alloc(&lev.prp, n + 1));
-    PS_TICK(); k_p_count<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.agg, excl, pc);
+    PS_TICK(); k_p_rowlen<<<grid_for(n, 256), 256, 0, st>>>(n, Trp, excl, pc);
     int32_t pnnz = 0;
     PS_TRY(scan_i32(ar, pc, lev.prp, n, &pnnz, st));
     lev.pnnz = pnnz;
     PS_TRY(ar.alloc(&lev.pci, size_t(pnnz) + 1));
     PS_TRY(ar.alloc(&lev.pv, (size_t(pnnz) + 1) * NC));
-    PS_TICK(); k_p_fill<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, om[0], om[1], om[2], excl,
-                                                    lev.prp, lev.pci, lev.pv);
+    PS_TICK(); k_p_finish<NC><<<grid_for(n, 256), 256, 0, st>>>(n, Trp, Tci, Tv, excl, lev.agg, lev.dg, om[0], om[1],
+                                                                 om[2], lev.prp, lev.pci, lev.pv);
     PS_CUDA(cudaGetLastError());
-    ar.release(pc);
+    ar.release(pc); ar.release(Trp); ar.release(Tci); ar.release(Tv);
     lev.plane = lanes_for(double(pnnz) / double(n));
     // restriction R = P^T
-    int64_t na = lev.nagg;
     int32_t *ccount, *cursor, *tci;
     double* tv;
     PS_TRY(ar.alloc(&ccount, na + 1));

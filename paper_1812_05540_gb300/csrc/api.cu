@@ -56,6 +56,9 @@ struct ps_handle {
   int* hflag = nullptr;   // pinned: 2 flags
   float ms_setup_u = 0, ms_setup_f = 0;
   int64_t spmv_part = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-iteration phase timers
+  cudaEvent_t fe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Algorithm 1 sub-phase timers
+  bool fine_pending = false;
 };
 
 namespace {
@@ -73,23 +76,30 @@ ps_status alg1(ps_handle* h, const double* v, double* z) {
   FlowWork<T>* W;
   if constexpr (sizeof(T) == 4) W = &h->w32;
   else W = &h->w64;
+  cudaEventRecord(h->fe[0], st);
   // step 1: z_u = M_uu^{-1} v_u
   if constexpr (sizeof(T) == 4) {
     PS_TICK(); k_d2f<<<grid_for(h->nu, 256), 256, 0, st>>>(v, h->vu32, h->nu);
     PS_TRY(amg_vcycle<float>(h->amg_u, sp, h->vu32, h->zu32, st));
+    cudaEventRecord(h->fe[1], st);
     PS_TICK(); k_f2d<<<grid_for(h->nu, 256), 256, 0, st>>>(h->zu32, z, h->nu);
     PS_TICK(); k_d2f<<<grid_for(h->nf, 256), 256, 0, st>>>(v + h->nu, W->vf, h->nf);
     // steps 2-4
     alg1_steps_2_4<float>(h->F, *W, h->zu32, st);
   } else {
     PS_TRY(amg_vcycle<double>(h->amg_u, sp, v, z, st));
+    cudaEventRecord(h->fe[1], st);
     PS_CUDA(cudaMemcpyAsync(W->vf, v + h->nu, sizeof(double) * h->nf, cudaMemcpyDeviceToDevice, st));
     alg1_steps_2_4<double>(h->F, *W, z, st);
   }
+  cudaEventRecord(h->fe[2], st);
   // step 5: z_p = M_pp^{-1} w_p
   PS_TRY(amg_vcycle<T>(h->amg_p, sp, W->wp, W->zp, st));
+  cudaEventRecord(h->fe[3], st);
   // steps 6-8
   alg1_steps_6_8<T>(h->F, *W, z + h->nu, h->prm.ilu_mode, st);
+  cudaEventRecord(h->fe[4], st);
+  h->fine_pending = true;
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
@@ -143,6 +153,8 @@ ps_status build_flow(ps_handle* h) {
   F.nnzb = tot;
   F.rp = h->J.ff_rp; F.ci = h->J.ff_ci;
   F.fu_rp = h->J.fu_rp; F.fu_ci = h->J.fu_ci; F.fu_v = h->J.fu_v;
+  F.spin_limit = h->prm.spin_limit > 0 ? h->prm.spin_limit : 2000000;
+  F.test_stall = h->prm.test_stall_wave;
   PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, h->dfs, h->mixed, st));
   if (h->mixed) {
     int64_t nfu = 0;
@@ -186,6 +198,9 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(copy_bsr(h, jac->A_fu, &J.fu_rp, &J.fu_ci, &J.fu_v));
   PS_TRY(copy_bsr(h, jac->A_ff, &J.ff_rp, &J.ff_ci, &J.ff_v));
   PS_TRY(copy_in(ar, jac->d_fs, sizeof(double) * 2 * h->nc, (void**)&h->dfs, h->prm.host_ptrs != 0, st));
+  J.nx = h->grid.nx; J.ny = h->grid.ny; J.nz = h->grid.nz;
+  bool structured = false;
+  PS_TRY(jac_build_stencil(ar, J, &structured, st));
   if (flow_check_pattern(ar, h->grid, J.ff_rp, J.ff_ci, st) != PS_OK) {
     set_reason("A_ff is not the 7-point TPFA pattern of the %dx%dx%d grid", h->grid.nx, h->grid.ny, h->grid.nz);
     return PS_ERR_INVALID;
@@ -221,7 +236,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(ar.alloc(&h->r, n));
   PS_TRY(ar.alloc(&h->b, n));
   PS_TRY(ar.alloc(&h->x, n));
-  int64_t gu = ceil_div(h->nn * 32, 256), gf = ceil_div(h->nc * 32, 256);
+  int64_t gu = ceil_div(h->nn * 32, 256), gf = ceil_div(h->nc * 32, 256);  // bound for both SpMV paths
   h->spmv_part = kRedBlocks + gu + gf;
   PS_TRY(ar.alloc(&h->part, h->spmv_part));
   PS_TRY(ar.alloc(&h->mpart, size_t(m + 2) * kRedBlocks));
@@ -231,6 +246,8 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(ar.alloc(&K.h1, m + 2)); PS_TRY(ar.alloc(&K.h2, m + 2)); PS_TRY(ar.alloc(&K.y, m + 1));
   PS_TRY(ar.alloc(&K.sc, 16)); PS_TRY(ar.alloc(&K.flag, 4));
   PS_CUDA(cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), st));
+  for (int e = 0; e < 4; ++e) PS_CUDA(cudaEventCreate(&h->ev[e]));
+  for (int e = 0; e < 5; ++e) PS_CUDA(cudaEventCreate(&h->fe[e]));
   PS_CUDA(cudaMallocHost(&h->hsc, 16 * sizeof(double)));
   PS_CUDA(cudaMallocHost(&h->hflag, 4 * sizeof(int)));
   PS_CUDA(cudaStreamSynchronize(st));
@@ -253,8 +270,8 @@ void ps_params_default(ps_params* p) {
   p->theta_u = 0.08; p->theta_p = 0.08;
   p->coarse_max_u = 500; p->coarse_max_p = 500;
   p->max_levels = 25;
-  p->ilu_mode = PS_ILU_LEVEL_LAUNCH;
-  p->spin_limit = 100000000;
+  p->ilu_mode = PS_ILU_PENCIL;
+  p->spin_limit = 2000000;
 }
 
 ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params, ps_handle** out) {
@@ -284,6 +301,13 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
     return s;
   }
   *out = h;
+  return PS_OK;
+}
+
+ps_status ps_set_test_stall(ps_handle* h, int32_t wave_cta_plus_one) {
+  if (!h || wave_cta_plus_one < 0) return PS_ERR_INVALID;
+  h->prm.test_stall_wave = wave_cta_plus_one;
+  h->F.test_stall = wave_cta_plus_one;
   return PS_OK;
 }
 
@@ -356,13 +380,16 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
       cycle_start(K, m, st);
       scale_vec(h->r, h->V, n, K.sc + 4, st);
       int jend = -1;
-      bool brk = false, nanf = false;
+      bool brk = false, nanf = false, timeout = false;
       for (int j = 0; j < m; ++j) {
         double* vj = h->V + int64_t(j) * n;
         double* zj = h->Z + int64_t(j) * n;
         double* w = h->V + int64_t(j + 1) * n;
+        cudaEventRecord(h->ev[0], st);
         PS_TRY(apply_prec(h, vj, zj));
+        cudaEventRecord(h->ev[1], st);
         jac_spmv(h->J, zj, w, nullptr, nullptr, st);
+        cudaEventRecord(h->ev[2], st);
         // classical Gram-Schmidt with selective reorthogonalisation
         multidot(h->V, n, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
         PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -372,16 +399,36 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
         mupdate(h->V, n, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
         arnoldi_finish(K, m, j, st);
         scale_vec(w, w, n, K.sc + 4, st);
+        cudaEventRecord(h->ev[3], st);
         ++total;
         PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h->hflag + 2, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
         double est = h->hsc[5], hn = h->hsc[6];
+        {
+          float a = 0, b = 0, c = 0;
+          cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+          cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+          cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
+          S.ms_prec += a; S.ms_spmv += b; S.ms_orth += c;
+          float f[4] = {0, 0, 0, 0};
+          for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&f[q], h->fe[q], h->fe[q + 1]);
+          S.ms_vcycle_u += f[0]; S.ms_flow24 += f[1]; S.ms_vcycle_p += f[2]; S.ms_ilu += f[3];
+        }
         S.est_relres = est;
         jend = j;
+        S.reorth += h->hflag[0];
+        if (h->hflag[2]) { timeout = true; break; }
         if (h->hflag[1]) { nanf = true; break; }
         if (!(hn > 1e-300 * bnorm)) brk = true;
         if (est <= tol || brk || total >= h->prm.max_iters) break;
+      }
+      if (timeout) {
+        PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
+        set_reason("a bounded wait of the wavefront ILU(0) sweep gave up");
+        result = PS_ERR_TIMEOUT;
+        break;
       }
       if (nanf) { result = PS_ERR_NAN; break; }
       hessenberg_solve(K, m, jend, st);
@@ -468,6 +515,10 @@ void ps_free(ps_handle* h) {
   h->arf.free_all();
   h->ar.free_all();
   cudaStreamSynchronize(h->st);
+  for (int e = 0; e < 4; ++e)
+    if (h->ev[e]) cudaEventDestroy(h->ev[e]);
+  for (int e = 0; e < 5; ++e)
+    if (h->fe[e]) cudaEventDestroy(h->fe[e]);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hflag) cudaFreeHost(h->hflag);
   delete h;
@@ -483,7 +534,8 @@ const char* ps_strerror(ps_status s) {
     case PS_ERR_NOT_CONVERGED: return "not converged within max_iters";
     case PS_ERR_BREAKDOWN: return "Krylov breakdown before convergence";
     case PS_ERR_NAN: return "NaN or Inf encountered";
-    case PS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PS_ERR_TIMEOUT:
+      return ps_internal::last_reason().empty() ? "bounded device wait timed out" : ps_internal::last_reason().c_str();
     case PS_ERR_BUDGET: return "HBM budget exceeded";
   }
   return "unknown status";

@@ -21,6 +21,16 @@ struct FlowStage {
   int nlev = 0;
   int32_t* lev_cells = nullptr;
   std::vector<int32_t> lev_off;          // host copy, nlev + 1
+  // S_ff^(FS) indexed by stencil slot, 28 entries per cell (z-1, y-1, x-1, self, x+1, y+1, z+1; 2x2
+  // row-major each), zero blocks outside the grid
+  double* s28 = nullptr;
+  float* s28_f = nullptr;
+  // sync-free wavefront sweeps: per-CTA progress counters (epoch-stamped) and error flag
+  int64_t *prog_fwd = nullptr, *prog_bwd = nullptr;
+  int* ilu_err = nullptr;
+  int64_t ilu_epoch = 0;
+  int64_t spin_limit = 2000000;
+  int test_stall = 0;
   // A_fu for Algorithm 1 step 2
   int32_t *fu_rp = nullptr, *fu_ci = nullptr;
   const double* fu_v = nullptr;

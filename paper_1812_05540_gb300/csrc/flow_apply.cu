@@ -8,15 +8,15 @@ namespace {
 
 template <class T>
 struct FlowView {
-  const T *fu, *sff, *aps, *dinv, *dss;
+  const T *fu, *sff, *aps, *dinv, *dss, *s28;
 };
 template <class T>
 FlowView<T> fview(const FlowStage& F) {
   FlowView<T> o;
   if constexpr (sizeof(T) == 4) {
-    o.fu = F.fu_vf; o.sff = F.sff_f; o.aps = F.aps_f; o.dinv = F.dinv_f; o.dss = F.dss_f;
+    o.fu = F.fu_vf; o.sff = F.sff_f; o.aps = F.aps_f; o.dinv = F.dinv_f; o.dss = F.dss_f; o.s28 = F.s28_f;
   } else {
-    o.fu = F.fu_v; o.sff = F.sff; o.aps = F.aps; o.dinv = F.dinv; o.dss = F.dss;
+    o.fu = F.fu_v; o.sff = F.sff; o.aps = F.aps; o.dinv = F.dinv; o.dss = F.dss; o.s28 = F.s28;
   }
   return o;
 }
@@ -131,6 +131,201 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
   zout[2 * i + 1] = double(zp[i] + e1);
 }
 
+// ---------------------------------------------------------------------------
+// Sync-free wavefront sweeps over the stencil-indexed S_ff^(FS).
+// Thread (ly, lz) of CTA (BY, BZ) owns the x-pencil (y, z) = (BY*kTY + ly,
+// BZ*kTZ + lz) and walks it sequentially: at CTA step s it handles position
+// s - ry - rz (ry, rz = distance from the producing CTA boundary), so its y- and
+// z-predecessors inside the CTA were computed at step s - 1 (double-buffered
+// shared array).  Everything that does not depend on the wavefront is loaded
+// one step ahead.  Boundary pencils take their predecessors from global memory:
+// before prefetching the value for step s + 1 each polls its producer CTA's
+// progress with an acquire load (bounded; on timeout it raises *err); each CTA
+// publishes its progress with a release store after the step's barrier.
+// ---------------------------------------------------------------------------
+constexpr int kTY = 16, kTZ = 8;
+constexpr int64_t kEpochStride = 1 << 20;  // > steps per sweep
+
+__device__ __forceinline__ int64_t ld_acquire(const int64_t* p) {
+  int64_t v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
+  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// bounded wait until *flag >= need; `seen` caches the last observed value
+__device__ __forceinline__ bool wait_progress(const int64_t* flag, int64_t need, int64_t& seen, int64_t limit,
+                                              const int* err) {
+  int64_t it = 0;
+  while (seen < need) {
+    seen = ld_acquire(flag);
+    if (seen >= need) break;
+    if (++it > limit) return false;
+    if ((it & 255) == 0 && *(volatile const int*)err) return false;
+  }
+  return true;
+}
+
+// per-cell data of one sweep step
+template <class T, bool FWD>
+struct StepData {
+  T S[7][4];  // forward: all 7 blocks; backward: blocks 4..6 (upper) used
+  T D[4];
+  T a0, a1;   // forward: y_i ; backward: t_i
+  T zs[7], zp[7];  // forward: neighbour z (s, p); backward: own z in zs[3], zp[3]
+};
+
+template <class T, bool FWD>
+__device__ __forceinline__ void load_step(StepData<T, FWD>& d, int64_t i, int x, int yy, int zz, int nx, int ny,
+                                          int nz, const T* __restrict__ S28, const T* __restrict__ dinv,
+                                          const T* __restrict__ y, const T* __restrict__ t,
+                                          const T* __restrict__ zs, const T* __restrict__ zp) {
+  const int64_t nxy = int64_t(nx) * ny;
+  const T* Si = S28 + i * 28;
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d.S[q][e] = (FWD || q >= 4) ? Si[q * 4 + e] : T(0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) d.D[e] = dinv[i * 4 + e];
+  if (FWD) {
+    d.a0 = y[2 * i]; d.a1 = y[2 * i + 1];
+    const int64_t nb[7] = {zz > 0 ? i - nxy : i, yy > 0 ? i - nx : i, x > 0 ? i - 1 : i, i,
+                           x + 1 < nx ? i + 1 : i, yy + 1 < ny ? i + nx : i, zz + 1 < nz ? i + nxy : i};
+#pragma unroll
+    for (int q = 0; q < 7; ++q) { d.zs[q] = zs[nb[q]]; d.zp[q] = zp[nb[q]]; }
+  } else {
+    d.a0 = t[2 * i]; d.a1 = t[2 * i + 1];
+    d.zs[3] = zs[i]; d.zp[3] = zp[i];
+  }
+}
+
+template <class T, bool FWD>
+__global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
+    int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ dinv, const T* __restrict__ y,
+    const T* __restrict__ zs, const T* __restrict__ zp, T* t, T* dz, double* __restrict__ zout, int64_t* progress,
+    int* err, int64_t epoch, int64_t limit, int stall) {
+  __shared__ T buf[2][kTZ][kTY][2];
+  __shared__ int abort_flag;
+  const int nby = (ny + kTY - 1) / kTY;
+  const int BY = blockIdx.x % nby, BZ = blockIdx.x / nby;
+  // test hook: the CTA numbered stall - 1 never runs nor publishes progress
+  if (stall > 0 && int(blockIdx.x) == stall - 1) return;
+  const int ly = threadIdx.x % kTY, lz = threadIdx.x / kTY;
+  const int yy = BY * kTY + ly, zz = BZ * kTZ + lz;
+  const bool valid = yy < ny && zz < nz;
+  const int64_t nxy = int64_t(nx) * ny;
+  const int last = nx + kTY + kTZ - 3;
+  const int64_t base = epoch * kEpochStride;
+  const int ry = FWD ? ly : kTY - 1 - ly, rz = FWD ? lz : kTZ - 1 - lz;
+  // boundary roles: take the y (z) predecessor from the producer CTA
+  const bool hy = valid && (FWD ? yy > 0 : yy + 1 < ny), hz = valid && (FWD ? zz > 0 : zz + 1 < nz);
+  const bool gy = hy && ry == 0, gz = hz && rz == 0;
+  const int64_t* fy = progress + (int64_t(BZ) * nby + (FWD ? BY - 1 : BY + 1));
+  const int64_t* fz = progress + (int64_t(FWD ? BZ - 1 : BZ + 1) * nby + BY);
+  const T* src = FWD ? t : dz;
+  const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
+  int64_t seen_y = 0, seen_z = 0;
+  if (threadIdx.x == 0) abort_flag = 0;
+  __syncthreads();
+  auto cell_at = [&](int s, int* xo) -> int64_t {
+    int xs = s - ry - rz;
+    if (!valid || xs < 0 || xs >= nx) return -1;
+    int x = FWD ? xs : nx - 1 - xs;
+    *xo = x;
+    return x + int64_t(nx) * (yy + int64_t(ny) * zz);
+  };
+  // prefetch for step 0
+  StepData<T, FWD> cur;
+  int xc = 0;
+  int64_t ic = cell_at(0, &xc);
+  if (ic >= 0) load_step<T, FWD>(cur, ic, xc, yy, zz, nx, ny, nz, S28, dinv, y, t, zs, zp);
+  T by0 = T(0), by1 = T(0), bz0 = T(0), bz1 = T(0);  // boundary predecessors for the current step
+  bool ok = true;
+  if (ic >= 0 && gy) {
+    ok = ok && wait_progress(fy, base + min(0 + kTY - 1, last), seen_y, limit, err);
+    if (ok) { by0 = __ldcg(src + 2 * (ic + jy)); by1 = __ldcg(src + 2 * (ic + jy) + 1); }
+  }
+  if (ic >= 0 && gz) {
+    ok = ok && wait_progress(fz, base + min(0 + kTZ - 1, last), seen_z, limit, err);
+    if (ok) { bz0 = __ldcg(src + 2 * (ic + jz)); bz1 = __ldcg(src + 2 * (ic + jz) + 1); }
+  }
+  if (!ok) { abort_flag = 1; atomicExch(err, 1); }
+  T prev0 = T(0), prev1 = T(0);
+  for (int step = 0; step <= last; ++step) {
+    // compute the current cell
+    if (ic >= 0) {
+      T ny0 = by0, ny1 = by1, nz0 = bz0, nz1 = bz1;
+      if (hy && !gy) {
+        const T* b = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
+        ny0 = b[0]; ny1 = b[1];
+      }
+      if (hz && !gz) {
+        const T* b = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
+        nz0 = b[0]; nz1 = b[1];
+      }
+      T r0, r1;
+      if (FWD) {
+        // w_i = y_i - sum_j S_ij z_j ; u_i = w_i - sum_{k<i} S_ik t_k ; t_i = inv(U_ii) u_i
+        T w0 = cur.a0, w1 = cur.a1;
+        const T l0[3] = {nz0, ny0, xc > 0 ? prev0 : T(0)}, l1[3] = {nz1, ny1, xc > 0 ? prev1 : T(0)};
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          T a = cur.zs[q] + (q < 3 ? l0[q] : T(0)), b = cur.zp[q] + (q < 3 ? l1[q] : T(0));
+          w0 -= cur.S[q][0] * a + cur.S[q][1] * b;
+          w1 -= cur.S[q][2] * a + cur.S[q][3] * b;
+        }
+        r0 = cur.D[0] * w0 + cur.D[1] * w1;
+        r1 = cur.D[2] * w0 + cur.D[3] * w1;
+        t[2 * ic] = r0;
+        t[2 * ic + 1] = r1;
+      } else {
+        // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j ; z_f = (z_s, z_p) + dz
+        const T u0[3] = {xc + 1 < nx ? prev0 : T(0), ny0, nz0}, u1[3] = {xc + 1 < nx ? prev1 : T(0), ny1, nz1};
+        T a0 = T(0), a1 = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          a0 += cur.S[4 + q][0] * u0[q] + cur.S[4 + q][1] * u1[q];
+          a1 += cur.S[4 + q][2] * u0[q] + cur.S[4 + q][3] * u1[q];
+        }
+        r0 = cur.a0 - (cur.D[0] * a0 + cur.D[1] * a1);
+        r1 = cur.a1 - (cur.D[2] * a0 + cur.D[3] * a1);
+        dz[2 * ic] = r0;
+        dz[2 * ic + 1] = r1;
+        zout[2 * ic] = double(cur.zs[3] + r0);
+        zout[2 * ic + 1] = double(cur.zp[3] + r1);
+      }
+      prev0 = r0;
+      prev1 = r1;
+      buf[step & 1][lz][ly][0] = r0;
+      buf[step & 1][lz][ly][1] = r1;
+    }
+    // prefetch the next step: own cell data, then boundary predecessors once published
+    int xn = 0;
+    int64_t in = step < last ? cell_at(step + 1, &xn) : -1;
+    if (in >= 0) {
+      load_step<T, FWD>(cur, in, xn, yy, zz, nx, ny, nz, S28, dinv, y, t, zs, zp);
+      bool okn = true;
+      if (gy) {
+        okn = okn && wait_progress(fy, base + min(step + kTY, last), seen_y, limit, err);
+        if (okn) { by0 = __ldcg(src + 2 * (in + jy)); by1 = __ldcg(src + 2 * (in + jy) + 1); }
+      }
+      if (gz) {
+        okn = okn && wait_progress(fz, base + min(step + kTZ, last), seen_z, limit, err);
+        if (okn) { bz0 = __ldcg(src + 2 * (in + jz)); bz1 = __ldcg(src + 2 * (in + jz) + 1); }
+      }
+      if (!okn) { abort_flag = 1; atomicExch(err, 1); }
+    }
+    ic = in;
+    xc = xn;
+    __syncthreads();
+    if (abort_flag) return;
+    if (threadIdx.x == 0) st_release(progress + blockIdx.x, base + step);
+  }
+}
+
 }  // namespace
 
 template <class T>
@@ -150,8 +345,37 @@ void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaS
 }
 
 template <class T>
+bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStream_t st) {
+  FlowView<T> V = fview<T>(F);
+  if (!V.s28) return false;
+  int nby = (F.ny + kTY - 1) / kTY, nbz = (F.nz + kTZ - 1) / kTZ;
+  unsigned grid = unsigned(nby * nbz);
+  FlowStage& Fm = const_cast<FlowStage&>(F);
+  for (int dir = 0; dir < 2; ++dir) {
+    int64_t epoch = ++Fm.ilu_epoch;
+    int nx = F.nx, ny = F.ny, nz = F.nz;
+    const T *s28 = V.s28, *dinv = V.dinv, *y = W.y, *zs = W.zs, *zp = W.zp;
+    T *t = W.t, *dz = W.dz;
+    int64_t* prog = dir == 0 ? F.prog_fwd : F.prog_bwd;
+    int* err = F.ilu_err;
+    int64_t lim = F.spin_limit;
+    int stall = F.test_stall;
+    void* args[] = {&nx, &ny, &nz, &s28, &dinv, &y, &zs, &zp, &t, &dz, &zout, &prog, &err, &epoch, &lim, &stall};
+    cudaError_t e = dir == 0
+        ? cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, true>, grid, kTY * kTZ, args, 0, st)
+        : cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, false>, grid, kTY * kTZ, args, 0, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    PS_TICK();
+  }
+  return true;
+}
+
+template <class T>
 void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int ilu_mode, cudaStream_t st) {
-  (void)ilu_mode;
+  if (ilu_mode == PS_ILU_PENCIL && F.prog_fwd && ilu_pencil<T>(F, W, zout, st)) return;
   FlowView<T> V = fview<T>(F);
   for (int l = 0; l < F.nlev; ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];

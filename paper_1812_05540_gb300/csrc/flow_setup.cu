@@ -107,6 +107,22 @@ __global__ void k_ilu_factor(const int32_t* __restrict__ cells, int32_t ncell_le
   inv22(D, &dinv[int64_t(i) * 4]);
 }
 
+// S_ff^(FS) by stencil slot (the row of a 7-point pattern is z-1, y-1, x-1, self, x+1, y+1, z+1 with
+// the missing neighbours left out), 28 entries per cell
+__global__ void k_s28(int nx, int ny, int nz, const int32_t* __restrict__ rp, const double* __restrict__ sff,
+                      double* __restrict__ out) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (c >= nc) return;
+  int i = int(c % nx), j = int((c / nx) % ny), k = int(c / (int64_t(nx) * ny));
+  const bool have[7] = {k > 0, j > 0, i > 0, true, i + 1 < nx, j + 1 < ny, k + 1 < nz};
+  int32_t q = rp[c];
+  for (int s = 0; s < 7; ++s) {
+    for (int e = 0; e < 4; ++e) out[c * 28 + s * 4 + e] = have[s] ? sff[int64_t(q) * 4 + e] : 0.0;
+    if (have[s]) ++q;
+  }
+}
+
 __global__ void k_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = float(a[t]);
@@ -139,7 +155,9 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(ar.alloc(&F.dps, nc));
     PS_TRY(ar.alloc(&F.dinv, nc * 4));
     PS_TRY(ar.alloc(&F.diagpos, nc));
+    PS_TRY(ar.alloc(&F.s28, nc * 28));
     if (mixed) {
+      PS_TRY(ar.alloc(&F.s28_f, nc * 28));
       PS_TRY(ar.alloc(&F.sff_f, nnzb * 4));
       PS_TRY(ar.alloc(&F.aps_f, nnzb));
       PS_TRY(ar.alloc(&F.dinv_f, nc * 4));
@@ -157,6 +175,13 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
     PS_TICK(); k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
+    int nb = ((F.ny + 15) / 16) * ((F.nz + 7) / 8);
+    PS_TRY(ar.alloc(&F.prog_fwd, nb + 1));
+    PS_TRY(ar.alloc(&F.prog_bwd, nb + 1));
+    PS_TRY(ar.alloc(&F.ilu_err, 4));
+    PS_CUDA(cudaMemsetAsync(F.prog_fwd, 0, sizeof(int64_t) * (nb + 1), st));
+    PS_CUDA(cudaMemsetAsync(F.prog_bwd, 0, sizeof(int64_t) * (nb + 1), st));
+    PS_CUDA(cudaMemsetAsync(F.ilu_err, 0, 4 * sizeof(int), st));
     F.lev_off.resize(F.nlev + 1);
     PS_CUDA(cudaMemcpyAsync(F.lev_off.data(), off, sizeof(int32_t) * (F.nlev + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
@@ -169,8 +194,10 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
                                                    F.dinv);
   }
+  PS_TICK(); k_s28<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.rp, F.sff, F.s28);
   PS_CUDA(cudaGetLastError());
   if (mixed) {
+    PS_TICK(); k_f32<<<grid_for(nc * 28, 256), 256, 0, st>>>(F.s28, F.s28_f, nc * 28);
     PS_TICK(); k_f32<<<grid_for(nnzb * 4, 256), 256, 0, st>>>(F.sff, F.sff_f, nnzb * 4);
     PS_TICK(); k_f32<<<grid_for(nnzb, 256), 256, 0, st>>>(F.aps, F.aps_f, nnzb);
     PS_TICK(); k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);

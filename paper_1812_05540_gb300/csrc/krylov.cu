@@ -130,6 +130,159 @@ __global__ void __launch_bounds__(256) k_spmv_f(JacDev J, const double* __restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stencil-indexed Jacobian.  Slots: A_uu 27 node neighbours (dk, dj, di) in
+// {-1,0,1}^3 ascending, A_uf 8 cells (dk, dj, di) in {-1,0}^3, A_fu 8 nodes in
+// {0,1}^3, A_ff 7 cells (z-1, y-1, x-1, self, x+1, y+1, z+1).  Missing
+// neighbours are zero blocks, so the sweep needs neither row pointers nor
+// column indices and every coefficient load is coalesced across rows.
+// ---------------------------------------------------------------------------
+struct Geo {
+  int nx, ny, nz;
+  __device__ __forceinline__ int64_t node(int i, int j, int k) const { return i + int64_t(nx + 1) * (j + int64_t(ny + 1) * k); }
+  __device__ __forceinline__ int64_t cell(int i, int j, int k) const { return i + int64_t(nx) * (j + int64_t(ny) * k); }
+};
+
+// neighbour of slot s in each family, or -1 when outside the grid
+__device__ __forceinline__ int64_t uu_nb(const Geo& g, int i, int j, int k, int s) {
+  int a = i + s % 3 - 1, b = j + (s / 3) % 3 - 1, c = k + s / 9 - 1;
+  if (a < 0 || b < 0 || c < 0 || a > g.nx || b > g.ny || c > g.nz) return -1;
+  return g.node(a, b, c);
+}
+__device__ __forceinline__ int64_t uf_nb(const Geo& g, int i, int j, int k, int s) {
+  int a = i + (s & 1) - 1, b = j + ((s >> 1) & 1) - 1, c = k + (s >> 2) - 1;
+  if (a < 0 || b < 0 || c < 0 || a >= g.nx || b >= g.ny || c >= g.nz) return -1;
+  return g.cell(a, b, c);
+}
+__device__ __forceinline__ int64_t fu_nb(const Geo& g, int i, int j, int k, int s) {
+  return g.node(i + (s & 1), j + ((s >> 1) & 1), k + (s >> 2));
+}
+__device__ __forceinline__ int64_t ff_nb(const Geo& g, int i, int j, int k, int s) {
+  const int di[7] = {0, 0, -1, 0, 1, 0, 0}, dj[7] = {0, -1, 0, 0, 0, 1, 0}, dk[7] = {-1, 0, 0, 0, 0, 0, 1};
+  int a = i + di[s], b = j + dj[s], c = k + dk[s];
+  if (a < 0 || b < 0 || c < 0 || a >= g.nx || b >= g.ny || c >= g.nz) return -1;
+  return g.cell(a, b, c);
+}
+
+// scatter one BSR family into its stencil arrays; flags rows whose pattern is not the stencil
+template <int FAM, int NS, int BS>
+__global__ void k_to_stencil(Geo g, int64_t nrows, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, double* __restrict__ out, int* __restrict__ bad) {
+  int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int i, j, k;
+  if (FAM <= 1) { i = int(r % (g.nx + 1)); j = int((r / (g.nx + 1)) % (g.ny + 1)); k = int(r / (int64_t(g.nx + 1) * (g.ny + 1))); }
+  else { i = int(r % g.nx); j = int((r / g.nx) % g.ny); k = int(r / (int64_t(g.nx) * g.ny)); }
+  int32_t q = rp[r], q1 = rp[r + 1];
+  for (int s = 0; s < NS; ++s) {
+    int64_t nb = FAM == 0 ? uu_nb(g, i, j, k, s) : FAM == 1 ? uf_nb(g, i, j, k, s) : FAM == 2 ? fu_nb(g, i, j, k, s)
+                                                                                          : ff_nb(g, i, j, k, s);
+    bool have = nb >= 0 && q < q1 && ci[q] == nb;
+    if (nb >= 0 && !have) atomicExch(bad, 1);
+    for (int e = 0; e < BS; ++e) out[(int64_t(s) * BS + e) * nrows + r] = have ? v[int64_t(q) * BS + e] : 0.0;
+    if (have) ++q;
+  }
+  if (q != q1) atomicExch(bad, 1);
+}
+
+__device__ __forceinline__ int64_t clampnb(int64_t nb, int64_t self) { return nb >= 0 ? nb : self; }
+
+// displacement rows, one thread per node
+__global__ void __launch_bounds__(256) k_spmv_u_st(JacDev J, const double* __restrict__ x, double* __restrict__ y,
+                                                   const double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[8];
+  Geo g{J.nx, J.ny, J.nz};
+  int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (I < J.nn) {
+    int i = int(I % (g.nx + 1)), j = int((I / (g.nx + 1)) % (g.ny + 1)), k = int(I / (int64_t(g.nx + 1) * (g.ny + 1)));
+    const int64_t n = J.nn;
+    const double* xf = x + 3 * n;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 3
+    for (int s = 0; s < 27; ++s) {
+      int64_t c = clampnb(uu_nb(g, i, j, k, s), I);
+      const double* A = J.uu_s + int64_t(s) * 9 * n + I;
+      double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+      a0 += __ldg(A) * x0 + __ldg(A + n) * x1 + __ldg(A + 2 * n) * x2;
+      a1 += __ldg(A + 3 * n) * x0 + __ldg(A + 4 * n) * x1 + __ldg(A + 5 * n) * x2;
+      a2 += __ldg(A + 6 * n) * x0 + __ldg(A + 7 * n) * x1 + __ldg(A + 8 * n) * x2;
+    }
+#pragma unroll 4
+    for (int s = 0; s < 8; ++s) {
+      int64_t c = uf_nb(g, i, j, k, s);
+      c = c >= 0 ? c : 0;
+      const double* A = J.uf_s + int64_t(s) * 6 * n + I;
+      double f0 = xf[2 * c], f1 = xf[2 * c + 1];
+      a0 += __ldg(A) * f0 + __ldg(A + n) * f1;
+      a1 += __ldg(A + 2 * n) * f0 + __ldg(A + 3 * n) * f1;
+      a2 += __ldg(A + 4 * n) * f0 + __ldg(A + 5 * n) * f1;
+    }
+    if (b) {
+      a0 = b[3 * I] - a0; a1 = b[3 * I + 1] - a1; a2 = b[3 * I + 2] - a2;
+      r2 = a0 * a0 + a1 * a1 + a2 * a2;
+    }
+    y[3 * I] = a0; y[3 * I + 1] = a1; y[3 * I + 2] = a2;
+  }
+  if (part) {
+    r2 = warp_sum(r2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s2 = 0.0;
+      for (int w = 0; w < 8; ++w) s2 += red[w];
+      part[blockIdx.x] = s2;
+    }
+  }
+}
+
+// flow rows, one thread per cell
+__global__ void __launch_bounds__(256) k_spmv_f_st(JacDev J, const double* __restrict__ x, double* __restrict__ y,
+                                                   const double* __restrict__ b, double* __restrict__ part) {
+  __shared__ double red[8];
+  Geo g{J.nx, J.ny, J.nz};
+  int64_t C = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double r2 = 0.0;
+  if (C < J.nc) {
+    int i = int(C % g.nx), j = int((C / g.nx) % g.ny), k = int(C / (int64_t(g.nx) * g.ny));
+    const int64_t n = J.nc;
+    const double* xf = x + 3 * J.nn;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+    for (int s = 0; s < 8; ++s) {
+      int64_t c = fu_nb(g, i, j, k, s);
+      const double* A = J.fu_s + int64_t(s) * 6 * n + C;
+      double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
+      a0 += __ldg(A) * x0 + __ldg(A + n) * x1 + __ldg(A + 2 * n) * x2;
+      a1 += __ldg(A + 3 * n) * x0 + __ldg(A + 4 * n) * x1 + __ldg(A + 5 * n) * x2;
+    }
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      int64_t c = clampnb(ff_nb(g, i, j, k, s), C);
+      const double* A = J.ff_s + int64_t(s) * 4 * n + C;
+      double f0 = xf[2 * c], f1 = xf[2 * c + 1];
+      a0 += __ldg(A) * f0 + __ldg(A + n) * f1;
+      a1 += __ldg(A + 2 * n) * f0 + __ldg(A + 3 * n) * f1;
+    }
+    int64_t o = 3 * J.nn + 2 * C;
+    if (b) {
+      a0 = b[o] - a0; a1 = b[o + 1] - a1;
+      r2 = a0 * a0 + a1 * a1;
+    }
+    y[o] = a0; y[o + 1] = a1;
+  }
+  if (part) {
+    r2 = warp_sum(r2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s2 = 0.0;
+      for (int w = 0; w < 8; ++w) s2 += red[w];
+      part[blockIdx.x] = s2;
+    }
+  }
+}
+
 // fold per-block partials into kRedBlocks slots (fixed mapping)
 __global__ void k_fold(const double* __restrict__ in, int64_t nin, double* __restrict__ out) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -213,7 +366,8 @@ __global__ void __launch_bounds__(256) k_mupdate(const double* __restrict__ V, i
   double r2 = 0.0;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     double s = w[e];
-    for (int c = 0; c < m; ++c) s -= V[int64_t(c) * ldv + e] * hs[c];
+#pragma unroll 8
+    for (int c = 0; c < m; ++c) s -= __ldg(V + int64_t(c) * ldv + e) * hs[c];
     w[e] = s;
     r2 += s * s;
   }
@@ -302,7 +456,42 @@ constexpr int kVecBlocks = 1216;  // 8 x 152 SMs
 
 }  // namespace
 
+ps_status jac_build_stencil(Arena& ar, JacDev& J, bool* ok, cudaStream_t st) {
+  Geo g{J.nx, J.ny, J.nz};
+  int* bad;
+  PS_TRY(ar.alloc(&bad, 1));
+  PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  PS_TRY(ar.alloc(&J.uu_s, size_t(27) * 9 * J.nn));
+  PS_TRY(ar.alloc(&J.uf_s, size_t(8) * 6 * J.nn));
+  PS_TRY(ar.alloc(&J.fu_s, size_t(8) * 6 * J.nc));
+  PS_TRY(ar.alloc(&J.ff_s, size_t(7) * 4 * J.nc));
+  PS_TICK(); k_to_stencil<0, 27, 9><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uu_rp, J.uu_ci, J.uu_v, J.uu_s, bad);
+  PS_TICK(); k_to_stencil<1, 8, 6><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uf_rp, J.uf_ci, J.uf_v, J.uf_s, bad);
+  PS_TICK(); k_to_stencil<2, 8, 6><<<grid_for(J.nc, 256), 256, 0, st>>>(g, J.nc, J.fu_rp, J.fu_ci, J.fu_v, J.fu_s, bad);
+  PS_TICK(); k_to_stencil<3, 7, 4><<<grid_for(J.nc, 256), 256, 0, st>>>(g, J.nc, J.ff_rp, J.ff_ci, J.ff_v, J.ff_s, bad);
+  PS_CUDA(cudaGetLastError());
+  int h = 0;
+  PS_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  ar.release(bad);
+  *ok = h == 0;
+  if (!*ok) {
+    ar.release(J.uu_s); ar.release(J.uf_s); ar.release(J.fu_s); ar.release(J.ff_s);
+    J.uu_s = J.uf_s = J.fu_s = J.ff_s = nullptr;
+  }
+  return PS_OK;
+}
+
 void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, double* part, cudaStream_t st) {
+  if (J.uu_s) {
+    int64_t gu = ceil_div(J.nn, 256), gf = ceil_div(J.nc, 256);
+    double* pu = part ? part + kRedBlocks : nullptr;
+    double* pf = part ? part + kRedBlocks + gu : nullptr;
+    PS_TICK(); k_spmv_u_st<<<unsigned(gu), 256, 0, st>>>(J, x, y, b, pu);
+    PS_TICK(); k_spmv_f_st<<<unsigned(gf), 256, 0, st>>>(J, x, y, b, pf);
+    if (part) { PS_TICK(); k_fold<<<grid_for(kRedBlocks, 256), 256, 0, st>>>(part + kRedBlocks, gu + gf, part); }
+    return;
+  }
   int64_t gu = ceil_div(J.nn * 32, 256), gf = ceil_div(J.nc * 32, 256);
   // partial sums: u blocks first, then f blocks, folded into kRedBlocks slots
   double* pu = part ? part + kRedBlocks : nullptr;

@@ -8,6 +8,11 @@ namespace ps_internal {
 
 struct JacDev {
   int64_t nn = 0, nc = 0;
+  int nx = 0, ny = 0, nz = 0;
+  // stencil-indexed copies of the four blocks, zero padded at the boundary,
+  // structure-of-arrays: [slot][entry][row] (null when a pattern is not the
+  // structured one; the CSR kernels are used then)
+  double *uu_s = nullptr, *uf_s = nullptr, *fu_s = nullptr, *ff_s = nullptr;
   int32_t *uu_rp = nullptr, *uu_ci = nullptr, *uf_rp = nullptr, *uf_ci = nullptr;
   int32_t *fu_rp = nullptr, *fu_ci = nullptr, *ff_rp = nullptr, *ff_ci = nullptr;
   const double *uu_v = nullptr, *uf_v = nullptr, *fu_v = nullptr, *ff_v = nullptr;
@@ -17,6 +22,8 @@ struct JacDev {
 // partial sums of r^2 into part[0..kRedBlocks)
 constexpr int kRedBlocks = 1024;
 void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, double* part, cudaStream_t st);
+// build the stencil-indexed copies; returns false (and leaves them null) if a pattern is not structured
+ps_status jac_build_stencil(Arena& ar, JacDev& J, bool* ok, cudaStream_t st);
 
 // h[c] = V[:,c] . w for c < m (V column-major, leading dimension ldv); also
 // ||w||^2 into h[m] when with_norm.  Partials in part (m+1 x kRedBlocks), result in h.

@@ -120,14 +120,15 @@ def test_hierarchy_parity(cfg, kw, cm):
         ps.ps_free(h)
 
 
+@pytest.mark.parametrize("ilu", [ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH])
 @pytest.mark.parametrize("cm", [16, 500])
-def test_apply_parity_fp64(cm):
+def test_apply_parity_fp64(cm, ilu):
     # Algorithm 1 in FP64 against the oracle's Algorithm 1 on the same vector
     g = _gpu()
     osys = oracle.System(oracle.default_params(0))
     P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
     dev = g.to_device(osys)
-    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm))
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm, ilu_mode=ilu))
     try:
         for seed in range(3):
             vs = np.random.default_rng(seed).standard_normal(osys.n)
@@ -146,7 +147,8 @@ SOLVE_CASES = [(0, {}, 16), (0, {}, 500), (1, dict(nx=24, ny=20, nz=10), 60), (2
 
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
 @pytest.mark.parametrize("cfg,kw,cm", SOLVE_CASES)
-def test_solve_parity(cfg, kw, cm, prec):
+@pytest.mark.parametrize("ilu", [ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH])
+def test_solve_parity(cfg, kw, cm, prec, ilu):
     # true FP64 relres <= 1e-8 (recomputed by the oracle), solution within 1e-6 of the oracle
     # solved to 1e-12, iterations within 10% (+1) of the oracle's FGMRES at 1e-8
     g = _gpu()
@@ -155,7 +157,8 @@ def test_solve_parity(cfg, kw, cm, prec):
     xo, sto = P.fgmres(tol=1e-12)
     _, sto8 = P.fgmres(tol=1e-8)
     dev = g.to_device(osys)
-    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=cm, coarse_max_p=cm))
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=cm, coarse_max_p=cm,
+                                                             ilu_mode=ilu))
     try:
         x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
         _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
@@ -167,3 +170,23 @@ def test_solve_parity(cfg, kw, cm, prec):
     assert abs(st.true_relres - relres) <= 1e-10
     assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
     assert abs(st.iters - sto8.iters) <= max(1, int(0.1 * sto8.iters) + 1), (st.iters, sto8.iters)
+
+
+@pytest.mark.parametrize("prec,rtol", [(ps.PS_FP64, 1e-12), (ps.PS_MIXED_FP32, 2e-5)])
+def test_pencil_wavefront_matches_level_launch(prec, rtol):
+    # the sync-free pencil sweep (several CTAs along y and z) and the level-by-level sweep apply the
+    # same ILU(0) factors: Algorithm 1 outputs agree to rounding
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(1, nx=12, ny=40, nz=20))
+    dev = g.to_device(osys)
+    out = []
+    for ilu in (ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH):
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, ilu_mode=ilu))
+        try:
+            v = torch.from_numpy(np.random.default_rng(7).standard_normal(osys.n)).cuda()
+            z = torch.empty_like(v)
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            out.append(z.cpu().numpy())
+        finally:
+            ps.ps_free(h)
+    assert np.linalg.norm(out[0] - out[1]) <= rtol * np.linalg.norm(out[1])
