@@ -368,7 +368,10 @@ def run_ours(args):
                  "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_64],
                  "solve_ms": [round(st.ms_solve, 2) for st in st_64],
                  "solve_phases_ms": {"precond": round(st_64[-1].ms_prec, 1), "spmv": round(st_64[-1].ms_spmv, 1),
-                                     "gram_schmidt": round(st_64[-1].ms_orth, 1)}},
+                                     "gram_schmidt": round(st_64[-1].ms_orth, 1),
+                                     "vcycle_u": round(st_64[-1].ms_vcycle_u, 1),
+                                     "flow_2_4": round(st_64[-1].ms_flow24, 1),
+                                     "vcycle_p": round(st_64[-1].ms_vcycle_p, 1), "ilu": round(st_64[-1].ms_ilu, 1)}},
         "mixed_speedup_vs_fp64": per_64 / per_mx,
         "true_relres_mixed": relres, "gen_s": gen_s,
         "roofline": {"kernel": "FP64 Jacobian SpMV (k_spmv_u + k_spmv_f)", "bound": "hbm",

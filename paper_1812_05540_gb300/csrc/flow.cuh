@@ -25,8 +25,8 @@ struct FlowStage {
   // row-major each), zero blocks outside the grid
   double* s28 = nullptr;
   float* s28_f = nullptr;
-  // sync-free wavefront sweeps: per-CTA progress counters (epoch-stamped) and error flag
-  int64_t *prog_fwd = nullptr, *prog_bwd = nullptr;
+  // sync-free wavefront sweeps: tagged halo words (4 per cell) and error flag
+  uint64_t* halo = nullptr;
   int* ilu_err = nullptr;
   int64_t ilu_epoch = 0;
   int64_t spin_limit = 2000000;
@@ -48,7 +48,7 @@ ps_status flow_check_pattern(Arena& ar, const ps_grid& g, const int32_t* ff_rp, 
 // called by the driver).  v_f, y, z_s, w_p, t, dz are per-cell work vectors.
 template <class T>
 struct FlowWork {
-  T *vf, *y, *zs, *wp, *zp, *t, *dz;
+  T *vf, *y, *zs, *wp, *zp, *t, *dz, *wf;
 };
 template <class T>
 ps_status flow_alloc_work(Arena& ar, const FlowStage& F, FlowWork<T>& W);

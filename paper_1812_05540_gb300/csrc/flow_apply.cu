@@ -137,192 +137,243 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
 // BZ*kTZ + lz) and walks it sequentially: at CTA step s it handles position
 // s - ry - rz (ry, rz = distance from the producing CTA boundary), so its y- and
 // z-predecessors inside the CTA were computed at step s - 1 (double-buffered
-// shared array).  Everything that does not depend on the wavefront is loaded
-// one step ahead.  Boundary pencils take their predecessors from global memory:
-// before prefetching the value for step s + 1 each polls its producer CTA's
-// progress with an acquire load (bounded; on timeout it raises *err); each CTA
-// publishes its progress with a release store after the step's barrier.
+// shared array, one barrier per step).  Values crossing a CTA boundary go
+// through a halo buffer of 64-bit words that each carry a 32-bit payload and the
+// 32-bit sweep tag (single-copy atomic stores, so no fence or flag is needed):
+// consumers prefetch the words they need two steps ahead and re-read them only
+// while the tag is not yet the current one; the wait is bounded and raises *err.
+// Everything that does not depend on the wavefront is prefetched three steps
+// ahead.
 // ---------------------------------------------------------------------------
 constexpr int kTY = 16, kTZ = 8;
-constexpr int64_t kEpochStride = 1 << 20;  // > steps per sweep
 
-__device__ __forceinline__ int64_t ld_acquire(const int64_t* p) {
-  int64_t v;
-  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+template <class T>
+struct HaloWord {
+  static constexpr int W = int(sizeof(T)) * 2 / 4;  // 32-bit chunks of a (v0, v1) pair
+};
+
+__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(int64_t* p, int64_t v) {
-  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+
+template <class T>
+__device__ __forceinline__ void halo_put(uint64_t* h, int64_t i, T v0, T v1, uint32_t tag) {
+  constexpr int W = HaloWord<T>::W;
+  uint32_t c[W];
+  if constexpr (sizeof(T) == 4) {
+    c[0] = __float_as_uint(v0);
+    c[1] = __float_as_uint(v1);
+  } else {
+    uint64_t a = __double_as_longlong(v0), b = __double_as_longlong(v1);
+    c[0] = uint32_t(a); c[1] = uint32_t(a >> 32); c[2] = uint32_t(b); c[3] = uint32_t(b >> 32);
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) st_relaxed64(h + i * W + k, (uint64_t(tag) << 32) | c[k]);
 }
 
-// bounded wait until *flag >= need; `seen` caches the last observed value
-__device__ __forceinline__ bool wait_progress(const int64_t* flag, int64_t need, int64_t& seen, int64_t limit,
-                                              const int* err) {
+template <class T>
+struct HaloVal {
+  uint64_t w[HaloWord<T>::W];
+};
+template <class T>
+__device__ __forceinline__ void halo_fetch(const uint64_t* h, int64_t i, HaloVal<T>& v) {
+#pragma unroll
+  for (int k = 0; k < HaloWord<T>::W; ++k) v.w[k] = ld_relaxed64(h + i * HaloWord<T>::W + k);
+}
+template <class T>
+__device__ __forceinline__ bool halo_ready(const HaloVal<T>& v, uint32_t tag) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < HaloWord<T>::W; ++k) ok = ok && uint32_t(v.w[k] >> 32) == tag;
+  return ok;
+}
+template <class T>
+__device__ __forceinline__ void halo_decode(const HaloVal<T>& v, T& v0, T& v1) {
+  if constexpr (sizeof(T) == 4) {
+    v0 = __uint_as_float(uint32_t(v.w[0]));
+    v1 = __uint_as_float(uint32_t(v.w[1]));
+  } else {
+    v0 = __longlong_as_double(int64_t(uint32_t(v.w[0]) | (uint64_t(uint32_t(v.w[1])) << 32)));
+    v1 = __longlong_as_double(int64_t(uint32_t(v.w[2]) | (uint64_t(uint32_t(v.w[3])) << 32)));
+  }
+}
+// bounded re-read until the word carries the current tag
+template <class T>
+__device__ __forceinline__ bool halo_wait(const uint64_t* h, int64_t i, uint32_t tag, HaloVal<T>& v, int64_t limit,
+                                          const int* err) {
   int64_t it = 0;
-  while (seen < need) {
-    seen = ld_acquire(flag);
-    if (seen >= need) break;
+  while (!halo_ready<T>(v, tag)) {
     if (++it > limit) return false;
     if ((it & 255) == 0 && *(volatile const int*)err) return false;
+    halo_fetch<T>(h, i, v);
   }
   return true;
 }
 
-// per-cell data of one sweep step
-template <class T, bool FWD>
-struct StepData {
-  T S[7][4];  // forward: all 7 blocks; backward: blocks 4..6 (upper) used
+// step 6 of Algorithm 1 as a stencil sweep: w_i = y_i - sum_j S_ij z_j (fully parallel)
+template <class T>
+__global__ void k_ff_residual(int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ y,
+                              const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ w) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (i >= nc) return;
+  int x = int(i % nx), yy = int((i / nx) % ny), zz = int(i / (int64_t(nx) * ny));
+  const int64_t nxy = int64_t(nx) * ny;
+  const int64_t nb[7] = {zz > 0 ? i - nxy : i, yy > 0 ? i - nx : i, x > 0 ? i - 1 : i, i,
+                         x + 1 < nx ? i + 1 : i, yy + 1 < ny ? i + nx : i, zz + 1 < nz ? i + nxy : i};
+  const T* S = S28 + i * 28;
+  T w0 = y[2 * i], w1 = y[2 * i + 1];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    T a = zs[nb[q]], b = zp[nb[q]];
+    w0 -= S[q * 4] * a + S[q * 4 + 1] * b;
+    w1 -= S[q * 4 + 2] * a + S[q * 4 + 3] * b;
+  }
+  w[2 * i] = w0;
+  w[2 * i + 1] = w1;
+}
+
+// per-cell data of one sweep step: forward (w_i, lower blocks, inv(U_ii)),
+// backward (t_i, upper blocks, inv(U_ii), z_i)
+template <class T>
+struct Cell {
+  T a0, a1;
+  T S[3][4];
   T D[4];
-  T a0, a1;   // forward: y_i ; backward: t_i
-  T zs[7], zp[7];  // forward: neighbour z (s, p); backward: own z in zs[3], zp[3]
+  T z0, z1;
 };
 
 template <class T, bool FWD>
-__device__ __forceinline__ void load_step(StepData<T, FWD>& d, int64_t i, int x, int yy, int zz, int nx, int ny,
-                                          int nz, const T* __restrict__ S28, const T* __restrict__ dinv,
-                                          const T* __restrict__ y, const T* __restrict__ t,
+__device__ __forceinline__ void load_cell(Cell<T>& d, int64_t i, const T* __restrict__ S28,
+                                          const T* __restrict__ dinv, const T* __restrict__ a,
                                           const T* __restrict__ zs, const T* __restrict__ zp) {
-  const int64_t nxy = int64_t(nx) * ny;
-  const T* Si = S28 + i * 28;
+  if (i < 0) return;
+  const T* Si = S28 + i * 28 + (FWD ? 0 : 16);
 #pragma unroll
-  for (int q = 0; q < 7; ++q)
+  for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) d.S[q][e] = (FWD || q >= 4) ? Si[q * 4 + e] : T(0);
+    for (int e = 0; e < 4; ++e) d.S[q][e] = Si[q * 4 + e];
 #pragma unroll
   for (int e = 0; e < 4; ++e) d.D[e] = dinv[i * 4 + e];
-  if (FWD) {
-    d.a0 = y[2 * i]; d.a1 = y[2 * i + 1];
-    const int64_t nb[7] = {zz > 0 ? i - nxy : i, yy > 0 ? i - nx : i, x > 0 ? i - 1 : i, i,
-                           x + 1 < nx ? i + 1 : i, yy + 1 < ny ? i + nx : i, zz + 1 < nz ? i + nxy : i};
-#pragma unroll
-    for (int q = 0; q < 7; ++q) { d.zs[q] = zs[nb[q]]; d.zp[q] = zp[nb[q]]; }
-  } else {
-    d.a0 = t[2 * i]; d.a1 = t[2 * i + 1];
-    d.zs[3] = zs[i]; d.zp[3] = zp[i];
+  d.a0 = a[2 * i];
+  d.a1 = a[2 * i + 1];
+  if (!FWD) {
+    d.z0 = zs[i];
+    d.z1 = zp[i];
   }
 }
 
 template <class T, bool FWD>
 __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
-    int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ dinv, const T* __restrict__ y,
-    const T* __restrict__ zs, const T* __restrict__ zp, T* t, T* dz, double* __restrict__ zout, int64_t* progress,
-    int* err, int64_t epoch, int64_t limit, int stall) {
+    int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ dinv, const T* __restrict__ w,
+    const T* __restrict__ zs, const T* __restrict__ zp, T* t, T* dz, double* __restrict__ zout, uint64_t* halo,
+    int* err, uint32_t tag, int64_t limit, int stall) {
   __shared__ T buf[2][kTZ][kTY][2];
   __shared__ int abort_flag;
   const int nby = (ny + kTY - 1) / kTY;
   const int BY = blockIdx.x % nby, BZ = blockIdx.x / nby;
-  // test hook: the CTA numbered stall - 1 never runs nor publishes progress
+  // test hook: the CTA numbered stall - 1 never runs, so its halo words never get the current tag
   if (stall > 0 && int(blockIdx.x) == stall - 1) return;
   const int ly = threadIdx.x % kTY, lz = threadIdx.x / kTY;
   const int yy = BY * kTY + ly, zz = BZ * kTZ + lz;
   const bool valid = yy < ny && zz < nz;
-  const int64_t nxy = int64_t(nx) * ny;
   const int last = nx + kTY + kTZ - 3;
-  const int64_t base = epoch * kEpochStride;
+  const int64_t nxy = int64_t(nx) * ny;
   const int ry = FWD ? ly : kTY - 1 - ly, rz = FWD ? lz : kTZ - 1 - lz;
-  // boundary roles: take the y (z) predecessor from the producer CTA
   const bool hy = valid && (FWD ? yy > 0 : yy + 1 < ny), hz = valid && (FWD ? zz > 0 : zz + 1 < nz);
-  const bool gy = hy && ry == 0, gz = hz && rz == 0;
-  const int64_t* fy = progress + (int64_t(BZ) * nby + (FWD ? BY - 1 : BY + 1));
-  const int64_t* fz = progress + (int64_t(FWD ? BZ - 1 : BZ + 1) * nby + BY);
-  const T* src = FWD ? t : dz;
+  const bool gy = hy && ry == 0, gz = hz && rz == 0;  // predecessor lives in another CTA
+  // this pencil feeds another CTA along y (z) when it sits on the far boundary
+  const bool py = valid && ry == kTY - 1 && (FWD ? yy + 1 < ny : yy > 0);
+  const bool pz = valid && rz == kTZ - 1 && (FWD ? zz + 1 < nz : zz > 0);
+  const T* a = FWD ? w : t;
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
-  int64_t seen_y = 0, seen_z = 0;
   if (threadIdx.x == 0) abort_flag = 0;
   __syncthreads();
-  auto cell_at = [&](int s, int* xo) -> int64_t {
+  auto cell_at = [&](int s) -> int64_t {
     int xs = s - ry - rz;
-    if (!valid || xs < 0 || xs >= nx) return -1;
+    if (!valid || s > last || xs < 0 || xs >= nx) return -1;
     int x = FWD ? xs : nx - 1 - xs;
-    *xo = x;
     return x + int64_t(nx) * (yy + int64_t(ny) * zz);
   };
-  // prefetch for step 0
-  StepData<T, FWD> cur;
-  int xc = 0;
-  int64_t ic = cell_at(0, &xc);
-  if (ic >= 0) load_step<T, FWD>(cur, ic, xc, yy, zz, nx, ny, nz, S28, dinv, y, t, zs, zp);
-  T by0 = T(0), by1 = T(0), bz0 = T(0), bz1 = T(0);  // boundary predecessors for the current step
-  bool ok = true;
-  if (ic >= 0 && gy) {
-    ok = ok && wait_progress(fy, base + min(0 + kTY - 1, last), seen_y, limit, err);
-    if (ok) { by0 = __ldcg(src + 2 * (ic + jy)); by1 = __ldcg(src + 2 * (ic + jy) + 1); }
-  }
-  if (ic >= 0 && gz) {
-    ok = ok && wait_progress(fz, base + min(0 + kTZ - 1, last), seen_z, limit, err);
-    if (ok) { bz0 = __ldcg(src + 2 * (ic + jz)); bz1 = __ldcg(src + 2 * (ic + jz) + 1); }
-  }
-  if (!ok) { abort_flag = 1; atomicExch(err, 1); }
+  Cell<T> c0, c1, c2;
+  int64_t i0 = cell_at(0), i1 = cell_at(1), i2 = cell_at(2);
+  load_cell<T, FWD>(c0, i0, S28, dinv, a, zs, zp);
+  load_cell<T, FWD>(c1, i1, S28, dinv, a, zs, zp);
+  load_cell<T, FWD>(c2, i2, S28, dinv, a, zs, zp);
+  // halo words for the current and the next step
+  HaloVal<T> hy0, hz0, hy1, hz1;
+  if (gy && i0 >= 0) halo_fetch<T>(halo, i0 + jy, hy0);
+  if (gz && i0 >= 0) halo_fetch<T>(halo, i0 + jz, hz0);
+  if (gy && i1 >= 0) halo_fetch<T>(halo, i1 + jy, hy1);
+  if (gz && i1 >= 0) halo_fetch<T>(halo, i1 + jz, hz1);
   T prev0 = T(0), prev1 = T(0);
   for (int step = 0; step <= last; ++step) {
-    // compute the current cell
-    if (ic >= 0) {
-      T ny0 = by0, ny1 = by1, nz0 = bz0, nz1 = bz1;
-      if (hy && !gy) {
-        const T* b = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
-        ny0 = b[0]; ny1 = b[1];
+    if (i0 >= 0) {
+      int xs = step - ry - rz;
+      int x = FWD ? xs : nx - 1 - xs;
+      T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
+      bool ok = true;
+      if (gy) {
+        ok = ok && halo_wait<T>(halo, i0 + jy, tag, hy0, limit, err);
+        halo_decode<T>(hy0, ny0, ny1);
+      } else if (hy) {
+        const T* q = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
+        ny0 = q[0]; ny1 = q[1];
       }
-      if (hz && !gz) {
-        const T* b = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
-        nz0 = b[0]; nz1 = b[1];
+      if (gz) {
+        ok = ok && halo_wait<T>(halo, i0 + jz, tag, hz0, limit, err);
+        halo_decode<T>(hz0, nz0, nz1);
+      } else if (hz) {
+        const T* q = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
+        nz0 = q[0]; nz1 = q[1];
       }
+      if (!ok) { abort_flag = 1; atomicExch(err, 1); }
       T r0, r1;
       if (FWD) {
-        // w_i = y_i - sum_j S_ij z_j ; u_i = w_i - sum_{k<i} S_ik t_k ; t_i = inv(U_ii) u_i
-        T w0 = cur.a0, w1 = cur.a1;
-        const T l0[3] = {nz0, ny0, xc > 0 ? prev0 : T(0)}, l1[3] = {nz1, ny1, xc > 0 ? prev1 : T(0)};
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          T a = cur.zs[q] + (q < 3 ? l0[q] : T(0)), b = cur.zp[q] + (q < 3 ? l1[q] : T(0));
-          w0 -= cur.S[q][0] * a + cur.S[q][1] * b;
-          w1 -= cur.S[q][2] * a + cur.S[q][3] * b;
-        }
-        r0 = cur.D[0] * w0 + cur.D[1] * w1;
-        r1 = cur.D[2] * w0 + cur.D[3] * w1;
-        t[2 * ic] = r0;
-        t[2 * ic + 1] = r1;
+        // u_i = w_i - sum_{k<i} S_ik t_k (blocks z-1, y-1, x-1) ; t_i = inv(U_ii) u_i
+        T px0 = x > 0 ? prev0 : T(0), px1 = x > 0 ? prev1 : T(0);
+        T u0 = c0.a0 - (c0.S[0][0] * nz0 + c0.S[0][1] * nz1) - (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) -
+               (c0.S[2][0] * px0 + c0.S[2][1] * px1);
+        T u1 = c0.a1 - (c0.S[0][2] * nz0 + c0.S[0][3] * nz1) - (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) -
+               (c0.S[2][2] * px0 + c0.S[2][3] * px1);
+        r0 = c0.D[0] * u0 + c0.D[1] * u1;
+        r1 = c0.D[2] * u0 + c0.D[3] * u1;
+        t[2 * i0] = r0;
+        t[2 * i0 + 1] = r1;
       } else {
-        // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j ; z_f = (z_s, z_p) + dz
-        const T u0[3] = {xc + 1 < nx ? prev0 : T(0), ny0, nz0}, u1[3] = {xc + 1 < nx ? prev1 : T(0), ny1, nz1};
-        T a0 = T(0), a1 = T(0);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          a0 += cur.S[4 + q][0] * u0[q] + cur.S[4 + q][1] * u1[q];
-          a1 += cur.S[4 + q][2] * u0[q] + cur.S[4 + q][3] * u1[q];
-        }
-        r0 = cur.a0 - (cur.D[0] * a0 + cur.D[1] * a1);
-        r1 = cur.a1 - (cur.D[2] * a0 + cur.D[3] * a1);
-        dz[2 * ic] = r0;
-        dz[2 * ic + 1] = r1;
-        zout[2 * ic] = double(cur.zs[3] + r0);
-        zout[2 * ic + 1] = double(cur.zp[3] + r1);
+        // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j (blocks x+1, y+1, z+1) ; z_f = z + dz
+        T px0 = x + 1 < nx ? prev0 : T(0), px1 = x + 1 < nx ? prev1 : T(0);
+        T s0 = (c0.S[0][0] * px0 + c0.S[0][1] * px1) + (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) +
+               (c0.S[2][0] * nz0 + c0.S[2][1] * nz1);
+        T s1 = (c0.S[0][2] * px0 + c0.S[0][3] * px1) + (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) +
+               (c0.S[2][2] * nz0 + c0.S[2][3] * nz1);
+        r0 = c0.a0 - (c0.D[0] * s0 + c0.D[1] * s1);
+        r1 = c0.a1 - (c0.D[2] * s0 + c0.D[3] * s1);
+        dz[2 * i0] = r0;
+        dz[2 * i0 + 1] = r1;
+        zout[2 * i0] = double(c0.z0 + r0);
+        zout[2 * i0 + 1] = double(c0.z1 + r1);
       }
+      if (py || pz) halo_put<T>(halo, i0, r0, r1, tag);
       prev0 = r0;
       prev1 = r1;
       buf[step & 1][lz][ly][0] = r0;
       buf[step & 1][lz][ly][1] = r1;
     }
-    // prefetch the next step: own cell data, then boundary predecessors once published
-    int xn = 0;
-    int64_t in = step < last ? cell_at(step + 1, &xn) : -1;
-    if (in >= 0) {
-      load_step<T, FWD>(cur, in, xn, yy, zz, nx, ny, nz, S28, dinv, y, t, zs, zp);
-      bool okn = true;
-      if (gy) {
-        okn = okn && wait_progress(fy, base + min(step + kTY, last), seen_y, limit, err);
-        if (okn) { by0 = __ldcg(src + 2 * (in + jy)); by1 = __ldcg(src + 2 * (in + jy) + 1); }
-      }
-      if (gz) {
-        okn = okn && wait_progress(fz, base + min(step + kTZ, last), seen_z, limit, err);
-        if (okn) { bz0 = __ldcg(src + 2 * (in + jz)); bz1 = __ldcg(src + 2 * (in + jz) + 1); }
-      }
-      if (!okn) { abort_flag = 1; atomicExch(err, 1); }
-    }
-    ic = in;
-    xc = xn;
+    // rotate the rings: cell data for step + 3, halo words for step + 2
+    c0 = c1; c1 = c2;
+    i0 = i1; i1 = i2; i2 = cell_at(step + 3);
+    load_cell<T, FWD>(c2, i2, S28, dinv, a, zs, zp);
+    hy0 = hy1; hz0 = hz1;
+    if (gy && i1 >= 0) halo_fetch<T>(halo, i1 + jy, hy1);
+    if (gz && i1 >= 0) halo_fetch<T>(halo, i1 + jz, hz1);
     __syncthreads();
     if (abort_flag) return;
-    if (threadIdx.x == 0) st_release(progress + blockIdx.x, base + step);
   }
 }
 
@@ -334,6 +385,7 @@ ps_status flow_alloc_work(Arena& ar, const FlowStage& F, FlowWork<T>& W) {
   PS_TRY(ar.alloc(&W.vf, 2 * nc)); PS_TRY(ar.alloc(&W.y, 2 * nc)); PS_TRY(ar.alloc(&W.zs, nc));
   PS_TRY(ar.alloc(&W.wp, nc)); PS_TRY(ar.alloc(&W.zp, nc)); PS_TRY(ar.alloc(&W.t, 2 * nc));
   PS_TRY(ar.alloc(&W.dz, 2 * nc));
+  PS_TRY(ar.alloc(&W.wf, 2 * nc));
   return PS_OK;
 }
 
@@ -347,20 +399,22 @@ void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaS
 template <class T>
 bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStream_t st) {
   FlowView<T> V = fview<T>(F);
-  if (!V.s28) return false;
+  if (!V.s28 || !F.halo) return false;
   int nby = (F.ny + kTY - 1) / kTY, nbz = (F.nz + kTZ - 1) / kTZ;
   unsigned grid = unsigned(nby * nbz);
   FlowStage& Fm = const_cast<FlowStage&>(F);
+  PS_TICK(); k_ff_residual<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, V.s28, W.y, W.zs, W.zp, W.wf);
   for (int dir = 0; dir < 2; ++dir) {
-    int64_t epoch = ++Fm.ilu_epoch;
+    uint32_t tag = uint32_t(++Fm.ilu_epoch);
+    if (tag == 0) tag = uint32_t(++Fm.ilu_epoch);  // 0 marks never-written halo words
     int nx = F.nx, ny = F.ny, nz = F.nz;
-    const T *s28 = V.s28, *dinv = V.dinv, *y = W.y, *zs = W.zs, *zp = W.zp;
+    const T *s28 = V.s28, *dinv = V.dinv, *a = W.wf, *zs = W.zs, *zp = W.zp;
     T *t = W.t, *dz = W.dz;
-    int64_t* prog = dir == 0 ? F.prog_fwd : F.prog_bwd;
+    uint64_t* halo = F.halo;
     int* err = F.ilu_err;
     int64_t lim = F.spin_limit;
     int stall = F.test_stall;
-    void* args[] = {&nx, &ny, &nz, &s28, &dinv, &y, &zs, &zp, &t, &dz, &zout, &prog, &err, &epoch, &lim, &stall};
+    void* args[] = {&nx, &ny, &nz, &s28, &dinv, &a, &zs, &zp, &t, &dz, &zout, &halo, &err, &tag, &lim, &stall};
     cudaError_t e = dir == 0
         ? cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, true>, grid, kTY * kTZ, args, 0, st)
         : cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, false>, grid, kTY * kTZ, args, 0, st);
@@ -375,7 +429,7 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
 
 template <class T>
 void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int ilu_mode, cudaStream_t st) {
-  if (ilu_mode == PS_ILU_PENCIL && F.prog_fwd && ilu_pencil<T>(F, W, zout, st)) return;
+  if (ilu_mode == PS_ILU_PENCIL && F.halo && ilu_pencil<T>(F, W, zout, st)) return;
   FlowView<T> V = fview<T>(F);
   for (int l = 0; l < F.nlev; ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];

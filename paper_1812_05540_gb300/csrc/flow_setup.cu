@@ -175,12 +175,9 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
     PS_TICK(); k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
-    int nb = ((F.ny + 15) / 16) * ((F.nz + 7) / 8);
-    PS_TRY(ar.alloc(&F.prog_fwd, nb + 1));
-    PS_TRY(ar.alloc(&F.prog_bwd, nb + 1));
+    PS_TRY(ar.alloc(&F.halo, size_t(nc) * 4));
     PS_TRY(ar.alloc(&F.ilu_err, 4));
-    PS_CUDA(cudaMemsetAsync(F.prog_fwd, 0, sizeof(int64_t) * (nb + 1), st));
-    PS_CUDA(cudaMemsetAsync(F.prog_bwd, 0, sizeof(int64_t) * (nb + 1), st));
+    PS_CUDA(cudaMemsetAsync(F.halo, 0, sizeof(uint64_t) * nc * 4, st));
     PS_CUDA(cudaMemsetAsync(F.ilu_err, 0, 4 * sizeof(int), st));
     F.lev_off.resize(F.nlev + 1);
     PS_CUDA(cudaMemcpyAsync(F.lev_off.data(), off, sizeof(int32_t) * (F.nlev + 1), cudaMemcpyDeviceToHost, st));
