@@ -51,6 +51,7 @@ typedef enum {
 enum { PS_FP64 = 0, PS_MIXED_FP32 = 1 };     /* preconditioner precision */
 enum { PS_SMOOTH_L1JACOBI = 0, PS_SMOOTH_CHEBYSHEV = 1 };
 enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
+enum { PS_ORTHO_MGS = 0, PS_ORTHO_CGS2 = 1 };    /* Arnoldi orthogonalisation */
 
 /* Cartesian box of nx*ny*nz cubic cells (§6 grids); hx = hy = hz. */
 typedef struct {
@@ -99,6 +100,12 @@ typedef struct {
   int32_t test_stall_wave;    /* testing only, 0 = off: k > 0 makes wavefront CTA k-1 skip its
                                  work so that the bounded waits of its consumers run out and
                                  ps_solve returns PS_ERR_TIMEOUT (no fault, no hang) */
+  int32_t ortho;              /* PS_ORTHO_MGS (default: modified Gram-Schmidt, one cooperative launch
+                                 per Arnoldi step) or PS_ORTHO_CGS2 (classical Gram-Schmidt with the
+                                 DGKS reorthogonalisation test) */
+  int32_t test_stall_gs;      /* testing only, 0 = off: k > 0 makes CTA k-1 of the Gram-Schmidt
+                                 launch skip its work, so the grid barrier waits of the others run
+                                 out and ps_solve returns PS_ERR_TIMEOUT (no fault, no hang) */
 } ps_params;
 
 typedef struct {
@@ -135,6 +142,9 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac);
 
 /* Testing only: set ps_params.test_stall_wave on an existing handle (0 = off). */
 ps_status ps_set_test_stall(ps_handle* h, int32_t wave_cta_plus_one);
+
+/* Testing only: set ps_params.test_stall_gs on an existing handle (0 = off). */
+ps_status ps_set_test_stall_gs(ps_handle* h, int32_t cta_plus_one);
 
 /* Iteration phase: x = FGMRES(A, M^{-1}, rhs) from x0 = 0 to the true FP64
    relative residual tol.  rhs, x: n = 3*nodes + 2*cells doubles.

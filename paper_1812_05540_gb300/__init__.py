@@ -18,6 +18,7 @@ PS_OK, PS_ERR_INVALID, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_NOT_CONVERGED, PS_ERR_BRE
 PS_FP64, PS_MIXED_FP32 = 0, 1
 PS_SMOOTH_L1JACOBI, PS_SMOOTH_CHEBYSHEV = 0, 1
 PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
+PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1
 PS_FIELDS_LOGNORMAL, PS_FIELDS_LAYERED, PS_FIELDS_CHANNELS, PS_FIELDS_HOMOGENEOUS = range(4)
 PS_GEN_GRAVITY, PS_GEN_DIRICHLET, PS_GEN_SCALE, PS_GEN_ACCUM, PS_GEN_FLUX, PS_GEN_FLUX_SAT, PS_GEN_COUPLING = \
     (1 << i for i in range(7))
@@ -45,7 +46,8 @@ class ps_params(C.Structure):
                 ("cheb_ratio", C.c_double), ("theta_u", C.c_double), ("theta_p", C.c_double),
                 ("coarse_max_u", C.c_int32), ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32),
                 ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
-                ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32)]
+                ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
+                ("ortho", C.c_int32), ("test_stall_gs", C.c_int32)]
 
 
 class ps_stats(C.Structure):
@@ -95,6 +97,7 @@ def lib():
         L.ps_setup.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.POINTER(ps_params), C.POINTER(H)]
         L.ps_setup_flow.argtypes = [H, C.POINTER(ps_jacobian)]
         L.ps_set_test_stall.argtypes = [H, C.c_int32]
+        L.ps_set_test_stall_gs.argtypes = [H, C.c_int32]
         L.ps_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(ps_stats)]
         L.ps_spmv.argtypes = [H, C.c_void_p, C.c_void_p]
         L.ps_apply_prec.argtypes = [H, C.c_void_p, C.c_void_p]
@@ -175,6 +178,10 @@ def ps_setup(jac, grid, params):
 
 def ps_set_test_stall(h, wave_cta_plus_one):
     _check(lib().ps_set_test_stall(h, wave_cta_plus_one), "ps_set_test_stall")
+
+
+def ps_set_test_stall_gs(h, cta_plus_one):
+    _check(lib().ps_set_test_stall_gs(h, cta_plus_one), "ps_set_test_stall_gs")
 
 
 def ps_setup_flow(h, jac):

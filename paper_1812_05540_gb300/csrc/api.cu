@@ -53,7 +53,12 @@ struct ps_handle {
   double *V = nullptr, *Z = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *part = nullptr, *mpart = nullptr;
   KrylovState K;
   double* hsc = nullptr;  // pinned: 8 scalars
-  int* hflag = nullptr;   // pinned: 2 flags
+  int* hflag = nullptr;   // pinned: Krylov flags [0..2], ILU error [3]
+  // modified Gram-Schmidt launch: CTAs (0 = not possible), ticket barrier counter and its base
+  int mgs_blocks = 0;
+  double* mgs_part = nullptr;
+  unsigned long long* mgs_bar = nullptr;
+  unsigned long long mgs_base = 0;
   float ms_setup_u = 0, ms_setup_f = 0;
   int64_t spmv_part = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-iteration phase timers
@@ -246,6 +251,15 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(ar.alloc(&K.h1, m + 2)); PS_TRY(ar.alloc(&K.h2, m + 2)); PS_TRY(ar.alloc(&K.y, m + 1));
   PS_TRY(ar.alloc(&K.sc, 16)); PS_TRY(ar.alloc(&K.flag, 4));
   PS_CUDA(cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), st));
+  if (h->prm.ortho == PS_ORTHO_MGS) {
+    PS_TRY(mgs_grid(&h->mgs_blocks));
+    if (h->mgs_blocks > 0) {
+      PS_TRY(ar.alloc(&h->mgs_part, size_t(2) * h->mgs_blocks));
+      PS_TRY(ar.alloc(&h->mgs_bar, 1));
+      PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
+      h->mgs_base = 0;
+    }
+  }
   for (int e = 0; e < 4; ++e) PS_CUDA(cudaEventCreate(&h->ev[e]));
   for (int e = 0; e < 5; ++e) PS_CUDA(cudaEventCreate(&h->fe[e]));
   PS_CUDA(cudaMallocHost(&h->hsc, 16 * sizeof(double)));
@@ -308,6 +322,12 @@ ps_status ps_set_test_stall(ps_handle* h, int32_t wave_cta_plus_one) {
   if (!h || wave_cta_plus_one < 0) return PS_ERR_INVALID;
   h->prm.test_stall_wave = wave_cta_plus_one;
   h->F.test_stall = wave_cta_plus_one;
+  return PS_OK;
+}
+
+ps_status ps_set_test_stall_gs(ps_handle* h, int32_t cta_plus_one) {
+  if (!h || cta_plus_one < 0) return PS_ERR_INVALID;
+  h->prm.test_stall_gs = cta_plus_one;
   return PS_OK;
 }
 
@@ -380,7 +400,7 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
       cycle_start(K, m, st);
       scale_vec(h->r, h->V, n, K.sc + 4, st);
       int jend = -1;
-      bool brk = false, nanf = false, timeout = false;
+      bool brk = false, nanf = false, timeout = false, gs_timeout = false;
       for (int j = 0; j < m; ++j) {
         double* vj = h->V + int64_t(j) * n;
         double* zj = h->Z + int64_t(j) * n;
@@ -390,20 +410,27 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
         cudaEventRecord(h->ev[1], st);
         jac_spmv(h->J, zj, w, nullptr, nullptr, st);
         cudaEventRecord(h->ev[2], st);
-        // classical Gram-Schmidt with selective reorthogonalisation
-        multidot(h->V, n, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
-        PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        mupdate(h->V, n, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
-        arnoldi_check(K, st);
-        multidot(h->V, n, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
-        mupdate(h->V, n, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
-        arnoldi_finish(K, m, j, st);
-        scale_vec(w, w, n, K.sc + 4, st);
+        if (h->prm.ortho == PS_ORTHO_MGS &&
+            mgs_step(h->V, n, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
+                     h->prm.test_stall_gs, st)) {
+          // modified Gram-Schmidt (w normalised in the same launch)
+          arnoldi_finish(K, m, j, st);
+        } else {
+          // classical Gram-Schmidt with selective reorthogonalisation
+          multidot(h->V, n, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
+          PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+          mupdate(h->V, n, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
+          arnoldi_check(K, st);
+          multidot(h->V, n, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
+          mupdate(h->V, n, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
+          arnoldi_finish(K, m, j, st);
+          scale_vec(w, w, n, K.sc + 4, st);
+        }
         cudaEventRecord(h->ev[3], st);
         ++total;
         PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h->hflag + 2, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PS_CUDA(cudaMemcpyAsync(h->hflag + 3, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
         double est = h->hsc[5], hn = h->hsc[6];
         {
@@ -419,14 +446,22 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
         S.est_relres = est;
         jend = j;
         S.reorth += h->hflag[0];
-        if (h->hflag[2]) { timeout = true; break; }
+        if (h->hflag[3]) { timeout = true; break; }
+        if (h->hflag[2]) { gs_timeout = true; break; }
         if (h->hflag[1]) { nanf = true; break; }
         if (!(hn > 1e-300 * bnorm)) brk = true;
         if (est <= tol || brk || total >= h->prm.max_iters) break;
       }
-      if (timeout) {
-        PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
-        set_reason("a bounded wait of the wavefront ILU(0) sweep gave up");
+      if (timeout || gs_timeout) {
+        if (h->hflag[3]) PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
+        if (h->hflag[2]) {
+          // the barrier counter is left mid-count: start it again from zero
+          PS_CUDA(cudaMemsetAsync(K.flag + 2, 0, sizeof(int), st));
+          PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
+          h->mgs_base = 0;
+        }
+        set_reason(timeout ? "a bounded wait of the wavefront ILU(0) sweep gave up"
+                           : "a bounded grid barrier wait of the Gram-Schmidt step gave up");
         result = PS_ERR_TIMEOUT;
         break;
       }

@@ -1,6 +1,7 @@
 // FP64 Jacobian SpMV and flexible-GMRES kernels.  Every reduction is taken in
 // a fixed order (per-block partial sums, then one block over the partials), so
 // repeated solves give identical iterates.
+#include <algorithm>
 #include <cmath>
 
 #include "krylov.cuh"
@@ -452,6 +453,116 @@ __global__ void k_hsolve(const double* H, const double* g, double* y, int m, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Arnoldi step by modified Gram-Schmidt in one cooperative launch: for
+// k = 0..j, h_k = v_k . w and w -= h_k v_k; then h_{j+1} = ||w|| and
+// v_{j+1} = w / h_{j+1}.  Pass k fuses the update by v_{k-1} with the dot by
+// v_k, so each pass is one sweep over the rows (two FP64 FMAs per row and
+// column, the least the method needs).  Every thread keeps the same rows in
+// every pass, so w needs no synchronisation; each pass ends with a grid barrier
+// (bounded ticket counter) after which every CTA sums the CTA partials in the
+// same fixed order, so all CTAs hold bit-identical h_k.
+// ---------------------------------------------------------------------------
+constexpr int kMgsThreads = 256;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// all CTAs arrive, then wait until the counter reaches target; false (and *err set) when the
+// wait gives up after limit polls or another CTA has already given up
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int64_t limit,
+                                             int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1ull);
+    int good = 1;
+    int64_t it = 0;
+    while (ld_acquire_u64(ctr) < target) {
+      if (++it > limit || ((it & 255) == 0 && *(volatile int*)err)) {
+        good = 0;
+        atomicExch(err, 1);
+        break;
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kMgsThreads) k_mgs(const double* __restrict__ V, int64_t ldv, int j,
+                                                     double* __restrict__ w, int64_t n, double* __restrict__ h,
+                                                     double* __restrict__ sc, int* __restrict__ flag,
+                                                     double* __restrict__ part, unsigned long long* bar,
+                                                     unsigned long long base, int64_t limit, int stall) {
+  // test hook: CTA stall - 1 never arrives, so the others' bounded barrier waits run out
+  if (stall > 0 && int(blockIdx.x) == stall - 1) return;
+  __shared__ double red[kMgsThreads / 32];
+  __shared__ double hs;
+  const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = int64_t(G) * kMgsThreads, t0 = int64_t(blockIdx.x) * kMgsThreads + threadIdx.x;
+  int* err = flag + 2;
+  double hk = 0.0;
+  for (int k = 0; k <= j + 1; ++k) {
+    const double* vp = V + int64_t(k > 0 ? k - 1 : 0) * ldv;  // v_{k-1}: last use
+    const double* vk = V + int64_t(k <= j ? k : 0) * ldv;      // v_k
+    double acc = 0.0;
+    if (k == 0) {
+#pragma unroll 4
+      for (int64_t e = t0; e < n; e += stride) acc = fma(vk[e], w[e], acc);
+    } else if (k <= j) {
+#pragma unroll 4
+      for (int64_t e = t0; e < n; e += stride) {
+        double we = fma(-hk, __ldcs(vp + e), w[e]);
+        w[e] = we;
+        acc = fma(vk[e], we, acc);
+      }
+    } else {
+#pragma unroll 4
+      for (int64_t e = t0; e < n; e += stride) {
+        double we = fma(-hk, __ldcs(vp + e), w[e]);
+        w[e] = we;
+        acc = fma(we, we, acc);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int q = 0; q < kMgsThreads / 32; ++q) s += red[q];
+      part[(k & 1) * G + blockIdx.x] = s;
+    }
+    if (!grid_barrier(bar, base + (unsigned long long)(k + 1) * G, limit, err)) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < G; i += kMgsThreads) s += __ldcg(part + (k & 1) * G + i);
+    s = warp_sum(s);
+    if (lane == 0) red[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < kMgsThreads / 32; ++q) t += red[q];
+      hs = t;
+    }
+    __syncthreads();
+    hk = hs;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (k <= j) h[k] = hk;
+      else { sc[1] = hk; flag[0] = 0; }
+    }
+  }
+  // hk = ||w||^2; the same reciprocal as the Arnoldi finish step computes
+  double hn = sqrt(hk);
+  double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (int64_t e = t0; e < n; e += stride) w[e] *= inv;
+}
+
 constexpr int kVecBlocks = 1216;  // 8 x 152 SMs
 
 }  // namespace
@@ -522,6 +633,34 @@ void scale_vec(const double* x, double* y, int64_t n, const double* scale, cudaS
   PS_TICK(); k_scale<<<kVecBlocks, 256, 0, st>>>(x, y, n, scale);
 }
 void fill_zero(double* x, int64_t n, cudaStream_t st) { PS_TICK(); k_zero<<<kVecBlocks, 256, 0, st>>>(x, n); }
+
+ps_status mgs_grid(int* blocks) {
+  int dev = 0, sms = 0, occ = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  PS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs, kMgsThreads, 0));
+  *blocks = coop ? sms * std::min(occ, 4) : 0;
+  return PS_OK;
+}
+
+bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part, int blocks,
+              unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, cudaStream_t st) {
+  if (blocks <= 0) return false;
+  unsigned long long b0 = *base;
+  double* h = K.h1;
+  double* sc = K.sc;
+  int* flag = K.flag;
+  void* args[] = {&V, &ldv, &j, &w, &n, &h, &sc, &flag, &part, &bar, &b0, &limit, &stall};
+  if (cudaLaunchCooperativeKernel((const void*)k_mgs, blocks, kMgsThreads, args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  PS_TICK();
+  *base = b0 + (unsigned long long)(j + 2) * blocks;
+  return true;
+}
 
 void arnoldi_check(KrylovState& K, cudaStream_t st) { PS_TICK(); k_arnoldi_check<<<1, 1, 0, st>>>(K.sc, K.flag); }
 void arnoldi_finish(KrylovState& K, int m, int j, cudaStream_t st) {

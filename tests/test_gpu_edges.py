@@ -73,6 +73,23 @@ def test_bounded_wait_times_out_and_handle_recovers(sysd):
         ps.ps_free(h)
 
 
+def test_gram_schmidt_barrier_times_out_and_handle_recovers(sysd):
+    # a Gram-Schmidt CTA that never reaches the grid barrier: the others give up after spin_limit
+    # polls, the solve reports PS_ERR_TIMEOUT, and the same handle then solves normally
+    osys, dev = sysd
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(spin_limit=20000, test_stall_gs=2))
+    try:
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        s, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8, raise_on_error=False)
+        assert s == ps.PS_ERR_TIMEOUT
+        assert "Gram-Schmidt" in ps.ps_strerror(s)
+        ps.ps_set_test_stall_gs(h, 0)
+        s, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8, raise_on_error=False)
+        assert s == ps.PS_OK and st.true_relres <= 1e-8
+    finally:
+        ps.ps_free(h)
+
+
 def test_host_pointer_path_matches_device_path(sysd):
     osys, dev = sysd
     import ctypes as C

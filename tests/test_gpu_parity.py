@@ -190,3 +190,33 @@ def test_pencil_wavefront_matches_level_launch(prec, rtol):
         finally:
             ps.ps_free(h)
     assert np.linalg.norm(out[0] - out[1]) <= rtol * np.linalg.norm(out[1])
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+def test_mgs_and_cgs2_agree(prec):
+    # both orthogonalisations of the Arnoldi step give the oracle's solution (the oracle uses
+    # modified Gram-Schmidt) to the solve tolerance, with iteration counts within one of each other
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(1, nx=24, ny=20, nz=10))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=60, coarse_max_p=60))
+    xo, _ = P.fgmres(tol=1e-12)
+    _, sto8 = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    its = {}
+    for ortho in (ps.PS_ORTHO_MGS, ps.PS_ORTHO_CGS2):
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=60, coarse_max_p=60,
+                                                                 ortho=ortho))
+        try:
+            x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+            _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+        finally:
+            ps.ps_free(h)
+        xs = x.cpu().numpy()
+        assert st.true_relres <= 1e-8
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+        its[ortho] = st.iters
+        if ortho == ps.PS_ORTHO_MGS:
+            assert st.reorth == 0
+    assert abs(its[ps.PS_ORTHO_MGS] - its[ps.PS_ORTHO_CGS2]) <= 1, its
+    if prec == ps.PS_FP64:
+        assert abs(its[ps.PS_ORTHO_MGS] - sto8.iters) <= 1, (its, sto8.iters)
