@@ -20,6 +20,12 @@ struct AmgLevel {
   float* dl1f = nullptr;
   double lam[3] = {0, 0, 0};  // Gershgorin bound of rho(D^{-1}A) per component
   int lanes = 32;             // threads per row in SpMV kernels
+  // level 0 on the structured grid (gx x gy x gz rows, x fastest): values by stencil slot,
+  // [slot][component][row], zero outside the grid; sns = 27 (box) or 7 (star), 0 = CSR only.
+  // One copy in the apply precision (sv_d for FP64, sv_f for mixed).
+  int sgx = 0, sgy = 0, sgz = 0, sns = 0;
+  double* sv_d = nullptr;
+  float* sv_f = nullptr;
   // transfer to level+1
   int64_t nagg = 0;
   int32_t* agg = nullptr;
@@ -32,10 +38,9 @@ struct AmgLevel {
   double* rv = nullptr;
   float* rvf = nullptr;
   int rlane = 8;
-  // coarsest level: dense inverse per component (row-major n x n)
+  // coarsest level: dense FP64 inverse per component (row-major n x n), used in both precisions
   bool coarsest = false;
   double* inv = nullptr;
-  float* invf = nullptr;
   // V-cycle work vectors (n*nc entries of the apply precision): iterate x and
   // its ping-pong partner t, residual r, Chebyshev direction d, right-hand
   // side b (written by the finer level's restriction) and result e (read by
@@ -59,6 +64,11 @@ struct AmgParams {
 // operators do not depend on thread scheduling.
 ps_status amg_build(Arena& ar, Amg& H, int nc, int64_t n, int64_t nnz, int32_t* rp, int32_t* ci, double* v,
                     const AmgParams& prm, cudaStream_t st);
+
+// Stencil-slot copy of the level-0 operator of a hierarchy on a gx x gy x gz grid with an ns-point
+// pattern (27 or 7).  Sets *ok = false (and leaves the level CSR-only) when some entry is not
+// one of the pattern's slots.
+ps_status amg_stencil(Arena& ar, Amg& H, int gx, int gy, int gz, int ns, bool mixed, bool* ok, cudaStream_t st);
 
 // Smoothing schedule
 struct SmoothParams {

@@ -742,10 +742,6 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       }
       PS_CUDA(cudaGetLastError());
       ar.release(M); ar.release(f);
-      if (prm.mixed) {
-        PS_TRY(ar.alloc(&lev.invf, size_t(NC) * n * n));
-        PS_TICK(); k_to_f32<<<grid_for(NC * n * n, 256), 256, 0, st>>>(lev.inv, lev.invf, NC * n * n);
-      }
     }
     if (strong) ar.release(strong);
     if (wgt) ar.release(wgt);
@@ -864,6 +860,87 @@ ps_status amg_build(Arena& ar, Amg& H, int nc, int64_t n, int64_t nnz, int32_t* 
   if (nc == 3) return build_impl<3>(ar, H, n, nnz, rp, ci, v, prm, st);
   if (nc == 1) return build_impl<1>(ar, H, n, nnz, rp, ci, v, prm, st);
   return PS_ERR_INVALID;
+}
+
+namespace {
+
+// slot of the neighbour offset (dx, dy, dz) in the ns-point pattern, -1 if it is not one
+__device__ __forceinline__ int stencil_slot(int ns, int dx, int dy, int dz) {
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return -1;
+  if (ns == 27) return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+  int nz = (dx != 0) + (dy != 0) + (dz != 0);
+  if (nz > 1) return -1;
+  if (dz == -1) return 0;
+  if (dy == -1) return 1;
+  if (dx == -1) return 2;
+  if (dx == 1) return 4;
+  if (dy == 1) return 5;
+  if (dz == 1) return 6;
+  return 3;
+}
+
+template <class T>
+__global__ void k_level_to_stencil(int64_t n, int gx, int gy, int ns, int nc, const int32_t* __restrict__ rp,
+                                   const int32_t* __restrict__ ci, const double* __restrict__ v, T* __restrict__ sv,
+                                   int* bad) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t gxy = int64_t(gx) * gy;
+  const int iz = int(i / gxy);
+  const int64_t rem = i - iz * gxy;
+  const int iy = int(rem / gx), ix = int(rem - int64_t(iy) * gx);
+  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+    int64_t j = ci[q];
+    const int jz = int(j / gxy);
+    const int64_t jr = j - jz * gxy;
+    const int jy = int(jr / gx), jx = int(jr - int64_t(jy) * gx);
+    int s = stencil_slot(ns, jx - ix, jy - iy, jz - iz);
+    if (s < 0) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    for (int c = 0; c < nc; ++c) sv[(int64_t(s) * nc + c) * n + i] = T(v[int64_t(q) * nc + c]);
+  }
+}
+
+}  // namespace
+
+ps_status amg_stencil(Arena& ar, Amg& H, int gx, int gy, int gz, int ns, bool mixed, bool* ok, cudaStream_t st) {
+  *ok = false;
+  if (H.L.empty()) return PS_OK;
+  AmgLevel& L = H.L[0];
+  if (L.coarsest || int64_t(gx) * gy * gz != L.n || (ns != 27 && ns != 7)) return PS_OK;
+  int nc = H.nc;
+  size_t cnt = size_t(ns) * nc * L.n;
+  int* bad = nullptr;
+  PS_TRY(ar.alloc(&bad, 1));
+  PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  if (mixed) {
+    PS_TRY(ar.alloc(&L.sv_f, cnt));
+    PS_CUDA(cudaMemsetAsync(L.sv_f, 0, cnt * sizeof(float), st));
+    PS_TICK(); k_level_to_stencil<float><<<grid_for(L.n, 256), 256, 0, st>>>(L.n, gx, gy, ns, nc, L.rp, L.ci, L.v,
+                                                                            L.sv_f, bad);
+  } else {
+    PS_TRY(ar.alloc(&L.sv_d, cnt));
+    PS_CUDA(cudaMemsetAsync(L.sv_d, 0, cnt * sizeof(double), st));
+    PS_TICK(); k_level_to_stencil<double><<<grid_for(L.n, 256), 256, 0, st>>>(L.n, gx, gy, ns, nc, L.rp, L.ci,
+                                                                             L.v, L.sv_d, bad);
+  }
+  PS_CUDA(cudaGetLastError());
+  int hb = 0;
+  PS_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  ar.release(bad);
+  if (hb) {
+    if (L.sv_f) ar.release(L.sv_f);
+    if (L.sv_d) ar.release(L.sv_d);
+    L.sv_f = nullptr;
+    L.sv_d = nullptr;
+    return PS_OK;
+  }
+  L.sgx = gx; L.sgy = gy; L.sgz = gz; L.sns = ns;
+  *ok = true;
+  return PS_OK;
 }
 
 }  // namespace ps_internal

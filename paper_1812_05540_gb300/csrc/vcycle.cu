@@ -30,49 +30,78 @@ struct Row {
   }
 };
 
-#define ROW_SETUP                                                        \
-  int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;         \
-  int64_t i = tid / LANES;                                               \
-  int sub = int(tid % LANES);                                            \
-  bool active = i < n;                                                   \
-  int32_t q0 = active ? rp[i] : 0, q1 = active ? rp[i + 1] : 0;
-
-// Chebyshev from x = 0, first two steps fused:
-// d0 = D^{-1} b / theta; r = D^{-1}(b - A d0); d1 = c1 d0 + c2 r; x = d0 + d1
+// Rows of a level operator in CSR form, LANES threads per row.
 template <class T, int NC, int LANES>
-__global__ void k_cheb_pre(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const T* __restrict__ v, const T* __restrict__ dg, const T* __restrict__ b,
-                           T* __restrict__ x, T* __restrict__ dout, double3 inv_theta, double3 c1, double3 c2) {
-  ROW_SETUP
-  const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
-  auto xf = [&](int32_t j, int c) { return (b[int64_t(j) * NC + c] / dg[int64_t(j) * NC + c]) * T(it[c]); };
-  T s[NC];
-  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
-  if (active && sub == 0) {
-    const double a1[3] = {c1.x, c1.y, c1.z}, a2[3] = {c2.x, c2.y, c2.z};
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T bi = b[i * NC + c], di = dg[i * NC + c];
-      T d0 = (bi / di) * T(it[c]);
-      T r = (bi - s[c]) / di;
-      T d1 = T(a1[c]) * d0 + T(a2[c]) * r;
-      x[i * NC + c] = d0 + d1;
-      if (dout) dout[i * NC + c] = d1;
-    }
+struct CsrRows {
+  static constexpr int kLanes = LANES;
+  const int32_t *rp, *ci;
+  const T* v;
+  template <class XF>
+  __device__ __forceinline__ void dot(int64_t i, int sub, bool active, XF xf, T (&s)[NC]) const {
+    int32_t q0 = active ? rp[i] : 0, q1 = active ? rp[i + 1] : 0;
+    Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  }
+};
+
+// Stencil slot q -> (dx, dy, dz): the full 27-point box (x fastest) or the 7-point star
+// (z-1, y-1, x-1, self, x+1, y+1, z+1).
+template <int NS>
+__device__ __forceinline__ void slot_offset(int q, int& dx, int& dy, int& dz) {
+  if constexpr (NS == 27) {
+    dx = q % 3 - 1; dy = (q / 3) % 3 - 1; dz = q / 9 - 1;
+  } else {
+    dx = q == 2 ? -1 : (q == 4 ? 1 : 0);
+    dy = q == 1 ? -1 : (q == 5 ? 1 : 0);
+    dz = q == 0 ? -1 : (q == 6 ? 1 : 0);
   }
 }
 
+// Rows of a level operator on the structured grid (gx x gy x gz rows, x fastest): values by
+// stencil slot, [slot][component][row], one thread per row, no column indices.
+template <class T, int NC, int NS>
+struct StencilRows {
+  static constexpr int kLanes = 1;
+  int gx, gy, gz;
+  int64_t n;
+  const T* v;
+  template <class XF>
+  __device__ __forceinline__ void dot(int64_t i, int, bool active, XF xf, T (&s)[NC]) const {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = T(0);
+    if (!active) return;
+    const int64_t gxy = int64_t(gx) * gy;
+    const int iz = int(i / gxy);
+    const int64_t rem = i - iz * gxy;
+    const int iy = int(rem / gx), ix = int(rem - int64_t(iy) * gx);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      int dx, dy, dz;
+      slot_offset<NS>(q, dx, dy, dz);
+      const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+      if (jx < 0 || jx >= gx || jy < 0 || jy >= gy || jz < 0 || jz >= gz) continue;
+      const int64_t j = i + dx + int64_t(gx) * (dy + int64_t(gy) * dz);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s[c] += __ldg(v + (int64_t(q) * NC + c) * n + i) * xf(j, c);
+    }
+  }
+};
+
+#define ROWS_SETUP                                                \
+  int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  \
+  int64_t i = tid / A::kLanes;                                    \
+  int sub = int(tid % A::kLanes);                                 \
+  bool active = i < n;
+
 // one Chebyshev step from a nonzero x: r = D^{-1}(b - A x); d = c1 d + c2 r; xo = x + d
 // (first == true: d = r / theta, i.e. c1 = 0, c2 = 1/theta)
-template <class T, int NC, int LANES>
-__global__ void k_cheb_step(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                            const T* __restrict__ v, const T* __restrict__ dg, const T* __restrict__ b,
+template <class T, int NC, class A>
+__global__ void k_cheb_step(A a, int64_t n, const T* __restrict__ dg, const T* __restrict__ b,
                             const T* __restrict__ x, T* __restrict__ xo, T* __restrict__ d, double3 c1, double3 c2,
                             int first) {
-  ROW_SETUP
-  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  ROWS_SETUP
+  auto xf = [&](int64_t j, int c) { return x[j * NC + c]; };
   T s[NC];
-  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  a.dot(i, sub, active, xf, s);
   if (active && sub == 0) {
     const double a1[3] = {c1.x, c1.y, c1.z}, a2[3] = {c2.x, c2.y, c2.z};
 #pragma unroll
@@ -86,14 +115,13 @@ __global__ void k_cheb_step(int64_t n, const int32_t* __restrict__ rp, const int
 }
 
 // l1-Jacobi: xo = x + (b - A x) / dl1
-template <class T, int NC, int LANES>
-__global__ void k_l1_step(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                          const T* __restrict__ v, const T* __restrict__ dl1, const T* __restrict__ b,
+template <class T, int NC, class A>
+__global__ void k_l1_step(A a, int64_t n, const T* __restrict__ dl1, const T* __restrict__ b,
                           const T* __restrict__ x, T* __restrict__ xo) {
-  ROW_SETUP
-  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+  ROWS_SETUP
+  auto xf = [&](int64_t j, int c) { return x[j * NC + c]; };
   T s[NC];
-  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  a.dot(i, sub, active, xf, s);
   if (active && sub == 0)
 #pragma unroll
     for (int c = 0; c < NC; ++c) xo[i * NC + c] = x[i * NC + c] + (b[i * NC + c] - s[c]) / dl1[i * NC + c];
@@ -105,27 +133,37 @@ __global__ void k_l1_first(int64_t n, const T* __restrict__ dl1, const T* __rest
   if (t < n * NC) x[t] = b[t] / dl1[t];
 }
 
+// first Chebyshev step from x = 0: x = D^{-1} b / theta (and d = x when d != nullptr)
 template <class T, int NC>
 __global__ void k_cheb_first1(int64_t n, const T* __restrict__ dg, const T* __restrict__ b, T* __restrict__ x,
-                              double3 inv_theta) {
+                              T* __restrict__ d, double3 inv_theta) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
-  if (t < n * NC) x[t] = (b[t] / dg[t]) * T(it[t % NC]);
+  if (t < n * NC) {
+    T v = (b[t] / dg[t]) * T(it[t % NC]);
+    x[t] = v;
+    if (d) d[t] = v;
+  }
 }
 
 // r = b - A x
-template <class T, int NC, int LANES>
-__global__ void k_resid(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                        const T* __restrict__ v, const T* __restrict__ b, const T* __restrict__ x,
-                        T* __restrict__ r) {
-  ROW_SETUP
-  auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
+template <class T, int NC, class A>
+__global__ void k_resid(A a, int64_t n, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+  ROWS_SETUP
+  auto xf = [&](int64_t j, int c) { return x[j * NC + c]; };
   T s[NC];
-  Row<T, NC, LANES>::dot(active, q0, q1, ci, v, xf, sub, s);
+  a.dot(i, sub, active, xf, s);
   if (active && sub == 0)
 #pragma unroll
     for (int c = 0; c < NC; ++c) r[i * NC + c] = b[i * NC + c] - s[c];
 }
+
+#define ROW_SETUP                                                        \
+  int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;         \
+  int64_t i = tid / LANES;                                               \
+  int sub = int(tid % LANES);                                            \
+  bool active = i < n;                                                   \
+  int32_t q0 = active ? rp[i] : 0, q1 = active ? rp[i + 1] : 0;
 
 // y = M x (restriction with R, or y += P x when add)
 template <class T, int NC, int LANES>
@@ -140,43 +178,62 @@ __global__ void k_spmv(int64_t n, const int32_t* __restrict__ rp, const int32_t*
     for (int c = 0; c < NC; ++c) y[i * NC + c] = add ? y[i * NC + c] + s[c] : s[c];
 }
 
-// coarsest: x = inv_c b_c per component, one warp per row
+// coarsest: x = inv_c b_c per component, one warp per row; the inverse and the sums stay FP64
+// in both precisions (the coarsest solve is one of the FP64 parts of the mixed mode)
 template <class T, int NC>
-__global__ void k_dense_solve(int64_t n, const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+__global__ void k_dense_solve(int64_t n, const double* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
   int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n * NC) return;
   int c = int(w / n);
   int64_t i = w % n;
-  const T* row = inv + (int64_t(c) * n + i) * n;
-  T s = T(0);
-  for (int64_t j = lane; j < n; j += 32) s += row[j] * b[j * NC + c];
+  const double* row = inv + (int64_t(c) * n + i) * n;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += row[j] * double(b[j * NC + c]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[i * NC + c] = s;
+  if (lane == 0) x[i * NC + c] = T(s);
 }
 
 template <class T>
 struct LevelT {
-  const T *v, *dg, *dl1, *pv, *rv, *inv;
+  const T *v, *dg, *dl1, *pv, *rv;
+  const double* inv;
+  const T* sv;  // stencil-slot values (level 0 on the structured grid) or null
 };
 template <class T>
 LevelT<T> view(const AmgLevel& L) {
   LevelT<T> o;
   if constexpr (sizeof(T) == 4) {
-    o.v = L.vf; o.dg = L.dgf; o.dl1 = L.dl1f; o.pv = L.pvf; o.rv = L.rvf; o.inv = L.invf;
+    o.v = L.vf; o.dg = L.dgf; o.dl1 = L.dl1f; o.pv = L.pvf; o.rv = L.rvf; o.inv = L.inv; o.sv = L.sv_f;
   } else {
-    o.v = L.v; o.dg = L.dg; o.dl1 = L.dl1; o.pv = L.pv; o.rv = L.rv; o.inv = L.inv;
+    o.v = L.v; o.dg = L.dg; o.dl1 = L.dl1; o.pv = L.pv; o.rv = L.rv; o.inv = L.inv; o.sv = L.sv_d;
   }
   return o;
 }
 
-#define DISPATCH_LANES(lanes, KERNEL, ...)                       \
-  switch (lanes) {                                               \
-    case 4: PS_TICK(); KERNEL<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
-    case 8: PS_TICK(); KERNEL<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(__VA_ARGS__); break;   \
-    case 16: PS_TICK(); KERNEL<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(__VA_ARGS__); break; \
-    default: PS_TICK(); KERNEL<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(__VA_ARGS__); break; \
+// calls f(rows) with the level's row accessor: stencil slots when the level has them, else CSR
+// with the level's lane count
+template <class T, int NC, class F>
+void with_rows(const AmgLevel& L, const LevelT<T>& V, F&& f) {
+  if (V.sv) {
+    if constexpr (NC == 3) {
+      if (L.sns == 27) { f(StencilRows<T, 3, 27>{L.sgx, L.sgy, L.sgz, L.n, V.sv}); return; }
+    } else {
+      if (L.sns == 7) { f(StencilRows<T, 1, 7>{L.sgx, L.sgy, L.sgz, L.n, V.sv}); return; }
+    }
   }
+  switch (L.lanes) {
+    case 4: f(CsrRows<T, NC, 4>{L.rp, L.ci, V.v}); break;
+    case 8: f(CsrRows<T, NC, 8>{L.rp, L.ci, V.v}); break;
+    case 16: f(CsrRows<T, NC, 16>{L.rp, L.ci, V.v}); break;
+    default: f(CsrRows<T, NC, 32>{L.rp, L.ci, V.v}); break;
+  }
+}
+
+template <class A>
+inline unsigned rows_grid(int64_t n) {
+  return grid_for(n * A::kLanes, 256);
+}
 
 struct ChebCoef {
   double3 inv_theta;
@@ -218,20 +275,23 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
   if (sp.kind == PS_SMOOTH_CHEBYSHEV) {
     ChebCoef cc = cheb_coef(L, NC, sp);
     int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
-    if (deg == 1) {
-      PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, cc.inv_theta);
-      return x;
-    }
-    DISPATCH_LANES(L.lanes, k_cheb_pre, n, L.rp, L.ci, V.v, V.dg, b, x, deg > 2 ? d : nullptr, cc.inv_theta,
-                   cc.c1[1], cc.c2[1]);
-    for (int k = 2; k < deg; ++k) {
-      DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, other, d, cc.c1[k], cc.c2[k], 0);
+    PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, deg > 1 ? d : nullptr,
+                                                                        cc.inv_theta);
+    for (int k = 1; k < deg; ++k) {
+      with_rows<T, NC>(L, V, [&](auto a) {
+        using A = decltype(a);
+        PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, other,
+                                                                           d, cc.c1[k], cc.c2[k], 0);
+      });
       std::swap(cur, other);
     }
   } else {
     PS_TICK(); k_l1_first<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dl1, b, x);
     for (int k = 1; k < sp.pre; ++k) {
-      DISPATCH_LANES(L.lanes, k_l1_step, n, L.rp, L.ci, V.v, V.dl1, b, cur, other);
+      with_rows<T, NC>(L, V, [&](auto a) {
+        using A = decltype(a);
+        PS_TICK(); k_l1_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dl1, b, cur, other);
+      });
       std::swap(cur, other);
     }
   }
@@ -248,11 +308,17 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
     int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
     for (int k = 0; k < deg; ++k) {
       T* dst = k == deg - 1 ? out : other;
-      if (k == 0)
-        DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, dst, deg > 1 ? d : nullptr,
-                       cc.c1[0], cc.post_c2, 1)
-      else
-        DISPATCH_LANES(L.lanes, k_cheb_step, n, L.rp, L.ci, V.v, V.dg, b, cur, dst, d, cc.c1[k], cc.c2[k], 0)
+      with_rows<T, NC>(L, V, [&](auto a) {
+        using A = decltype(a);
+        if (k == 0) {
+          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst,
+                                                                             deg > 1 ? d : nullptr, cc.c1[0],
+                                                                             cc.post_c2, 1);
+        } else {
+          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst, d, cc.c1[k],
+                                                                             cc.c2[k], 0);
+        }
+      });
       other = cur;
       cur = dst;
     }
@@ -260,7 +326,10 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
     int sweeps = sp.post < 1 ? 1 : sp.post;
     for (int k = 0; k < sweeps; ++k) {
       T* dst = k == sweeps - 1 ? out : other;
-      DISPATCH_LANES(L.lanes, k_l1_step, n, L.rp, L.ci, V.v, V.dl1, b, cur, dst);
+      with_rows<T, NC>(L, V, [&](auto a) {
+        using A = decltype(a);
+        PS_TICK(); k_l1_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dl1, b, cur, dst);
+      });
       other = cur;
       cur = dst;
     }
@@ -295,7 +364,10 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
   T* bc = static_cast<T*>(C.b);
   T* ec = static_cast<T*>(C.e);
   T* xs = smooth_zero<T, NC>(L, V, sp, b, x, t, d, st);
-  DISPATCH_LANES(L.lanes, k_resid, n, L.rp, L.ci, V.v, b, xs, r);
+  with_rows<T, NC>(L, V, [&](auto a) {
+    using A = decltype(a);
+    PS_TICK(); k_resid<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, b, xs, r);
+  });
   spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, V.rv, r, bc, 0, st);
   vcycle_level<T, NC>(H, l + 1, sp, bc, ec, st);
   spmv_lanes<T, NC>(L.plane, n, L.prp, L.pci, V.pv, ec, xs, 1, st);
