@@ -133,6 +133,8 @@ def lib():
         L.or_fgmres_diag.argtypes = [C.c_int64, _PD, _PD, _PD, C.c_double, C.c_int, C.c_int, C.POINTER(Stats)]
         L.or_dense_solve.argtypes = [C.POINTER(_System), _PD, _PD]
         L.or_lu_solve.argtypes = [C.c_int64, _PD, _PD, _PD]
+        L.or_smoother_apply.argtypes = [C.c_int64, _PI64, _PI32, _PD, _PD, _PD, C.c_int, C.c_int, C.c_double,
+                                        C.c_int]
         L.or_splitmix64.argtypes = [C.c_uint64]
         L.or_splitmix64.restype = C.c_uint64
         L.or_correlated_field.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -359,6 +361,21 @@ def lu_solve(A, b):
     rc = lib().or_lu_solve(len(b), _d(A), _d(b), _d(x))
     if rc:
         raise RuntimeError("singular")
+    return x
+
+
+def smoother_apply(rp, ci, v, b, kind, count, ratio=20.0, x0=None):
+    """One V-cycle level smoother on a scalar CSR matrix: kind 1 = Chebyshev of degree count on
+    D^{-1}A over [lambda_hat/ratio, lambda_hat], kind 0 = count l1-Jacobi sweeps; from x0 (or 0)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    rc = lib().or_smoother_apply(len(b), rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v), _d(b), _d(x),
+                                 kind, count, ratio, 1 if x0 is None else 0)
+    if rc:
+        raise RuntimeError("row without a diagonal entry")
     return x
 
 

@@ -1706,6 +1706,33 @@ int or_amg_vcycle(const or_prec* p, int which, int comp, const double* b, double
   std::memcpy(x, xx.data(), xx.size() * sizeof(double));
   return 0;
 }
+// one smoother application on a scalar CSR matrix (test access to the level-0 smoothers of the
+// V-cycle): kind 1 = Chebyshev of the given degree over [lambda_hat/ratio, lambda_hat] of D^{-1}A,
+// kind 0 = that many l1-Jacobi sweeps; x holds the start iterate unless zero != 0
+int or_smoother_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* b, double* x,
+                      int kind, int count, double ratio, int zero) {
+  Level lev;
+  lev.A.n = lev.A.m = n;
+  lev.A.nc = 1;
+  lev.A.rp.assign(rp, rp + n + 1);
+  lev.A.ci.assign(ci, ci + rp[n]);
+  lev.A.v.assign(v, v + rp[n]);
+  lev.dl1 = l1_diag(lev.A);
+  lev.lam = gershgorin(lev.A);
+  lev.dg.assign(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t q = lev.A.find(i, i);
+    if (q < 0) return 1;
+    lev.dg[i] = lev.A.v[q];
+  }
+  vec bb(b, b + n), xx(n, 0.0);
+  if (!zero) xx.assign(x, x + n);
+  if (kind == 1) chebyshev(lev, 1, 0, bb, xx, count, ratio, zero != 0);
+  else l1_jacobi(lev, 1, 0, bb, xx, count);
+  std::memcpy(x, xx.data(), n * sizeof(double));
+  return 0;
+}
+
 int64_t or_spp_nnz(const or_prec* p) { return p->spp.nnz(); }
 int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v) {
   std::memcpy(rp, p->spp.rp.data(), p->spp.rp.size() * sizeof(int64_t));

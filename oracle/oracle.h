@@ -143,6 +143,10 @@ int64_t or_amg_p_nnz(const or_prec* p, int which, int level);
 int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v);
 /* one V-cycle of component comp on level-0 input b */
 int or_amg_vcycle(const or_prec* p, int which, int comp, const double* b, double* x);
+// one level-0 smoother application on a scalar CSR matrix (kind 1 Chebyshev of degree count over
+// [lambda_hat/ratio, lambda_hat] of D^{-1}A; kind 0 count l1-Jacobi sweeps); zero: start from x = 0
+int or_smoother_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* b, double* x,
+                      int kind, int count, double ratio, int zero);
 /* S_pp^(cpr-fs) (§5.3) as CSR, and the fixed-stress S_ff (§5.1) as 2x2 BSR */
 int64_t or_spp_nnz(const or_prec* p);
 int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v);

@@ -1,5 +1,7 @@
 """Pins of the oracle's Jacobian generator against what the paper and the
 mathematics fix (no GPU).  Each test names the passage it checks."""
+import os
+
 import numpy as np
 import pytest
 
@@ -22,14 +24,29 @@ def test_splitmix64_published_vector():
     assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
 
 
-@pytest.mark.parametrize("dims,dof", [((32, 32, 16), 88307), ((64, 64, 32), 680419)])
-def test_dof_counts_match_table2(dims, dof):
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_rows(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+@pytest.mark.parametrize("row", _golden_rows("table2_staircase_dofs.txt"))
+def test_dof_counts_match_table2(row):
     # §6.1 Table 2: 88,307 and 680,419 DoF on the staircase meshes (all nodes x3 + 2 per cell)
-    nx, ny, nz = dims
+    nx, ny, nz, dof = (int(t) for t in row)
     gp = homogeneous(nx=nx, ny=ny, nz=nz, flags=OR_ACCUM)
     s = oracle.System(gp)
     assert s.n == dof
     assert s.n_u == 3 * (nx + 1) * (ny + 1) * (nz + 1) and s.n_f == 2 * nx * ny * nz
+
+
+def test_generator_constants_match_table1():
+    # §6 Table 1: reference densities and residual saturations used by every configuration
+    gp = oracle.default_params(0)
+    for name, value, _unit in _golden_rows("table1_parameters.txt"):
+        assert getattr(gp, name) == float(value), name
 
 
 def test_reference_integrals_closed_forms():

@@ -265,3 +265,67 @@ def test_terzaghi_consolidation():
         ser = (4 * p0 / np.pi) * np.sum(np.sin((2 * m + 1) * np.pi * zd / (2 * H)) / (2 * m + 1)
                                         * np.exp(-(2 * m + 1) ** 2 * np.pi ** 2 * cv * ti / (4 * H * H)), axis=0)
         assert np.abs(pi - ser).max() <= 0.02 * p0, (ti / T, np.abs(pi - ser).max() / p0)
+
+
+def _periodic_laplacian(n, eps):
+    # circulant tridiag(-1, 2 + eps, -1): diag(A) = 2 + eps and l1 row sums 4 + eps in every row,
+    # Fourier modes cos(2 pi k i / n) are eigenvectors with eigenvalue 2 + eps - 2 cos(2 pi k / n)
+    rp = np.arange(0, 3 * n + 1, 3, dtype=np.int64)
+    ci, v = [], []
+    for i in range(n):
+        row = sorted([((i - 1) % n, -1.0), (i, 2.0 + eps), ((i + 1) % n, -1.0)])
+        ci += [c for c, _ in row]
+        v += [a for _, a in row]
+    return rp, np.array(ci, dtype=np.int32), np.array(v)
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+@pytest.mark.parametrize("ratio", [20.0, 7.0])
+def test_chebyshev_smoother_error_polynomial(degree, ratio):
+    # Chebyshev smoothing on D^{-1}A over [lmax/ratio, lmax], lmax = the Gershgorin bound (Adams et al.
+    # 2003): the error of each eigenvector of D^{-1}A is multiplied by the scaled Chebyshev polynomial
+    # p_m(t) = T_m((theta - t)/delta) / T_m(theta/delta), from x = 0 and from a nonzero start
+    n, eps = 64, 0.5
+    rp, ci, v = _periodic_laplacian(n, eps)
+    lmax = (4.0 + eps) / (2.0 + eps)
+    lmin = lmax / ratio
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+
+    def p(t):
+        return np.polynomial.chebyshev.chebval((theta - t) / delta, [0] * degree + [1]) / \
+            np.polynomial.chebyshev.chebval(theta / delta, [0] * degree + [1])
+
+    i = np.arange(n)
+    A = np.zeros((n, n))
+    for r in range(n):
+        A[r, ci[rp[r]:rp[r + 1]]] = v[rp[r]:rp[r + 1]]
+    for k in (1, 5, 16, 31):
+        vk = np.cos(2 * np.pi * k * i / n)
+        mu = (2.0 + eps - 2.0 * np.cos(2 * np.pi * k / n)) / (2.0 + eps)
+        x = oracle.smoother_apply(rp, ci, v, A @ vk, 1, degree, ratio)
+        assert np.allclose(x, (1.0 - p(mu)) * vk, rtol=0, atol=1e-12)
+        # nonzero start x0 = 0.5 v_j: error v_k - 0.5 v_j
+        j = 3
+        vj = np.cos(2 * np.pi * j * i / n)
+        muj = (2.0 + eps - 2.0 * np.cos(2 * np.pi * j / n)) / (2.0 + eps)
+        x = oracle.smoother_apply(rp, ci, v, A @ vk, 1, degree, ratio, x0=0.5 * vj)
+        expect = vk - (p(mu) * vk - 0.5 * p(muj) * vj)
+        assert np.allclose(x, expect, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 5])
+def test_l1_jacobi_smoother_error_factor(sweeps):
+    # l1-Jacobi (Baker et al. 2011): e <- (I - D_l1^{-1} A) e with D_l1 = diag(sum_j |a_ij|); on the
+    # circulant operator D_l1 = (4 + eps) I, so each Fourier mode is damped by (1 - lambda/(4+eps))^s
+    n, eps = 48, 0.25
+    rp, ci, v = _periodic_laplacian(n, eps)
+    i = np.arange(n)
+    A = np.zeros((n, n))
+    for r in range(n):
+        A[r, ci[rp[r]:rp[r + 1]]] = v[rp[r]:rp[r + 1]]
+    for k in (0, 2, 12, 24):
+        vk = np.cos(2 * np.pi * k * i / n)
+        lam = 2.0 + eps - 2.0 * np.cos(2 * np.pi * k / n)
+        g = (1.0 - lam / (4.0 + eps)) ** sweeps
+        x = oracle.smoother_apply(rp, ci, v, A @ vk, 0, sweeps)
+        assert np.allclose(x, (1.0 - g) * vk, rtol=0, atol=1e-12)
