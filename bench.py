@@ -43,6 +43,17 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(t, world, device):
+    """The slowest rank's time: replicas share nothing but this reduction and the barriers."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -169,6 +180,74 @@ def algorithmic_spmv_bytes(s):
     return b + 2 * s.n * 8
 
 
+RESTART = 100
+
+
+def algorithmic_spmv_fma(s):
+    j = s.jac
+    return sum(blk.nnzb * bs for blk, bs in ((j.A_uu, 9), (j.A_uf, 6), (j.A_fu, 6), (j.A_ff, 4)))
+
+
+def arnoldi_steps(iters, restarts, m):
+    """Arnoldi step indices j of a solve: full cycles of m steps, then the last cycle."""
+    js = []
+    left = iters
+    for _ in range(restarts):
+        k = min(m, left)
+        js += list(range(k))
+        left -= k
+    js += list(range(left))
+    return js or [0]
+
+
+def mgs_flops(n, j):
+    # step j: j+1 dots and j+1 updates (2 flops per row each), ||w||^2 (2), scaling (1)
+    return n * (4.0 * (j + 1) + 3.0)
+
+
+def mgs_bytes_alg(n, j):
+    # compulsory traffic: each basis vector v_0..v_j read once, w read and written once
+    return 8.0 * n * (j + 1) + 16.0 * n
+
+
+def fp64_peak_tflops(sms, peaks):
+    """FP64 peak from the unit count and clock: 2 FP64 FMA per SM per clock (4 flops)."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return sms * 4.0 * mhz * 1e6 / 1e12, "derived: %d SMs x 4 FP64 flop/clk x %.0f MHz" % (sms, mhz)
+
+
+def load_traffic():
+    """Per-launch DRAM bytes from a committed ncu capture, kept only while the kernel's source is
+    the one that was profiled."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+    out = {}
+    for name, r in rec.items():
+        src = os.path.join(ROOT, r.get("source", ""))
+        try:
+            sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        except OSError:
+            continue
+        if sha == r.get("source_sha1"):
+            out[name] = r
+    return out
+
+
+def traffic_per_launch(traffic, name, n, js):
+    r = traffic.get(name)
+    if not r:
+        return None
+    if js is None:
+        return r["bytes_per_launch"]
+    # captured as DRAM bytes per row per (basis vectors + 2); scaled to this solve's steps
+    per = r["bytes_per_row_per_column"]
+    return sum(per * n * (j + 3) for j in js) / len(js)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -226,11 +305,7 @@ def run_ours(args):
             ck = clocks.stop() if clocks else None
             launches = ps.ps_launch_count() - l0
             barrier()
-            t = e0.elapsed_time(e1) / 1000.0
-            if world > 1:
-                tt = torch.tensor([t], device="cuda")
-                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-                t = float(tt.item())
+            t = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
             return t, stats, launches, ck
 
         for _ in range(args.warmup):
@@ -256,8 +331,9 @@ def run_ours(args):
         rhs_np = dev_to_numpy(s.rhs, n, np.float64)
         relres = float(np.linalg.norm(rhs_np - y.cpu().numpy()) / np.linalg.norm(rhs_np))
 
-        # dominant-kernel roofline: the FP64 Jacobian SpMV, timed alone on its stream
+        # FP64 Jacobian SpMV timed alone on its stream (secondary roofline)
         nb = algorithmic_spmv_bytes(s)
+        nfma = algorithmic_spmv_fma(s)
         xs = torch.randn(n, dtype=torch.float64, device="cuda")
         for _ in range(3):
             ps.ps_spmv(h, xs.data_ptr(), y.data_ptr())
@@ -277,12 +353,37 @@ def run_ours(args):
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except (OSError, ValueError):
             pass
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = nb / t_spmv / 1e9
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "spmv_traffic.json")
-        if os.path.exists(tfile):
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        fp64_peak, fp64_src = fp64_peak_tflops(sms, peaks)
+        traffic = load_traffic()
+
+        # dominant kernel of the mixed solve: the modified Gram-Schmidt launch of each Arnoldi step,
+        # timed by the library's CUDA events on its stream inside the timed solves
+        st_last = st_mx[-1]
+        js = arnoldi_steps(st_last.iters, st_last.restarts, RESTART)
+        mgs_flop = sum(mgs_flops(n, j) for j in js)
+        mgs_bytes = sum(mgs_bytes_alg(n, j) for j in js)
+        mgs_s = st_last.ms_orth / 1000.0
+        mgs_tflops = mgs_flop / mgs_s / 1e12
+        spmv_tflops = 2.0 * nfma / t_spmv / 1e12
+        rooflines = [
+            {"kernel": "k_mgs (Arnoldi step, modified Gram-Schmidt, FP64)", "bound": "alu",
+             "achieved": mgs_tflops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": mgs_tflops / fp64_peak,
+             "traffic": traffic_per_launch(traffic, "k_mgs", n, js),
+             "algorithmic_flops_per_launch": mgs_flop / len(js),
+             "algorithmic_bytes_per_launch": mgs_bytes / len(js), "launches": len(js),
+             "launch_ms": 1000.0 * mgs_s / len(js), "peak_source": fp64_src,
+             "hbm_frac": mgs_bytes / mgs_s / 1e9 / hbm_peak},
+            {"kernel": "FP64 Jacobian SpMV (k_spmv_u_st + k_spmv_f_st)", "bound": "alu", "achieved": spmv_tflops,
+             "peak": fp64_peak, "unit": "TFLOP/s", "frac": spmv_tflops / fp64_peak,
+             "traffic": traffic_per_launch(traffic, "spmv", n, None),
+             "algorithmic_flops_per_launch": 2.0 * nfma, "algorithmic_bytes_per_launch": nb,
+             "launch_ms": 1000.0 * t_spmv, "peak_source": fp64_src,
+             "hbm_achieved_gbs": nb / t_spmv / 1e9, "hbm_peak_gbs": hbm_peak, "hbm_frac": nb / t_spmv / 1e9 / hbm_peak,
+             "hbm_peak_source": hbm_src},
+        ]
 
         # end to end through the C ABI with host buffers (pinned), copies inside the timed region
         e2e = None
@@ -331,11 +432,7 @@ def run_ours(args):
                 step_host()
             e1.record(stream)
             torch.cuda.synchronize()
-            te = e0.elapsed_time(e1) / 1000.0
-            if world > 1:
-                tt = torch.tensor([te], device="cuda")
-                torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-                te = float(tt.item())
+            te = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
             e2e = {"value": te / args.steps / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(n * 8)}
         ps.ps_system_free(sysp)
@@ -358,6 +455,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (3.7 GB FP64 Jacobian per SpMV)", "replicas": world},
         "iters_mixed": it_mx, "iters_fp64": it_64,
         "setup_ms_mixed": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_mx],
+        "setup_split_ms_mixed": {"mechanics": round(st_mx[-1].ms_setup_u, 2), "flow": round(st_mx[-1].ms_setup_f, 2)},
+        "warm_s_mixed": (st_mx[-1].ms_setup_f + st_mx[-1].ms_solve) / 1000.0,
+        "levels": {"mechanics": st_mx[-1].levels_u, "pressure": st_mx[-1].levels_p},
+        "handle_gb_mixed": round(st_mx[-1].handle_bytes / 1e9, 3),
         "solve_ms_mixed": [round(st.ms_solve, 2) for st in st_mx],
         "solve_phases_ms_mixed": {"precond": round(st_mx[-1].ms_prec, 1), "spmv": round(st_mx[-1].ms_spmv, 1),
                                   "gram_schmidt": round(st_mx[-1].ms_orth, 1),
@@ -374,10 +475,8 @@ def run_ours(args):
                                      "vcycle_p": round(st_64[-1].ms_vcycle_p, 1), "ilu": round(st_64[-1].ms_ilu, 1)}},
         "mixed_speedup_vs_fp64": per_64 / per_mx,
         "true_relres_mixed": relres, "gen_s": gen_s,
-        "roofline": {"kernel": "FP64 Jacobian SpMV (k_spmv_u + k_spmv_f)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes": nb, "launch_ms": 1000.0 * t_spmv,
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"},
+        "roofline": {k: rooflines[0][k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")},
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "clocks": ck,
         "e2e": e2e,

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 
+#include <type_traits>
+
 #include "amg.cuh"
 
 namespace ps_internal {
@@ -305,52 +307,73 @@ __global__ void k_rank_rows(int64_t n, const int32_t* __restrict__ rp, const int
 }
 
 // ---- SpGEMM C = X Y, one warp per row, shared-memory hash + sorted list ----
-constexpr int kHash = 2048;   // hash slots per warp
-constexpr int kUniq = 1024;   // distinct output columns per row
+// Rows are binned by capacity class C (at most C distinct output columns, 2C hash
+// slots) so that short rows -- most rows of A P on the fine levels -- use small
+// tables and many warps per SM; rows above the largest class use the dense path.
+constexpr int kUniq = 1024;   // largest class
 constexpr int kEmpty = -1;
+constexpr int kClasses = 4;
+__host__ __device__ constexpr int class_cap(int b) { return b == 0 ? 32 : b == 1 ? 128 : b == 2 ? 512 : 1024; }
 
+template <int H>
 __device__ __forceinline__ bool hash_insert(int32_t* tab, int32_t key, int* overflow) {
-  uint32_t h = (uint32_t(key) * 2654435761u) & (kHash - 1);
-  for (int probe = 0; probe < kHash; ++probe) {
+  uint32_t h = (uint32_t(key) * 2654435761u) & (H - 1);
+  for (int probe = 0; probe < H; ++probe) {
     int32_t prev = atomicCAS(&tab[h], kEmpty, key);
     if (prev == kEmpty) return true;
     if (prev == key) return false;
-    h = (h + 1) & (kHash - 1);
+    h = (h + 1) & (H - 1);
   }
   *overflow = 1;
   return false;
 }
 
-// collect the distinct columns of row i into tab; returns their count (all lanes)
+// collect the distinct columns of row i into tab (H slots); returns their count (all lanes)
+template <int H>
 __device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
                               const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci, int32_t* tab,
                               int lane, int* overflow) {
-  for (int t = lane; t < kHash; t += 32) tab[t] = kEmpty;
+  for (int t = lane; t < H; t += 32) tab[t] = kEmpty;
   __syncwarp();
   int cnt = 0;
   for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
     int32_t k = xci[q];
     for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32)
-      if (hash_insert(tab, yci[r], overflow)) ++cnt;
+      if (hash_insert<H>(tab, yci[r], overflow)) ++cnt;
   }
   __syncwarp();
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   return cnt;
 }
 
-// rows whose distinct columns exceed the shared-memory capacity are listed in
-// longrows[] and handled by the dense-accumulator kernels below
-__global__ void k_spgemm_count(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
-                               const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
-                               int32_t* __restrict__ cnt, uint8_t* __restrict__ islong,
-                               int32_t* __restrict__ longrows, int32_t* __restrict__ nlong) {
+// upper bound of the distinct columns of each row (the number of products) and its count class
+__global__ void k_spgemm_bound(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                               const int32_t* __restrict__ yrp, int32_t* __restrict__ lists,
+                               int32_t* __restrict__ counts) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t ub = 0;
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) ub += yrp[xci[q] + 1] - yrp[xci[q]];
+  int b = ub <= class_cap(0) ? 0 : ub <= class_cap(1) ? 1 : ub <= class_cap(2) ? 2 : 3;
+  lists[int64_t(b) * n + atomicAdd(&counts[b], 1)] = int32_t(i);
+}
+
+// rows listed in rows[0..nrows): exact distinct-column count with a table of 2C slots; rows
+// with more than kUniq columns (possible in the last class only) go to longrows[]
+template <int C>
+__global__ void k_spgemm_count(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                               const int32_t* __restrict__ xci, const int32_t* __restrict__ yrp,
+                               const int32_t* __restrict__ yci, int32_t* __restrict__ cnt,
+                               uint8_t* __restrict__ islong, int32_t* __restrict__ longrows,
+                               int32_t* __restrict__ nlong) {
   extern __shared__ int32_t smem[];
   int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
-  if (i >= n) return;
-  int32_t* tab = smem + wib * kHash;
+  int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (w >= nrows) return;
+  int64_t i = rows[w];
+  int32_t* tab = smem + wib * (2 * C);
   int ovf = 0;
-  int c = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
+  int c = spgemm_collect<2 * C>(i, xrp, xci, yrp, yci, tab, lane, &ovf);
   ovf = __any_sync(0xffffffffu, ovf);
   if (lane == 0) {
     bool lg = ovf || c > kUniq;
@@ -358,6 +381,16 @@ __global__ void k_spgemm_count(int64_t n, const int32_t* __restrict__ xrp, const
     islong[i] = lg ? 1 : 0;
     if (lg) longrows[atomicAdd(nlong, 1)] = int32_t(i);
   }
+}
+
+// fill classes from the exact counts (long rows, cnt = 0 and listed apart, are skipped)
+__global__ void k_spgemm_fill_bins(int64_t n, const int32_t* __restrict__ cnt, int32_t* __restrict__ lists,
+                                   int32_t* __restrict__ counts) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t u = cnt[i];
+  int b = u <= class_cap(0) ? 0 : u <= class_cap(1) ? 1 : u <= class_cap(2) ? 2 : 3;
+  lists[int64_t(b) * n + atomicAdd(&counts[b], 1)] = int32_t(i);
 }
 
 // dense path, one CTA per long row: stamp[j] marks the columns seen for this row
@@ -446,35 +479,39 @@ __global__ void k_spgemm_dense_fill(const int32_t* __restrict__ rows, int32_t nr
   }
 }
 
-template <int NC>
-__global__ void k_spgemm_fill(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
-                              const double* __restrict__ xv, const int32_t* __restrict__ yrp,
-                              const int32_t* __restrict__ yci, const double* __restrict__ yv,
-                              const int32_t* __restrict__ crp, int32_t* __restrict__ cci, double* __restrict__ cv,
-                              const uint8_t* __restrict__ islong, int* __restrict__ err) {
+template <int NC, int C>
+__global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                              const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                              const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                              const double* __restrict__ yv, const int32_t* __restrict__ crp,
+                              int32_t* __restrict__ cci, double* __restrict__ cv, const uint8_t* __restrict__ islong,
+                              int* __restrict__ err) {
   extern __shared__ unsigned char sraw[];
+  constexpr int H = 2 * C;
   int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
-  if (i >= n) return;
-  size_t per = size_t(kHash) * 4 + size_t(kUniq) * 4 + size_t(kUniq) * NC * 8;
+  int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (w >= nrows) return;
+  int64_t i = rows[w];
+  if (islong[i]) return;
+  constexpr size_t per = size_t(H) * 4 + size_t(C) * 4 + size_t(C) * NC * 8;
   unsigned char* base = sraw + per * wib;
   int32_t* tab = reinterpret_cast<int32_t*>(base);
-  int32_t* list = reinterpret_cast<int32_t*>(base + kHash * 4);
-  double* acc = reinterpret_cast<double*>(base + kHash * 4 + kUniq * 4);
+  int32_t* list = reinterpret_cast<int32_t*>(base + H * 4);
+  double* acc = reinterpret_cast<double*>(base + H * 4 + C * 4);
   int ovf = 0;
-  if (islong[i]) return;
-  int u = spgemm_collect(i, xrp, xci, yrp, yci, tab, lane, &ovf);
-  if (u > kUniq || __any_sync(0xffffffffu, ovf)) {
+  int u = spgemm_collect<H>(i, xrp, xci, yrp, yci, tab, lane, &ovf);
+  if (u > C || __any_sync(0xffffffffu, ovf)) {
     if (lane == 0) atomicExch(err, 1);
     return;
   }
-  // compact the table into list[0..u)
-  __shared__ int fill_ctr[8];
-  if (lane == 0) fill_ctr[wib] = 0;
-  __syncwarp();
-  for (int t = lane; t < kHash; t += 32) {
-    int32_t key = tab[t];
-    if (key != kEmpty) list[atomicAdd(&fill_ctr[wib], 1)] = key;
+  // compact the table into list[0..u) (the order is fixed by the sort below)
+  int pos = 0;
+  for (int t0 = 0; t0 < H; t0 += 32) {
+    int32_t key = tab[t0 + lane];
+    bool f = key != kEmpty;
+    unsigned mk = __ballot_sync(0xffffffffu, f);
+    if (f) list[pos + __popc(mk & ((1u << lane) - 1u))] = key;
+    pos += __popc(mk);
   }
   __syncwarp();
   // bitonic sort of list[0..P), P = next power of two >= u, padded with INT_MAX
@@ -596,22 +633,49 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
   if (t < n) b[t] = float(a[t]);
 }
 
+// launch f<C>(warps per block, dynamic shared bytes) for capacity class b
+template <class F>
+void for_class(int b, F&& f) {
+  switch (b) {
+    case 0: f(std::integral_constant<int, 32>()); break;
+    case 1: f(std::integral_constant<int, 128>()); break;
+    case 2: f(std::integral_constant<int, 512>()); break;
+    default: f(std::integral_constant<int, 1024>()); break;
+  }
+}
+
 template <int NC>
 ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int32_t* xci, const double* xv,
                  const int32_t* yrp, const int32_t* yci, const double* yv, int32_t** crp, int32_t** cci, double** cv,
                  int64_t* cnnz, int* d_err, cudaStream_t st) {
-  int32_t *cnt, *longrows, *nlong;
+  int32_t *cnt, *longrows, *nlong, *lists, *counts;
   uint8_t* islong;
   PS_TRY(ar.alloc(&cnt, n + 1));
   PS_TRY(ar.alloc(crp, n + 1));
   PS_TRY(ar.alloc(&islong, n + 1));
   PS_TRY(ar.alloc(&longrows, n + 1));
   PS_TRY(ar.alloc(&nlong, 1));
+  PS_TRY(ar.alloc(&lists, size_t(kClasses) * n + 1));
+  PS_TRY(ar.alloc(&counts, 2 * kClasses));
   PS_CUDA(cudaMemsetAsync(nlong, 0, sizeof(int32_t), st));
-  const int wpb_c = 4;
-  size_t sm_c = size_t(wpb_c) * kHash * 4;
-  PS_TICK(); k_spgemm_count<<<grid_for(n, wpb_c), 32 * wpb_c, sm_c, st>>>(n, xrp, xci, yrp, yci, cnt, islong, longrows,
-                                                                          nlong);
+  PS_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * kClasses, st));
+  // count pass, binned by the product bound
+  PS_TICK(); k_spgemm_bound<<<grid_for(n, 256), 256, 0, st>>>(n, xrp, xci, yrp, lists, counts);
+  int32_t hc[2 * kClasses];
+  PS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < kClasses; ++b) {
+    int32_t nr = hc[b];
+    if (nr == 0) continue;
+    const int32_t* rows = lists + int64_t(b) * n;
+    for_class(b, [&](auto cc) {
+      constexpr int C = decltype(cc)::value;
+      const int wpb = C <= 128 ? 8 : 4;
+      size_t sm = size_t(wpb) * 2 * C * 4;
+      PS_TICK(); k_spgemm_count<C><<<unsigned((nr + wpb - 1) / wpb), 32 * wpb, sm, st>>>(
+          rows, nr, xrp, xci, yrp, yci, cnt, islong, longrows, nlong);
+    });
+  }
   PS_CUDA(cudaGetLastError());
   int32_t hl = 0;
   PS_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -638,12 +702,26 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   *cnnz = tot;
   PS_TRY(ar.alloc(cci, size_t(tot) + 1));
   PS_TRY(ar.alloc(cv, (size_t(tot) + 1) * NC));
-  const int wpb = NC == 3 ? 2 : 4;
-  size_t per = size_t(kHash) * 4 + size_t(kUniq) * 4 + size_t(kUniq) * NC * 8;
-  size_t sm = per * wpb;
-  PS_CUDA(cudaFuncSetAttribute(k_spgemm_fill<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  PS_TICK(); k_spgemm_fill<NC><<<grid_for(n, wpb), 32 * wpb, sm, st>>>(n, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv,
-                                                                       islong, d_err);
+  // fill pass, binned by the exact count (long rows, whose count came from the dense pass, land in
+  // the last class and are skipped there by islong)
+  PS_CUDA(cudaMemsetAsync(counts + kClasses, 0, sizeof(int32_t) * kClasses, st));
+  PS_TICK(); k_spgemm_fill_bins<<<grid_for(n, 256), 256, 0, st>>>(n, cnt, lists, counts + kClasses);
+  PS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < kClasses; ++b) {
+    int32_t nr = hc[kClasses + b];
+    if (nr == 0) continue;
+    const int32_t* rows = lists + int64_t(b) * n;
+    for_class(b, [&](auto cc) {
+      constexpr int C = decltype(cc)::value;
+      const int wpb = C <= 128 ? 8 : (C <= 512 ? 4 : 2);
+      size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8;
+      size_t sm = per * wpb;
+      cudaFuncSetAttribute(k_spgemm_fill<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      PS_TICK(); k_spgemm_fill<NC, C><<<unsigned((nr + wpb - 1) / wpb), 32 * wpb, sm, st>>>(
+          rows, nr, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, islong, d_err);
+    });
+  }
   PS_CUDA(cudaGetLastError());
   for (int64_t b0 = 0; b0 < hl; b0 += B) {
     int32_t nb = int32_t(hl - b0 < B ? hl - b0 : B);
@@ -652,7 +730,8 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   }
   PS_CUDA(cudaGetLastError());
   if (stamp) { ar.release(stamp); ar.release(acc); }
-  ar.release(cnt); ar.release(islong); ar.release(longrows); ar.release(nlong);
+  ar.release(cnt); ar.release(islong); ar.release(longrows); ar.release(nlong); ar.release(lists);
+  ar.release(counts);
   return PS_OK;
 }
 
