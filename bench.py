@@ -38,6 +38,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="solve", choices=["solve", "batch", "serve"],
+                    help="solve: one config-2 solve per step (default); batch: the 64 uneven config-3 systems; "
+                         "serve: a Poisson request trace (config 4)")
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests in the trace")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate, requests/s")
+    ap.add_argument("--slots", type=int, default=8, help="batch/serve: requests in flight at once")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling only: stop FGMRES after this many iterations (bounded ncu launch lists)")
     return ap.parse_args()
@@ -485,10 +491,156 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched (config 3) and served (config 4) workloads through the request server
+# ---------------------------------------------------------------------------
+def batch_sizes(count=64, seed=3000):
+    """nx, ny ~ U{16..48} and nz ~ U{8..24}, independently (config-3 size draw)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(16, 49)), int(rng.integers(16, 49)), int(rng.integers(8, 25))) for _ in range(count)]
+
+
+def serve_sizes(count, seed=4999):
+    """N ~ log-U[8k, 500k] cells with nx = ny = 2 nz, nz = round((N/4)^(1/3)) (config-4 size draw)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        N = float(np.exp(rng.uniform(np.log(8e3), np.log(5e5))))
+        nz = max(2, int(round((N / 4.0) ** (1.0 / 3.0))))
+        out.append((2 * nz, 2 * nz, nz))
+    return out
+
+
+def percentile(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_server_trace(ps, torch, systems, trace, slots, budget, precision, tol=TOL):
+    """Submits each request (system index, arrival time, rhs count) at its arrival time; returns
+    per-request infos and the makespan.  Right-hand sides and solutions live on the device only while
+    their request is in flight."""
+    import threading
+    import numpy as np
+    params = ps.ps_params_default(precision=precision)
+    srv = ps.ps_server_create(slots, budget, params)
+    done = []
+    pending = []
+    lock = threading.Lock()
+    cv = threading.Condition(lock)
+    finished = [False]
+
+    def waiter():
+        k = 0
+        while True:
+            with cv:
+                while k >= len(pending) and not finished[0]:
+                    cv.wait()
+                if k >= len(pending):
+                    return
+                t, bufs = pending[k]
+            st, info = ps.ps_server_wait(srv, t)
+            done.append((st, info))
+            with cv:
+                pending[k] = None
+            k += 1
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    rng = np.random.default_rng(4000)
+    t0 = ps.ps_server_clock(srv)
+    for (si, t_arr, nrhs) in trace:
+        s = systems[si].contents
+        rhs = [torch.from_numpy(rng.uniform(-1.0, 1.0, s.n)).cuda() for _ in range(nrhs)]
+        xs = [torch.empty(s.n, dtype=torch.float64, device="cuda") for _ in range(nrhs)]
+        torch.cuda.current_stream().synchronize()
+        while ps.ps_server_clock(srv) - t0 < t_arr:
+            time.sleep(min(0.002, max(0.0, t_arr - (ps.ps_server_clock(srv) - t0))))
+        t = ps.ps_server_submit(srv, s.jac, s.grid, [r.data_ptr() for r in rhs], [x.data_ptr() for x in xs], tol,
+                                t0 + t_arr)
+        with cv:
+            pending.append((t, (rhs, xs)))
+            cv.notify()
+    with cv:
+        finished[0] = True
+        cv.notify()
+    th.join()
+    info = ps.ps_server_info_get(srv)
+    ps.ps_server_destroy(srv)
+    infos = [i for _, i in done]
+    statuses = [st for st, _ in done]
+    makespan = max(i.t_end for i in infos) - t0
+    return infos, statuses, makespan, info
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1812_05540_gb300 import _build
+    _build.build()
+    import paper_1812_05540_gb300 as ps
+    if args.workload == "batch":
+        sizes = batch_sizes()
+        trace = [(i, 0.0, 1) for i in range(len(sizes))]
+        budget = 0
+        label = "64 independent config-1-statistics Jacobians, nx,ny ~ U{16..48}, nz ~ U{8..24}"
+    else:
+        pool = 64
+        sizes = serve_sizes(pool)
+        rng = np.random.default_rng(4999)
+        t = 0.0
+        trace = []
+        for r in range(args.requests):
+            t += float(rng.exponential(1.0 / args.rate))
+            trace.append((r % pool, t, int(np.random.default_rng(4000 + r).integers(1, 5))))
+        budget = 120 * 10**9
+        label = ("Poisson trace, %d requests at %.0f/s; sizes log-U[8k, 500k] cells (pool of %d seeded systems), "
+                 "1-4 RHS per request" % (args.requests, args.rate, pool))
+    systems = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        gp = ps.ps_gen_default(1, nx=nx, ny=ny, nz=nz, seed=(3000 if args.workload == "batch" else 4000) + i)
+        systems.append(ps.ps_generate(gp))
+    torch.cuda.synchronize()
+    # warm-up: the smallest system once through the server (pool, kernels, streams)
+    small = int(np.argmin([sz[0] * sz[1] * sz[2] for sz in sizes]))
+    run_server_trace(ps, torch, systems, [(small, 0.0, 1)], 1, 0, ps.PS_MIXED_FP32)
+    infos, sts, makespan, sinfo = run_server_trace(ps, torch, systems, trace, args.slots, budget, ps.PS_MIXED_FP32)
+    lat = [i.t_end - i.t_arrival for i in infos]
+    solves = sum(i.nrhs for i in infos)
+    ok = all(st == ps.PS_OK for st in sts) and max(i.worst_relres for i in infos) <= TOL
+    # baseline: the same trace one request at a time in FP64
+    b_infos, b_sts, b_makespan, _ = run_server_trace(ps, torch, systems, trace, 1, budget, ps.PS_FP64)
+    b_lat = [i.t_end - i.t_arrival for i in b_infos]
+    b_solves = sum(i.nrhs for i in b_infos)
+    for sp in systems:
+        ps.ps_system_free(sp)
+    dofs = [3 * (a + 1) * (b + 1) * (c + 1) + 2 * a * b * c for a, b, c in sizes]
+    line = {"metric": "served solves/s, p50/p99 latency" if args.workload == "serve" else
+            "batched solves/s, 64 uneven systems", "value": solves / makespan, "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": label, "slots": args.slots, "hbm_budget": budget, "tol": TOL,
+                       "dof_min": min(dofs), "dof_max": max(dofs)},
+            "requests": len(infos), "solves": solves, "makespan_s": makespan,
+            "latency_s": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "max": max(lat)},
+            "all_converged": ok, "worst_relres": max(i.worst_relres for i in infos),
+            "iters_total": sum(i.iters for i in infos),
+            "max_inflight_requests": sinfo.max_inflight_requests, "max_inflight_gb": sinfo.max_inflight_bytes / 1e9,
+            "fp64_one_at_a_time": {"value": b_solves / b_makespan, "unit": "solves/s", "makespan_s": b_makespan,
+                                   "latency_s": {"p50": percentile(b_lat, 50), "p99": percentile(b_lat, 99)},
+                                   "all_converged": all(st == ps.PS_OK for st in b_sts)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "solve":
+        run_workload(args)
     else:
         run_ours(args)
 

@@ -190,6 +190,54 @@ ps_status ps_residual_noalloc(const ps_jacobian* jac, const ps_grid* grid, const
 /* Frees everything the handle owns (synchronises its stream). */
 void ps_free(ps_handle* h);
 
+/* ---- request server: many independent solves in flight (batched and served workloads) ----
+   A server runs whole requests -- ps_setup, one ps_solve per right-hand side, ps_free -- on `slots`
+   worker threads, each with its own CUDA stream, so requests overlap on the device.  Requests are
+   admitted first come, first served when a worker is idle and the estimated device bytes of the
+   request's handle (ps_setup_bytes_estimate) fit under hbm_budget next to the requests in flight.
+   The paper solves one system at a time (§5.4); this is the batching/serving layer around that
+   solve, with the same kernels, so a request gives the same x alone and in the mix. */
+typedef struct ps_server ps_server;
+typedef struct {
+  int32_t slots;          /* requests in flight at once (worker threads / CUDA streams), 1..256 */
+  int64_t hbm_budget;     /* bytes of handles in flight at once, by estimate; 0 = unlimited */
+  ps_params params;       /* solver parameters of every request (params.stream is ignored) */
+} ps_server_params;
+typedef struct {
+  uint64_t ticket;
+  ps_status status;                  /* first failing status of the request's setup or solves */
+  int32_t nrhs, iters;               /* iterations summed over the right-hand sides */
+  double worst_relres;               /* largest true FP64 relative residual over the right-hand sides */
+  double t_arrival, t_start, t_end;  /* seconds on the server clock (ps_server_clock) */
+  int64_t bytes;                     /* device bytes the request's handle held */
+} ps_request_info;
+typedef struct {
+  int64_t submitted, completed;
+  int64_t max_inflight_bytes;        /* largest sum of admitted estimates seen */
+  int64_t max_inflight_requests;
+} ps_server_info;
+
+/* Device bytes a handle for this Jacobian will hold (estimate with a 20 % margin). */
+int64_t ps_setup_bytes_estimate(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params);
+/* Starts the worker threads on the current device.  Errors: PS_ERR_INVALID. */
+ps_status ps_server_create(const ps_server_params* params, ps_server** out);
+/* Seconds since ps_server_create (steady clock). */
+double ps_server_clock(const ps_server* s);
+/* Queues one request: nrhs right-hand sides rhs[k] and solutions x[k] (device pointers, or host pointers
+   with params.host_ptrs = 1), relative tolerance tol; t_arrival (server clock, < 0 = now) is the
+   arrival time its latency is measured from.  The caller keeps every array of *jac, rhs[k] and x[k]
+   alive and untouched until ps_server_wait returns for the ticket.  Errors: PS_ERR_INVALID,
+   PS_ERR_BUDGET (estimate above hbm_budget; nothing queued). */
+ps_status ps_server_submit(ps_server* s, const ps_jacobian* jac, const ps_grid* grid, int32_t nrhs,
+                           const double* const* rhs, double* const* x, double tol, double t_arrival,
+                           uint64_t* ticket);
+/* Blocks until the request is done, fills *info (may be NULL) and returns its status; the ticket is
+   then forgotten. */
+ps_status ps_server_wait(ps_server* s, uint64_t ticket, ps_request_info* info);
+ps_status ps_server_info_get(ps_server* s, ps_server_info* info);
+/* Runs every queued request to completion, then stops the workers and frees the server. */
+void ps_server_destroy(ps_server* s);
+
 /* ---- seeded synthetic Jacobian generator (test input; §6 physics) ---- */
 enum { PS_FIELDS_LOGNORMAL = 0, PS_FIELDS_LAYERED = 1, PS_FIELDS_CHANNELS = 2,
        PS_FIELDS_HOMOGENEOUS = 3 };

@@ -59,6 +59,21 @@ class ps_stats(C.Structure):
                 ("ms_flow24", C.c_float), ("ms_vcycle_p", C.c_float), ("ms_ilu", C.c_float)]
 
 
+class ps_server_params(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("hbm_budget", C.c_int64), ("params", ps_params)]
+
+
+class ps_request_info(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int32), ("nrhs", C.c_int32), ("iters", C.c_int32),
+                ("worst_relres", C.c_double), ("t_arrival", C.c_double), ("t_start", C.c_double),
+                ("t_end", C.c_double), ("bytes", C.c_int64)]
+
+
+class ps_server_info(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("max_inflight_bytes", C.c_int64),
+                ("max_inflight_requests", C.c_int64)]
+
+
 class ps_gen_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
                 ("seed", C.c_uint64), ("field_kind", C.c_int32), ("flags", C.c_uint32),
@@ -116,6 +131,19 @@ def lib():
         L.ps_system_free.restype = None
         L.ps_residual_noalloc.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
+        S = C.c_void_p
+        L.ps_setup_bytes_estimate.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.POINTER(ps_params)]
+        L.ps_setup_bytes_estimate.restype = C.c_int64
+        L.ps_server_create.argtypes = [C.POINTER(ps_server_params), C.POINTER(S)]
+        L.ps_server_clock.argtypes = [S]
+        L.ps_server_clock.restype = C.c_double
+        L.ps_server_submit.argtypes = [S, C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.c_int32,
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double, C.c_double,
+                                       C.POINTER(C.c_uint64)]
+        L.ps_server_wait.argtypes = [S, C.c_uint64, C.POINTER(ps_request_info)]
+        L.ps_server_info_get.argtypes = [S, C.POINTER(ps_server_info)]
+        L.ps_server_destroy.argtypes = [S]
+        L.ps_server_destroy.restype = None
         L.ps_launch_count.argtypes = []
         L.ps_launch_count.restype = C.c_int64
         L.ps_strerror.argtypes = [C.c_int]
@@ -250,3 +278,47 @@ def ps_flow_copy(h, nnzb, ncells):
 def bsr(n_brow, n_bcol, br, bc, rowptr, colind, val, nnzb):
     """ps_bsr from three pointers (ints)."""
     return ps_bsr(n_brow, n_bcol, nnzb, br, bc, rowptr, colind, val)
+
+
+# ---- request server ----
+def ps_setup_bytes_estimate(jac, grid, params):
+    return lib().ps_setup_bytes_estimate(C.byref(jac), C.byref(grid), C.byref(params))
+
+
+def ps_server_create(slots, hbm_budget=0, params=None):
+    sp = ps_server_params(slots, hbm_budget, params if params is not None else ps_params_default())
+    s = C.c_void_p()
+    _check(lib().ps_server_create(C.byref(sp), C.byref(s)), "ps_server_create")
+    return s
+
+
+def ps_server_clock(s):
+    return lib().ps_server_clock(s)
+
+
+def ps_server_submit(s, jac, grid, rhs_ptrs, x_ptrs, tol, t_arrival=-1.0):
+    """rhs_ptrs, x_ptrs: lists of device (or host) addresses, one per right-hand side."""
+    k = len(rhs_ptrs)
+    R = (C.c_void_p * k)(*rhs_ptrs)
+    X = (C.c_void_p * k)(*x_ptrs)
+    t = C.c_uint64()
+    _check(lib().ps_server_submit(s, C.byref(jac), C.byref(grid), k, R, X, tol, t_arrival, C.byref(t)),
+           "ps_server_submit")
+    return t.value
+
+
+def ps_server_wait(s, ticket):
+    """Returns (status, ps_request_info)."""
+    info = ps_request_info()
+    st = lib().ps_server_wait(s, ticket, C.byref(info))
+    return st, info
+
+
+def ps_server_info_get(s):
+    info = ps_server_info()
+    _check(lib().ps_server_info_get(s, C.byref(info)), "ps_server_info_get")
+    return info
+
+
+def ps_server_destroy(s):
+    lib().ps_server_destroy(s)

@@ -648,6 +648,9 @@ ps_status mgs_grid(int* blocks) {
 bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part, int blocks,
               unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, cudaStream_t st) {
   if (blocks <= 0) return false;
+  // small systems use fewer CTAs (at least 16 rows per thread) so that concurrent requests overlap
+  int64_t want = (n + int64_t(kMgsThreads) * 16 - 1) / (int64_t(kMgsThreads) * 16);
+  if (want < blocks) blocks = int(want < 1 ? 1 : want);
   unsigned long long b0 = *base;
   double* h = K.h1;
   double* sc = K.sc;

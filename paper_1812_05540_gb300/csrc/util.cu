@@ -8,25 +8,23 @@
 namespace ps_internal {
 
 std::atomic<int64_t> g_launches{0};
-static std::string g_last_error;
-static std::mutex g_err_mu;
+// per host thread, so that concurrent requests of the server keep their own messages
+static thread_local std::string g_last_error;
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
-  std::lock_guard<std::mutex> lk(g_err_mu);
   char buf[512];
   snprintf(buf, sizeof(buf), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line, cudaGetErrorString(e));
   g_last_error = buf;
 }
 const std::string& last_error() { return g_last_error; }
 
-static std::string g_reason;
+static thread_local std::string g_reason;
 void set_reason(const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
-  std::lock_guard<std::mutex> lk(g_err_mu);
   g_reason = buf;
 }
 const std::string& last_reason() { return g_reason; }

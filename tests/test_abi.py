@@ -27,7 +27,8 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match_abi():
     import paper_1812_05540_gb300 as ps
     for n in ("ps_setup", "ps_setup_flow", "ps_solve", "ps_free", "ps_generate", "ps_system_free", "ps_spmv",
-              "ps_apply_prec", "ps_strerror", "ps_params_default", "ps_gen_default"):
+              "ps_apply_prec", "ps_strerror", "ps_params_default", "ps_gen_default", "ps_server_create",
+              "ps_server_submit", "ps_server_wait", "ps_server_destroy", "ps_setup_bytes_estimate"):
         assert callable(getattr(ps, n))
 
 
@@ -40,8 +41,9 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "ps.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ps_grid), sizeof(ps_bsr), sizeof(ps_jacobian),
-         sizeof(ps_params), sizeof(ps_stats), sizeof(ps_gen_params), sizeof(ps_system), (size_t)0);
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ps_grid), sizeof(ps_bsr), sizeof(ps_jacobian),
+         sizeof(ps_params), sizeof(ps_stats), sizeof(ps_gen_params), sizeof(ps_system),
+         sizeof(ps_server_params), sizeof(ps_request_info), sizeof(ps_server_info));
   return 0;
 }
 '''
@@ -52,5 +54,6 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         sizes = [int(v) for v in subprocess.check_output([exe]).split()]
     mine = [ctypes.sizeof(t) for t in (ps.ps_grid, ps.ps_bsr, ps.ps_jacobian, ps.ps_params, ps.ps_stats,
-                                       ps.ps_gen_params, ps.ps_system)]
-    assert sizes[:7] == mine
+                                       ps.ps_gen_params, ps.ps_system, ps.ps_server_params, ps.ps_request_info,
+                                       ps.ps_server_info)]
+    assert sizes == mine
