@@ -106,6 +106,11 @@ typedef struct {
   int32_t test_stall_gs;      /* testing only, 0 = off: k > 0 makes CTA k-1 of the Gram-Schmidt
                                  launch skip its work, so the grid barrier waits of the others run
                                  out and ps_solve returns PS_ERR_TIMEOUT (no fault, no hang) */
+  int32_t ortho_sweep;        /* PS_ORTHO_MGS: basis vectors projected out per sweep over the rows
+                                 (1, 2, 4 or 8; default 8).  The coefficients equal those of
+                                 one-vector-at-a-time modified Gram-Schmidt in exact arithmetic
+                                 (forward substitution with the in-block Gram entries); larger
+                                 sweeps need fewer grid barriers */
 } ps_params;
 
 typedef struct {

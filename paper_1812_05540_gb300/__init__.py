@@ -47,7 +47,7 @@ class ps_params(C.Structure):
                 ("coarse_max_u", C.c_int32), ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32),
                 ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
                 ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
-                ("ortho", C.c_int32), ("test_stall_gs", C.c_int32)]
+                ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32)]
 
 
 class ps_stats(C.Structure):

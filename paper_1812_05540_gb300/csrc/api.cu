@@ -1,4 +1,5 @@
 // C ABI: setup phase, Algorithm 1 and the flexible-GMRES iteration phase.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -55,7 +56,7 @@ struct ps_handle {
   double* hsc = nullptr;  // pinned: 8 scalars
   int* hflag = nullptr;   // pinned: Krylov flags [0..2], ILU error [3]
   // modified Gram-Schmidt launch: CTAs (0 = not possible), ticket barrier counter and its base
-  int mgs_blocks = 0;
+  int mgs_blocks[4] = {0, 0, 0, 0};
   double* mgs_part = nullptr;
   unsigned long long* mgs_bar = nullptr;
   unsigned long long mgs_base = 0;
@@ -256,9 +257,11 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(ar.alloc(&K.sc, 16)); PS_TRY(ar.alloc(&K.flag, 4));
   PS_CUDA(cudaMemsetAsync(K.flag, 0, 4 * sizeof(int), st));
   if (h->prm.ortho == PS_ORTHO_MGS) {
-    PS_TRY(mgs_grid(&h->mgs_blocks));
-    if (h->mgs_blocks > 0) {
-      PS_TRY(ar.alloc(&h->mgs_part, size_t(2) * h->mgs_blocks));
+    PS_TRY(mgs_grid(h->mgs_blocks));
+    int mb = std::max(std::max(h->mgs_blocks[0], h->mgs_blocks[1]), std::max(h->mgs_blocks[2], h->mgs_blocks[3]));
+    if (mb > 0) {
+      PS_TRY(ar.alloc(&h->mgs_part, size_t(mgs_partials()) * mb));
+      PS_TRY(ar.alloc(&K.gram, size_t(m + 1) * mgs_gram_stride()));
       PS_TRY(ar.alloc(&h->mgs_bar, 1));
       PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
       h->mgs_base = 0;
@@ -290,6 +293,7 @@ void ps_params_default(ps_params* p) {
   p->max_levels = 25;
   p->ilu_mode = PS_ILU_PENCIL;
   p->spin_limit = 2000000;
+  p->ortho_sweep = 8;
 }
 
 ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params, ps_handle** out) {
@@ -416,7 +420,7 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
         cudaEventRecord(h->ev[2], st);
         if (h->prm.ortho == PS_ORTHO_MGS &&
             mgs_step(h->V, n, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
-                     h->prm.test_stall_gs, st)) {
+                     h->prm.test_stall_gs, h->prm.ortho_sweep, st)) {
           // modified Gram-Schmidt (w normalised in the same launch)
           arnoldi_finish(K, m, j, st);
         } else {

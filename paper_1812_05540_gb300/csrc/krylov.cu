@@ -454,21 +454,33 @@ __global__ void k_hsolve(const double* H, const double* g, double* y, int m, int
 }
 
 // ---------------------------------------------------------------------------
-// Arnoldi step by modified Gram-Schmidt in one cooperative launch: for
-// k = 0..j, h_k = v_k . w and w -= h_k v_k; then h_{j+1} = ||w|| and
-// v_{j+1} = w / h_{j+1}.  Pass k fuses the update by v_{k-1} with the dot by
-// v_k, so each pass is one sweep over the rows (two FP64 FMAs per row and
-// column, the least the method needs).  Every thread keeps the same rows in
-// every pass, so w needs no synchronisation; each pass ends with a grid barrier
-// (bounded ticket counter) after which every CTA sums the CTA partials in the
-// same fixed order, so all CTAs hold bit-identical h_k.
+// Arnoldi step by modified Gram-Schmidt in one cooperative launch, kS basis
+// vectors per sweep.  Modified Gram-Schmidt takes, for k = 0..j in turn,
+// h_k = v_k . w_k and w_{k+1} = w_k - h_k v_k.  Expanding w_k over one block B
+// of consecutive k gives h_k = v_k . w_B - sum_{l in B, l < k} h_l (v_k . v_l):
+// the same coefficients follow from the dots of the block's vectors with the w
+// at the block start and the in-block Gram entries v_k . v_l, by a forward
+// substitution.  So sweep p forms the block's dots (and, in the last block, the
+// Gram entries of the newest vector v_j with its block-mates; older entries are
+// kept from the launches that created them), and also applies the update of the
+// previous block, whose coefficients the grid barrier between sweeps made known.
+// Each sweep costs two FP64 FMAs per row and basis vector, as plain modified
+// Gram-Schmidt does, with one grid barrier per kS vectors instead of one per
+// vector.  After the last sweep, h_{j+1} = ||w|| and v_{j+1} = w / h_{j+1}.
+// Every thread keeps the same rows in every sweep, so w needs no
+// synchronisation; after each barrier every CTA sums the CTA partials in one
+// fixed order, so all CTAs hold bit-identical coefficients.
 // ---------------------------------------------------------------------------
 constexpr int kMgsThreads = 256;
+constexpr int kS = 8;            // most basis vectors per sweep (row stride of the Gram store)
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // all CTAs arrive, then wait until the counter reaches target; false (and *err set) when the
@@ -478,8 +490,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(ctr, 1ull);
+    red_release_add(ctr, 1ull);
     int good = 1;
     int64_t it = 0;
     while (ld_acquire_u64(ctr) < target) {
@@ -489,76 +500,171 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
         break;
       }
     }
-    __threadfence();
     ok = good;
   }
   __syncthreads();
   return ok != 0;
 }
 
-__global__ void __launch_bounds__(kMgsThreads) k_mgs(const double* __restrict__ V, int64_t ldv, int j,
+// Gm[k * kS + (l - S * (k / S))] = v_k . v_l for the block-mates l < k of v_k (S vectors per sweep).
+template <int S>
+__global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const double* __restrict__ V, int64_t ldv, int j,
                                                      double* __restrict__ w, int64_t n, double* __restrict__ h,
-                                                     double* __restrict__ sc, int* __restrict__ flag,
-                                                     double* __restrict__ part, unsigned long long* bar,
-                                                     unsigned long long base, int64_t limit, int stall) {
+                                                     double* __restrict__ Gm, double* __restrict__ sc,
+                                                     int* __restrict__ flag, double* __restrict__ part,
+                                                     unsigned long long* bar, unsigned long long base, int64_t limit,
+                                                     int stall) {
   // test hook: CTA stall - 1 never arrives, so the others' bounded barrier waits run out
   if (stall > 0 && int(blockIdx.x) == stall - 1) return;
-  __shared__ double red[kMgsThreads / 32];
-  __shared__ double hs;
+  constexpr int R = 2 * S;  // partial sums per sweep: S dots, S - 1 Gram entries, ||w||^2 (last slot)
+  __shared__ double red[kMgsThreads / 32][R];
+  __shared__ double sums[R];
+  __shared__ double scratch[kMgsThreads / 16];
   const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t stride = int64_t(G) * kMgsThreads, t0 = int64_t(blockIdx.x) * kMgsThreads + threadIdx.x;
   int* err = flag + 2;
-  double hk = 0.0;
-  for (int k = 0; k <= j + 1; ++k) {
-    const double* vp = V + int64_t(k > 0 ? k - 1 : 0) * ldv;  // v_{k-1}: last use
-    const double* vk = V + int64_t(k <= j ? k : 0) * ldv;      // v_k
-    double acc = 0.0;
-    if (k == 0) {
-#pragma unroll 4
-      for (int64_t e = t0; e < n; e += stride) acc = fma(vk[e], w[e], acc);
-    } else if (k <= j) {
-#pragma unroll 4
+  const int nb = j / S + 1;  // blocks of basis vectors 0..j
+  double hp[S];              // coefficients of the previous block
+  int pc0 = 0, pcn = 0;      // previous block: first column and size
+#pragma unroll
+  for (int c = 0; c < S; ++c) hp[c] = 0.0;
+  double wn2 = 0.0;
+  for (int p = 0; p <= nb; ++p) {
+    const int c0 = p * S;
+    const int cn = p < nb ? min(S, j + 1 - c0) : 0;  // vectors dotted in this sweep
+    const bool last = p == nb - 1;
+    const int ng = last ? cn - 1 : 0;                // Gram entries of v_j with its block-mates
+    const double* vprev[S];
+    const double* vcur[S];
+#pragma unroll
+    for (int c = 0; c < S; ++c) {
+      vprev[c] = V + int64_t(pc0 + (c < pcn ? c : 0)) * ldv;
+      vcur[c] = V + int64_t(c0 + (c < cn ? c : 0)) * ldv;
+    }
+    const double* vjp = V + int64_t(j) * ldv;
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    if (p < nb && pcn == S && cn == S && ng == 0) {
+      // full blocks: update by the previous block, dots with this one
+#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
       for (int64_t e = t0; e < n; e += stride) {
-        double we = fma(-hk, __ldcs(vp + e), w[e]);
+        double we = w[e];
+#pragma unroll
+        for (int c = 0; c < S; ++c) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
         w[e] = we;
-        acc = fma(vk[e], we, acc);
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[c] = fma(vcur[c][e], we, acc[c]);
+      }
+    } else if (p < nb && pcn == 0 && cn == S && ng == 0) {
+      // first sweep: dots only
+#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
+      for (int64_t e = t0; e < n; e += stride) {
+        const double we = w[e];
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc[c] = fma(vcur[c][e], we, acc[c]);
+      }
+    } else if (p == nb && pcn == S) {
+      // last sweep after a full block: update and ||w||^2
+#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
+      for (int64_t e = t0; e < n; e += stride) {
+        double we = w[e];
+#pragma unroll
+        for (int c = 0; c < S; ++c) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
+        w[e] = we;
+        acc[R - 1] = fma(we, we, acc[R - 1]);
       }
     } else {
-#pragma unroll 4
+      // partial blocks (the block holding v_j, and the update by it)
+#pragma unroll 2
       for (int64_t e = t0; e < n; e += stride) {
-        double we = fma(-hk, __ldcs(vp + e), w[e]);
-        w[e] = we;
-        acc = fma(we, we, acc);
+        double we = w[e];
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+          if (c < pcn) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
+        if (pcn > 0) w[e] = we;
+        if (p < nb) {
+          const double vj = ng > 0 ? vjp[e] : 0.0;
+#pragma unroll
+          for (int c = 0; c < S; ++c)
+            if (c < cn) {
+              const double v = vcur[c][e];
+              acc[c] = fma(v, we, acc[c]);
+              if (c < ng) acc[S + c] = fma(v, vj, acc[S + c]);
+            }
+        } else {
+          acc[R - 1] = fma(we, we, acc[R - 1]);
+        }
       }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) red[wid] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int q = 0; q < kMgsThreads / 32; ++q) s += red[q];
-      part[(k & 1) * G + blockIdx.x] = s;
+    // CTA partials of the sweep's sums
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double v = warp_sum(acc[r]);
+      if (lane == 0) red[wid][r] = v;
     }
-    if (!grid_barrier(bar, base + (unsigned long long)(k + 1) * G, limit, err)) return;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < G; i += kMgsThreads) s += __ldcg(part + (k & 1) * G + i);
-    s = warp_sum(s);
-    if (lane == 0) red[wid] = s;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < R) {
       double t = 0.0;
-      for (int q = 0; q < kMgsThreads / 32; ++q) t += red[q];
-      hs = t;
+      for (int q = 0; q < kMgsThreads / 32; ++q) t += red[q][threadIdx.x];
+      part[(int64_t(p & 1) * R + threadIdx.x) * G + blockIdx.x] = t;
+    }
+    if (!grid_barrier(bar, base + (unsigned long long)(p + 1) * G, limit, err)) return;
+    // every CTA sums the G partials of each quantity in the same order: kMgsThreads / R threads per
+    // quantity, each a strided share, then a fixed shuffle tree and a fixed sum over the warps
+    {
+      constexpr int TPQ = kMgsThreads / R;
+      const int r = threadIdx.x / TPQ, sub = threadIdx.x % TPQ;
+      const double* pp = part + (int64_t(p & 1) * R + r) * G;
+      double t = 0.0;
+      for (int i = sub; i < G; i += TPQ) t += __ldcg(pp + i);
+      constexpr int W = TPQ < 32 ? TPQ : 32;
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, W);
+      if (sub % W == 0) scratch[threadIdx.x / W] = t;
+      __syncthreads();
+      if (threadIdx.x < R) {
+        constexpr int PW = TPQ / W;  // groups of W threads per quantity
+        double u = 0.0;
+        for (int q = 0; q < PW; ++q) u += scratch[threadIdx.x * PW + q];
+        sums[threadIdx.x] = u;
+      }
     }
     __syncthreads();
-    hk = hs;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (k <= j) h[k] = hk;
-      else { sc[1] = hk; flag[0] = 0; }
+    if (p < nb) {
+      // forward substitution with the in-block Gram entries (the same in every thread)
+#pragma unroll
+      for (int c = 0; c < S; ++c) {
+        if (c >= cn) { hp[c] = 0.0; continue; }
+        double hk = sums[c];
+        const int k = c0 + c;
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          if (l >= c) break;
+          double g = (k == j) ? sums[S + l] : __ldcg(Gm + int64_t(k) * kS + l);
+          hk -= hp[l] * g;
+        }
+        hp[c] = hk;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < S; ++c)
+          if (c < cn) h[c0 + c] = hp[c];
+        for (int l = 0; l < ng; ++l) Gm[int64_t(j) * kS + l] = sums[S + l];
+      }
+      pc0 = c0;
+      pcn = cn;
+    } else {
+      wn2 = sums[R - 1];
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc[1] = wn2;
+        flag[0] = 0;
+      }
     }
+    __syncthreads();  // sums[] and red[] are rewritten in the next sweep
   }
-  // hk = ||w||^2; the same reciprocal as the Arnoldi finish step computes
-  double hn = sqrt(hk);
+  // the same reciprocal as the Arnoldi finish step computes
+  double hn = sqrt(wn2);
   double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   for (int64_t e = t0; e < n; e += stride) w[e] *= inv;
 }
@@ -635,33 +741,47 @@ void scale_vec(const double* x, double* y, int64_t n, const double* scale, cudaS
 void fill_zero(double* x, int64_t n, cudaStream_t st) { PS_TICK(); k_zero<<<kVecBlocks, 256, 0, st>>>(x, n); }
 
 ps_status mgs_grid(int* blocks) {
-  int dev = 0, sms = 0, occ = 0;
+  // blocks[i]: co-resident CTAs of the sweep width 1 << i (1, 2, 4, 8), 0 without cooperative launch
+  int dev = 0, sms = 0, coop = 0;
   PS_CUDA(cudaGetDevice(&dev));
   PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int coop = 0;
   PS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mgs, kMgsThreads, 0));
-  *blocks = coop ? sms * std::min(occ, 4) : 0;
+  const void* fns[4] = {(const void*)k_mgs<1>, (const void*)k_mgs<2>, (const void*)k_mgs<4>, (const void*)k_mgs<8>};
+  for (int i = 0; i < 4; ++i) {
+    int occ = 0;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[i], kMgsThreads, 0));
+    blocks[i] = coop ? sms * std::min(occ, 4) : 0;
+  }
   return PS_OK;
 }
 
-bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part, int blocks,
-              unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, cudaStream_t st) {
+int mgs_gram_stride() { return kS; }
+int mgs_partials() { return 4 * kS; }
+
+bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part,
+              const int* blocks_by_sweep,
+              unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, int sweep,
+              cudaStream_t st) {
+  const int S = sweep >= 8 ? 8 : sweep >= 4 ? 4 : sweep >= 2 ? 2 : 1;
+  int blocks = blocks_by_sweep[S == 8 ? 3 : S == 4 ? 2 : S == 2 ? 1 : 0];
   if (blocks <= 0) return false;
   // small systems use fewer CTAs (at least 16 rows per thread) so that concurrent requests overlap
   int64_t want = (n + int64_t(kMgsThreads) * 16 - 1) / (int64_t(kMgsThreads) * 16);
   if (want < blocks) blocks = int(want < 1 ? 1 : want);
   unsigned long long b0 = *base;
   double* h = K.h1;
+  double* Gm = K.gram;
   double* sc = K.sc;
   int* flag = K.flag;
-  void* args[] = {&V, &ldv, &j, &w, &n, &h, &sc, &flag, &part, &bar, &b0, &limit, &stall};
-  if (cudaLaunchCooperativeKernel((const void*)k_mgs, blocks, kMgsThreads, args, 0, st) != cudaSuccess) {
+  void* args[] = {&V, &ldv, &j, &w, &n, &h, &Gm, &sc, &flag, &part, &bar, &b0, &limit, &stall};
+  const void* fn = S == 8 ? (const void*)k_mgs<8> : S == 4 ? (const void*)k_mgs<4> : S == 2 ? (const void*)k_mgs<2>
+                                                                                     : (const void*)k_mgs<1>;
+  if (cudaLaunchCooperativeKernel(fn, blocks, kMgsThreads, args, 0, st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   PS_TICK();
-  *base = b0 + (unsigned long long)(j + 2) * blocks;
+  *base = b0 + (unsigned long long)(j / S + 2) * blocks;
   return true;
 }
 

@@ -41,18 +41,24 @@ void scale_vec(const double* x, double* y, int64_t n, const double* scale, cudaS
 void fill_zero(double* x, int64_t n, cudaStream_t st);
 
 // small dense FGMRES state on the device (declared below); modified Gram-Schmidt step in one
-// cooperative launch: h1[0..j] = dots, sc[1] = ||w||^2 after projection, w normalised in place,
-// flag[0] = 0; a grid barrier that gives up sets flag[2].  Returns false when the launch is not
-// possible (blocks = 0 or a cooperative-launch error): the caller falls back to CGS2.
+// cooperative launch: h1[0..j] = coefficients, sc[1] = ||w||^2 after projection, w normalised in
+// place, flag[0] = 0; a grid barrier that gives up sets flag[2].  Returns false when the launch is
+// not possible (blocks = 0 or a cooperative-launch error): the caller falls back to CGS2.
+// K.gram holds (m + 1) x mgs_gram_stride() in-block Gram entries; part holds mgs_partials() x blocks.
 struct KrylovState;
-ps_status mgs_grid(int* blocks);
-bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part, int blocks,
-              unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, cudaStream_t st);
+ps_status mgs_grid(int* blocks);  // four entries: sweeps of 1, 2, 4, 8 vectors
+int mgs_gram_stride();
+int mgs_partials();
+bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovState& K, double* part,
+              const int* blocks_by_sweep,
+              unsigned long long* bar, unsigned long long* base, int64_t limit, int stall, int sweep,
+              cudaStream_t st);
 
 // small dense FGMRES state on the device
 struct KrylovState {
   double* H;    // (m+1) x m column-major
   double *cs, *sn, *g, *h1, *h2, *y;
+  double* gram;  // in-block Gram entries of the basis (modified Gram-Schmidt sweeps)
   double* sc;   // scalars: [0] ||w||^2, [1] ||w'||^2, [2] ||w''||^2, [3] beta, [4] 1/hn, [5] est, [6] hn, [7] bnorm
   int* flag;    // [0] reorthogonalise, [1] nan, [2] a Gram-Schmidt grid barrier gave up
 };

@@ -220,3 +220,26 @@ def test_mgs_and_cgs2_agree(prec):
     assert abs(its[ps.PS_ORTHO_MGS] - its[ps.PS_ORTHO_CGS2]) <= 1, its
     if prec == ps.PS_FP64:
         assert abs(its[ps.PS_ORTHO_MGS] - sto8.iters) <= 1, (its, sto8.iters)
+
+
+@pytest.mark.parametrize("sweep", [1, 2, 4, 8])
+def test_mgs_sweep_widths_match_the_oracle(sweep):
+    # projecting 1, 2, 4 or 8 basis vectors per sweep (forward substitution with the in-block Gram
+    # entries) gives the coefficients of one-at-a-time modified Gram-Schmidt: the oracle's solution
+    # and, in FP64, its iteration count within one
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(1, nx=24, ny=20, nz=10))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=60, coarse_max_p=60))
+    xo, _ = P.fgmres(tol=1e-12)
+    _, sto8 = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=60, coarse_max_p=60, ortho_sweep=sweep))
+    try:
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    assert st.true_relres <= 1e-8
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - sto8.iters) <= 1, (st.iters, sto8.iters)
