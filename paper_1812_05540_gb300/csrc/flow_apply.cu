@@ -142,7 +142,7 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
 // 32-bit sweep tag (single-copy atomic stores, so no fence or flag is needed):
 // consumers prefetch the words they need two steps ahead and re-read them only
 // while the tag is not yet the current one; the wait is bounded and raises *err.
-// Everything that does not depend on the wavefront is prefetched three steps
+// Everything that does not depend on the wavefront is prefetched kP steps
 // ahead.
 // ---------------------------------------------------------------------------
 constexpr int kTY = 16, kTZ = 8;
@@ -248,24 +248,75 @@ struct Cell {
   T z0, z1;
 };
 
+// Per-cell operands of a sweep step staged in shared memory by asynchronous copies, kP steps ahead:
+// [S (3 blocks of the sweep's side) | inv(U_ii) | right-hand side pair | z pair] = 20 values.
+constexpr int kCellVals = 20;
+template <class T>
+__host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 8 : 4; }
+template <class T>
+__host__ __device__ constexpr size_t ring_bytes() { return size_t(ring_depth<T>()) * kTY * kTZ * kCellVals * sizeof(T); }
+
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes_const16) {
+  unsigned d = unsigned(__cvta_generic_to_shared(sdst));
+  if (bytes_const16 == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+  else if (bytes_const16 == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// stage cell i's operands into dst (16-byte aligned); nothing for i < 0
 template <class T, bool FWD>
-__device__ __forceinline__ void load_cell(Cell<T>& d, int64_t i, const T* __restrict__ S28,
-                                          const T* __restrict__ dinv, const T* __restrict__ a,
-                                          const T* __restrict__ zs, const T* __restrict__ zp) {
+__device__ __forceinline__ void stage_cell(T* dst, int64_t i, const T* __restrict__ S28, const T* __restrict__ dinv,
+                                           const T* a, const T* __restrict__ zs, const T* __restrict__ zp) {
   if (i < 0) return;
+  constexpr int V16 = 16 / int(sizeof(T));  // values per 16-byte chunk
   const T* Si = S28 + i * 28 + (FWD ? 0 : 16);
 #pragma unroll
-  for (int q = 0; q < 3; ++q)
+  for (int k = 0; k < 12; k += V16) cp_async(dst + k, Si + k, 16);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) d.S[q][e] = Si[q * 4 + e];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) d.D[e] = dinv[i * 4 + e];
-  d.a0 = a[2 * i];
-  d.a1 = a[2 * i + 1];
+  for (int k = 0; k < 4; k += V16) cp_async(dst + 12 + k, dinv + i * 4 + k, 16);
+  cp_async(dst + 16, a + 2 * i, 2 * int(sizeof(T)));
   if (!FWD) {
-    d.z0 = zs[i];
-    d.z1 = zp[i];
+    cp_async(dst + 18, zs + i, int(sizeof(T)));
+    cp_async(dst + 19, zp + i, int(sizeof(T)));
   }
+}
+
+// move a staged cell from its ring slot to registers (16-byte vector reads)
+template <class T>
+__device__ __forceinline__ void read_cell(const T* sv, Cell<T>& c) {
+  T v[kCellVals];
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < kCellVals; k += 4) {
+      float4 f = *reinterpret_cast<const float4*>(sv + k);
+      v[k] = f.x; v[k + 1] = f.y; v[k + 2] = f.z; v[k + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kCellVals; k += 2) {
+      double2 f = *reinterpret_cast<const double2*>(sv + k);
+      v[k] = f.x; v[k + 1] = f.y;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c.S[r][e] = v[r * 4 + e];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) c.D[e] = v[12 + e];
+  c.a0 = v[16]; c.a1 = v[17]; c.z0 = v[18]; c.z1 = v[19];
+}
+
+template <class T>
+__device__ __forceinline__ void store2(T* p, T a, T b) {
+  if constexpr (sizeof(T) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  else *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
 template <class T, bool FWD>
@@ -273,7 +324,7 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
     int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ dinv, const T* __restrict__ w,
     const T* __restrict__ zs, const T* __restrict__ zp, T* t, T* dz, double* __restrict__ zout, uint64_t* halo,
     int* err, uint32_t tag, int64_t limit, int stall) {
-  __shared__ T buf[2][kTZ][kTY][2];
+  __shared__ __align__(16) T buf[2][kTZ][kTY][2];
   __shared__ int abort_flag;
   const int nby = (ny + kTY - 1) / kTY;
   const int BY = blockIdx.x % nby, BZ = blockIdx.x / nby;
@@ -294,87 +345,124 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
   if (threadIdx.x == 0) abort_flag = 0;
   __syncthreads();
-  auto cell_at = [&](int s) -> int64_t {
-    int xs = s - ry - rz;
-    if (!valid || s > last || xs < 0 || xs >= nx) return -1;
-    int x = FWD ? xs : nx - 1 - xs;
-    return x + int64_t(nx) * (yy + int64_t(ny) * zz);
+  // step s of this thread is cell x(s) of its pencil, xs = s - (ry + rz) in [0, nx)
+  const int64_t pbase = int64_t(nx) * (yy + int64_t(ny) * zz);
+  const int off = ry + rz;
+  auto cell_of = [&](int st) -> int64_t {
+    const int xs = st - off;
+    if (!valid || xs < 0 || xs >= nx) return -1;
+    return pbase + (FWD ? xs : nx - 1 - xs);
   };
-  Cell<T> c0, c1, c2;
-  int64_t i0 = cell_at(0), i1 = cell_at(1), i2 = cell_at(2);
-  load_cell<T, FWD>(c0, i0, S28, dinv, a, zs, zp);
-  load_cell<T, FWD>(c1, i1, S28, dinv, a, zs, zp);
-  load_cell<T, FWD>(c2, i2, S28, dinv, a, zs, zp);
-  // halo words for the current and the next step
-  HaloVal<T> hy0, hz0, hy1, hz1;
-  if (gy && i0 >= 0) halo_fetch<T>(halo, i0 + jy, hy0);
-  if (gz && i0 >= 0) halo_fetch<T>(halo, i0 + jz, hz0);
-  if (gy && i1 >= 0) halo_fetch<T>(halo, i1 + jy, hy1);
-  if (gz && i1 >= 0) halo_fetch<T>(halo, i1 + jz, hz1);
-  T prev0 = T(0), prev1 = T(0);
-  for (int step = 0; step <= last; ++step) {
-    if (i0 >= 0) {
-      int xs = step - ry - rz;
-      int x = FWD ? xs : nx - 1 - xs;
-      T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
-      bool ok = true;
-      if (gy) {
-        ok = ok && halo_wait<T>(halo, i0 + jy, tag, hy0, limit, err);
-        halo_decode<T>(hy0, ny0, ny1);
-      } else if (hy) {
-        const T* q = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
-        ny0 = q[0]; ny1 = q[1];
-      }
-      if (gz) {
-        ok = ok && halo_wait<T>(halo, i0 + jz, tag, hz0, limit, err);
-        halo_decode<T>(hz0, nz0, nz1);
-      } else if (hz) {
-        const T* q = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
-        nz0 = q[0]; nz1 = q[1];
-      }
-      if (!ok) { abort_flag = 1; atomicExch(err, 1); }
-      T r0, r1;
-      if (FWD) {
-        // u_i = w_i - sum_{k<i} S_ik t_k (blocks z-1, y-1, x-1) ; t_i = inv(U_ii) u_i
-        T px0 = x > 0 ? prev0 : T(0), px1 = x > 0 ? prev1 : T(0);
-        T u0 = c0.a0 - (c0.S[0][0] * nz0 + c0.S[0][1] * nz1) - (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) -
-               (c0.S[2][0] * px0 + c0.S[2][1] * px1);
-        T u1 = c0.a1 - (c0.S[0][2] * nz0 + c0.S[0][3] * nz1) - (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) -
-               (c0.S[2][2] * px0 + c0.S[2][3] * px1);
-        r0 = c0.D[0] * u0 + c0.D[1] * u1;
-        r1 = c0.D[2] * u0 + c0.D[3] * u1;
-        t[2 * i0] = r0;
-        t[2 * i0 + 1] = r1;
-      } else {
-        // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j (blocks x+1, y+1, z+1) ; z_f = z + dz
-        T px0 = x + 1 < nx ? prev0 : T(0), px1 = x + 1 < nx ? prev1 : T(0);
-        T s0 = (c0.S[0][0] * px0 + c0.S[0][1] * px1) + (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) +
-               (c0.S[2][0] * nz0 + c0.S[2][1] * nz1);
-        T s1 = (c0.S[0][2] * px0 + c0.S[0][3] * px1) + (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) +
-               (c0.S[2][2] * nz0 + c0.S[2][3] * nz1);
-        r0 = c0.a0 - (c0.D[0] * s0 + c0.D[1] * s1);
-        r1 = c0.a1 - (c0.D[2] * s0 + c0.D[3] * s1);
-        dz[2 * i0] = r0;
-        dz[2 * i0 + 1] = r1;
-        zout[2 * i0] = double(c0.z0 + r0);
-        zout[2 * i0 + 1] = double(c0.z1 + r1);
-      }
-      if (py || pz) halo_put<T>(halo, i0, r0, r1, tag);
-      prev0 = r0;
-      prev1 = r1;
-      buf[step & 1][lz][ly][0] = r0;
-      buf[step & 1][lz][ly][1] = r1;
-    }
-    // rotate the rings: cell data for step + 3, halo words for step + 2
-    c0 = c1; c1 = c2;
-    i0 = i1; i1 = i2; i2 = cell_at(step + 3);
-    load_cell<T, FWD>(c2, i2, S28, dinv, a, zs, zp);
-    hy0 = hy1; hz0 = hz1;
-    if (gy && i1 >= 0) halo_fetch<T>(halo, i1 + jy, hy1);
-    if (gz && i1 >= 0) halo_fetch<T>(halo, i1 + jz, hz1);
-    __syncthreads();
-    if (abort_flag) return;
+  // Cell operands: a ring of kP slots in shared memory filled by asynchronous copies kP steps ahead
+  // (one commit group per step).  Halo words: two register slots, fetched two steps ahead.  Each
+  // step's critical part -- read the y/z neighbours, finish the 2x2 update, publish -- comes right
+  // after the barrier; the next step's operands are read from the ring and its term with the
+  // x-neighbour (this thread's own previous result) is formed before the barrier.  The loop over
+  // the ring slots is unrolled so that every slot and register index is a compile-time constant.
+  constexpr int kP = ring_depth<T>();
+  extern __shared__ __align__(16) unsigned char ring_raw[];
+  T* ring = reinterpret_cast<T*>(ring_raw);
+  auto slot = [&](int q) { return ring + (size_t(q) * (kTY * kTZ) + threadIdx.x) * kCellVals; };
+  HaloVal<T> hyr[2], hzr[2];
+#pragma unroll
+  for (int q = 0; q < kP; ++q) {
+    stage_cell<T, FWD>(slot(q), cell_of(q), S28, dinv, a, zs, zp);
+    cp_async_commit();
   }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t ih = cell_of(q);
+    if (gy && ih >= 0) halo_fetch<T>(halo, ih + jy, hyr[q]);
+    if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[q]);
+  }
+  // two register cells alternate: cs[s & 1] holds step s
+  Cell<T> cs[2];
+  T p0[2], p1[2];  // x-neighbour part of step s: FWD a - S_x-1 t_x-1, BWD S_x+1 dz_x+1
+  int64_t ic[2];
+  cp_async_wait<kP - 1>();
+  read_cell<T>(slot(0), cs[0]);
+  ic[0] = cell_of(0);
+  if (FWD) { p0[0] = cs[0].a0; p1[0] = cs[0].a1; } else { p0[0] = T(0); p1[0] = T(0); }
+  for (int s0 = 0; s0 <= last; s0 += kP) {
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      const int step = s0 + q;
+      if (step > last) break;  // the same in every thread of the CTA
+      const int cur = q & 1, nxt = (q + 1) & 1;
+      const Cell<T>& c0 = cs[cur];
+      const int64_t i0 = ic[cur];
+      T r0 = T(0), r1 = T(0);
+      if (i0 >= 0) {
+        T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
+        bool ok = true;
+        if (gy) {
+          ok = ok && halo_wait<T>(halo, i0 + jy, tag, hyr[cur], limit, err);
+          halo_decode<T>(hyr[cur], ny0, ny1);
+        } else if (hy) {
+          const T* qq = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
+          ny0 = qq[0]; ny1 = qq[1];
+        }
+        if (gz) {
+          ok = ok && halo_wait<T>(halo, i0 + jz, tag, hzr[cur], limit, err);
+          halo_decode<T>(hzr[cur], nz0, nz1);
+        } else if (hz) {
+          const T* qq = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
+          nz0 = qq[0]; nz1 = qq[1];
+        }
+        if (!ok) { abort_flag = 1; atomicExch(err, 1); }
+        if (FWD) {
+          // u_i = w_i - sum_{k<i} S_ik t_k (blocks z-1, y-1, x-1) ; t_i = inv(U_ii) u_i
+          T u0 = p0[cur] - (c0.S[0][0] * nz0 + c0.S[0][1] * nz1) - (c0.S[1][0] * ny0 + c0.S[1][1] * ny1);
+          T u1 = p1[cur] - (c0.S[0][2] * nz0 + c0.S[0][3] * nz1) - (c0.S[1][2] * ny0 + c0.S[1][3] * ny1);
+          r0 = c0.D[0] * u0 + c0.D[1] * u1;
+          r1 = c0.D[2] * u0 + c0.D[3] * u1;
+          store2<T>(t + 2 * i0, r0, r1);
+        } else {
+          // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j (blocks x+1, y+1, z+1) ; z_f = z + dz
+          T s0v = p0[cur] + (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) + (c0.S[2][0] * nz0 + c0.S[2][1] * nz1);
+          T s1v = p1[cur] + (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) + (c0.S[2][2] * nz0 + c0.S[2][3] * nz1);
+          r0 = c0.a0 - (c0.D[0] * s0v + c0.D[1] * s1v);
+          r1 = c0.a1 - (c0.D[2] * s0v + c0.D[3] * s1v);
+          store2<T>(dz + 2 * i0, r0, r1);
+          // z_f may start at an odd multiple of 8 bytes (it follows the 3 * nodes displacement entries)
+          zout[2 * i0] = double(c0.z0 + r0);
+          zout[2 * i0 + 1] = double(c0.z1 + r1);
+        }
+        if (py || pz) halo_put<T>(halo, i0, r0, r1, tag);
+        store2<T>(buf[step & 1][lz][ly], r0, r1);
+      }
+      // refill this step's ring slot for step + kP, then take step + 1's operands from the ring
+      stage_cell<T, FWD>(slot(q), cell_of(step + kP), S28, dinv, a, zs, zp);
+      cp_async_commit();
+      cp_async_wait<kP - 1>();
+      read_cell<T>(slot((q + 1) % kP), cs[nxt]);
+      ic[nxt] = cell_of(step + 1);
+      {
+        // x-neighbour term of step + 1: this thread's result of step when both lie on the pencil
+        const bool hasx = ic[nxt] >= 0 && i0 >= 0;
+        const T x0 = hasx ? r0 : T(0), x1 = hasx ? r1 : T(0);
+        const Cell<T>& cn = cs[nxt];
+        if (FWD) {
+          p0[nxt] = cn.a0 - (cn.S[2][0] * x0 + cn.S[2][1] * x1);
+          p1[nxt] = cn.a1 - (cn.S[2][2] * x0 + cn.S[2][3] * x1);
+        } else {
+          p0[nxt] = cn.S[0][0] * x0 + cn.S[0][1] * x1;
+          p1[nxt] = cn.S[0][2] * x0 + cn.S[0][3] * x1;
+        }
+      }
+      {
+        const int64_t ih = cell_of(step + 2);
+        if (gy && ih >= 0) halo_fetch<T>(halo, ih + jy, hyr[cur]);
+        if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[cur]);
+      }
+      __syncthreads();
+      if (q == kP - 1 && abort_flag) {
+        cp_async_wait<0>();  // own copies in flight
+        return;
+      }
+    }
+  }
+  cp_async_wait<0>();
 }
 
 }  // namespace
@@ -415,9 +503,9 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
     int64_t lim = F.spin_limit;
     int stall = F.test_stall;
     void* args[] = {&nx, &ny, &nz, &s28, &dinv, &a, &zs, &zp, &t, &dz, &zout, &halo, &err, &tag, &lim, &stall};
-    cudaError_t e = dir == 0
-        ? cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, true>, grid, kTY * kTZ, args, 0, st)
-        : cudaLaunchCooperativeKernel((const void*)k_ilu_pencil<T, false>, grid, kTY * kTZ, args, 0, st);
+    const void* fn = dir == 0 ? (const void*)k_ilu_pencil<T, true> : (const void*)k_ilu_pencil<T, false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ring_bytes<T>()));
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kTY * kTZ, args, ring_bytes<T>(), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return false;
