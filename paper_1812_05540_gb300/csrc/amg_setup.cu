@@ -328,6 +328,45 @@ __device__ __forceinline__ bool hash_insert(int32_t* tab, int32_t key, int* over
   return false;
 }
 
+// Enumerates the products x_iq y_kr (k = xci[q]) of row i in (q, r) order, 32 at a time: each lane
+// takes one product, found by a warp scan of the Y row lengths of 32 X entries and a shuffle search.
+// f(valid, e, r) is called by every lane (it may shuffle); e is the lane that holds the product's X
+// entry (its q, k and value), r the position of the Y entry.
+template <class F>
+__device__ __forceinline__ void for_products(int64_t i, const int32_t* __restrict__ xrp,
+                                             const int32_t* __restrict__ xci, const int32_t* __restrict__ yrp,
+                                             int lane, F&& f) {
+  const int32_t q0 = xrp[i], q1 = xrp[i + 1];
+  for (int32_t qc = q0; qc < q1; qc += 32) {
+    const int32_t q = qc + lane;
+    const bool v = q < q1;
+    const int32_t k = v ? xci[q] : 0;
+    const int32_t lo = v ? yrp[k] : 0;
+    const int32_t len = v ? yrp[k + 1] - lo : 0;
+    int32_t inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    const int32_t excl = inc - len;
+    for (int32_t p0 = 0; p0 < total; p0 += 32) {
+      const int32_t p = p0 + lane;
+      // the entry holding product p: the last lane whose first product is <= p
+      int e = 0;
+#pragma unroll
+      for (int stp = 16; stp > 0; stp >>= 1) {
+        int32_t ex = __shfl_sync(0xffffffffu, excl, e + stp);
+        if (ex <= p) e += stp;
+      }
+      const int32_t lo_e = __shfl_sync(0xffffffffu, lo, e);
+      const int32_t ex_e = __shfl_sync(0xffffffffu, excl, e);
+      f(p < total, e, lo_e + (p - ex_e), qc);
+    }
+  }
+}
+
 // collect the distinct columns of row i into tab (H slots); returns their count (all lanes)
 template <int H>
 __device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
@@ -336,11 +375,9 @@ __device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const 
   for (int t = lane; t < H; t += 32) tab[t] = kEmpty;
   __syncwarp();
   int cnt = 0;
-  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
-    int32_t k = xci[q];
-    for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32)
-      if (hash_insert<H>(tab, yci[r], overflow)) ++cnt;
-  }
+  for_products(i, xrp, xci, yrp, lane, [&](bool valid, int, int32_t r, int32_t) {
+    if (valid && hash_insert<H>(tab, yci[r], overflow)) ++cnt;
+  });
   __syncwarp();
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   return cnt;
@@ -493,11 +530,12 @@ __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, c
   if (w >= nrows) return;
   int64_t i = rows[w];
   if (islong[i]) return;
-  constexpr size_t per = size_t(H) * 4 + size_t(C) * 4 + size_t(C) * NC * 8;
+  constexpr size_t per = size_t(H) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 8;
   unsigned char* base = sraw + per * wib;
   int32_t* tab = reinterpret_cast<int32_t*>(base);
   int32_t* list = reinterpret_cast<int32_t*>(base + H * 4);
   double* acc = reinterpret_cast<double*>(base + H * 4 + C * 4);
+  double* stg = acc + C * NC;  // one product per lane, staged for the in-order fold
   int ovf = 0;
   int u = spgemm_collect<H>(i, xrp, xci, yrp, yci, tab, lane, &ovf);
   if (u > C || __any_sync(0xffffffffu, ovf)) {
@@ -533,25 +571,43 @@ __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, c
     }
   for (int t = lane; t < u * NC; t += 32) acc[t] = 0.0;
   __syncwarp();
-  // numeric: products added in ascending order of the inner index k
-  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
-    int32_t k = xci[q];
+  // numeric: for each output column, products added one at a time in ascending order of the inner
+  // index k (products are enumerated q-major; within a round of 32, lanes that hit the same column
+  // are folded in by the lowest of them in lane order)
+  for_products(i, xrp, xci, yrp, lane, [&](bool valid, int e, int32_t r, int32_t qc) {
     double x[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) x[c] = xv[int64_t(q) * NC + c];
-    for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32) {
-      int32_t j = yci[r];
+    for (int c = 0; c < NC; ++c) {
+      const int32_t qe = qc + e;
+      double xl = 0.0;
+      if (qe < xrp[i + 1]) xl = xv[int64_t(qe) * NC + c];
+      x[c] = xl;
+    }
+    int pos = 0;
+    if (valid) {
+      const int32_t j = yci[r];
       int lo = 0, hi = u;
       while (lo < hi) {
         int m = (lo + hi) >> 1;
         if (list[m] < j) lo = m + 1;
         else hi = m;
       }
+      pos = lo;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[lo * NC + c] = acc[lo * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+      for (int c = 0; c < NC; ++c) stg[lane * NC + c] = x[c] * yv[int64_t(r) * NC + c];
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? pos : (1 << 30) + lane);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        double a = acc[pos * NC + c];
+        for (unsigned m = peers; m; m &= m - 1) a = a + stg[(__ffs(m) - 1) * NC + c];
+        acc[pos * NC + c] = a;
+      }
     }
     __syncwarp();
-  }
+  });
   int32_t o = crp[i];
   for (int t = lane; t < u; t += 32) {
     cci[o + t] = list[t];
@@ -715,7 +771,7 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     for_class(b, [&](auto cc) {
       constexpr int C = decltype(cc)::value;
       const int wpb = C <= 128 ? 8 : (C <= 512 ? 4 : 2);
-      size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8;
+      size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 8;
       size_t sm = per * wpb;
       cudaFuncSetAttribute(k_spgemm_fill<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
       PS_TICK(); k_spgemm_fill<NC, C><<<unsigned((nr + wpb - 1) / wpb), 32 * wpb, sm, st>>>(
