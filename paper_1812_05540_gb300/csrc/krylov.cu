@@ -205,9 +205,10 @@ __global__ void __launch_bounds__(256) k_spmv_u_st(JacDev J, const double* __res
       int64_t c = clampnb(uu_nb(g, i, j, k, s), I);
       const double* A = J.uu_s + int64_t(s) * 9 * n + I;
       double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      a0 += __ldg(A) * x0 + __ldg(A + n) * x1 + __ldg(A + 2 * n) * x2;
-      a1 += __ldg(A + 3 * n) * x0 + __ldg(A + 4 * n) * x1 + __ldg(A + 5 * n) * x2;
-      a2 += __ldg(A + 6 * n) * x0 + __ldg(A + 7 * n) * x1 + __ldg(A + 8 * n) * x2;
+      // one FMA per block entry (the FP64 pipe is the bound: no separate products or sums)
+      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + n), x1, a0); a0 = fma(__ldg(A + 2 * n), x2, a0);
+      a1 = fma(__ldg(A + 3 * n), x0, a1); a1 = fma(__ldg(A + 4 * n), x1, a1); a1 = fma(__ldg(A + 5 * n), x2, a1);
+      a2 = fma(__ldg(A + 6 * n), x0, a2); a2 = fma(__ldg(A + 7 * n), x1, a2); a2 = fma(__ldg(A + 8 * n), x2, a2);
     }
 #pragma unroll 4
     for (int s = 0; s < 8; ++s) {
@@ -215,9 +216,9 @@ __global__ void __launch_bounds__(256) k_spmv_u_st(JacDev J, const double* __res
       c = c >= 0 ? c : 0;
       const double* A = J.uf_s + int64_t(s) * 6 * n + I;
       double f0 = xf[2 * c], f1 = xf[2 * c + 1];
-      a0 += __ldg(A) * f0 + __ldg(A + n) * f1;
-      a1 += __ldg(A + 2 * n) * f0 + __ldg(A + 3 * n) * f1;
-      a2 += __ldg(A + 4 * n) * f0 + __ldg(A + 5 * n) * f1;
+      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + n), f1, a0);
+      a1 = fma(__ldg(A + 2 * n), f0, a1); a1 = fma(__ldg(A + 3 * n), f1, a1);
+      a2 = fma(__ldg(A + 4 * n), f0, a2); a2 = fma(__ldg(A + 5 * n), f1, a2);
     }
     if (b) {
       a0 = b[3 * I] - a0; a1 = b[3 * I + 1] - a1; a2 = b[3 * I + 2] - a2;
@@ -254,16 +255,16 @@ __global__ void __launch_bounds__(256) k_spmv_f_st(JacDev J, const double* __res
       int64_t c = fu_nb(g, i, j, k, s);
       const double* A = J.fu_s + int64_t(s) * 6 * n + C;
       double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      a0 += __ldg(A) * x0 + __ldg(A + n) * x1 + __ldg(A + 2 * n) * x2;
-      a1 += __ldg(A + 3 * n) * x0 + __ldg(A + 4 * n) * x1 + __ldg(A + 5 * n) * x2;
+      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + n), x1, a0); a0 = fma(__ldg(A + 2 * n), x2, a0);
+      a1 = fma(__ldg(A + 3 * n), x0, a1); a1 = fma(__ldg(A + 4 * n), x1, a1); a1 = fma(__ldg(A + 5 * n), x2, a1);
     }
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       int64_t c = clampnb(ff_nb(g, i, j, k, s), C);
       const double* A = J.ff_s + int64_t(s) * 4 * n + C;
       double f0 = xf[2 * c], f1 = xf[2 * c + 1];
-      a0 += __ldg(A) * f0 + __ldg(A + n) * f1;
-      a1 += __ldg(A + 2 * n) * f0 + __ldg(A + 3 * n) * f1;
+      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + n), f1, a0);
+      a1 = fma(__ldg(A + 2 * n), f0, a1); a1 = fma(__ldg(A + 3 * n), f1, a1);
     }
     int64_t o = 3 * J.nn + 2 * C;
     if (b) {
