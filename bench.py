@@ -325,6 +325,8 @@ def run_ours(args):
             ps.ps_system_free(sysp)
             return
         t_64, st_64 = (t_mx, st_mx) if args.no_fp64 else timed(ps.PS_FP64, args.steps)[:2]
+        # BF16-prolongator variant of the mixed mode: time and iteration cost
+        t_bp, st_bp = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_BF16P, args.steps)[:2]
         per_mx = t_mx / args.steps
         per_64 = t_64 / args.steps
 
@@ -480,6 +482,10 @@ def run_ours(args):
                                      "flow_2_4": round(st_64[-1].ms_flow24, 1),
                                      "vcycle_p": round(st_64[-1].ms_vcycle_p, 1), "ilu": round(st_64[-1].ms_ilu, 1)}},
         "mixed_speedup_vs_fp64": per_64 / per_mx,
+        "bf16_prolongator": None if st_bp is None else {
+            "value": t_bp / args.steps / world, "iters": [st.iters for st in st_bp],
+            "solve_ms": [round(st.ms_solve, 2) for st in st_bp],
+            "vcycle_u_ms": round(st_bp[-1].ms_vcycle_u, 1), "vcycle_p_ms": round(st_bp[-1].ms_vcycle_p, 1)},
         "true_relres_mixed": relres, "gen_s": gen_s,
         "roofline": {k: rooflines[0][k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")},
         "rooflines": rooflines,

@@ -48,7 +48,9 @@ typedef enum {
   PS_ERR_BUDGET = 8          /* the handle would exceed ps_params.hbm_budget */
 } ps_status;
 
-enum { PS_FP64 = 0, PS_MIXED_FP32 = 1 };     /* preconditioner precision */
+/* preconditioner precision: FP64; FP32 (FP64 Krylov, SpMV, fixed-stress diagonal and coarsest solve);
+   or FP32 with the AMG prolongators and restrictors stored in BF16 (read as BF16, summed in FP32) */
+enum { PS_FP64 = 0, PS_MIXED_FP32 = 1, PS_MIXED_BF16P = 2 };
 enum { PS_SMOOTH_L1JACOBI = 0, PS_SMOOTH_CHEBYSHEV = 1 };
 enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
 enum { PS_ORTHO_MGS = 0, PS_ORTHO_CGS2 = 1 };    /* Arnoldi orthogonalisation */
@@ -81,7 +83,7 @@ typedef struct {
 } ps_jacobian;
 
 typedef struct {
-  int32_t precision;          /* PS_FP64 or PS_MIXED_FP32 (FP32 preconditioner, FP64 Krylov) */
+  int32_t precision;          /* PS_FP64, PS_MIXED_FP32 (FP32 preconditioner, FP64 Krylov) or PS_MIXED_BF16P */
   int32_t restart;            /* FGMRES restart length m (default 100) */
   int32_t max_iters;          /* total Krylov iterations (default 1000) */
   int32_t smoother;           /* PS_SMOOTH_* (default Chebyshev) */

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libps.so")
 
 PS_OK, PS_ERR_INVALID, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_NOT_CONVERGED, PS_ERR_BREAKDOWN, PS_ERR_NAN, \
     PS_ERR_TIMEOUT, PS_ERR_BUDGET = range(9)
-PS_FP64, PS_MIXED_FP32 = 0, 1
+PS_FP64, PS_MIXED_FP32, PS_MIXED_BF16P = 0, 1, 2
 PS_SMOOTH_L1JACOBI, PS_SMOOTH_CHEBYSHEV = 0, 1
 PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
 PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1

@@ -2,6 +2,8 @@
 // §5.2 (three SDC displacement components on shared nodal aggregates, nc = 3)
 // and §5.3 (pressure, nc = 1).
 #pragma once
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "internal.cuh"
@@ -37,6 +39,8 @@ struct AmgLevel {
   int32_t *rrp = nullptr, *rci = nullptr;
   double* rv = nullptr;
   float* rvf = nullptr;
+  // BF16 copies of P and R for the BF16-prolongator variant of the mixed mode (null otherwise)
+  __nv_bfloat16 *pvb = nullptr, *rvb = nullptr;
   int rlane = 8;
   // coarsest level: dense FP64 inverse per component (row-major n x n), used in both precisions
   bool coarsest = false;
@@ -57,6 +61,7 @@ struct AmgParams {
   double theta;
   int coarse_max, max_levels;
   bool mixed;
+  bool bf16p;  // also keep BF16 copies of P and R (transfer operators read in BF16, summed in FP32)
 };
 
 // Build the hierarchy from the level-0 operator (rp/ci/v are adopted: the

@@ -684,6 +684,10 @@ __global__ void k_gj_elim(int64_t n, int64_t k, double* __restrict__ M, double* 
   else B[r * n + j - n] = B[r * n + j - n] - m * B[k * n + j - n];
 }
 
+__global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = __double2bfloat16(a[t]);
+}
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = float(a[t]);
@@ -961,6 +965,12 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_TRY(ar.alloc(&lev.rvf, size_t(pnnz) * NC + 1));
       PS_TICK(); k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.pv, lev.pvf, pnnz * NC);
       PS_TICK(); k_to_f32<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.rv, lev.rvf, pnnz * NC);
+      if (prm.bf16p) {
+        PS_TRY(ar.alloc(&lev.pvb, size_t(pnnz) * NC + 8));
+        PS_TRY(ar.alloc(&lev.rvb, size_t(pnnz) * NC + 8));
+        PS_TICK(); k_to_bf16<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.pv, lev.pvb, pnnz * NC);
+        PS_TICK(); k_to_bf16<<<grid_for(pnnz * NC, 256), 256, 0, st>>>(lev.rv, lev.rvb, pnnz * NC);
+      }
     }
     // Galerkin product A_c = R (A P)
     int32_t *aprp, *apci, *crp, *cci;

@@ -41,6 +41,7 @@ struct ps_handle {
   ps_grid grid;
   int64_t nn = 0, nc = 0, nu = 0, nf = 0, n = 0;
   bool mixed = false;
+  bool bf16p = false;  // BF16 transfer operators (PS_MIXED_BF16P)
   JacDev J;
   double* dfs = nullptr;
   Amg amg_u, amg_p;
@@ -174,6 +175,7 @@ ps_status build_flow(ps_handle* h) {
   AmgParams ap;
   ap.theta = h->prm.theta_p; ap.coarse_max = h->prm.coarse_max_p; ap.max_levels = h->prm.max_levels;
   ap.mixed = h->mixed;
+  ap.bf16p = h->bf16p;
   PS_TRY(amg_build(ar, h->amg_p, 1, h->nc, F.nnzb, F.rp, F.ci, F.spp, ap, st));
   bool sp_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_p, h->grid.nx, h->grid.ny, h->grid.nz, 7, h->mixed, &sp_ok, st));
@@ -221,6 +223,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   AmgParams ap;
   ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
   ap.mixed = h->mixed;
+  ap.bf16p = h->bf16p;
   PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
   bool su_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
@@ -306,7 +309,8 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
       !bsr_ok(jac->A_ff, nc, nc, 2, 2) || !jac->d_fs)
     return PS_ERR_INVALID;
   if (params->restart < 1 || params->restart > 120 || params->max_iters < 1) return PS_ERR_INVALID;
-  if (params->precision != PS_FP64 && params->precision != PS_MIXED_FP32) return PS_ERR_INVALID;
+  if (params->precision != PS_FP64 && params->precision != PS_MIXED_FP32 && params->precision != PS_MIXED_BF16P)
+    return PS_ERR_INVALID;
   ps_handle* h = new ps_handle();
   h->prm = *params;
   h->grid = *grid;
@@ -315,7 +319,8 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   h->arf.stream = h->st;
   h->ar.budget = params->hbm_budget;
   h->nn = nn; h->nc = nc; h->nu = 3 * nn; h->nf = 2 * nc; h->n = h->nu + h->nf;
-  h->mixed = params->precision == PS_MIXED_FP32;
+  h->mixed = params->precision == PS_MIXED_FP32 || params->precision == PS_MIXED_BF16P;
+  h->bf16p = params->precision == PS_MIXED_BF16P;
   h->m = params->restart;
   ps_status s = setup_impl(h, jac);
   if (s != PS_OK) {

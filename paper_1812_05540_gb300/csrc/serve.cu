@@ -136,7 +136,7 @@ int64_t ps_setup_bytes_estimate(const ps_jacobian* jac, const ps_grid* g, const 
   int64_t nc = int64_t(g->nx) * g->ny * g->nz;
   int64_t n = 3 * nn + 2 * nc;
   int64_t m = p->restart > 0 ? p->restart : 100;
-  bool mixed = p->precision == PS_MIXED_FP32;
+  bool mixed = p->precision == PS_MIXED_FP32 || p->precision == PS_MIXED_BF16P;
   int64_t b = 0;
   b += bsr_bytes(jac->A_uu) + bsr_bytes(jac->A_uf) + bsr_bytes(jac->A_fu) + bsr_bytes(jac->A_ff);
   b += nn * (27 * 9 + 8 * 6) * 8 + nc * (8 * 6 + 7 * 4) * 8;               // stencil copy of the Jacobian

@@ -2,6 +2,8 @@
 // M_pp^{-1} of §5.3): Chebyshev or l1-Jacobi smoothing, residual, restriction
 // by R = P^T, coarse correction by P, dense coarsest solve.  Vectors hold nc
 // interleaved components (node-major x,y,z for the SDC mechanics operator).
+#include <cuda_bf16.h>
+
 #include <utility>
 
 #include "amg.cuh"
@@ -9,19 +11,30 @@
 namespace ps_internal {
 namespace {
 
+// matrix values as stored (FP64, FP32, or BF16 for the prolongator variant) to the apply precision
+template <class T>
+__device__ __forceinline__ T val(const T* p) { return __ldg(p); }
+template <class T>
+__device__ __forceinline__ T val_as(const __nv_bfloat16* p) { return T(__bfloat162float(*p)); }
+
 template <class T, int NC, int LANES>
 struct Row {
   // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum
-  template <class XF>
+  template <class XF, class TV>
   __device__ __forceinline__ static void dot(bool active, int32_t q0, int32_t q1, const int32_t* __restrict__ ci,
-                                             const T* __restrict__ v, XF xf, int sub, T (&s)[NC]) {
+                                             const TV* __restrict__ v, XF xf, int sub, T (&s)[NC]) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) s[c] = T(0);
     if (active)
       for (int32_t q = q0 + sub; q < q1; q += LANES) {
         int32_t j = __ldg(ci + q);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] += __ldg(v + int64_t(q) * NC + c) * xf(j, c);
+        for (int c = 0; c < NC; ++c) {
+          T a;
+          if constexpr (sizeof(TV) == 2) a = val_as<T>(v + int64_t(q) * NC + c);
+          else a = T(__ldg(v + int64_t(q) * NC + c));
+          s[c] += a * xf(j, c);
+        }
       }
 #pragma unroll
     for (int off = LANES / 2; off > 0; off >>= 1)
@@ -165,10 +178,10 @@ __global__ void k_resid(A a, int64_t n, const T* __restrict__ b, const T* __rest
   bool active = i < n;                                                   \
   int32_t q0 = active ? rp[i] : 0, q1 = active ? rp[i + 1] : 0;
 
-// y = M x (restriction with R, or y += P x when add)
-template <class T, int NC, int LANES>
+// y = M x (restriction with R, or y += P x when add); M's values stored as TV
+template <class T, int NC, int LANES, class TV>
 __global__ void k_spmv(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                       const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, int add) {
+                       const TV* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, int add) {
   ROW_SETUP
   auto xf = [&](int32_t j, int c) { return x[int64_t(j) * NC + c]; };
   T s[NC];
@@ -336,14 +349,14 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
   }
 }
 
-template <class T, int NC>
-void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const T* v, const T* x, T* y, int add,
+template <class T, int NC, class TV>
+void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const TV* v, const T* x, T* y, int add,
                 cudaStream_t st) {
   switch (lanes) {
-    case 4: PS_TICK(); k_spmv<T, NC, 4><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 8: PS_TICK(); k_spmv<T, NC, 8><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 16: PS_TICK(); k_spmv<T, NC, 16><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    default: PS_TICK(); k_spmv<T, NC, 32><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 4: PS_TICK(); k_spmv<T, NC, 4, TV><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 8: PS_TICK(); k_spmv<T, NC, 8, TV><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 16: PS_TICK(); k_spmv<T, NC, 16, TV><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    default: PS_TICK(); k_spmv<T, NC, 32, TV><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
   }
 }
 
@@ -368,9 +381,11 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
     using A = decltype(a);
     PS_TICK(); k_resid<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, b, xs, r);
   });
-  spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, V.rv, r, bc, 0, st);
+  if (L.rvb && sizeof(T) == 4) spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, L.rvb, r, bc, 0, st);
+  else spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, V.rv, r, bc, 0, st);
   vcycle_level<T, NC>(H, l + 1, sp, bc, ec, st);
-  spmv_lanes<T, NC>(L.plane, n, L.prp, L.pci, V.pv, ec, xs, 1, st);
+  if (L.pvb && sizeof(T) == 4) spmv_lanes<T, NC>(L.plane, n, L.prp, L.pci, L.pvb, ec, xs, 1, st);
+  else spmv_lanes<T, NC>(L.plane, n, L.prp, L.pci, V.pv, ec, xs, 1, st);
   smooth_post<T, NC>(L, V, sp, b, xs, xs == x ? t : x, d, out, st);
 }
 

@@ -243,3 +243,29 @@ def test_mgs_sweep_widths_match_the_oracle(sweep):
     assert st.true_relres <= 1e-8
     assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
     assert abs(st.iters - sto8.iters) <= 1, (st.iters, sto8.iters)
+
+
+@pytest.mark.parametrize("cfg,kw,cm", [(1, dict(nx=24, ny=20, nz=10), 60), (2, dict(nx=20, ny=44, nz=17), 100)])
+def test_bf16_prolongator_variant(cfg, kw, cm):
+    # FP32 preconditioner with the AMG transfer operators stored in BF16: the flexible FP64 outer loop
+    # still reaches the true FP64 relres and the oracle's solution; the iteration count is reported
+    # against the FP32 variant (at most 20 % more here)
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    xo, _ = P.fgmres(tol=1e-12)
+    dev = g.to_device(osys)
+    its = {}
+    for prec in (ps.PS_MIXED_FP32, ps.PS_MIXED_BF16P):
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=cm, coarse_max_p=cm))
+        try:
+            x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+            _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+        finally:
+            ps.ps_free(h)
+        xs = x.cpu().numpy()
+        relres = np.linalg.norm(osys.rhs - osys.spmv(xs)) / np.linalg.norm(osys.rhs)
+        assert relres <= 1e-8
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+        its[prec] = st.iters
+    assert its[ps.PS_MIXED_BF16P] <= int(1.2 * its[ps.PS_MIXED_FP32]) + 1, its
