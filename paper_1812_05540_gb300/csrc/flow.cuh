@@ -25,6 +25,10 @@ struct FlowStage {
   // row-major each), zero blocks outside the grid
   double* s28 = nullptr;
   float* s28_f = nullptr;
+  // records of the sync-free sweeps, 20 values per cell (forward: lower blocks, inv(U_ii), w; backward:
+  // upper blocks, inv(U_ii), t, z_s, z_p), in the apply precision
+  float *pk_fwd_f = nullptr, *pk_bwd_f = nullptr;
+  double *pk_fwd_d = nullptr, *pk_bwd_d = nullptr;
   // sync-free wavefront sweeps: tagged halo words (4 per cell) and error flag
   uint64_t* halo = nullptr;
   int* ilu_err = nullptr;

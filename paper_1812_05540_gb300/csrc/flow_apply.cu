@@ -248,58 +248,59 @@ struct Cell {
   T z0, z1;
 };
 
-// Per-cell operands of a sweep step staged in shared memory by asynchronous copies, kP steps ahead:
-// [S (3 blocks of the sweep's side) | inv(U_ii) | right-hand side pair | z pair] = 20 values.
-constexpr int kCellVals = 20;
+// Per-cell records of a sweep, packed at setup and per apply so that the cells of one pencil are
+// contiguous: [3 blocks of the sweep's side (12) | inv(U_ii) (4) | right-hand side pair (2) | z pair (2)].
+// Forward records hold the lower blocks (z-1, y-1, x-1) and w; backward records the upper blocks
+// (x+1, y+1, z+1), t (written by the forward sweep) and z_s, z_p.
+constexpr int kRec = 20;
+// cells per copy window and thread
 template <class T>
-__host__ __device__ constexpr int ring_depth() { return sizeof(T) == 4 ? 8 : 4; }
+__host__ __device__ constexpr int win_cells() { return sizeof(T) == 4 ? 4 : 2; }
 template <class T>
-__host__ __device__ constexpr size_t ring_bytes() { return size_t(ring_depth<T>()) * kTY * kTZ * kCellVals * sizeof(T); }
+__host__ __device__ constexpr size_t win_bytes() {  // two window buffers for the CTA
+  return size_t(2) * kTY * kTZ * win_cells<T>() * kRec * sizeof(T);
+}
 
-__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes_const16) {
+__device__ __forceinline__ void mbar_init(uint64_t* m, unsigned count) {
+  unsigned a = unsigned(__cvta_generic_to_shared(m));
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* m, unsigned bytes) {
+  unsigned a = unsigned(__cvta_generic_to_shared(m));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, unsigned parity) {
+  unsigned a = unsigned(__cvta_generic_to_shared(m));
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bulk copy of bytes (multiple of 16, both addresses 16-byte aligned) completing on mbarrier m
+__device__ __forceinline__ void bulk_copy(void* sdst, const void* gsrc, unsigned bytes, uint64_t* m) {
   unsigned d = unsigned(__cvta_generic_to_shared(sdst));
-  if (bytes_const16 == 16)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-  else if (bytes_const16 == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// stage cell i's operands into dst (16-byte aligned); nothing for i < 0
-template <class T, bool FWD>
-__device__ __forceinline__ void stage_cell(T* dst, int64_t i, const T* __restrict__ S28, const T* __restrict__ dinv,
-                                           const T* a, const T* __restrict__ zs, const T* __restrict__ zp) {
-  if (i < 0) return;
-  constexpr int V16 = 16 / int(sizeof(T));  // values per 16-byte chunk
-  const T* Si = S28 + i * 28 + (FWD ? 0 : 16);
-#pragma unroll
-  for (int k = 0; k < 12; k += V16) cp_async(dst + k, Si + k, 16);
-#pragma unroll
-  for (int k = 0; k < 4; k += V16) cp_async(dst + 12 + k, dinv + i * 4 + k, 16);
-  cp_async(dst + 16, a + 2 * i, 2 * int(sizeof(T)));
-  if (!FWD) {
-    cp_async(dst + 18, zs + i, int(sizeof(T)));
-    cp_async(dst + 19, zp + i, int(sizeof(T)));
-  }
+  unsigned b = unsigned(__cvta_generic_to_shared(m));
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(gsrc), "r"(bytes), "r"(b)
+               : "memory");
 }
 
-// move a staged cell from its ring slot to registers (16-byte vector reads)
+// move one record from shared memory to registers (16-byte vector reads)
 template <class T>
 __device__ __forceinline__ void read_cell(const T* sv, Cell<T>& c) {
-  T v[kCellVals];
+  T v[kRec];
   if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int k = 0; k < kCellVals; k += 4) {
+    for (int k = 0; k < kRec; k += 4) {
       float4 f = *reinterpret_cast<const float4*>(sv + k);
       v[k] = f.x; v[k + 1] = f.y; v[k + 2] = f.z; v[k + 3] = f.w;
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kCellVals; k += 2) {
+    for (int k = 0; k < kRec; k += 2) {
       double2 f = *reinterpret_cast<const double2*>(sv + k);
       v[k] = f.x; v[k + 1] = f.y;
     }
@@ -319,13 +320,45 @@ __device__ __forceinline__ void store2(T* p, T a, T b) {
   else *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 
+// step 6 for the pencil sweeps: w into the forward records, z_s and z_p into the backward records
+template <class T>
+__global__ void k_ff_residual_pack(int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ y,
+                                   const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ pf,
+                                   T* __restrict__ pb) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t nc = int64_t(nx) * ny * nz;
+  if (i >= nc) return;
+  int x = int(i % nx), yy = int((i / nx) % ny), zz = int(i / (int64_t(nx) * ny));
+  const int64_t nxy = int64_t(nx) * ny;
+  const int64_t nb[7] = {zz > 0 ? i - nxy : i, yy > 0 ? i - nx : i, x > 0 ? i - 1 : i, i,
+                         x + 1 < nx ? i + 1 : i, yy + 1 < ny ? i + nx : i, zz + 1 < nz ? i + nxy : i};
+  const T* S = S28 + i * 28;
+  T w0 = y[2 * i], w1 = y[2 * i + 1];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    T a = zs[nb[q]], b = zp[nb[q]];
+    w0 -= S[q * 4] * a + S[q * 4 + 1] * b;
+    w1 -= S[q * 4 + 2] * a + S[q * 4 + 3] * b;
+  }
+  store2<T>(pf + i * kRec + 16, w0, w1);
+  store2<T>(pb + i * kRec + 18, zs[i], zp[i]);
+}
+
+// Sync-free wavefront sweep over the packed records (see the block comment above kTY).  Each thread's
+// records for a window of win_cells steps are one contiguous range of its pencil: one bulk copy per
+// thread and window, two window buffers, completion on one mbarrier per buffer (128 arrivals plus
+// the copied bytes).  FWD writes t into the backward records; the backward sweep writes z_f.
 template <class T, bool FWD>
-__global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
-    int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ dinv, const T* __restrict__ w,
-    const T* __restrict__ zs, const T* __restrict__ zp, T* t, T* dz, double* __restrict__ zout, uint64_t* halo,
-    int* err, uint32_t tag, int64_t limit, int stall) {
+__global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz, const T* __restrict__ rec,
+                                                         T* __restrict__ rec_bwd, double* __restrict__ zout,
+                                                         uint64_t* halo, int* err, uint32_t tag, int64_t limit,
+                                                         int stall) {
+  constexpr int W = win_cells<T>();
   __shared__ __align__(16) T buf[2][kTZ][kTY][2];
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int abort_flag;
+  extern __shared__ __align__(16) unsigned char win_raw[];
+  T* win = reinterpret_cast<T*>(win_raw);
   const int nby = (ny + kTY - 1) / kTY;
   const int BY = blockIdx.x % nby, BZ = blockIdx.x / nby;
   // test hook: the CTA numbered stall - 1 never runs, so its halo words never get the current tag
@@ -341,51 +374,65 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
   // this pencil feeds another CTA along y (z) when it sits on the far boundary
   const bool py = valid && ry == kTY - 1 && (FWD ? yy + 1 < ny : yy > 0);
   const bool pz = valid && rz == kTZ - 1 && (FWD ? zz + 1 < nz : zz > 0);
-  const T* a = FWD ? w : t;
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
-  if (threadIdx.x == 0) abort_flag = 0;
-  __syncthreads();
-  // step s of this thread is cell x(s) of its pencil, xs = s - (ry + rz) in [0, nx)
-  const int64_t pbase = int64_t(nx) * (yy + int64_t(ny) * zz);
-  const int off = ry + rz;
+  const int64_t pbase = valid ? int64_t(nx) * (yy + int64_t(ny) * zz) : 0;
+  const int off = ry + rz;  // step s handles pencil position xs = s - off
   auto cell_of = [&](int st) -> int64_t {
     const int xs = st - off;
     if (!valid || xs < 0 || xs >= nx) return -1;
     return pbase + (FWD ? xs : nx - 1 - xs);
   };
-  // Cell operands: a ring of kP slots in shared memory filled by asynchronous copies kP steps ahead
-  // (one commit group per step).  Halo words: two register slots, fetched two steps ahead.  Each
-  // step's critical part -- read the y/z neighbours, finish the 2x2 update, publish -- comes right
-  // after the barrier; the next step's operands are read from the ring and its term with the
-  // x-neighbour (this thread's own previous result) is formed before the barrier.  The loop over
-  // the ring slots is unrolled so that every slot and register index is a compile-time constant.
-  constexpr int kP = ring_depth<T>();
-  extern __shared__ __align__(16) unsigned char ring_raw[];
-  T* ring = reinterpret_cast<T*>(ring_raw);
-  auto slot = [&](int q) { return ring + (size_t(q) * (kTY * kTZ) + threadIdx.x) * kCellVals; };
-  HaloVal<T> hyr[2], hzr[2];
-#pragma unroll
-  for (int q = 0; q < kP; ++q) {
-    stage_cell<T, FWD>(slot(q), cell_of(q), S28, dinv, a, zs, zp);
-    cp_async_commit();
+  // window k holds steps [k W, k W + W): the x range [xlo, xlo + W), records in ascending x
+  auto win_xlo = [&](int k) { return FWD ? k * W - off : nx + off - k * W - W; };
+  auto slot = [&](int b, int p) { return win + ((size_t(b) * (kTY * kTZ) + threadIdx.x) * W + p) * kRec; };
+  auto request = [&](int k) {
+    const int b = k & 1;
+    const int xlo = win_xlo(k);
+    const int x0 = max(xlo, 0), x1 = min(xlo + W, nx);
+    unsigned bytes = (valid && x1 > x0) ? unsigned(x1 - x0) * kRec * sizeof(T) : 0u;
+    mbar_arrive_tx(&mbar[b], bytes);
+    if (bytes) bulk_copy(slot(b, x0 - xlo), rec + (pbase + x0) * kRec, bytes, &mbar[b]);
+  };
+  auto wait_window = [&](int k) -> bool {
+    int64_t it = 0;
+    while (!mbar_try_wait(&mbar[k & 1], unsigned((k >> 1) & 1))) {
+      if (++it > limit) return false;
+    }
+    return true;
+  };
+  auto rec_of = [&](int st) -> const T* {  // the record of step st (its window must have landed)
+    const int k = st / W;
+    const int x = FWD ? st - off : nx - 1 - (st - off);
+    return slot(k & 1, x - win_xlo(k));
+  };
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&mbar[0], kTY * kTZ);
+    mbar_init(&mbar[1], kTY * kTZ);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+  request(0);
+  request(1);
+  HaloVal<T> hyr[2], hzr[2];
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int64_t ih = cell_of(q);
     if (gy && ih >= 0) halo_fetch<T>(halo, ih + jy, hyr[q]);
     if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[q]);
   }
-  // two register cells alternate: cs[s & 1] holds step s
   Cell<T> cs[2];
-  T p0[2], p1[2];  // x-neighbour part of step s: FWD a - S_x-1 t_x-1, BWD S_x+1 dz_x+1
+  T p0[2], p1[2];  // x-neighbour part of step s: FWD w - S_x-1 t_x-1, BWD S_x+1 dz_x+1
   int64_t ic[2];
-  cp_async_wait<kP - 1>();
-  read_cell<T>(slot(0), cs[0]);
+  bool ok0 = wait_window(0);
+  if (!ok0) { atomicExch(err, 1); abort_flag = 1; }
   ic[0] = cell_of(0);
-  if (FWD) { p0[0] = cs[0].a0; p1[0] = cs[0].a1; } else { p0[0] = T(0); p1[0] = T(0); }
-  for (int s0 = 0; s0 <= last; s0 += kP) {
+  if (ic[0] >= 0) read_cell<T>(rec_of(0), cs[0]);
+  if (FWD) { p0[0] = ic[0] >= 0 ? cs[0].a0 : T(0); p1[0] = ic[0] >= 0 ? cs[0].a1 : T(0); }
+  else { p0[0] = T(0); p1[0] = T(0); }
+  for (int s0 = 0; s0 <= last; s0 += 2 * W) {
 #pragma unroll
-    for (int q = 0; q < kP; ++q) {
+    for (int q = 0; q < 2 * W; ++q) {
       const int step = s0 + q;
       if (step > last) break;  // the same in every thread of the CTA
       const int cur = q & 1, nxt = (q + 1) & 1;
@@ -416,14 +463,13 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
           T u1 = p1[cur] - (c0.S[0][2] * nz0 + c0.S[0][3] * nz1) - (c0.S[1][2] * ny0 + c0.S[1][3] * ny1);
           r0 = c0.D[0] * u0 + c0.D[1] * u1;
           r1 = c0.D[2] * u0 + c0.D[3] * u1;
-          store2<T>(t + 2 * i0, r0, r1);
+          store2<T>(rec_bwd + i0 * kRec + 16, r0, r1);
         } else {
           // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j (blocks x+1, y+1, z+1) ; z_f = z + dz
           T s0v = p0[cur] + (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) + (c0.S[2][0] * nz0 + c0.S[2][1] * nz1);
           T s1v = p1[cur] + (c0.S[1][2] * ny0 + c0.S[1][3] * ny1) + (c0.S[2][2] * nz0 + c0.S[2][3] * nz1);
           r0 = c0.a0 - (c0.D[0] * s0v + c0.D[1] * s1v);
           r1 = c0.a1 - (c0.D[2] * s0v + c0.D[3] * s1v);
-          store2<T>(dz + 2 * i0, r0, r1);
           // z_f may start at an odd multiple of 8 bytes (it follows the 3 * nodes displacement entries)
           zout[2 * i0] = double(c0.z0 + r0);
           zout[2 * i0 + 1] = double(c0.z1 + r1);
@@ -431,23 +477,23 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
         if (py || pz) halo_put<T>(halo, i0, r0, r1, tag);
         store2<T>(buf[step & 1][lz][ly], r0, r1);
       }
-      // refill this step's ring slot for step + kP, then take step + 1's operands from the ring
-      stage_cell<T, FWD>(slot(q), cell_of(step + kP), S28, dinv, a, zs, zp);
-      cp_async_commit();
-      cp_async_wait<kP - 1>();
-      read_cell<T>(slot((q + 1) % kP), cs[nxt]);
+      // step + 1's record (its window is waited for when step + 1 starts a window)
+      if ((step + 1) % W == 0 && step + 1 <= last) {
+        if (!wait_window((step + 1) / W)) { abort_flag = 1; atomicExch(err, 1); }
+      }
       ic[nxt] = cell_of(step + 1);
+      if (ic[nxt] >= 0) read_cell<T>(rec_of(step + 1), cs[nxt]);
       {
         // x-neighbour term of step + 1: this thread's result of step when both lie on the pencil
         const bool hasx = ic[nxt] >= 0 && i0 >= 0;
         const T x0 = hasx ? r0 : T(0), x1 = hasx ? r1 : T(0);
         const Cell<T>& cn = cs[nxt];
         if (FWD) {
-          p0[nxt] = cn.a0 - (cn.S[2][0] * x0 + cn.S[2][1] * x1);
-          p1[nxt] = cn.a1 - (cn.S[2][2] * x0 + cn.S[2][3] * x1);
+          p0[nxt] = ic[nxt] >= 0 ? cn.a0 - (cn.S[2][0] * x0 + cn.S[2][1] * x1) : T(0);
+          p1[nxt] = ic[nxt] >= 0 ? cn.a1 - (cn.S[2][2] * x0 + cn.S[2][3] * x1) : T(0);
         } else {
-          p0[nxt] = cn.S[0][0] * x0 + cn.S[0][1] * x1;
-          p1[nxt] = cn.S[0][2] * x0 + cn.S[0][3] * x1;
+          p0[nxt] = ic[nxt] >= 0 ? cn.S[0][0] * x0 + cn.S[0][1] * x1 : T(0);
+          p1[nxt] = ic[nxt] >= 0 ? cn.S[0][2] * x0 + cn.S[0][3] * x1 : T(0);
         }
       }
       {
@@ -456,13 +502,21 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(
         if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[cur]);
       }
       __syncthreads();
-      if (q == kP - 1 && abort_flag) {
-        cp_async_wait<0>();  // own copies in flight
-        return;
+      if ((step + 1) % W == 0) {
+        // every thread has read its last record of window step / W: refill that buffer two windows on
+        if (abort_flag) {
+          // the next window may still be landing in shared memory: wait for it (bounded) before leaving
+          if (step + 1 <= last) wait_window((step + 1) / W);
+          return;
+        }
+        const int k = step / W + 2;
+        if (k * W <= last) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          request(k);
+        }
       }
     }
   }
-  cp_async_wait<0>();
 }
 
 }  // namespace
@@ -487,25 +541,28 @@ void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaS
 template <class T>
 bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStream_t st) {
   FlowView<T> V = fview<T>(F);
-  if (!V.s28 || !F.halo) return false;
+  T* pf = sizeof(T) == 4 ? reinterpret_cast<T*>(F.pk_fwd_f) : reinterpret_cast<T*>(F.pk_fwd_d);
+  T* pb = sizeof(T) == 4 ? reinterpret_cast<T*>(F.pk_bwd_f) : reinterpret_cast<T*>(F.pk_bwd_d);
+  if (!V.s28 || !F.halo || !pf || !pb) return false;
   int nby = (F.ny + kTY - 1) / kTY, nbz = (F.nz + kTZ - 1) / kTZ;
   unsigned grid = unsigned(nby * nbz);
   FlowStage& Fm = const_cast<FlowStage&>(F);
-  PS_TICK(); k_ff_residual<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, V.s28, W.y, W.zs, W.zp, W.wf);
+  PS_TICK(); k_ff_residual_pack<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, V.s28, W.y, W.zs, W.zp, pf,
+                                                                      pb);
   for (int dir = 0; dir < 2; ++dir) {
     uint32_t tag = uint32_t(++Fm.ilu_epoch);
     if (tag == 0) tag = uint32_t(++Fm.ilu_epoch);  // 0 marks never-written halo words
     int nx = F.nx, ny = F.ny, nz = F.nz;
-    const T *s28 = V.s28, *dinv = V.dinv, *a = W.wf, *zs = W.zs, *zp = W.zp;
-    T *t = W.t, *dz = W.dz;
+    const T* rec = dir == 0 ? pf : pb;
+    T* rec_bwd = pb;
     uint64_t* halo = F.halo;
     int* err = F.ilu_err;
     int64_t lim = F.spin_limit;
     int stall = F.test_stall;
-    void* args[] = {&nx, &ny, &nz, &s28, &dinv, &a, &zs, &zp, &t, &dz, &zout, &halo, &err, &tag, &lim, &stall};
+    void* args[] = {&nx, &ny, &nz, &rec, &rec_bwd, &zout, &halo, &err, &tag, &lim, &stall};
     const void* fn = dir == 0 ? (const void*)k_ilu_pencil<T, true> : (const void*)k_ilu_pencil<T, false>;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ring_bytes<T>()));
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kTY * kTZ, args, ring_bytes<T>(), st);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_bytes<T>()));
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kTY * kTZ, args, win_bytes<T>(), st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return false;

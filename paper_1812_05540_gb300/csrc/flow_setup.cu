@@ -123,6 +123,22 @@ __global__ void k_s28(int nx, int ny, int nz, const int32_t* __restrict__ rp, co
   }
 }
 
+// S/inv(U_ii) part of the sweep records (see FlowStage): forward lower blocks, backward upper blocks
+template <class T>
+__global__ void k_pack_sd(int64_t nc, const T* __restrict__ s28, const T* __restrict__ dinv, T* __restrict__ pf,
+                          T* __restrict__ pb) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int e = 0; e < 12; ++e) {
+    pf[c * 20 + e] = s28[c * 28 + e];
+    pb[c * 20 + e] = s28[c * 28 + 16 + e];
+  }
+  for (int e = 0; e < 4; ++e) {
+    pf[c * 20 + 12 + e] = dinv[c * 4 + e];
+    pb[c * 20 + 12 + e] = dinv[c * 4 + e];
+  }
+}
+
 __global__ void k_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = float(a[t]);
@@ -175,6 +191,17 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
     PS_TICK(); k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
+    if (mixed) {
+      PS_TRY(ar.alloc(&F.pk_fwd_f, size_t(nc) * 20));
+      PS_TRY(ar.alloc(&F.pk_bwd_f, size_t(nc) * 20));
+      PS_CUDA(cudaMemsetAsync(F.pk_fwd_f, 0, sizeof(float) * nc * 20, st));
+      PS_CUDA(cudaMemsetAsync(F.pk_bwd_f, 0, sizeof(float) * nc * 20, st));
+    } else {
+      PS_TRY(ar.alloc(&F.pk_fwd_d, size_t(nc) * 20));
+      PS_TRY(ar.alloc(&F.pk_bwd_d, size_t(nc) * 20));
+      PS_CUDA(cudaMemsetAsync(F.pk_fwd_d, 0, sizeof(double) * nc * 20, st));
+      PS_CUDA(cudaMemsetAsync(F.pk_bwd_d, 0, sizeof(double) * nc * 20, st));
+    }
     PS_TRY(ar.alloc(&F.halo, size_t(nc) * 4));
     PS_TRY(ar.alloc(&F.ilu_err, 4));
     PS_CUDA(cudaMemsetAsync(F.halo, 0, sizeof(uint64_t) * nc * 4, st));
@@ -200,7 +227,11 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TICK(); k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
     PS_TICK(); k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
     PS_CUDA(cudaGetLastError());
+    PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.dinv_f, F.pk_fwd_f, F.pk_bwd_f);
+  } else {
+    PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.dinv, F.pk_fwd_d, F.pk_bwd_d);
   }
+  PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
