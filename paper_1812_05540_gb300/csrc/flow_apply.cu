@@ -377,11 +377,6 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
   const int64_t pbase = valid ? int64_t(nx) * (yy + int64_t(ny) * zz) : 0;
   const int off = ry + rz;  // step s handles pencil position xs = s - off
-  auto cell_of = [&](int st) -> int64_t {
-    const int xs = st - off;
-    if (!valid || xs < 0 || xs >= nx) return -1;
-    return pbase + (FWD ? xs : nx - 1 - xs);
-  };
   // window k holds steps [k W, k W + W): the x range [xlo, xlo + W), records in ascending x
   auto win_xlo = [&](int k) { return FWD ? k * W - off : nx + off - k * W - W; };
   auto slot = [&](int b, int p) { return win + ((size_t(b) * (kTY * kTZ) + threadIdx.x) * W + p) * kRec; };
@@ -400,11 +395,6 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
     }
     return true;
   };
-  auto rec_of = [&](int st) -> const T* {  // the record of step st (its window must have landed)
-    const int k = st / W;
-    const int x = FWD ? st - off : nx - 1 - (st - off);
-    return slot(k & 1, x - win_xlo(k));
-  };
   if (threadIdx.x == 0) {
     abort_flag = 0;
     mbar_init(&mbar[0], kTY * kTZ);
@@ -414,22 +404,32 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
   __syncthreads();
   request(0);
   request(1);
+  // Per-step state kept incrementally: xs = step - off is the pencil position and gi the cell index
+  // (one step moves gi by +1 forward, -1 backward).  In the loop below the slot loop is unrolled over
+  // two windows, so a step's window buffer and record position are compile-time constants.
+  constexpr int64_t kStep = FWD ? 1 : -1;
+  const unsigned unx = unsigned(nx);
+  auto on = [&](int xs) { return valid && unsigned(xs) < unx; };
+  const T* tbase = win + size_t(threadIdx.x) * W * kRec;
+  auto rec_at = [&](int q2) -> const T* {  // record of the step whose unrolled index is q2 (mod 2W)
+    const int b = (q2 / W) & 1, pos = FWD ? (q2 % W) : (W - 1 - q2 % W);
+    return tbase + size_t(b) * (kTY * kTZ) * W * kRec + pos * kRec;
+  };
   HaloVal<T> hyr[2], hzr[2];
+  int xs = -off;                        // step 0
+  int64_t gi = pbase + (FWD ? xs : nx - 1 - xs);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int64_t ih = cell_of(q);
-    if (gy && ih >= 0) halo_fetch<T>(halo, ih + jy, hyr[q]);
-    if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[q]);
+    if (gy && on(xs + q)) halo_fetch<T>(halo, gi + q * kStep + jy, hyr[q]);
+    if (gz && on(xs + q)) halo_fetch<T>(halo, gi + q * kStep + jz, hzr[q]);
   }
   Cell<T> cs[2];
   T p0[2], p1[2];  // x-neighbour part of step s: FWD w - S_x-1 t_x-1, BWD S_x+1 dz_x+1
-  int64_t ic[2];
   bool ok0 = wait_window(0);
   if (!ok0) { atomicExch(err, 1); abort_flag = 1; }
-  ic[0] = cell_of(0);
-  if (ic[0] >= 0) read_cell<T>(rec_of(0), cs[0]);
-  if (FWD) { p0[0] = ic[0] >= 0 ? cs[0].a0 : T(0); p1[0] = ic[0] >= 0 ? cs[0].a1 : T(0); }
-  else { p0[0] = T(0); p1[0] = T(0); }
+  if (on(xs)) read_cell<T>(rec_at(0), cs[0]);
+  p0[0] = (FWD && on(xs)) ? cs[0].a0 : T(0);
+  p1[0] = (FWD && on(xs)) ? cs[0].a1 : T(0);
   for (int s0 = 0; s0 <= last; s0 += 2 * W) {
 #pragma unroll
     for (int q = 0; q < 2 * W; ++q) {
@@ -437,23 +437,24 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
       if (step > last) break;  // the same in every thread of the CTA
       const int cur = q & 1, nxt = (q + 1) & 1;
       const Cell<T>& c0 = cs[cur];
-      const int64_t i0 = ic[cur];
+      const bool act = on(xs);
+      const int64_t i0 = gi;
       T r0 = T(0), r1 = T(0);
-      if (i0 >= 0) {
+      if (act) {
         T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
         bool ok = true;
         if (gy) {
           ok = ok && halo_wait<T>(halo, i0 + jy, tag, hyr[cur], limit, err);
           halo_decode<T>(hyr[cur], ny0, ny1);
         } else if (hy) {
-          const T* qq = buf[(step - 1) & 1][lz][FWD ? ly - 1 : ly + 1];
+          const T* qq = buf[(q + 1) & 1][lz][FWD ? ly - 1 : ly + 1];
           ny0 = qq[0]; ny1 = qq[1];
         }
         if (gz) {
           ok = ok && halo_wait<T>(halo, i0 + jz, tag, hzr[cur], limit, err);
           halo_decode<T>(hzr[cur], nz0, nz1);
         } else if (hz) {
-          const T* qq = buf[(step - 1) & 1][FWD ? lz - 1 : lz + 1][ly];
+          const T* qq = buf[(q + 1) & 1][FWD ? lz - 1 : lz + 1][ly];
           nz0 = qq[0]; nz1 = qq[1];
         }
         if (!ok) { abort_flag = 1; atomicExch(err, 1); }
@@ -475,34 +476,32 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
           zout[2 * i0 + 1] = double(c0.z1 + r1);
         }
         if (py || pz) halo_put<T>(halo, i0, r0, r1, tag);
-        store2<T>(buf[step & 1][lz][ly], r0, r1);
+        store2<T>(buf[q & 1][lz][ly], r0, r1);
       }
       // step + 1's record (its window is waited for when step + 1 starts a window)
-      if ((step + 1) % W == 0 && step + 1 <= last) {
+      if ((q + 1) % W == 0 && step + 1 <= last) {
         if (!wait_window((step + 1) / W)) { abort_flag = 1; atomicExch(err, 1); }
       }
-      ic[nxt] = cell_of(step + 1);
-      if (ic[nxt] >= 0) read_cell<T>(rec_of(step + 1), cs[nxt]);
+      const bool actn = on(xs + 1);
+      if (actn) read_cell<T>(rec_at((q + 1) % (2 * W)), cs[nxt]);
       {
         // x-neighbour term of step + 1: this thread's result of step when both lie on the pencil
-        const bool hasx = ic[nxt] >= 0 && i0 >= 0;
-        const T x0 = hasx ? r0 : T(0), x1 = hasx ? r1 : T(0);
+        const T x0 = act ? r0 : T(0), x1 = act ? r1 : T(0);
         const Cell<T>& cn = cs[nxt];
         if (FWD) {
-          p0[nxt] = ic[nxt] >= 0 ? cn.a0 - (cn.S[2][0] * x0 + cn.S[2][1] * x1) : T(0);
-          p1[nxt] = ic[nxt] >= 0 ? cn.a1 - (cn.S[2][2] * x0 + cn.S[2][3] * x1) : T(0);
+          p0[nxt] = actn ? cn.a0 - (cn.S[2][0] * x0 + cn.S[2][1] * x1) : T(0);
+          p1[nxt] = actn ? cn.a1 - (cn.S[2][2] * x0 + cn.S[2][3] * x1) : T(0);
         } else {
-          p0[nxt] = ic[nxt] >= 0 ? cn.S[0][0] * x0 + cn.S[0][1] * x1 : T(0);
-          p1[nxt] = ic[nxt] >= 0 ? cn.S[0][2] * x0 + cn.S[0][3] * x1 : T(0);
+          p0[nxt] = actn ? cn.S[0][0] * x0 + cn.S[0][1] * x1 : T(0);
+          p1[nxt] = actn ? cn.S[0][2] * x0 + cn.S[0][3] * x1 : T(0);
         }
       }
-      {
-        const int64_t ih = cell_of(step + 2);
-        if (gy && ih >= 0) halo_fetch<T>(halo, ih + jy, hyr[cur]);
-        if (gz && ih >= 0) halo_fetch<T>(halo, ih + jz, hzr[cur]);
-      }
+      if (gy && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jy, hyr[cur]);
+      if (gz && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jz, hzr[cur]);
+      ++xs;
+      gi += kStep;
       __syncthreads();
-      if ((step + 1) % W == 0) {
+      if ((q + 1) % W == 0) {
         // every thread has read its last record of window step / W: refill that buffer two windows on
         if (abort_flag) {
           // the next window may still be landing in shared memory: wait for it (bounded) before leaving
