@@ -180,7 +180,9 @@ __global__ void k_to_stencil(Geo g, int64_t nrows, const int32_t* __restrict__ r
                                                                                           : ff_nb(g, i, j, k, s);
     bool have = nb >= 0 && q < q1 && ci[q] == nb;
     if (nb >= 0 && !have) atomicExch(bad, 1);
-    for (int e = 0; e < BS; ++e) out[(int64_t(s) * BS + e) * nrows + r] = have ? v[int64_t(q) * BS + e] : 0.0;
+    // blocked by 32 rows: [row / 32][slot][entry][row % 32]
+    for (int e = 0; e < BS; ++e)
+      out[((r >> 5) * int64_t(NS * BS) + s * BS + e) * 32 + (r & 31)] = have ? v[int64_t(q) * BS + e] : 0.0;
     if (have) ++q;
   }
   if (q != q1) atomicExch(bad, 1);
@@ -203,22 +205,22 @@ __global__ void __launch_bounds__(256) k_spmv_u_st(JacDev J, const double* __res
 #pragma unroll 3
     for (int s = 0; s < 27; ++s) {
       int64_t c = clampnb(uu_nb(g, i, j, k, s), I);
-      const double* A = J.uu_s + int64_t(s) * 9 * n + I;
+      const double* A = J.uu_s + (I >> 5) * int64_t(27 * 9 * 32) + (I & 31) + s * 9 * 32;
       double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
       // one FMA per block entry (the FP64 pipe is the bound: no separate products or sums)
-      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + n), x1, a0); a0 = fma(__ldg(A + 2 * n), x2, a0);
-      a1 = fma(__ldg(A + 3 * n), x0, a1); a1 = fma(__ldg(A + 4 * n), x1, a1); a1 = fma(__ldg(A + 5 * n), x2, a1);
-      a2 = fma(__ldg(A + 6 * n), x0, a2); a2 = fma(__ldg(A + 7 * n), x1, a2); a2 = fma(__ldg(A + 8 * n), x2, a2);
+      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + 32), x1, a0); a0 = fma(__ldg(A + 2 * 32), x2, a0);
+      a1 = fma(__ldg(A + 3 * 32), x0, a1); a1 = fma(__ldg(A + 4 * 32), x1, a1); a1 = fma(__ldg(A + 5 * 32), x2, a1);
+      a2 = fma(__ldg(A + 6 * 32), x0, a2); a2 = fma(__ldg(A + 7 * 32), x1, a2); a2 = fma(__ldg(A + 8 * 32), x2, a2);
     }
 #pragma unroll 4
     for (int s = 0; s < 8; ++s) {
       int64_t c = uf_nb(g, i, j, k, s);
       c = c >= 0 ? c : 0;
-      const double* A = J.uf_s + int64_t(s) * 6 * n + I;
+      const double* A = J.uf_s + (I >> 5) * int64_t(8 * 6 * 32) + (I & 31) + s * 6 * 32;
       double f0 = xf[2 * c], f1 = xf[2 * c + 1];
-      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + n), f1, a0);
-      a1 = fma(__ldg(A + 2 * n), f0, a1); a1 = fma(__ldg(A + 3 * n), f1, a1);
-      a2 = fma(__ldg(A + 4 * n), f0, a2); a2 = fma(__ldg(A + 5 * n), f1, a2);
+      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + 32), f1, a0);
+      a1 = fma(__ldg(A + 2 * 32), f0, a1); a1 = fma(__ldg(A + 3 * 32), f1, a1);
+      a2 = fma(__ldg(A + 4 * 32), f0, a2); a2 = fma(__ldg(A + 5 * 32), f1, a2);
     }
     if (b) {
       a0 = b[3 * I] - a0; a1 = b[3 * I + 1] - a1; a2 = b[3 * I + 2] - a2;
@@ -247,24 +249,23 @@ __global__ void __launch_bounds__(256) k_spmv_f_st(JacDev J, const double* __res
   double r2 = 0.0;
   if (C < J.nc) {
     int i = int(C % g.nx), j = int((C / g.nx) % g.ny), k = int(C / (int64_t(g.nx) * g.ny));
-    const int64_t n = J.nc;
     const double* xf = x + 3 * J.nn;
     double a0 = 0.0, a1 = 0.0;
 #pragma unroll 4
     for (int s = 0; s < 8; ++s) {
       int64_t c = fu_nb(g, i, j, k, s);
-      const double* A = J.fu_s + int64_t(s) * 6 * n + C;
+      const double* A = J.fu_s + (C >> 5) * int64_t(8 * 6 * 32) + (C & 31) + s * 6 * 32;
       double x0 = x[3 * c], x1 = x[3 * c + 1], x2 = x[3 * c + 2];
-      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + n), x1, a0); a0 = fma(__ldg(A + 2 * n), x2, a0);
-      a1 = fma(__ldg(A + 3 * n), x0, a1); a1 = fma(__ldg(A + 4 * n), x1, a1); a1 = fma(__ldg(A + 5 * n), x2, a1);
+      a0 = fma(__ldg(A), x0, a0); a0 = fma(__ldg(A + 32), x1, a0); a0 = fma(__ldg(A + 2 * 32), x2, a0);
+      a1 = fma(__ldg(A + 3 * 32), x0, a1); a1 = fma(__ldg(A + 4 * 32), x1, a1); a1 = fma(__ldg(A + 5 * 32), x2, a1);
     }
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       int64_t c = clampnb(ff_nb(g, i, j, k, s), C);
-      const double* A = J.ff_s + int64_t(s) * 4 * n + C;
+      const double* A = J.ff_s + (C >> 5) * int64_t(7 * 4 * 32) + (C & 31) + s * 4 * 32;
       double f0 = xf[2 * c], f1 = xf[2 * c + 1];
-      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + n), f1, a0);
-      a1 = fma(__ldg(A + 2 * n), f0, a1); a1 = fma(__ldg(A + 3 * n), f1, a1);
+      a0 = fma(__ldg(A), f0, a0); a0 = fma(__ldg(A + 32), f1, a0);
+      a1 = fma(__ldg(A + 2 * 32), f0, a1); a1 = fma(__ldg(A + 3 * 32), f1, a1);
     }
     int64_t o = 3 * J.nn + 2 * C;
     if (b) {
@@ -679,10 +680,11 @@ ps_status jac_build_stencil(Arena& ar, JacDev& J, bool* ok, cudaStream_t st) {
   int* bad;
   PS_TRY(ar.alloc(&bad, 1));
   PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
-  PS_TRY(ar.alloc(&J.uu_s, size_t(27) * 9 * J.nn));
-  PS_TRY(ar.alloc(&J.uf_s, size_t(8) * 6 * J.nn));
-  PS_TRY(ar.alloc(&J.fu_s, size_t(8) * 6 * J.nc));
-  PS_TRY(ar.alloc(&J.ff_s, size_t(7) * 4 * J.nc));
+  const size_t bn = size_t((J.nn + 31) / 32) * 32, bc = size_t((J.nc + 31) / 32) * 32;  // whole 32-row blocks
+  PS_TRY(ar.alloc(&J.uu_s, size_t(27) * 9 * bn));
+  PS_TRY(ar.alloc(&J.uf_s, size_t(8) * 6 * bn));
+  PS_TRY(ar.alloc(&J.fu_s, size_t(8) * 6 * bc));
+  PS_TRY(ar.alloc(&J.ff_s, size_t(7) * 4 * bc));
   PS_TICK(); k_to_stencil<0, 27, 9><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uu_rp, J.uu_ci, J.uu_v, J.uu_s, bad);
   PS_TICK(); k_to_stencil<1, 8, 6><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uf_rp, J.uf_ci, J.uf_v, J.uf_s, bad);
   PS_TICK(); k_to_stencil<2, 8, 6><<<grid_for(J.nc, 256), 256, 0, st>>>(g, J.nc, J.fu_rp, J.fu_ci, J.fu_v, J.fu_s, bad);

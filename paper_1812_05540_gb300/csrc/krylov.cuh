@@ -9,9 +9,9 @@ namespace ps_internal {
 struct JacDev {
   int64_t nn = 0, nc = 0;
   int nx = 0, ny = 0, nz = 0;
-  // stencil-indexed copies of the four blocks, zero padded at the boundary,
-  // structure-of-arrays: [slot][entry][row] (null when a pattern is not the
-  // structured one; the CSR kernels are used then)
+  // stencil-indexed copies of the four blocks, zero padded at the boundary, blocked by 32 rows:
+  // [row / 32][slot][entry][row % 32] (null when a pattern is not the structured one; the CSR
+  // kernels are used then)
   double *uu_s = nullptr, *uf_s = nullptr, *fu_s = nullptr, *ff_s = nullptr;
   int32_t *uu_rp = nullptr, *uu_ci = nullptr, *uf_rp = nullptr, *uf_ci = nullptr;
   int32_t *fu_rp = nullptr, *fu_ci = nullptr, *ff_rp = nullptr, *ff_ci = nullptr;
