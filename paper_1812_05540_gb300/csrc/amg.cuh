@@ -55,7 +55,16 @@ struct AmgLevel {
 struct Amg {
   int nc = 1;
   std::vector<AmgLevel> L;
+  // the V-cycle captured as a CUDA graph for one (input, output, stream) triple, replayed while the
+  // triple stays the same; gnodes kernel launches per replay
+  cudaGraphExec_t gexec = nullptr;
+  const void* gb = nullptr;
+  void* gx = nullptr;
+  cudaStream_t gst = nullptr;
+  int64_t gnodes = 0;
 };
+// destroys the captured V-cycle graph, if any
+void amg_release_graph(Amg& H);
 
 struct AmgParams {
   double theta;

@@ -355,6 +355,8 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.fu_v), jac->A_fu.val, sizeof(double) * jac->A_fu.nnzb * 6, kind, st));
   PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.ff_v), jac->A_ff.val, sizeof(double) * jac->A_ff.nnzb * 4, kind, st));
   PS_CUDA(cudaMemcpyAsync(h->dfs, jac->d_fs, sizeof(double) * 2 * h->nc, kind, st));
+  cudaStreamSynchronize(st);
+  amg_release_graph(h->amg_p);
   h->arf.free_all();
   h->F = FlowStage();
   h->amg_p = Amg();
@@ -560,6 +562,9 @@ ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv) {
 
 void ps_free(ps_handle* h) {
   if (!h) return;
+  cudaStreamSynchronize(h->st);
+  amg_release_graph(h->amg_u);
+  amg_release_graph(h->amg_p);
   h->arf.free_all();
   h->ar.free_all();
   cudaStreamSynchronize(h->st);

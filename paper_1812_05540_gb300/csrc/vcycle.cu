@@ -389,6 +389,12 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
   smooth_post<T, NC>(L, V, sp, b, xs, xs == x ? t : x, d, out, st);
 }
 
+template <class T>
+void vcycle_launch(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st) {
+  if (H.nc == 3) vcycle_level<T, 3>(H, 0, sp, b, x, st);
+  else vcycle_level<T, 1>(H, 0, sp, b, x, st);
+}
+
 }  // namespace
 
 template <class T>
@@ -403,10 +409,53 @@ ps_status amg_alloc_work(Arena& ar, Amg& H) {
   return PS_OK;
 }
 
+void amg_release_graph(Amg& H) {
+  if (H.gexec) cudaGraphExecDestroy(H.gexec);
+  H.gexec = nullptr;
+  H.gb = nullptr;
+  H.gx = nullptr;
+  H.gst = nullptr;
+  H.gnodes = 0;
+}
+
+// The V-cycle is about thirty short kernels whose arguments depend only on the hierarchy, b and x:
+// captured once into a CUDA graph and replayed, so that the coarse levels do not wait on kernel
+// launches.  Streams that cannot be captured (the legacy default stream) run the kernels directly.
 template <class T>
 ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st) {
-  if (H.nc == 3) vcycle_level<T, 3>(H, 0, sp, b, x, st);
-  else vcycle_level<T, 1>(H, 0, sp, b, x, st);
+  if (H.gexec && H.gb == b && H.gx == x && H.gst == st) {
+    PS_CUDA(cudaGraphLaunch(H.gexec, st));
+    g_launches.fetch_add(H.gnodes, std::memory_order_relaxed);
+    return PS_OK;
+  }
+  if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+    amg_release_graph(H);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      vcycle_launch<T>(H, sp, b, x, st);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (e == cudaSuccess && g) {
+        size_t nodes = 0;
+        cudaGraphGetNodes(g, nullptr, &nodes);
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e == cudaSuccess) {
+          H.gexec = ex;
+          H.gb = b;
+          H.gx = x;
+          H.gst = st;
+          H.gnodes = int64_t(nodes);  // the kernels ticked while capturing run in this first launch
+          PS_CUDA(cudaGraphLaunch(ex, st));
+          return PS_OK;
+        }
+      }
+      cudaGetLastError();
+    } else {
+      cudaGetLastError();
+    }
+  }
+  vcycle_launch<T>(H, sp, b, x, st);
   PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
