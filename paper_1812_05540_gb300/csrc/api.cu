@@ -172,6 +172,16 @@ ps_status build_flow(ps_handle* h) {
     PS_TRY(ar.alloc(&F.fu_vf, nfu * 6 + 1));
     PS_TICK(); k_d2f<<<grid_for(nfu * 6, 256), 256, 0, st>>>(h->J.fu_v, F.fu_vf, nfu * 6);
   }
+  // steps 2 and 4 on the structured grid: A_fu from the Jacobian's stencil copy (FP32 copy in mixed mode)
+  if (h->J.fu_s) {
+    if (h->mixed) {
+      const int64_t cnt = (h->nc + 31) / 32 * 32 * 8 * 6;
+      PS_TRY(ar.alloc(&F.fu_st_f, cnt));
+      PS_TICK(); k_d2f<<<grid_for(cnt, 256), 256, 0, st>>>(h->J.fu_s, F.fu_st_f, cnt);
+    } else {
+      F.fu_st_d = h->J.fu_s;
+    }
+  }
   AmgParams ap;
   ap.theta = h->prm.theta_p; ap.coarse_max = h->prm.coarse_max_p; ap.max_levels = h->prm.max_levels;
   ap.mixed = h->mixed;

@@ -39,6 +39,13 @@ struct FlowStage {
   int32_t *fu_rp = nullptr, *fu_ci = nullptr;
   const double* fu_v = nullptr;
   float* fu_vf = nullptr;
+  // stencil-slot copies for steps 2 and 4 (null when the patterns are not the structured ones): A_fu
+  // by cell corner, blocked by 32 cells [cell / 32][8 corners][6][cell % 32]; A_ps by 7-point slot,
+  // [cell / 32][7][cell % 32]; FP64 (the Jacobian's own stencil copy) and FP32
+  const double* fu_st_d = nullptr;
+  float* fu_st_f = nullptr;
+  double* aps_st_d = nullptr;
+  float* aps_st_f = nullptr;
 };
 
 // Build S_ff^(FS), S_pp, the level lists and the ILU(0) factors from the

@@ -54,6 +54,49 @@ __global__ void k_step23(int64_t nc, const int32_t* __restrict__ rp, const int32
   }
 }
 
+// steps 2-3 with A_fu by cell corner (blocked by 32 cells), one thread per cell
+template <class T>
+__global__ void k_step23_st(int nx, int ny, int nz, const T* __restrict__ fu, const T* __restrict__ vf,
+                            const T* __restrict__ zu, const T* __restrict__ dss, T* __restrict__ y,
+                            T* __restrict__ zs) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nc = int64_t(nx) * ny * nz;
+  if (c >= nc) return;
+  const int i = int(c % nx), j = int((c / nx) % ny), k = int(c / (int64_t(nx) * ny));
+  const T* A = fu + (c >> 5) * int64_t(8 * 6 * 32) + (c & 31);
+  T a0 = T(0), a1 = T(0);
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int64_t J = (i + (s & 1)) + int64_t(nx + 1) * ((j + ((s >> 1) & 1)) + int64_t(ny + 1) * (k + (s >> 2)));
+    const T x0 = zu[3 * J], x1 = zu[3 * J + 1], x2 = zu[3 * J + 2];
+    const T* b = A + s * 6 * 32;
+    a0 = fma(b[0], x0, a0); a0 = fma(b[32], x1, a0); a0 = fma(b[64], x2, a0);
+    a1 = fma(b[96], x0, a1); a1 = fma(b[128], x1, a1); a1 = fma(b[160], x2, a1);
+  }
+  const T ys = vf[2 * c] - a0, yp = vf[2 * c + 1] - a1;
+  y[2 * c] = ys;
+  y[2 * c + 1] = yp;
+  zs[c] = ys / dss[c];
+}
+
+// step 4 with A_ps by 7-point slot (blocked by 32 cells), one thread per cell
+template <class T>
+__global__ void k_step4_st(int nx, int ny, int nz, const T* __restrict__ aps, const T* __restrict__ y,
+                           const T* __restrict__ zs, T* __restrict__ wp) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nc = int64_t(nx) * ny * nz, nxy = int64_t(nx) * ny;
+  if (c >= nc) return;
+  const int i = int(c % nx), j = int((c / nx) % ny), k = int(c / nxy);
+  const int64_t nb[7] = {c - nxy, c - nx, c - 1, c, c + 1, c + nx, c + nxy};
+  const bool in[7] = {k > 0, j > 0, i > 0, true, i + 1 < nx, j + 1 < ny, k + 1 < nz};
+  const T* A = aps + (c >> 5) * int64_t(7 * 32) + (c & 31);
+  T a = T(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    if (in[q]) a = fma(A[q * 32], zs[nb[q]], a);
+  wp[c] = y[2 * c + 1] - a;
+}
+
 // step 4: w_p = y_p - A_ps z_s with the complete A_ps (8 lanes per cell)
 template <class T>
 __global__ void k_step4(int64_t nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -533,8 +576,19 @@ ps_status flow_alloc_work(Arena& ar, const FlowStage& F, FlowWork<T>& W) {
 template <class T>
 void alg1_steps_2_4(const FlowStage& F, const FlowWork<T>& W, const T* zu, cudaStream_t st) {
   FlowView<T> V = fview<T>(F);
-  PS_TICK(); k_step23<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.fu_rp, F.fu_ci, V.fu, W.vf, zu, V.dss, W.y, W.zs);
-  PS_TICK(); k_step4<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.rp, F.ci, V.aps, W.y, W.zs, W.wp);
+  const T* fu_st = sizeof(T) == 4 ? reinterpret_cast<const T*>(F.fu_st_f) : reinterpret_cast<const T*>(F.fu_st_d);
+  const T* aps_st = sizeof(T) == 4 ? reinterpret_cast<const T*>(F.aps_st_f) : reinterpret_cast<const T*>(F.aps_st_d);
+  if (fu_st) {
+    PS_TICK(); k_step23_st<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, fu_st, W.vf, zu, V.dss, W.y, W.zs);
+  } else {
+    PS_TICK(); k_step23<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.fu_rp, F.fu_ci, V.fu, W.vf, zu, V.dss, W.y,
+                                                                  W.zs);
+  }
+  if (aps_st) {
+    PS_TICK(); k_step4_st<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, aps_st, W.y, W.zs, W.wp);
+  } else {
+    PS_TICK(); k_step4<T><<<grid_for(F.nc * 8, 256), 256, 0, st>>>(F.nc, F.rp, F.ci, V.aps, W.y, W.zs, W.wp);
+  }
 }
 
 template <class T>

@@ -123,6 +123,15 @@ __global__ void k_s28(int nx, int ny, int nz, const int32_t* __restrict__ rp, co
   }
 }
 
+// A_ps by 7-point slot, blocked by 32 cells, from the stencil blocks of S_ff^(FS) (the fixed-stress
+// terms change only the (s, p) and (p, p) entries, so entry (p, s) is A_ps)
+template <class T>
+__global__ void k_aps_st(int64_t nc, const T* __restrict__ s28, T* __restrict__ out) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int q = 0; q < 7; ++q) out[((c >> 5) * 7 + q) * 32 + (c & 31)] = s28[c * 28 + q * 4 + 2];
+}
+
 // S/inv(U_ii) part of the sweep records (see FlowStage): forward lower blocks, backward upper blocks
 template <class T>
 __global__ void k_pack_sd(int64_t nc, const T* __restrict__ s28, const T* __restrict__ dinv, T* __restrict__ pf,
@@ -228,8 +237,12 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TICK(); k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
     PS_CUDA(cudaGetLastError());
     PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.dinv_f, F.pk_fwd_f, F.pk_bwd_f);
+    if (!F.aps_st_f) PS_TRY(ar.alloc(&F.aps_st_f, size_t((nc + 31) / 32) * 32 * 7));
+    PS_TICK(); k_aps_st<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.aps_st_f);
   } else {
     PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.dinv, F.pk_fwd_d, F.pk_bwd_d);
+    if (!F.aps_st_d) PS_TRY(ar.alloc(&F.aps_st_d, size_t((nc + 31) / 32) * 32 * 7));
+    PS_TICK(); k_aps_st<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.aps_st_d);
   }
   PS_CUDA(cudaGetLastError());
   return PS_OK;
