@@ -313,6 +313,7 @@ __global__ void k_rank_rows(int64_t n, const int32_t* __restrict__ rp, const int
 constexpr int kUniq = 1024;   // largest class
 constexpr int kEmpty = -1;
 constexpr int kClasses = 4;
+constexpr int64_t kDenseMaxCols = 1024;  // dense-accumulator path for long rows up to this many columns
 __host__ __device__ constexpr int class_cap(int b) { return b == 0 ? 32 : b == 1 ? 128 : b == 2 ? 512 : 1024; }
 
 template <int H>
@@ -421,13 +422,31 @@ __global__ void k_spgemm_count(const int32_t* __restrict__ rows, int32_t nrows, 
 }
 
 // fill classes from the exact counts (long rows, cnt = 0 and listed apart, are skipped)
+// With few output columns (dense_ok), rows with more than class_cap(1) distinct columns go to the
+// dense-accumulator path, one CTA per row, instead of a warp with a large hash table: they are
+// marked long and appended to longrows.  Long rows are not binned.
 __global__ void k_spgemm_fill_bins(int64_t n, const int32_t* __restrict__ cnt, int32_t* __restrict__ lists,
-                                   int32_t* __restrict__ counts) {
+                                   int32_t* __restrict__ counts, int dense_ok, uint8_t* __restrict__ islong,
+                                   int32_t* __restrict__ longrows, int32_t* __restrict__ nlong) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || islong[i]) return;
   int32_t u = cnt[i];
+  if (dense_ok && u > class_cap(1)) {
+    islong[i] = 1;
+    longrows[atomicAdd(nlong, 1)] = int32_t(i);
+    return;
+  }
   int b = u <= class_cap(0) ? 0 : u <= class_cap(1) ? 1 : u <= class_cap(2) ? 2 : 3;
   lists[int64_t(b) * n + atomicAdd(&counts[b], 1)] = int32_t(i);
+}
+
+// rows of the largest product-bound class handled by the dense path from the count pass on
+__global__ void k_spgemm_mark_long(const int32_t* __restrict__ rows, int32_t nr, uint8_t* __restrict__ islong,
+                                   int32_t* __restrict__ longrows, int32_t* __restrict__ nlong) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nr) return;
+  islong[rows[t]] = 1;
+  longrows[atomicAdd(nlong, 1)] = rows[t];
 }
 
 // dense path, one CTA per long row: stamp[j] marks the columns seen for this row
@@ -724,10 +743,17 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   int32_t hc[2 * kClasses];
   PS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
   PS_CUDA(cudaStreamSynchronize(st));
+  // few output columns: the dense path (one CTA per row) takes the rows with the most products
+  const bool dense_ok = m <= kDenseMaxCols;
+  PS_CUDA(cudaMemsetAsync(islong, 0, size_t(n) + 1, st));
   for (int b = 0; b < kClasses; ++b) {
     int32_t nr = hc[b];
     if (nr == 0) continue;
     const int32_t* rows = lists + int64_t(b) * n;
+    if (dense_ok && b == kClasses - 1) {
+      PS_TICK(); k_spgemm_mark_long<<<grid_for(nr, 256), 256, 0, st>>>(rows, nr, islong, longrows, nlong);
+      continue;
+    }
     for_class(b, [&](auto cc) {
       constexpr int C = decltype(cc)::value;
       const int wpb = C <= 128 ? 8 : 4;
@@ -762,12 +788,29 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   *cnnz = tot;
   PS_TRY(ar.alloc(cci, size_t(tot) + 1));
   PS_TRY(ar.alloc(cv, (size_t(tot) + 1) * NC));
-  // fill pass, binned by the exact count (long rows, whose count came from the dense pass, land in
-  // the last class and are skipped there by islong)
+  // fill pass, binned by the exact count; long rows (and, with few output columns, rows with many
+  // distinct columns) take the dense path
   PS_CUDA(cudaMemsetAsync(counts + kClasses, 0, sizeof(int32_t) * kClasses, st));
-  PS_TICK(); k_spgemm_fill_bins<<<grid_for(n, 256), 256, 0, st>>>(n, cnt, lists, counts + kClasses);
+  PS_TICK(); k_spgemm_fill_bins<<<grid_for(n, 256), 256, 0, st>>>(n, cnt, lists, counts + kClasses, dense_ok ? 1 : 0,
+                                                                islong, longrows, nlong);
   PS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   PS_CUDA(cudaStreamSynchronize(st));
+  if (hl > B) {
+    // more long rows than the count pass had: a larger batch of accumulators (tags are unique per
+    // row, so fresh zeroed stamps serve any row)
+    int64_t per = m * (4 + 8 * NC);
+    int64_t Bmax = (int64_t(256) << 20) / (per > 0 ? per : 1);
+    if (Bmax < 1) Bmax = 1;
+    int64_t Bn = hl < Bmax ? hl : Bmax;
+    if (Bn > B) {
+      if (stamp) { ar.release(stamp); ar.release(acc); }
+      B = Bn;
+      PS_TRY(ar.alloc(&stamp, size_t(B) * m + 1));
+      PS_TRY(ar.alloc(&acc, (size_t(B) * m + 1) * NC));
+      PS_CUDA(cudaMemsetAsync(stamp, 0, sizeof(int32_t) * (size_t(B) * m + 1), st));
+    }
+  }
   for (int b = 0; b < kClasses; ++b) {
     int32_t nr = hc[kClasses + b];
     if (nr == 0) continue;
