@@ -52,6 +52,7 @@ struct ps_handle {
   double* zu64 = nullptr;
   // Krylov
   int m = 100;
+  int64_t ldv = 0;  // basis column stride: n rounded up to 32 rows, rows n..ldv-1 kept zero
   double *V = nullptr, *Z = nullptr, *r = nullptr, *b = nullptr, *x = nullptr, *part = nullptr, *mpart = nullptr;
   KrylovState K;
   double* hsc = nullptr;  // pinned: 8 scalars
@@ -254,7 +255,8 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   // Krylov workspace
   int m = h->m;
   int64_t n = h->n;
-  PS_TRY(ar.alloc(&h->V, size_t(n) * (m + 1)));
+  h->ldv = (n + 31) / 32 * 32;
+  PS_TRY(ar.alloc(&h->V, size_t(h->ldv) * (m + 1)));
   PS_TRY(ar.alloc(&h->Z, size_t(n) * m));
   PS_TRY(ar.alloc(&h->r, n));
   PS_TRY(ar.alloc(&h->b, n));
@@ -404,6 +406,9 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
   PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
   double* xk = h->x;
   fill_zero(xk, n, st);
+  const int64_t ldv = h->ldv;
+  if (ldv > n)  // padding rows of the basis (a failed solve may have left a NaN there)
+    PS_CUDA(cudaMemset2DAsync(h->V + n, size_t(ldv) * sizeof(double), 0, size_t(ldv - n) * sizeof(double), m + 1, st));
   // ||b||
   multidot(h->V, n, 0, h->b, n, h->mpart, K.sc + 7, 1, nullptr, st);
   PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -427,27 +432,27 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
       int jend = -1;
       bool brk = false, nanf = false, timeout = false, gs_timeout = false;
       for (int j = 0; j < m; ++j) {
-        double* vj = h->V + int64_t(j) * n;
+        double* vj = h->V + j * ldv;
         double* zj = h->Z + int64_t(j) * n;
-        double* w = h->V + int64_t(j + 1) * n;
+        double* w = h->V + (j + 1) * ldv;
         cudaEventRecord(h->ev[0], st);
         PS_TRY(apply_prec(h, vj, zj));
         cudaEventRecord(h->ev[1], st);
         jac_spmv(h->J, zj, w, nullptr, nullptr, st);
         cudaEventRecord(h->ev[2], st);
         if (h->prm.ortho == PS_ORTHO_MGS &&
-            mgs_step(h->V, n, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
+            mgs_step(h->V, ldv, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
                      h->prm.test_stall_gs, h->prm.ortho_sweep, st)) {
           // modified Gram-Schmidt (w normalised in the same launch)
           arnoldi_finish(K, m, j, st);
         } else {
           // classical Gram-Schmidt with selective reorthogonalisation
-          multidot(h->V, n, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
+          multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
           PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-          mupdate(h->V, n, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
+          mupdate(h->V, ldv, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
           arnoldi_check(K, st);
-          multidot(h->V, n, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
-          mupdate(h->V, n, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
+          multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
+          mupdate(h->V, ldv, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
           arnoldi_finish(K, m, j, st);
           scale_vec(w, w, n, K.sc + 4, st);
         }

@@ -2,7 +2,9 @@
 // a fixed order (per-block partial sums, then one block over the partials), so
 // repeated solves give identical iterates.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 
 #include "krylov.cuh"
 
@@ -509,9 +511,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
 }
 
 // Gm[k * kS + (l - S * (k / S))] = v_k . v_l for the block-mates l < k of v_k (S vectors per sweep).
+// Rows are taken in pairs (one 16-byte load per vector and pair): the basis columns are ldv apart with
+// ldv even, and when n is odd the row n of every column is kept zero, so the last pair adds nothing.
 template <int S>
 __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const double* __restrict__ V, int64_t ldv, int j,
-                                                     double* __restrict__ w, int64_t n, double* __restrict__ h,
+                                                     double* __restrict__ w, int n2, double* __restrict__ h,
                                                      double* __restrict__ Gm, double* __restrict__ sc,
                                                      int* __restrict__ flag, double* __restrict__ part,
                                                      unsigned long long* bar, unsigned long long base, int64_t limit,
@@ -523,7 +527,10 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
   __shared__ double sums[R];
   __shared__ double scratch[kMgsThreads / 16];
   const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t stride = int64_t(G) * kMgsThreads, t0 = int64_t(blockIdx.x) * kMgsThreads + threadIdx.x;
+  const int stride = G * kMgsThreads, t0 = int(blockIdx.x) * kMgsThreads + int(threadIdx.x);
+  const double2* __restrict__ V2 = reinterpret_cast<const double2*>(V);
+  double2* __restrict__ w2 = reinterpret_cast<double2*>(w);
+  const int64_t ld2 = ldv / 2;
   int* err = flag + 2;
   const int nb = j / S + 1;  // blocks of basis vectors 0..j
   double hp[S];              // coefficients of the previous block
@@ -536,66 +543,91 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
     const int cn = p < nb ? min(S, j + 1 - c0) : 0;  // vectors dotted in this sweep
     const bool last = p == nb - 1;
     const int ng = last ? cn - 1 : 0;                // Gram entries of v_j with its block-mates
-    const double* vprev[S];
-    const double* vcur[S];
+    const double2* vprev[S];
+    const double2* vcur[S];
 #pragma unroll
     for (int c = 0; c < S; ++c) {
-      vprev[c] = V + int64_t(pc0 + (c < pcn ? c : 0)) * ldv;
-      vcur[c] = V + int64_t(c0 + (c < cn ? c : 0)) * ldv;
+      vprev[c] = V2 + int64_t(pc0 + (c < pcn ? c : 0)) * ld2;
+      vcur[c] = V2 + int64_t(c0 + (c < cn ? c : 0)) * ld2;
     }
-    const double* vjp = V + int64_t(j) * ldv;
+    const double2* vjp = V2 + int64_t(j) * ld2;
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
     if (p < nb && pcn == S && cn == S && ng == 0) {
       // full blocks: update by the previous block, dots with this one
-#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
-      for (int64_t e = t0; e < n; e += stride) {
-        double we = w[e];
+#pragma unroll(S <= 2 ? 2 : 1)
+      for (int e = t0; e < n2; e += stride) {
+        double2 we = w2[e];
 #pragma unroll
-        for (int c = 0; c < S; ++c) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
-        w[e] = we;
+        for (int c = 0; c < S; ++c) {
+          const double2 v = __ldcs(vprev[c] + e);
+          we.x = fma(-hp[c], v.x, we.x);
+          we.y = fma(-hp[c], v.y, we.y);
+        }
+        w2[e] = we;
 #pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = fma(vcur[c][e], we, acc[c]);
+        for (int c = 0; c < S; ++c) {
+          const double2 v = vcur[c][e];
+          acc[c] = fma(v.x, we.x, acc[c]);
+          acc[c] = fma(v.y, we.y, acc[c]);
+        }
       }
     } else if (p < nb && pcn == 0 && cn == S && ng == 0) {
       // first sweep: dots only
-#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
-      for (int64_t e = t0; e < n; e += stride) {
-        const double we = w[e];
+#pragma unroll(S <= 2 ? 2 : 1)
+      for (int e = t0; e < n2; e += stride) {
+        const double2 we = w2[e];
 #pragma unroll
-        for (int c = 0; c < S; ++c) acc[c] = fma(vcur[c][e], we, acc[c]);
+        for (int c = 0; c < S; ++c) {
+          const double2 v = vcur[c][e];
+          acc[c] = fma(v.x, we.x, acc[c]);
+          acc[c] = fma(v.y, we.y, acc[c]);
+        }
       }
     } else if (p == nb && pcn == S) {
       // last sweep after a full block: update and ||w||^2
-#pragma unroll(S <= 2 ? 4 : (S == 4 ? 2 : 1))
-      for (int64_t e = t0; e < n; e += stride) {
-        double we = w[e];
+#pragma unroll(S <= 2 ? 2 : 1)
+      for (int e = t0; e < n2; e += stride) {
+        double2 we = w2[e];
 #pragma unroll
-        for (int c = 0; c < S; ++c) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
-        w[e] = we;
-        acc[R - 1] = fma(we, we, acc[R - 1]);
+        for (int c = 0; c < S; ++c) {
+          const double2 v = __ldcs(vprev[c] + e);
+          we.x = fma(-hp[c], v.x, we.x);
+          we.y = fma(-hp[c], v.y, we.y);
+        }
+        w2[e] = we;
+        acc[R - 1] = fma(we.x, we.x, acc[R - 1]);
+        acc[R - 1] = fma(we.y, we.y, acc[R - 1]);
       }
     } else {
       // partial blocks (the block holding v_j, and the update by it)
-#pragma unroll 2
-      for (int64_t e = t0; e < n; e += stride) {
-        double we = w[e];
+      for (int e = t0; e < n2; e += stride) {
+        double2 we = w2[e];
 #pragma unroll
         for (int c = 0; c < S; ++c)
-          if (c < pcn) we = fma(-hp[c], __ldcs(vprev[c] + e), we);
-        if (pcn > 0) w[e] = we;
+          if (c < pcn) {
+            const double2 v = __ldcs(vprev[c] + e);
+            we.x = fma(-hp[c], v.x, we.x);
+            we.y = fma(-hp[c], v.y, we.y);
+          }
+        if (pcn > 0) w2[e] = we;
         if (p < nb) {
-          const double vj = ng > 0 ? vjp[e] : 0.0;
+          const double2 vj = ng > 0 ? vjp[e] : make_double2(0.0, 0.0);
 #pragma unroll
           for (int c = 0; c < S; ++c)
             if (c < cn) {
-              const double v = vcur[c][e];
-              acc[c] = fma(v, we, acc[c]);
-              if (c < ng) acc[S + c] = fma(v, vj, acc[S + c]);
+              const double2 v = vcur[c][e];
+              acc[c] = fma(v.x, we.x, acc[c]);
+              acc[c] = fma(v.y, we.y, acc[c]);
+              if (c < ng) {
+                acc[S + c] = fma(v.x, vj.x, acc[S + c]);
+                acc[S + c] = fma(v.y, vj.y, acc[S + c]);
+              }
             }
         } else {
-          acc[R - 1] = fma(we, we, acc[R - 1]);
+          acc[R - 1] = fma(we.x, we.x, acc[R - 1]);
+          acc[R - 1] = fma(we.y, we.y, acc[R - 1]);
         }
       }
     }
@@ -668,7 +700,12 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
   // the same reciprocal as the Arnoldi finish step computes
   double hn = sqrt(wn2);
   double inv = hn > 0.0 ? 1.0 / hn : 0.0;
-  for (int64_t e = t0; e < n; e += stride) w[e] *= inv;
+  for (int e = t0; e < n2; e += stride) {
+    double2 we = w2[e];
+    we.x *= inv;
+    we.y *= inv;
+    w2[e] = we;
+  }
 }
 
 constexpr int kVecBlocks = 1216;  // 8 x 152 SMs
@@ -771,12 +808,18 @@ bool mgs_step(const double* V, int64_t ldv, int j, double* w, int64_t n, KrylovS
   // small systems use fewer CTAs (at least 16 rows per thread) so that concurrent requests overlap
   int64_t want = (n + int64_t(kMgsThreads) * 16 - 1) / (int64_t(kMgsThreads) * 16);
   if (want < blocks) blocks = int(want < 1 ? 1 : want);
+  // rows in pairs: 16-byte aligned columns an even ldv apart, and pair indices that stay in int range
+  const int64_t n2l = (n + 1) / 2;
+  if ((ldv & 1) || ldv < 2 * n2l || (reinterpret_cast<uintptr_t>(V) & 15) || (reinterpret_cast<uintptr_t>(w) & 15) ||
+      n2l + int64_t(blocks) * kMgsThreads > int64_t(INT32_MAX))
+    return false;
+  int n2 = int(n2l);
   unsigned long long b0 = *base;
   double* h = K.h1;
   double* Gm = K.gram;
   double* sc = K.sc;
   int* flag = K.flag;
-  void* args[] = {&V, &ldv, &j, &w, &n, &h, &Gm, &sc, &flag, &part, &bar, &b0, &limit, &stall};
+  void* args[] = {&V, &ldv, &j, &w, &n2, &h, &Gm, &sc, &flag, &part, &bar, &b0, &limit, &stall};
   const void* fn = S == 8 ? (const void*)k_mgs<8> : S == 4 ? (const void*)k_mgs<4> : S == 2 ? (const void*)k_mgs<2>
                                                                                      : (const void*)k_mgs<1>;
   if (cudaLaunchCooperativeKernel(fn, blocks, kMgsThreads, args, 0, st) != cudaSuccess) {

@@ -43,7 +43,8 @@ void fill_zero(double* x, int64_t n, cudaStream_t st);
 // small dense FGMRES state on the device (declared below); modified Gram-Schmidt step in one
 // cooperative launch: h1[0..j] = coefficients, sc[1] = ||w||^2 after projection, w normalised in
 // place, flag[0] = 0; a grid barrier that gives up sets flag[2].  Returns false when the launch is
-// not possible (blocks = 0 or a cooperative-launch error): the caller falls back to CGS2.
+// not possible (blocks = 0 or a cooperative-launch error): the caller falls back to CGS2.  Rows are
+// read in pairs: V and w 16-byte aligned, ldv even, and when n is odd row n of every column is zero.
 // K.gram holds (m + 1) x mgs_gram_stride() in-block Gram entries; part holds mgs_partials() x blocks.
 struct KrylovState;
 ps_status mgs_grid(int* blocks);  // four entries: sweeps of 1, 2, 4, 8 vectors
