@@ -5,6 +5,7 @@
 // This translation unit is compiled without floating-point contraction and
 // every floating-point sum is taken in a fixed order (ascending column / inner
 // index), so the aggregates and coarse operators are reproducible bit for bit.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 
@@ -1097,7 +1098,7 @@ ps_status amg_stencil(Arena& ar, Amg& H, int gx, int gy, int gz, int ns, bool mi
   *ok = false;
   if (H.L.empty()) return PS_OK;
   AmgLevel& L = H.L[0];
-  if (L.coarsest || int64_t(gx) * gy * gz != L.n || (ns != 27 && ns != 7)) return PS_OK;
+  if (L.coarsest || int64_t(gx) * gy * gz != L.n || L.n >= int64_t(INT32_MAX) || (ns != 27 && ns != 7)) return PS_OK;
   int nc = H.nc;
   size_t cnt = size_t(ns) * nc * L.n;
   int* bad = nullptr;

@@ -82,17 +82,20 @@ struct StencilRows {
 #pragma unroll
     for (int c = 0; c < NC; ++c) s[c] = T(0);
     if (!active) return;
-    const int64_t gxy = int64_t(gx) * gy;
-    const int iz = int(i / gxy);
-    const int64_t rem = i - iz * gxy;
-    const int iy = int(rem / gx), ix = int(rem - int64_t(iy) * gx);
+    // the grid has fewer than 2^31 rows (amg_stencil checks it), so coordinates fit in int
+    const int gxy = gx * gy, ii = int(i);
+    const int iz = ii / gxy, rem = ii - iz * gxy;
+    const int iy = rem / gx, ix = rem - iy * gx;
+    const bool inx[3] = {ix > 0, true, ix < gx - 1}, iny[3] = {iy > 0, true, iy < gy - 1},
+               inz[3] = {iz > 0, true, iz < gz - 1};
+    // values of slots that leave the grid are stored as zero: such a slot reads x at the row
+    // itself, so every slot is loaded without a branch and adds exactly zero
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       int dx, dy, dz;
       slot_offset<NS>(q, dx, dy, dz);
-      const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
-      if (jx < 0 || jx >= gx || jy < 0 || jy >= gy || jz < 0 || jz >= gz) continue;
-      const int64_t j = i + dx + int64_t(gx) * (dy + int64_t(gy) * dz);
+      const bool in = inx[dx + 1] && iny[dy + 1] && inz[dz + 1];
+      const int64_t j = i + (in ? dx + gx * dy + gxy * dz : 0);
 #pragma unroll
       for (int c = 0; c < NC; ++c) s[c] += __ldg(v + (int64_t(q) * NC + c) * n + i) * xf(j, c);
     }
