@@ -510,6 +510,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
   return ok != 0;
 }
 
+// Warp sums of R values per lane (R a power of two, at most 32) by a transposing butterfly: at each of
+// the first log2(R) levels a lane keeps one half of its values, sends the other half to its partner and
+// adds what it receives, so the adds per lane are R/2 + R/4 + ... instead of 5 R.  Afterwards the lanes
+// of each group of 32 / R hold the full sum of value *which, the same in every lane of the group.
+template <int R>
+__device__ __forceinline__ double warp_sum_many(double (&a)[R], int lane, int& which) {
+  int idx = 0;
+  int mask = 16;
+#pragma unroll
+  for (int half = R / 2; half >= 1; half /= 2, mask >>= 1) {
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double keep = up ? a[half + i] : a[i];
+      const double send = up ? a[i] : a[half + i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+    idx = (idx << 1) | (up ? 1 : 0);
+  }
+  double v = a[0];
+#pragma unroll
+  for (; mask > 0; mask >>= 1) v += __shfl_xor_sync(0xffffffffu, v, mask);
+  which = idx;
+  return v;
+}
+
 // Gm[k * kS + (l - S * (k / S))] = v_k . v_l for the block-mates l < k of v_k (S vectors per sweep).
 // Rows are taken in pairs (one 16-byte load per vector and pair): the basis columns are ldv apart with
 // ldv even, and when n is odd the row n of every column is kept zero, so the last pair adds nothing.
@@ -632,10 +658,10 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
       }
     }
     // CTA partials of the sweep's sums
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      double v = warp_sum(acc[r]);
-      if (lane == 0) red[wid][r] = v;
+    {
+      int which = 0;
+      const double v = warp_sum_many<R>(acc, lane, which);
+      if ((lane & ((32 / R) - 1)) == 0) red[wid][which] = v;
     }
     __syncthreads();
     if (threadIdx.x < R) {
