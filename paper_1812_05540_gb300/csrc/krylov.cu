@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
   __shared__ double red[kMgsThreads / 32][R];
   __shared__ double sums[R];
   __shared__ double scratch[kMgsThreads / 16];
+  __shared__ double hs[S];  // the sweep's coefficients
   const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int stride = G * kMgsThreads, t0 = int(blockIdx.x) * kMgsThreads + int(threadIdx.x);
   const double2* __restrict__ V2 = reinterpret_cast<const double2*>(V);
@@ -692,26 +693,34 @@ __global__ void __launch_bounds__(kMgsThreads, S <= 4 ? 4 : 2) k_mgs(const doubl
     }
     __syncthreads();
     if (p < nb) {
-      // forward substitution with the in-block Gram entries (the same in every thread)
+      // forward substitution with the in-block Gram entries, by one thread; the others read the
+      // coefficients from shared memory
+      if (threadIdx.x == 0) {
+        double hq[S];
 #pragma unroll
-      for (int c = 0; c < S; ++c) {
-        if (c >= cn) { hp[c] = 0.0; continue; }
-        double hk = sums[c];
-        const int k = c0 + c;
+        for (int c = 0; c < S; ++c) {
+          if (c >= cn) { hq[c] = 0.0; continue; }
+          double hk = sums[c];
+          const int k = c0 + c;
 #pragma unroll
-        for (int l = 0; l < S; ++l) {
-          if (l >= c) break;
-          double g = (k == j) ? sums[S + l] : __ldcg(Gm + int64_t(k) * kS + l);
-          hk -= hp[l] * g;
+          for (int l = 0; l < S; ++l) {
+            if (l >= c) break;
+            double g = (k == j) ? sums[S + l] : __ldcg(Gm + int64_t(k) * kS + l);
+            hk -= hq[l] * g;
+          }
+          hq[c] = hk;
+          hs[c] = hk;
         }
-        hp[c] = hk;
-      }
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (blockIdx.x == 0) {
 #pragma unroll
-        for (int c = 0; c < S; ++c)
-          if (c < cn) h[c0 + c] = hp[c];
-        for (int l = 0; l < ng; ++l) Gm[int64_t(j) * kS + l] = sums[S + l];
+          for (int c = 0; c < S; ++c)
+            if (c < cn) h[c0 + c] = hq[c];
+          for (int l = 0; l < ng; ++l) Gm[int64_t(j) * kS + l] = sums[S + l];
+        }
       }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < S; ++c) hp[c] = hs[c];
       pc0 = c0;
       pcn = cn;
     } else {
