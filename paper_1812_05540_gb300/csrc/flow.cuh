@@ -6,6 +6,30 @@
 
 namespace ps_internal {
 
+// Tiles of the sync-free ILU(0) sweeps: CTA (BY, BZ) owns the x-pencils of a kTY x kTZ tile of (y, z),
+// thread ly + kTY * lz the pencil (BY * kTY + ly, BZ * kTZ + lz).  At CTA step s a thread handles pencil
+// position s - ry - rz, with (ry, rz) = (ly, lz) in the forward sweep and (kTY-1-ly, kTZ-1-lz) in the
+// backward one (position p is x = p forward and x = nx - 1 - p backward), so a sweep takes
+// nx + kTY + kTZ - 2 steps.  Each cell has one record of kRec values per sweep.  The records are stored
+// in the order a CTA consumes them, [tile][step][thread][kRec], steps padded to whole copy windows, so
+// that one bulk copy moves a whole window of a tile.
+constexpr int kTY = 16, kTZ = 8, kRec = 20;
+template <class T>
+__host__ __device__ constexpr int win_cells() { return sizeof(T) == 4 ? 4 : 2; }  // steps per copy window
+// records per thread and tile of one sweep (a whole number of windows)
+__host__ __device__ inline int sweep_steps(int nx, int W) { return (nx + kTY + kTZ - 2 + W - 1) / W * W; }
+__host__ __device__ inline int64_t sweep_tiles(int ny, int nz) {
+  return int64_t((ny + kTY - 1) / kTY) * ((nz + kTZ - 1) / kTZ);
+}
+// offset (in values) of the record of cell (x, y, z) in the forward (fwd) or backward sweep
+__host__ __device__ inline int64_t sweep_rec(bool fwd, int nx, int ny, int steps, int x, int y, int z) {
+  const int nby = (ny + kTY - 1) / kTY;
+  const int ly = y % kTY, lz = z % kTZ;
+  const int s = fwd ? x + ly + lz : (nx - 1 - x) + (kTY - 1 - ly) + (kTZ - 1 - lz);
+  const int64_t tile = (y / kTY) + int64_t(nby) * (z / kTZ);
+  return ((tile * steps + s) * (kTY * kTZ) + ly + kTY * lz) * kRec;
+}
+
 struct FlowStage {
   int nx = 0, ny = 0, nz = 0;
   int64_t nc = 0, nnzb = 0;
@@ -25,8 +49,10 @@ struct FlowStage {
   // row-major each), zero blocks outside the grid
   double* s28 = nullptr;
   float* s28_f = nullptr;
-  // records of the sync-free sweeps, 20 values per cell (forward: lower blocks, inv(U_ii), w; backward:
-  // upper blocks, inv(U_ii), t, z_s, z_p), in the apply precision
+  // records of the sync-free sweeps, kRec values per cell (forward: lower blocks, inv(U_ii), w; backward:
+  // upper blocks, inv(U_ii), t, z_s, z_p), in the apply precision, at sweep_rec(...) with
+  // pk_steps = sweep_steps(nx, win_cells<T>())
+  int pk_steps = 0;
   float *pk_fwd_f = nullptr, *pk_bwd_f = nullptr;
   double *pk_fwd_d = nullptr, *pk_bwd_d = nullptr;
   // sync-free wavefront sweeps: tagged halo words (4 per cell) and error flag

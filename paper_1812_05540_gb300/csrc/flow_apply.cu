@@ -188,7 +188,6 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
 // Everything that does not depend on the wavefront is prefetched kP steps
 // ahead.
 // ---------------------------------------------------------------------------
-constexpr int kTY = 16, kTZ = 8;
 
 template <class T>
 struct HaloWord {
@@ -291,14 +290,10 @@ struct Cell {
   T z0, z1;
 };
 
-// Per-cell records of a sweep, packed at setup and per apply so that the cells of one pencil are
-// contiguous: [3 blocks of the sweep's side (12) | inv(U_ii) (4) | right-hand side pair (2) | z pair (2)].
+// Per-cell records of a sweep, packed at setup and per apply in the order the CTAs consume them
+// (sweep_rec): [3 blocks of the sweep's side (12) | inv(U_ii) (4) | right-hand side pair (2) | z pair (2)].
 // Forward records hold the lower blocks (z-1, y-1, x-1) and w; backward records the upper blocks
 // (x+1, y+1, z+1), t (written by the forward sweep) and z_s, z_p.
-constexpr int kRec = 20;
-// cells per copy window and thread
-template <class T>
-__host__ __device__ constexpr int win_cells() { return sizeof(T) == 4 ? 4 : 2; }
 template <class T>
 __host__ __device__ constexpr size_t win_bytes() {  // two window buffers for the CTA
   return size_t(2) * kTY * kTZ * win_cells<T>() * kRec * sizeof(T);
@@ -365,9 +360,9 @@ __device__ __forceinline__ void store2(T* p, T a, T b) {
 
 // step 6 for the pencil sweeps: w into the forward records, z_s and z_p into the backward records
 template <class T>
-__global__ void k_ff_residual_pack(int nx, int ny, int nz, const T* __restrict__ S28, const T* __restrict__ y,
-                                   const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ pf,
-                                   T* __restrict__ pb) {
+__global__ void k_ff_residual_pack(int nx, int ny, int nz, int steps, const T* __restrict__ S28,
+                                   const T* __restrict__ y, const T* __restrict__ zs, const T* __restrict__ zp,
+                                   T* __restrict__ pf, T* __restrict__ pb) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   int64_t nc = int64_t(nx) * ny * nz;
   if (i >= nc) return;
@@ -383,16 +378,17 @@ __global__ void k_ff_residual_pack(int nx, int ny, int nz, const T* __restrict__
     w0 -= S[q * 4] * a + S[q * 4 + 1] * b;
     w1 -= S[q * 4 + 2] * a + S[q * 4 + 3] * b;
   }
-  store2<T>(pf + i * kRec + 16, w0, w1);
-  store2<T>(pb + i * kRec + 18, zs[i], zp[i]);
+  store2<T>(pf + sweep_rec(true, nx, ny, steps, x, yy, zz) + 16, w0, w1);
+  store2<T>(pb + sweep_rec(false, nx, ny, steps, x, yy, zz) + 18, zs[i], zp[i]);
 }
 
-// Sync-free wavefront sweep over the packed records (see the block comment above kTY).  Each thread's
-// records for a window of win_cells steps are one contiguous range of its pencil: one bulk copy per
-// thread and window, two window buffers, completion on one mbarrier per buffer (128 arrivals plus
-// the copied bytes).  FWD writes t into the backward records; the backward sweep writes z_f.
+// Sync-free wavefront sweep over the packed records (see the block comment above).  A window of
+// win_cells steps of a tile is one contiguous range of the records ([tile][step][thread]): thread 0
+// moves it with one bulk copy into one of two window buffers, completing on that buffer's mbarrier
+// (one arrival plus the copied bytes).  FWD writes t into the backward records; the backward sweep
+// writes z_f.
 template <class T, bool FWD>
-__global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz, const T* __restrict__ rec,
+__global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz, int steps, const T* __restrict__ rec,
                                                          T* __restrict__ rec_bwd, double* __restrict__ zout,
                                                          uint64_t* halo, int* err, uint32_t tag, int64_t limit,
                                                          int stall) {
@@ -420,16 +416,14 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
   const int64_t pbase = valid ? int64_t(nx) * (yy + int64_t(ny) * zz) : 0;
   const int off = ry + rz;  // step s handles pencil position xs = s - off
-  // window k holds steps [k W, k W + W): the x range [xlo, xlo + W), records in ascending x
-  auto win_xlo = [&](int k) { return FWD ? k * W - off : nx + off - k * W - W; };
-  auto slot = [&](int b, int p) { return win + ((size_t(b) * (kTY * kTZ) + threadIdx.x) * W + p) * kRec; };
-  auto request = [&](int k) {
+  // window k holds steps [k W, k W + W) of the whole tile: W * kTY * kTZ records, step-major
+  constexpr unsigned kWinVals = unsigned(W) * kTY * kTZ * kRec;
+  const T* trec = rec + size_t(blockIdx.x) * steps * (kTY * kTZ) * kRec;
+  auto request = [&](int k) {  // thread 0 only; k * W < steps
     const int b = k & 1;
-    const int xlo = win_xlo(k);
-    const int x0 = max(xlo, 0), x1 = min(xlo + W, nx);
-    unsigned bytes = (valid && x1 > x0) ? unsigned(x1 - x0) * kRec * sizeof(T) : 0u;
-    mbar_arrive_tx(&mbar[b], bytes);
-    if (bytes) bulk_copy(slot(b, x0 - xlo), rec + (pbase + x0) * kRec, bytes, &mbar[b]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_tx(&mbar[b], kWinVals * unsigned(sizeof(T)));
+    bulk_copy(win + size_t(b) * kWinVals, trec + size_t(k) * kWinVals, kWinVals * unsigned(sizeof(T)), &mbar[b]);
   };
   auto wait_window = [&](int k) -> bool {
     int64_t it = 0;
@@ -440,24 +434,30 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
   };
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    mbar_init(&mbar[0], kTY * kTZ);
-    mbar_init(&mbar[1], kTY * kTZ);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  request(0);
-  request(1);
+  if (threadIdx.x == 0) {
+    request(0);
+    if (W <= last) request(1);
+  }
   // Per-step state kept incrementally: xs = step - off is the pencil position and gi the cell index
   // (one step moves gi by +1 forward, -1 backward).  In the loop below the slot loop is unrolled over
   // two windows, so a step's window buffer and record position are compile-time constants.
   constexpr int64_t kStep = FWD ? 1 : -1;
   const unsigned unx = unsigned(nx);
   auto on = [&](int xs) { return valid && unsigned(xs) < unx; };
-  const T* tbase = win + size_t(threadIdx.x) * W * kRec;
+  const T* tbase = win + size_t(threadIdx.x) * kRec;
   auto rec_at = [&](int q2) -> const T* {  // record of the step whose unrolled index is q2 (mod 2W)
-    const int b = (q2 / W) & 1, pos = FWD ? (q2 % W) : (W - 1 - q2 % W);
-    return tbase + size_t(b) * (kTY * kTZ) * W * kRec + pos * kRec;
+    const int b = (q2 / W) & 1, pos = q2 % W;
+    return tbase + (size_t(b) * W + pos) * (kTY * kTZ) * kRec;
   };
+  // forward sweep: t of the cell at pencil position xs goes to its backward record, backward step
+  // nx - 1 - xs + (kTY - 1 - ly) + (kTZ - 1 - lz) of the same tile and thread
+  T* tout = FWD ? rec_bwd + (size_t(blockIdx.x) * steps * (kTY * kTZ) + threadIdx.x) * kRec + 16 : nullptr;
+  const int boff = (kTY - 1 - ly) + (kTZ - 1 - lz) + nx - 1;
   HaloVal<T> hyr[2], hzr[2];
   int xs = -off;                        // step 0
   int64_t gi = pbase + (FWD ? xs : nx - 1 - xs);
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
           T u1 = p1[cur] - (c0.S[0][2] * nz0 + c0.S[0][3] * nz1) - (c0.S[1][2] * ny0 + c0.S[1][3] * ny1);
           r0 = c0.D[0] * u0 + c0.D[1] * u1;
           r1 = c0.D[2] * u0 + c0.D[3] * u1;
-          store2<T>(rec_bwd + i0 * kRec + 16, r0, r1);
+          store2<T>(tout + size_t(boff - xs) * (kTY * kTZ) * kRec, r0, r1);
         } else {
           // dz_i = t_i - inv(U_ii) sum_{j>i} S_ij dz_j (blocks x+1, y+1, z+1) ; z_f = z + dz
           T s0v = p0[cur] + (c0.S[1][0] * ny0 + c0.S[1][1] * ny1) + (c0.S[2][0] * nz0 + c0.S[2][1] * nz1);
@@ -552,10 +552,7 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
           return;
         }
         const int k = step / W + 2;
-        if (k * W <= last) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          request(k);
-        }
+        if (k * W <= last && threadIdx.x == 0) request(k);
       }
     }
   }
@@ -600,8 +597,9 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
   int nby = (F.ny + kTY - 1) / kTY, nbz = (F.nz + kTZ - 1) / kTZ;
   unsigned grid = unsigned(nby * nbz);
   FlowStage& Fm = const_cast<FlowStage&>(F);
-  PS_TICK(); k_ff_residual_pack<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, V.s28, W.y, W.zs, W.zp, pf,
-                                                                      pb);
+  if (F.pk_steps != sweep_steps(F.nx, win_cells<T>())) return false;
+  PS_TICK(); k_ff_residual_pack<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, V.s28, W.y, W.zs,
+                                                                      W.zp, pf, pb);
   for (int dir = 0; dir < 2; ++dir) {
     uint32_t tag = uint32_t(++Fm.ilu_epoch);
     if (tag == 0) tag = uint32_t(++Fm.ilu_epoch);  // 0 marks never-written halo words
@@ -612,7 +610,8 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
     int* err = F.ilu_err;
     int64_t lim = F.spin_limit;
     int stall = F.test_stall;
-    void* args[] = {&nx, &ny, &nz, &rec, &rec_bwd, &zout, &halo, &err, &tag, &lim, &stall};
+    int steps = F.pk_steps;
+    void* args[] = {&nx, &ny, &nz, &steps, &rec, &rec_bwd, &zout, &halo, &err, &tag, &lim, &stall};
     const void* fn = dir == 0 ? (const void*)k_ilu_pencil<T, true> : (const void*)k_ilu_pencil<T, false>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_bytes<T>()));
     cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kTY * kTZ, args, win_bytes<T>(), st);

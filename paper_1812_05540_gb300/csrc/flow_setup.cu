@@ -134,17 +134,20 @@ __global__ void k_aps_st(int64_t nc, const T* __restrict__ s28, T* __restrict__ 
 
 // S/inv(U_ii) part of the sweep records (see FlowStage): forward lower blocks, backward upper blocks
 template <class T>
-__global__ void k_pack_sd(int64_t nc, const T* __restrict__ s28, const T* __restrict__ dinv, T* __restrict__ pf,
-                          T* __restrict__ pb) {
+__global__ void k_pack_sd(int nx, int ny, int nz, int steps, const T* __restrict__ s28, const T* __restrict__ dinv,
+                          T* __restrict__ pf, T* __restrict__ pb) {
   int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
+  if (c >= int64_t(nx) * ny * nz) return;
+  const int x = int(c % nx), y = int((c / nx) % ny), z = int(c / (int64_t(nx) * ny));
+  T* f = pf + sweep_rec(true, nx, ny, steps, x, y, z);
+  T* b = pb + sweep_rec(false, nx, ny, steps, x, y, z);
   for (int e = 0; e < 12; ++e) {
-    pf[c * 20 + e] = s28[c * 28 + e];
-    pb[c * 20 + e] = s28[c * 28 + 16 + e];
+    f[e] = s28[c * 28 + e];
+    b[e] = s28[c * 28 + 16 + e];
   }
   for (int e = 0; e < 4; ++e) {
-    pf[c * 20 + 12 + e] = dinv[c * 4 + e];
-    pb[c * 20 + 12 + e] = dinv[c * 4 + e];
+    f[12 + e] = dinv[c * 4 + e];
+    b[12 + e] = dinv[c * 4 + e];
   }
 }
 
@@ -200,16 +203,19 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(scan_i32(ar, cnt, off, F.nlev, nullptr, st));
     PS_CUDA(cudaMemcpyAsync(cursor, off, sizeof(int32_t) * F.nlev, cudaMemcpyDeviceToDevice, st));
     PS_TICK(); k_level_fill<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, cursor, F.lev_cells);
+    // sweep records, [tile][step][thread][kRec]; slots of cells outside the grid stay zero
+    F.pk_steps = sweep_steps(F.nx, mixed ? win_cells<float>() : win_cells<double>());
+    const size_t nrec = size_t(sweep_tiles(F.ny, F.nz)) * F.pk_steps * (kTY * kTZ) * kRec;
     if (mixed) {
-      PS_TRY(ar.alloc(&F.pk_fwd_f, size_t(nc) * 20));
-      PS_TRY(ar.alloc(&F.pk_bwd_f, size_t(nc) * 20));
-      PS_CUDA(cudaMemsetAsync(F.pk_fwd_f, 0, sizeof(float) * nc * 20, st));
-      PS_CUDA(cudaMemsetAsync(F.pk_bwd_f, 0, sizeof(float) * nc * 20, st));
+      PS_TRY(ar.alloc(&F.pk_fwd_f, nrec));
+      PS_TRY(ar.alloc(&F.pk_bwd_f, nrec));
+      PS_CUDA(cudaMemsetAsync(F.pk_fwd_f, 0, sizeof(float) * nrec, st));
+      PS_CUDA(cudaMemsetAsync(F.pk_bwd_f, 0, sizeof(float) * nrec, st));
     } else {
-      PS_TRY(ar.alloc(&F.pk_fwd_d, size_t(nc) * 20));
-      PS_TRY(ar.alloc(&F.pk_bwd_d, size_t(nc) * 20));
-      PS_CUDA(cudaMemsetAsync(F.pk_fwd_d, 0, sizeof(double) * nc * 20, st));
-      PS_CUDA(cudaMemsetAsync(F.pk_bwd_d, 0, sizeof(double) * nc * 20, st));
+      PS_TRY(ar.alloc(&F.pk_fwd_d, nrec));
+      PS_TRY(ar.alloc(&F.pk_bwd_d, nrec));
+      PS_CUDA(cudaMemsetAsync(F.pk_fwd_d, 0, sizeof(double) * nrec, st));
+      PS_CUDA(cudaMemsetAsync(F.pk_bwd_d, 0, sizeof(double) * nrec, st));
     }
     PS_TRY(ar.alloc(&F.halo, size_t(nc) * 4));
     PS_TRY(ar.alloc(&F.ilu_err, 4));
@@ -236,11 +242,13 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TICK(); k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
     PS_TICK(); k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
     PS_CUDA(cudaGetLastError());
-    PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.dinv_f, F.pk_fwd_f, F.pk_bwd_f);
+    PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28_f, F.dinv_f,
+                                                                  F.pk_fwd_f, F.pk_bwd_f);
     if (!F.aps_st_f) PS_TRY(ar.alloc(&F.aps_st_f, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.aps_st_f);
   } else {
-    PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.dinv, F.pk_fwd_d, F.pk_bwd_d);
+    PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28, F.dinv,
+                                                                   F.pk_fwd_d, F.pk_bwd_d);
     if (!F.aps_st_d) PS_TRY(ar.alloc(&F.aps_st_d, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.aps_st_d);
   }

@@ -18,6 +18,7 @@
 #include <thread>
 #include <vector>
 
+#include "flow.cuh"
 #include "internal.cuh"
 
 namespace {
@@ -144,6 +145,9 @@ int64_t ps_setup_bytes_estimate(const ps_jacobian* jac, const ps_grid* g, const 
   int64_t lev0 = jac->A_uu.nnzb * 3 * 8 + jac->A_ff.nnzb * 8;               // SDC and S_pp values
   b += lev0 * 3 / 2 * (mixed ? 2 : 1) + (mixed ? nn * 27 * 3 * 4 + nc * 7 * 4 : nn * 27 * 3 * 8 + nc * 7 * 8);
   b += jac->A_ff.nnzb * 48 + nc * 28 * 8;                                   // flow stage
+  const int w = mixed ? ps_internal::win_cells<float>() : ps_internal::win_cells<double>();
+  b += 2 * ps_internal::sweep_tiles(g->ny, g->nz) * ps_internal::sweep_steps(g->nx, w) *
+       (ps_internal::kTY * ps_internal::kTZ) * ps_internal::kRec * (mixed ? 4 : 8);  // ILU sweep records
   b += n * 8 * 24;                                                          // work vectors
   return b + b / 5;                                                         // 20 % margin
 }
