@@ -100,9 +100,9 @@ ps_status amg_alloc_work(Arena& ar, Amg& H);
 
 // SpMV lane choice from the mean row length
 inline int lanes_for(double mean_row) {
-  if (mean_row <= 10) return 4;
-  if (mean_row <= 24) return 8;
-  if (mean_row <= 96) return 16;
+  if (mean_row <= 16) return 4;
+  if (mean_row <= 48) return 8;
+  if (mean_row <= 192) return 16;
   return 32;
 }
 
