@@ -66,15 +66,18 @@ __device__ __forceinline__ int32_t find_col(const int32_t* __restrict__ ci, int3
   return lo;
 }
 
-// symmetric strength graph: i~j if max(abar_ij, abar_ji) >= theta sqrt(abar_ii abar_jj)
+// symmetric strength graph: i~j if max(abar_ij, abar_ji) >= theta sqrt(abar_ii abar_jj); kStrLanes
+// threads per row, each entry decided on its own
+constexpr int kStrLanes = 8;
 template <int NC>
 __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ v, const double* __restrict__ dgbar,
                            const uint8_t* __restrict__ excl, double theta, uint8_t* __restrict__ strong,
                            double* __restrict__ wgt) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = t / kStrLanes;
   if (i >= n) return;
-  for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
+  for (int32_t q = rp[i] + int32_t(t % kStrLanes); q < rp[i + 1]; q += kStrLanes) {
     int32_t j = ci[q];
     uint8_t s = 0;
     double w = 0.0;
@@ -106,55 +109,97 @@ __global__ void k_mis_init(int64_t n, const int32_t* __restrict__ rp, const uint
   for (int32_t q = rp[i]; q < rp[i + 1]; ++q) any = any || strong[q];
   st[i] = (excl[i] || !any) ? 3 : 0;
 }
+// The four round kernels take kMisLanes threads per row: each lane scans a strided share of the row
+// and the lanes combine by max (priorities) or by or (flags), which do not depend on the order, so the
+// rounds decide exactly as one thread per row would.  Every lane reaches the shuffles; only lane 0
+// of a row writes.
+constexpr int kMisLanes = 8;
+__device__ __forceinline__ int64_t group_max(int64_t v) {
+#pragma unroll
+  for (int o = kMisLanes / 2; o > 0; o >>= 1) {
+    const int64_t u = __shfl_xor_sync(0xffffffffu, v, o, kMisLanes);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+__device__ __forceinline__ bool group_any(bool b) {
+  const unsigned m = __ballot_sync(0xffffffffu, b);
+  const int lane = int(threadIdx.x & 31);
+  return ((m >> (lane & ~(kMisLanes - 1))) & ((1u << kMisLanes) - 1u)) != 0u;
+}
+#define MIS_ROW                                                      \
+  const int64_t t_ = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; \
+  const int64_t i = t_ / kMisLanes;                                  \
+  const int sub = int(t_ % kMisLanes);                               \
+  const bool act = i < n;
+
 __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st, int level,
                          int64_t* __restrict__ m1) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t m = st[i] == 0 ? mis_key(i, level) : -1;
-  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
-    if (strong[q] && st[ci[q]] == 0) {
-      int64_t k = mis_key(ci[q], level);
-      m = k > m ? k : m;
-    }
-  m1[i] = m;
+  MIS_ROW
+  int64_t m = -1;
+  if (act) {
+    if (sub == 0 && st[i] == 0) m = mis_key(i, level);
+    for (int32_t q = rp[i] + sub; q < rp[i + 1]; q += kMisLanes)
+      if (strong[q] && st[ci[q]] == 0) {
+        int64_t k = mis_key(ci[q], level);
+        m = k > m ? k : m;
+      }
+  }
+  m = group_max(m);
+  if (act && sub == 0) m1[i] = m;
 }
 __global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const int64_t* __restrict__ m1, int level,
                          uint8_t* __restrict__ st, uint8_t* __restrict__ nr) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t m = m1[i];
-  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
-    if (strong[q]) {
-      int64_t k = m1[ci[q]];
-      m = k > m ? k : m;
-    }
-  uint8_t r = (st[i] == 0 && m == mis_key(i, level)) ? 1 : 0;
-  nr[i] = r;
-  if (r) st[i] = 1;
+  MIS_ROW
+  int64_t m = -1;
+  if (act) {
+    if (sub == 0) m = m1[i];
+    for (int32_t q = rp[i] + sub; q < rp[i + 1]; q += kMisLanes)
+      if (strong[q]) {
+        int64_t k = m1[ci[q]];
+        m = k > m ? k : m;
+      }
+  }
+  m = group_max(m);
+  if (act && sub == 0) {
+    uint8_t r = (st[i] == 0 && m == mis_key(i, level)) ? 1 : 0;
+    nr[i] = r;
+    if (r) st[i] = 1;
+  }
 }
 __global__ void k_mis_c1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ nr,
                          uint8_t* __restrict__ c1) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint8_t c = nr[i];
-  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
-    if (strong[q] && nr[ci[q]]) c = 1;
-  c1[i] = c;
+  MIS_ROW
+  bool c = false;
+  if (act) {
+    if (sub == 0) c = nr[i] != 0;
+    for (int32_t q = rp[i] + sub; q < rp[i + 1]; q += kMisLanes)
+      if (strong[q] && nr[ci[q]]) c = true;
+  }
+  c = group_any(c);
+  if (act && sub == 0) c1[i] = c ? 1 : 0;
 }
 __global__ void k_mis_c2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ c1,
                          uint8_t* __restrict__ st, int32_t* __restrict__ undecided) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n || st[i] != 0) return;
-  uint8_t c = c1[i];
-  for (int32_t q = rp[i]; q < rp[i + 1]; ++q)
-    if (strong[q] && c1[ci[q]]) c = 1;
-  if (c) st[i] = 2;
-  else atomicAdd(undecided, 1);
+  MIS_ROW
+  const bool undec = act && st[i] == 0;
+  bool c = false;
+  if (undec) {
+    if (sub == 0) c = c1[i] != 0;
+    for (int32_t q = rp[i] + sub; q < rp[i + 1]; q += kMisLanes)
+      if (strong[q] && c1[ci[q]]) c = true;
+  }
+  c = group_any(c);
+  if (undec && sub == 0) {
+    if (c) st[i] = 2;
+    else atomicAdd(undecided, 1);
+  }
 }
+#undef MIS_ROW
 
 __global__ void k_is_root(int64_t n, const uint8_t* __restrict__ st, int32_t* __restrict__ f) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -867,7 +912,8 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     if (!coarsest) {
       PS_TRY(ar.alloc(&strong, nnz));
       PS_TRY(ar.alloc(&wgt, nnz));
-      PS_TICK(); k_strength<NC><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, theta, strong, wgt);
+      PS_TICK(); k_strength<NC><<<grid_for(n * kStrLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl,
+                                                                             theta, strong, wgt);
       PS_TRY(ar.alloc(&stt, n));
       int64_t* m1;
       uint8_t *nr, *c1;
@@ -876,10 +922,10 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, strong, excl, stt);
       for (int round = 0;; ++round) {
         PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
-        PS_TICK(); k_mis_m1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
-        PS_TICK(); k_mis_m2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
-        PS_TICK(); k_mis_c1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
-        PS_TICK(); k_mis_c2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
+        PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
+        PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
+        PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
+        PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
         int32_t h_und = 0;
         PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         PS_CUDA(cudaStreamSynchronize(st));
