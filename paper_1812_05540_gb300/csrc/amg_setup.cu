@@ -431,15 +431,39 @@ __device__ int spgemm_collect(int64_t i, const int32_t* __restrict__ xrp, const 
 }
 
 // upper bound of the distinct columns of each row (the number of products) and its count class
+// slot of this lane in the list of class b (b < 0: none) with one atomic per warp and class; every
+// lane of the warp must call it
+template <int NCLS>
+__device__ __forceinline__ int32_t warp_append(int b, int32_t* const (&ctr)[NCLS]) {
+  const int lane = int(threadIdx.x & 31);
+  int32_t slot = -1;
+#pragma unroll
+  for (int c = 0; c < NCLS; ++c) {
+    const unsigned m = __ballot_sync(0xffffffffu, b == c);
+    if (m == 0u) continue;
+    const int leader = __ffs(int(m)) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr[c], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (b == c) slot = base + __popc(m & ((1u << lane) - 1u));
+  }
+  return slot;
+}
+
+// rows binned by their product bound (sum of the Y-row lengths over the X row)
 __global__ void k_spgemm_bound(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
                                const int32_t* __restrict__ yrp, int32_t* __restrict__ lists,
                                int32_t* __restrict__ counts) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int64_t ub = 0;
-  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) ub += yrp[xci[q] + 1] - yrp[xci[q]];
-  int b = ub <= class_cap(0) ? 0 : ub <= class_cap(1) ? 1 : ub <= class_cap(2) ? 2 : 3;
-  lists[int64_t(b) * n + atomicAdd(&counts[b], 1)] = int32_t(i);
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int b = -1;
+  if (i < n) {
+    int64_t ub = 0;
+    for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) ub += yrp[xci[q] + 1] - yrp[xci[q]];
+    b = ub <= class_cap(0) ? 0 : ub <= class_cap(1) ? 1 : ub <= class_cap(2) ? 2 : 3;
+  }
+  int32_t* const ctr[4] = {counts, counts + 1, counts + 2, counts + 3};
+  const int32_t slot = warp_append<4>(b, ctr);
+  if (b >= 0) lists[int64_t(b) * n + slot] = int32_t(i);
 }
 
 // rows listed in rows[0..nrows): exact distinct-column count with a table of 2C slots; rows
@@ -474,16 +498,21 @@ __global__ void k_spgemm_count(const int32_t* __restrict__ rows, int32_t nrows, 
 __global__ void k_spgemm_fill_bins(int64_t n, const int32_t* __restrict__ cnt, int32_t* __restrict__ lists,
                                    int32_t* __restrict__ counts, int dense_ok, uint8_t* __restrict__ islong,
                                    int32_t* __restrict__ longrows, int32_t* __restrict__ nlong) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n || islong[i]) return;
-  int32_t u = cnt[i];
-  if (dense_ok && u > class_cap(1)) {
-    islong[i] = 1;
-    longrows[atomicAdd(nlong, 1)] = int32_t(i);
-    return;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int b = -1;  // 0..3: capacity class, 4: the dense path
+  if (i < n && !islong[i]) {
+    const int32_t u = cnt[i];
+    if (dense_ok && u > class_cap(1)) b = 4;
+    else b = u <= class_cap(0) ? 0 : u <= class_cap(1) ? 1 : u <= class_cap(2) ? 2 : 3;
   }
-  int b = u <= class_cap(0) ? 0 : u <= class_cap(1) ? 1 : u <= class_cap(2) ? 2 : 3;
-  lists[int64_t(b) * n + atomicAdd(&counts[b], 1)] = int32_t(i);
+  int32_t* const ctr[5] = {counts, counts + 1, counts + 2, counts + 3, nlong};
+  const int32_t slot = warp_append<5>(b, ctr);
+  if (b == 4) {
+    islong[i] = 1;
+    longrows[slot] = int32_t(i);
+  } else if (b >= 0) {
+    lists[int64_t(b) * n + slot] = int32_t(i);
+  }
 }
 
 // rows of the largest product-bound class handled by the dense path from the count pass on
