@@ -185,8 +185,8 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
 // 32-bit sweep tag (single-copy atomic stores, so no fence or flag is needed):
 // consumers prefetch the words they need two steps ahead and re-read them only
 // while the tag is not yet the current one; the wait is bounded and raises *err.
-// Everything that does not depend on the wavefront is prefetched kP steps
-// ahead.
+// The cell records, which do not depend on the wavefront, arrive by bulk copy
+// one to two copy windows ahead (see k_ilu_pencil).
 // ---------------------------------------------------------------------------
 
 template <class T>
