@@ -183,8 +183,9 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
 // shared array, one barrier per step).  Values crossing a CTA boundary go
 // through a halo buffer of 64-bit words that each carry a 32-bit payload and the
 // 32-bit sweep tag (single-copy atomic stores, so no fence or flag is needed):
-// consumers prefetch the words they need two steps ahead and re-read them only
-// while the tag is not yet the current one; the wait is bounded and raises *err.
+// consumers prefetch the words they need two steps ahead, at the start of a step,
+// and re-read them only while the tag is not yet the current one; the wait is
+// bounded and raises *err.
 // The cell records, which do not depend on the wavefront, arrive by bulk copy
 // one to two copy windows ahead (see k_ilu_pencil).
 // ---------------------------------------------------------------------------
@@ -483,8 +484,8 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
       const bool act = on(xs);
       const int64_t i0 = gi;
       T r0 = T(0), r1 = T(0);
+      T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
       if (act) {
-        T ny0 = T(0), ny1 = T(0), nz0 = T(0), nz1 = T(0);
         bool ok = true;
         if (gy) {
           ok = ok && halo_wait<T>(halo, i0 + jy, tag, hyr[cur], limit, err);
@@ -501,6 +502,12 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
           nz0 = qq[0]; nz1 = qq[1];
         }
         if (!ok) { abort_flag = 1; atomicExch(err, 1); }
+      }
+      // halo words of step + 2 into the slots just read: issued before this step's update, the loads
+      // have the rest of this step and all of the next to arrive
+      if (gy && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jy, hyr[cur]);
+      if (gz && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jz, hzr[cur]);
+      if (act) {
         if (FWD) {
           // u_i = w_i - sum_{k<i} S_ik t_k (blocks z-1, y-1, x-1) ; t_i = inv(U_ii) u_i
           T u0 = p0[cur] - (c0.S[0][0] * nz0 + c0.S[0][1] * nz1) - (c0.S[1][0] * ny0 + c0.S[1][1] * ny1);
@@ -539,8 +546,6 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
           p1[nxt] = actn ? cn.S[0][2] * x0 + cn.S[0][3] * x1 : T(0);
         }
       }
-      if (gy && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jy, hyr[cur]);
-      if (gz && on(xs + 2)) halo_fetch<T>(halo, gi + 2 * kStep + jz, hzr[cur]);
       ++xs;
       gi += kStep;
       __syncthreads();
