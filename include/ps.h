@@ -224,7 +224,10 @@ typedef struct {
   int64_t max_inflight_requests;
 } ps_server_info;
 
-/* Device bytes a handle for this Jacobian will hold (estimate with a 20 % margin). */
+/* Device bytes a handle for this Jacobian will hold (estimate with a 20 % margin).  Host arithmetic on
+   the block counts and the grid only: the array pointers in jac are not read and no device is used.
+   Counts the Jacobian copies, the FP64 stencil copy, both AMG hierarchies, the flow stage with its
+   ILU(0) sweep records, the Krylov bases and the work vectors.  Returns 0 when an argument is NULL. */
 int64_t ps_setup_bytes_estimate(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params);
 /* Starts the worker threads on the current device.  Errors: PS_ERR_INVALID. */
 ps_status ps_server_create(const ps_server_params* params, ps_server** out);
