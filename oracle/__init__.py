@@ -119,6 +119,8 @@ def lib():
         L.or_amg_aggregates.restype = C.c_int64
         L.or_amg_roots.argtypes = [C.c_void_p, C.c_int, C.c_int, _PU8]
         L.or_amg_roots.restype = C.c_int64
+        L.or_aggregate.argtypes = [C.c_int64, C.c_int, _PI64, _PI32, _PD, C.c_double, C.c_int, _PI32, _PU8]
+        L.or_aggregate.restype = C.c_int64
         L.or_amg_p_nnz.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.or_amg_p_nnz.restype = C.c_int64
         L.or_amg_prolongator.argtypes = [C.c_void_p, C.c_int, C.c_int, _PI64, _PI32, _PD]
@@ -330,6 +332,19 @@ def fgmres_diag(diag, b, tol=1e-10, restart=100, max_iters=1000):
     st = Stats()
     lib().or_fgmres_diag(len(b), _d(diag), _d(b), _d(x), tol, restart, max_iters, C.byref(st))
     return x, st
+
+
+def aggregate(rp, ci, v, nc=1, theta=0.08, level=0):
+    """Aggregates and distance-2 MIS roots of a CSR level operator (nc values per entry)."""
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    ci = np.ascontiguousarray(ci, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    n = len(rp) - 1
+    agg = np.empty(n, np.int32)
+    root = np.zeros(n, np.uint8)
+    na = lib().or_aggregate(n, nc, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v), theta, level,
+                            agg.ctypes.data_as(_PI32), root.ctypes.data_as(_PU8))
+    return agg, root.astype(bool), na
 
 
 def ref_integrals(h):

@@ -1691,6 +1691,20 @@ int64_t or_amg_roots(const or_prec* p, int which, int level, uint8_t* root) {
   if (!L.root.empty()) std::memcpy(root, L.root.data(), L.root.size());
   return int64_t(L.root.size());
 }
+// aggregation of a caller-given level operator (CSR, nc values per entry, sorted columns): the
+// strength graph, distance-2 MIS rounds under the priority key of `level`, phase 1 and phase 2
+int64_t or_aggregate(int64_t n, int nc, const int64_t* rp, const int32_t* ci, const double* v, double theta,
+                     int level, int32_t* agg, uint8_t* root) {
+  Level lev;
+  lev.A.n = lev.A.m = n; lev.A.nc = nc;
+  lev.A.rp.assign(rp, rp + n + 1);
+  lev.A.ci.assign(ci, ci + rp[n]);
+  lev.A.v.assign(v, v + rp[n] * nc);
+  aggregate(lev, theta, level);
+  std::memcpy(agg, lev.agg.data(), size_t(n) * sizeof(int32_t));
+  std::memcpy(root, lev.root.data(), size_t(n));
+  return lev.nagg;
+}
 int64_t or_amg_p_nnz(const or_prec* p, int which, int level) { return pick(p, which)->L[level].P.nnz(); }
 int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v) {
   const CSR& A = pick(p, which)->L[level].P;

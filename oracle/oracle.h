@@ -139,6 +139,11 @@ int or_amg_level_matrix(const or_prec* p, int which, int level, int64_t* rp, int
 int64_t or_amg_aggregates(const or_prec* p, int which, int level, int32_t* agg);
 /* 1 for the distance-2 MIS roots of level `level` */
 int64_t or_amg_roots(const or_prec* p, int which, int level, uint8_t* root);
+/* aggregation (strength graph, distance-2 MIS under the priority key of `level`, phase 1, phase 2) of a
+   caller-given CSR operator with nc values per entry and sorted columns; agg[n] (-1 = not aggregated),
+   root[n]; returns the number of aggregates */
+int64_t or_aggregate(int64_t n, int nc, const int64_t* rp, const int32_t* ci, const double* v, double theta,
+                     int level, int32_t* agg, uint8_t* root);
 int64_t or_amg_p_nnz(const or_prec* p, int which, int level);
 int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v);
 /* one V-cycle of component comp on level-0 input b */
