@@ -186,10 +186,14 @@ ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv);
    static device array of (2^19 + 1024) doubles, 4 MiB, which every GPU that
    loads the library holds until exit.  The first call on each device looks up
    that array's device address (cudaGetSymbolAddress) with the device current;
-   make that first call before any stream capture.  Systems with more than
-   2^22 node + cell rows in total are rejected with PS_ERR_INVALID.  Every call
-   shares the array, so calls that overlap on the GPU race: the caller must not
-   run two at once.  Work is enqueued on stream (NULL = legacy stream) and not
+   make that first call before any stream capture.  The address is kept for the
+   life of the process: do not call this entry point after cudaDeviceReset.
+   The partial sums fill one slot per 8 rows of each block, so a system is
+   accepted when ceil(nodes / 8) + ceil(cells / 8) <= 2^19 (about 2^22 rows in
+   total); larger ones are rejected with PS_ERR_INVALID.  r must not overlap x
+   or b (r == x or r == b is rejected with PS_ERR_INVALID).  Every call shares
+   the array, so calls that overlap on the GPU race: the caller must not run two
+   at once.  Work is enqueued on stream (NULL = legacy stream) and not
    synchronised; *rnorm2 is valid once the stream reaches that point. */
 ps_status ps_residual_noalloc(const ps_jacobian* jac, const ps_grid* grid, const double* x, const double* b,
                               double* r, double* rnorm2, void* stream);
@@ -290,6 +294,10 @@ const char* ps_strerror(ps_status s);
 /* Number of CUDA kernels this library has launched in the process so far
    (monotone counter; differences bracket a region of interest). */
 int64_t ps_launch_count(void);
+
+/* Number of device allocations the library has made in the process so far (monotone counter; every
+   device buffer of a handle, generator output or server request is one). */
+int64_t ps_alloc_count(void);
 
 #ifdef __cplusplus
 }

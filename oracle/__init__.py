@@ -19,6 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 OR_GRAVITY, OR_DIRICHLET, OR_SCALE, OR_ACCUM, OR_FLUX, OR_FLUX_SAT, OR_COUPLING = (1 << i for i in range(7))
 OR_ALL = 0x7F
@@ -29,19 +30,23 @@ LOCAL_ILU0, LOCAL_EXACT = 0, 1
 PRESS_AMG, PRESS_EXACT = 0, 1
 
 
-def build(force=False):
-    """Compile oracle.cpp with g++ (x86 here, aarch64 on the GPU host)."""
+def build(force=False, openmp=False):
+    """Compile oracle.cpp with g++ (x86 here, aarch64 on the GPU host).  openmp=True builds the same
+    source with -fopenmp (row loops on all host cores, results bit-identical to the serial build)."""
     src = os.path.join(_HERE, "oracle.cpp")
     hdr = os.path.join(_HERE, "oracle.h")
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
-        return _LIB
+    out = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return out
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB + ".%d.tmp" % os.getpid()
+    tmp = out + ".%d.tmp" % os.getpid()
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", src, "-o", tmp]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
 
 
 class GenParams(C.Structure):
@@ -92,13 +97,21 @@ class TerzaghiParams(C.Structure):
                 ("rho0", C.c_double), ("sigma0", C.c_double), ("dt", C.c_double), ("nsteps", C.c_int32)]
 
 
-_lib = None
+_libs = {}
+_use_openmp = False
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def select(openmp):
+    """Choose the build that new Systems (and their Precs) use: serial (False) or OpenMP (True)."""
+    global _use_openmp
+    _use_openmp = bool(openmp)
+
+
+def lib(openmp=None):
+    openmp = _use_openmp if openmp is None else bool(openmp)
+    if openmp not in _libs:
+        L = C.CDLL(build(openmp=openmp))
+        L.or_num_threads.restype = C.c_int
         L.or_generate.argtypes = [C.POINTER(GenParams), C.POINTER(C.POINTER(_System))]
         L.or_system_free.argtypes = [C.POINTER(_System)]
         L.or_default_params.argtypes = [C.POINTER(GenParams), C.c_int]
@@ -142,8 +155,12 @@ def lib():
         L.or_correlated_field.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_int, _PD]
         L.or_terzaghi.argtypes = [C.POINTER(TerzaghiParams), _PD, _PD, _PD, _PD, _PD]
-        _lib = L
-    return _lib
+        _libs[openmp] = L
+    return _libs[openmp]
+
+
+def num_threads(openmp=None):
+    return lib(openmp).or_num_threads()
 
 
 def _d(a):
@@ -169,7 +186,8 @@ class System:
 
     def __init__(self, gp):
         ptr = C.POINTER(_System)()
-        rc = lib().or_generate(C.byref(gp), C.byref(ptr))
+        self._L = lib()
+        rc = self._L.or_generate(C.byref(gp), C.byref(ptr))
         if rc:
             raise RuntimeError("or_generate failed: %d" % rc)
         self._ptr = ptr
@@ -193,14 +211,14 @@ class System:
 
     def __del__(self):
         try:
-            lib().or_system_free(self._ptr)
+            self._L.or_system_free(self._ptr)
         except Exception:
             pass
 
     def spmv(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.empty(self.n)
-        lib().or_spmv(self._ptr, _d(x), _d(y))
+        self._L.or_spmv(self._ptr, _d(x), _d(y))
         return y
 
     def dense(self):
@@ -219,7 +237,7 @@ class System:
     def dense_solve(self, b):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.empty(self.n)
-        rc = lib().or_dense_solve(self._ptr, _d(b), _d(x))
+        rc = self._L.or_dense_solve(self._ptr, _d(b), _d(x))
         if rc:
             raise RuntimeError("or_dense_solve failed: %d" % rc)
         return x
@@ -238,82 +256,83 @@ class Prec:
         self.system = system
         self.pp = pp if pp is not None else default_prec_params()
         h = C.c_void_p()
-        rc = lib().or_prec_setup(system._ptr, C.byref(self.pp), C.byref(h))
+        self._L = system._L
+        rc = self._L.or_prec_setup(system._ptr, C.byref(self.pp), C.byref(h))
         if rc:
             raise RuntimeError("or_prec_setup failed: %d" % rc)
         self._h = h
 
     def __del__(self):
         try:
-            lib().or_prec_free(self._h)
+            self._L.or_prec_free(self._h)
         except Exception:
             pass
 
     def apply(self, v):
         v = np.ascontiguousarray(v, dtype=np.float64)
         z = np.empty(self.system.n)
-        lib().or_prec_apply(self._h, _d(v), z.ctypes.data_as(_PD))
+        self._L.or_prec_apply(self._h, _d(v), z.ctypes.data_as(_PD))
         return z
 
     def nlevels(self, which):
-        return lib().or_amg_nlevels(self._h, which)
+        return self._L.or_amg_nlevels(self._h, which)
 
     def level(self, which, l):
-        n = lib().or_amg_level_n(self._h, which, l)
-        nnz = lib().or_amg_level_nnz(self._h, which, l)
+        n = self._L.or_amg_level_n(self._h, which, l)
+        nnz = self._L.or_amg_level_nnz(self._h, which, l)
         nc = 3 if which == 0 else 1
         rp = np.empty(n + 1, np.int64)
         ci = np.empty(nnz, np.int32)
         v = np.empty(nnz * nc)
-        lib().or_amg_level_matrix(self._h, which, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
+        self._L.or_amg_level_matrix(self._h, which, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
         return rp, ci, v.reshape(nnz, nc)
 
     def aggregates(self, which, l):
-        n = lib().or_amg_level_n(self._h, which, l)
+        n = self._L.or_amg_level_n(self._h, which, l)
         agg = np.empty(n, np.int32)
-        na = lib().or_amg_aggregates(self._h, which, l, agg.ctypes.data_as(_PI32))
+        na = self._L.or_amg_aggregates(self._h, which, l, agg.ctypes.data_as(_PI32))
         return agg, na
 
     def roots(self, which, l):
-        n = lib().or_amg_level_n(self._h, which, l)
+        n = self._L.or_amg_level_n(self._h, which, l)
         r = np.zeros(n, np.uint8)
-        lib().or_amg_roots(self._h, which, l, r.ctypes.data_as(_PU8))
+        self._L.or_amg_roots(self._h, which, l, r.ctypes.data_as(_PU8))
         return r.astype(bool)
 
     def prolongator(self, which, l):
-        n = lib().or_amg_level_n(self._h, which, l)
-        nnz = lib().or_amg_p_nnz(self._h, which, l)
+        n = self._L.or_amg_level_n(self._h, which, l)
+        nnz = self._L.or_amg_p_nnz(self._h, which, l)
         nc = 3 if which == 0 else 1
         rp = np.empty(n + 1, np.int64)
         ci = np.empty(nnz, np.int32)
         v = np.empty(nnz * nc)
-        lib().or_amg_prolongator(self._h, which, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
+        self._L.or_amg_prolongator(self._h, which, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
         return rp, ci, v.reshape(nnz, nc)
 
     def vcycle(self, which, comp, b):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.empty_like(b)
-        lib().or_amg_vcycle(self._h, which, comp, _d(b), _d(x))
+        self._L.or_amg_vcycle(self._h, which, comp, _d(b), _d(x))
         return x
 
     def spp(self):
         nc = self.system.n_cells
-        nnz = lib().or_spp_nnz(self._h)
+        nnz = self._L.or_spp_nnz(self._h)
         rp = np.empty(nc + 1, np.int64)
         ci = np.empty(nnz, np.int32)
         v = np.empty(nnz)
-        lib().or_spp(self._h, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
+        self._L.or_spp(self._h, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
         return rp, ci, v
 
     def ilu_dinv(self):
         d = np.empty(4 * self.system.n_cells)
-        lib().or_ilu_dinv(self._h, _d(d))
+        self._L.or_ilu_dinv(self._h, _d(d))
         return d
 
     def ilu_apply(self, w):
         w = np.ascontiguousarray(w, dtype=np.float64)
         dz = np.empty_like(w)
-        lib().or_ilu_apply(self._h, _d(w), _d(dz))
+        self._L.or_ilu_apply(self._h, _d(w), _d(dz))
         return dz
 
     def fgmres(self, b=None, tol=1e-8, restart=100, max_iters=1000):
@@ -321,7 +340,7 @@ class Prec:
         b = s.rhs if b is None else np.ascontiguousarray(b, dtype=np.float64)
         x = np.empty(s.n)
         st = Stats()
-        lib().or_fgmres(s._ptr, self._h, _d(b), _d(x), tol, restart, max_iters, C.byref(st))
+        self._L.or_fgmres(s._ptr, self._h, _d(b), _d(x), tol, restart, max_iters, C.byref(st))
         return x, st
 
 

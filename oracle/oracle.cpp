@@ -6,7 +6,11 @@
 // literal: every routine restates one passage of the paper (cited inline) in
 // the order the paper states it, with no blocking, fusion or reordering.
 //
-// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (see __init__.py).
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (see __init__.py), and
+// a second build of the same source with -fopenmp, whose row loops run on all
+// host cores.  Every sum over a vector is taken in fixed chunks (dot below) and
+// every row's arithmetic is done by one thread in the order written, so the
+// two builds return bit-identical results.
 // -ffp-contract=off keeps every a*b+c as two roundings so that the integer
 // decisions taken from floating point (strength of connection, aggregation)
 // are reproducible on x86 and Arm hosts.
@@ -20,12 +24,39 @@
 #include <functional>
 #include <map>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
 typedef std::vector<double> vec;
 const double kMilliDarcy = 9.869233e-16;  // m^2
 const double kPi = 3.14159265358979323846;
+
+// Inner product sum_e a[e] b[e] taken in fixed chunks of kChunk entries: each chunk is summed in index
+// order, then the chunk sums are added in chunk order.  The chunking does not depend on the thread count.
+const int64_t kChunk = 4096;
+double dot(const double* a, const double* b, int64_t n) {
+  const int64_t nch = (n + kChunk - 1) / kChunk;
+  vec part(size_t(nch), 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < nch; ++k) {
+    double s = 0.0;
+    const int64_t e1 = std::min(n, (k + 1) * kChunk);
+    for (int64_t e = k * kChunk; e < e1; ++e) s += a[e] * b[e];
+    part[k] = s;
+  }
+  double s = 0.0;
+  for (int64_t k = 0; k < nch; ++k) s += part[k];
+  return s;
+}
+
+// Row ranges for loops whose rows produce a variable number of outputs: rows [lo(t), lo(t+1)) form task t.
+// Tasks are filled independently and concatenated in task order, so the result does not depend on how
+// tasks are spread over threads.
+const int kTasks = 64;
+inline int64_t task_lo(int64_t n, int t) { return n * t / kTasks; }
 
 // ---------------------------------------------------------------------------
 // Counter-based random numbers: splitmix64 (S. Vigna), used as a pure
@@ -725,6 +756,7 @@ struct CSR {
 };
 
 void csr_spmv(const CSR& A, int comp, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < A.n; ++i) {
     double s = 0.0;
     for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) s += A.v[q * A.nc + comp] * x[A.ci[q]];
@@ -754,29 +786,39 @@ CSR transpose(const CSR& A) {
 CSR spgemm(const CSR& X, const CSR& Y) {
   CSR C; C.n = X.n; C.m = Y.m; C.nc = X.nc;
   C.rp.assign(C.n + 1, 0);
-  std::vector<int64_t> mark(Y.m, -1);
-  vec acc(size_t(Y.m) * X.nc, 0.0);
-  std::vector<int32_t> cols;
-  for (int64_t i = 0; i < X.n; ++i) {
-    cols.clear();
-    for (int64_t q = X.rp[i]; q < X.rp[i + 1]; ++q) {
-      int64_t k = X.ci[q];
-      for (int64_t r = Y.rp[k]; r < Y.rp[k + 1]; ++r) {
-        int64_t j = Y.ci[r];
-        if (mark[j] != i) {
-          mark[j] = i;
-          cols.push_back(int32_t(j));
-          for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = 0.0;
+  std::vector<std::vector<int32_t>> tci(kTasks);
+  std::vector<vec> tv(kTasks);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < kTasks; ++t) {
+    std::vector<int64_t> mark(Y.m, -1);
+    vec acc(size_t(Y.m) * X.nc, 0.0);
+    std::vector<int32_t> cols;
+    for (int64_t i = task_lo(X.n, t); i < task_lo(X.n, t + 1); ++i) {
+      cols.clear();
+      for (int64_t q = X.rp[i]; q < X.rp[i + 1]; ++q) {
+        int64_t k = X.ci[q];
+        for (int64_t r = Y.rp[k]; r < Y.rp[k + 1]; ++r) {
+          int64_t j = Y.ci[r];
+          if (mark[j] != i) {
+            mark[j] = i;
+            cols.push_back(int32_t(j));
+            for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = 0.0;
+          }
+          for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = acc[j * X.nc + c] + X.v[q * X.nc + c] * Y.v[r * X.nc + c];
         }
-        for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = acc[j * X.nc + c] + X.v[q * X.nc + c] * Y.v[r * X.nc + c];
       }
+      std::sort(cols.begin(), cols.end());
+      for (int32_t j : cols) {
+        tci[t].push_back(j);
+        for (int c = 0; c < X.nc; ++c) tv[t].push_back(acc[j * X.nc + c]);
+      }
+      C.rp[i + 1] = int64_t(cols.size());
     }
-    std::sort(cols.begin(), cols.end());
-    for (int32_t j : cols) {
-      C.ci.push_back(j);
-      for (int c = 0; c < X.nc; ++c) C.v.push_back(acc[j * X.nc + c]);
-    }
-    C.rp[i + 1] = int64_t(C.ci.size());
+  }
+  for (int64_t i = 0; i < C.n; ++i) C.rp[i + 1] += C.rp[i];
+  for (int t = 0; t < kTasks; ++t) {
+    C.ci.insert(C.ci.end(), tci[t].begin(), tci[t].end());
+    C.v.insert(C.v.end(), tv[t].begin(), tv[t].end());
   }
   return C;
 }
@@ -819,6 +861,7 @@ void aggregate(Level& lev, double theta, int level) {
   int64_t n = A.n;
   vec dg(n, 0.0);
   std::vector<uint8_t> excluded(n, 1);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i)
     for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
       if (A.ci[q] == i) dg[i] = abar(A, q);
@@ -829,6 +872,7 @@ void aggregate(Level& lev, double theta, int level) {
   // symmetric strength graph: edge i~j if max(abar_ij, abar_ji) >= theta*sqrt(abar_ii*abar_jj)
   std::vector<uint8_t> strong(A.nnz(), 0);
   vec wgt(A.nnz(), 0.0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     if (excluded[i]) continue;
     for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
@@ -846,6 +890,7 @@ void aggregate(Level& lev, double theta, int level) {
   // smoothed aggregation).  Their prolongator rows still follow (I - w D^{-1} A) P_tent.
   lev.excl = excluded;
   std::vector<uint8_t> st(n, 0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     bool any = false;
     for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) any = any || strong[q];
@@ -858,26 +903,32 @@ void aggregate(Level& lev, double theta, int level) {
     bool any = false;
     for (int64_t i = 0; i < n; ++i) if (st[i] == 0) { any = true; break; }
     if (!any) break;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       int64_t m = st[i] == 0 ? mis_key(i, level) : -1;
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
         if (strong[q] && st[A.ci[q]] == 0) m = std::max(m, mis_key(A.ci[q], level));
       m1[i] = m;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       int64_t m = m1[i];
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
         if (strong[q]) m = std::max(m, m1[A.ci[q]]);
       m2[i] = m;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) nr[i] = (st[i] == 0 && m2[i] == mis_key(i, level));
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) if (nr[i]) st[i] = 1;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       uint8_t c = nr[i];
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
         if (strong[q] && nr[A.ci[q]]) c = 1;
       c1[i] = c;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       if (st[i] != 0) continue;
       uint8_t c = c1[i];
@@ -894,6 +945,7 @@ void aggregate(Level& lev, double theta, int level) {
   lev.nagg = na;
   // phase 1: strong neighbours of a root join it
   std::vector<int32_t> ph1 = lev.agg;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     if (st[i] != 2) continue;
     for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
@@ -901,6 +953,7 @@ void aggregate(Level& lev, double theta, int level) {
   }
   // phase 2: leftovers join the aggregate of their strongest phase-1 neighbour
   lev.agg = ph1;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     if (st[i] != 2 || ph1[i] >= 0) continue;
     double bw = -1.0; int32_t ba = -1;
@@ -917,15 +970,19 @@ void aggregate(Level& lev, double theta, int level) {
 // Gershgorin bound lambda_hat = max_i sum_j |a_ij| / |a_ii| per component
 vec gershgorin(const CSR& A) {
   vec lam(A.nc, 0.0);
-  for (int c = 0; c < A.nc; ++c)
+  for (int c = 0; c < A.nc; ++c) {
+    vec ratio(A.n);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A.n; ++i) {
       double s = 0.0, d = 0.0;
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
         s = s + std::fabs(A.v[q * A.nc + c]);
         if (A.ci[q] == i) d = A.v[q * A.nc + c];
       }
-      lam[c] = std::max(lam[c], s / std::fabs(d));
+      ratio[i] = s / std::fabs(d);
     }
+    for (int64_t i = 0; i < A.n; ++i) lam[c] = std::max(lam[c], ratio[i]);
+  }
   return lam;
 }
 
@@ -937,9 +994,13 @@ CSR smoothed_prolongator(const Level& lev) {
   vec lam = gershgorin(A), omega(nc);
   for (int c = 0; c < nc; ++c) omega[c] = (4.0 / 3.0) / lam[c];
   CSR P; P.n = n; P.m = lev.nagg; P.nc = nc; P.rp.assign(n + 1, 0);
-  std::vector<int32_t> aggs;
-  for (int64_t i = 0; i < n; ++i) {
-    if (!lev.excl[i]) {
+  std::vector<std::vector<int32_t>> tci(kTasks);
+  std::vector<vec> tv(kTasks);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < kTasks; ++t) {
+    std::vector<int32_t> aggs;
+    for (int64_t i = task_lo(n, t); i < task_lo(n, t + 1); ++i) {
+      if (lev.excl[i]) continue;
       aggs.clear();
       for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
         if (lev.agg[A.ci[q]] >= 0) aggs.push_back(lev.agg[A.ci[q]]);
@@ -947,24 +1008,30 @@ CSR smoothed_prolongator(const Level& lev) {
       aggs.erase(std::unique(aggs.begin(), aggs.end()), aggs.end());
       int64_t qd = A.find(i, i);
       for (int32_t a : aggs) {
-        P.ci.push_back(a);
+        tci[t].push_back(a);
         for (int c = 0; c < nc; ++c) {
           double S = 0.0;
           for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
             if (lev.agg[A.ci[q]] == a) S = S + A.v[q * nc + c];
           double coef = omega[c] / A.v[qd * nc + c];
           double delta = a == lev.agg[i] ? 1.0 : 0.0;
-          P.v.push_back(delta - coef * S);
+          tv[t].push_back(delta - coef * S);
         }
       }
+      P.rp[i + 1] = int64_t(aggs.size());
     }
-    P.rp[i + 1] = int64_t(P.ci.size());
+  }
+  for (int64_t i = 0; i < n; ++i) P.rp[i + 1] += P.rp[i];
+  for (int t = 0; t < kTasks; ++t) {
+    P.ci.insert(P.ci.end(), tci[t].begin(), tci[t].end());
+    P.v.insert(P.v.end(), tv[t].begin(), tv[t].end());
   }
   return P;
 }
 
 vec l1_diag(const CSR& A) {
   vec d(A.n * A.nc, 0.0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < A.n; ++i)
     for (int c = 0; c < A.nc; ++c) {
       double s = 0.0;
@@ -1032,18 +1099,24 @@ void chebyshev(const Level& lev, int nc, int c, const vec& b, vec& x, int degree
   double sigma = theta / delta, rho = 1.0 / sigma;
   vec r(n), d(n), Ax(n);
   if (zero) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] / lev.dg[i * nc + c];
   } else {
     csr_spmv(lev.A, c, x.data(), Ax.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i * nc + c];
   }
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) d[i] = r[i] / theta;
   for (int k = 0; k < degree; ++k) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + d[i];
     if (k == degree - 1) break;
     csr_spmv(lev.A, c, x.data(), Ax.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i * nc + c];
     double rn = 1.0 / (2.0 * sigma - rho);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) d[i] = rn * rho * d[i] + 2.0 * rn / delta * r[i];
     rho = rn;
   }
@@ -1054,6 +1127,7 @@ void l1_jacobi(const Level& lev, int nc, int c, const vec& b, vec& x, int sweeps
   vec Ax(n);
   for (int it = 0; it < sweeps; ++it) {
     csr_spmv(lev.A, c, x.data(), Ax.data());
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + (b[i] - Ax[i]) / lev.dl1[i * nc + c];
   }
 }
@@ -1069,12 +1143,14 @@ void vcycle(const AMG& H, int l, int c, const vec& b, vec& x, const Smooth& sm) 
   vec Ax(n);
   csr_spmv(lev.A, c, x.data(), Ax.data());
   vec r(n);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - Ax[i];
   vec bc(lev.R.n), xc;
   csr_spmv(lev.R, c, r.data(), bc.data());
   vcycle(H, l + 1, c, bc, xc, sm);
   vec Pe(n);
   csr_spmv(lev.P, c, xc.data(), Pe.data());
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) x[i] = x[i] + Pe[i];
   if (sm.kind == 0) l1_jacobi(lev, H.nc, c, b, x, sm.post);
   else chebyshev(lev, H.nc, c, b, x, sm.degree, sm.ratio, false);
@@ -1139,6 +1215,14 @@ struct or_prec {
 extern "C" {
 
 uint64_t or_splitmix64(uint64_t state) { return sm64(state); }
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void or_correlated_field(uint64_t seed, int field, int nx, int ny, int nz, int Lx, int Ly, int Lz, double* out) {
   vec f = correlated_field(seed, field, nx, ny, nz, Lx, Ly, Lz);
@@ -1214,6 +1298,7 @@ void or_system_free(or_system* s) {
 void or_spmv(const or_system* s, const double* x, double* y) {
   const double* xu = x;
   const double* xf = x + s->n_u;
+#pragma omp parallel for schedule(static)
   for (int64_t I = 0; I < s->n_nodes; ++I) {
     double acc[3] = {0, 0, 0};
     for (int64_t q = s->uu_rp[I]; q < s->uu_rp[I + 1]; ++q)
@@ -1224,6 +1309,7 @@ void or_spmv(const or_system* s, const double* x, double* y) {
         for (int e = 0; e < 2; ++e) acc[d] += s->uf_v[q * 6 + d * 2 + e] * xf[2 * int64_t(s->uf_ci[q]) + e];
     for (int d = 0; d < 3; ++d) y[3 * I + d] = acc[d];
   }
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < s->n_cells; ++c) {
     double acc[2] = {0, 0};
     for (int64_t q = s->fu_rp[c]; q < s->fu_rp[c + 1]; ++q)
@@ -1362,19 +1448,16 @@ typedef std::function<void(const double*, double*)> Op;
 void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, double tol, int m, int maxit,
             or_stats* st) {
   std::memset(st, 0, sizeof(*st));
-  double bn = 0.0;
-  for (int64_t i = 0; i < n; ++i) bn += b[i] * b[i];
-  bn = std::sqrt(bn);
+  double bn = std::sqrt(dot(b, b, n));
   for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
   if (bn == 0.0) { st->converged = 1; return; }
   vec r(b, b + n), w(n);
   int total = 0;
   for (;;) {
-    double beta = 0.0;
-    for (int64_t i = 0; i < n; ++i) beta += r[i] * r[i];
-    beta = std::sqrt(beta);
+    double beta = std::sqrt(dot(r.data(), r.data(), n));
     std::vector<vec> V, Z;
     V.emplace_back(n);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) V[0][i] = r[i] / beta;
     vec H(size_t(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
     g[0] = beta;
@@ -1385,14 +1468,12 @@ void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, dou
       M(V[j].data(), Z[j].data());
       A(Z[j].data(), w.data());
       for (int i = 0; i <= j; ++i) {
-        double h = 0.0;
-        for (int64_t e = 0; e < n; ++e) h += w[e] * V[i][e];
+        double h = dot(w.data(), V[i].data(), n);
         H[i * m + j] = h;
+#pragma omp parallel for schedule(static)
         for (int64_t e = 0; e < n; ++e) w[e] -= h * V[i][e];
       }
-      double hn = 0.0;
-      for (int64_t e = 0; e < n; ++e) hn += w[e] * w[e];
-      hn = std::sqrt(hn);
+      double hn = std::sqrt(dot(w.data(), w.data(), n));
       H[(j + 1) * m + j] = hn;
       for (int i = 0; i < j; ++i) {
         double a = H[i * m + j], c = H[(i + 1) * m + j];
@@ -1411,6 +1492,7 @@ void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, dou
       if (!(hn > 1e-300)) brk = true;
       if (st->est_relres <= tol || brk || total >= maxit || j == m - 1) break;
       V.emplace_back(n);
+#pragma omp parallel for schedule(static)
       for (int64_t e = 0; e < n; ++e) V[j + 1][e] = w[e] / hn;
     }
     vec y(jend + 1);
@@ -1419,11 +1501,14 @@ void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, dou
       for (int k2 = i + 1; k2 <= jend; ++k2) s -= H[i * m + k2] * y[k2];
       y[i] = s / H[i * m + i];
     }
-    for (int i = 0; i <= jend; ++i)
+    for (int i = 0; i <= jend; ++i) {
+#pragma omp parallel for schedule(static)
       for (int64_t e = 0; e < n; ++e) x[e] += y[i] * Z[i][e];
+    }
     A(x, w.data());
-    double rn = 0.0;
-    for (int64_t e = 0; e < n; ++e) { r[e] = b[e] - w[e]; rn += r[e] * r[e]; }
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) r[e] = b[e] - w[e];
+    double rn = dot(r.data(), r.data(), n);
     st->true_relres = std::sqrt(rn) / bn;
     st->iters = total;
     if (std::isnan(st->true_relres)) return;
@@ -1472,6 +1557,7 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
   BSR Auu = to_bsr(s, 0);
   // §5.1, fixed-stress Schur approximation: S_ff^(FS) = A_ff + blockdiag([[0, D_sp],[0, D_pp]])
   P->Sff = P->A_ff;
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
     int64_t q = P->Sff.find(c, c);
     P->Sff.v[q * 4 + 1] = P->Sff.v[q * 4 + 1] + s->d_fs[2 * c];
@@ -1488,6 +1574,7 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
   P->spp.n = P->spp.m = nc; P->spp.nc = 1;
   P->spp.rp = P->Sff.rp; P->spp.ci = P->Sff.ci;
   P->spp.v.resize(P->Sff.ci.size());
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
     double ratio = P->dps[c] / P->dss[c];
     for (int64_t q = P->Sff.rp[c]; q < P->Sff.rp[c + 1]; ++q)
@@ -1611,8 +1698,10 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
   if (P->pp.mech_mode == OR_MECH_AMG) {
     for (int c = 0; c < 3; ++c) {
       vec b(nn), x;
+#pragma omp parallel for schedule(static)
       for (int64_t I = 0; I < nn; ++I) b[I] = v[3 * I + c];
       vcycle(P->amg_u, 0, c, b, x, smooth_of(P->pp));
+#pragma omp parallel for schedule(static)
       for (int64_t I = 0; I < nn; ++I) zu[3 * I + c] = x[I];
     }
   } else {
@@ -1620,6 +1709,7 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
   }
   // step 2: y_f = v_f - A_fu z_u
   vec yf(nf);
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c)
     for (int a = 0; a < 2; ++a) {
       double acc = 0.0;
@@ -1633,8 +1723,10 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
   } else {
     // step 3: z_s = D_ss^{-1} y_s
     vec zs(nc), wp(nc), zp(nc);
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) zs[c] = yf[2 * c] / P->dss[c];
     // step 4: w_p = y_p - A_ps z_s (complete A_ps)
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) {
       double acc = 0.0;
       for (int64_t q = P->A_ff.rp[c]; q < P->A_ff.rp[c + 1]; ++q) acc += P->A_ff.v[q * 4 + 2] * zs[P->A_ff.ci[q]];
@@ -1648,9 +1740,11 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
     } else {
       P->lu_pp.solve(wp.data(), zp.data());
     }
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) { zf[2 * c] = zs[c]; zf[2 * c + 1] = zp[c]; }
     // step 6: w_f = y_f - S_ff^(FS) z_f
     vec wf(nf);
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c)
       for (int a = 0; a < 2; ++a) {
         double acc = 0.0;
@@ -1663,9 +1757,12 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
     if (P->pp.local_mode == OR_LOCAL_ILU0) or_ilu_apply(P, wf.data(), dz.data());
     else P->lu_local.solve(wf.data(), dz.data());
     // step 8: z_f += dz_f
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < nf; ++e) zf[e] += dz[e];
   }
+#pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < nu; ++e) z[e] = zu[e];
+#pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < nf; ++e) z[nu + e] = zf[e];
 }
 

@@ -81,6 +81,9 @@ typedef struct {
   double *E, *nu, *kh, *kv, *phi0, *sw, *p;
 } or_system;
 
+/* host threads the row loops of this build use (1 unless built with -fopenmp) */
+int or_num_threads(void);
+
 /* splitmix64 output for the given state (Vigna's published generator) */
 uint64_t or_splitmix64(uint64_t state);
 

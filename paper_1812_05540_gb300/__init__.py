@@ -146,6 +146,8 @@ def lib():
         L.ps_server_destroy.restype = None
         L.ps_launch_count.argtypes = []
         L.ps_launch_count.restype = C.c_int64
+        L.ps_alloc_count.argtypes = []
+        L.ps_alloc_count.restype = C.c_int64
         L.ps_strerror.argtypes = [C.c_int]
         L.ps_strerror.restype = C.c_char_p
         _lib = L
@@ -169,6 +171,10 @@ def ps_strerror(status):
 
 def ps_launch_count():
     return lib().ps_launch_count()
+
+
+def ps_alloc_count():
+    return lib().ps_alloc_count()
 
 
 def ps_params_default(**kw):

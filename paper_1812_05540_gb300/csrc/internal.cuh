@@ -29,6 +29,8 @@ namespace ps_internal {
 
 // number of kernels launched by this library (for launch accounting)
 extern std::atomic<int64_t> g_launches;
+// number of device allocations made through Arena::alloc (the library's only device allocation path)
+extern std::atomic<int64_t> g_allocs;
 #define PS_TICK() ps_internal::g_launches.fetch_add(1, std::memory_order_relaxed)
 
 void set_last_error(cudaError_t e, const char* what, const char* file, int line);

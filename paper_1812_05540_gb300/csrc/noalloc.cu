@@ -180,21 +180,44 @@ bool shape_ok(const ps_bsr& B, int64_t rows, int64_t cols, int br, int bc) {
 
 extern "C" ps_status ps_residual_noalloc(const ps_jacobian* jac, const ps_grid* grid, const double* x,
                                          const double* b, double* r, double* rnorm2, void* stream) {
-  if (!jac || !grid || !x || !b || !r || !rnorm2) return PS_ERR_INVALID;
-  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return PS_ERR_INVALID;
+  if (!jac || !grid || !x || !b || !r || !rnorm2) {
+    ps_internal::set_reason("ps_residual_noalloc: a null pointer argument");
+    return PS_ERR_INVALID;
+  }
+  if (r == x || r == b) {
+    ps_internal::set_reason("ps_residual_noalloc: r must not be the same array as x or b");
+    return PS_ERR_INVALID;
+  }
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) {
+    ps_internal::set_reason("ps_residual_noalloc: grid %dx%dx%d has an empty dimension", grid->nx, grid->ny,
+                            grid->nz);
+    return PS_ERR_INVALID;
+  }
   int64_t nn = int64_t(grid->nx + 1) * (grid->ny + 1) * (grid->nz + 1);
   int64_t nc = int64_t(grid->nx) * grid->ny * grid->nz;
-  if (!shape_ok(jac->A_uu, nn, nn, 3, 3) || !shape_ok(jac->A_uf, nn, nc, 3, 2) ||
-      !shape_ok(jac->A_fu, nc, nn, 2, 3) || !shape_ok(jac->A_ff, nc, nc, 2, 2))
-    return PS_ERR_INVALID;
+  const struct {
+    const ps_bsr* B;
+    const char* name;
+    int64_t rows, cols;
+    int br, bc;
+  } blocks[4] = {{&jac->A_uu, "A_uu", nn, nn, 3, 3}, {&jac->A_uf, "A_uf", nn, nc, 3, 2},
+                 {&jac->A_fu, "A_fu", nc, nn, 2, 3}, {&jac->A_ff, "A_ff", nc, nc, 2, 2}};
+  for (const auto& k : blocks)
+    if (!shape_ok(*k.B, k.rows, k.cols, k.br, k.bc)) {
+      ps_internal::set_reason("ps_residual_noalloc: %s must be %lld x %lld blocks of %dx%d with non-null arrays",
+                              k.name, (long long)k.rows, (long long)k.cols, k.br, k.bc);
+      return PS_ERR_INVALID;
+    }
   const int64_t rows_per_block = kThreads / 32;
   int64_t gu = (nn + rows_per_block - 1) / rows_per_block;
   int64_t gf = (nc + rows_per_block - 1) / rows_per_block;
   if (gu + gf > kMaxPartials) {
-    ps_internal::set_reason("ps_residual_noalloc: %lld node + %lld cell rows exceed the fixed scratch of %lld "
-                            "row blocks (at most %lld rows in total)",
-                            (long long)nn, (long long)nc, (long long)kMaxPartials,
-                            (long long)(kMaxPartials * rows_per_block));
+    ps_internal::set_reason("ps_residual_noalloc: %lld node + %lld cell rows need %lld blocks of %lld rows, "
+                            "more than the fixed scratch of %lld (ceil(nodes/%lld) + ceil(cells/%lld) must be "
+                            "at most %lld)",
+                            (long long)nn, (long long)nc, (long long)(gu + gf), (long long)rows_per_block,
+                            (long long)kMaxPartials, (long long)rows_per_block, (long long)rows_per_block,
+                            (long long)kMaxPartials);
     return PS_ERR_INVALID;
   }
   double* scratch = nullptr;

@@ -8,6 +8,7 @@
 namespace ps_internal {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_allocs{0};
 // per host thread, so that concurrent requests of the server keep their own messages
 static thread_local std::string g_last_error;
 
@@ -66,6 +67,7 @@ ps_status Arena::alloc(void** p, size_t nbytes) {
   }
   ptrs.push_back(*p);
   bytes += int64_t(nbytes);
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   return PS_OK;
 }
 
@@ -244,3 +246,4 @@ void rowptr_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t st) 
 }  // namespace ps_internal
 
 extern "C" int64_t ps_launch_count(void) { return ps_internal::g_launches.load(); }
+extern "C" int64_t ps_alloc_count(void) { return ps_internal::g_allocs.load(); }

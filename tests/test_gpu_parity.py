@@ -121,11 +121,13 @@ def test_hierarchy_parity(cfg, kw, cm):
 
 
 @pytest.mark.parametrize("ilu", [ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH])
-@pytest.mark.parametrize("cm", [16, 500])
-def test_apply_parity_fp64(cm, ilu):
-    # Algorithm 1 in FP64 against the oracle's Algorithm 1 on the same vector
+@pytest.mark.parametrize("cfg,kw,cm", [(0, {}, 16), (0, {}, 500), (1, dict(nx=24, ny=20, nz=10), 500),
+                                       (2, dict(nx=20, ny=44, nz=17), 500)])
+def test_apply_parity_fp64(cfg, kw, cm, ilu):
+    # Algorithm 1 in FP64 against the oracle's Algorithm 1 on the same vector; the two larger grids have
+    # multi-level hierarchies at the default coarse size (500)
     g = _gpu()
-    osys = oracle.System(oracle.default_params(0))
+    osys = oracle.System(oracle.default_params(cfg, **kw))
     P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
     dev = g.to_device(osys)
     h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm, ilu_mode=ilu))

@@ -32,8 +32,11 @@ def test_residual_noalloc_matches_allocating_path():
         y = torch.empty_like(b)
         for seed in (0, 1):  # two calls in a row on the shared scratch
             x = torch.from_numpy(np.random.default_rng(seed).standard_normal(osys.n)).cuda()
+            torch.cuda.synchronize()
+            allocs = ps.ps_alloc_count()
             ps.ps_residual_noalloc(dev.jac, dev.grid, x.data_ptr(), b.data_ptr(), r.data_ptr(), rn2.data_ptr())
             torch.cuda.synchronize()
+            assert ps.ps_alloc_count() == allocs  # the call made no device allocation
             ps.ps_spmv(h, x.data_ptr(), y.data_ptr())
             ref = (b - y).cpu().numpy()
             got = r.cpu().numpy()
@@ -53,4 +56,32 @@ def test_residual_noalloc_rejects_oversized_systems():
     jac = ps.ps_jacobian(blk(nn, nn, 3, 3), blk(nn, nc, 3, 2), blk(nc, nn, 2, 3), blk(nc, nc, 2, 2), 1, None)
     with pytest.raises(ps.PsError) as e:
         ps.ps_residual_noalloc(jac, grid, 1, 1, 1, 1)
+    assert e.value.status == ps.PS_ERR_INVALID and "scratch" in str(e.value)
+
+
+def test_residual_noalloc_rejects_bad_arguments_with_a_reason():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    grid = ps.ps_grid(4, 4, 2, 10.0, 10.0, 10.0)
+    nn, nc = 5 * 5 * 3, 4 * 4 * 2
+    blk = lambda r, c, br, bc: ps.ps_bsr(r, c, 0, br, bc, 1, 1, 1)
+    jac = ps.ps_jacobian(blk(nn, nn, 3, 3), blk(nn, nc, 3, 2), blk(nc, nn, 2, 3), blk(nc, nc, 2, 2), 1, None)
+    # r aliasing x or b is refused on the host
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_residual_noalloc(jac, grid, 8, 16, 8, 24)
+    assert e.value.status == ps.PS_ERR_INVALID and "same array" in str(e.value)
+    # a block of the wrong shape is named
+    bad = ps.ps_jacobian(blk(nn, nn, 3, 3), blk(nn, nc, 3, 2), blk(nc, nn, 2, 3), blk(nc, nc + 1, 2, 2), 1, None)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_residual_noalloc(bad, grid, 8, 16, 24, 32)
+    assert e.value.status == ps.PS_ERR_INVALID and "A_ff" in str(e.value)
+    # one row block past the scratch: ceil(nodes/8) + ceil(cells/8) = 2^19 + 1
+    nx, ny, nz = 113, 189, 97
+    nodes, cells = (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
+    assert -(-nodes // 8) + -(-cells // 8) == 2 ** 19 + 1
+    big = ps.ps_grid(nx, ny, nz, 10.0, 10.0, 10.0)
+    bj = ps.ps_jacobian(blk(nodes, nodes, 3, 3), blk(nodes, cells, 3, 2), blk(cells, nodes, 2, 3),
+                        blk(cells, cells, 2, 2), 1, None)
+    with pytest.raises(ps.PsError) as e:
+        ps.ps_residual_noalloc(bj, big, 8, 16, 24, 32)
     assert e.value.status == ps.PS_ERR_INVALID and "scratch" in str(e.value)
