@@ -246,6 +246,33 @@ def fp64_peak_tflops(sms, peaks):
     return sms * 4.0 * mhz * 1e6 / 1e12, "derived: %d SMs x 4 FP64 flop/clk x %.0f MHz" % (sms, mhz)
 
 
+def vcycle_bytes(levels, nc, degree=2):
+    """Algorithmic bytes of one V-cycle (Chebyshev of the given degree, one pre- and one post-smoothing
+    application) from the level shapes: every matrix read once per use (level operator once per pass,
+    P and R once, the coarsest dense FP64 inverse once) and every vector a step reads or writes once.
+    levels: tuples (rows, entries, next rows, P entries, stencil slots, value bytes, P/R value bytes,
+    coarsest), as ps_amg_level_shape returns them."""
+    total = 0
+    for n, e, m, p, ns, s, sp, coarsest in levels:
+        vec = n * nc * s
+        if coarsest:
+            total += n * n * nc * 8 + 2 * vec
+            continue
+        op = ns * nc * s * n if ns else e * (nc * s + 4) + 4 * (n + 1)
+        passes = 2 * degree  # degree - 1 operator passes of pre-smoothing from x = 0, residual, degree post
+        # vectors read or written, per kernel: the first two pre steps in one pass (b, D^{-1}/theta, D in;
+        # x out; d out when more steps follow), further pre steps (x, b, D, d in; x out; d out but the
+        # last), the residual (x, b in; r out), the first post step (x, b, D in; x, d out), further post
+        # steps (x, b, D, d in; x out; d out but the last)
+        vectors = (4 + (degree > 2)) + sum(5 + (k < degree - 1) for k in range(2, degree)) + 3
+        vectors += 4 + (degree > 1) + sum(5 + (k < degree - 1) for k in range(1, degree))
+        transfer = p * (nc * sp + 4)
+        total += passes * op + vectors * vec
+        total += transfer + 4 * (n + 1) + m * nc * s + 2 * vec  # x += P e
+        total += transfer + 4 * (m + 1) + vec + m * nc * s  # b_c = R r
+    return total
+
+
 def load_traffic():
     """Per-launch DRAM bytes from a committed ncu capture, kept only while the kernel's source is
     the one that was profiled."""
@@ -301,8 +328,8 @@ def run_ours(args):
         n = s.n
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
 
-        def step(prec):
-            p = ps.ps_params_default(precision=prec, stream=sptr)
+        def step(prec, **kw):
+            p = ps.ps_params_default(precision=prec, stream=sptr, **kw)
             if args.profile_iters:
                 p.max_iters = args.profile_iters
             h = ps.ps_setup(s.jac, s.grid, p)
@@ -318,7 +345,7 @@ def run_ours(args):
             if world > 1:
                 torch.distributed.barrier()
 
-        def timed(prec, steps, clocks=None):
+        def timed(prec, steps, clocks=None, **kw):
             stats = []
             barrier()
             torch.cuda.synchronize()
@@ -329,7 +356,7 @@ def run_ours(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(steps):
-                stats.append(step(prec))
+                stats.append(step(prec, **kw))
             e1.record(stream)
             torch.cuda.synchronize()
             ck = clocks.stop() if clocks else None
@@ -351,6 +378,9 @@ def run_ours(args):
         t_64, st_64 = (t_mx, st_mx) if args.no_fp64 else timed(ps.PS_FP64, args.steps)[:2]
         # BF16-prolongator variant of the mixed mode: time and iteration cost
         t_bp, st_bp = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_BF16P, args.steps)[:2]
+        # the other local stage of §5.3 (option 1): three sweeps of block Gauss-Seidel instead of ILU(0)
+        t_gs, st_gs = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
+                                                               local_stage=ps.PS_LOCAL_HBGS)[:2]
         per_mx = t_mx / args.steps
         per_64 = t_64 / args.steps
 
@@ -363,6 +393,11 @@ def run_ours(args):
         rhs_np = dev_to_numpy(s.rhs, n, np.float64)
         relres = float(np.linalg.norm(rhs_np - y.cpu().numpy()) / np.linalg.norm(rhs_np))
         x_last = x.cpu().numpy()
+
+        # level shapes of both hierarchies in the mixed mode (V-cycle traffic per apply)
+        hm = ps.ps_setup(s.jac, s.grid, ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr))
+        shapes = {w: [ps.ps_amg_level_shape(hm, w, l) for l in range(ps.ps_amg_nlevels(hm, w))] for w in (0, 1)}
+        ps.ps_free(hm)
 
         # FP64 Jacobian SpMV timed alone on its stream (secondary roofline)
         nb = algorithmic_spmv_bytes(s)
@@ -417,6 +452,18 @@ def run_ours(args):
              "hbm_achieved_gbs": nb / t_spmv / 1e9, "hbm_peak_gbs": hbm_peak, "hbm_frac": nb / t_spmv / 1e9 / hbm_peak,
              "hbm_peak_source": hbm_src},
         ]
+
+        # V-cycles of the mixed solve: algorithmic bytes per apply over the per-apply time from the library's
+        # events on its stream (Algorithm 1 steps 1 and 5 of every iteration of the last timed solve)
+        for w, name, ms in ((0, "mechanics V-cycle, all levels (Algorithm 1 step 1)", st_last.ms_vcycle_u),
+                            (1, "pressure V-cycle, all levels (Algorithm 1 step 5)", st_last.ms_vcycle_p)):
+            vb = vcycle_bytes(shapes[w], 3 if w == 0 else 1)
+            t_apply = ms / 1000.0 / st_last.iters
+            gbs = vb / t_apply / 1e9
+            rooflines.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": gbs / hbm_peak, "traffic": None, "algorithmic_bytes_per_launch": vb,
+                              "launch_ms": 1000.0 * t_apply, "peak_source": hbm_src,
+                              "levels": [list(x) for x in shapes[w]]})
 
         # end to end through the C ABI with host buffers (pinned), copies inside the timed region
         e2e = None
@@ -513,6 +560,13 @@ def run_ours(args):
             "value": t_bp / args.steps / world, "iters": [st.iters for st in st_bp],
             "solve_ms": [round(st.ms_solve, 2) for st in st_bp],
             "vcycle_u_ms": round(st_bp[-1].ms_vcycle_u, 1), "vcycle_p_ms": round(st_bp[-1].ms_vcycle_p, 1)},
+        "local_stage_hbgs": None if st_gs is None else {
+            "value": t_gs / args.steps / world, "iters": [st.iters for st in st_gs],
+            "solve_ms": [round(st.ms_solve, 2) for st in st_gs],
+            "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_gs],
+            "local_stage_ms": round(st_gs[-1].ms_ilu, 1),
+            "note": "M_L = 3 sweeps of block Gauss-Seidel on S_ff^(FS), red-black cell order (paper §5.3 option 1); "
+                    "the headline uses option 2, block ILU(0)"},
         "true_relres_mixed": relres, "gen_s": gen_s,
         "roofline": {k: rooflines[0][k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic")},
         "rooflines": rooflines,

@@ -53,6 +53,9 @@ typedef enum {
 enum { PS_FP64 = 0, PS_MIXED_FP32 = 1, PS_MIXED_BF16P = 2 };
 enum { PS_SMOOTH_L1JACOBI = 0, PS_SMOOTH_CHEBYSHEV = 1 };
 enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
+/* local stage M_L of §5.3: option 2, one sweep of block ILU(0) (default); option 1, local_sweeps sweeps of
+   block Gauss-Seidel on the interleaved S_ff^(FS), cells taken in red-black order */
+enum { PS_LOCAL_ILU0 = 0, PS_LOCAL_HBGS = 1 };
 enum { PS_ORTHO_MGS = 0, PS_ORTHO_CGS2 = 1 };    /* Arnoldi orthogonalisation */
 
 /* Cartesian box of nx*ny*nz cubic cells (§6 grids); hx = hy = hz. */
@@ -113,6 +116,8 @@ typedef struct {
                                  one-vector-at-a-time modified Gram-Schmidt in exact arithmetic
                                  (forward substitution with the in-block Gram entries); larger
                                  sweeps need fewer grid barriers */
+  int32_t local_stage;        /* PS_LOCAL_ILU0 (default) or PS_LOCAL_HBGS (§5.3 option 1) */
+  int32_t local_sweeps;       /* PS_LOCAL_HBGS: block Gauss-Seidel sweeps (default 3, as in §6.1) */
 } ps_params;
 
 typedef struct {
@@ -169,6 +174,12 @@ ps_status ps_apply_prec(ps_handle* h, const double* v, double* z);
 int32_t ps_amg_nlevels(ps_handle* h, int32_t which);
 ps_status ps_amg_level_info(ps_handle* h, int32_t which, int32_t level, int64_t* n, int64_t* nnz,
                             int64_t* nagg);
+/* Shape of one level as the V-cycle applies it (for traffic accounting): shape[0] rows, [1] operator
+   entries, [2] rows of the next level (0 on the coarsest), [3] prolongator entries (R = P^T has as
+   many), [4] stencil slots of the level's stencil copy (27 or 7; 0 when the level runs in CSR form),
+   [5] bytes per stored operator value in the apply precision (4 or 8), [6] bytes per stored P and R
+   value (2 with BF16 transfer operators), [7] 1 on the coarsest level (dense FP64 inverse). */
+ps_status ps_amg_level_shape(ps_handle* h, int32_t which, int32_t level, int64_t* shape);
 /* host copies: rowptr[n+1], colind[nnz], val[nnz*ncomp] (ncomp 3 or 1), agg[n] (-1 excluded) */
 ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t* rowptr, int32_t* colind,
                             double* val, int32_t* agg);

@@ -26,7 +26,7 @@ OR_ALL = 0x7F
 FIELDS_LOGNORMAL, FIELDS_LAYERED, FIELDS_CHANNELS, FIELDS_HOMOGENEOUS = range(4)
 MECH_AMG, MECH_EXACT = 0, 1
 FLOW_CPR, FLOW_EXACT_FS, FLOW_EXACT_SCHUR = 0, 1, 2
-LOCAL_ILU0, LOCAL_EXACT = 0, 1
+LOCAL_ILU0, LOCAL_EXACT, LOCAL_GS = 0, 1, 2
 PRESS_AMG, PRESS_EXACT = 0, 1
 
 
@@ -83,7 +83,8 @@ class PrecParams(C.Structure):
                 ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32), ("pre", C.c_int32),
                 ("post", C.c_int32), ("smoother", C.c_int32), ("cheb_degree", C.c_int32),
                 ("cheb_ratio", C.c_double), ("mech_mode", C.c_int32), ("flow_mode", C.c_int32),
-                ("local_mode", C.c_int32), ("press_mode", C.c_int32), ("full_exact", C.c_int32)]
+                ("local_mode", C.c_int32), ("press_mode", C.c_int32), ("full_exact", C.c_int32),
+                ("local_sweeps", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -143,6 +144,7 @@ def lib(openmp=None):
         L.or_spp.argtypes = [C.c_void_p, _PI64, _PI32, _PD]
         L.or_ilu_dinv.argtypes = [C.c_void_p, _PD]
         L.or_ilu_apply.argtypes = [C.c_void_p, _PD, _PD]
+        L.or_gs_apply.argtypes = [C.c_void_p, _PD, _PD, C.c_int]
         L.or_fgmres.argtypes = [C.POINTER(_System), C.c_void_p, _PD, _PD, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(Stats)]
         L.or_fgmres_diag.argtypes = [C.c_int64, _PD, _PD, _PD, C.c_double, C.c_int, C.c_int, C.POINTER(Stats)]
@@ -333,6 +335,12 @@ class Prec:
         w = np.ascontiguousarray(w, dtype=np.float64)
         dz = np.empty_like(w)
         self._L.or_ilu_apply(self._h, _d(w), _d(dz))
+        return dz
+
+    def gs_apply(self, w, sweeps):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        dz = np.empty_like(w)
+        self._L.or_gs_apply(self._h, _d(w), _d(dz), sweeps)
         return dz
 
     def fgmres(self, b=None, tol=1e-8, restart=100, max_iters=1000):

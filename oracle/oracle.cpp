@@ -1209,6 +1209,7 @@ struct or_prec {
   AMG amg_u, amg_p;
   BSR ilu;              // L (unit, strictly lower) and U (upper) blocks in the S_ff pattern
   vec dinv;             // inv(U_ii)
+  vec gs_dinv;          // inv of the diagonal blocks of S_ff^(FS) (block Gauss-Seidel)
   DenseLU lu_uu, lu_flow, lu_local, lu_pp, lu_full;
 };
 
@@ -1546,6 +1547,7 @@ void or_default_prec_params(or_prec_params* pp) {
   pp->max_levels = 25;
   pp->pre = 1; pp->post = 1;
   pp->smoother = 1; pp->cheb_degree = 2; pp->cheb_ratio = 20.0;
+  pp->local_sweeps = 3;
 }
 
 int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
@@ -1621,6 +1623,9 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
     }
     inv22(&P->ilu.v[P->ilu.find(i, i) * 4], &P->dinv[4 * i]);
   }
+  // §5.3 option 1: block Gauss-Seidel needs the inverse diagonal blocks of S_ff^(FS)
+  P->gs_dinv.assign(4 * nc, 0.0);
+  for (int64_t i = 0; i < nc; ++i) inv22(&P->Sff.v[P->Sff.find(i, i) * 4], &P->gs_dinv[4 * i]);
   if (pp->flow_mode == OR_FLOW_EXACT_FS || pp->local_mode == OR_LOCAL_EXACT) {
     vec d(size_t(s->n_f) * s->n_f, 0.0);
     bsr_dense(P->Sff, d, 0, 0, s->n_f);
@@ -1685,6 +1690,35 @@ int or_ilu_apply(const or_prec* P, const double* w, double* dz) {
     dz[2 * i] = D[0] * a0 + D[1] * a1;
     dz[2 * i + 1] = D[2] * a0 + D[3] * a1;
   }
+  return 0;
+}
+
+// §5.3 option 1, block Gauss-Seidel on the interleaved S_ff^(FS): each sweep updates every cell in turn,
+// z_i = inv(S_ii) (w_i - sum_{j != i} S_ij z_j) with the newest z_j.  The cells are taken in red-black order
+// (colour (i + j + k) mod 2 of the cell's grid coordinates, colour 0 first): a face neighbour always has the
+// other colour, so each colour's updates are independent of one another.
+int or_gs_apply(const or_prec* P, const double* w, double* dz, int sweeps) {
+  const or_system* s = P->s;
+  int64_t nc = s->n_cells;
+  const int64_t nx = s->nx, ny = s->ny;
+  for (int64_t e = 0; e < 2 * nc; ++e) dz[e] = 0.0;
+  for (int it = 0; it < sweeps; ++it)
+    for (int colour = 0; colour < 2; ++colour)
+      for (int64_t i = 0; i < nc; ++i) {
+        const int64_t ci = i % nx, cj = (i / nx) % ny, ck = i / (nx * ny);
+        if (((ci + cj + ck) & 1) != colour) continue;
+        double a0 = w[2 * i], a1 = w[2 * i + 1];
+        for (int64_t q = P->Sff.rp[i]; q < P->Sff.rp[i + 1]; ++q) {
+          int64_t j = P->Sff.ci[q];
+          if (j == i) continue;
+          const double* S = &P->Sff.v[q * 4];
+          a0 -= S[0] * dz[2 * j] + S[1] * dz[2 * j + 1];
+          a1 -= S[2] * dz[2 * j] + S[3] * dz[2 * j + 1];
+        }
+        const double* D = &P->gs_dinv[4 * i];
+        dz[2 * i] = D[0] * a0 + D[1] * a1;
+        dz[2 * i + 1] = D[2] * a0 + D[3] * a1;
+      }
   return 0;
 }
 
@@ -1755,6 +1789,7 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
     // step 7: dz_f = M_L^{-1} w_f
     vec dz(nf);
     if (P->pp.local_mode == OR_LOCAL_ILU0) or_ilu_apply(P, wf.data(), dz.data());
+    else if (P->pp.local_mode == OR_LOCAL_GS) or_gs_apply(P, wf.data(), dz.data(), P->pp.local_sweeps);
     else P->lu_local.solve(wf.data(), dz.data());
     // step 8: z_f += dz_f
 #pragma omp parallel for schedule(static)

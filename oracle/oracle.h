@@ -110,7 +110,7 @@ int or_residual(const or_gen_params* gp, const double* dx, double* r);
 /* preconditioner */
 enum { OR_MECH_AMG = 0, OR_MECH_EXACT = 1 };                 /* M_uu */
 enum { OR_FLOW_CPR = 0, OR_FLOW_EXACT_FS = 1, OR_FLOW_EXACT_SCHUR = 2 }; /* M_ff */
-enum { OR_LOCAL_ILU0 = 0, OR_LOCAL_EXACT = 1 };               /* M_L */
+enum { OR_LOCAL_ILU0 = 0, OR_LOCAL_EXACT = 1, OR_LOCAL_GS = 2 }; /* M_L: ILU(0), exact, block Gauss-Seidel */
 enum { OR_PRESS_AMG = 0, OR_PRESS_EXACT = 1 };                /* M_pp */
 
 typedef struct {
@@ -123,6 +123,7 @@ typedef struct {
   double cheb_ratio;    /* Chebyshev interval [lambda_hat/ratio, lambda_hat] */
   int32_t mech_mode, flow_mode, local_mode, press_mode;
   int32_t full_exact; /* M^{-1} = A^{-1} (dense, tiny systems only) */
+  int32_t local_sweeps; /* OR_LOCAL_GS: block Gauss-Seidel sweeps (3 in §6.1) */
 } or_prec_params;
 
 typedef struct or_prec or_prec;
@@ -162,6 +163,9 @@ int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v);
 int or_ilu_dinv(const or_prec* p, double* dinv);
 /* apply M_L^{-1} (block ILU(0)) to a flow vector */
 int or_ilu_apply(const or_prec* p, const double* w, double* dz);
+/* option 1 of §5.3: `sweeps` sweeps of block Gauss-Seidel on the interleaved S_ff^(FS) from dz = 0, cells
+   visited in red-black order (colour (i + j + k) mod 2, colour 0 first, ascending id within a colour) */
+int or_gs_apply(const or_prec* p, const double* w, double* dz, int sweeps);
 
 typedef struct {
   int32_t iters, restarts, converged, breakdown;

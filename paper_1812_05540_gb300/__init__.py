@@ -47,7 +47,8 @@ class ps_params(C.Structure):
                 ("coarse_max_u", C.c_int32), ("coarse_max_p", C.c_int32), ("max_levels", C.c_int32),
                 ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
                 ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
-                ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32)]
+                ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
+                ("local_stage", C.c_int32), ("local_sweeps", C.c_int32)]
 
 
 class ps_stats(C.Structure):
@@ -120,6 +121,7 @@ def lib():
         L.ps_amg_nlevels.restype = C.c_int32
         L.ps_amg_level_info.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_int64)]
+        L.ps_amg_level_shape.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
         L.ps_amg_level_copy.argtypes = [H, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ps_flow_copy.argtypes = [H, C.c_void_p, C.c_void_p]
         L.ps_free.argtypes = [H]
@@ -257,6 +259,13 @@ def ps_amg_level_info(h, which, level):
     n, nnz, nagg = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().ps_amg_level_info(h, which, level, C.byref(n), C.byref(nnz), C.byref(nagg)), "ps_amg_level_info")
     return n.value, nnz.value, nagg.value
+
+
+def ps_amg_level_shape(h, which, level):
+    """(rows, entries, next rows, P entries, stencil slots, operator value bytes, P/R value bytes, coarsest)"""
+    out = (C.c_int64 * 8)()
+    _check(lib().ps_amg_level_shape(h, which, level, out), "ps_amg_level_shape")
+    return tuple(int(v) for v in out)
 
 
 def ps_amg_level_copy(h, which, level):

@@ -50,6 +50,9 @@ struct AmgLevel {
   // side b (written by the finer level's restriction) and result e (read by
   // the finer level's prolongation)
   void *x = nullptr, *t = nullptr, *r = nullptr, *d = nullptr, *b = nullptr, *e = nullptr;
+  // Chebyshev smoothing: D^{-1} / theta per row and component (n*nc, apply precision), the scaling of
+  // the first step from x = 0
+  void* dsi = nullptr;
 };
 
 struct Amg {
@@ -94,9 +97,9 @@ struct SmoothParams {
 // x = V-cycle(b) on the level-0 vectors (interleaved nc components), T = float or double
 template <class T>
 ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st);
-// allocate the per-level work vectors for precision T
+// allocate the per-level work vectors for precision T (and the Chebyshev first-step scaling of sp)
 template <class T>
-ps_status amg_alloc_work(Arena& ar, Amg& H);
+ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st);
 
 // SpMV lane choice from the mean row length
 inline int lanes_for(double mean_row) {

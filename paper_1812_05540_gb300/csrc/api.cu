@@ -105,7 +105,7 @@ ps_status alg1(ps_handle* h, const double* v, double* z) {
   PS_TRY(amg_vcycle<T>(h->amg_p, sp, W->wp, W->zp, st));
   cudaEventRecord(h->fe[3], st);
   // steps 6-8
-  alg1_steps_6_8<T>(h->F, *W, z + h->nu, h->prm.ilu_mode, st);
+  alg1_steps_6_8<T>(h->F, *W, z + h->nu, h->prm.ilu_mode, st);  // ILU(0) or block Gauss-Seidel, per F.local
   cudaEventRecord(h->fe[4], st);
   h->fine_pending = true;
   PS_CUDA(cudaGetLastError());
@@ -162,6 +162,8 @@ ps_status build_flow(ps_handle* h) {
   F.rp = h->J.ff_rp; F.ci = h->J.ff_ci;
   F.fu_rp = h->J.fu_rp; F.fu_ci = h->J.fu_ci; F.fu_v = h->J.fu_v;
   F.spin_limit = h->prm.spin_limit > 0 ? h->prm.spin_limit : 2000000;
+  F.local = h->prm.local_stage;
+  F.gs_sweeps = h->prm.local_sweeps;
   F.test_stall = h->prm.test_stall_wave;
   PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, h->dfs, h->mixed, st));
   if (h->mixed) {
@@ -191,10 +193,10 @@ ps_status build_flow(ps_handle* h) {
   bool sp_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_p, h->grid.nx, h->grid.ny, h->grid.nz, 7, h->mixed, &sp_ok, st));
   if (h->mixed) {
-    PS_TRY(amg_alloc_work<float>(ar, h->amg_p));
+    PS_TRY(amg_alloc_work<float>(ar, h->amg_p, smooth_params(h->prm), st));
     PS_TRY(flow_alloc_work<float>(ar, F, h->w32));
   } else {
-    PS_TRY(amg_alloc_work<double>(ar, h->amg_p));
+    PS_TRY(amg_alloc_work<double>(ar, h->amg_p, smooth_params(h->prm), st));
     PS_TRY(flow_alloc_work<double>(ar, F, h->w64));
   }
   cudaEventRecord(e1, st);
@@ -239,11 +241,11 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   bool su_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
   if (h->mixed) {
-    PS_TRY(amg_alloc_work<float>(ar, h->amg_u));
+    PS_TRY(amg_alloc_work<float>(ar, h->amg_u, smooth_params(h->prm), st));
     PS_TRY(ar.alloc(&h->vu32, h->nu));
     PS_TRY(ar.alloc(&h->zu32, h->nu));
   } else {
-    PS_TRY(amg_alloc_work<double>(ar, h->amg_u));
+    PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
   }
   cudaEventRecord(e1, st);
   PS_CUDA(cudaEventSynchronize(e1));
@@ -309,6 +311,8 @@ void ps_params_default(ps_params* p) {
   p->ilu_mode = PS_ILU_PENCIL;
   p->spin_limit = 2000000;
   p->ortho_sweep = 8;
+  p->local_stage = PS_LOCAL_ILU0;
+  p->local_sweeps = 3;
 }
 
 ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params, ps_handle** out) {
@@ -323,6 +327,11 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   if (params->restart < 1 || params->restart > 120 || params->max_iters < 1) return PS_ERR_INVALID;
   if (params->precision != PS_FP64 && params->precision != PS_MIXED_FP32 && params->precision != PS_MIXED_BF16P)
     return PS_ERR_INVALID;
+  if (params->local_stage != PS_LOCAL_ILU0 && params->local_stage != PS_LOCAL_HBGS) return PS_ERR_INVALID;
+  if (params->local_stage == PS_LOCAL_HBGS && (params->local_sweeps < 1 || params->local_sweeps > 64)) {
+    set_reason("local_sweeps must be 1..64 for the block Gauss-Seidel local stage");
+    return PS_ERR_INVALID;
+  }
   ps_handle* h = new ps_handle();
   h->prm = *params;
   h->grid = *grid;
@@ -539,6 +548,23 @@ ps_status ps_amg_level_info(ps_handle* h, int32_t which, int32_t level, int64_t*
   if (n) *n = A.L[level].n;
   if (nnz) *nnz = A.L[level].nnz;
   if (nagg) *nagg = A.L[level].nagg;
+  return PS_OK;
+}
+
+ps_status ps_amg_level_shape(ps_handle* h, int32_t which, int32_t level, int64_t* shape) {
+  if (!h || !shape) return PS_ERR_INVALID;
+  Amg& A = which == 0 ? h->amg_u : h->amg_p;
+  if (level < 0 || level >= int32_t(A.L.size())) return PS_ERR_INVALID;
+  const AmgLevel& L = A.L[level];
+  const bool st = h->mixed ? L.sv_f != nullptr : L.sv_d != nullptr;
+  shape[0] = L.n;
+  shape[1] = L.nnz;
+  shape[2] = L.coarsest ? 0 : L.nagg;
+  shape[3] = L.coarsest ? 0 : L.pnnz;
+  shape[4] = st ? L.sns : 0;
+  shape[5] = h->mixed ? 4 : 8;
+  shape[6] = h->bf16p && L.pvb ? 2 : (h->mixed ? 4 : 8);
+  shape[7] = L.coarsest ? 1 : 0;
   return PS_OK;
 }
 

@@ -30,6 +30,11 @@ __host__ __device__ inline int64_t sweep_rec(bool fwd, int nx, int ny, int steps
   return ((tile * steps + s) * (kTY * kTZ) + ly + kTY * lz) * kRec;
 }
 
+// Block Gauss-Seidel colour slots: slot p of colour col is the cell (x, y, z) with
+// x = 2 (p % hx) + ((col + y + z) & 1), y = (p / hx) % ny, z = p / (hx ny), hx = ceil(nx / 2); slots with
+// x >= nx (odd nx) are empty.  Face neighbours always have the other colour.
+__host__ __device__ inline int gs_hx(int nx) { return (nx + 1) / 2; }
+
 struct FlowStage {
   int nx = 0, ny = 0, nz = 0;
   int64_t nc = 0, nnzb = 0;
@@ -49,6 +54,14 @@ struct FlowStage {
   // row-major each), zero blocks outside the grid
   double* s28 = nullptr;
   float* s28_f = nullptr;
+  // local stage: PS_LOCAL_ILU0 (the ILU(0) factors, sweep records and halo words below) or PS_LOCAL_HBGS
+  // (block Gauss-Seidel: per colour, the six face blocks and inv(S_ii) of each cell, 28 values, blocked
+  // by 32 cells, [colour][p / 32][28][p % 32] with p the cell's index within its colour; see gs_index)
+  int local = 0;
+  int gs_sweeps = 3;
+  int64_t gs_ncp = 0;  // slots per colour: nz * ny * ceil(nx / 2)
+  float* gs_rec_f = nullptr;
+  double* gs_rec_d = nullptr;
   // records of the sync-free sweeps, kRec values per cell (forward: lower blocks, inv(U_ii), w; backward:
   // upper blocks, inv(U_ii), t, z_s, z_p), in the apply precision, at sweep_rec(...) with
   // pk_steps = sweep_steps(nx, win_cells<T>())

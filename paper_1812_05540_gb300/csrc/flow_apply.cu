@@ -281,6 +281,48 @@ __global__ void k_ff_residual(int nx, int ny, int nz, const T* __restrict__ S28,
   w[2 * i + 1] = w1;
 }
 
+// §5.3 option 1, block Gauss-Seidel on the interleaved S_ff^(FS): one colour of one sweep.  Thread p owns
+// colour slot p (gs_index); the colour's cells share no face, so each is updated from the other colour's
+// newest values: dz_i = inv(S_ii) (w_i - sum_j S_ij dz_j) over the face neighbours j, in slot order
+// (z-1, y-1, x-1, x+1, y+1, z+1).  Blocks of neighbours outside the grid are stored as zero and read dz at
+// the cell itself, so every slot loads without a branch.  ZERO: the first colour of the first sweep (every
+// dz_j is still 0).  LAST: the last sweep also writes z_f + dz_f (FP64) for its cells to zout.
+template <class T, bool ZERO, bool LAST>
+__global__ void k_gs_colour(int nx, int ny, int nz, int col, int64_t ncp, const T* __restrict__ rec,
+                            const T* __restrict__ w, T* __restrict__ dz, const T* __restrict__ zs,
+                            const T* __restrict__ zp, double* __restrict__ zout) {
+  const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= ncp) return;
+  const int hx = gs_hx(nx);
+  const int m = int(p % hx);
+  const int64_t row = p / hx;
+  const int y = int(row % ny), z = int(row / ny);
+  const int x = 2 * m + ((col + y + z) & 1);
+  if (x >= nx) return;
+  const int64_t nxy = int64_t(nx) * ny;
+  const int64_t i = x + nx * int64_t(y) + nxy * z;
+  const T* R = rec + ((int64_t(col) * ((ncp + 31) / 32) + (p >> 5)) * 28) * 32 + (p & 31);
+  T a0 = w[2 * i], a1 = w[2 * i + 1];
+  if (!ZERO) {
+    const int64_t nb[6] = {z > 0 ? i - nxy : i, y > 0 ? i - nx : i, x > 0 ? i - 1 : i,
+                           x + 1 < nx ? i + 1 : i, y + 1 < ny ? i + nx : i, z + 1 < nz ? i + nxy : i};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const T d0 = dz[2 * nb[q]], d1 = dz[2 * nb[q] + 1];
+      a0 -= R[(4 * q) * 32] * d0 + R[(4 * q + 1) * 32] * d1;
+      a1 -= R[(4 * q + 2) * 32] * d0 + R[(4 * q + 3) * 32] * d1;
+    }
+  }
+  const T e0 = R[24 * 32] * a0 + R[25 * 32] * a1;
+  const T e1 = R[26 * 32] * a0 + R[27 * 32] * a1;
+  dz[2 * i] = e0;
+  dz[2 * i + 1] = e1;
+  if (LAST) {
+    zout[2 * i] = double(zs[i] + e0);
+    zout[2 * i + 1] = double(zp[i] + e1);
+  }
+}
+
 // per-cell data of one sweep step: forward (w_i, lower blocks, inv(U_ii)),
 // backward (t_i, upper blocks, inv(U_ii), z_i)
 template <class T>
@@ -629,8 +671,35 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
   return true;
 }
 
+// steps 6-8 with the block Gauss-Seidel local stage: w_f = y_f - S_ff^(FS) z_f, then gs_sweeps sweeps of
+// two colours from dz = 0, the last one adding z_f into zout
+template <class T>
+void gs_local(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStream_t st) {
+  FlowView<T> V = fview<T>(F);
+  const T* rec = sizeof(T) == 4 ? reinterpret_cast<const T*>(F.gs_rec_f) : reinterpret_cast<const T*>(F.gs_rec_d);
+  PS_TICK(); k_ff_residual<T><<<grid_for(F.nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, V.s28, W.y, W.zs, W.zp, W.wf);
+  const unsigned g = grid_for(F.gs_ncp, 256);
+  for (int sw = 0; sw < F.gs_sweeps; ++sw)
+    for (int col = 0; col < 2; ++col) {
+      const bool last = sw == F.gs_sweeps - 1;
+      PS_TICK();
+      if (sw == 0 && col == 0) {
+        if (last) k_gs_colour<T, true, true><<<g, 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.gs_ncp, rec, W.wf, W.dz, W.zs, W.zp, zout);
+        else k_gs_colour<T, true, false><<<g, 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.gs_ncp, rec, W.wf, W.dz, W.zs, W.zp, zout);
+      } else if (last) {
+        k_gs_colour<T, false, true><<<g, 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.gs_ncp, rec, W.wf, W.dz, W.zs, W.zp, zout);
+      } else {
+        k_gs_colour<T, false, false><<<g, 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.gs_ncp, rec, W.wf, W.dz, W.zs, W.zp, zout);
+      }
+    }
+}
+
 template <class T>
 void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int ilu_mode, cudaStream_t st) {
+  if (F.local == PS_LOCAL_HBGS) {
+    gs_local<T>(F, W, zout, st);
+    return;
+  }
   if (ilu_mode == PS_ILU_PENCIL && F.halo && ilu_pencil<T>(F, W, zout, st)) return;
   FlowView<T> V = fview<T>(F);
   for (int l = 0; l < F.nlev; ++l) {

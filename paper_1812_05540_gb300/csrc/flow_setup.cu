@@ -123,6 +123,34 @@ __global__ void k_s28(int nx, int ny, int nz, const int32_t* __restrict__ rp, co
   }
 }
 
+// Block Gauss-Seidel records (§5.3 option 1): per colour slot p, the face blocks of S_ff^(FS) in slot order
+// (z-1, y-1, x-1, x+1, y+1, z+1; zero outside the grid) and inv(S_ii), 28 values, blocked by 32 slots.
+// Empty slots (odd nx) keep zeros.
+template <class T>
+__global__ void k_gs_pack(int nx, int ny, int nz, int col, const double* __restrict__ s28, T* __restrict__ rec) {
+  const int hx = gs_hx(nx);
+  const int64_t ncp = int64_t(nz) * ny * hx;
+  int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= ncp) return;
+  const int m = int(p % hx);
+  const int64_t row = p / hx;
+  const int y = int(row % ny), z = int(row / ny);
+  const int x = 2 * m + ((col + y + z) & 1);
+  T* R = rec + (((int64_t(col) * ((ncp + 31) / 32)) + (p >> 5)) * 28) * 32 + (p & 31);
+  if (x >= nx) {
+    for (int v = 0; v < 28; ++v) R[v * 32] = T(0);
+    return;
+  }
+  const int64_t c = x + int64_t(nx) * (y + int64_t(ny) * z);
+  const double* S = s28 + c * 28;
+  const int slot[6] = {0, 1, 2, 4, 5, 6};
+  for (int q = 0; q < 6; ++q)
+    for (int e = 0; e < 4; ++e) R[(q * 4 + e) * 32] = T(S[slot[q] * 4 + e]);
+  double D[4];
+  inv22(S + 12, D);
+  for (int e = 0; e < 4; ++e) R[(24 + e) * 32] = T(D[e]);
+}
+
 // A_ps by 7-point slot, blocked by 32 cells, from the stencil blocks of S_ff^(FS) (the fixed-stress
 // terms change only the (s, p) and (p, p) entries, so entry (p, s) is A_ps)
 template <class T>
@@ -184,6 +212,8 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TRY(ar.alloc(&F.dinv, nc * 4));
     PS_TRY(ar.alloc(&F.diagpos, nc));
     PS_TRY(ar.alloc(&F.s28, nc * 28));
+    PS_TRY(ar.alloc(&F.ilu_err, 4));  // bounded-wait error flag, read after every iteration in both local modes
+    PS_CUDA(cudaMemsetAsync(F.ilu_err, 0, 4 * sizeof(int), st));
     if (mixed) {
       PS_TRY(ar.alloc(&F.s28_f, nc * 28));
       PS_TRY(ar.alloc(&F.sff_f, nnzb * 4));
@@ -191,6 +221,14 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
       PS_TRY(ar.alloc(&F.dinv_f, nc * 4));
       PS_TRY(ar.alloc(&F.dss_f, nc));
     }
+    if (F.local == PS_LOCAL_HBGS) {
+      F.gs_ncp = int64_t(F.nz) * F.ny * gs_hx(F.nx);
+      const size_t nrec = size_t(2) * ((F.gs_ncp + 31) / 32) * 28 * 32;
+      if (mixed) PS_TRY(ar.alloc(&F.gs_rec_f, nrec));
+      else PS_TRY(ar.alloc(&F.gs_rec_d, nrec));
+    }
+  }
+  if (F.local != PS_LOCAL_HBGS && !F.halo) {
     // wavefront levels
     F.nlev = F.nx + F.ny + F.nz - 2;
     int32_t *cnt, *off, *cursor;
@@ -218,9 +256,7 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
       PS_CUDA(cudaMemsetAsync(F.pk_bwd_d, 0, sizeof(double) * nrec, st));
     }
     PS_TRY(ar.alloc(&F.halo, size_t(nc) * 4));
-    PS_TRY(ar.alloc(&F.ilu_err, 4));
     PS_CUDA(cudaMemsetAsync(F.halo, 0, sizeof(uint64_t) * nc * 4, st));
-    PS_CUDA(cudaMemsetAsync(F.ilu_err, 0, 4 * sizeof(int), st));
     F.lev_off.resize(F.nlev + 1);
     PS_CUDA(cudaMemcpyAsync(F.lev_off.data(), off, sizeof(int32_t) * (F.nlev + 1), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
@@ -228,13 +264,20 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
   }
   PS_TICK(); k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
                                                F.diagpos);
-  for (int l = 0; l < F.nlev; ++l) {
+  for (int l = 0; l < (F.local == PS_LOCAL_HBGS ? 0 : F.nlev); ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
     PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
                                                    F.dinv);
   }
   PS_TICK(); k_s28<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.rp, F.sff, F.s28);
   PS_CUDA(cudaGetLastError());
+  if (F.local == PS_LOCAL_HBGS) {
+    for (int col = 0; col < 2; ++col) {
+      if (mixed) { PS_TICK(); k_gs_pack<float><<<grid_for(F.gs_ncp, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.s28, F.gs_rec_f); }
+      else { PS_TICK(); k_gs_pack<double><<<grid_for(F.gs_ncp, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, col, F.s28, F.gs_rec_d); }
+    }
+    PS_CUDA(cudaGetLastError());
+  }
   if (mixed) {
     PS_TICK(); k_f32<<<grid_for(nc * 28, 256), 256, 0, st>>>(F.s28, F.s28_f, nc * 28);
     PS_TICK(); k_f32<<<grid_for(nnzb * 4, 256), 256, 0, st>>>(F.sff, F.sff_f, nnzb * 4);
@@ -242,13 +285,17 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_TICK(); k_f32<<<grid_for(nc * 4, 256), 256, 0, st>>>(F.dinv, F.dinv_f, nc * 4);
     PS_TICK(); k_f32<<<grid_for(nc, 256), 256, 0, st>>>(F.dss, F.dss_f, nc);
     PS_CUDA(cudaGetLastError());
-    PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28_f, F.dinv_f,
-                                                                  F.pk_fwd_f, F.pk_bwd_f);
+    if (F.pk_fwd_f) {
+      PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28_f, F.dinv_f,
+                                                                    F.pk_fwd_f, F.pk_bwd_f);
+    }
     if (!F.aps_st_f) PS_TRY(ar.alloc(&F.aps_st_f, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.aps_st_f);
   } else {
-    PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28, F.dinv,
-                                                                   F.pk_fwd_d, F.pk_bwd_d);
+    if (F.pk_fwd_d) {
+      PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28, F.dinv,
+                                                                     F.pk_fwd_d, F.pk_bwd_d);
+    }
     if (!F.aps_st_d) PS_TRY(ar.alloc(&F.aps_st_d, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.aps_st_d);
   }

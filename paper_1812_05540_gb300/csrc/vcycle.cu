@@ -109,11 +109,11 @@ struct StencilRows {
   bool active = i < n;
 
 // one Chebyshev step from a nonzero x: r = D^{-1}(b - A x); d = c1 d + c2 r; xo = x + d
-// (first == true: d = r / theta, i.e. c1 = 0, c2 = 1/theta)
+// (first == true: d = r / theta, i.e. c1 = 0, c2 = 1/theta); d is stored when store_d (a later step reads it)
 template <class T, int NC, class A>
 __global__ void k_cheb_step(A a, int64_t n, const T* __restrict__ dg, const T* __restrict__ b,
                             const T* __restrict__ x, T* __restrict__ xo, T* __restrict__ d, double3 c1, double3 c2,
-                            int first) {
+                            int first, int store_d) {
   ROWS_SETUP
   auto xf = [&](int64_t j, int c) { return x[j * NC + c]; };
   T s[NC];
@@ -125,9 +125,41 @@ __global__ void k_cheb_step(A a, int64_t n, const T* __restrict__ dg, const T* _
       T r = (b[i * NC + c] - s[c]) / dg[i * NC + c];
       T dn = first ? T(a2[c]) * r : T(a1[c]) * d[i * NC + c] + T(a2[c]) * r;
       xo[i * NC + c] = x[i * NC + c] + dn;
+      if (store_d) d[i * NC + c] = dn;
+    }
+  }
+}
+
+// The first two Chebyshev steps from x = 0 in one pass.  The first step's iterate x1 = D^{-1} b / theta is
+// formed wherever the row touches it (dsi = D^{-1} / theta), so it is neither stored nor read back; then
+// r = D^{-1}(b - A x1), d = c1 x1 + c2 r (the first direction is x1 itself), xo = x1 + d, and d is stored
+// when later steps need it.
+template <class T, int NC, class A>
+__global__ void k_cheb_zero2(A a, int64_t n, const T* __restrict__ dg, const T* __restrict__ dsi,
+                             const T* __restrict__ b, T* __restrict__ xo, T* __restrict__ d, double3 c1, double3 c2) {
+  ROWS_SETUP
+  auto xf = [&](int64_t j, int c) { return b[j * NC + c] * dsi[j * NC + c]; };
+  T s[NC];
+  a.dot(i, sub, active, xf, s);
+  if (active && sub == 0) {
+    const double a1[3] = {c1.x, c1.y, c1.z}, a2[3] = {c2.x, c2.y, c2.z};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T x1 = b[i * NC + c] * dsi[i * NC + c];
+      const T r = (b[i * NC + c] - s[c]) / dg[i * NC + c];
+      const T dn = T(a1[c]) * x1 + T(a2[c]) * r;
+      xo[i * NC + c] = x1 + dn;
       if (d) d[i * NC + c] = dn;
     }
   }
+}
+
+// dsi = D^{-1} / theta per row and component
+template <class T, int NC>
+__global__ void k_dsi(int64_t n, const T* __restrict__ dg, T* __restrict__ dsi, double3 inv_theta) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
+  if (t < n * NC) dsi[t] = T(it[t % NC]) / dg[t];
 }
 
 // l1-Jacobi: xo = x + (b - A x) / dl1
@@ -291,13 +323,26 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
   if (sp.kind == PS_SMOOTH_CHEBYSHEV) {
     ChebCoef cc = cheb_coef(L, NC, sp);
     int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
-    PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, deg > 1 ? d : nullptr,
-                                                                        cc.inv_theta);
-    for (int k = 1; k < deg; ++k) {
+    int k0 = 1;
+    if (deg > 1 && L.dsi) {
+      // steps 0 and 1 in one pass
+      with_rows<T, NC>(L, V, [&](auto a) {
+        using A = decltype(a);
+        PS_TICK(); k_cheb_zero2<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, static_cast<const T*>(L.dsi),
+                                                                            b, x, deg > 2 ? d : nullptr, cc.c1[1],
+                                                                            cc.c2[1]);
+      });
+      k0 = 2;
+    } else {
+      PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, deg > 1 ? d : nullptr,
+                                                                          cc.inv_theta);
+    }
+    for (int k = k0; k < deg; ++k) {
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
         PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, other,
-                                                                           d, cc.c1[k], cc.c2[k], 0);
+                                                                           d, cc.c1[k], cc.c2[k], 0,
+                                                                           k < deg - 1);
       });
       std::swap(cur, other);
     }
@@ -327,12 +372,11 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
         if (k == 0) {
-          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst,
-                                                                             deg > 1 ? d : nullptr, cc.c1[0],
-                                                                             cc.post_c2, 1);
+          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst, d, cc.c1[0],
+                                                                             cc.post_c2, 1, deg > 1);
         } else {
           PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst, d, cc.c1[k],
-                                                                             cc.c2[k], 0);
+                                                                             cc.c2[k], 0, k < deg - 1);
         }
       });
       other = cur;
@@ -401,14 +445,24 @@ void vcycle_launch(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_
 }  // namespace
 
 template <class T>
-ps_status amg_alloc_work(Arena& ar, Amg& H) {
+ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st) {
   for (auto& L : H.L) {
     size_t m = size_t(L.n) * H.nc + 1;
     T *x, *t, *r, *d, *b, *e;
     PS_TRY(ar.alloc(&x, m)); PS_TRY(ar.alloc(&t, m)); PS_TRY(ar.alloc(&r, m)); PS_TRY(ar.alloc(&d, m));
     PS_TRY(ar.alloc(&b, m)); PS_TRY(ar.alloc(&e, m));
     L.x = x; L.t = t; L.r = r; L.d = d; L.b = b; L.e = e;
+    if (sp.kind == PS_SMOOTH_CHEBYSHEV && sp.degree > 1 && !L.coarsest) {
+      T* dsi;
+      PS_TRY(ar.alloc(&dsi, m));
+      ChebCoef cc = cheb_coef(L, H.nc, sp);
+      const T* dg = view<T>(L).dg;
+      if (H.nc == 3) { PS_TICK(); k_dsi<T, 3><<<grid_for(L.n * 3, 256), 256, 0, st>>>(L.n, dg, dsi, cc.inv_theta); }
+      else { PS_TICK(); k_dsi<T, 1><<<grid_for(L.n, 256), 256, 0, st>>>(L.n, dg, dsi, cc.inv_theta); }
+      L.dsi = dsi;
+    }
   }
+  PS_CUDA(cudaGetLastError());
   return PS_OK;
 }
 
@@ -463,8 +517,8 @@ ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStrea
   return PS_OK;
 }
 
-template ps_status amg_alloc_work<float>(Arena&, Amg&);
-template ps_status amg_alloc_work<double>(Arena&, Amg&);
+template ps_status amg_alloc_work<float>(Arena&, Amg&, const SmoothParams&, cudaStream_t);
+template ps_status amg_alloc_work<double>(Arena&, Amg&, const SmoothParams&, cudaStream_t);
 template ps_status amg_vcycle<float>(Amg&, const SmoothParams&, const float*, float*, cudaStream_t);
 template ps_status amg_vcycle<double>(Amg&, const SmoothParams&, const double*, double*, cudaStream_t);
 

@@ -71,3 +71,28 @@ def test_traffic_records_are_dropped_once_the_source_changes(tmp_path, monkeypat
     assert bench.traffic_per_launch(t, "spmv", n, None) is None
     src.write_text("__global__ void k() { }\n")
     assert bench.load_traffic() == {}
+
+
+def test_vcycle_bytes_two_level_hand_count():
+    # level 0: 10 rows, CSR with 28 entries, nc = 1, FP32 values; P has 12 entries onto 3 coarse rows;
+    # level 1 (coarsest): 3 rows, dense FP64 inverse
+    L0 = (10, 28, 3, 12, 0, 4, 4, 0)
+    L1 = (3, 9, 0, 0, 0, 4, 4, 1)
+    vec0, vec1 = 10 * 4, 3 * 4
+    op = 28 * (4 + 4) + 4 * 11                     # values + column indices + row pointers, per pass
+    # 4 operator passes; vectors: fused first two pre steps 4 (b, D^{-1}/theta, D in; x out), residual 3,
+    # first post step 5 (x, b, D in; x, d out), second post step 5 (x, b, D, d in; x out)
+    level0 = 4 * op + 17 * vec0
+    level0 += 12 * 8 + 4 * 11 + vec1 + 2 * vec0    # x += P e
+    level0 += 12 * 8 + 4 * 4 + vec0 + vec1         # b_c = R r
+    level1 = 3 * 3 * 8 + 2 * vec1                  # dense inverse + b, x
+    assert bench.vcycle_bytes([L0, L1], 1) == level0 + level1
+
+
+def test_vcycle_bytes_stencil_level_has_no_indices():
+    # a 7-point stencil level reads 7 values per row and no column index or row pointer per pass
+    L0 = (100, 500, 10, 300, 7, 4, 4, 0)
+    L0_csr = (100, 500, 10, 300, 0, 4, 4, 0)
+    L1 = (10, 30, 0, 0, 0, 4, 4, 1)
+    d = bench.vcycle_bytes([L0_csr, L1], 1) - bench.vcycle_bytes([L0, L1], 1)
+    assert d == 4 * ((500 * 8 + 4 * 101) - 7 * 4 * 100)

@@ -55,7 +55,7 @@ def test_residual_noalloc_rejects_oversized_systems():
     blk = lambda r, c, br, bc: ps.ps_bsr(r, c, 0, br, bc, 1, 1, 1)
     jac = ps.ps_jacobian(blk(nn, nn, 3, 3), blk(nn, nc, 3, 2), blk(nc, nn, 2, 3), blk(nc, nc, 2, 2), 1, None)
     with pytest.raises(ps.PsError) as e:
-        ps.ps_residual_noalloc(jac, grid, 1, 1, 1, 1)
+        ps.ps_residual_noalloc(jac, grid, 8, 16, 24, 32)
     assert e.value.status == ps.PS_ERR_INVALID and "scratch" in str(e.value)
 
 
