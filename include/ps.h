@@ -56,6 +56,13 @@ enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
 /* local stage M_L of §5.3: option 2, one sweep of block ILU(0) (default); option 1, local_sweeps sweeps of
    block Gauss-Seidel on the interleaved S_ff^(FS), cells taken in red-black order */
 enum { PS_LOCAL_ILU0 = 0, PS_LOCAL_HBGS = 1 };
+/* CPR pressure reduction of §5.3: quasi-IMPES (diagonal entries of A_ss, A_ps; default) or true-IMPES
+   (column sums of A_ss, A_ps) */
+enum { PS_CPR_QUASI_IMPES = 0, PS_CPR_TRUE_IMPES = 1 };
+/* outer iteration: flexible GMRES (default), or the sequential fixed-stress strategy of the §5.4 remark,
+   the preconditioner inside a Richardson iteration x <- x + M^{-1}(b - A x) (one mechanics-then-flow pass
+   per iteration; max_iters bounds the passes) */
+enum { PS_SOLVER_FGMRES = 0, PS_SOLVER_RICHARDSON = 1 };
 enum { PS_ORTHO_MGS = 0, PS_ORTHO_CGS2 = 1 };    /* Arnoldi orthogonalisation */
 
 /* Cartesian box of nx*ny*nz cubic cells (§6 grids); hx = hy = hz. */
@@ -118,6 +125,8 @@ typedef struct {
                                  sweeps need fewer grid barriers */
   int32_t local_stage;        /* PS_LOCAL_ILU0 (default) or PS_LOCAL_HBGS (§5.3 option 1) */
   int32_t local_sweeps;       /* PS_LOCAL_HBGS: block Gauss-Seidel sweeps (default 3, as in §6.1) */
+  int32_t cpr_reduction;      /* PS_CPR_QUASI_IMPES (default) or PS_CPR_TRUE_IMPES */
+  int32_t solver;             /* PS_SOLVER_FGMRES (default) or PS_SOLVER_RICHARDSON */
 } ps_params;
 
 typedef struct {

@@ -28,6 +28,7 @@ MECH_AMG, MECH_EXACT = 0, 1
 FLOW_CPR, FLOW_EXACT_FS, FLOW_EXACT_SCHUR = 0, 1, 2
 LOCAL_ILU0, LOCAL_EXACT, LOCAL_GS = 0, 1, 2
 PRESS_AMG, PRESS_EXACT = 0, 1
+CPR_QUASI_IMPES, CPR_TRUE_IMPES = 0, 1
 
 
 def build(force=False, openmp=False):
@@ -84,7 +85,7 @@ class PrecParams(C.Structure):
                 ("post", C.c_int32), ("smoother", C.c_int32), ("cheb_degree", C.c_int32),
                 ("cheb_ratio", C.c_double), ("mech_mode", C.c_int32), ("flow_mode", C.c_int32),
                 ("local_mode", C.c_int32), ("press_mode", C.c_int32), ("full_exact", C.c_int32),
-                ("local_sweeps", C.c_int32)]
+                ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -147,6 +148,8 @@ def lib(openmp=None):
         L.or_gs_apply.argtypes = [C.c_void_p, _PD, _PD, C.c_int]
         L.or_fgmres.argtypes = [C.POINTER(_System), C.c_void_p, _PD, _PD, C.c_double, C.c_int, C.c_int,
                                 C.POINTER(Stats)]
+        L.or_richardson.argtypes = [C.POINTER(_System), C.c_void_p, _PD, _PD, C.c_double, C.c_int,
+                                    C.POINTER(Stats)]
         L.or_fgmres_diag.argtypes = [C.c_int64, _PD, _PD, _PD, C.c_double, C.c_int, C.c_int, C.POINTER(Stats)]
         L.or_dense_solve.argtypes = [C.POINTER(_System), _PD, _PD]
         L.or_lu_solve.argtypes = [C.c_int64, _PD, _PD, _PD]
@@ -336,6 +339,14 @@ class Prec:
         dz = np.empty_like(w)
         self._L.or_ilu_apply(self._h, _d(w), _d(dz))
         return dz
+
+    def richardson(self, b=None, tol=1e-8, max_iters=1000):
+        s = self.system
+        b = s.rhs if b is None else np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty(s.n)
+        st = Stats()
+        self._L.or_richardson(s._ptr, self._h, _d(b), _d(x), tol, max_iters, C.byref(st))
+        return x, st
 
     def gs_apply(self, w, sweeps):
         w = np.ascontiguousarray(w, dtype=np.float64)

@@ -1565,13 +1565,24 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
     P->Sff.v[q * 4 + 1] = P->Sff.v[q * 4 + 1] + s->d_fs[2 * c];
     P->Sff.v[q * 4 + 3] = P->Sff.v[q * 4 + 3] + s->d_fs[2 * c + 1];
   }
-  // §5.3 quasi-IMPES: D_ss = diagm(A_ss), D_ps = diagm(A_ps);
+  // §5.3 quasi-IMPES: D_ss = diagm(A_ss), D_ps = diagm(A_ps); or true-IMPES: D_ss = diag(A_ss^T e),
+  // D_ps = diag(A_ps^T e), column sums taken over the rows in ascending order;
   // S_pp = A_pp^(FS) - D_ps D_ss^{-1} A_sp^(FS)
   P->dss.resize(nc); P->dps.resize(nc);
-  for (int64_t c = 0; c < nc; ++c) {
-    int64_t q = P->A_ff.find(c, c);
-    P->dss[c] = P->A_ff.v[q * 4 + 0];
-    P->dps[c] = P->A_ff.v[q * 4 + 2];
+  if (pp->cpr_reduction == OR_CPR_TRUE_IMPES) {
+    for (int64_t c = 0; c < nc; ++c) { P->dss[c] = 0.0; P->dps[c] = 0.0; }
+    for (int64_t r = 0; r < nc; ++r)
+      for (int64_t q = P->A_ff.rp[r]; q < P->A_ff.rp[r + 1]; ++q) {
+        int64_t c = P->A_ff.ci[q];
+        P->dss[c] = P->dss[c] + P->A_ff.v[q * 4 + 0];
+        P->dps[c] = P->dps[c] + P->A_ff.v[q * 4 + 2];
+      }
+  } else {
+    for (int64_t c = 0; c < nc; ++c) {
+      int64_t q = P->A_ff.find(c, c);
+      P->dss[c] = P->A_ff.v[q * 4 + 0];
+      P->dps[c] = P->A_ff.v[q * 4 + 2];
+    }
   }
   P->spp.n = P->spp.m = nc; P->spp.nc = 1;
   P->spp.rp = P->Sff.rp; P->spp.ci = P->Sff.ci;
@@ -1897,6 +1908,34 @@ int or_fgmres(const or_system* s, or_prec* p, const double* b, double* x, double
   Op M = [p](const double* in, double* out) { or_prec_apply(p, in, out); };
   fgmres(s->n, A, M, b, x, tol, restart, max_iters, st);
   return st->converged ? 0 : 4;
+}
+
+// Sequential fixed-stress strategy of the §5.4 remark: the preconditioner inside a Richardson iteration,
+// x_{k+1} = x_k + M^{-1} (b - A x_k), x_0 = 0.  Step 1 of Algorithm 1 corrects the displacements, steps 2-8
+// then correct the flow unknowns, so each iteration is one mechanics-then-flow pass.
+int or_richardson(const or_system* s, or_prec* p, const double* b, double* x, double tol, int max_iters,
+                  or_stats* st) {
+  std::memset(st, 0, sizeof(*st));
+  const int64_t n = s->n;
+  const double bn = std::sqrt(dot(b, b, n));
+  vec r(n), z(n), Ax(n);
+  for (int64_t e = 0; e < n; ++e) x[e] = 0.0;
+  if (bn == 0.0) { st->converged = 1; return 0; }
+  for (;;) {
+    or_spmv(s, x, Ax.data());
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) r[e] = b[e] - Ax[e];
+    const double rr = std::sqrt(dot(r.data(), r.data(), n)) / bn;
+    st->true_relres = rr;
+    st->est_relres = rr;
+    if (std::isnan(rr)) return 0;
+    if (rr <= tol) { st->converged = 1; return 0; }
+    if (st->iters >= max_iters) return 0;
+    or_prec_apply(p, r.data(), z.data());
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n; ++e) x[e] = x[e] + z[e];
+    st->iters++;
+  }
 }
 
 int or_fgmres_diag(int64_t n, const double* diag, const double* b, double* x, double tol, int restart,

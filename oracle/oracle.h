@@ -112,6 +112,7 @@ enum { OR_MECH_AMG = 0, OR_MECH_EXACT = 1 };                 /* M_uu */
 enum { OR_FLOW_CPR = 0, OR_FLOW_EXACT_FS = 1, OR_FLOW_EXACT_SCHUR = 2 }; /* M_ff */
 enum { OR_LOCAL_ILU0 = 0, OR_LOCAL_EXACT = 1, OR_LOCAL_GS = 2 }; /* M_L: ILU(0), exact, block Gauss-Seidel */
 enum { OR_PRESS_AMG = 0, OR_PRESS_EXACT = 1 };                /* M_pp */
+enum { OR_CPR_QUASI_IMPES = 0, OR_CPR_TRUE_IMPES = 1 };        /* D_ss, D_ps of the CPR reduction */
 
 typedef struct {
   double theta_u, theta_p;
@@ -124,6 +125,7 @@ typedef struct {
   int32_t mech_mode, flow_mode, local_mode, press_mode;
   int32_t full_exact; /* M^{-1} = A^{-1} (dense, tiny systems only) */
   int32_t local_sweeps; /* OR_LOCAL_GS: block Gauss-Seidel sweeps (3 in §6.1) */
+  int32_t cpr_reduction; /* OR_CPR_QUASI_IMPES (diagonal entries) or OR_CPR_TRUE_IMPES (column sums), §5.3 */
 } or_prec_params;
 
 typedef struct or_prec or_prec;
@@ -175,6 +177,10 @@ typedef struct {
 /* FGMRES(m) with right preconditioning (§4), x0 = 0 */
 int or_fgmres(const or_system* s, or_prec* p, const double* b, double* x, double tol,
               int restart, int max_iters, or_stats* st);
+/* sequential fixed-stress strategy (§5.4 remark): Richardson iteration x <- x + M^{-1}(b - A x) from x0 = 0
+   until ||b - A x|| <= tol ||b|| or max_iters applications of M^{-1} */
+int or_richardson(const or_system* s, or_prec* p, const double* b, double* x, double tol, int max_iters,
+                  or_stats* st);
 /* the same Krylov loop on a diagonal operator with identity preconditioner */
 int or_fgmres_diag(int64_t n, const double* diag, const double* b, double* x, double tol,
                    int restart, int max_iters, or_stats* st);

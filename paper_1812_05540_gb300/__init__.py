@@ -19,6 +19,9 @@ PS_FP64, PS_MIXED_FP32, PS_MIXED_BF16P = 0, 1, 2
 PS_SMOOTH_L1JACOBI, PS_SMOOTH_CHEBYSHEV = 0, 1
 PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
 PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1
+PS_LOCAL_ILU0, PS_LOCAL_HBGS = 0, 1
+PS_CPR_QUASI_IMPES, PS_CPR_TRUE_IMPES = 0, 1
+PS_SOLVER_FGMRES, PS_SOLVER_RICHARDSON = 0, 1
 PS_FIELDS_LOGNORMAL, PS_FIELDS_LAYERED, PS_FIELDS_CHANNELS, PS_FIELDS_HOMOGENEOUS = range(4)
 PS_GEN_GRAVITY, PS_GEN_DIRICHLET, PS_GEN_SCALE, PS_GEN_ACCUM, PS_GEN_FLUX, PS_GEN_FLUX_SAT, PS_GEN_COUPLING = \
     (1 << i for i in range(7))
@@ -48,7 +51,8 @@ class ps_params(C.Structure):
                 ("ilu_mode", C.c_int32), ("spin_limit", C.c_int64), ("host_ptrs", C.c_int32),
                 ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
                 ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
-                ("local_stage", C.c_int32), ("local_sweeps", C.c_int32)]
+                ("local_stage", C.c_int32), ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
+                ("solver", C.c_int32)]
 
 
 class ps_stats(C.Structure):

@@ -163,6 +163,7 @@ ps_status build_flow(ps_handle* h) {
   F.fu_rp = h->J.fu_rp; F.fu_ci = h->J.fu_ci; F.fu_v = h->J.fu_v;
   F.spin_limit = h->prm.spin_limit > 0 ? h->prm.spin_limit : 2000000;
   F.local = h->prm.local_stage;
+  F.cpr = h->prm.cpr_reduction;
   F.gs_sweeps = h->prm.local_sweeps;
   F.test_stall = h->prm.test_stall_wave;
   PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, h->dfs, h->mixed, st));
@@ -328,6 +329,9 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   if (params->precision != PS_FP64 && params->precision != PS_MIXED_FP32 && params->precision != PS_MIXED_BF16P)
     return PS_ERR_INVALID;
   if (params->local_stage != PS_LOCAL_ILU0 && params->local_stage != PS_LOCAL_HBGS) return PS_ERR_INVALID;
+  if (params->cpr_reduction != PS_CPR_QUASI_IMPES && params->cpr_reduction != PS_CPR_TRUE_IMPES)
+    return PS_ERR_INVALID;
+  if (params->solver != PS_SOLVER_FGMRES && params->solver != PS_SOLVER_RICHARDSON) return PS_ERR_INVALID;
   if (params->local_stage == PS_LOCAL_HBGS && (params->local_sweeps < 1 || params->local_sweeps > 64)) {
     set_reason("local_sweeps must be 1..64 for the block Gauss-Seidel local stage");
     return PS_ERR_INVALID;
@@ -401,8 +405,91 @@ ps_status ps_apply_prec(ps_handle* h, const double* v, double* z) {
   return PS_OK;
 }
 
+namespace {
+
+// Sequential fixed-stress strategy (§5.4 remark): x_{k+1} = x_k + M^{-1}(b - A x_k) from x_0 = 0, with the
+// true FP64 residual checked before every pass.  Work vectors: r (residual), Z's first column (M^{-1} r).
+ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* stats) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  KrylovState& K = h->K;
+  const bool host = h->prm.host_ptrs != 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  double* xk = h->x;
+  double* z = h->Z;
+  fill_zero(xk, n, st);
+  const double one = 1.0;
+  PS_CUDA(cudaMemcpyAsync(K.y, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  multidot(h->V, n, 0, h->b, n, h->mpart, K.sc + 7, 1, nullptr, st);
+  PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  const double bn2 = h->hsc[7];
+  ps_stats S;
+  std::memset(&S, 0, sizeof(S));
+  ps_status result = PS_OK;
+  if (std::isnan(bn2)) {
+    result = PS_ERR_NAN;
+  } else if (bn2 > 0.0) {
+    const double bnorm = std::sqrt(bn2);
+    for (;;) {
+      jac_spmv(h->J, xk, h->r, h->b, h->part, st);
+      finish_sum(h->part, K.sc + 3, st);
+      PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PS_CUDA(cudaMemcpyAsync(h->hflag + 3, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      PS_CUDA(cudaStreamSynchronize(st));
+      if (h->hflag[3]) {
+        PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
+        set_reason("a bounded wait of the wavefront ILU(0) sweep gave up");
+        result = PS_ERR_TIMEOUT;
+        break;
+      }
+      const double rr = std::sqrt(h->hsc[3]) / bnorm;
+      S.true_relres = rr;
+      S.est_relres = rr;
+      if (std::isnan(rr)) { result = PS_ERR_NAN; break; }
+      if (rr <= tol) break;
+      if (S.iters >= h->prm.max_iters) { result = PS_ERR_NOT_CONVERGED; break; }
+      cudaEventRecord(h->ev[0], st);
+      PS_TRY(apply_prec(h, h->r, z));
+      cudaEventRecord(h->ev[1], st);
+      maxpy(z, n, 1, K.y, xk, n, st);
+      S.iters++;
+      {
+        // phase times of the previous pass (its events completed with the synchronisation above)
+        float a = 0;
+        PS_CUDA(cudaEventSynchronize(h->ev[1]));
+        cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+        S.ms_prec += a;
+        float f[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&f[q], h->fe[q], h->fe[q + 1]);
+        S.ms_vcycle_u += f[0]; S.ms_flow24 += f[1]; S.ms_vcycle_p += f[2]; S.ms_ilu += f[3];
+      }
+    }
+  }
+  PS_CUDA(cudaMemcpyAsync(x, xk, sizeof(double) * n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  cudaEventRecord(e1, st);
+  PS_CUDA(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&S.ms_solve, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.ms_setup_u = h->ms_setup_u;
+  S.ms_setup_f = h->ms_setup_f;
+  S.handle_bytes = h->ar.bytes + h->arf.bytes;
+  S.levels_u = int32_t(h->amg_u.L.size());
+  S.levels_p = int32_t(h->amg_p.L.size());
+  if (stats) *stats = S;
+  return result;
+}
+
+}  // namespace
+
 ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* stats) {
   if (!h || !rhs || !x || !(tol > 0.0)) return PS_ERR_INVALID;
+  if (h->prm.solver == PS_SOLVER_RICHARDSON) return solve_richardson(h, rhs, x, tol, stats);
   cudaStream_t st = h->st;
   int64_t n = h->n;
   int m = h->m;

@@ -58,6 +58,7 @@ struct FlowStage {
   // (block Gauss-Seidel: per colour, the six face blocks and inv(S_ii) of each cell, 28 values, blocked
   // by 32 cells, [colour][p / 32][28][p % 32] with p the cell's index within its colour; see gs_index)
   int local = 0;
+  int cpr = 0;  // PS_CPR_QUASI_IMPES or PS_CPR_TRUE_IMPES
   int gs_sweeps = 3;
   int64_t gs_ncp = 0;  // slots per colour: nz * ny * ceil(nx / 2)
   float* gs_rec_f = nullptr;

@@ -39,17 +39,30 @@ __global__ void k_check7(int nx, int ny, int nz, const int32_t* __restrict__ rp,
 }
 
 // S_ff^(FS) = A_ff + [[0 D_sp] [0 D_pp]] on the diagonal (§5.1);
-// quasi-IMPES: d_ss = (A_ss)_ii, d_ps = (A_ps)_ii, S_pp = A_pp^(FS) - (d_ps/d_ss) A_sp^(FS) (§5.3)
+// quasi-IMPES: d_ss = (A_ss)_ii, d_ps = (A_ps)_ii; true-IMPES: d_ss = (A_ss^T e)_i, d_ps = (A_ps^T e)_i, the
+// column sums taken over the rows in ascending order (the 7-point pattern is structurally symmetric, so
+// the rows of column c are the columns of row c); S_pp = A_pp^(FS) - (d_ps/d_ss) A_sp^(FS) (§5.3)
 __global__ void k_sff_spp(int64_t nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const double* __restrict__ aff, const double* __restrict__ dfs, double* __restrict__ sff,
                           double* __restrict__ spp, double* __restrict__ dss, double* __restrict__ dps,
-                          double* __restrict__ aps, int32_t* __restrict__ diagpos) {
+                          double* __restrict__ aps, int32_t* __restrict__ diagpos, int true_impes) {
   int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   int32_t qd = rp[c];
   while (ci[qd] != c) ++qd;
   diagpos[c] = qd;
   double s = aff[int64_t(qd) * 4 + 0], ps = aff[int64_t(qd) * 4 + 2];
+  if (true_impes) {
+    s = 0.0;
+    ps = 0.0;
+    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) {
+      const int32_t r = ci[q];
+      int32_t qr = rp[r];
+      while (ci[qr] != c) ++qr;
+      s = s + aff[int64_t(qr) * 4 + 0];
+      ps = ps + aff[int64_t(qr) * 4 + 2];
+    }
+  }
   dss[c] = s;
   dps[c] = ps;
   double ratio = ps / s;
@@ -263,7 +276,7 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     ar.release(cnt); ar.release(off); ar.release(cursor);
   }
   PS_TICK(); k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
-                                               F.diagpos);
+                                               F.diagpos, F.cpr == PS_CPR_TRUE_IMPES);
   for (int l = 0; l < (F.local == PS_LOCAL_HBGS ? 0 : F.nlev); ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
     PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,

@@ -1,0 +1,102 @@
+"""The paper's reduction and solver-strategy variants on the GPU against the oracle (needs a GB300):
+
+  * true-IMPES reduction (§5.3, column-sum lumping of A_ss and A_ps): S_pp and both hierarchies bit-exact,
+    Algorithm 1 in FP64 within 1e-10, FGMRES with the benchmark spec's tolerances;
+  * sequential fixed-stress strategy (§5.4 remark, the preconditioner inside a Richardson iteration): the
+    same pass count as the oracle's Richardson iteration within 10 %, true relres <= 1e-8 and the oracle's
+    solution within 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1812_05540_gb300 as ps
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    ps.lib()
+
+
+def _g():
+    from tests import _gpu as g
+    return g
+
+
+@pytest.mark.parametrize("cfg,kw,cm", [(0, {}, 16), (1, dict(nx=24, ny=20, nz=10), 60),
+                                       (2, dict(nx=21, ny=44, nz=17), 500)])
+def test_true_impes_hierarchy_and_apply(cfg, kw, cm):
+    g = _g()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm,
+                                                     cpr_reduction=oracle.CPR_TRUE_IMPES))
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm,
+                                                             cpr_reduction=ps.PS_CPR_TRUE_IMPES))
+    try:
+        rp, ci, spp_o = P.spp()
+        spp, _ = ps.ps_flow_copy(h, len(ci), osys.n_cells)
+        assert np.array_equal(spp, spp_o)
+        nl = P.nlevels(1)
+        assert ps.ps_amg_nlevels(h, 1) == nl
+        for l in range(nl):
+            orp, oci, ov = P.level(1, l)
+            rp_, ci_, v_, agg = ps.ps_amg_level_copy(h, 1, l)
+            assert np.array_equal(ci_, oci) and np.array_equal(v_, ov), l
+        vs = np.random.default_rng(4).standard_normal(osys.n)
+        v = torch.from_numpy(vs).cuda()
+        z = torch.empty_like(v)
+        ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+        zo = P.apply(vs)
+        assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+    finally:
+        ps.ps_free(h)
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+def test_true_impes_solve(prec):
+    g = _g()
+    osys = oracle.System(oracle.default_params(2, nx=21, ny=44, nz=17))
+    P = oracle.Prec(osys, oracle.default_prec_params(cpr_reduction=oracle.CPR_TRUE_IMPES))
+    xo, _ = P.fgmres(tol=1e-12)
+    _, sto8 = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, cpr_reduction=ps.PS_CPR_TRUE_IMPES))
+    try:
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(osys.rhs - osys.spmv(xs)) <= 1e-8 * np.linalg.norm(osys.rhs)
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - sto8.iters) <= max(1, int(0.1 * sto8.iters) + 1), (st.iters, sto8.iters)
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+@pytest.mark.parametrize("cfg,kw", [(0, {}), (1, dict(nx=24, ny=20, nz=10))])
+def test_richardson_matches_oracle(cfg, kw, prec):
+    g = _g()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys)
+    xr, stor = P.richardson(tol=1e-8, max_iters=2000)
+    xo, _ = P.fgmres(tol=1e-12)
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, solver=ps.PS_SOLVER_RICHARDSON,
+                                                             max_iters=2000))
+    try:
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    relres = np.linalg.norm(osys.rhs - osys.spmv(xs)) / np.linalg.norm(osys.rhs)
+    assert relres <= 1e-8 and abs(relres - st.true_relres) <= 1e-10
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - stor.iters) <= max(1, int(0.1 * stor.iters)), (st.iters, stor.iters)
