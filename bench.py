@@ -384,7 +384,36 @@ def run_ours(args):
         # the true-IMPES pressure reduction of §5.3 in place of quasi-IMPES
         t_ti, st_ti = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
                                                                cpr_reduction=ps.PS_CPR_TRUE_IMPES)[:2]
+        # the row-sum-lumped (algebraic) fixed-stress diagonal of the §5.1 remark
+        t_rs, st_rs = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
+                                                               fs_mode=ps.PS_FS_RSL)[:2]
         # the sequential fixed-stress strategy of the §5.4 remark (Richardson on M^{-1}), one step
+        # the uniaxial fixed-stress modulus of the §5.1 remark (the generator's d_fs with K_dr + 4G/3)
+        uni = None
+        if not args.no_fp64:
+            gpu_ = ps.ps_gen_default(args.config, fs_modulus=1)
+            sys_u = ps.ps_generate(gpu_, sptr)
+            su = sys_u.contents
+            xu = torch.zeros(n, dtype=torch.float64, device="cuda")
+            stu = []
+            torch.cuda.synchronize()
+            eu0 = torch.cuda.Event(enable_timing=True)
+            eu1 = torch.cuda.Event(enable_timing=True)
+            eu0.record(stream)
+            for _ in range(args.steps):
+                hu = ps.ps_setup(su.jac, su.grid, ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr))
+                try:
+                    stu.append(ps.ps_solve(hu, su.rhs, xu.data_ptr(), TOL)[1])
+                finally:
+                    ps.ps_free(hu)
+            eu1.record(stream)
+            torch.cuda.synchronize()
+            uni = {"value": eu0.elapsed_time(eu1) / 1000.0 / args.steps / world, "iters": [t.iters for t in stu],
+                   "solve_ms": [round(t.ms_solve, 2) for t in stu],
+                   "note": "fixed-stress diagonal with the uniaxial modulus K_dr + 4G/3 (paper §5.1 remark on "
+                           "one-dimensional loading) in place of K_dr"}
+            ps.ps_system_free(sys_u)
+            del xu
         t_ri, st_ri, ri_err = None, None, None
         if not args.no_fp64:
             try:
@@ -581,6 +610,13 @@ def run_ours(args):
             "value": t_ti / args.steps / world, "iters": [st.iters for st in st_ti],
             "solve_ms": [round(st.ms_solve, 2) for st in st_ti],
             "note": "true-IMPES reduction (column sums of A_ss, A_ps; paper §5.3) in place of quasi-IMPES"},
+        "fs_uniaxial_modulus": uni,
+        "fs_row_sum_lumping": None if st_rs is None else {
+            "value": t_rs / args.steps / world, "iters": [st.iters for st in st_rs],
+            "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_rs],
+            "solve_ms": [round(st.ms_solve, 2) for st in st_rs],
+            "note": "fixed-stress diagonal by row-sum lumping, -diag(A_fu M_uu^{-1} A_up e) with one FP64 "
+                    "mechanics V-cycle (paper §5.1 remark), in place of the K_dr-based d_fs"},
         "sequential_fixed_stress": {"error": ri_err} if st_ri is None and ri_err else None if st_ri is None else {
             "value": t_ri / world, "passes": st_ri[-1].iters, "true_relres": st_ri[-1].true_relres,
             "solve_ms": round(st_ri[-1].ms_solve, 2),

@@ -63,6 +63,10 @@ enum { PS_CPR_QUASI_IMPES = 0, PS_CPR_TRUE_IMPES = 1 };
    the preconditioner inside a Richardson iteration x <- x + M^{-1}(b - A x) (one mechanics-then-flow pass
    per iteration; max_iters bounds the passes) */
 enum { PS_SOLVER_FGMRES = 0, PS_SOLVER_RICHARDSON = 1 };
+/* fixed-stress diagonal (D_sp, D_pp) added to A_ff: the caller's d_fs (default), or the row-sum lumping of
+   the §5.1 remark, -diag(A_su w) and -diag(A_pu w) with w = M_uu^{-1} (A_up e) (one FP64 mechanics
+   V-cycle per displacement component; d_fs is then ignored) */
+enum { PS_FS_GIVEN = 0, PS_FS_RSL = 1 };
 enum { PS_ORTHO_MGS = 0, PS_ORTHO_CGS2 = 1 };    /* Arnoldi orthogonalisation */
 
 /* Cartesian box of nx*ny*nz cubic cells (§6 grids); hx = hy = hz. */
@@ -127,6 +131,7 @@ typedef struct {
   int32_t local_sweeps;       /* PS_LOCAL_HBGS: block Gauss-Seidel sweeps (default 3, as in §6.1) */
   int32_t cpr_reduction;      /* PS_CPR_QUASI_IMPES (default) or PS_CPR_TRUE_IMPES */
   int32_t solver;             /* PS_SOLVER_FGMRES (default) or PS_SOLVER_RICHARDSON */
+  int32_t fs_mode;            /* PS_FS_GIVEN (default) or PS_FS_RSL */
 } ps_params;
 
 typedef struct {
@@ -289,6 +294,8 @@ typedef struct {
   uint32_t flags;
   double dt, biot, c_w, c_nw, c_r, mu_w, mu_nw, rho_w0, rho_nw0, rho_s0, s_wr, s_nwr, grav, p_ref, dp_amp, corey;
   double E0, nu0, kappa0, phi0, sw0;
+  int32_t fs_modulus;  /* fixed-stress diagonal of §5.1 with the drained bulk modulus K_dr (0, default) or
+                          the uniaxial modulus K_dr + 4G/3 (1; the §5.1 remark on one-dimensional loading) */
 } ps_gen_params;
 
 /* A generated system: every pointer is device memory owned by the library. */

@@ -29,6 +29,7 @@ FLOW_CPR, FLOW_EXACT_FS, FLOW_EXACT_SCHUR = 0, 1, 2
 LOCAL_ILU0, LOCAL_EXACT, LOCAL_GS = 0, 1, 2
 PRESS_AMG, PRESS_EXACT = 0, 1
 CPR_QUASI_IMPES, CPR_TRUE_IMPES = 0, 1
+FS_GIVEN, FS_RSL, FS_RSL_EXACT = 0, 1, 2
 
 
 def build(force=False, openmp=False):
@@ -59,7 +60,7 @@ class GenParams(C.Structure):
                 ("s_wr", C.c_double), ("s_nwr", C.c_double), ("grav", C.c_double),
                 ("p_ref", C.c_double), ("dp_amp", C.c_double), ("corey", C.c_double),
                 ("E0", C.c_double), ("nu0", C.c_double), ("kappa0", C.c_double),
-                ("phi0", C.c_double), ("sw0", C.c_double)]
+                ("phi0", C.c_double), ("sw0", C.c_double), ("fs_modulus", C.c_int32)]
 
 
 _PD, _PI64, _PI32, _PU8 = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
@@ -85,7 +86,8 @@ class PrecParams(C.Structure):
                 ("post", C.c_int32), ("smoother", C.c_int32), ("cheb_degree", C.c_int32),
                 ("cheb_ratio", C.c_double), ("mech_mode", C.c_int32), ("flow_mode", C.c_int32),
                 ("local_mode", C.c_int32), ("press_mode", C.c_int32), ("full_exact", C.c_int32),
-                ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32)]
+                ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
+                ("fs_mode", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -144,6 +146,7 @@ def lib(openmp=None):
         L.or_spp_nnz.restype = C.c_int64
         L.or_spp.argtypes = [C.c_void_p, _PI64, _PI32, _PD]
         L.or_ilu_dinv.argtypes = [C.c_void_p, _PD]
+        L.or_fs_diag.argtypes = [C.c_void_p, _PD]
         L.or_ilu_apply.argtypes = [C.c_void_p, _PD, _PD]
         L.or_gs_apply.argtypes = [C.c_void_p, _PD, _PD, C.c_int]
         L.or_fgmres.argtypes = [C.POINTER(_System), C.c_void_p, _PD, _PD, C.c_double, C.c_int, C.c_int,
@@ -328,6 +331,11 @@ class Prec:
         v = np.empty(nnz)
         self._L.or_spp(self._h, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
         return rp, ci, v
+
+    def fs_diag(self):
+        d = np.empty(2 * self.system.n_cells)
+        self._L.or_fs_diag(self._h, _d(d))
+        return d
 
     def ilu_dinv(self):
         d = np.empty(4 * self.system.n_cells)

@@ -564,9 +564,10 @@ void assemble(const or_gen_params& gp, const Grid& g, const Fields& F, const Sta
           blk[2] += -V * m.phi * m.rnw;
           blk[3] += V * ((1.0 - s) * m.rnw * m.dphidp + m.phi * (1.0 - s) * gp.rho_nw0 * gp.c_nw);
         }
-        // §5.1 fixed-stress diagonals
-        J.dfs[2 * c + 0] = V * b * b / m.Kdr * s * m.rw;
-        J.dfs[2 * c + 1] = V * b * b / m.Kdr * (1.0 - s) * m.rnw;
+        // §5.1 fixed-stress diagonals, with K_dr or (remark on one-dimensional loading) the uniaxial modulus
+        const double Kfs = gp.fs_modulus == 1 ? m.Kdr + 4.0 * m.G / 3.0 : m.Kdr;
+        J.dfs[2 * c + 0] = V * b * b / Kfs * s * m.rw;
+        J.dfs[2 * c + 1] = V * b * b / Kfs * (1.0 - s) * m.rnw;
       }
   // face loop: TPFA Jacobian (App. B face blocks, with the Jacobian's sign:
   // row K gets -dt dF, row L gets +dt dF)
@@ -1200,6 +1201,18 @@ static Smooth smooth_of(const or_prec_params& pp) {
   return s;
 }
 
+// M_uu^{-1} of §5.2 on a node-major displacement vector: one V-cycle per component on the shared hierarchy
+static void mech_apply(const AMG& H, const Smooth& sm, int64_t nn, const double* vu, double* zu) {
+  for (int c = 0; c < 3; ++c) {
+    vec b(nn), x;
+#pragma omp parallel for schedule(static)
+    for (int64_t I = 0; I < nn; ++I) b[I] = vu[3 * I + c];
+    vcycle(H, 0, c, b, x, sm);
+#pragma omp parallel for schedule(static)
+    for (int64_t I = 0; I < nn; ++I) zu[3 * I + c] = x[I];
+  }
+}
+
 struct or_prec {
   const or_system* s = nullptr;
   or_prec_params pp;
@@ -1210,6 +1223,7 @@ struct or_prec {
   BSR ilu;              // L (unit, strictly lower) and U (upper) blocks in the S_ff pattern
   vec dinv;             // inv(U_ii)
   vec gs_dinv;          // inv of the diagonal blocks of S_ff^(FS) (block Gauss-Seidel)
+  vec dfs;              // (D_sp, D_pp) per cell added to S_ff: the system's d_fs or the row-sum lumping
   DenseLU lu_uu, lu_flow, lu_local, lu_pp, lu_full;
 };
 
@@ -1557,13 +1571,52 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
   P->A_fu = to_bsr(s, 2);
   P->A_ff = to_bsr(s, 3);
   BSR Auu = to_bsr(s, 0);
+  // §5.2: M_uu = amg(A_uu^(SDC)), three displacement components, shared aggregates
+  if (pp->mech_mode == OR_MECH_AMG) {
+    CSR A0; A0.n = A0.m = nn; A0.nc = 3; A0.rp = Auu.rp; A0.ci = Auu.ci;
+    A0.v.resize(Auu.ci.size() * 3);
+    for (size_t q = 0; q < Auu.ci.size(); ++q)
+      for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = Auu.v[q * 9 + d * 4];
+    if (!build_amg(P->amg_u, std::move(A0), pp->theta_u, pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
+  } else {
+    vec d(size_t(s->n_u) * s->n_u, 0.0);
+    bsr_dense(Auu, d, 0, 0, s->n_u);
+    P->lu_uu.factor(s->n_u, std::move(d));
+  }
+  // fixed-stress diagonal: the system's d_fs, or the row-sum lumping of the §5.1 remark,
+  // D_sp = -diag(A_su A_uu^{-1} A_up e), D_pp = -diag(A_pu A_uu^{-1} A_up e), with A_uu^{-1} replaced by
+  // one application of M_uu^{-1} (OR_FS_RSL) or taken exactly by dense LU (OR_FS_RSL_EXACT)
+  P->dfs.assign(s->d_fs, s->d_fs + 2 * nc);
+  if (pp->fs_mode == OR_FS_RSL || pp->fs_mode == OR_FS_RSL_EXACT) {
+    BSR Auf = to_bsr(s, 1);
+    vec aupe(3 * nn, 0.0), w(3 * nn, 0.0);
+    for (int64_t I = 0; I < nn; ++I)
+      for (int64_t q = Auf.rp[I]; q < Auf.rp[I + 1]; ++q)
+        for (int d = 0; d < 3; ++d) aupe[3 * I + d] = aupe[3 * I + d] + Auf.v[q * 6 + d * 2 + 1];
+    if (pp->fs_mode == OR_FS_RSL) {
+      if (pp->mech_mode != OR_MECH_AMG) { delete P; return 3; }
+      mech_apply(P->amg_u, smooth_of(*pp), nn, aupe.data(), w.data());
+    } else {
+      vec d(size_t(s->n_u) * s->n_u, 0.0);
+      bsr_dense(Auu, d, 0, 0, s->n_u);
+      DenseLU lu; lu.factor(s->n_u, std::move(d));
+      lu.solve(aupe.data(), w.data());
+    }
+    for (int64_t c = 0; c < nc; ++c)
+      for (int a = 0; a < 2; ++a) {
+        double acc = 0.0;
+        for (int64_t q = P->A_fu.rp[c]; q < P->A_fu.rp[c + 1]; ++q)
+          for (int e = 0; e < 3; ++e) acc += P->A_fu.v[q * 6 + a * 3 + e] * w[3 * int64_t(P->A_fu.ci[q]) + e];
+        P->dfs[2 * c + a] = -acc;
+      }
+  }
   // §5.1, fixed-stress Schur approximation: S_ff^(FS) = A_ff + blockdiag([[0, D_sp],[0, D_pp]])
   P->Sff = P->A_ff;
 #pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) {
     int64_t q = P->Sff.find(c, c);
-    P->Sff.v[q * 4 + 1] = P->Sff.v[q * 4 + 1] + s->d_fs[2 * c];
-    P->Sff.v[q * 4 + 3] = P->Sff.v[q * 4 + 3] + s->d_fs[2 * c + 1];
+    P->Sff.v[q * 4 + 1] = P->Sff.v[q * 4 + 1] + P->dfs[2 * c];
+    P->Sff.v[q * 4 + 3] = P->Sff.v[q * 4 + 3] + P->dfs[2 * c + 1];
   }
   // §5.3 quasi-IMPES: D_ss = diagm(A_ss), D_ps = diagm(A_ps); or true-IMPES: D_ss = diag(A_ss^T e),
   // D_ps = diag(A_ps^T e), column sums taken over the rows in ascending order;
@@ -1592,18 +1645,6 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
     double ratio = P->dps[c] / P->dss[c];
     for (int64_t q = P->Sff.rp[c]; q < P->Sff.rp[c + 1]; ++q)
       P->spp.v[q] = P->Sff.v[q * 4 + 3] - ratio * P->Sff.v[q * 4 + 1];
-  }
-  // §5.2: M_uu = amg(A_uu^(SDC)), three displacement components, shared aggregates
-  if (pp->mech_mode == OR_MECH_AMG) {
-    CSR A0; A0.n = A0.m = nn; A0.nc = 3; A0.rp = Auu.rp; A0.ci = Auu.ci;
-    A0.v.resize(Auu.ci.size() * 3);
-    for (size_t q = 0; q < Auu.ci.size(); ++q)
-      for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = Auu.v[q * 9 + d * 4];
-    if (!build_amg(P->amg_u, std::move(A0), pp->theta_u, pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
-  } else {
-    vec d(size_t(s->n_u) * s->n_u, 0.0);
-    bsr_dense(Auu, d, 0, 0, s->n_u);
-    P->lu_uu.factor(s->n_u, std::move(d));
   }
   if (pp->press_mode == OR_PRESS_AMG) {
     if (!build_amg(P->amg_p, P->spp, pp->theta_p, pp->coarse_max_p, pp->max_levels)) { delete P; return 2; }
@@ -1741,14 +1782,7 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
   // step 1: z_u = M_uu^{-1} v_u
   vec zu(nu);
   if (P->pp.mech_mode == OR_MECH_AMG) {
-    for (int c = 0; c < 3; ++c) {
-      vec b(nn), x;
-#pragma omp parallel for schedule(static)
-      for (int64_t I = 0; I < nn; ++I) b[I] = v[3 * I + c];
-      vcycle(P->amg_u, 0, c, b, x, smooth_of(P->pp));
-#pragma omp parallel for schedule(static)
-      for (int64_t I = 0; I < nn; ++I) zu[3 * I + c] = x[I];
-    }
+    mech_apply(P->amg_u, smooth_of(P->pp), nn, v, zu.data());
   } else {
     P->lu_uu.solve(v, zu.data());
   }
@@ -1897,6 +1931,11 @@ int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v) {
   std::memcpy(v, p->spp.v.data(), p->spp.v.size() * sizeof(double));
   return 0;
 }
+int or_fs_diag(const or_prec* p, double* dfs) {
+  std::memcpy(dfs, p->dfs.data(), p->dfs.size() * sizeof(double));
+  return 0;
+}
+
 int or_ilu_dinv(const or_prec* p, double* dinv) {
   std::memcpy(dinv, p->dinv.data(), p->dinv.size() * sizeof(double));
   return 0;

@@ -61,6 +61,9 @@ typedef struct {
   double corey;          /* relative-permeability exponent (2 in §6) */
   /* homogeneous fields (field_kind == OR_FIELDS_HOMOGENEOUS) */
   double E0, nu0, kappa0, phi0, sw0;
+  /* modulus of the fixed-stress diagonal (§5.1): 0 = drained bulk modulus K_dr (default), 1 = uniaxial
+     (constrained) modulus K_dr + 4G/3 of the remark on one-dimensional loading */
+  int32_t fs_modulus;
 } or_gen_params;
 
 typedef struct {
@@ -113,6 +116,7 @@ enum { OR_FLOW_CPR = 0, OR_FLOW_EXACT_FS = 1, OR_FLOW_EXACT_SCHUR = 2 }; /* M_ff
 enum { OR_LOCAL_ILU0 = 0, OR_LOCAL_EXACT = 1, OR_LOCAL_GS = 2 }; /* M_L: ILU(0), exact, block Gauss-Seidel */
 enum { OR_PRESS_AMG = 0, OR_PRESS_EXACT = 1 };                /* M_pp */
 enum { OR_CPR_QUASI_IMPES = 0, OR_CPR_TRUE_IMPES = 1 };        /* D_ss, D_ps of the CPR reduction */
+enum { OR_FS_GIVEN = 0, OR_FS_RSL = 1, OR_FS_RSL_EXACT = 2 };  /* D_sp, D_pp of S_ff^(FS) */
 
 typedef struct {
   double theta_u, theta_p;
@@ -126,6 +130,9 @@ typedef struct {
   int32_t full_exact; /* M^{-1} = A^{-1} (dense, tiny systems only) */
   int32_t local_sweeps; /* OR_LOCAL_GS: block Gauss-Seidel sweeps (3 in §6.1) */
   int32_t cpr_reduction; /* OR_CPR_QUASI_IMPES (diagonal entries) or OR_CPR_TRUE_IMPES (column sums), §5.3 */
+  int32_t fs_mode;       /* fixed-stress diagonal of S_ff: OR_FS_GIVEN (the system's d_fs), OR_FS_RSL (row-sum
+                            lumping of the §5.1 remark with one application of M_uu^{-1}), OR_FS_RSL_EXACT
+                            (the same with A_uu^{-1} by dense LU; tiny systems) */
 } or_prec_params;
 
 typedef struct or_prec or_prec;
@@ -161,6 +168,8 @@ int or_smoother_apply(int64_t n, const int64_t* rp, const int32_t* ci, const dou
 /* S_pp^(cpr-fs) (§5.3) as CSR, and the fixed-stress S_ff (§5.1) as 2x2 BSR */
 int64_t or_spp_nnz(const or_prec* p);
 int or_spp(const or_prec* p, int64_t* rp, int32_t* ci, double* v);
+/* the (D_sp, D_pp) pairs added to the diagonal blocks of S_ff (2 per cell) */
+int or_fs_diag(const or_prec* p, double* dfs);
 /* ILU(0) inverse diagonal blocks inv(U_ii), 4 per cell */
 int or_ilu_dinv(const or_prec* p, double* dinv);
 /* apply M_L^{-1} (block ILU(0)) to a flow vector */

@@ -22,6 +22,7 @@ PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1
 PS_LOCAL_ILU0, PS_LOCAL_HBGS = 0, 1
 PS_CPR_QUASI_IMPES, PS_CPR_TRUE_IMPES = 0, 1
 PS_SOLVER_FGMRES, PS_SOLVER_RICHARDSON = 0, 1
+PS_FS_GIVEN, PS_FS_RSL = 0, 1
 PS_FIELDS_LOGNORMAL, PS_FIELDS_LAYERED, PS_FIELDS_CHANNELS, PS_FIELDS_HOMOGENEOUS = range(4)
 PS_GEN_GRAVITY, PS_GEN_DIRICHLET, PS_GEN_SCALE, PS_GEN_ACCUM, PS_GEN_FLUX, PS_GEN_FLUX_SAT, PS_GEN_COUPLING = \
     (1 << i for i in range(7))
@@ -52,7 +53,7 @@ class ps_params(C.Structure):
                 ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
                 ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
                 ("local_stage", C.c_int32), ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
-                ("solver", C.c_int32)]
+                ("solver", C.c_int32), ("fs_mode", C.c_int32)]
 
 
 class ps_stats(C.Structure):
@@ -87,7 +88,7 @@ class ps_gen_params(C.Structure):
                 ("rho_nw0", C.c_double), ("rho_s0", C.c_double), ("s_wr", C.c_double), ("s_nwr", C.c_double),
                 ("grav", C.c_double), ("p_ref", C.c_double), ("dp_amp", C.c_double), ("corey", C.c_double),
                 ("E0", C.c_double), ("nu0", C.c_double), ("kappa0", C.c_double), ("phi0", C.c_double),
-                ("sw0", C.c_double)]
+                ("sw0", C.c_double), ("fs_modulus", C.c_int32)]
 
 
 _PD = C.POINTER(C.c_double)

@@ -97,6 +97,9 @@ struct SmoothParams {
 // x = V-cycle(b) on the level-0 vectors (interleaved nc components), T = float or double
 template <class T>
 ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st);
+// x = V-cycle(b) launched directly (no graph capture), for one-off applications during setup
+template <class T>
+ps_status amg_vcycle_direct(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st);
 // allocate the per-level work vectors for precision T (and the Chebyshev first-step scaling of sp)
 template <class T>
 ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st);

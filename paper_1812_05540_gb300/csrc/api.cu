@@ -26,6 +26,30 @@ __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = double(a[t]);
 }
+// row-sum lumping (§5.1 remark): A_up e per node (the p column of every 3x2 block of A_uf, summed over the row)
+__global__ void k_rsl_aupe(int64_t nn, const int32_t* __restrict__ rp, const double* __restrict__ uf,
+                           double* __restrict__ out) {
+  int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (I >= nn) return;
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int32_t q = rp[I]; q < rp[I + 1]; ++q)
+    for (int d = 0; d < 3; ++d) a[d] = a[d] + uf[int64_t(q) * 6 + d * 2 + 1];
+  for (int d = 0; d < 3; ++d) out[3 * I + d] = a[d];
+}
+// D_sp = -(A_su w)_c, D_pp = -(A_pu w)_c per cell
+__global__ void k_rsl_dfs(int64_t nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ fu, const double* __restrict__ w, double* __restrict__ dfs) {
+  int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  for (int a = 0; a < 2; ++a) {
+    double acc = 0.0;
+    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) {
+      const int64_t J = ci[q];
+      for (int e = 0; e < 3; ++e) acc += fu[int64_t(q) * 6 + a * 3 + e] * w[3 * J + e];
+    }
+    dfs[2 * c + a] = -acc;
+  }
+}
 __global__ void k_i32_to_i64(const int32_t* __restrict__ a, int64_t* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = a[t];
@@ -44,6 +68,9 @@ struct ps_handle {
   bool bf16p = false;  // BF16 transfer operators (PS_MIXED_BF16P)
   JacDev J;
   double* dfs = nullptr;
+  // row-sum-lumped fixed stress (PS_FS_RSL): w = M_uu^{-1} (A_up e) per node, and the (D_sp, D_pp) it gives
+  double* rsl_w = nullptr;
+  double* rsl_dfs = nullptr;
   Amg amg_u, amg_p;
   FlowStage F;
   FlowWork<float> w32;
@@ -166,7 +193,14 @@ ps_status build_flow(ps_handle* h) {
   F.cpr = h->prm.cpr_reduction;
   F.gs_sweeps = h->prm.local_sweeps;
   F.test_stall = h->prm.test_stall_wave;
-  PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, h->dfs, h->mixed, st));
+  const double* dfs = h->dfs;
+  if (h->prm.fs_mode == PS_FS_RSL) {
+    PS_TRY(ar.alloc(&h->rsl_dfs, 2 * h->nc));
+    PS_TICK(); k_rsl_dfs<<<grid_for(h->nc, 256), 256, 0, st>>>(h->nc, h->J.fu_rp, h->J.fu_ci, h->J.fu_v, h->rsl_w,
+                                                              h->rsl_dfs);
+    dfs = h->rsl_dfs;
+  }
+  PS_TRY(flow_setup(ar, F, h->J.ff_rp, h->J.ff_ci, h->J.ff_v, dfs, h->mixed, st));
   if (h->mixed) {
     int64_t nfu = 0;
     int32_t t2 = 0;
@@ -247,6 +281,28 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     PS_TRY(ar.alloc(&h->zu32, h->nu));
   } else {
     PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
+  }
+  if (h->prm.fs_mode == PS_FS_RSL) {
+    // w = M_uu^{-1} (A_up e): one FP64 V-cycle on a view of the mechanics hierarchy with its own FP64 work
+    // vectors (the fixed-stress diagonal is one of the FP64 parts of the mixed mode)
+    double* aupe;
+    PS_TRY(ar.alloc(&aupe, h->nu));
+    PS_TRY(ar.alloc(&h->rsl_w, h->nu));
+    PS_TICK(); k_rsl_aupe<<<grid_for(h->nn, 256), 256, 0, st>>>(h->nn, J.uf_rp, J.uf_v, aupe);
+    Amg S = h->amg_u;
+    S.gexec = nullptr;
+    for (auto& L : S.L) {
+      L.x = L.t = L.r = L.d = L.b = L.e = L.dsi = nullptr;
+      L.sv_f = nullptr;
+    }
+    Arena tmp;
+    tmp.stream = st;
+    ps_status rs = amg_alloc_work<double>(tmp, S, smooth_params(h->prm), st);
+    if (rs == PS_OK) rs = amg_vcycle_direct<double>(S, smooth_params(h->prm), aupe, h->rsl_w, st);
+    cudaStreamSynchronize(st);
+    tmp.free_all();
+    ar.release(aupe);
+    PS_TRY(rs);
   }
   cudaEventRecord(e1, st);
   PS_CUDA(cudaEventSynchronize(e1));
@@ -332,6 +388,7 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   if (params->cpr_reduction != PS_CPR_QUASI_IMPES && params->cpr_reduction != PS_CPR_TRUE_IMPES)
     return PS_ERR_INVALID;
   if (params->solver != PS_SOLVER_FGMRES && params->solver != PS_SOLVER_RICHARDSON) return PS_ERR_INVALID;
+  if (params->fs_mode != PS_FS_GIVEN && params->fs_mode != PS_FS_RSL) return PS_ERR_INVALID;
   if (params->local_stage == PS_LOCAL_HBGS && (params->local_sweeps < 1 || params->local_sweeps > 64)) {
     set_reason("local_sweeps must be 1..64 for the block Gauss-Seidel local stage");
     return PS_ERR_INVALID;

@@ -284,9 +284,10 @@ __global__ void k_ff_residual(int nx, int ny, int nz, const T* __restrict__ S28,
 // §5.3 option 1, block Gauss-Seidel on the interleaved S_ff^(FS): one colour of one sweep.  Thread p owns
 // colour slot p (gs_index); the colour's cells share no face, so each is updated from the other colour's
 // newest values: dz_i = inv(S_ii) (w_i - sum_j S_ij dz_j) over the face neighbours j, in slot order
-// (z-1, y-1, x-1, x+1, y+1, z+1).  Blocks of neighbours outside the grid are stored as zero and read dz at
-// the cell itself, so every slot loads without a branch.  ZERO: the first colour of the first sweep (every
-// dz_j is still 0).  LAST: the last sweep also writes z_f + dz_f (FP64) for its cells to zout.
+// (z-1, y-1, x-1, x+1, y+1, z+1); neighbours outside the grid are skipped (their stored blocks are zero, and
+// dz is not read there: the cell's own dz may still hold a previous apply's value).  ZERO: the first colour
+// of the first sweep (every dz_j is still 0).  LAST: the last sweep also writes z_f + dz_f (FP64) for its
+// cells to zout.
 template <class T, bool ZERO, bool LAST>
 __global__ void k_gs_colour(int nx, int ny, int nz, int col, int64_t ncp, const T* __restrict__ rec,
                             const T* __restrict__ w, T* __restrict__ dz, const T* __restrict__ zs,
@@ -304,11 +305,11 @@ __global__ void k_gs_colour(int nx, int ny, int nz, int col, int64_t ncp, const 
   const T* R = rec + ((int64_t(col) * ((ncp + 31) / 32) + (p >> 5)) * 28) * 32 + (p & 31);
   T a0 = w[2 * i], a1 = w[2 * i + 1];
   if (!ZERO) {
-    const int64_t nb[6] = {z > 0 ? i - nxy : i, y > 0 ? i - nx : i, x > 0 ? i - 1 : i,
-                           x + 1 < nx ? i + 1 : i, y + 1 < ny ? i + nx : i, z + 1 < nz ? i + nxy : i};
+    const int64_t nb[6] = {i - nxy, i - nx, i - 1, i + 1, i + nx, i + nxy};
+    const bool in[6] = {z > 0, y > 0, x > 0, x + 1 < nx, y + 1 < ny, z + 1 < nz};
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const T d0 = dz[2 * nb[q]], d1 = dz[2 * nb[q] + 1];
+      const T d0 = in[q] ? dz[2 * nb[q]] : T(0), d1 = in[q] ? dz[2 * nb[q] + 1] : T(0);
       a0 -= R[(4 * q) * 32] * d0 + R[(4 * q + 1) * 32] * d1;
       a1 -= R[(4 * q + 2) * 32] * d0 + R[(4 * q + 3) * 32] * d1;
     }

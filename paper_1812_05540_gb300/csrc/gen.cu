@@ -172,6 +172,7 @@ __global__ void k_fields(FieldArgs fa, const double* __restrict__ ghat, const do
 struct Phys {
   double dt, b, c_w, c_nw, c_r, mu_w, mu_nw, rho_w0, rho_nw0, rho_s0, s_wr, s_nwr, grav, p_ref, corey, h;
   uint32_t flags;
+  int fs_modulus;  // 0: K_dr in the fixed-stress diagonal, 1: uniaxial modulus K_dr + 4G/3
 };
 struct CellMat {
   double lam, G, Kdr, dphidp, phi, rw, rnw, drho_deps, drho_dp, drho_ds;
@@ -511,9 +512,10 @@ __global__ void k_values_ff(Grid3 g, Phys P, const CellMat* __restrict__ M, cons
     }
   }
   for (int t = 0; t < 4; ++t) val[qd * 4 + t] = dg[t];
-  // §5.1 fixed-stress diagonal entries
-  dfs[2 * c + 0] = V * P.b * P.b / m.Kdr * s * m.rw;
-  dfs[2 * c + 1] = V * P.b * P.b / m.Kdr * (1.0 - s) * m.rnw;
+  // §5.1 fixed-stress diagonal entries (K_dr, or the uniaxial modulus of the §5.1 remark)
+  const double Kfs = P.fs_modulus == 1 ? m.Kdr + 4.0 * m.G / 3.0 : m.Kdr;
+  dfs[2 * c + 0] = V * P.b * P.b / Kfs * s * m.rw;
+  dfs[2 * c + 1] = V * P.b * P.b / Kfs * (1.0 - s) * m.rnw;
 }
 
 // ---- Dirichlet elimination and scaling ----
@@ -692,6 +694,7 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   P.dt = gp->dt; P.b = gp->biot; P.c_w = gp->c_w; P.c_nw = gp->c_nw; P.c_r = gp->c_r; P.mu_w = gp->mu_w;
   P.mu_nw = gp->mu_nw; P.rho_w0 = gp->rho_w0; P.rho_nw0 = gp->rho_nw0; P.rho_s0 = gp->rho_s0; P.s_wr = gp->s_wr;
   P.s_nwr = gp->s_nwr; P.grav = gp->grav; P.p_ref = gp->p_ref; P.corey = gp->corey; P.h = gp->h; P.flags = gp->flags;
+  P.fs_modulus = gp->fs_modulus;
   CellMat* M;
   PS_TRY(ar.alloc(&M, nc));
   PS_TICK(); k_material<<<grid_for(nc, 256), 256, 0, st>>>(P, nc, E, nu, phi, sw, p, M);

@@ -517,6 +517,14 @@ ps_status amg_vcycle(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStrea
   return PS_OK;
 }
 
+template <class T>
+ps_status amg_vcycle_direct(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st) {
+  vcycle_launch<T>(H, sp, b, x, st);
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+template ps_status amg_vcycle_direct<double>(Amg&, const SmoothParams&, const double*, double*, cudaStream_t);
 template ps_status amg_alloc_work<float>(Arena&, Amg&, const SmoothParams&, cudaStream_t);
 template ps_status amg_alloc_work<double>(Arena&, Amg&, const SmoothParams&, cudaStream_t);
 template ps_status amg_vcycle<float>(Amg&, const SmoothParams&, const float*, float*, cudaStream_t);

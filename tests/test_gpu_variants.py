@@ -4,7 +4,9 @@
     Algorithm 1 in FP64 within 1e-10, FGMRES with the north-star tolerances;
   * sequential fixed-stress strategy (§5.4 remark, the preconditioner inside a Richardson iteration): the
     same pass count as the oracle's Richardson iteration within 10 %, true relres <= 1e-8 and the oracle's
-    solution within 1e-6."""
+    solution within 1e-6;
+  * row-sum-lumped fixed-stress diagonal (§5.1 remark): S_pp within 1e-12, Algorithm 1 and the solve as
+    above."""
 import numpy as np
 import pytest
 
@@ -100,3 +102,37 @@ def test_richardson_matches_oracle(cfg, kw, prec):
     assert relres <= 1e-8 and abs(relres - st.true_relres) <= 1e-10
     assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
     assert abs(st.iters - stor.iters) <= max(1, int(0.1 * stor.iters)), (st.iters, stor.iters)
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+@pytest.mark.parametrize("cfg,kw", [(0, {}), (1, dict(nx=24, ny=20, nz=10))])
+def test_rsl_fixed_stress(cfg, kw, prec):
+    # row-sum-lumped fixed-stress diagonal (§5.1 remark), w = M_uu^{-1} (A_up e) by one FP64 mechanics
+    # V-cycle on both sides: S_pp within 1e-12 of the oracle's (the V-cycles round differently), Algorithm 1
+    # in FP64 within 1e-10, and the FGMRES solve with the benchmark spec's tolerances
+    g = _g()
+    osys = oracle.System(oracle.default_params(cfg, **kw))
+    P = oracle.Prec(osys, oracle.default_prec_params(fs_mode=oracle.FS_RSL))
+    xo, _ = P.fgmres(tol=1e-12)
+    _, sto8 = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, fs_mode=ps.PS_FS_RSL))
+    try:
+        rp, ci, spp_o = P.spp()
+        spp, _ = ps.ps_flow_copy(h, len(ci), osys.n_cells)
+        assert np.abs(spp - spp_o).max() <= 1e-12 * np.abs(spp_o).max()
+        if prec == ps.PS_FP64:
+            vs = np.random.default_rng(6).standard_normal(osys.n)
+            v = torch.from_numpy(vs).cuda()
+            z = torch.empty_like(v)
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            zo = P.apply(vs)
+            assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+        x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(osys.rhs - osys.spmv(xs)) <= 1e-8 * np.linalg.norm(osys.rhs)
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - sto8.iters) <= max(1, int(0.1 * sto8.iters) + 1), (st.iters, sto8.iters)

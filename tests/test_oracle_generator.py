@@ -243,3 +243,19 @@ def test_correlated_field_variance_and_autocorrelation():
         assert abs(c - np.exp(-d * d / (4.0 * L * L))) < 0.05
     c = np.mean(f[1:] * f[:-1])
     assert abs(c - np.exp(-1 / 4.0)) < 0.05
+
+
+def test_uniaxial_fixed_stress_modulus():
+    # §5.1 remark: under one-dimensional loading the uniaxial (constrained) modulus K_v replaces K_dr in the
+    # fixed-stress diagonal.  With K_dr = E / (3 (1 - 2 nu)) and K_v = E (1 - nu) / ((1 + nu) (1 - 2 nu)),
+    # every cell's D_sp and D_pp scale by K_dr / K_v = (1 + nu) / (3 (1 - nu)); nothing else changes.
+    kw = dict(nx=6, ny=5, nz=4)
+    a = oracle.System(oracle.default_params(1, **kw))
+    b = oracle.System(oracle.default_params(1, fs_modulus=1, **kw))
+    nu = a.fields["nu"]
+    ratio = (1.0 + nu) / (3.0 * (1.0 - nu))
+    assert np.allclose(b.d_fs.reshape(-1, 2), a.d_fs.reshape(-1, 2) * ratio[:, None], rtol=1e-13, atol=0)
+    for name in ("uu", "uf", "fu", "ff"):
+        for x, y in zip(a.blocks[name], b.blocks[name]):
+            assert np.array_equal(x, y)
+    assert np.array_equal(a.rhs, b.rhs)
