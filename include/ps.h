@@ -177,6 +177,23 @@ ps_status ps_set_test_stall_gs(ps_handle* h, int32_t cta_plus_one);
    PS_ERR_NOT_CONVERGED still fills x and *st (st may be NULL). */
 ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* st);
 
+/* Batched setup: n independent systems (jac[i] on grid[i]), each with params except the stream: handle i
+   gets a stream of its own (created by the library and destroyed by ps_free).  The setups run on up to
+   eight host threads at once, so their kernels overlap on the device.  On failure every handle made so
+   far is freed, out[] is zeroed and the first failing status is returned.  The paper solves one system
+   at a time (§5.4); this is the batching layer around that setup. */
+ps_status ps_setup_batch(int32_t n, const ps_jacobian* jac, const ps_grid* grid, const ps_params* params,
+                         ps_handle** out);
+
+/* Batched iteration phase: the FGMRES solves of n handles (rhs[i], x[i] as in ps_solve) advanced in
+   lockstep, one Arnoldi step (or cycle end) of every unfinished system per round, each on its handle's
+   stream, with one host synchronisation per round for all of them.  Each system runs the kernels of
+   ps_solve in the same order, so x[i] equals what ps_solve gives for it.  stats[i] (may be NULL) gets each
+   system's statistics; the first non-OK status is returned.  Handles with the Richardson solver are
+   solved one after another. */
+ps_status ps_solve_batch(int32_t n, ps_handle* const* h, const double* const* rhs, double* const* x, double tol,
+                         ps_stats* stats);
+
 /* y = A x with the stored FP64 Jacobian (device pointers). */
 ps_status ps_spmv(ps_handle* h, const double* x, double* y);
 

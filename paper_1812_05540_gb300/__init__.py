@@ -126,6 +126,10 @@ def lib():
         L.ps_amg_nlevels.restype = C.c_int32
         L.ps_amg_level_info.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_int64)]
+        L.ps_setup_batch.argtypes = [C.c_int32, C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.POINTER(ps_params),
+                                     C.POINTER(H)]
+        L.ps_solve_batch.argtypes = [C.c_int32, C.POINTER(H), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                     C.c_double, C.POINTER(ps_stats)]
         L.ps_amg_level_shape.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
         L.ps_amg_level_copy.argtypes = [H, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ps_flow_copy.argtypes = [H, C.c_void_p, C.c_void_p]
@@ -264,6 +268,29 @@ def ps_amg_level_info(h, which, level):
     n, nnz, nagg = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().ps_amg_level_info(h, which, level, C.byref(n), C.byref(nnz), C.byref(nagg)), "ps_amg_level_info")
     return n.value, nnz.value, nagg.value
+
+
+def ps_setup_batch(jacs, grids, params):
+    """Handles of len(jacs) systems set up together; each handle owns a stream of its own."""
+    n = len(jacs)
+    JA = (ps_jacobian * n)(*jacs)
+    GA = (ps_grid * n)(*grids)
+    out = (C.c_void_p * n)()
+    _check(lib().ps_setup_batch(n, JA, GA, C.byref(params), out), "ps_setup_batch")
+    return list(out)
+
+
+def ps_solve_batch(handles, rhs_ptrs, x_ptrs, tol, raise_on_error=True):
+    """Lockstep FGMRES of every handle; returns (status, [ps_stats])."""
+    n = len(handles)
+    HA = (C.c_void_p * n)(*handles)
+    RA = (C.c_void_p * n)(*rhs_ptrs)
+    XA = (C.c_void_p * n)(*x_ptrs)
+    st = (ps_stats * n)()
+    s = lib().ps_solve_batch(n, HA, RA, XA, tol, st)
+    if raise_on_error:
+        _check(s, "ps_solve_batch")
+    return s, list(st)
 
 
 def ps_amg_level_shape(h, which, level):

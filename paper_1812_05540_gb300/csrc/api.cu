@@ -1,7 +1,10 @@
 // C ABI: setup phase, Algorithm 1 and the flexible-GMRES iteration phase.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <thread>
+#include <vector>
 
 #include "amg.cuh"
 #include "flow.cuh"
@@ -94,6 +97,7 @@ struct ps_handle {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-iteration phase timers
   cudaEvent_t fe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Algorithm 1 sub-phase timers
   bool fine_pending = false;
+  bool own_stream = false;  // the stream was created by ps_setup_batch and is destroyed by ps_free
 };
 
 namespace {
@@ -544,140 +548,209 @@ ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double to
 
 }  // namespace
 
+}  // extern "C"
+
+namespace {
+
+// One FGMRES(m) solve (§4, flexible right preconditioning) as a resumable sequence of device steps, so
+// that ps_solve runs one and ps_solve_batch runs many in lockstep on their own streams with one host
+// synchronisation per step for all of them.  A step is either one Arnoldi iteration (Algorithm 1, the
+// FP64 Jacobian SpMV, Gram-Schmidt, Givens update, status copy) or the end of a cycle (Hessenberg solve,
+// x += Z y, true residual).  Each system runs the same kernels in the same order either way.
+struct FgmresRun {
+  ps_handle* h = nullptr;
+  const double* rhs = nullptr;
+  double* x = nullptr;
+  double tol = 0.0;
+  ps_stats S;
+  ps_status result = PS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double bnorm = 0.0;
+  int total = 0, j = 0, jend = -1;
+  bool brk = false;
+  bool done = false;
+  bool cycle_end = false;  // the next step closes the cycle
+  bool fresh_cycle = true; // the next Arnoldi iteration opens a cycle
+
+  // ||b|| and the start of the first cycle (one synchronisation)
+  ps_status start(ps_handle* hh, const double* b_in, double* x_out, double t) {
+    h = hh; rhs = b_in; x = x_out; tol = t;
+    std::memset(&S, 0, sizeof(S));
+    cudaStream_t st = h->st;
+    const int64_t n = h->n;
+    KrylovState& K = h->K;
+    const bool host = h->prm.host_ptrs != 0;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    fill_zero(h->x, n, st);
+    const int64_t ldv = h->ldv;
+    if (ldv > n)  // padding rows of the basis (a failed solve may have left a NaN there)
+      PS_CUDA(cudaMemset2DAsync(h->V + n, size_t(ldv) * sizeof(double), 0, size_t(ldv - n) * sizeof(double), h->m + 1,
+                                st));
+    multidot(h->V, n, 0, h->b, n, h->mpart, K.sc + 7, 1, nullptr, st);
+    PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    const double bn2 = h->hsc[7];
+    if (!(bn2 > 0.0)) {
+      if (std::isnan(bn2)) result = PS_ERR_NAN;
+      done = true;
+      return PS_OK;
+    }
+    bnorm = std::sqrt(bn2);
+    h->hsc[8] = bn2;
+    h->hsc[9] = bnorm;
+    PS_CUDA(cudaMemcpyAsync(K.sc + 3, &h->hsc[8], sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(K.sc + 7, &h->hsc[9], sizeof(double), cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaMemcpyAsync(h->r, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    return PS_OK;
+  }
+
+  // enqueue the next step (no synchronisation)
+  ps_status enqueue() {
+    cudaStream_t st = h->st;
+    const int64_t n = h->n, ldv = h->ldv;
+    const int m = h->m;
+    KrylovState& K = h->K;
+    if (cycle_end) {
+      hessenberg_solve(K, m, jend, st);
+      maxpy(h->Z, n, jend + 1, K.y, h->x, n, st);
+      jac_spmv(h->J, h->x, h->r, h->b, h->part, st);
+      finish_sum(h->part, K.sc + 3, st);
+      PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      return PS_OK;
+    }
+    if (fresh_cycle) {
+      cycle_start(K, m, st);
+      scale_vec(h->r, h->V, n, K.sc + 4, st);
+      j = 0;
+      jend = -1;
+      brk = false;
+      fresh_cycle = false;
+    }
+    double* vj = h->V + j * ldv;
+    double* zj = h->Z + int64_t(j) * n;
+    double* w = h->V + (j + 1) * ldv;
+    cudaEventRecord(h->ev[0], st);
+    PS_TRY(apply_prec(h, vj, zj));
+    cudaEventRecord(h->ev[1], st);
+    jac_spmv(h->J, zj, w, nullptr, nullptr, st);
+    cudaEventRecord(h->ev[2], st);
+    if (h->prm.ortho == PS_ORTHO_MGS &&
+        mgs_step(h->V, ldv, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
+                 h->prm.test_stall_gs, h->prm.ortho_sweep, st)) {
+      // modified Gram-Schmidt (w normalised in the same launch)
+      arnoldi_finish(K, m, j, st);
+    } else {
+      // classical Gram-Schmidt with selective reorthogonalisation
+      multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
+      PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      mupdate(h->V, ldv, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
+      arnoldi_check(K, st);
+      multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
+      mupdate(h->V, ldv, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
+      arnoldi_finish(K, m, j, st);
+      scale_vec(w, w, n, K.sc + 4, st);
+    }
+    cudaEventRecord(h->ev[3], st);
+    PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(h->hflag + 3, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return PS_OK;
+  }
+
+  // after the stream has reached the end of the enqueued step: read its status and choose the next one
+  ps_status after_sync() {
+    cudaStream_t st = h->st;
+    KrylovState& K = h->K;
+    if (cycle_end) {
+      cycle_end = false;
+      const double rr = std::sqrt(h->hsc[3]) / bnorm;
+      S.true_relres = rr;
+      S.iters = total;
+      if (std::isnan(rr)) { result = PS_ERR_NAN; done = true; }
+      else if (rr <= tol) { result = PS_OK; done = true; }
+      else if (brk) { result = PS_ERR_BREAKDOWN; done = true; }
+      else if (total >= h->prm.max_iters) { result = PS_ERR_NOT_CONVERGED; done = true; }
+      else { S.restarts++; fresh_cycle = true; }
+      return PS_OK;
+    }
+    ++total;
+    const double est = h->hsc[5], hn = h->hsc[6];
+    {
+      float a = 0, b = 0, c = 0;
+      cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+      cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+      cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
+      S.ms_prec += a; S.ms_spmv += b; S.ms_orth += c;
+      float f[4] = {0, 0, 0, 0};
+      for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&f[q], h->fe[q], h->fe[q + 1]);
+      S.ms_vcycle_u += f[0]; S.ms_flow24 += f[1]; S.ms_vcycle_p += f[2]; S.ms_ilu += f[3];
+    }
+    S.est_relres = est;
+    jend = j;
+    S.reorth += h->hflag[0];
+    if (h->hflag[3] || h->hflag[2]) {
+      const bool wave = h->hflag[3] != 0;
+      if (h->hflag[3]) PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
+      if (h->hflag[2]) {
+        // the barrier counter is left mid-count: start it again from zero
+        PS_CUDA(cudaMemsetAsync(K.flag + 2, 0, sizeof(int), st));
+        PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
+        h->mgs_base = 0;
+      }
+      set_reason(wave ? "a bounded wait of the wavefront ILU(0) sweep gave up"
+                      : "a bounded grid barrier wait of the Gram-Schmidt step gave up");
+      result = PS_ERR_TIMEOUT;
+      S.iters = total;
+      done = true;
+      return PS_OK;
+    }
+    if (h->hflag[1]) { result = PS_ERR_NAN; S.iters = total; done = true; return PS_OK; }
+    if (!(hn > 1e-300 * bnorm)) brk = true;
+    if (est <= tol || brk || total >= h->prm.max_iters || j == h->m - 1) cycle_end = true;
+    else ++j;
+    return PS_OK;
+  }
+
+  // x out, timings, stats (synchronises the stream)
+  ps_status finish(ps_stats* stats) {
+    cudaStream_t st = h->st;
+    const bool host = h->prm.host_ptrs != 0;
+    PS_CUDA(cudaMemcpyAsync(x, h->x, sizeof(double) * h->n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            st));
+    cudaEventRecord(e1, st);
+    PS_CUDA(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&S.ms_solve, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
+    S.ms_setup_u = h->ms_setup_u;
+    S.ms_setup_f = h->ms_setup_f;
+    S.handle_bytes = h->ar.bytes + h->arf.bytes;
+    S.levels_u = int32_t(h->amg_u.L.size());
+    S.levels_p = int32_t(h->amg_p.L.size());
+    if (stats) *stats = S;
+    return result;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
 ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_stats* stats) {
   if (!h || !rhs || !x || !(tol > 0.0)) return PS_ERR_INVALID;
   if (h->prm.solver == PS_SOLVER_RICHARDSON) return solve_richardson(h, rhs, x, tol, stats);
-  cudaStream_t st = h->st;
-  int64_t n = h->n;
-  int m = h->m;
-  KrylovState& K = h->K;
-  bool host = h->prm.host_ptrs != 0;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, st);
-  PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-  double* xk = h->x;
-  fill_zero(xk, n, st);
-  const int64_t ldv = h->ldv;
-  if (ldv > n)  // padding rows of the basis (a failed solve may have left a NaN there)
-    PS_CUDA(cudaMemset2DAsync(h->V + n, size_t(ldv) * sizeof(double), 0, size_t(ldv - n) * sizeof(double), m + 1, st));
-  // ||b||
-  multidot(h->V, n, 0, h->b, n, h->mpart, K.sc + 7, 1, nullptr, st);
-  PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  PS_CUDA(cudaStreamSynchronize(st));
-  double bn2 = h->hsc[7];
-  ps_stats S;
-  std::memset(&S, 0, sizeof(S));
-  ps_status result = PS_OK;
-  if (!(bn2 > 0.0)) {
-    if (std::isnan(bn2)) result = PS_ERR_NAN;
-  } else {
-    double bnorm = std::sqrt(bn2);
-    double hb[2] = {bn2, bnorm};
-    PS_CUDA(cudaMemcpyAsync(K.sc + 3, &hb[0], sizeof(double), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(K.sc + 7, &hb[1], sizeof(double), cudaMemcpyHostToDevice, st));
-    PS_CUDA(cudaMemcpyAsync(h->r, h->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    int total = 0;
-    for (;;) {
-      cycle_start(K, m, st);
-      scale_vec(h->r, h->V, n, K.sc + 4, st);
-      int jend = -1;
-      bool brk = false, nanf = false, timeout = false, gs_timeout = false;
-      for (int j = 0; j < m; ++j) {
-        double* vj = h->V + j * ldv;
-        double* zj = h->Z + int64_t(j) * n;
-        double* w = h->V + (j + 1) * ldv;
-        cudaEventRecord(h->ev[0], st);
-        PS_TRY(apply_prec(h, vj, zj));
-        cudaEventRecord(h->ev[1], st);
-        jac_spmv(h->J, zj, w, nullptr, nullptr, st);
-        cudaEventRecord(h->ev[2], st);
-        if (h->prm.ortho == PS_ORTHO_MGS &&
-            mgs_step(h->V, ldv, j, w, n, K, h->mgs_part, h->mgs_blocks, h->mgs_bar, &h->mgs_base, h->prm.spin_limit,
-                     h->prm.test_stall_gs, h->prm.ortho_sweep, st)) {
-          // modified Gram-Schmidt (w normalised in the same launch)
-          arnoldi_finish(K, m, j, st);
-        } else {
-          // classical Gram-Schmidt with selective reorthogonalisation
-          multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h1, 1, nullptr, st);
-          PS_CUDA(cudaMemcpyAsync(K.sc + 0, K.h1 + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
-          mupdate(h->V, ldv, j + 1, K.h1, w, n, h->mpart, K.sc + 1, nullptr, st);
-          arnoldi_check(K, st);
-          multidot(h->V, ldv, j + 1, w, n, h->mpart, K.h2, 0, K.flag, st);
-          mupdate(h->V, ldv, j + 1, K.h2, w, n, h->mpart, K.sc + 2, K.flag, st);
-          arnoldi_finish(K, m, j, st);
-          scale_vec(w, w, n, K.sc + 4, st);
-        }
-        cudaEventRecord(h->ev[3], st);
-        ++total;
-        PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h->hflag, K.flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaMemcpyAsync(h->hflag + 3, h->F.ilu_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaStreamSynchronize(st));
-        double est = h->hsc[5], hn = h->hsc[6];
-        {
-          float a = 0, b = 0, c = 0;
-          cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
-          cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
-          cudaEventElapsedTime(&c, h->ev[2], h->ev[3]);
-          S.ms_prec += a; S.ms_spmv += b; S.ms_orth += c;
-          float f[4] = {0, 0, 0, 0};
-          for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&f[q], h->fe[q], h->fe[q + 1]);
-          S.ms_vcycle_u += f[0]; S.ms_flow24 += f[1]; S.ms_vcycle_p += f[2]; S.ms_ilu += f[3];
-        }
-        S.est_relres = est;
-        jend = j;
-        S.reorth += h->hflag[0];
-        if (h->hflag[3]) { timeout = true; break; }
-        if (h->hflag[2]) { gs_timeout = true; break; }
-        if (h->hflag[1]) { nanf = true; break; }
-        if (!(hn > 1e-300 * bnorm)) brk = true;
-        if (est <= tol || brk || total >= h->prm.max_iters) break;
-      }
-      if (timeout || gs_timeout) {
-        if (h->hflag[3]) PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
-        if (h->hflag[2]) {
-          // the barrier counter is left mid-count: start it again from zero
-          PS_CUDA(cudaMemsetAsync(K.flag + 2, 0, sizeof(int), st));
-          PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
-          h->mgs_base = 0;
-        }
-        set_reason(timeout ? "a bounded wait of the wavefront ILU(0) sweep gave up"
-                           : "a bounded grid barrier wait of the Gram-Schmidt step gave up");
-        result = PS_ERR_TIMEOUT;
-        break;
-      }
-      if (nanf) { result = PS_ERR_NAN; break; }
-      hessenberg_solve(K, m, jend, st);
-      maxpy(h->Z, n, jend + 1, K.y, xk, n, st);
-      jac_spmv(h->J, xk, h->r, h->b, h->part, st);
-      finish_sum(h->part, K.sc + 3, st);
-      PS_CUDA(cudaMemcpyAsync(h->hsc, K.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      PS_CUDA(cudaStreamSynchronize(st));
-      double rr = std::sqrt(h->hsc[3]) / bnorm;
-      S.true_relres = rr;
-      S.iters = total;
-      if (std::isnan(rr)) { result = PS_ERR_NAN; break; }
-      if (rr <= tol) { result = PS_OK; break; }
-      if (brk) { result = PS_ERR_BREAKDOWN; break; }
-      if (total >= h->prm.max_iters) { result = PS_ERR_NOT_CONVERGED; break; }
-      S.restarts++;
-    }
+  FgmresRun run;
+  PS_TRY(run.start(h, rhs, x, tol));
+  while (!run.done) {
+    PS_TRY(run.enqueue());
+    PS_CUDA(cudaStreamSynchronize(h->st));
+    PS_TRY(run.after_sync());
   }
-  PS_CUDA(cudaMemcpyAsync(x, xk, sizeof(double) * n, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-  cudaEventRecord(e1, st);
-  PS_CUDA(cudaEventSynchronize(e1));
-  cudaEventElapsedTime(&S.ms_solve, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  S.ms_setup_u = h->ms_setup_u;
-  S.ms_setup_f = h->ms_setup_f;
-  S.handle_bytes = h->ar.bytes + h->arf.bytes;
-  S.levels_u = int32_t(h->amg_u.L.size());
-  S.levels_p = int32_t(h->amg_p.L.size());
-  if (stats) *stats = S;
-  return result;
+  return run.finish(stats);
 }
 
 int32_t ps_amg_nlevels(ps_handle* h, int32_t which) {
@@ -759,7 +832,93 @@ void ps_free(ps_handle* h) {
     if (h->fe[e]) cudaEventDestroy(h->fe[e]);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hflag) cudaFreeHost(h->hflag);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
+}
+
+ps_status ps_setup_batch(int32_t n, const ps_jacobian* jac, const ps_grid* grid, const ps_params* params,
+                         ps_handle** out) {
+  if (n < 0 || (n > 0 && (!jac || !grid || !params || !out))) return PS_ERR_INVALID;
+  for (int32_t i = 0; i < n; ++i) out[i] = nullptr;
+  std::vector<ps_status> st(n, PS_OK);
+  std::atomic<int32_t> next{0};
+  auto worker = [&]() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (;;) {
+      const int32_t i = next.fetch_add(1);
+      if (i >= n) return;
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        st[i] = PS_ERR_CUDA;
+        continue;
+      }
+      ps_params p = *params;
+      p.stream = s;
+      st[i] = ps_setup(&jac[i], &grid[i], &p, &out[i]);
+      if (st[i] == PS_OK) out[i]->own_stream = true;
+      else cudaStreamDestroy(s);
+    }
+  };
+  int dev = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  const int nthreads = std::min<int32_t>(n, 8);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t)
+    pool.emplace_back([&, dev]() {
+      cudaSetDevice(dev);
+      worker();
+    });
+  for (auto& t : pool) t.join();
+  for (int32_t i = 0; i < n; ++i)
+    if (st[i] != PS_OK) {
+      for (int32_t k = 0; k < n; ++k) {
+        ps_free(out[k]);
+        out[k] = nullptr;
+      }
+      return st[i];
+    }
+  return PS_OK;
+}
+
+ps_status ps_solve_batch(int32_t n, ps_handle* const* h, const double* const* rhs, double* const* x, double tol,
+                         ps_stats* stats) {
+  if (n < 0 || (n > 0 && (!h || !rhs || !x)) || !(tol > 0.0)) return PS_ERR_INVALID;
+  for (int32_t i = 0; i < n; ++i)
+    if (!h[i] || !rhs[i] || !x[i]) return PS_ERR_INVALID;
+  ps_status first = PS_OK;
+  std::vector<FgmresRun> runs(n);
+  std::vector<char> lockstep(n, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    if (h[i]->prm.solver == PS_SOLVER_RICHARDSON) {
+      ps_status s = ps_solve(h[i], rhs[i], x[i], tol, stats ? &stats[i] : nullptr);
+      if (first == PS_OK && s != PS_OK) first = s;
+      continue;
+    }
+    lockstep[i] = 1;
+    PS_TRY(runs[i].start(h[i], rhs[i], x[i], tol));
+  }
+  for (;;) {
+    bool any = false;
+    for (int32_t i = 0; i < n; ++i)
+      if (lockstep[i] && !runs[i].done) {
+        PS_TRY(runs[i].enqueue());
+        any = true;
+      }
+    if (!any) break;
+    for (int32_t i = 0; i < n; ++i)
+      if (lockstep[i] && !runs[i].done) {
+        PS_CUDA(cudaStreamSynchronize(h[i]->st));
+        PS_TRY(runs[i].after_sync());
+      }
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (lockstep[i]) {
+      ps_status s = runs[i].finish(stats ? &stats[i] : nullptr);
+      if (first == PS_OK && s != PS_OK) first = s;
+    }
+  return first;
 }
 
 const char* ps_strerror(ps_status s) {
