@@ -63,8 +63,11 @@ def test_true_impes_hierarchy_and_apply(cfg, kw, cm):
 
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
 def test_true_impes_solve(prec):
+    # (on the channelised 21x44x17 slab and the full 64x64x32 grid the true-IMPES reduction stalls in
+    # the oracle as well as on the GPU: its D_ss keeps only the accumulation term, far below the upstream
+    # flux derivatives of the high-permeability cells; the test uses a grid where it converges)
     g = _g()
-    osys = oracle.System(oracle.default_params(2, nx=21, ny=44, nz=17))
+    osys = oracle.System(oracle.default_params(1, nx=24, ny=20, nz=10))
     P = oracle.Prec(osys, oracle.default_prec_params(cpr_reduction=oracle.CPR_TRUE_IMPES))
     xo, _ = P.fgmres(tol=1e-12)
     _, sto8 = P.fgmres(tol=1e-8)
