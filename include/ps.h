@@ -161,9 +161,15 @@ void ps_params_default(ps_params* p);
 ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params* params,
                    ps_handle** out);
 
-/* Rebuild the flow stage (S_ff^(FS), S_pp, pressure AMG, ILU(0)) from new A_fu,
-   A_ff and d_fs values with unchanged patterns, keeping the mechanics AMG: the
-   per-Newton flow setup of §5.2/§5.4. */
+/* Per-Newton flow setup of §5.4: new A_fu, A_ff and d_fs values (patterns as
+   given to ps_setup) rebuild the flow stage (S_ff^(FS), S_pp, pressure AMG,
+   local stage) while the mechanics AMG built by ps_setup is kept.  When
+   jac->A_uu.val and jac->A_uf.val are non-NULL their new values (same
+   patterns) replace the stored ones for the outer Jacobian SpMV; NULL keeps
+   the stored values.  The stored Jacobian then is the new one throughout,
+   so ps_solve solves the new system.  A row-sum-lumped fixed-stress diagonal
+   (PS_FS_RSL) keeps the M_uu^{-1} A_up e vector of ps_setup and applies the
+   new A_fu to it.  Errors: PS_ERR_INVALID (shape or pattern change). */
 ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac);
 
 /* Testing only: set ps_params.test_stall_wave on an existing handle (0 = off). */
@@ -185,12 +191,13 @@ ps_status ps_solve(ps_handle* h, const double* rhs, double* x, double tol, ps_st
 ps_status ps_setup_batch(int32_t n, const ps_jacobian* jac, const ps_grid* grid, const ps_params* params,
                          ps_handle** out);
 
-/* Batched iteration phase: the FGMRES solves of n handles (rhs[i], x[i] as in ps_solve) advanced in
-   lockstep, one Arnoldi step (or cycle end) of every unfinished system per round, each on its handle's
-   stream, with one host synchronisation per round for all of them.  Each system runs the kernels of
-   ps_solve in the same order, so x[i] equals what ps_solve gives for it.  stats[i] (may be NULL) gets each
-   system's statistics; the first non-OK status is returned.  Handles with the Richardson solver are
-   solved one after another. */
+/* Batched iteration phase: the FGMRES solves of n handles (rhs[i], x[i] as in ps_solve).  The systems
+   are dealt round-robin to up to eight host threads; each thread advances its group in lockstep, one
+   Arnoldi step (or cycle end) of every unfinished system per round, each on its handle's stream, with
+   one host synchronisation per round for the group.  Each system runs the kernels of ps_solve in the
+   same order, so x[i] equals what ps_solve gives for it.  stats[i] (may be NULL) gets each system's
+   statistics; the first non-OK status in system order is returned.  Handles with the Richardson solver
+   are solved whole by their group's thread.  Handles must be distinct. */
 ps_status ps_solve_batch(int32_t n, ps_handle* const* h, const double* const* rhs, double* const* x, double tol,
                          ps_stats* stats);
 

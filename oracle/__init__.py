@@ -124,6 +124,8 @@ def lib(openmp=None):
         L.or_residual.argtypes = [C.POINTER(GenParams), _PD, _PD]
         L.or_default_prec_params.argtypes = [C.POINTER(PrecParams)]
         L.or_prec_setup.argtypes = [C.POINTER(_System), C.POINTER(PrecParams), C.POINTER(C.c_void_p)]
+        L.or_prec_setup_reuse.argtypes = [C.POINTER(_System), C.POINTER(_System), C.POINTER(PrecParams),
+                                           C.POINTER(C.c_void_p)]
         L.or_prec_free.argtypes = [C.c_void_p]
         L.or_prec_apply.argtypes = [C.c_void_p, _PD, _PD]
         L.or_amg_nlevels.argtypes = [C.c_void_p, C.c_int]
@@ -260,12 +262,17 @@ def default_prec_params(**kw):
 
 
 class Prec:
-    def __init__(self, system, pp=None):
+    def __init__(self, system, pp=None, mech_system=None):
+        """mech_system: build M_uu from that system's A_uu instead (flow-setup reuse of §5.4)."""
         self.system = system
+        self.mech_system = mech_system
         self.pp = pp if pp is not None else default_prec_params()
         h = C.c_void_p()
         self._L = system._L
-        rc = self._L.or_prec_setup(system._ptr, C.byref(self.pp), C.byref(h))
+        if mech_system is not None:
+            rc = self._L.or_prec_setup_reuse(system._ptr, mech_system._ptr, C.byref(self.pp), C.byref(h))
+        else:
+            rc = self._L.or_prec_setup(system._ptr, C.byref(self.pp), C.byref(h))
         if rc:
             raise RuntimeError("or_prec_setup failed: %d" % rc)
         self._h = h

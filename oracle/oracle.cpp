@@ -1565,6 +1565,11 @@ void or_default_prec_params(or_prec_params* pp) {
 }
 
 int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
+  return or_prec_setup_reuse(s, s, pp, out);
+}
+
+int or_prec_setup_reuse(const or_system* s, const or_system* mech, const or_prec_params* pp, or_prec** out) {
+  if (mech->n_nodes != s->n_nodes || mech->nnzb_uu != s->nnzb_uu) return 4;
   or_prec* P = new or_prec();
   P->s = s; P->pp = *pp;
   int64_t nc = s->n_cells, nn = s->n_nodes;
@@ -1573,10 +1578,11 @@ int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
   BSR Auu = to_bsr(s, 0);
   // §5.2: M_uu = amg(A_uu^(SDC)), three displacement components, shared aggregates
   if (pp->mech_mode == OR_MECH_AMG) {
-    CSR A0; A0.n = A0.m = nn; A0.nc = 3; A0.rp = Auu.rp; A0.ci = Auu.ci;
-    A0.v.resize(Auu.ci.size() * 3);
-    for (size_t q = 0; q < Auu.ci.size(); ++q)
-      for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = Auu.v[q * 9 + d * 4];
+    BSR AuuM = to_bsr(mech, 0);
+    CSR A0; A0.n = A0.m = nn; A0.nc = 3; A0.rp = AuuM.rp; A0.ci = AuuM.ci;
+    A0.v.resize(AuuM.ci.size() * 3);
+    for (size_t q = 0; q < AuuM.ci.size(); ++q)
+      for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = AuuM.v[q * 9 + d * 4];
     if (!build_amg(P->amg_u, std::move(A0), pp->theta_u, pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
   } else {
     vec d(size_t(s->n_u) * s->n_u, 0.0);

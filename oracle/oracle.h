@@ -139,6 +139,9 @@ typedef struct or_prec or_prec;
 
 void or_default_prec_params(or_prec_params* pp);
 int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out);
+/* the same with the mechanics AMG M_uu built from mech's A_uu (same grid): the flow-setup reuse of §5.4,
+   where M_uu is built once and kept while the Jacobian changes from one Newton step to the next */
+int or_prec_setup_reuse(const or_system* s, const or_system* mech, const or_prec_params* pp, or_prec** out);
 void or_prec_free(or_prec* p);
 void or_prec_apply(or_prec* p, const double* v, double* z);
 

@@ -67,6 +67,7 @@ struct ps_handle {
   ps_params prm;
   ps_grid grid;
   int64_t nn = 0, nc = 0, nu = 0, nf = 0, n = 0;
+  int64_t nnzb_uu = 0, nnzb_uf = 0, nnzb_fu = 0;  // block patterns given to ps_setup
   bool mixed = false;
   bool bf16p = false;  // BF16 transfer operators (PS_MIXED_BF16P)
   JacDev J;
@@ -405,6 +406,7 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   h->arf.stream = h->st;
   h->ar.budget = params->hbm_budget;
   h->nn = nn; h->nc = nc; h->nu = 3 * nn; h->nf = 2 * nc; h->n = h->nu + h->nf;
+  h->nnzb_uu = jac->A_uu.nnzb; h->nnzb_uf = jac->A_uf.nnzb; h->nnzb_fu = jac->A_fu.nnzb;
   h->mixed = params->precision == PS_MIXED_FP32 || params->precision == PS_MIXED_BF16P;
   h->bf16p = params->precision == PS_MIXED_BF16P;
   h->m = params->restart;
@@ -433,14 +435,30 @@ ps_status ps_set_test_stall_gs(ps_handle* h, int32_t cta_plus_one) {
 ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   if (!h || !jac) return PS_ERR_INVALID;
   if (!bsr_ok(jac->A_fu, h->nc, h->nn, 2, 3) || !bsr_ok(jac->A_ff, h->nc, h->nc, 2, 2) || !jac->d_fs ||
-      jac->A_ff.nnzb != h->F.nnzb)
+      jac->A_ff.nnzb != h->F.nnzb || jac->A_fu.nnzb != h->nnzb_fu) {
+    set_reason("ps_setup_flow: A_fu, A_ff and d_fs must keep the patterns given to ps_setup");
     return PS_ERR_INVALID;
+  }
+  // new mechanics-row values are optional: A_uu and A_uf with the setup's patterns, used by the outer
+  // Jacobian SpMV; the mechanics AMG built at ps_setup is kept either way
+  const bool new_uu = jac->A_uu.val != nullptr, new_uf = jac->A_uf.val != nullptr;
+  if ((new_uu && (!bsr_ok(jac->A_uu, h->nn, h->nn, 3, 3) || jac->A_uu.nnzb != h->nnzb_uu)) ||
+      (new_uf && (!bsr_ok(jac->A_uf, h->nn, h->nc, 3, 2) || jac->A_uf.nnzb != h->nnzb_uf))) {
+    set_reason("ps_setup_flow: A_uu and A_uf, when given, must keep the patterns given to ps_setup");
+    return PS_ERR_INVALID;
+  }
   cudaStream_t st = h->st;
   bool host = h->prm.host_ptrs != 0;
   auto kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (new_uu)
+    PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.uu_v), jac->A_uu.val, sizeof(double) * h->nnzb_uu * 9, kind, st));
+  if (new_uf)
+    PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.uf_v), jac->A_uf.val, sizeof(double) * h->nnzb_uf * 6, kind, st));
   PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.fu_v), jac->A_fu.val, sizeof(double) * jac->A_fu.nnzb * 6, kind, st));
   PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.ff_v), jac->A_ff.val, sizeof(double) * jac->A_ff.nnzb * 4, kind, st));
   PS_CUDA(cudaMemcpyAsync(h->dfs, jac->d_fs, sizeof(double) * 2 * h->nc, kind, st));
+  // the outer SpMV reads the stencil-indexed copies: refill them from the new values
+  PS_TRY(jac_refresh_stencil(h->ar, h->J, (new_uu ? 1 : 0) | (new_uf ? 2 : 0) | 4 | 8, st));
   cudaStreamSynchronize(st);
   amg_release_graph(h->amg_p);
   h->arf.free_all();
@@ -887,38 +905,54 @@ ps_status ps_solve_batch(int32_t n, ps_handle* const* h, const double* const* rh
   if (n < 0 || (n > 0 && (!h || !rhs || !x)) || !(tol > 0.0)) return PS_ERR_INVALID;
   for (int32_t i = 0; i < n; ++i)
     if (!h[i] || !rhs[i] || !x[i]) return PS_ERR_INVALID;
-  ps_status first = PS_OK;
+  std::vector<ps_status> res(n, PS_OK);
   std::vector<FgmresRun> runs(n);
-  std::vector<char> lockstep(n, 0);
-  for (int32_t i = 0; i < n; ++i) {
-    if (h[i]->prm.solver == PS_SOLVER_RICHARDSON) {
-      ps_status s = ps_solve(h[i], rhs[i], x[i], tol, stats ? &stats[i] : nullptr);
-      if (first == PS_OK && s != PS_OK) first = s;
-      continue;
+  // systems are dealt round-robin to up to eight host threads; each thread advances its group in lockstep,
+  // one step of every unfinished system per round and one synchronisation per round, so the launch work of
+  // the groups proceeds in parallel
+  const int nthreads = std::min<int32_t>(n, 8);
+  int dev = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  auto group = [&](int t) -> void {
+    cudaSetDevice(dev);
+    std::vector<int32_t> mine;
+    for (int32_t i = t; i < n; i += nthreads) {
+      if (h[i]->prm.solver == PS_SOLVER_RICHARDSON) {
+        res[i] = ps_solve(h[i], rhs[i], x[i], tol, stats ? &stats[i] : nullptr);
+        continue;
+      }
+      res[i] = runs[i].start(h[i], rhs[i], x[i], tol);
+      if (res[i] == PS_OK) mine.push_back(i);
     }
-    lockstep[i] = 1;
-    PS_TRY(runs[i].start(h[i], rhs[i], x[i], tol));
-  }
-  for (;;) {
-    bool any = false;
-    for (int32_t i = 0; i < n; ++i)
-      if (lockstep[i] && !runs[i].done) {
-        PS_TRY(runs[i].enqueue());
-        any = true;
-      }
-    if (!any) break;
-    for (int32_t i = 0; i < n; ++i)
-      if (lockstep[i] && !runs[i].done) {
-        PS_CUDA(cudaStreamSynchronize(h[i]->st));
-        PS_TRY(runs[i].after_sync());
-      }
-  }
+    std::vector<char> failed(n, 0);
+    for (;;) {
+      bool any = false;
+      for (int32_t i : mine)
+        if (!runs[i].done && !failed[i]) {
+          ps_status e = runs[i].enqueue();
+          if (e != PS_OK) { res[i] = e; failed[i] = 1; continue; }
+          any = true;
+        }
+      if (!any) break;
+      for (int32_t i : mine)
+        if (!runs[i].done && !failed[i]) {
+          cudaError_t ce = cudaStreamSynchronize(h[i]->st);
+          if (ce != cudaSuccess) { set_last_error(ce, "cudaStreamSynchronize", __FILE__, __LINE__); res[i] = PS_ERR_CUDA; failed[i] = 1; continue; }
+          ps_status e = runs[i].after_sync();
+          if (e != PS_OK) { res[i] = e; failed[i] = 1; }
+        }
+    }
+    for (int32_t i : mine) {
+      ps_status e = runs[i].finish(stats ? &stats[i] : nullptr);
+      if (!failed[i]) res[i] = e;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(group, t);
+  for (auto& th : pool) th.join();
   for (int32_t i = 0; i < n; ++i)
-    if (lockstep[i]) {
-      ps_status s = runs[i].finish(stats ? &stats[i] : nullptr);
-      if (first == PS_OK && s != PS_OK) first = s;
-    }
-  return first;
+    if (res[i] != PS_OK) return res[i];
+  return PS_OK;
 }
 
 const char* ps_strerror(ps_status s) {

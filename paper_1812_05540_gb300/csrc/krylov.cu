@@ -774,6 +774,22 @@ ps_status jac_build_stencil(Arena& ar, JacDev& J, bool* ok, cudaStream_t st) {
   return PS_OK;
 }
 
+ps_status jac_refresh_stencil(Arena& ar, JacDev& J, int mask, cudaStream_t st) {
+  if (!J.uu_s) return PS_OK;
+  Geo g{J.nx, J.ny, J.nz};
+  int* bad;
+  PS_TRY(ar.alloc(&bad, 1));
+  PS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  if (mask & 1) { PS_TICK(); k_to_stencil<0, 27, 9><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uu_rp, J.uu_ci, J.uu_v, J.uu_s, bad); }
+  if (mask & 2) { PS_TICK(); k_to_stencil<1, 8, 6><<<grid_for(J.nn, 256), 256, 0, st>>>(g, J.nn, J.uf_rp, J.uf_ci, J.uf_v, J.uf_s, bad); }
+  if (mask & 4) { PS_TICK(); k_to_stencil<2, 8, 6><<<grid_for(J.nc, 256), 256, 0, st>>>(g, J.nc, J.fu_rp, J.fu_ci, J.fu_v, J.fu_s, bad); }
+  if (mask & 8) { PS_TICK(); k_to_stencil<3, 7, 4><<<grid_for(J.nc, 256), 256, 0, st>>>(g, J.nc, J.ff_rp, J.ff_ci, J.ff_v, J.ff_s, bad); }
+  PS_CUDA(cudaGetLastError());
+  PS_CUDA(cudaStreamSynchronize(st));
+  ar.release(bad);
+  return PS_OK;
+}
+
 void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, double* part, cudaStream_t st) {
   if (J.uu_s) {
     int64_t gu = ceil_div(J.nn, 256), gf = ceil_div(J.nc, 256);

@@ -24,6 +24,9 @@ constexpr int kRedBlocks = 1024;
 void jac_spmv(const JacDev& J, const double* x, double* y, const double* b, double* part, cudaStream_t st);
 // build the stencil-indexed copies; returns false (and leaves them null) if a pattern is not structured
 ps_status jac_build_stencil(Arena& ar, JacDev& J, bool* ok, cudaStream_t st);
+// refill existing stencil-indexed copies from the CSR values (same patterns); mask bit k = block k of
+// (A_uu, A_uf, A_fu, A_ff)
+ps_status jac_refresh_stencil(Arena& ar, JacDev& J, int mask, cudaStream_t st);
 
 // h[c] = V[:,c] . w for c < m (V column-major, leading dimension ldv); also
 // ||w||^2 into h[m] when with_norm.  Partials in part (m+1 x kRedBlocks), result in h.

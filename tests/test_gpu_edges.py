@@ -133,3 +133,38 @@ def test_setup_flow_rebuild_matches_fresh_setup(sysd):
         assert torch.equal(x1, x2)
     finally:
         ps.ps_free(h)
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+def test_setup_flow_with_the_next_newton_jacobian_matches_oracle(prec):
+    # §5.4 flow-setup reuse against the oracle: the handle is set up on one Jacobian, then ps_setup_flow gets
+    # the next Newton state's blocks (all four, so the outer SpMV is the new operator) and keeps the mechanics
+    # AMG of the first; the oracle builds M_uu from the first Jacobian and the rest from the second
+    from tests import _gpu as g
+    import oracle
+    kw = dict(nx=24, ny=20, nz=10)
+    s1 = oracle.System(oracle.default_params(1, **kw))
+    s2 = oracle.System(oracle.default_params(1, dp_amp=2e6, **kw))
+    R = oracle.Prec(s2, mech_system=s1)
+    xo, _ = R.fgmres(tol=1e-12)
+    _, sto8 = R.fgmres(tol=1e-8)
+    d1, d2 = g.to_device(s1), g.to_device(s2)
+    h = ps.ps_setup(d1.jac, d1.grid, ps.ps_params_default(precision=prec))
+    try:
+        ps.ps_setup_flow(h, d2.jac)
+        if prec == ps.PS_FP64:
+            vs = np.random.default_rng(9).standard_normal(s2.n)
+            v = torch.from_numpy(vs).cuda()
+            z = torch.empty_like(v)
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            zo = R.apply(vs)
+            assert np.linalg.norm(z.cpu().numpy() - zo) <= 1e-10 * np.linalg.norm(zo)
+        x = torch.zeros(s2.n, dtype=torch.float64, device="cuda")
+        _, st = ps.ps_solve(h, d2.rhs.data_ptr(), x.data_ptr(), 1e-8)
+    finally:
+        ps.ps_free(h)
+    xs = x.cpu().numpy()
+    relres = np.linalg.norm(s2.rhs - s2.spmv(xs)) / np.linalg.norm(s2.rhs)
+    assert relres <= 1e-8 and abs(relres - st.true_relres) <= 1e-10
+    assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert abs(st.iters - sto8.iters) <= max(1, int(0.1 * sto8.iters) + 1), (st.iters, sto8.iters)

@@ -329,3 +329,21 @@ def test_l1_jacobi_smoother_error_factor(sweeps):
         g = (1.0 - lam / (4.0 + eps)) ** sweeps
         x = oracle.smoother_apply(rp, ci, v, A @ vk, 0, sweeps)
         assert np.allclose(x, (1.0 - g) * vk, rtol=0, atol=1e-12)
+
+
+def test_reuse_keeps_the_mechanics_hierarchy_and_takes_the_new_flow_stage():
+    # flow-setup reuse (§5.4): M_uu built from one Jacobian, everything else from the next Newton step's
+    kw = dict(nx=8, ny=7, nz=5)
+    s1 = oracle.System(oracle.default_params(1, **kw))
+    s2 = oracle.System(oracle.default_params(1, dp_amp=2e6, **kw))
+    assert not np.array_equal(s1.blocks["uu"][2], s2.blocks["uu"][2])
+    assert not np.array_equal(s1.blocks["ff"][2], s2.blocks["ff"][2])
+    P1, P2 = oracle.Prec(s1), oracle.Prec(s2)
+    R = oracle.Prec(s2, mech_system=s1)
+    b = np.random.default_rng(0).standard_normal(s1.n_nodes)
+    for c in range(3):
+        assert np.array_equal(R.vcycle(0, c, b), P1.vcycle(0, c, b))
+    assert np.array_equal(R.spp()[2], P2.spp()[2])
+    assert np.array_equal(R.vcycle(1, 0, b[:s2.n_cells]), P2.vcycle(1, 0, b[:s2.n_cells]))
+    x, st = R.fgmres(tol=1e-8)
+    assert st.converged and np.linalg.norm(s2.rhs - s2.spmv(x)) <= 1e-8 * np.linalg.norm(s2.rhs)
