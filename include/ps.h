@@ -145,6 +145,8 @@ typedef struct {
   int32_t reorth;                   /* Arnoldi steps that needed the second Gram-Schmidt pass */
   float ms_vcycle_u, ms_flow24, ms_vcycle_p, ms_ilu;  /* parts of ms_prec: Algorithm 1 step 1, steps
                                                           2-4, step 5, steps 6-8 */
+  float ms_copy_in;                 /* part of ms_setup_u: copying the four Jacobian blocks and d_fs into
+                                       the handle (host to device with host_ptrs = 1) */
 } ps_stats;
 
 typedef struct ps_handle ps_handle;

@@ -62,7 +62,8 @@ class ps_stats(C.Structure):
                 ("ms_solve", C.c_float), ("bytes_model", C.c_int64), ("handle_bytes", C.c_int64),
                 ("levels_u", C.c_int32), ("levels_p", C.c_int32), ("ms_prec", C.c_float), ("ms_spmv", C.c_float),
                 ("ms_orth", C.c_float), ("reorth", C.c_int32), ("ms_vcycle_u", C.c_float),
-                ("ms_flow24", C.c_float), ("ms_vcycle_p", C.c_float), ("ms_ilu", C.c_float)]
+                ("ms_flow24", C.c_float), ("ms_vcycle_p", C.c_float), ("ms_ilu", C.c_float),
+                ("ms_copy_in", C.c_float)]
 
 
 class ps_server_params(C.Structure):

@@ -104,8 +104,11 @@ ps_status amg_vcycle_direct(Amg& H, const SmoothParams& sp, const T* b, T* x, cu
 template <class T>
 ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st);
 
-// SpMV lane choice from the mean row length
+// SpMV lane choice from the mean row length (rows of a few entries, as in the level-0 prolongators, take
+// one or two threads each)
 inline int lanes_for(double mean_row) {
+  if (mean_row <= 4) return 1;
+  if (mean_row <= 8) return 2;
   if (mean_row <= 16) return 4;
   if (mean_row <= 48) return 8;
   if (mean_row <= 192) return 16;

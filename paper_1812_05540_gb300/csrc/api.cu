@@ -93,7 +93,7 @@ struct ps_handle {
   double* mgs_part = nullptr;
   unsigned long long* mgs_bar = nullptr;
   unsigned long long mgs_base = 0;
-  float ms_setup_u = 0, ms_setup_f = 0;
+  float ms_setup_u = 0, ms_setup_f = 0, ms_copy_in = 0;
   int64_t spmv_part = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-iteration phase timers
   cudaEvent_t fe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // Algorithm 1 sub-phase timers
@@ -261,6 +261,14 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(copy_bsr(h, jac->A_fu, &J.fu_rp, &J.fu_ci, &J.fu_v));
   PS_TRY(copy_bsr(h, jac->A_ff, &J.ff_rp, &J.ff_ci, &J.ff_v));
   PS_TRY(copy_in(ar, jac->d_fs, sizeof(double) * 2 * h->nc, (void**)&h->dfs, h->prm.host_ptrs != 0, st));
+  {
+    cudaEvent_t ec;
+    cudaEventCreate(&ec);
+    cudaEventRecord(ec, st);
+    PS_CUDA(cudaEventSynchronize(ec));
+    cudaEventElapsedTime(&h->ms_copy_in, e0, ec);
+    cudaEventDestroy(ec);
+  }
   J.nx = h->grid.nx; J.ny = h->grid.ny; J.nz = h->grid.nz;
   bool structured = false;
   PS_TRY(jac_build_stencil(ar, J, &structured, st));
@@ -557,6 +565,7 @@ ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double to
   cudaEventDestroy(e1);
   S.ms_setup_u = h->ms_setup_u;
   S.ms_setup_f = h->ms_setup_f;
+  S.ms_copy_in = h->ms_copy_in;
   S.handle_bytes = h->ar.bytes + h->arf.bytes;
   S.levels_u = int32_t(h->amg_u.L.size());
   S.levels_p = int32_t(h->amg_p.L.size());
@@ -746,6 +755,8 @@ struct FgmresRun {
     e0 = e1 = nullptr;
     S.ms_setup_u = h->ms_setup_u;
     S.ms_setup_f = h->ms_setup_f;
+    S.ms_copy_in = h->ms_copy_in;
+  S.ms_copy_in = h->ms_copy_in;
     S.handle_bytes = h->ar.bytes + h->arf.bytes;
     S.levels_u = int32_t(h->amg_u.L.size());
     S.levels_p = int32_t(h->amg_p.L.size());

@@ -271,6 +271,8 @@ void with_rows(const AmgLevel& L, const LevelT<T>& V, F&& f) {
     }
   }
   switch (L.lanes) {
+    case 1: f(CsrRows<T, NC, 1>{L.rp, L.ci, V.v}); break;
+    case 2: f(CsrRows<T, NC, 2>{L.rp, L.ci, V.v}); break;
     case 4: f(CsrRows<T, NC, 4>{L.rp, L.ci, V.v}); break;
     case 8: f(CsrRows<T, NC, 8>{L.rp, L.ci, V.v}); break;
     case 16: f(CsrRows<T, NC, 16>{L.rp, L.ci, V.v}); break;
@@ -324,7 +326,9 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
     ChebCoef cc = cheb_coef(L, NC, sp);
     int deg = sp.degree < 1 ? 1 : (sp.degree > 8 ? 8 : sp.degree);
     int k0 = 1;
-    if (deg > 1 && L.dsi) {
+    // the fused pair reads b and D^{-1}/theta at every stencil neighbour instead of one iterate; on the
+    // 27-point three-component level that doubles the gathered bytes, so there the first step stays apart
+    if (deg > 1 && L.dsi && !(NC == 3 && V.sv)) {
       // steps 0 and 1 in one pass
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
@@ -400,6 +404,8 @@ template <class T, int NC, class TV>
 void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const TV* v, const T* x, T* y, int add,
                 cudaStream_t st) {
   switch (lanes) {
+    case 1: PS_TICK(); k_spmv<T, NC, 1, TV><<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 2: PS_TICK(); k_spmv<T, NC, 2, TV><<<grid_for(n * 2, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
     case 4: PS_TICK(); k_spmv<T, NC, 4, TV><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
     case 8: PS_TICK(); k_spmv<T, NC, 8, TV><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
     case 16: PS_TICK(); k_spmv<T, NC, 16, TV><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
