@@ -562,6 +562,17 @@ def run_ours(args):
             hjac = ps.ps_jacobian(blocks[0], blocks[1], blocks[2], blocks[3], dfs.data_ptr(), None)
 
             host_parts = []
+            # the same pinned A_uu values copied by torch, for the copy rate of the host link on this machine
+            vuu = host[0][2]
+            dvu = torch.empty_like(vuu, device="cuda")
+            rates = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                dvu.copy_(vuu, non_blocking=True)
+                torch.cuda.synchronize()
+                rates.append(vuu.numel() * 8 / (time.perf_counter() - w0) / 1e9)
+            del dvu
 
             def step_host():
                 # wall-clock split of one host-pointer step: setup (including the 3.6 GB of copies), solve
@@ -595,7 +606,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             te = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
             e2e = {"value": te / args.steps / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(n * 8), "parts": host_parts[-args.steps:]}
+                   "d2h_bytes_per_step": int(n * 8), "parts": host_parts[-args.steps:],
+                   "torch_pinned_h2d_gbs": [round(r, 1) for r in rates], "host_is_pinned": bool(vuu.is_pinned())}
         ps.ps_system_free(sysp)
         served = None if (args.no_serve or world > 1) else served_section(ps, torch)
 
