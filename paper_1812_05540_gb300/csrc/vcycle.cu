@@ -19,51 +19,23 @@ __device__ __forceinline__ T val_as(const __nv_bfloat16* p) { return T(__bfloat1
 
 template <class T, int NC, int LANES>
 struct Row {
-  template <class TV>
-  __device__ __forceinline__ static T ld(const TV* __restrict__ v, int32_t q, int c) {
-    if constexpr (sizeof(TV) == 2) return val_as<T>(v + int64_t(q) * NC + c);
-    else return T(__ldg(v + int64_t(q) * NC + c));
-  }
-  // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum.  Each lane
-  // takes its entries four at a time with the four column indices and values loaded first, so that four
-  // index-then-gather chains are in flight at once (the short coarse-level rows are latency-bound); the
-  // products are still added one by one in entry order.
+  // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum
   template <class XF, class TV>
   __device__ __forceinline__ static void dot(bool active, int32_t q0, int32_t q1, const int32_t* __restrict__ ci,
                                              const TV* __restrict__ v, XF xf, int sub, T (&s)[NC]) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) s[c] = T(0);
-    if (active) {
-      int32_t q = q0 + sub;
-      for (; q + 3 * LANES < q1; q += 4 * LANES) {
-        const int32_t j0 = __ldg(ci + q), j1 = __ldg(ci + q + LANES), j2 = __ldg(ci + q + 2 * LANES),
-                      j3 = __ldg(ci + q + 3 * LANES);
-        T a[4][NC], x[4][NC];
+    if (active)
+      for (int32_t q = q0 + sub; q < q1; q += LANES) {
+        int32_t j = __ldg(ci + q);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          a[0][c] = ld(v, q, c);
-          a[1][c] = ld(v, q + LANES, c);
-          a[2][c] = ld(v, q + 2 * LANES, c);
-          a[3][c] = ld(v, q + 3 * LANES, c);
+          T a;
+          if constexpr (sizeof(TV) == 2) a = val_as<T>(v + int64_t(q) * NC + c);
+          else a = T(__ldg(v + int64_t(q) * NC + c));
+          s[c] += a * xf(j, c);
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          x[0][c] = xf(j0, c);
-          x[1][c] = xf(j1, c);
-          x[2][c] = xf(j2, c);
-          x[3][c] = xf(j3, c);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) s[c] += a[u][c] * x[u][c];
       }
-      for (; q < q1; q += LANES) {
-        const int32_t j = __ldg(ci + q);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) s[c] += ld(v, q, c) * xf(j, c);
-      }
-    }
 #pragma unroll
     for (int off = LANES / 2; off > 0; off >>= 1)
 #pragma unroll
