@@ -62,7 +62,11 @@ def build(force=False, verbose=False):
                 raise RuntimeError("nvcc failed for %s" % cmd[-3])
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+        # the CUDA runtime is linked shared, so that a process that already uses it (PyTorch) and the library
+        # share one runtime instance: host memory pinned through the other's allocator is then seen as pinned
+        # here too, and host-pointer copies take the direct DMA path
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath," + cudalib, "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             print(r.stdout, r.stderr)
