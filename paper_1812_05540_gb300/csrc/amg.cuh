@@ -65,6 +65,14 @@ struct Amg {
   void* gx = nullptr;
   cudaStream_t gst = nullptr;
   int64_t gnodes = 0;
+  // the levels from tail_l0 down run as one cooperative launch with bounded grid barriers between their
+  // steps (k_vcycle_tail), when set up: tail points to the device array of their descriptors, tail_bar to
+  // the barrier counter (zeroed before every launch); err is the handle's bounded-wait error flag
+  void* tail = nullptr;
+  int tail_l0 = 0, tail_levels = 0, tail_grid = 0;
+  unsigned long long* tail_bar = nullptr;
+  int* err = nullptr;
+  int64_t spin_limit = 2000000;
 };
 // destroys the captured V-cycle graph, if any
 void amg_release_graph(Amg& H);

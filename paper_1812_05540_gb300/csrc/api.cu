@@ -304,6 +304,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     PS_TICK(); k_rsl_aupe<<<grid_for(h->nn, 256), 256, 0, st>>>(h->nn, J.uf_rp, J.uf_v, aupe);
     Amg S = h->amg_u;
     S.gexec = nullptr;
+    S.tail = nullptr;
     for (auto& L : S.L) {
       L.x = L.t = L.r = L.d = L.b = L.e = L.dsi = nullptr;
       L.sv_f = nullptr;
@@ -324,6 +325,10 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   cudaEventDestroy(e1);
   // §5.3 flow stage
   PS_TRY(build_flow(h));
+  // the V-cycles' bounded grid barriers report through the same flag as the wavefront waits
+  h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_u.spin_limit = h->amg_p.spin_limit = h->F.spin_limit;
   // Krylov workspace
   int m = h->m;
   int64_t n = h->n;
@@ -381,6 +386,7 @@ void ps_params_default(ps_params* p) {
   p->ilu_mode = PS_ILU_PENCIL;
   p->spin_limit = 2000000;
   p->ortho_sweep = 8;
+  p->vcycle_tail = 1;
   p->local_stage = PS_LOCAL_ILU0;
   p->local_sweeps = 3;
 }
@@ -474,7 +480,13 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   h->amg_p = Amg();
   h->w32 = FlowWork<float>();
   h->w64 = FlowWork<double>();
-  return build_flow(h);
+  PS_TRY(build_flow(h));
+  // the mechanics V-cycle graph holds the old flag's address: capture it again with the new one
+  amg_release_graph(h->amg_u);
+  h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_u.spin_limit = h->amg_p.spin_limit = h->F.spin_limit;
+  return PS_OK;
 }
 
 ps_status ps_spmv(ps_handle* h, const double* x, double* y) {
@@ -530,7 +542,7 @@ ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double to
       PS_CUDA(cudaStreamSynchronize(st));
       if (h->hflag[3]) {
         PS_CUDA(cudaMemsetAsync(h->F.ilu_err, 0, sizeof(int), st));
-        set_reason("a bounded wait of the wavefront ILU(0) sweep gave up");
+        set_reason("a bounded wait of the wavefront ILU(0) sweep or of a V-cycle grid barrier gave up");
         result = PS_ERR_TIMEOUT;
         break;
       }
@@ -727,7 +739,7 @@ struct FgmresRun {
         PS_CUDA(cudaMemsetAsync(h->mgs_bar, 0, sizeof(unsigned long long), st));
         h->mgs_base = 0;
       }
-      set_reason(wave ? "a bounded wait of the wavefront ILU(0) sweep gave up"
+      set_reason(wave ? "a bounded wait of the wavefront ILU(0) sweep or of a V-cycle grid barrier gave up"
                       : "a bounded grid barrier wait of the Gram-Schmidt step gave up");
       result = PS_ERR_TIMEOUT;
       S.iters = total;

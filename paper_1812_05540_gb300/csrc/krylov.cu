@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "gridsync.cuh"
 #include "krylov.cuh"
 
 namespace ps_internal {
@@ -477,38 +478,6 @@ __global__ void k_hsolve(const double* H, const double* g, double* y, int m, int
 // ---------------------------------------------------------------------------
 constexpr int kMgsThreads = 256;
 constexpr int kS = 8;            // most basis vectors per sweep (row stride of the Gram store)
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// all CTAs arrive, then wait until the counter reaches target; false (and *err set) when the
-// wait gives up after limit polls or another CTA has already given up
-__device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int64_t limit,
-                                             int* err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    red_release_add(ctr, 1ull);
-    int good = 1;
-    int64_t it = 0;
-    while (ld_acquire_u64(ctr) < target) {
-      if (++it > limit || ((it & 255) == 0 && *(volatile int*)err)) {
-        good = 0;
-        atomicExch(err, 1);
-        break;
-      }
-    }
-    ok = good;
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 // Warp sums of R values per lane (R a power of two, at most 32) by a transposing butterfly: at each of
 // the first log2(R) levels a lane keeps one half of its values, sends the other half to its partner and

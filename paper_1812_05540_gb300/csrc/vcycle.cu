@@ -4,9 +4,13 @@
 // interleaved components (node-major x,y,z for the SDC mechanics operator).
 #include <cuda_bf16.h>
 
+#include <cstring>
+#include <type_traits>
+#include <vector>
 #include <utility>
 
 #include "amg.cuh"
+#include "gridsync.cuh"
 
 namespace ps_internal {
 namespace {
@@ -242,6 +246,186 @@ __global__ void k_dense_solve(int64_t n, const double* __restrict__ inv, const T
   if (lane == 0) x[i * NC + c] = T(s);
 }
 
+// ---------------------------------------------------------------------------
+// The coarse end of the V-cycle in one cooperative launch.  Below the finest level every level is small
+// and its kernels are bound by launch and drain latency, not bandwidth: about five microseconds per kernel
+// on levels whose data moves in one.  k_vcycle_tail runs the steps of levels tail_l0 .. coarsest in order
+// (down: smoothing pair, residual, restriction; the dense coarsest solve; up: prolongation, two post
+// steps), each as a grid-stride loop over the level's rows, with a bounded grid barrier between steps.
+// Each step is the same arithmetic as its own kernel (same row split into lanes, same order of sums), so the
+// result is bit-identical to the kernel-per-step path.  Used for Chebyshev of degree 2 with FP32 or FP64
+// transfer operators; other schedules keep the kernel-per-step path.
+// ---------------------------------------------------------------------------
+template <class T>
+struct TailLevel {
+  int64_t n, nnext;
+  int lanes, plane, rlane, coarsest;
+  const int32_t *rp, *ci, *prp, *pci, *rrp, *rci;
+  const T *v, *dg, *dsi, *pv, *rv;
+  const double* inv;
+  T *x, *t, *r, *d, *b, *e;
+  double3 c1, c2, pc2;  // Chebyshev step 1 coefficients, and 1/theta for the first post step
+};
+
+// rows [0, n) in groups of LANES lanes; a warp's groups advance together, since the row sums shuffle
+// across the whole warp
+template <int LANES, class F>
+__device__ __forceinline__ void tail_rows(int64_t n, F&& f) {
+  constexpr int G = 32 / LANES;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t w = warp; w * G < n; w += nwarps) {
+    const int64_t i = w * G + lane / LANES;
+    f(i, lane % LANES, i < n);
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void by_lanes(int lanes, F&& f) {
+  switch (lanes) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    default: f(std::integral_constant<int, 32>()); break;
+  }
+}
+
+template <class T, int NC>
+__global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restrict__ lv, int nl,
+                                                     unsigned long long* bar, int64_t limit, int* err) {
+  const unsigned long long G = gridDim.x;
+  unsigned long long phase = 0;
+  auto sync = [&]() -> bool { ++phase; return grid_barrier(bar, phase * G, limit, err); };
+  // down the levels
+  for (int k = 0; k + 1 < nl; ++k) {
+    const TailLevel<T> L = lv[k];
+    const double a1[3] = {L.c1.x, L.c1.y, L.c1.z}, a2[3] = {L.c2.x, L.c2.y, L.c2.z};
+    // Chebyshev steps 0 and 1 from x = 0 in one pass (as k_cheb_zero2, degree 2: d is not kept)
+    by_lanes(L.lanes, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int64_t j, int c) { return L.b[j * NC + c] * L.dsi[j * NC + c]; };
+        T s[NC];
+        CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const T x1 = L.b[i * NC + c] * L.dsi[i * NC + c];
+            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
+            const T dn = T(a1[c]) * x1 + T(a2[c]) * r;
+            L.x[i * NC + c] = x1 + dn;
+          }
+      });
+    });
+    if (!sync()) return;
+    // r = b - A x (as k_resid)
+    by_lanes(L.lanes, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int64_t j, int c) { return L.x[j * NC + c]; };
+        T s[NC];
+        CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) L.r[i * NC + c] = L.b[i * NC + c] - s[c];
+      });
+    });
+    if (!sync()) return;
+    // b_coarse = R r (as k_spmv)
+    const TailLevel<T>& C = lv[k + 1];
+    T* bc = C.b;
+    by_lanes(L.rlane, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.nnext, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int32_t j, int c) { return L.r[int64_t(j) * NC + c]; };
+        T s[NC];
+        const int32_t q0 = active ? L.rrp[i] : 0, q1 = active ? L.rrp[i + 1] : 0;
+        Row<T, NC, LANES>::dot(active, q0, q1, L.rci, L.rv, xf, sub, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) bc[i * NC + c] = s[c];
+      });
+    });
+    if (!sync()) return;
+  }
+  // coarsest: e = inv b per component, one warp per row (as k_dense_solve)
+  {
+    const TailLevel<T> L = lv[nl - 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = warp; w < L.n * NC; w += nwarps) {
+      const int c = int(w / L.n);
+      const int64_t i = w % L.n;
+      const double* row = L.inv + (int64_t(c) * L.n + i) * L.n;
+      double s = 0.0;
+      for (int64_t j = lane; j < L.n; j += 32) s += row[j] * double(L.b[j * NC + c]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) L.e[i * NC + c] = T(s);
+    }
+    if (!sync()) return;
+  }
+  // up the levels
+  for (int k = nl - 2; k >= 0; --k) {
+    const TailLevel<T> L = lv[k];
+    const T* ec = lv[k + 1].e;
+    const double a1[3] = {L.c1.x, L.c1.y, L.c1.z}, a2[3] = {L.c2.x, L.c2.y, L.c2.z},
+                 p2[3] = {L.pc2.x, L.pc2.y, L.pc2.z};
+    // x += P e_coarse (as k_spmv with add)
+    by_lanes(L.plane, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int32_t j, int c) { return ec[int64_t(j) * NC + c]; };
+        T s[NC];
+        const int32_t q0 = active ? L.prp[i] : 0, q1 = active ? L.prp[i + 1] : 0;
+        Row<T, NC, LANES>::dot(active, q0, q1, L.pci, L.pv, xf, sub, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) L.x[i * NC + c] = L.x[i * NC + c] + s[c];
+      });
+    });
+    if (!sync()) return;
+    // first post step: t = x + d, d = D^{-1}(b - A x) / theta (as k_cheb_step, first)
+    by_lanes(L.lanes, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int64_t j, int c) { return L.x[j * NC + c]; };
+        T s[NC];
+        CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
+            const T dn = T(p2[c]) * r;
+            L.t[i * NC + c] = L.x[i * NC + c] + dn;
+            L.d[i * NC + c] = dn;
+          }
+      });
+    });
+    if (!sync()) return;
+    // second post step: e = t + c1 d + c2 D^{-1}(b - A t) (as k_cheb_step)
+    by_lanes(L.lanes, [&](auto LN) {
+      constexpr int LANES = decltype(LN)::value;
+      tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
+        auto xf = [&](int64_t j, int c) { return L.t[j * NC + c]; };
+        T s[NC];
+        CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
+        if (active && sub == 0)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
+            const T dn = T(a1[c]) * L.d[i * NC + c] + T(a2[c]) * r;
+            L.e[i * NC + c] = L.t[i * NC + c] + dn;
+          }
+      });
+    });
+    if (k > 0 && !sync()) return;
+  }
+}
+
 template <class T>
 struct LevelT {
   const T *v, *dg, *dl1, *pv, *rv;
@@ -413,11 +597,37 @@ void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, cons
   }
 }
 
+// the tail levels in one cooperative launch; false when the launch was not possible (the caller then runs
+// the kernel-per-step path)
+template <class T, int NC>
+bool launch_tail(Amg& H, cudaStream_t st) {
+  const TailLevel<T>* lv = static_cast<const TailLevel<T>*>(H.tail);
+  int nl = H.tail_levels;
+  unsigned long long* bar = H.tail_bar;
+  int64_t limit = H.spin_limit;
+  int* err = H.err;
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  void* args[] = {&lv, &nl, &bar, &limit, &err};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_vcycle_tail<T, NC>, H.tail_grid, 256, args, 0, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  PS_TICK();
+  return true;
+}
+
 template <class T, int NC>
 void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cudaStream_t st) {
   AmgLevel& L = H.L[l];
   LevelT<T> V = view<T>(L);
   int64_t n = L.n;
+  if (l >= 1 && l == H.tail_l0 && H.tail && H.err && b == static_cast<const T*>(L.b) && out == static_cast<T*>(L.e) &&
+      launch_tail<T, NC>(H, st))
+    return;
   if (L.coarsest) {
     PS_TICK(); k_dense_solve<T, NC><<<grid_for(n * NC * 32, 256), 256, 0, st>>>(n, V.inv, b, out);
     return;
@@ -450,6 +660,59 @@ void vcycle_launch(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_
 
 }  // namespace
 
+// descriptors of the levels below the finest for k_vcycle_tail (Chebyshev degree 2, FP32 or FP64 transfer
+// operators, cooperative launch available); leaves H.tail null otherwise
+template <class T>
+ps_status tail_setup(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st) {
+  H.tail = nullptr;
+  const int nlev = int(H.L.size());
+  if (sp.kind != PS_SMOOTH_CHEBYSHEV || sp.degree != 2 || nlev < 3) return PS_OK;
+  for (int l = 1; l < nlev; ++l) {
+    const AmgLevel& L = H.L[l];
+    if (l < nlev - 1 && (!L.dsi || L.coarsest || L.pvb || L.rvb || L.sv_f || L.sv_d)) return PS_OK;
+  }
+  if (!H.L[nlev - 1].coarsest) return PS_OK;
+  int dev = 0, coop = 0, sms = 0, occ = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const void* fn = H.nc == 3 ? (const void*)k_vcycle_tail<T, 3> : (const void*)k_vcycle_tail<T, 1>;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0));
+  if (!coop || occ < 1) return PS_OK;
+  std::vector<TailLevel<T>> tl;
+  for (int l = 1; l < nlev; ++l) {
+    const AmgLevel& L = H.L[l];
+    const LevelT<T> V = view<T>(L);
+    TailLevel<T> t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = L.n;
+    t.coarsest = L.coarsest ? 1 : 0;
+    t.lanes = L.lanes; t.plane = L.plane; t.rlane = L.rlane;
+    t.rp = L.rp; t.ci = L.ci; t.v = V.v; t.dg = V.dg; t.dsi = static_cast<const T*>(L.dsi);
+    t.inv = L.inv;
+    t.x = static_cast<T*>(L.x); t.t = static_cast<T*>(L.t); t.r = static_cast<T*>(L.r);
+    t.d = static_cast<T*>(L.d); t.b = static_cast<T*>(L.b); t.e = static_cast<T*>(L.e);
+    if (!L.coarsest) {
+      t.nnext = H.L[l + 1].n;
+      t.prp = L.prp; t.pci = L.pci; t.pv = V.pv;
+      t.rrp = L.rrp; t.rci = L.rci; t.rv = V.rv;
+      ChebCoef cc = cheb_coef(L, H.nc, sp);
+      t.c1 = cc.c1[1]; t.c2 = cc.c2[1]; t.pc2 = cc.post_c2;
+    }
+    tl.push_back(t);
+  }
+  TailLevel<T>* d;
+  PS_TRY(ar.alloc(&d, tl.size()));
+  PS_CUDA(cudaMemcpyAsync(d, tl.data(), sizeof(TailLevel<T>) * tl.size(), cudaMemcpyHostToDevice, st));
+  PS_TRY(ar.alloc(&H.tail_bar, 1));
+  PS_CUDA(cudaStreamSynchronize(st));
+  H.tail = d;
+  H.tail_l0 = 1;
+  H.tail_levels = int(tl.size());
+  H.tail_grid = sms * (occ < 2 ? occ : 2);
+  return PS_OK;
+}
+
 template <class T>
 ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st) {
   for (auto& L : H.L) {
@@ -469,7 +732,7 @@ ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t
     }
   }
   PS_CUDA(cudaGetLastError());
-  return PS_OK;
+  return tail_setup<T>(ar, H, sp, st);
 }
 
 void amg_release_graph(Amg& H) {

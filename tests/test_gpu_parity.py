@@ -272,3 +272,29 @@ def test_bf16_prolongator_variant(cfg, kw, cm):
         assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
         its[prec] = st.iters
     assert its[ps.PS_MIXED_BF16P] <= int(1.2 * its[ps.PS_MIXED_FP32]) + 1, its
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+def test_vcycle_tail_matches_kernel_per_step(prec):
+    # the levels below the finest in one cooperative launch (bounded grid barriers between the steps) do the
+    # arithmetic of the kernel-per-step path in the same order: Algorithm 1 gives the same bits either way,
+    # on a grid whose hierarchies have four levels
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(2, nx=21, ny=44, nz=17))
+    dev = g.to_device(osys)
+    out = []
+    side = torch.cuda.Stream()  # a stream that can be captured, so the V-cycles run as CUDA graphs
+    for tail in (1, 0):
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, vcycle_tail=tail,
+                                                                 stream=side.cuda_stream))
+        try:
+            assert ps.ps_amg_nlevels(h, 0) >= 3 and ps.ps_amg_nlevels(h, 1) >= 3
+            v = torch.from_numpy(np.random.default_rng(8).standard_normal(osys.n)).cuda()
+            z = torch.empty_like(v)
+            torch.cuda.synchronize()
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())  # the second apply replays the captured graph
+            out.append(z.cpu().numpy())
+        finally:
+            ps.ps_free(h)
+    assert np.array_equal(out[0], out[1])
