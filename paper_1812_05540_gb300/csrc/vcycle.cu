@@ -21,6 +21,11 @@ __device__ __forceinline__ T val(const T* p) { return __ldg(p); }
 template <class T>
 __device__ __forceinline__ T val_as(const __nv_bfloat16* p) { return T(__bfloat162float(*p)); }
 
+// a * b + c with one rounding, written out so that every kernel forms the Chebyshev update the same way
+// (an implicit contraction of a sum of two products may fuse either product)
+__device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <class T, int NC, int LANES>
 struct Row {
   // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum
@@ -127,7 +132,7 @@ __global__ void k_cheb_step(A a, int64_t n, const T* __restrict__ dg, const T* _
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       T r = (b[i * NC + c] - s[c]) / dg[i * NC + c];
-      T dn = first ? T(a2[c]) * r : T(a1[c]) * d[i * NC + c] + T(a2[c]) * r;
+      T dn = first ? T(a2[c]) * r : mad(T(a1[c]), d[i * NC + c], T(a2[c]) * r);
       xo[i * NC + c] = x[i * NC + c] + dn;
       if (store_d) d[i * NC + c] = dn;
     }
@@ -151,7 +156,7 @@ __global__ void k_cheb_zero2(A a, int64_t n, const T* __restrict__ dg, const T* 
     for (int c = 0; c < NC; ++c) {
       const T x1 = b[i * NC + c] * dsi[i * NC + c];
       const T r = (b[i * NC + c] - s[c]) / dg[i * NC + c];
-      const T dn = T(a1[c]) * x1 + T(a2[c]) * r;
+      const T dn = mad(T(a1[c]), x1, T(a2[c]) * r);
       xo[i * NC + c] = x1 + dn;
       if (d) d[i * NC + c] = dn;
     }
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
           for (int c = 0; c < NC; ++c) {
             const T x1 = L.b[i * NC + c] * L.dsi[i * NC + c];
             const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
-            const T dn = T(a1[c]) * x1 + T(a2[c]) * r;
+            const T dn = mad(T(a1[c]), x1, T(a2[c]) * r);
             L.x[i * NC + c] = x1 + dn;
           }
       });
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
-            const T dn = T(a1[c]) * L.d[i * NC + c] + T(a2[c]) * r;
+            const T dn = mad(T(a1[c]), L.d[i * NC + c], T(a2[c]) * r);
             L.e[i * NC + c] = L.t[i * NC + c] + dn;
           }
       });
