@@ -132,9 +132,10 @@ typedef struct {
   int32_t cpr_reduction;      /* PS_CPR_QUASI_IMPES (default) or PS_CPR_TRUE_IMPES */
   int32_t solver;             /* PS_SOLVER_FGMRES (default) or PS_SOLVER_RICHARDSON */
   int32_t fs_mode;            /* PS_FS_GIVEN (default) or PS_FS_RSL */
-  int32_t vcycle_tail;        /* 1 (default): the V-cycle levels below the finest run as one cooperative
-                                 launch with bounded grid barriers between their steps (Chebyshev degree 2,
-                                 FP32/FP64 transfer operators); 0: one kernel per step.  Same results. */
+  int32_t vcycle_tail;        /* 1: the V-cycle levels below the finest run as one cooperative launch with
+                                 bounded grid barriers between their steps (Chebyshev degree 2, FP32/FP64
+                                 transfer operators); 0 (default): one kernel per step, replayed as a CUDA
+                                 graph, which measured faster.  Same results either way. */
 } ps_params;
 
 typedef struct {

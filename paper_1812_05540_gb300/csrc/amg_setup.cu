@@ -5,6 +5,7 @@
 // This translation unit is compiled without floating-point contraction and
 // every floating-point sum is taken in a fixed order (ascending column / inner
 // index), so the aggregates and coarse operators are reproducible bit for bit.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -12,6 +13,7 @@
 #include <type_traits>
 
 #include "amg.cuh"
+#include "gridsync.cuh"
 
 namespace ps_internal {
 namespace {
@@ -778,6 +780,77 @@ __global__ void k_gj_elim(int64_t n, int64_t k, double* __restrict__ M, double* 
   else B[r * n + j - n] = B[r * n + j - n] - m * B[k * n + j - n];
 }
 
+// The whole Gauss-Jordan inverse in one cooperative launch (every CTA co-resident): for each pivot k, CTA c
+// (c < nc) finds, swaps and normalises the pivot row of component c exactly as k_gj_pivot does, then all
+// CTAs eliminate column k from every other row of every component as k_gj_elim does, with a bounded grid
+// barrier after each of the two steps (2 n barriers in place of 2 n launches).  Data written in an earlier
+// step is loaded through L2 (ld.global.cg).
+__global__ void __launch_bounds__(256) k_gj_all(int64_t n, int nc, double* __restrict__ M, double* __restrict__ I,
+                                                double* __restrict__ f, unsigned long long* bar, int64_t limit,
+                                                int* err) {
+  const unsigned long long G = gridDim.x;
+  unsigned long long phase = 0;
+  __shared__ double bv[256];
+  __shared__ int64_t bi[256];
+  for (int64_t k = 0; k < n; ++k) {
+    if (int(blockIdx.x) < nc) {
+      const int c = blockIdx.x;
+      double* A = M + int64_t(c) * n * n;
+      double* B = I + int64_t(c) * n * n;
+      double best = -1.0;
+      int64_t arg = k;
+      for (int64_t r = k + threadIdx.x; r < n; r += blockDim.x) {
+        double a = fabs(__ldcg(A + r * n + k));
+        if (a > best) { best = a; arg = r; }
+      }
+      bv[threadIdx.x] = best;
+      bi[threadIdx.x] = arg;
+      __syncthreads();
+      for (int off = blockDim.x >> 1; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+          double o = bv[threadIdx.x + off];
+          int64_t oi = bi[threadIdx.x + off];
+          if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+            bv[threadIdx.x] = o;
+            bi[threadIdx.x] = oi;
+          }
+        }
+        __syncthreads();
+      }
+      const int64_t p = bi[0];
+      if (p != k)
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+          double t = __ldcg(A + k * n + j); A[k * n + j] = __ldcg(A + p * n + j); A[p * n + j] = t;
+          t = __ldcg(B + k * n + j); B[k * n + j] = __ldcg(B + p * n + j); B[p * n + j] = t;
+        }
+      __syncthreads();
+      const double piv = A[k * n + k];
+      __syncthreads();
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        A[k * n + j] = A[k * n + j] / piv;
+        B[k * n + j] = B[k * n + j] / piv;
+      }
+      __syncthreads();
+      for (int64_t r = threadIdx.x; r < n; r += blockDim.x) f[int64_t(c) * n + r] = A[r * n + k];
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, ++phase * G, limit, err)) return;
+    const int64_t w2 = 2 * n, items = int64_t(nc) * n * w2;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < items; t += int64_t(G) * blockDim.x) {
+      const int64_t j = t % w2, r = (t / w2) % n;
+      const int c = int(t / (w2 * n));
+      if (r == k) continue;
+      const double m = __ldcg(f + int64_t(c) * n + r);
+      if (m == 0.0) continue;
+      double* A = M + int64_t(c) * n * n;
+      double* B = I + int64_t(c) * n * n;
+      if (j < n) A[r * n + j] = __ldcg(A + r * n + j) - m * __ldcg(A + k * n + j);
+      else B[r * n + j - n] = __ldcg(B + r * n + j - n) - m * __ldcg(B + k * n + j - n);
+    }
+    if (!grid_barrier(bar, ++phase * G, limit, err)) return;
+  }
+}
+
 __global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = __double2bfloat16(a[t]);
@@ -913,6 +986,41 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   return PS_OK;
 }
 
+// The coarsest inverse by k_gj_all: 0 done, 1 not launched (no cooperative launch; the caller runs the
+// launch-per-step path), 2 a grid barrier wait gave up (the inverse is incomplete)
+int gj_cooperative(int64_t n, int nc, double* M, double* I, double* f, Arena& ar, cudaStream_t st) {
+  int dev = 0, coop = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_all, 256, 0) != cudaSuccess || !coop || occ < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  unsigned long long* bar;
+  int* err;
+  if (ar.alloc(&bar, 1) != PS_OK) return 1;
+  if (ar.alloc(&err, 1) != PS_OK) { ar.release(bar); return 1; }
+  cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  int64_t limit = 20000000;
+  const unsigned grid = unsigned(std::max(nc, sms));
+  void* args[] = {&n, &nc, &M, &I, &f, &bar, &limit, &err};
+  int result = 0;
+  if (cudaLaunchCooperativeKernel((const void*)k_gj_all, grid, 256, args, 0, st) != cudaSuccess) {
+    cudaGetLastError();
+    result = 1;
+  } else {
+    PS_TICK();
+    int h = 0;
+    cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (h) result = 2;
+  }
+  ar.release(bar);
+  ar.release(err);
+  return result;
+}
+
 template <int NC>
 ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, int32_t* ci0, double* v0,
                      const AmgParams& prm, cudaStream_t st) {
@@ -993,10 +1101,17 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * NC * n * n, st));
       PS_CUDA(cudaMemsetAsync(lev.inv, 0, sizeof(double) * NC * n * n, st));
       PS_TICK(); k_dense_unpack<<<grid_for(n, 128), 128, 0, st>>>(n, NC, lev.rp, lev.ci, lev.v, M, lev.inv);
-      for (int64_t k = 0; k < n; ++k) {
-        PS_TICK(); k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
-        dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), NC);
-        PS_TICK(); k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
+      const int gj = gj_cooperative(n, NC, M, lev.inv, f, ar, st);
+      if (gj == 2) {
+        set_reason("a bounded grid barrier wait of the coarsest-level Gauss-Jordan inverse gave up");
+        return PS_ERR_TIMEOUT;
+      }
+      if (gj == 1) {
+        for (int64_t k = 0; k < n; ++k) {
+          PS_TICK(); k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
+          dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), NC);
+          PS_TICK(); k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
+        }
       }
       PS_CUDA(cudaGetLastError());
       ar.release(M); ar.release(f);

@@ -386,7 +386,7 @@ void ps_params_default(ps_params* p) {
   p->ilu_mode = PS_ILU_PENCIL;
   p->spin_limit = 2000000;
   p->ortho_sweep = 8;
-  p->vcycle_tail = 1;
+  p->vcycle_tail = 0;
   p->local_stage = PS_LOCAL_ILU0;
   p->local_sweeps = 3;
 }
