@@ -381,6 +381,88 @@ def run_ours(args):
             ps.ps_system_free(sysp)
             return
         t_64, st_64 = (t_mx, st_mx) if args.no_fp64 else timed(ps.PS_FP64, args.steps)[:2]
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region; taken right
+        # after the device-pointer arms (after the variant runs below, the same copies measured several times
+        # slower)
+        e2e = None
+        if not args.no_e2e:
+            host = {}
+            ptrs = {}
+            def hcopy(ptr, count, dtype, tdtype):
+                t = torch.empty(count, dtype=tdtype, pin_memory=True)
+                src = dev_to_numpy(ptr, count, dtype)
+                t.copy_(torch.from_numpy(src))
+                return t
+            j = s.jac
+            blocks = []
+            h2d = 0
+            for blk, bs in ((j.A_uu, 9), (j.A_uf, 6), (j.A_fu, 6), (j.A_ff, 4)):
+                rp = hcopy(blk.rowptr, blk.n_brow + 1, np.int64, torch.int64)
+                ci = hcopy(blk.colind, blk.nnzb, np.int32, torch.int32)
+                v = hcopy(blk.val, blk.nnzb * bs, np.float64, torch.float64)
+                host[len(host)] = (rp, ci, v)
+                blocks.append(ps.ps_bsr(blk.n_brow, blk.n_bcol, blk.nnzb, blk.br, blk.bc, rp.data_ptr(),
+                                        ci.data_ptr(), v.data_ptr()))
+                h2d += rp.numel() * 8 + ci.numel() * 4 + v.numel() * 8
+            dfs = hcopy(j.d_fs, 2 * s.n_cells, np.float64, torch.float64)
+            rhs_h = hcopy(s.rhs, n, np.float64, torch.float64)
+            x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            h2d += dfs.numel() * 8 + rhs_h.numel() * 8
+            hjac = ps.ps_jacobian(blocks[0], blocks[1], blocks[2], blocks[3], dfs.data_ptr(), None)
+
+            host_parts = []
+            pool_before = ps.ps_pool_bytes()
+            # the same pinned A_uu values copied by torch, for the copy rate of the host link on this box
+            vuu = host[0][2]
+            rates = []
+            dvu = None
+            for fresh in (True, False, True):
+                if fresh:
+                    dvu = torch.empty_like(vuu, device="cuda")
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                dvu.copy_(vuu, non_blocking=True)
+                torch.cuda.synchronize()
+                rates.append(vuu.numel() * 8 / (time.perf_counter() - w0) / 1e9)
+            del dvu
+
+            def step_host():
+                # wall-clock split of one host-pointer step: setup (including the 3.6 GB of copies), solve
+                # (including rhs in and x out), free
+                p = ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr, host_ptrs=1)
+                w0 = time.perf_counter()
+                hh = ps.ps_setup(hjac, s.grid, p)
+                w1 = time.perf_counter()
+                try:
+                    status, st = ps.ps_solve(hh, rhs_h.data_ptr(), x_h.data_ptr(), TOL, raise_on_error=False)
+                finally:
+                    w2 = time.perf_counter()
+                    ps.ps_free(hh)
+                    w3 = time.perf_counter()
+                host_parts.append({"setup_s": w1 - w0, "solve_s": w2 - w1, "free_s": w3 - w2,
+                                   "setup_events_ms": round(st.ms_setup_u + st.ms_setup_f, 2),
+                                   "copy_in_ms": round(st.ms_copy_in, 2),
+                                   "solve_events_ms": round(st.ms_solve, 2), "iters": st.iters})
+                if status != ps.PS_OK:
+                    raise RuntimeError("e2e solve failed: %s" % ps.ps_strerror(status))
+
+            step_host()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step_host()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            te = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
+            e2e = {"value": te / args.steps / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(n * 8), "parts": host_parts[-args.steps:],
+                   "torch_pinned_h2d_gbs": {"fresh_destination": round(rates[0], 1), "same_destination": round(rates[1], 1),
+                                            "second_fresh_destination": round(rates[2], 1)},
+                   "host_is_pinned": bool(vuu.is_pinned()),
+                   "library_pool_bytes_before": {"reserved": pool_before[0], "used": pool_before[1]}}
         # BF16-prolongator variant of the mixed mode: time and iteration cost
         t_bp, st_bp = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_BF16P, args.steps)[:2]
         # the other local stage of §5.3 (option 1): three sweeps of block Gauss-Seidel instead of ILU(0)
@@ -534,84 +616,14 @@ def run_ours(args):
                               "launch_ms": 1000.0 * t_apply, "peak_source": hbm_src,
                               "levels": [list(x) for x in shapes[w]]})
 
-        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-        e2e = None
-        if not args.no_e2e:
-            host = {}
-            ptrs = {}
-            def hcopy(ptr, count, dtype, tdtype):
-                t = torch.empty(count, dtype=tdtype, pin_memory=True)
-                src = dev_to_numpy(ptr, count, dtype)
-                t.copy_(torch.from_numpy(src))
-                return t
-            j = s.jac
-            blocks = []
-            h2d = 0
-            for blk, bs in ((j.A_uu, 9), (j.A_uf, 6), (j.A_fu, 6), (j.A_ff, 4)):
-                rp = hcopy(blk.rowptr, blk.n_brow + 1, np.int64, torch.int64)
-                ci = hcopy(blk.colind, blk.nnzb, np.int32, torch.int32)
-                v = hcopy(blk.val, blk.nnzb * bs, np.float64, torch.float64)
-                host[len(host)] = (rp, ci, v)
-                blocks.append(ps.ps_bsr(blk.n_brow, blk.n_bcol, blk.nnzb, blk.br, blk.bc, rp.data_ptr(),
-                                        ci.data_ptr(), v.data_ptr()))
-                h2d += rp.numel() * 8 + ci.numel() * 4 + v.numel() * 8
-            dfs = hcopy(j.d_fs, 2 * s.n_cells, np.float64, torch.float64)
-            rhs_h = hcopy(s.rhs, n, np.float64, torch.float64)
-            x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
-            h2d += dfs.numel() * 8 + rhs_h.numel() * 8
-            hjac = ps.ps_jacobian(blocks[0], blocks[1], blocks[2], blocks[3], dfs.data_ptr(), None)
-
-            host_parts = []
-            # the same pinned A_uu values copied by torch, for the copy rate of the host link on this box
-            vuu = host[0][2]
-            rates = []
-            dvu = None
-            for fresh in (True, False, True):
-                if fresh:
-                    dvu = torch.empty_like(vuu, device="cuda")
-                torch.cuda.synchronize()
-                w0 = time.perf_counter()
-                dvu.copy_(vuu, non_blocking=True)
-                torch.cuda.synchronize()
-                rates.append(vuu.numel() * 8 / (time.perf_counter() - w0) / 1e9)
-            del dvu
-
-            def step_host():
-                # wall-clock split of one host-pointer step: setup (including the 3.6 GB of copies), solve
-                # (including rhs in and x out), free
-                p = ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr, host_ptrs=1)
-                w0 = time.perf_counter()
-                hh = ps.ps_setup(hjac, s.grid, p)
-                w1 = time.perf_counter()
-                try:
-                    status, st = ps.ps_solve(hh, rhs_h.data_ptr(), x_h.data_ptr(), TOL, raise_on_error=False)
-                finally:
-                    w2 = time.perf_counter()
-                    ps.ps_free(hh)
-                    w3 = time.perf_counter()
-                host_parts.append({"setup_s": w1 - w0, "solve_s": w2 - w1, "free_s": w3 - w2,
-                                   "setup_events_ms": round(st.ms_setup_u + st.ms_setup_f, 2),
-                                   "copy_in_ms": round(st.ms_copy_in, 2),
-                                   "solve_events_ms": round(st.ms_solve, 2), "iters": st.iters})
-                if status != ps.PS_OK:
-                    raise RuntimeError("e2e solve failed: %s" % ps.ps_strerror(status))
-
-            step_host()
-            barrier()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
+        if e2e is not None:
+            # the same host-pointer steps again after the variant runs, with the pool's size at that point
+            pool_after = ps.ps_pool_bytes()
+            n_before = len(host_parts)
+            for _ in range(2):
                 step_host()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            te = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
-            e2e = {"value": te / args.steps / world, "unit": "s", "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(n * 8), "parts": host_parts[-args.steps:],
-                   "torch_pinned_h2d_gbs": {"fresh_destination": round(rates[0], 1), "same_destination": round(rates[1], 1),
-                                            "second_fresh_destination": round(rates[2], 1)},
-                   "host_is_pinned": bool(vuu.is_pinned())}
+            e2e["after_variants"] = {"parts": host_parts[n_before:],
+                                     "library_pool_bytes": {"reserved": pool_after[0], "used": pool_after[1]}}
         ps.ps_system_free(sysp)
         served = None if (args.no_serve or world > 1) else served_section(ps, torch)
 

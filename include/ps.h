@@ -356,6 +356,10 @@ int64_t ps_launch_count(void);
    device buffer of a handle, generator output or server request is one). */
 int64_t ps_alloc_count(void);
 
+/* Device bytes the library's memory pool on the current device holds (*reserved, including freed blocks it
+   keeps for reuse) and has handed out (*used). */
+ps_status ps_pool_bytes(int64_t* reserved, int64_t* used);
+
 #ifdef __cplusplus
 }
 #endif

@@ -158,6 +158,7 @@ def lib():
         L.ps_server_destroy.restype = None
         L.ps_launch_count.argtypes = []
         L.ps_launch_count.restype = C.c_int64
+        L.ps_pool_bytes.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ps_alloc_count.argtypes = []
         L.ps_alloc_count.restype = C.c_int64
         L.ps_strerror.argtypes = [C.c_int]
@@ -187,6 +188,13 @@ def ps_launch_count():
 
 def ps_alloc_count():
     return lib().ps_alloc_count()
+
+
+def ps_pool_bytes():
+    """(reserved, used) device bytes of the library's memory pool on the current device."""
+    r, u = C.c_int64(), C.c_int64()
+    _check(lib().ps_pool_bytes(C.byref(r), C.byref(u)), "ps_pool_bytes")
+    return r.value, u.value
 
 
 def ps_params_default(**kw):

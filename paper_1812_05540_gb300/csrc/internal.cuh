@@ -55,6 +55,9 @@ struct Arena {
   void free_all();
 };
 
+// the library's stream-ordered memory pool on the current device (null if it could not be created)
+cudaMemPool_t pool_for_current_device();
+
 // ---- device utilities (util.cu) ----
 // exclusive scan of n int32 counts; out has n+1 entries, out[n] = total (also
 // returned in *total when non-null, which synchronises the stream)

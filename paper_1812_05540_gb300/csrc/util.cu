@@ -32,7 +32,7 @@ const std::string& last_reason() { return g_reason; }
 
 // One stream-ordered pool per device; freed blocks stay cached in the pool so
 // that repeated setups do not pay for cudaMalloc.
-static cudaMemPool_t pool_for_current_device() {
+cudaMemPool_t pool_for_current_device() {
   static std::mutex mu;
   static cudaMemPool_t pools[64] = {};
   int dev = 0;
@@ -247,3 +247,17 @@ void rowptr_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t st) 
 
 extern "C" int64_t ps_launch_count(void) { return ps_internal::g_launches.load(); }
 extern "C" int64_t ps_alloc_count(void) { return ps_internal::g_allocs.load(); }
+
+extern "C" ps_status ps_pool_bytes(int64_t* reserved, int64_t* used) {
+  if (!reserved || !used) return PS_ERR_INVALID;
+  *reserved = 0;
+  *used = 0;
+  cudaMemPool_t pool = ps_internal::pool_for_current_device();
+  if (!pool) return PS_OK;
+  uint64_t r = 0, u = 0;
+  PS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r));
+  PS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u));
+  *reserved = int64_t(r);
+  *used = int64_t(u);
+  return PS_OK;
+}
