@@ -87,7 +87,7 @@ class PrecParams(C.Structure):
                 ("cheb_ratio", C.c_double), ("mech_mode", C.c_int32), ("flow_mode", C.c_int32),
                 ("local_mode", C.c_int32), ("press_mode", C.c_int32), ("full_exact", C.c_int32),
                 ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
-                ("fs_mode", C.c_int32)]
+                ("fs_mode", C.c_int32), ("ilu_tile_y", C.c_int32), ("ilu_tile_z", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -1562,6 +1562,8 @@ void or_default_prec_params(or_prec_params* pp) {
   pp->pre = 1; pp->post = 1;
   pp->smoother = 1; pp->cheb_degree = 2; pp->cheb_ratio = 20.0;
   pp->local_sweeps = 3;
+  pp->ilu_tile_y = 0;
+  pp->ilu_tile_z = 0;
 }
 
 int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {
@@ -1660,8 +1662,22 @@ int or_prec_setup_reuse(const or_system* s, const or_system* mech, const or_prec
       for (int64_t q = P->spp.rp[i]; q < P->spp.rp[i + 1]; ++q) d[i * nc + P->spp.ci[q]] = P->spp.v[q];
     P->lu_pp.factor(nc, std::move(d));
   }
-  // §5.3 option 2: block ILU(0) of the interleaved S_ff^(FS), natural cell order (IKJ)
+  // §5.3 option 2: block ILU(0) of the interleaved S_ff^(FS), natural cell order (IKJ).  Processor-local
+  // ILU(0) (the paper's runs factor each process's own rows): the ILU(0) of S_ff with the blocks that couple
+  // cells of different subdomains set to zero, a subdomain being a column of ty x tz cells in (y, z)
   P->ilu = P->Sff;
+  if (pp->ilu_tile_y > 0 && pp->ilu_tile_z > 0) {
+    const int64_t gx = s->nx, gy = s->ny;
+    const int64_t nby = (gy + pp->ilu_tile_y - 1) / pp->ilu_tile_y;
+    auto sub = [&](int64_t c) {
+      const int64_t y = (c / gx) % gy, z = c / (gx * gy);
+      return y / pp->ilu_tile_y + nby * (z / pp->ilu_tile_z);
+    };
+    for (int64_t i = 0; i < nc; ++i)
+      for (int64_t q = P->ilu.rp[i]; q < P->ilu.rp[i + 1]; ++q)
+        if (sub(P->ilu.ci[q]) != sub(i))
+          for (int e = 0; e < 4; ++e) P->ilu.v[q * 4 + e] = 0.0;
+  }
   P->dinv.assign(4 * nc, 0.0);
   for (int64_t i = 0; i < nc; ++i) {
     for (int64_t qk = P->ilu.rp[i]; qk < P->ilu.rp[i + 1]; ++qk) {
