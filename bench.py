@@ -414,17 +414,21 @@ def run_ours(args):
             pool_before = ps.ps_pool_bytes()
             # the same pinned A_uu values copied by torch, for the copy rate of the host link on this machine
             vuu = host[0][2]
-            rates = []
-            dvu = None
-            for fresh in (True, False, True):
-                if fresh:
-                    dvu = torch.empty_like(vuu, device="cuda")
-                torch.cuda.synchronize()
-                w0 = time.perf_counter()
-                dvu.copy_(vuu, non_blocking=True)
-                torch.cuda.synchronize()
-                rates.append(vuu.numel() * 8 / (time.perf_counter() - w0) / 1e9)
-            del dvu
+
+            def torch_rates():
+                rates = []
+                dvu = None
+                for fresh in (True, False, True):
+                    if fresh:
+                        dvu = torch.empty_like(vuu, device="cuda")
+                    torch.cuda.synchronize()
+                    w0 = time.perf_counter()
+                    dvu.copy_(vuu, non_blocking=True)
+                    torch.cuda.synchronize()
+                    rates.append(vuu.numel() * 8 / (time.perf_counter() - w0) / 1e9)
+                return rates
+
+            rates = torch_rates()
 
             def step_host():
                 # wall-clock split of one host-pointer step: setup (including the 3.6 GB of copies), solve
@@ -466,6 +470,10 @@ def run_ours(args):
         # BF16-prolongator variant of the mixed mode: time and iteration cost
         t_bp, st_bp = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_BF16P, args.steps)[:2]
         # the other local stage of §5.3 (option 1): three sweeps of block Gauss-Seidel instead of ILU(0)
+        # processor-local ILU(0) (the paper's runs factor each process's rows, §6): one subdomain per sweep
+        # tile of 16 x 8 cell columns, so the two triangular sweeps need no exchange between tiles
+        t_il, st_il = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
+                                                               ilu_scope=ps.PS_ILU_LOCAL)[:2]
         t_gs, st_gs = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
                                                                local_stage=ps.PS_LOCAL_HBGS)[:2]
         # the true-IMPES pressure reduction of §5.3 in place of quasi-IMPES (one solve, at most 300 iterations:
@@ -619,11 +627,13 @@ def run_ours(args):
         if e2e is not None:
             # the same host-pointer steps again after the variant runs, with the pool's size at that point
             pool_after = ps.ps_pool_bytes()
+            rates_after = torch_rates()
             n_before = len(host_parts)
             for _ in range(2):
                 step_host()
             e2e["after_variants"] = {"parts": host_parts[n_before:],
-                                     "library_pool_bytes": {"reserved": pool_after[0], "used": pool_after[1]}}
+                                     "library_pool_bytes": {"reserved": pool_after[0], "used": pool_after[1]},
+                                     "torch_pinned_h2d_gbs": [round(r, 1) for r in rates_after]}
         ps.ps_system_free(sysp)
         served = None if (args.no_serve or world > 1) else served_section(ps, torch)
 
@@ -671,6 +681,14 @@ def run_ours(args):
             "value": t_bp / args.steps / world, "iters": [st.iters for st in st_bp],
             "solve_ms": [round(st.ms_solve, 2) for st in st_bp],
             "vcycle_u_ms": round(st_bp[-1].ms_vcycle_u, 1), "vcycle_p_ms": round(st_bp[-1].ms_vcycle_p, 1)},
+        "ilu_processor_local": None if st_il is None else {
+            "value": t_il / args.steps / world, "iters": [st.iters for st in st_il],
+            "solve_ms": [round(st.ms_solve, 2) for st in st_il],
+            "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_il],
+            "local_stage_ms": round(st_il[-1].ms_ilu, 1),
+            "note": "processor-local ILU(0) (paper §6: each process factors its own rows): subdomains of "
+                    "16 x 8 cell columns spanning x, one per sweep tile (%d), no exchange between them"
+                    % (((s.grid.ny + 15) // 16) * ((s.grid.nz + 7) // 8))},
         "local_stage_hbgs": None if st_gs is None else {
             "value": t_gs / args.steps / world, "iters": [st.iters for st in st_gs],
             "solve_ms": [round(st.ms_solve, 2) for st in st_gs],

@@ -56,6 +56,11 @@ enum { PS_ILU_LEVEL_LAUNCH = 0, PS_ILU_PENCIL = 1 };
 /* local stage M_L of §5.3: option 2, one sweep of block ILU(0) (default); option 1, local_sweeps sweeps of
    block Gauss-Seidel on the interleaved S_ff^(FS), cells taken in red-black order */
 enum { PS_LOCAL_ILU0 = 0, PS_LOCAL_HBGS = 1 };
+/* scope of the ILU(0) local stage: the whole flow system, or processor-local (§6: each process factors
+   the rows it owns), with subdomains of PS_ILU_TILE_Y x PS_ILU_TILE_Z cell columns in (y, z) spanning x */
+enum { PS_ILU_GLOBAL = 0, PS_ILU_LOCAL = 1 };
+#define PS_ILU_TILE_Y 16
+#define PS_ILU_TILE_Z 8
 /* CPR pressure reduction of §5.3: quasi-IMPES (diagonal entries of A_ss, A_ps; default) or true-IMPES
    (column sums of A_ss, A_ps) */
 enum { PS_CPR_QUASI_IMPES = 0, PS_CPR_TRUE_IMPES = 1 };
@@ -136,6 +141,14 @@ typedef struct {
                                  bounded grid barriers between their steps (Chebyshev degree 2, FP32/FP64
                                  transfer operators); 0 (default): one kernel per step, replayed as a CUDA
                                  graph, which measured faster.  Same results either way. */
+  int32_t pdl;                /* 1 (default): each V-cycle kernel after the first is launched with
+                                 programmatic dependent launch, so its CTAs are scheduled while the
+                                 previous kernel drains and wait on the device for its completion;
+                                 0: plain stream order.  Same results either way. */
+  int32_t ilu_scope;          /* PS_ILU_GLOBAL (default): ILU(0) of the whole S_ff^(FS); PS_ILU_LOCAL:
+                                 processor-local ILU(0), the ILU(0) of S_ff^(FS) without the blocks that
+                                 couple different subdomains (columns of PS_ILU_TILE_Y x PS_ILU_TILE_Z
+                                 cells), whose sweeps need no exchange between subdomains */
 } ps_params;
 
 typedef struct {

@@ -20,6 +20,8 @@ PS_SMOOTH_L1JACOBI, PS_SMOOTH_CHEBYSHEV = 0, 1
 PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
 PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1
 PS_LOCAL_ILU0, PS_LOCAL_HBGS = 0, 1
+PS_ILU_GLOBAL, PS_ILU_LOCAL = 0, 1
+PS_ILU_TILE_Y, PS_ILU_TILE_Z = 16, 8
 PS_CPR_QUASI_IMPES, PS_CPR_TRUE_IMPES = 0, 1
 PS_SOLVER_FGMRES, PS_SOLVER_RICHARDSON = 0, 1
 PS_FS_GIVEN, PS_FS_RSL = 0, 1
@@ -53,7 +55,8 @@ class ps_params(C.Structure):
                 ("hbm_budget", C.c_int64), ("stream", C.c_void_p), ("test_stall_wave", C.c_int32),
                 ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
                 ("local_stage", C.c_int32), ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
-                ("solver", C.c_int32), ("fs_mode", C.c_int32), ("vcycle_tail", C.c_int32)]
+                ("solver", C.c_int32), ("fs_mode", C.c_int32), ("vcycle_tail", C.c_int32),
+                ("pdl", C.c_int32), ("ilu_scope", C.c_int32)]
 
 
 class ps_stats(C.Structure):

@@ -73,6 +73,8 @@ struct Amg {
   unsigned long long* tail_bar = nullptr;
   int* err = nullptr;
   int64_t spin_limit = 2000000;
+  // 1: the V-cycle's kernels after its first use programmatic dependent launch
+  int pdl = 1;
 };
 // destroys the captured V-cycle graph, if any
 void amg_release_graph(Amg& H);

@@ -197,6 +197,7 @@ ps_status build_flow(ps_handle* h) {
   F.local = h->prm.local_stage;
   F.cpr = h->prm.cpr_reduction;
   F.gs_sweeps = h->prm.local_sweeps;
+  F.ilu_local = h->prm.ilu_scope == PS_ILU_LOCAL ? 1 : 0;
   F.test_stall = h->prm.test_stall_wave;
   const double* dfs = h->dfs;
   if (h->prm.fs_mode == PS_FS_RSL) {
@@ -328,6 +329,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   // the V-cycles' bounded grid barriers report through the same flag as the wavefront waits
   h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
   h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_u.pdl = h->amg_p.pdl = h->prm.pdl ? 1 : 0;
   h->amg_u.spin_limit = h->amg_p.spin_limit = h->F.spin_limit;
   // Krylov workspace
   int m = h->m;
@@ -387,6 +389,8 @@ void ps_params_default(ps_params* p) {
   p->spin_limit = 2000000;
   p->ortho_sweep = 8;
   p->vcycle_tail = 0;
+  p->pdl = 1;
+  p->ilu_scope = PS_ILU_GLOBAL;
   p->local_stage = PS_LOCAL_ILU0;
   p->local_sweeps = 3;
 }
@@ -485,6 +489,7 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   amg_release_graph(h->amg_u);
   h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
   h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
+  h->amg_u.pdl = h->amg_p.pdl = h->prm.pdl ? 1 : 0;
   h->amg_u.spin_limit = h->amg_p.spin_limit = h->F.spin_limit;
   return PS_OK;
 }

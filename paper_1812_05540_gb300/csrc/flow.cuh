@@ -13,7 +13,12 @@ namespace ps_internal {
 // nx + kTY + kTZ - 2 steps.  Each cell has one record of kRec values per sweep.  The records are stored
 // in the order a CTA consumes them, [tile][step][thread][kRec], steps padded to whole copy windows, so
 // that one bulk copy moves a whole window of a tile.
-constexpr int kTY = 16, kTZ = 8, kRec = 20;
+constexpr int kTY = PS_ILU_TILE_Y, kTZ = PS_ILU_TILE_Z, kRec = 20;
+// processor-local ILU(0): face neighbours i and j lie in different subdomains (the sweep tiles above)
+__host__ __device__ inline bool cross_tile(int64_t i, int64_t j, int nx, int ny) {
+  const int64_t yi = (i / nx) % ny, zi = i / (int64_t(nx) * ny), yj = (j / nx) % ny, zj = j / (int64_t(nx) * ny);
+  return yi / kTY != yj / kTY || zi / kTZ != zj / kTZ;
+}
 template <class T>
 __host__ __device__ constexpr int win_cells() { return sizeof(T) == 4 ? 4 : 2; }  // steps per copy window
 // records per thread and tile of one sweep (a whole number of windows)
@@ -58,6 +63,7 @@ struct FlowStage {
   // (block Gauss-Seidel: per colour, the six face blocks and inv(S_ii) of each cell, 28 values, blocked
   // by 32 cells, [colour][p / 32][28][p % 32] with p the cell's index within its colour; see gs_index)
   int local = 0;
+  int ilu_local = 0;  // PS_ILU_LOCAL: no ILU(0) coupling between cells of different sweep tiles
   int cpr = 0;  // PS_CPR_QUASI_IMPES or PS_CPR_TRUE_IMPES
   int gs_sweeps = 3;
   int64_t gs_ncp = 0;  // slots per colour: nz * ny * ceil(nx / 2)

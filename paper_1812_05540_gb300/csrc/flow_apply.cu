@@ -118,11 +118,13 @@ __global__ void k_step4(int64_t nc, const int32_t* __restrict__ rp, const int32_
 
 // ILU forward sweep fused with step 6, one wavefront level:
 //   w_i = y_i - sum_j S_ij z_j ; u_i = w_i - sum_{k<i} S_ik t_k ; t_i = inv(U_ii) u_i
+// (processor-local scope: the sum over k leaves out cells of other tiles)
 template <class T>
 __global__ void k_ilu_fwd(const int32_t* __restrict__ cells, int32_t m, const int32_t* __restrict__ rp,
                           const int32_t* __restrict__ ci, const int32_t* __restrict__ diagpos,
                           const T* __restrict__ sff, const T* __restrict__ dinv, const T* __restrict__ y,
-                          const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ t) {
+                          const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ t, int nx, int ny,
+                          int local) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m) return;
   int32_t i = cells[idx];
@@ -134,7 +136,7 @@ __global__ void k_ilu_fwd(const int32_t* __restrict__ cells, int32_t m, const in
     T zsj = zs[j], zpj = zp[j];
     w0 -= S[0] * zsj + S[1] * zpj;
     w1 -= S[2] * zsj + S[3] * zpj;
-    if (q < qd) {
+    if (q < qd && !(local && cross_tile(i, j, nx, ny))) {
       T t0 = t[2 * j], t1 = t[2 * j + 1];
       w0 -= S[0] * t0 + S[1] * t1;
       w1 -= S[2] * t0 + S[3] * t1;
@@ -152,7 +154,7 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
                           const int32_t* __restrict__ ci, const int32_t* __restrict__ diagpos,
                           const T* __restrict__ sff, const T* __restrict__ dinv, const T* __restrict__ t,
                           const T* __restrict__ zs, const T* __restrict__ zp, T* __restrict__ dz,
-                          double* __restrict__ zout) {
+                          double* __restrict__ zout, int nx, int ny, int local) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m) return;
   int32_t i = cells[idx];
@@ -160,6 +162,7 @@ __global__ void k_ilu_bwd(const int32_t* __restrict__ cells, int32_t m, const in
   T a0 = T(0), a1 = T(0);
   for (int32_t q = qd + 1; q < rp[i + 1]; ++q) {
     int32_t j = ci[q];
+    if (local && cross_tile(i, j, nx, ny)) continue;
     const T* S = sff + int64_t(q) * 4;
     T d0 = dz[2 * j], d1 = dz[2 * j + 1];
     a0 += S[0] * d0 + S[1] * d1;
@@ -435,7 +438,7 @@ template <class T, bool FWD>
 __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz, int steps, const T* __restrict__ rec,
                                                          T* __restrict__ rec_bwd, double* __restrict__ zout,
                                                          uint64_t* halo, int* err, uint32_t tag, int64_t limit,
-                                                         int stall) {
+                                                         int stall, int local) {
   constexpr int W = win_cells<T>();
   __shared__ __align__(16) T buf[2][kTZ][kTY][2];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -452,11 +455,13 @@ __global__ void __launch_bounds__(kTY * kTZ) k_ilu_pencil(int nx, int ny, int nz
   const int last = nx + kTY + kTZ - 3;
   const int64_t nxy = int64_t(nx) * ny;
   const int ry = FWD ? ly : kTY - 1 - ly, rz = FWD ? lz : kTZ - 1 - lz;
-  const bool hy = valid && (FWD ? yy > 0 : yy + 1 < ny), hz = valid && (FWD ? zz > 0 : zz + 1 < nz);
+  // processor-local scope: a predecessor in another tile is not coupled, and no CTA waits on another
+  const bool hy = valid && (FWD ? yy > 0 : yy + 1 < ny) && !(local && ry == 0),
+             hz = valid && (FWD ? zz > 0 : zz + 1 < nz) && !(local && rz == 0);
   const bool gy = hy && ry == 0, gz = hz && rz == 0;  // predecessor lives in another CTA
   // this pencil feeds another CTA along y (z) when it sits on the far boundary
-  const bool py = valid && ry == kTY - 1 && (FWD ? yy + 1 < ny : yy > 0);
-  const bool pz = valid && rz == kTZ - 1 && (FWD ? zz + 1 < nz : zz > 0);
+  const bool py = !local && valid && ry == kTY - 1 && (FWD ? yy + 1 < ny : yy > 0);
+  const bool pz = !local && valid && rz == kTZ - 1 && (FWD ? zz + 1 < nz : zz > 0);
   const int64_t jy = FWD ? -int64_t(nx) : int64_t(nx), jz = FWD ? -nxy : nxy;
   const int64_t pbase = valid ? int64_t(nx) * (yy + int64_t(ny) * zz) : 0;
   const int off = ry + rz;  // step s handles pencil position xs = s - off
@@ -659,7 +664,8 @@ bool ilu_pencil(const FlowStage& F, const FlowWork<T>& W, double* zout, cudaStre
     int64_t lim = F.spin_limit;
     int stall = F.test_stall;
     int steps = F.pk_steps;
-    void* args[] = {&nx, &ny, &nz, &steps, &rec, &rec_bwd, &zout, &halo, &err, &tag, &lim, &stall};
+    int local = F.ilu_local;
+    void* args[] = {&nx, &ny, &nz, &steps, &rec, &rec_bwd, &zout, &halo, &err, &tag, &lim, &stall, &local};
     const void* fn = dir == 0 ? (const void*)k_ilu_pencil<T, true> : (const void*)k_ilu_pencil<T, false>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(win_bytes<T>()));
     cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kTY * kTZ, args, win_bytes<T>(), st);
@@ -706,12 +712,12 @@ void alg1_steps_6_8(const FlowStage& F, const FlowWork<T>& W, double* zout, int 
   for (int l = 0; l < F.nlev; ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
     PS_TICK(); k_ilu_fwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
-                                                   V.dinv, W.y, W.zs, W.zp, W.t);
+                                                   V.dinv, W.y, W.zs, W.zp, W.t, F.nx, F.ny, F.ilu_local);
   }
   for (int l = F.nlev - 1; l >= 0; --l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
     PS_TICK(); k_ilu_bwd<T><<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, V.sff,
-                                                   V.dinv, W.t, W.zs, W.zp, W.dz, zout);
+                                                   V.dinv, W.t, W.zs, W.zp, W.dz, zout, F.nx, F.ny, F.ilu_local);
   }
 }
 

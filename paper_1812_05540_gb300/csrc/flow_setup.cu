@@ -99,9 +99,11 @@ __global__ void k_level_fill(int nx, int ny, int nz, int32_t* __restrict__ curso
 // 7-point stencil no two lower neighbours of a cell are coupled, so the IKJ
 // elimination only updates the diagonal block:
 //   U_ii = S_ii - sum_{k<i} (S_ik inv(U_kk)) S_ki   (k ascending)
+// Processor-local scope (local != 0): lower neighbours in another sweep tile are left out, which is the
+// ILU(0) of S_ff^(FS) without the blocks that couple different tiles.
 __global__ void k_ilu_factor(const int32_t* __restrict__ cells, int32_t ncell_lev, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ ci, const int32_t* __restrict__ diagpos,
-                             const double* __restrict__ sff, double* __restrict__ dinv) {
+                             const double* __restrict__ sff, double* __restrict__ dinv, int nx, int ny, int local) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncell_lev) return;
   int32_t i = cells[t];
@@ -109,6 +111,7 @@ __global__ void k_ilu_factor(const int32_t* __restrict__ cells, int32_t ncell_le
   double D[4] = {sff[int64_t(qd) * 4], sff[int64_t(qd) * 4 + 1], sff[int64_t(qd) * 4 + 2], sff[int64_t(qd) * 4 + 3]};
   for (int32_t q = rp[i]; q < qd; ++q) {
     int32_t k = ci[q];
+    if (local && cross_tile(i, k, nx, ny)) continue;
     double L[4], U[4];
     mul22(&sff[int64_t(q) * 4], &dinv[int64_t(k) * 4], L);
     // (k, i) is the upper block of row k
@@ -173,18 +176,22 @@ __global__ void k_aps_st(int64_t nc, const T* __restrict__ s28, T* __restrict__ 
   for (int q = 0; q < 7; ++q) out[((c >> 5) * 7 + q) * 32 + (c & 31)] = s28[c * 28 + q * 4 + 2];
 }
 
-// S/inv(U_ii) part of the sweep records (see FlowStage): forward lower blocks, backward upper blocks
+// S/inv(U_ii) part of the sweep records (see FlowStage): forward lower blocks, backward upper blocks; with
+// the processor-local scope the blocks towards another tile are zero
 template <class T>
 __global__ void k_pack_sd(int nx, int ny, int nz, int steps, const T* __restrict__ s28, const T* __restrict__ dinv,
-                          T* __restrict__ pf, T* __restrict__ pb) {
+                          T* __restrict__ pf, T* __restrict__ pb, int local) {
   int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (c >= int64_t(nx) * ny * nz) return;
   const int x = int(c % nx), y = int((c / nx) % ny), z = int(c / (int64_t(nx) * ny));
   T* f = pf + sweep_rec(true, nx, ny, steps, x, y, z);
   T* b = pb + sweep_rec(false, nx, ny, steps, x, y, z);
+  // forward slots z-1, y-1, x-1; backward slots x+1, y+1, z+1
+  const bool fkeep[3] = {!local || z % kTZ != 0, !local || y % kTY != 0, true};
+  const bool bkeep[3] = {true, !local || y % kTY != kTY - 1, !local || z % kTZ != kTZ - 1};
   for (int e = 0; e < 12; ++e) {
-    f[e] = s28[c * 28 + e];
-    b[e] = s28[c * 28 + 16 + e];
+    f[e] = fkeep[e / 4] ? s28[c * 28 + e] : T(0);
+    b[e] = bkeep[e / 4] ? s28[c * 28 + 16 + e] : T(0);
   }
   for (int e = 0; e < 4; ++e) {
     f[12 + e] = dinv[c * 4 + e];
@@ -280,7 +287,7 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
   for (int l = 0; l < (F.local == PS_LOCAL_HBGS ? 0 : F.nlev); ++l) {
     int32_t m = F.lev_off[l + 1] - F.lev_off[l];
     PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
-                                                   F.dinv);
+                                                   F.dinv, F.nx, F.ny, F.ilu_local);
   }
   PS_TICK(); k_s28<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.rp, F.sff, F.s28);
   PS_CUDA(cudaGetLastError());
@@ -300,14 +307,14 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
     PS_CUDA(cudaGetLastError());
     if (F.pk_fwd_f) {
       PS_TICK(); k_pack_sd<float><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28_f, F.dinv_f,
-                                                                    F.pk_fwd_f, F.pk_bwd_f);
+                                                                    F.pk_fwd_f, F.pk_bwd_f, F.ilu_local);
     }
     if (!F.aps_st_f) PS_TRY(ar.alloc(&F.aps_st_f, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<float><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28_f, F.aps_st_f);
   } else {
     if (F.pk_fwd_d) {
       PS_TICK(); k_pack_sd<double><<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.pk_steps, F.s28, F.dinv,
-                                                                     F.pk_fwd_d, F.pk_bwd_d);
+                                                                     F.pk_fwd_d, F.pk_bwd_d, F.ilu_local);
     }
     if (!F.aps_st_d) PS_TRY(ar.alloc(&F.aps_st_d, size_t((nc + 31) / 32) * 32 * 7));
     PS_TICK(); k_aps_st<double><<<grid_for(nc, 256), 256, 0, st>>>(nc, F.s28, F.aps_st_d);

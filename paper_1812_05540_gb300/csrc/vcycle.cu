@@ -26,6 +26,16 @@ __device__ __forceinline__ T val_as(const __nv_bfloat16* p) { return T(__bfloat1
 __device__ __forceinline__ float mad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Programmatic dependent launch.  The V-cycle's kernels after its first are launched with programmatic
+// stream serialisation (vl below), so a kernel's CTAs may be scheduled while its predecessor drains.  Every
+// such kernel first waits at griddepcontrol.wait, which returns once the predecessor grid has completed and
+// its memory operations are visible, and only then reads or writes anything; it then lets its own successor
+// launch.  A kernel launched without the attribute passes both instructions at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <class T, int NC, int LANES>
 struct Row {
   // s[c] = sum_q v[q*NC+c] * x[j*NC+c] over one CSR row with LANES lanes; all lanes get the sum
@@ -112,6 +122,7 @@ struct StencilRows {
 };
 
 #define ROWS_SETUP                                                \
+  pdl_enter();                                                    \
   int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  \
   int64_t i = tid / A::kLanes;                                    \
   int sub = int(tid % A::kLanes);                                 \
@@ -186,6 +197,7 @@ __global__ void k_l1_step(A a, int64_t n, const T* __restrict__ dl1, const T* __
 
 template <class T, int NC>
 __global__ void k_l1_first(int64_t n, const T* __restrict__ dl1, const T* __restrict__ b, T* __restrict__ x) {
+  pdl_enter();
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n * NC) x[t] = b[t] / dl1[t];
 }
@@ -194,6 +206,7 @@ __global__ void k_l1_first(int64_t n, const T* __restrict__ dl1, const T* __rest
 template <class T, int NC>
 __global__ void k_cheb_first1(int64_t n, const T* __restrict__ dg, const T* __restrict__ b, T* __restrict__ x,
                               T* __restrict__ d, double3 inv_theta) {
+  pdl_enter();
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const double it[3] = {inv_theta.x, inv_theta.y, inv_theta.z};
   if (t < n * NC) {
@@ -216,6 +229,7 @@ __global__ void k_resid(A a, int64_t n, const T* __restrict__ b, const T* __rest
 }
 
 #define ROW_SETUP                                                        \
+  pdl_enter();                                                           \
   int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;         \
   int64_t i = tid / LANES;                                               \
   int sub = int(tid % LANES);                                            \
@@ -239,6 +253,7 @@ __global__ void k_spmv(int64_t n, const int32_t* __restrict__ rp, const int32_t*
 // in both precisions (the coarsest solve is one of the FP64 parts of the mixed mode)
 template <class T, int NC>
 __global__ void k_dense_solve(int64_t n, const double* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  pdl_enter();
   int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n * NC) return;
@@ -469,6 +484,27 @@ void with_rows(const AmgLevel& L, const LevelT<T>& V, F&& f) {
   }
 }
 
+// Launch state of the V-cycle being enqueued by this host thread: 0 plain launches; 1 the next launch is the
+// V-cycle's first (plain), later ones programmatic; 2 programmatic launches.
+thread_local int t_pdl = 0;
+
+// launch of a V-cycle kernel with 256 threads per CTA, programmatic when t_pdl says so
+template <class... KA, class... Args>
+void vl(void (*k)(KA...), unsigned grid, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = t_pdl == 2 ? 1 : 0;
+  if (t_pdl == 1) t_pdl = 2;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <class A>
 inline unsigned rows_grid(int64_t n) {
   return grid_for(n * A::kLanes, 256);
@@ -521,30 +557,30 @@ T* smooth_zero(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, co
       // steps 0 and 1 in one pass
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
-        PS_TICK(); k_cheb_zero2<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, static_cast<const T*>(L.dsi),
+        PS_TICK(); vl(k_cheb_zero2<T, NC, A>, rows_grid<A>(n), st, a, n, V.dg, static_cast<const T*>(L.dsi),
                                                                             b, x, deg > 2 ? d : nullptr, cc.c1[1],
                                                                             cc.c2[1]);
       });
       k0 = 2;
     } else {
-      PS_TICK(); k_cheb_first1<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dg, b, x, deg > 1 ? d : nullptr,
+      PS_TICK(); vl(k_cheb_first1<T, NC>, grid_for(n * NC, 256), st, n, V.dg, b, x, deg > 1 ? d : nullptr,
                                                                           cc.inv_theta);
     }
     for (int k = k0; k < deg; ++k) {
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
-        PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, other,
+        PS_TICK(); vl(k_cheb_step<T, NC, A>, rows_grid<A>(n), st, a, n, V.dg, b, cur, other,
                                                                            d, cc.c1[k], cc.c2[k], 0,
                                                                            k < deg - 1);
       });
       std::swap(cur, other);
     }
   } else {
-    PS_TICK(); k_l1_first<T, NC><<<grid_for(n * NC, 256), 256, 0, st>>>(n, V.dl1, b, x);
+    PS_TICK(); vl(k_l1_first<T, NC>, grid_for(n * NC, 256), st, n, V.dl1, b, x);
     for (int k = 1; k < sp.pre; ++k) {
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
-        PS_TICK(); k_l1_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dl1, b, cur, other);
+        PS_TICK(); vl(k_l1_step<T, NC, A>, rows_grid<A>(n), st, a, n, V.dl1, b, cur, other);
       });
       std::swap(cur, other);
     }
@@ -565,10 +601,10 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
         if (k == 0) {
-          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst, d, cc.c1[0],
+          PS_TICK(); vl(k_cheb_step<T, NC, A>, rows_grid<A>(n), st, a, n, V.dg, b, cur, dst, d, cc.c1[0],
                                                                              cc.post_c2, 1, deg > 1);
         } else {
-          PS_TICK(); k_cheb_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dg, b, cur, dst, d, cc.c1[k],
+          PS_TICK(); vl(k_cheb_step<T, NC, A>, rows_grid<A>(n), st, a, n, V.dg, b, cur, dst, d, cc.c1[k],
                                                                              cc.c2[k], 0, k < deg - 1);
         }
       });
@@ -581,7 +617,7 @@ void smooth_post(const AmgLevel& L, const LevelT<T>& V, const SmoothParams& sp, 
       T* dst = k == sweeps - 1 ? out : other;
       with_rows<T, NC>(L, V, [&](auto a) {
         using A = decltype(a);
-        PS_TICK(); k_l1_step<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, V.dl1, b, cur, dst);
+        PS_TICK(); vl(k_l1_step<T, NC, A>, rows_grid<A>(n), st, a, n, V.dl1, b, cur, dst);
       });
       other = cur;
       cur = dst;
@@ -593,12 +629,12 @@ template <class T, int NC, class TV>
 void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, const TV* v, const T* x, T* y, int add,
                 cudaStream_t st) {
   switch (lanes) {
-    case 1: PS_TICK(); k_spmv<T, NC, 1, TV><<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 2: PS_TICK(); k_spmv<T, NC, 2, TV><<<grid_for(n * 2, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 4: PS_TICK(); k_spmv<T, NC, 4, TV><<<grid_for(n * 4, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 8: PS_TICK(); k_spmv<T, NC, 8, TV><<<grid_for(n * 8, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    case 16: PS_TICK(); k_spmv<T, NC, 16, TV><<<grid_for(n * 16, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
-    default: PS_TICK(); k_spmv<T, NC, 32, TV><<<grid_for(n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, y, add); break;
+    case 1: PS_TICK(); vl(k_spmv<T, NC, 1, TV>, grid_for(n, 256), st, n, rp, ci, v, x, y, add); break;
+    case 2: PS_TICK(); vl(k_spmv<T, NC, 2, TV>, grid_for(n * 2, 256), st, n, rp, ci, v, x, y, add); break;
+    case 4: PS_TICK(); vl(k_spmv<T, NC, 4, TV>, grid_for(n * 4, 256), st, n, rp, ci, v, x, y, add); break;
+    case 8: PS_TICK(); vl(k_spmv<T, NC, 8, TV>, grid_for(n * 8, 256), st, n, rp, ci, v, x, y, add); break;
+    case 16: PS_TICK(); vl(k_spmv<T, NC, 16, TV>, grid_for(n * 16, 256), st, n, rp, ci, v, x, y, add); break;
+    default: PS_TICK(); vl(k_spmv<T, NC, 32, TV>, grid_for(n * 32, 256), st, n, rp, ci, v, x, y, add); break;
   }
 }
 
@@ -634,7 +670,7 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
       launch_tail<T, NC>(H, st))
     return;
   if (L.coarsest) {
-    PS_TICK(); k_dense_solve<T, NC><<<grid_for(n * NC * 32, 256), 256, 0, st>>>(n, V.inv, b, out);
+    PS_TICK(); vl(k_dense_solve<T, NC>, grid_for(n * NC * 32, 256), st, n, V.inv, b, out);
     return;
   }
   T* x = static_cast<T*>(L.x);
@@ -647,7 +683,7 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
   T* xs = smooth_zero<T, NC>(L, V, sp, b, x, t, d, st);
   with_rows<T, NC>(L, V, [&](auto a) {
     using A = decltype(a);
-    PS_TICK(); k_resid<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, b, xs, r);
+    PS_TICK(); vl(k_resid<T, NC, A>, rows_grid<A>(n), st, a, n, b, xs, r);
   });
   if (L.rvb && sizeof(T) == 4) spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, L.rvb, r, bc, 0, st);
   else spmv_lanes<T, NC>(L.rlane, C.n, L.rrp, L.rci, V.rv, r, bc, 0, st);
@@ -659,8 +695,10 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
 
 template <class T>
 void vcycle_launch(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_t st) {
+  t_pdl = H.pdl ? 1 : 0;
   if (H.nc == 3) vcycle_level<T, 3>(H, 0, sp, b, x, st);
   else vcycle_level<T, 1>(H, 0, sp, b, x, st);
+  t_pdl = 0;
 }
 
 }  // namespace
