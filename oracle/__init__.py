@@ -24,7 +24,7 @@ _LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 OR_GRAVITY, OR_DIRICHLET, OR_SCALE, OR_ACCUM, OR_FLUX, OR_FLUX_SAT, OR_COUPLING = (1 << i for i in range(7))
 OR_ALL = 0x7F
 FIELDS_LOGNORMAL, FIELDS_LAYERED, FIELDS_CHANNELS, FIELDS_HOMOGENEOUS = range(4)
-MECH_AMG, MECH_EXACT = 0, 1
+MECH_AMG, MECH_EXACT, MECH_AMG_RBM = 0, 1, 2
 FLOW_CPR, FLOW_EXACT_FS, FLOW_EXACT_SCHUR = 0, 1, 2
 LOCAL_ILU0, LOCAL_EXACT, LOCAL_GS = 0, 1, 2
 PRESS_AMG, PRESS_EXACT = 0, 1
@@ -144,6 +144,13 @@ def lib(openmp=None):
         L.or_amg_p_nnz.restype = C.c_int64
         L.or_amg_prolongator.argtypes = [C.c_void_p, C.c_int, C.c_int, _PI64, _PI32, _PD]
         L.or_amg_vcycle.argtypes = [C.c_void_p, C.c_int, C.c_int, _PD, _PD]
+        L.or_rbm_nlevels.argtypes = [C.c_void_p]
+        L.or_rbm_level_shape.argtypes = [C.c_void_p, C.c_int, _PI64]
+        L.or_rbm_level_matrix.argtypes = [C.c_void_p, C.c_int, _PI64, _PI32, _PD]
+        L.or_rbm_level_data.argtypes = [C.c_void_p, C.c_int, _PI32, _PD, _PD, _PD]
+        L.or_rbm_prolongator.argtypes = [C.c_void_p, C.c_int, _PI64, _PI32, _PD]
+        L.or_rbm_vcycle.argtypes = [C.c_void_p, _PD, _PD]
+        L.or_rigid_body_modes.argtypes = [C.c_int, C.c_int, C.c_int, _PD]
         L.or_spp_nnz.argtypes = [C.c_void_p]
         L.or_spp_nnz.restype = C.c_int64
         L.or_spp.argtypes = [C.c_void_p, _PI64, _PI32, _PD]
@@ -167,6 +174,12 @@ def lib(openmp=None):
         L.or_terzaghi.argtypes = [C.POINTER(TerzaghiParams), _PD, _PD, _PD, _PD, _PD]
         _libs[openmp] = L
     return _libs[openmp]
+
+
+def rigid_body_modes(nx, ny, nz):
+    B = np.empty(((nx + 1) * (ny + 1) * (nz + 1) * 3, 6))
+    lib().or_rigid_body_modes(nx, ny, nz, _d(B))
+    return B
 
 
 def num_threads(openmp=None):
@@ -328,6 +341,51 @@ class Prec:
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.empty_like(b)
         self._L.or_amg_vcycle(self._h, which, comp, _d(b), _d(x))
+        return x
+
+    # rigid-body-mode smoothed aggregation (mech_mode=MECH_AMG_RBM)
+    def rbm_nlevels(self):
+        return self._L.or_rbm_nlevels(self._h)
+
+    def rbm_shape(self, l):
+        sh = np.zeros(6, np.int64)
+        assert self._L.or_rbm_level_shape(self._h, l, sh.ctypes.data_as(_PI64)) == 0
+        return dict(n=int(sh[0]), b=int(sh[1]), nnzb=int(sh[2]), nagg=int(sh[3]), pnnzb=int(sh[4]),
+                    coarsest=bool(sh[5]))
+
+    def rbm_level(self, l):
+        sh = self.rbm_shape(l)
+        n, b, nnz = sh["n"], sh["b"], sh["nnzb"]
+        rp = np.empty(n + 1, np.int64)
+        ci = np.empty(nnz, np.int32)
+        v = np.empty(nnz * b * b)
+        self._L.or_rbm_level_matrix(self._h, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32), _d(v))
+        return rp, ci, v.reshape(nnz, b, b)
+
+    def rbm_data(self, l):
+        sh = self.rbm_shape(l)
+        n, b = sh["n"], sh["b"]
+        agg = np.empty(n, np.int32)
+        B = np.empty((n * b, 6))
+        Pt = np.empty((n * b, 6))
+        lam = np.zeros(1)
+        self._L.or_rbm_level_data(self._h, l, agg.ctypes.data_as(_PI32), _d(B), _d(Pt), _d(lam))
+        return agg, B, Pt, float(lam[0])
+
+    def rbm_prolongator(self, l):
+        sh = self.rbm_shape(l)
+        n, b, nnz = sh["n"], sh["b"], sh["pnnzb"]
+        rp = np.empty(n + 1, np.int64)
+        ci = np.empty(nnz, np.int32)
+        v = np.empty(nnz * b * 6)
+        assert self._L.or_rbm_prolongator(self._h, l, rp.ctypes.data_as(_PI64), ci.ctypes.data_as(_PI32),
+                                          _d(v)) == 0
+        return rp, ci, v.reshape(nnz, b, 6)
+
+    def rbm_vcycle(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        assert self._L.or_rbm_vcycle(self._h, _d(b), _d(x)) == 0
         return x
 
     def spp(self):

@@ -1190,6 +1190,375 @@ void bsr_dense(const BSR& A, vec& d, int64_t r0, int64_t c0, int64_t ld) {
           d[(r0 + I * A.br + a) * ld + c0 + int64_t(A.ci[q]) * A.bc + b] = A.v[(q * A.br + a) * A.bc + b];
 }
 
+
+// ---------------------------------------------------------------------------
+// Rigid-body-mode smoothed aggregation on the full A_uu: the usual AMG for elasticity, the alternative to the
+// separate-displacement-component approximation that §5.2 takes.  Block operators (3 x 3 at the finest
+// level, 6 x 6 below), a near-nullspace of the six rigid-body modes, a tentative prolongator from a modified
+// Gram-Schmidt QR of the modes restricted to each aggregate, P = (I - omega D^{-1} A) P_tent with the point
+// diagonal D, Galerkin coarse operators, Chebyshev smoothing on D^{-1} A and dense LU on the coarsest level.
+// ---------------------------------------------------------------------------
+constexpr int kModes = 6;
+
+struct BLevel {
+  BSR A, P, R;               // A: b x b blocks, P: b x 6, R = P^T: 6 x b
+  int b = 3;
+  std::vector<int32_t> agg;  // aggregate of each node (-1: not aggregated)
+  int64_t nagg = 0;
+  vec B;                     // near-nullspace, n b rows of 6
+  vec Pt;                    // tentative prolongator, n b rows of 6 (zero rows for nodes outside aggregates)
+  vec dg;                    // point diagonal, n b
+  double lam = 0.0;          // Gershgorin bound of rho(D^{-1} A) over the point rows
+  DenseLU lu;                // coarsest level
+  bool coarsest = false;
+};
+struct BAMG {
+  std::vector<BLevel> L;
+};
+
+// y = A x over point rows; each point row sums its blocks in column order, a block's entries in column order
+void bsr_apply(const BSR& A, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < A.nbr; ++i)
+    for (int a = 0; a < A.br; ++a) {
+      double s = 0.0;
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        for (int e = 0; e < A.bc; ++e) s = s + A.v[(q * A.br + a) * A.bc + e] * x[int64_t(A.ci[q]) * A.bc + e];
+      y[i * A.br + a] = s;
+    }
+}
+
+// transpose with transposed blocks; entries of each output row in ascending input-row order
+BSR bsr_transpose(const BSR& A) {
+  BSR T; T.nbr = A.nbc; T.nbc = A.nbr; T.br = A.bc; T.bc = A.br;
+  T.rp.assign(T.nbr + 1, 0);
+  for (int32_t c : A.ci) T.rp[c + 1]++;
+  for (int64_t i = 0; i < T.nbr; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size()); T.v.resize(A.v.size());
+  std::vector<int64_t> fill(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t i = 0; i < A.nbr; ++i)
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+      int64_t pos = fill[A.ci[q]]++;
+      T.ci[pos] = int32_t(i);
+      for (int a = 0; a < A.br; ++a)
+        for (int e = 0; e < A.bc; ++e) T.v[(pos * T.br + e) * T.bc + a] = A.v[(q * A.br + a) * A.bc + e];
+    }
+  return T;
+}
+
+// C = X Y with block products.  For each output block the block products X_ik Y_kj are added in ascending
+// order of k, starting from zero; each entry of a block product sums its inner index in ascending order.
+BSR bsr_spgemm(const BSR& X, const BSR& Y) {
+  BSR C; C.nbr = X.nbr; C.nbc = Y.nbc; C.br = X.br; C.bc = Y.bc;
+  const int br = X.br, bk = X.bc, bc = Y.bc, bs = br * bc;
+  C.rp.assign(C.nbr + 1, 0);
+  std::vector<std::vector<int32_t>> tci(kTasks);
+  std::vector<vec> tv(kTasks);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < kTasks; ++t) {
+    std::vector<int64_t> mark(Y.nbc, -1);
+    vec acc(size_t(Y.nbc) * bs, 0.0);
+    std::vector<int32_t> cols;
+    for (int64_t i = task_lo(X.nbr, t); i < task_lo(X.nbr, t + 1); ++i) {
+      cols.clear();
+      for (int64_t q = X.rp[i]; q < X.rp[i + 1]; ++q) {
+        const int64_t k = X.ci[q];
+        const double* xb = &X.v[q * br * bk];
+        for (int64_t r = Y.rp[k]; r < Y.rp[k + 1]; ++r) {
+          const int64_t j = Y.ci[r];
+          const double* yb = &Y.v[r * bk * bc];
+          if (mark[j] != i) {
+            mark[j] = i;
+            cols.push_back(int32_t(j));
+            for (int e = 0; e < bs; ++e) acc[j * bs + e] = 0.0;
+          }
+          for (int a = 0; a < br; ++a)
+            for (int c = 0; c < bc; ++c) {
+              double p = 0.0;
+              for (int e = 0; e < bk; ++e) p = p + xb[a * bk + e] * yb[e * bc + c];
+              acc[j * bs + a * bc + c] = acc[j * bs + a * bc + c] + p;
+            }
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int32_t j : cols) {
+        tci[t].push_back(j);
+        for (int e = 0; e < bs; ++e) tv[t].push_back(acc[j * bs + e]);
+      }
+      C.rp[i + 1] = int64_t(cols.size());
+    }
+  }
+  for (int64_t i = 0; i < C.nbr; ++i) C.rp[i + 1] += C.rp[i];
+  for (int t = 0; t < kTasks; ++t) {
+    C.ci.insert(C.ci.end(), tci[t].begin(), tci[t].end());
+    C.v.insert(C.v.end(), tv[t].begin(), tv[t].end());
+  }
+  return C;
+}
+
+// the six rigid-body modes at the nodes of the grid: translations along x, y, z and rotations about the
+// axes through the grid's centre, (0, -z, y), (z, 0, -x), (-y, x, 0), coordinates in cell widths
+vec rigid_body_modes(int nx, int ny, int nz) {
+  const int64_t nn = int64_t(nx + 1) * (ny + 1) * (nz + 1);
+  vec B(size_t(nn) * 3 * kModes, 0.0);
+  for (int64_t I = 0; I < nn; ++I) {
+    const int64_t i = I % (nx + 1), j = (I / (nx + 1)) % (ny + 1), k = I / (int64_t(nx + 1) * (ny + 1));
+    const double x = double(i) - 0.5 * nx, y = double(j) - 0.5 * ny, z = double(k) - 0.5 * nz;
+    double* r = &B[I * 3 * kModes];
+    // row d of node I: r[d * 6 + mode]
+    r[0 * 6 + 0] = 1.0; r[1 * 6 + 1] = 1.0; r[2 * 6 + 2] = 1.0;
+    r[1 * 6 + 3] = -z; r[2 * 6 + 3] = y;
+    r[0 * 6 + 4] = z;  r[2 * 6 + 4] = -x;
+    r[0 * 6 + 5] = -y; r[1 * 6 + 5] = x;
+  }
+  return B;
+}
+
+// strength matrix of a block operator: one value per block, its Frobenius norm (entries summed row by row)
+CSR block_strength(const BSR& A) {
+  CSR S; S.n = A.nbr; S.m = A.nbc; S.nc = 1; S.rp = A.rp; S.ci = A.ci;
+  const int bs = A.br * A.bc;
+  S.v.resize(A.ci.size());
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < int64_t(A.ci.size()); ++q) {
+    double s = 0.0;
+    for (int e = 0; e < bs; ++e) s = s + A.v[q * bs + e] * A.v[q * bs + e];
+    S.v[q] = std::sqrt(s);
+  }
+  return S;
+}
+
+// lambda_hat = max over point rows of sum_j |a_ij| / |a_ii| (blocks in column order, entries in column order)
+double block_gershgorin(const BSR& A) {
+  const int b = A.br;
+  vec ratio(A.nbr * b, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < A.nbr; ++i)
+    for (int a = 0; a < b; ++a) {
+      double s = 0.0, d = 0.0;
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        for (int e = 0; e < A.bc; ++e) {
+          const double v = A.v[(q * b + a) * A.bc + e];
+          s = s + std::fabs(v);
+          if (A.ci[q] == i && e == a) d = v;
+        }
+      ratio[i * b + a] = s / std::fabs(d);
+    }
+  double lam = 0.0;
+  for (double r : ratio) lam = std::max(lam, r);
+  return lam;
+}
+
+// Tentative prolongator and coarse near-nullspace: per aggregate (nodes in ascending order, b rows each) the
+// modes restricted to the aggregate, B_a = Q_a R_a by modified Gram-Schmidt (columns in order; a column whose
+// remainder is at most 1e-10 of its norm is dependent on the earlier ones: zero column of Q_a, zero row of
+// R_a).  P_tent has one b x 6 block per aggregated node, Q_a's rows of that node; the coarse modes are R_a.
+void tentative(BLevel& lev, vec& Bc) {
+  const int b = lev.b;
+  const int64_t n = lev.A.nbr;
+  std::vector<std::vector<int64_t>> mem(lev.nagg);
+  for (int64_t i = 0; i < n; ++i)
+    if (lev.agg[i] >= 0) mem[lev.agg[i]].push_back(i);
+  lev.Pt.assign(size_t(n) * b * kModes, 0.0);
+  Bc.assign(size_t(lev.nagg) * kModes * kModes, 0.0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t a = 0; a < lev.nagg; ++a) {
+    const int64_t m = int64_t(mem[a].size()) * b;
+    vec Q(size_t(m) * kModes);
+    for (size_t t = 0; t < mem[a].size(); ++t)
+      for (int d = 0; d < b; ++d)
+        for (int k = 0; k < kModes; ++k) Q[(t * b + d) * kModes + k] = lev.B[(mem[a][t] * b + d) * kModes + k];
+    double R[kModes][kModes] = {{0.0}};
+    for (int k = 0; k < kModes; ++k) {
+      double n0 = 0.0;
+      for (int64_t r = 0; r < m; ++r) n0 = n0 + Q[r * kModes + k] * Q[r * kModes + k];
+      n0 = std::sqrt(n0);
+      for (int j = 0; j < k; ++j) {
+        double c = 0.0;
+        for (int64_t r = 0; r < m; ++r) c = c + Q[r * kModes + j] * Q[r * kModes + k];
+        R[j][k] = c;
+        for (int64_t r = 0; r < m; ++r) Q[r * kModes + k] = Q[r * kModes + k] - c * Q[r * kModes + j];
+      }
+      double nk = 0.0;
+      for (int64_t r = 0; r < m; ++r) nk = nk + Q[r * kModes + k] * Q[r * kModes + k];
+      nk = std::sqrt(nk);
+      if (nk > 1e-10 * n0 && nk > 0.0) {
+        R[k][k] = nk;
+        for (int64_t r = 0; r < m; ++r) Q[r * kModes + k] = Q[r * kModes + k] / nk;
+      } else {
+        for (int64_t r = 0; r < m; ++r) Q[r * kModes + k] = 0.0;
+      }
+    }
+    for (size_t t = 0; t < mem[a].size(); ++t)
+      for (int d = 0; d < b; ++d)
+        for (int k = 0; k < kModes; ++k) lev.Pt[(mem[a][t] * b + d) * kModes + k] = Q[(t * b + d) * kModes + k];
+    for (int r = 0; r < kModes; ++r)
+      for (int k = 0; k < kModes; ++k) Bc[(a * kModes + r) * kModes + k] = R[r][k];
+  }
+}
+
+// P = (I - omega D^{-1} A) P_tent, omega = (4/3) / lambda_hat.  Row of node i (none for nodes that aggregation
+// left out): a block for every aggregate among the nodes of A's row, in ascending order;
+// block(i, a) = [a == agg(i)] P_tent(i) - omega D_i^{-1} S, S = sum over the row's nodes j in aggregate a
+// (ascending) of A_ij P_tent(j).
+BSR rbm_prolongator(const BLevel& lev) {
+  const BSR& A = lev.A;
+  const int b = lev.b;
+  const int64_t n = A.nbr;
+  const double omega = (4.0 / 3.0) / lev.lam;
+  BSR P; P.nbr = n; P.nbc = lev.nagg; P.br = b; P.bc = kModes; P.rp.assign(n + 1, 0);
+  const int bs = b * kModes;
+  std::vector<std::vector<int32_t>> tci(kTasks);
+  std::vector<vec> tv(kTasks);
+  std::vector<uint8_t> excl(n, 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+      if (A.ci[q] != i)
+        for (int e = 0; e < b * b; ++e)
+          if (A.v[q * b * b + e] != 0.0) excl[i] = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < kTasks; ++t) {
+    std::vector<int32_t> aggs;
+    for (int64_t i = task_lo(n, t); i < task_lo(n, t + 1); ++i) {
+      if (excl[i]) continue;
+      aggs.clear();
+      for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q)
+        if (lev.agg[A.ci[q]] >= 0) aggs.push_back(lev.agg[A.ci[q]]);
+      std::sort(aggs.begin(), aggs.end());
+      aggs.erase(std::unique(aggs.begin(), aggs.end()), aggs.end());
+      for (int32_t a : aggs) {
+        double S[6][kModes] = {{0.0}};
+        for (int64_t q = A.rp[i]; q < A.rp[i + 1]; ++q) {
+          const int64_t j = A.ci[q];
+          if (lev.agg[j] != a) continue;
+          for (int r = 0; r < b; ++r)
+            for (int c = 0; c < kModes; ++c) {
+              double p = 0.0;
+              for (int e = 0; e < b; ++e) p = p + A.v[(q * b + r) * b + e] * lev.Pt[(j * b + e) * kModes + c];
+              S[r][c] = S[r][c] + p;
+            }
+        }
+        tci[t].push_back(a);
+        for (int r = 0; r < b; ++r)
+          for (int c = 0; c < kModes; ++c) {
+            const double delta = a == lev.agg[i] ? lev.Pt[(i * b + r) * kModes + c] : 0.0;
+            tv[t].push_back(delta - (omega / lev.dg[i * b + r]) * S[r][c]);
+          }
+      }
+      P.rp[i + 1] = int64_t(aggs.size());
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) P.rp[i + 1] += P.rp[i];
+  for (int t = 0; t < kTasks; ++t) {
+    P.ci.insert(P.ci.end(), tci[t].begin(), tci[t].end());
+    P.v.insert(P.v.end(), tv[t].begin(), tv[t].end());
+  }
+  (void)bs;
+  return P;
+}
+
+bool build_rbm(BAMG& H, BSR A0, vec B0, double theta0, int coarse_max, int max_levels) {
+  H.L.clear();
+  H.L.emplace_back();
+  H.L[0].A = std::move(A0);
+  H.L[0].b = 3;
+  H.L[0].B = std::move(B0);
+  double theta = theta0;
+  for (int l = 0;; ++l) {
+    BLevel& lev = H.L[l];
+    const int b = lev.b;
+    const int64_t n = lev.A.nbr;
+    bool coarsest = n <= coarse_max || l + 1 >= max_levels;
+    if (!coarsest) {
+      Level sl;
+      sl.A = block_strength(lev.A);
+      aggregate(sl, theta, l);
+      lev.agg = sl.agg;
+      lev.nagg = sl.nagg;
+      if (lev.nagg == 0 || double(n) / double(lev.nagg) < 1.2) coarsest = true;
+    }
+    lev.dg.assign(n * b, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t q = lev.A.find(i, i);
+      for (int a = 0; a < b; ++a) lev.dg[i * b + a] = lev.A.v[(q * b + a) * b + a];
+    }
+    if (coarsest) {
+      if (n * b > 12000) return false;
+      lev.coarsest = true;
+      lev.agg.clear(); lev.nagg = 0;
+      vec d(size_t(n * b) * (n * b), 0.0);
+      bsr_dense(lev.A, d, 0, 0, n * b);
+      lev.lu.factor(n * b, std::move(d));
+      break;
+    }
+    lev.lam = block_gershgorin(lev.A);
+    vec Bc;
+    tentative(lev, Bc);
+    lev.P = rbm_prolongator(lev);
+    lev.R = bsr_transpose(lev.P);
+    BSR AP = bsr_spgemm(lev.A, lev.P);
+    BSR Ac = bsr_spgemm(lev.R, AP);
+    // a mode that an aggregate cannot represent (dependent column of its QR) gives a zero prolongator column,
+    // hence a zero row and column of A_c: its diagonal entry is set to one, which decouples that coarse unknown
+    for (int64_t I = 0; I < Ac.nbr; ++I) {
+      const int64_t q = Ac.find(I, I);
+      for (int k = 0; k < kModes; ++k)
+        if (Ac.v[(q * kModes + k) * kModes + k] == 0.0) Ac.v[(q * kModes + k) * kModes + k] = 1.0;
+    }
+    H.L.emplace_back();
+    BLevel& nx = H.L[l + 1];
+    nx.A = std::move(Ac);
+    nx.b = kModes;
+    nx.B = std::move(Bc);
+    theta *= 0.5;
+  }
+  return true;
+}
+
+// Chebyshev smoother on D^{-1} A over [lambda_hat/ratio, lambda_hat], the recurrence of chebyshev() above
+void block_chebyshev(const BLevel& lev, const vec& b, vec& x, int degree, double ratio, bool zero) {
+  const int64_t n = lev.A.nbr * lev.b;
+  double lmax = lev.lam, lmin = lmax / ratio;
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  double sigma = theta / delta, rho = 1.0 / sigma;
+  vec r(n), d(n), Ax(n);
+  if (zero) {
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] / lev.dg[i];
+  } else {
+    bsr_apply(lev.A, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i];
+  }
+  for (int64_t i = 0; i < n; ++i) d[i] = r[i] / theta;
+  for (int k = 0; k < degree; ++k) {
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + d[i];
+    if (k == degree - 1) break;
+    bsr_apply(lev.A, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = (b[i] - Ax[i]) / lev.dg[i];
+    double rn = 1.0 / (2.0 * sigma - rho);
+    for (int64_t i = 0; i < n; ++i) d[i] = rn * rho * d[i] + 2.0 * rn / delta * r[i];
+    rho = rn;
+  }
+}
+
+// V-cycle on the block hierarchy: pre-smoothing from x = 0, x += P V(R (b - A x)), post-smoothing
+void block_vcycle(const BAMG& H, int l, const vec& b, vec& x, const Smooth& sm) {
+  const BLevel& lev = H.L[l];
+  const int64_t n = lev.A.nbr * lev.b;
+  x.assign(n, 0.0);
+  if (lev.coarsest) { lev.lu.solve(b.data(), x.data()); return; }
+  block_chebyshev(lev, b, x, sm.degree, sm.ratio, true);
+  vec Ax(n), r(n);
+  bsr_apply(lev.A, x.data(), Ax.data());
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - Ax[i];
+  vec bc(lev.R.nbr * kModes), xc;
+  bsr_apply(lev.R, r.data(), bc.data());
+  block_vcycle(H, l + 1, bc, xc, sm);
+  vec Pe(n);
+  bsr_apply(lev.P, xc.data(), Pe.data());
+  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + Pe[i];
+  block_chebyshev(lev, b, x, sm.degree, sm.ratio, false);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1220,6 +1589,7 @@ struct or_prec {
   vec dss, dps;         // quasi-IMPES diagonals, §5.3
   CSR spp;
   AMG amg_u, amg_p;
+  BAMG amg_rbm;         // OR_MECH_AMG_RBM: rigid-body-mode smoothed aggregation on the full A_uu
   BSR ilu;              // L (unit, strictly lower) and U (upper) blocks in the S_ff pattern
   vec dinv;             // inv(U_ii)
   vec gs_dinv;          // inv of the diagonal blocks of S_ff^(FS) (block Gauss-Seidel)
@@ -1586,6 +1956,10 @@ int or_prec_setup_reuse(const or_system* s, const or_system* mech, const or_prec
     for (size_t q = 0; q < AuuM.ci.size(); ++q)
       for (int d = 0; d < 3; ++d) A0.v[q * 3 + d] = AuuM.v[q * 9 + d * 4];
     if (!build_amg(P->amg_u, std::move(A0), pp->theta_u, pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
+  } else if (pp->mech_mode == OR_MECH_AMG_RBM) {
+    if (pp->smoother != 1) { delete P; return 4; }
+    if (!build_rbm(P->amg_rbm, to_bsr(mech, 0), rigid_body_modes(s->nx, s->ny, s->nz), pp->theta_u,
+                   pp->coarse_max_u, pp->max_levels)) { delete P; return 2; }
   } else {
     vec d(size_t(s->n_u) * s->n_u, 0.0);
     bsr_dense(Auu, d, 0, 0, s->n_u);
@@ -1602,8 +1976,16 @@ int or_prec_setup_reuse(const or_system* s, const or_system* mech, const or_prec
       for (int64_t q = Auf.rp[I]; q < Auf.rp[I + 1]; ++q)
         for (int d = 0; d < 3; ++d) aupe[3 * I + d] = aupe[3 * I + d] + Auf.v[q * 6 + d * 2 + 1];
     if (pp->fs_mode == OR_FS_RSL) {
-      if (pp->mech_mode != OR_MECH_AMG) { delete P; return 3; }
-      mech_apply(P->amg_u, smooth_of(*pp), nn, aupe.data(), w.data());
+      if (pp->mech_mode == OR_MECH_AMG) {
+        mech_apply(P->amg_u, smooth_of(*pp), nn, aupe.data(), w.data());
+      } else if (pp->mech_mode == OR_MECH_AMG_RBM) {
+        vec wv;
+        block_vcycle(P->amg_rbm, 0, aupe, wv, smooth_of(*pp));
+        w = wv;
+      } else {
+        delete P;
+        return 3;
+      }
     } else {
       vec d(size_t(s->n_u) * s->n_u, 0.0);
       bsr_dense(Auu, d, 0, 0, s->n_u);
@@ -1805,6 +2187,10 @@ void or_prec_apply(or_prec* P, const double* v, double* z) {
   vec zu(nu);
   if (P->pp.mech_mode == OR_MECH_AMG) {
     mech_apply(P->amg_u, smooth_of(P->pp), nn, v, zu.data());
+  } else if (P->pp.mech_mode == OR_MECH_AMG_RBM) {
+    vec vu(v, v + 3 * nn), xu;
+    block_vcycle(P->amg_rbm, 0, vu, xu, smooth_of(P->pp));
+    zu.assign(xu.begin(), xu.end());
   } else {
     P->lu_uu.solve(v, zu.data());
   }
@@ -1904,6 +2290,51 @@ int64_t or_aggregate(int64_t n, int nc, const int64_t* rp, const int32_t* ci, co
   std::memcpy(root, lev.root.data(), size_t(n));
   return lev.nagg;
 }
+int or_rbm_nlevels(const or_prec* p) { return int(p->amg_rbm.L.size()); }
+int or_rbm_level_shape(const or_prec* p, int level, int64_t* shape) {
+  if (level < 0 || level >= int(p->amg_rbm.L.size())) return 1;
+  const BLevel& L = p->amg_rbm.L[level];
+  shape[0] = L.A.nbr; shape[1] = L.b; shape[2] = int64_t(L.A.ci.size()); shape[3] = L.nagg;
+  shape[4] = int64_t(L.P.ci.size()); shape[5] = L.coarsest ? 1 : 0;
+  return 0;
+}
+int or_rbm_level_matrix(const or_prec* p, int level, int64_t* rp, int32_t* ci, double* v) {
+  if (level < 0 || level >= int(p->amg_rbm.L.size())) return 1;
+  const BSR& A = p->amg_rbm.L[level].A;
+  std::copy(A.rp.begin(), A.rp.end(), rp);
+  std::copy(A.ci.begin(), A.ci.end(), ci);
+  std::copy(A.v.begin(), A.v.end(), v);
+  return 0;
+}
+int or_rbm_level_data(const or_prec* p, int level, int32_t* agg, double* B, double* Pt, double* lam) {
+  if (level < 0 || level >= int(p->amg_rbm.L.size())) return 1;
+  const BLevel& L = p->amg_rbm.L[level];
+  if (agg) for (int64_t i = 0; i < L.A.nbr; ++i) agg[i] = L.coarsest ? -1 : L.agg[i];
+  if (B) std::copy(L.B.begin(), L.B.end(), B);
+  if (Pt) { if (L.coarsest) std::fill(Pt, Pt + L.A.nbr * L.b * kModes, 0.0); else std::copy(L.Pt.begin(), L.Pt.end(), Pt); }
+  if (lam) *lam = L.lam;
+  return 0;
+}
+int or_rbm_prolongator(const or_prec* p, int level, int64_t* rp, int32_t* ci, double* v) {
+  if (level < 0 || level >= int(p->amg_rbm.L.size()) || p->amg_rbm.L[level].coarsest) return 1;
+  const BSR& P = p->amg_rbm.L[level].P;
+  std::copy(P.rp.begin(), P.rp.end(), rp);
+  std::copy(P.ci.begin(), P.ci.end(), ci);
+  std::copy(P.v.begin(), P.v.end(), v);
+  return 0;
+}
+int or_rbm_vcycle(const or_prec* p, const double* b, double* x) {
+  if (p->amg_rbm.L.empty()) return 1;
+  vec bb(b, b + p->amg_rbm.L[0].A.nbr * 3), xx;
+  block_vcycle(p->amg_rbm, 0, bb, xx, smooth_of(p->pp));
+  std::copy(xx.begin(), xx.end(), x);
+  return 0;
+}
+void or_rigid_body_modes(int nx, int ny, int nz, double* B) {
+  vec v = rigid_body_modes(nx, ny, nz);
+  std::copy(v.begin(), v.end(), B);
+}
+
 int64_t or_amg_p_nnz(const or_prec* p, int which, int level) { return pick(p, which)->L[level].P.nnz(); }
 int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v) {
   const CSR& A = pick(p, which)->L[level].P;

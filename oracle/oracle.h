@@ -111,7 +111,7 @@ void or_ref_integrals(double h, double* G, double* IN, double* IdN, double* INdN
 int or_residual(const or_gen_params* gp, const double* dx, double* r);
 
 /* preconditioner */
-enum { OR_MECH_AMG = 0, OR_MECH_EXACT = 1 };                 /* M_uu */
+enum { OR_MECH_AMG = 0, OR_MECH_EXACT = 1, OR_MECH_AMG_RBM = 2 };  /* M_uu: SDC AMG, exact, rigid-body-mode SA */
 enum { OR_FLOW_CPR = 0, OR_FLOW_EXACT_FS = 1, OR_FLOW_EXACT_SCHUR = 2 }; /* M_ff */
 enum { OR_LOCAL_ILU0 = 0, OR_LOCAL_EXACT = 1, OR_LOCAL_GS = 2 }; /* M_L: ILU(0), exact, block Gauss-Seidel */
 enum { OR_PRESS_AMG = 0, OR_PRESS_EXACT = 1 };                /* M_pp */
@@ -165,6 +165,18 @@ int64_t or_amg_roots(const or_prec* p, int which, int level, uint8_t* root);
 int64_t or_aggregate(int64_t n, int nc, const int64_t* rp, const int32_t* ci, const double* v, double theta,
                      int level, int32_t* agg, uint8_t* root);
 int64_t or_amg_p_nnz(const or_prec* p, int which, int level);
+/* rigid-body-mode smoothed aggregation (OR_MECH_AMG_RBM) on the full A_uu: levels, and per level
+   shape = {block rows n, block size b (3 finest, 6 below), block nnz, aggregates, P block nnz, coarsest},
+   the b x b BSR operator, the aggregates agg[n], the near-nullspace B[n b][6], the tentative prolongator
+   Pt[n b][6], the Gershgorin bound, and P as a b x 6 BSR; one V-cycle at the finest level */
+int or_rbm_nlevels(const or_prec* p);
+int or_rbm_level_shape(const or_prec* p, int level, int64_t* shape);
+int or_rbm_level_matrix(const or_prec* p, int level, int64_t* rp, int32_t* ci, double* v);
+int or_rbm_level_data(const or_prec* p, int level, int32_t* agg, double* B, double* Pt, double* lam);
+int or_rbm_prolongator(const or_prec* p, int level, int64_t* rp, int32_t* ci, double* v);
+int or_rbm_vcycle(const or_prec* p, const double* b, double* x);
+/* the six rigid-body modes at the grid's nodes, node-major rows (x, y, z) of 6 */
+void or_rigid_body_modes(int nx, int ny, int nz, double* B);
 int or_amg_prolongator(const or_prec* p, int which, int level, int64_t* rp, int32_t* ci, double* v);
 /* one V-cycle of component comp on level-0 input b */
 int or_amg_vcycle(const or_prec* p, int which, int comp, const double* b, double* x);
