@@ -470,10 +470,17 @@ def run_ours(args):
         # BF16-prolongator variant of the mixed mode: time and iteration cost
         t_bp, st_bp = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_BF16P, args.steps)[:2]
         # the other local stage of §5.3 (option 1): three sweeps of block Gauss-Seidel instead of ILU(0)
-        # processor-local ILU(0) (the paper's runs factor each process's rows, §6): one subdomain per sweep
-        # tile of 16 x 8 cell columns, so the two triangular sweeps need no exchange between tiles
+        # rigid-body-mode smoothed aggregation on the full A_uu in place of the SDC hierarchy (one try: its setup
+        # may refuse a level whose rows outgrow the setup kernels)
+        t_rb, st_rb, rb_err = None, None, None
+        if not args.no_fp64:
+            try:
+                t_rb, st_rb = timed(ps.PS_MIXED_FP32, args.steps, mech_amg=ps.PS_MECH_RBM)[:2]
+            except RuntimeError as ex:
+                rb_err = str(ex)
+        # the global ILU(0) in place of the processor-local default: the sweeps exchange tile faces
         t_il, st_il = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
-                                                               ilu_scope=ps.PS_ILU_LOCAL)[:2]
+                                                               ilu_scope=ps.PS_ILU_GLOBAL)[:2]
         t_gs, st_gs = (None, None) if args.no_fp64 else timed(ps.PS_MIXED_FP32, args.steps,
                                                                local_stage=ps.PS_LOCAL_HBGS)[:2]
         # the true-IMPES pressure reduction of §5.3 in place of quasi-IMPES (one solve, at most 300 iterations:
@@ -654,6 +661,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": dict(config_of(args.config), **{
                    "precision": "mixed: FP32 preconditioner (AMG, ILU), FP64 Jacobian SpMV + FGMRES(100)",
+                   "local_stage": "processor-local block ILU(0), %d subdomains of 16 x 8 cell columns (paper §6)"
+                                  % (((s.grid.ny + 15) // 16) * ((s.grid.nz + 7) // 8)),
                    "l2": "inputs larger than L2 (3.7 GB FP64 Jacobian per SpMV)", "replicas": world}),
         "iters_mixed": it_mx, "iters_fp64": it_64,
         "setup_ms_mixed": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_mx],
@@ -681,14 +690,22 @@ def run_ours(args):
             "value": t_bp / args.steps / world, "iters": [st.iters for st in st_bp],
             "solve_ms": [round(st.ms_solve, 2) for st in st_bp],
             "vcycle_u_ms": round(st_bp[-1].ms_vcycle_u, 1), "vcycle_p_ms": round(st_bp[-1].ms_vcycle_p, 1)},
-        "ilu_processor_local": None if st_il is None else {
+        "mechanics_rbm_sa": {"error": rb_err} if st_rb is None and rb_err else None if st_rb is None else {
+            "value": t_rb / args.steps / world, "iters": [st.iters for st in st_rb],
+            "solve_ms": [round(st.ms_solve, 2) for st in st_rb],
+            "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_rb],
+            "setup_mechanics_ms": round(st_rb[-1].ms_setup_u, 2),
+            "vcycle_u_ms": round(st_rb[-1].ms_vcycle_u, 1), "levels": st_rb[-1].levels_u,
+            "handle_gb": round(st_rb[-1].handle_bytes / 1e9, 3),
+            "note": "M_uu = rigid-body-mode smoothed aggregation on the full A_uu (3x3 blocks, six rigid-body "
+                    "modes, 6x6 coarse blocks) in place of the SDC hierarchy of paper §5.2"},
+        "ilu_global": None if st_il is None else {
             "value": t_il / args.steps / world, "iters": [st.iters for st in st_il],
             "solve_ms": [round(st.ms_solve, 2) for st in st_il],
             "setup_ms": [round(st.ms_setup_u + st.ms_setup_f, 2) for st in st_il],
             "local_stage_ms": round(st_il[-1].ms_ilu, 1),
-            "note": "processor-local ILU(0) (paper §6: each process factors its own rows): subdomains of "
-                    "16 x 8 cell columns spanning x, one per sweep tile (%d), no exchange between them"
-                    % (((s.grid.ny + 15) // 16) * ((s.grid.nz + 7) // 8))},
+            "note": "global ILU(0) of S_ff^(FS) in place of the processor-local default: the pencil "
+                    "wavefront sweeps exchange the faces of the 16 x 8 tiles through tagged halo words"},
         "local_stage_hbgs": None if st_gs is None else {
             "value": t_gs / args.steps / world, "iters": [st.iters for st in st_gs],
             "solve_ms": [round(st.ms_solve, 2) for st in st_gs],

@@ -59,6 +59,9 @@ enum { PS_LOCAL_ILU0 = 0, PS_LOCAL_HBGS = 1 };
 /* scope of the ILU(0) local stage: the whole flow system, or processor-local (§6: each process factors
    the rows it owns), with subdomains of PS_ILU_TILE_Y x PS_ILU_TILE_Z cell columns in (y, z) spanning x */
 enum { PS_ILU_GLOBAL = 0, PS_ILU_LOCAL = 1 };
+/* mechanics AMG M_uu: on the separate-displacement-component approximation A_uu^(SDC) (§5.2, default), or
+   rigid-body-mode smoothed aggregation on the full A_uu (the usual elasticity AMG the paper sets aside) */
+enum { PS_MECH_SDC = 0, PS_MECH_RBM = 1 };
 #define PS_ILU_TILE_Y 16
 #define PS_ILU_TILE_Z 8
 /* CPR pressure reduction of §5.3: quasi-IMPES (diagonal entries of A_ss, A_ps; default) or true-IMPES
@@ -145,10 +148,15 @@ typedef struct {
                                  programmatic dependent launch, so its CTAs are scheduled while the
                                  previous kernel drains and wait on the device for its completion;
                                  0: plain stream order.  Same results either way. */
-  int32_t ilu_scope;          /* PS_ILU_GLOBAL (default): ILU(0) of the whole S_ff^(FS); PS_ILU_LOCAL:
-                                 processor-local ILU(0), the ILU(0) of S_ff^(FS) without the blocks that
-                                 couple different subdomains (columns of PS_ILU_TILE_Y x PS_ILU_TILE_Z
-                                 cells), whose sweeps need no exchange between subdomains */
+  int32_t ilu_scope;          /* PS_ILU_LOCAL (default): processor-local ILU(0) as in the paper's runs, the
+                                 ILU(0) of S_ff^(FS) without the blocks that couple different subdomains
+                                 (columns of PS_ILU_TILE_Y x PS_ILU_TILE_Z cells), whose sweeps need no
+                                 exchange between subdomains; PS_ILU_GLOBAL: ILU(0) of the whole
+                                 S_ff^(FS), the sweeps exchanging tile faces through tagged halo words */
+  int32_t mech_amg;           /* PS_MECH_SDC (default) or PS_MECH_RBM: 3 x 3 blocks on the nodes, the six
+                                 rigid-body modes as near-nullspace, 6 x 6 blocks on the aggregates below,
+                                 QR-based tentative prolongator, Jacobi-smoothed P, Galerkin levels;
+                                 Chebyshev smoothing only (PS_ERR_INVALID otherwise) */
 } ps_params;
 
 typedef struct {
@@ -240,6 +248,16 @@ ps_status ps_amg_level_shape(ps_handle* h, int32_t which, int32_t level, int64_t
 /* host copies: rowptr[n+1], colind[nnz], val[nnz*ncomp] (ncomp 3 or 1), agg[n] (-1 excluded) */
 ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t* rowptr, int32_t* colind,
                             double* val, int32_t* agg);
+/* Rigid-body-mode hierarchy (mech_amg = PS_MECH_RBM) for parity checks: the level count (0 otherwise);
+   shape[0] block rows, [1] block size b (3 on the finest level, 6 below), [2] operator blocks,
+   [3] aggregates (0 on the coarsest level), [4] prolongator blocks, [5] 1 on the coarsest level; host
+   copies of a level's operator (rowptr[n+1], colind[nnzb], val[nnzb*b*b] row-major blocks) and aggregates
+   agg[n], and of its prolongator (b x 6 blocks) */
+int32_t ps_rbm_nlevels(ps_handle* h);
+ps_status ps_rbm_level_shape(ps_handle* h, int32_t level, int64_t* shape);
+ps_status ps_rbm_level_copy(ps_handle* h, int32_t level, int64_t* rowptr, int32_t* colind, double* val,
+                            int32_t* agg);
+ps_status ps_rbm_prolongator_copy(ps_handle* h, int32_t level, int64_t* rowptr, int32_t* colind, double* val);
 /* S_pp values in the A_ff pattern and ILU inverse diagonal blocks (host copies) */
 ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv);
 

@@ -1932,8 +1932,8 @@ void or_default_prec_params(or_prec_params* pp) {
   pp->pre = 1; pp->post = 1;
   pp->smoother = 1; pp->cheb_degree = 2; pp->cheb_ratio = 20.0;
   pp->local_sweeps = 3;
-  pp->ilu_tile_y = 0;
-  pp->ilu_tile_z = 0;
+  pp->ilu_tile_y = 16;
+  pp->ilu_tile_z = 8;
 }
 
 int or_prec_setup(const or_system* s, const or_prec_params* pp, or_prec** out) {

@@ -134,9 +134,10 @@ typedef struct {
                             lumping of the §5.1 remark with one application of M_uu^{-1}), OR_FS_RSL_EXACT
                             (the same with A_uu^{-1} by dense LU; tiny systems) */
   int32_t ilu_tile_y, ilu_tile_z; /* OR_LOCAL_ILU0 scope: 0, 0 = global ILU(0); ty, tz > 0 = processor-local
-                                     ILU(0) (§6 remark: each process factors its own rows), the subdomains
-                                     being the cell columns of ty x tz cells in (y, z) spanning x, i.e. the
-                                     ILU(0) of S_ff with the blocks coupling different subdomains removed */
+                                     ILU(0) (§6: each process factors its own rows), the subdomains being the
+                                     cell columns of ty x tz cells in (y, z) spanning x, i.e. the ILU(0) of
+                                     S_ff with the blocks coupling different subdomains removed
+                                     (default 16 x 8) */
 } or_prec_params;
 
 typedef struct or_prec or_prec;

@@ -21,6 +21,7 @@ PS_ILU_LEVEL_LAUNCH, PS_ILU_PENCIL = 0, 1
 PS_ORTHO_MGS, PS_ORTHO_CGS2 = 0, 1
 PS_LOCAL_ILU0, PS_LOCAL_HBGS = 0, 1
 PS_ILU_GLOBAL, PS_ILU_LOCAL = 0, 1
+PS_MECH_SDC, PS_MECH_RBM = 0, 1
 PS_ILU_TILE_Y, PS_ILU_TILE_Z = 16, 8
 PS_CPR_QUASI_IMPES, PS_CPR_TRUE_IMPES = 0, 1
 PS_SOLVER_FGMRES, PS_SOLVER_RICHARDSON = 0, 1
@@ -56,7 +57,7 @@ class ps_params(C.Structure):
                 ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
                 ("local_stage", C.c_int32), ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
                 ("solver", C.c_int32), ("fs_mode", C.c_int32), ("vcycle_tail", C.c_int32),
-                ("pdl", C.c_int32), ("ilu_scope", C.c_int32)]
+                ("pdl", C.c_int32), ("ilu_scope", C.c_int32), ("mech_amg", C.c_int32)]
 
 
 class ps_stats(C.Structure):
@@ -135,6 +136,10 @@ def lib():
         L.ps_solve_batch.argtypes = [C.c_int32, C.POINTER(H), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                      C.c_double, C.POINTER(ps_stats)]
         L.ps_amg_level_shape.argtypes = [H, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+        L.ps_rbm_nlevels.argtypes = [H]
+        L.ps_rbm_level_shape.argtypes = [H, C.c_int32, C.POINTER(C.c_int64)]
+        L.ps_rbm_level_copy.argtypes = [H, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.ps_rbm_prolongator_copy.argtypes = [H, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ps_amg_level_copy.argtypes = [H, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.ps_flow_copy.argtypes = [H, C.c_void_p, C.c_void_p]
         L.ps_free.argtypes = [H]
@@ -324,6 +329,42 @@ def ps_amg_level_copy(h, which, level):
     _check(lib().ps_amg_level_copy(h, which, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, agg.ctypes.data),
            "ps_amg_level_copy")
     return rp, ci[:nnz], v[:nnz * nc].reshape(nnz, nc), agg
+
+
+def ps_rbm_nlevels(h):
+    return lib().ps_rbm_nlevels(h)
+
+
+def ps_rbm_level_shape(h, level):
+    out = (C.c_int64 * 6)()
+    _check(lib().ps_rbm_level_shape(h, level, out), "ps_rbm_level_shape")
+    return dict(n=out[0], b=out[1], nnzb=out[2], nagg=out[3], pnnzb=out[4], coarsest=bool(out[5]))
+
+
+def ps_rbm_level_copy(h, level):
+    """Host copies (numpy) of a rigid-body-mode level: rowptr, colind, blocks (nnzb, b, b), aggregates."""
+    import numpy as np
+    sh = ps_rbm_level_shape(h, level)
+    n, b, nnz = sh["n"], sh["b"], sh["nnzb"]
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(max(nnz, 1), np.int32)
+    v = np.empty(max(nnz, 1) * b * b)
+    agg = np.empty(n, np.int32)
+    _check(lib().ps_rbm_level_copy(h, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, agg.ctypes.data),
+           "ps_rbm_level_copy")
+    return rp, ci[:nnz], v[:nnz * b * b].reshape(nnz, b, b), agg
+
+
+def ps_rbm_prolongator_copy(h, level):
+    import numpy as np
+    sh = ps_rbm_level_shape(h, level)
+    n, b, nnz = sh["n"], sh["b"], sh["pnnzb"]
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(max(nnz, 1), np.int32)
+    v = np.empty(max(nnz, 1) * b * 6)
+    _check(lib().ps_rbm_prolongator_copy(h, level, rp.ctypes.data, ci.ctypes.data, v.ctypes.data),
+           "ps_rbm_prolongator_copy")
+    return rp, ci[:nnz], v[:nnz * b * 6].reshape(nnz, b, 6)
 
 
 def ps_flow_copy(h, nnzb, ncells):

@@ -1,6 +1,6 @@
 """Compile libps.so (CUDA, sm_103a) in-tree with nvcc.
 
-The two translation units that form setup-phase quantities feeding integer
+The translation units that form setup-phase quantities feeding integer
 decisions (aggregation) are compiled with --fmad=false so that every a*b+c is
 rounded twice, as in a plain IEEE evaluation of the same formula.
 """
@@ -16,8 +16,8 @@ LIB = os.path.join(BUILD, "libps.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["util.cu", "gen.cu", "amg_setup.cu", "vcycle.cu", "flow_setup.cu", "flow_apply.cu", "krylov.cu",
-           "api.cu", "noalloc.cu", "serve.cu"]
-NO_FMA = {"amg_setup.cu", "flow_setup.cu", "gen.cu"}
+           "api.cu", "noalloc.cu", "serve.cu", "rbm_setup.cu", "rbm_apply.cu"]
+NO_FMA = {"amg_setup.cu", "flow_setup.cu", "gen.cu", "rbm_setup.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

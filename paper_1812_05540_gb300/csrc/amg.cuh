@@ -114,6 +114,16 @@ ps_status amg_vcycle_direct(Amg& H, const SmoothParams& sp, const T* b, T* x, cu
 template <class T>
 ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st);
 
+// Aggregation of a scalar operator (one value per entry, sorted columns): the strength graph, distance-2 MIS
+// and joining phases of the SDC hierarchy's levels.  *agg (n, -1 = not aggregated) and *excl (n, 1 = row
+// without off-diagonal entries) are allocated in ar.
+ps_status amg_aggregate_scalar(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                               const double* v, double theta, int level, int32_t** agg, int64_t* nagg,
+                               uint8_t** excl, cudaStream_t st);
+// inverse of a dense n x n FP64 matrix by Gauss-Jordan with partial pivoting: M (row-major) is destroyed,
+// inv must hold the identity on entry
+ps_status amg_dense_inverse(Arena& ar, int64_t n, double* M, double* inv, cudaStream_t st);
+
 // SpMV lane choice from the mean row length (rows of a few entries, as in the level-0 prolongators, take
 // one or two threads each)
 inline int lanes_for(double mean_row) {

@@ -1021,6 +1021,74 @@ int gj_cooperative(int64_t n, int nc, double* M, double* I, double* f, Arena& ar
   return result;
 }
 
+// Gauss-Jordan inverses of nc dense n x n matrices (M is overwritten, inv starts as the identity): one
+// cooperative launch, else one launch pair per pivot
+ps_status gj_inverse(int64_t n, int nc, double* M, double* inv, double* f, Arena& ar, cudaStream_t st) {
+  const int gj = gj_cooperative(n, nc, M, inv, f, ar, st);
+  if (gj == 2) {
+    set_reason("a bounded grid barrier wait of the coarsest-level Gauss-Jordan inverse gave up");
+    return PS_ERR_TIMEOUT;
+  }
+  if (gj == 1) {
+    for (int64_t k = 0; k < n; ++k) {
+      PS_TICK(); k_gj_pivot<<<nc, 256, 0, st>>>(n, k, M, inv, f);
+      dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), unsigned(nc));
+      PS_TICK(); k_gj_elim<<<g, 128, 0, st>>>(n, k, M, inv, f);
+    }
+  }
+  PS_CUDA(cudaGetLastError());
+  return PS_OK;
+}
+
+// Aggregation of one level: symmetric strength graph, distance-2 MIS rounds under the priority key of the
+// level, phase 1 (strong neighbours of a root join it), phase 2 (leftovers join their strongest phase-1
+// neighbour).  dgbar and excl as k_diag_excl leaves them; *agg is allocated here (-1: not aggregated).
+template <int NC>
+ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci, const double* v,
+                         const double* dgbar, const uint8_t* excl, double theta, int l, int32_t** agg, int64_t* nagg,
+                         cudaStream_t st) {
+  uint8_t *strong = nullptr, *stt = nullptr;
+  double* wgt = nullptr;
+  PS_TRY(ar.alloc(&strong, nnz));
+  PS_TRY(ar.alloc(&wgt, nnz));
+  PS_TICK(); k_strength<NC><<<grid_for(n * kStrLanes, 256), 256, 0, st>>>(n, rp, ci, v, dgbar, excl, theta, strong,
+                                                                         wgt);
+  PS_TRY(ar.alloc(&stt, n));
+  int64_t* m1;
+  uint8_t *nr, *c1;
+  int32_t* und;
+  PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, 1));
+  PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, rp, strong, excl, stt);
+  for (int round = 0;; ++round) {
+    PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
+    PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, l, m1);
+    PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, l, stt, nr);
+    PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, nr, c1);
+    PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, c1, stt, und);
+    int32_t h_und = 0;
+    PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (h_und == 0) break;
+    if (round > 100000) {
+      set_reason("aggregation did not terminate on level %d", l);
+      return PS_ERR_INVALID;
+    }
+  }
+  int32_t *isr, *rscan, *ph1;
+  PS_TRY(ar.alloc(&isr, n)); PS_TRY(ar.alloc(&rscan, n + 1)); PS_TRY(ar.alloc(&ph1, n));
+  PS_TRY(ar.alloc(agg, n));
+  PS_TICK(); k_is_root<<<grid_for(n, 256), 256, 0, st>>>(n, stt, isr);
+  int32_t na = 0;
+  PS_TRY(scan_i32(ar, isr, rscan, n, &na, st));
+  PS_TICK(); k_agg_phase1<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, strong, stt, rscan, ph1);
+  PS_TICK(); k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, strong, wgt, stt, ph1, *agg);
+  PS_CUDA(cudaGetLastError());
+  *nagg = na;
+  ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(isr); ar.release(rscan);
+  ar.release(ph1); ar.release(strong); ar.release(wgt); ar.release(stt);
+  return PS_OK;
+}
+
 template <int NC>
 ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, int32_t* ci0, double* v0,
                      const AmgParams& prm, cudaStream_t st) {
@@ -1044,46 +1112,10 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     PS_TICK(); k_diag_excl<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl, lev.dg);
     PS_CUDA(cudaGetLastError());
     bool coarsest = n <= prm.coarse_max || l + 1 >= prm.max_levels;
-    uint8_t *strong = nullptr, *stt = nullptr;
-    double* wgt = nullptr;
     if (!coarsest) {
-      PS_TRY(ar.alloc(&strong, nnz));
-      PS_TRY(ar.alloc(&wgt, nnz));
-      PS_TICK(); k_strength<NC><<<grid_for(n * kStrLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, dgbar, excl,
-                                                                             theta, strong, wgt);
-      PS_TRY(ar.alloc(&stt, n));
-      int64_t* m1;
-      uint8_t *nr, *c1;
-      int32_t* und;
-      PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, 1));
-      PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, strong, excl, stt);
-      for (int round = 0;; ++round) {
-        PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
-        PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, l, m1);
-        PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, m1, l, stt, nr);
-        PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, nr, c1);
-        PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, c1, stt, und);
-        int32_t h_und = 0;
-        PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        PS_CUDA(cudaStreamSynchronize(st));
-        if (h_und == 0) break;
-        if (round > 100000) {
-          set_reason("aggregation did not terminate on level %d", l);
-          return PS_ERR_INVALID;
-        }
-      }
-      int32_t *isr, *rscan, *ph1;
-      PS_TRY(ar.alloc(&isr, n)); PS_TRY(ar.alloc(&rscan, n + 1)); PS_TRY(ar.alloc(&ph1, n));
-      PS_TRY(ar.alloc(&lev.agg, n));
-      PS_TICK(); k_is_root<<<grid_for(n, 256), 256, 0, st>>>(n, stt, isr);
-      int32_t na = 0;
-      PS_TRY(scan_i32(ar, isr, rscan, n, &na, st));
-      PS_TICK(); k_agg_phase1<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, stt, rscan, ph1);
-      PS_TICK(); k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.ci, strong, wgt, stt, ph1, lev.agg);
-      PS_CUDA(cudaGetLastError());
+      int64_t na = 0;
+      PS_TRY(aggregate_impl<NC>(ar, n, nnz, lev.rp, lev.ci, lev.v, dgbar, excl, theta, l, &lev.agg, &na, st));
       lev.nagg = na;
-      ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(isr); ar.release(rscan);
-      ar.release(ph1);
       if (na == 0 || double(n) / double(na) < 1.2) coarsest = true;
     }
     if (coarsest) {
@@ -1101,24 +1133,9 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
       PS_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * NC * n * n, st));
       PS_CUDA(cudaMemsetAsync(lev.inv, 0, sizeof(double) * NC * n * n, st));
       PS_TICK(); k_dense_unpack<<<grid_for(n, 128), 128, 0, st>>>(n, NC, lev.rp, lev.ci, lev.v, M, lev.inv);
-      const int gj = gj_cooperative(n, NC, M, lev.inv, f, ar, st);
-      if (gj == 2) {
-        set_reason("a bounded grid barrier wait of the coarsest-level Gauss-Jordan inverse gave up");
-        return PS_ERR_TIMEOUT;
-      }
-      if (gj == 1) {
-        for (int64_t k = 0; k < n; ++k) {
-          PS_TICK(); k_gj_pivot<<<NC, 256, 0, st>>>(n, k, M, lev.inv, f);
-          dim3 g(unsigned(ceil_div(2 * n, 128)), unsigned(n), NC);
-          PS_TICK(); k_gj_elim<<<g, 128, 0, st>>>(n, k, M, lev.inv, f);
-        }
-      }
-      PS_CUDA(cudaGetLastError());
+      PS_TRY(gj_inverse(n, NC, M, lev.inv, f, ar, st));
       ar.release(M); ar.release(f);
     }
-    if (strong) ar.release(strong);
-    if (wgt) ar.release(wgt);
-    if (stt) ar.release(stt);
     if (coarsest) { ar.release(dgbar); ar.release(excl); }
     if (prm.mixed) {
       PS_TRY(ar.alloc(&lev.vf, nnz * NC));
@@ -1239,6 +1256,29 @@ ps_status amg_build(Arena& ar, Amg& H, int nc, int64_t n, int64_t nnz, int32_t* 
   if (nc == 3) return build_impl<3>(ar, H, n, nnz, rp, ci, v, prm, st);
   if (nc == 1) return build_impl<1>(ar, H, n, nnz, rp, ci, v, prm, st);
   return PS_ERR_INVALID;
+}
+
+ps_status amg_aggregate_scalar(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                               const double* v, double theta, int level, int32_t** agg, int64_t* nagg,
+                               uint8_t** excl, cudaStream_t st) {
+  double *dgbar, *dg;
+  PS_TRY(ar.alloc(&dgbar, n));
+  PS_TRY(ar.alloc(&dg, n));
+  PS_TRY(ar.alloc(excl, n));
+  PS_TICK(); k_diag_excl<1><<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, dgbar, *excl, dg);
+  PS_CUDA(cudaGetLastError());
+  PS_TRY(aggregate_impl<1>(ar, n, nnz, rp, ci, v, dgbar, *excl, theta, level, agg, nagg, st));
+  ar.release(dgbar);
+  ar.release(dg);
+  return PS_OK;
+}
+
+ps_status amg_dense_inverse(Arena& ar, int64_t n, double* M, double* inv, cudaStream_t st) {
+  double* f;
+  PS_TRY(ar.alloc(&f, n));
+  PS_TRY(gj_inverse(n, 1, M, inv, f, ar, st));
+  ar.release(f);
+  return PS_OK;
 }
 
 namespace {

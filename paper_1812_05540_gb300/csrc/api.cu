@@ -9,6 +9,7 @@
 #include "amg.cuh"
 #include "flow.cuh"
 #include "krylov.cuh"
+#include "rbm.cuh"
 
 using namespace ps_internal;
 
@@ -76,6 +77,8 @@ struct ps_handle {
   double* rsl_w = nullptr;
   double* rsl_dfs = nullptr;
   Amg amg_u, amg_p;
+  Rbm rbm_u;          // PS_MECH_RBM: the mechanics hierarchy in place of amg_u
+  bool rbm = false;
   FlowStage F;
   FlowWork<float> w32;
   FlowWork<double> w64;
@@ -120,14 +123,16 @@ ps_status alg1(ps_handle* h, const double* v, double* z) {
   // step 1: z_u = M_uu^{-1} v_u
   if constexpr (sizeof(T) == 4) {
     PS_TICK(); k_d2f<<<grid_for(h->nu, 256), 256, 0, st>>>(v, h->vu32, h->nu);
-    PS_TRY(amg_vcycle<float>(h->amg_u, sp, h->vu32, h->zu32, st));
+    if (h->rbm) PS_TRY(rbm_vcycle<float>(h->rbm_u, sp, h->vu32, h->zu32, st));
+    else PS_TRY(amg_vcycle<float>(h->amg_u, sp, h->vu32, h->zu32, st));
     cudaEventRecord(h->fe[1], st);
     PS_TICK(); k_f2d<<<grid_for(h->nu, 256), 256, 0, st>>>(h->zu32, z, h->nu);
     PS_TICK(); k_d2f<<<grid_for(h->nf, 256), 256, 0, st>>>(v + h->nu, W->vf, h->nf);
     // steps 2-4
     alg1_steps_2_4<float>(h->F, *W, h->zu32, st);
   } else {
-    PS_TRY(amg_vcycle<double>(h->amg_u, sp, v, z, st));
+    if (h->rbm) PS_TRY(rbm_vcycle<double>(h->rbm_u, sp, v, z, st));
+    else PS_TRY(amg_vcycle<double>(h->amg_u, sp, v, z, st));
     cudaEventRecord(h->fe[1], st);
     PS_CUDA(cudaMemcpyAsync(W->vf, v + h->nu, sizeof(double) * h->nf, cudaMemcpyDeviceToDevice, st));
     alg1_steps_2_4<double>(h->F, *W, z, st);
@@ -148,10 +153,54 @@ ps_status apply_prec(ps_handle* h, const double* v, double* z) {
   return h->mixed ? alg1<float>(h, v, z) : alg1<double>(h, v, z);
 }
 
+// streaming copy of n16 16-byte words, four independent loads in flight per thread
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    dst[i] = a; dst[i + stride] = b; dst[i + 2 * stride] = c; dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = src[i];
+}
+
+// Copy of one input array into device memory the handle owns.  Host memory that CUDA has pinned is mapped
+// into the device's address space: a streaming kernel reads it over the host link, the whole array in one
+// launch, without a copy-engine transfer; pageable host memory, unaligned arrays and device memory use
+// cudaMemcpyAsync.
+ps_status copy_to(const void* src, size_t bytes, void* dst, bool host, cudaStream_t st) {
+  if (bytes == 0) return PS_OK;
+  if (host && bytes >= 16) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+        (reinterpret_cast<uintptr_t>(at.devicePointer) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      static int sms = 0;
+      if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+      }
+      const int64_t n16 = int64_t(bytes / 16);
+      const int64_t blocks = std::min<int64_t>(int64_t(sms) * 8, (n16 + 255) / 256);
+      PS_TICK(); k_copy16<<<unsigned(blocks), 256, 0, st>>>(static_cast<const uint4*>(at.devicePointer),
+                                                          static_cast<uint4*>(dst), n16);
+      PS_CUDA(cudaGetLastError());
+      const size_t tail = bytes - size_t(n16) * 16;
+      if (tail)
+        PS_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + n16 * 16, static_cast<const char*>(src) + n16 * 16, tail,
+                                cudaMemcpyHostToDevice, st));
+      return PS_OK;
+    }
+    cudaGetLastError();
+  }
+  PS_CUDA(cudaMemcpyAsync(dst, src, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  return PS_OK;
+}
+
 ps_status copy_in(Arena& ar, const void* src, size_t bytes, void** dst, bool host, cudaStream_t st) {
   PS_TRY(ar.alloc(dst, bytes));
-  PS_CUDA(cudaMemcpyAsync(*dst, src, bytes, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-  return PS_OK;
+  return copy_to(src, bytes, *dst, host, st);
 }
 
 ps_status copy_bsr(ps_handle* h, const ps_bsr& B, int32_t** rp, int32_t** ci, const double** v) {
@@ -161,9 +210,7 @@ ps_status copy_bsr(ps_handle* h, const ps_bsr& B, int32_t** rp, int32_t** ci, co
   PS_TRY(h->ar.alloc(rp, B.n_brow + 1));
   rowptr_to_i32(rp64, *rp, B.n_brow + 1, h->st);
   PS_TRY(h->ar.alloc(ci, B.nnzb + 1));
-  if (B.nnzb > 0)
-    PS_CUDA(cudaMemcpyAsync(*ci, B.colind, sizeof(int32_t) * B.nnzb,
-                            host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  PS_TRY(copy_to(B.colind, sizeof(int32_t) * B.nnzb, *ci, host, h->st));
   void* vv;
   PS_TRY(copy_in(h->ar, B.val, sizeof(double) * B.nnzb * B.br * B.bc, &vv, host, h->st));
   *v = static_cast<const double*>(vv);
@@ -277,24 +324,31 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     set_reason("A_ff is not the 7-point TPFA pattern of the %dx%dx%d grid", h->grid.nx, h->grid.ny, h->grid.nz);
     return PS_ERR_INVALID;
   }
-  // §5.2 mechanics: amg(A_uu^(SDC)) on the three diagonal components of each 3x3 block
   int64_t nnzb = jac->A_uu.nnzb;
-  double* sdc;
-  PS_TRY(ar.alloc(&sdc, nnzb * 3));
-  PS_TICK(); k_sdc<<<grid_for(nnzb, 256), 256, 0, st>>>(nnzb, J.uu_v, sdc);
-  AmgParams ap;
-  ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
-  ap.mixed = h->mixed;
-  ap.bf16p = h->bf16p;
-  PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
-  bool su_ok = false;
-  PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
+  if (h->rbm) {
+    // rigid-body-mode smoothed aggregation on the full A_uu
+    PS_TRY(rbm_build(ar, h->rbm_u, h->grid.nx, h->grid.ny, h->grid.nz, nnzb, J.uu_rp, J.uu_ci, J.uu_v,
+                     h->prm.theta_u, h->prm.coarse_max_u, h->prm.max_levels, h->mixed, st));
+    if (h->mixed) PS_TRY(rbm_alloc_work<float>(ar, h->rbm_u, st));
+    else PS_TRY(rbm_alloc_work<double>(ar, h->rbm_u, st));
+  } else {
+    // §5.2 mechanics: amg(A_uu^(SDC)) on the three diagonal components of each 3x3 block
+    double* sdc;
+    PS_TRY(ar.alloc(&sdc, nnzb * 3));
+    PS_TICK(); k_sdc<<<grid_for(nnzb, 256), 256, 0, st>>>(nnzb, J.uu_v, sdc);
+    AmgParams ap;
+    ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
+    ap.mixed = h->mixed;
+    ap.bf16p = h->bf16p;
+    PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
+    bool su_ok = false;
+    PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
+    if (h->mixed) PS_TRY(amg_alloc_work<float>(ar, h->amg_u, smooth_params(h->prm), st));
+    else PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
+  }
   if (h->mixed) {
-    PS_TRY(amg_alloc_work<float>(ar, h->amg_u, smooth_params(h->prm), st));
     PS_TRY(ar.alloc(&h->vu32, h->nu));
     PS_TRY(ar.alloc(&h->zu32, h->nu));
-  } else {
-    PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
   }
   if (h->prm.fs_mode == PS_FS_RSL) {
     // w = M_uu^{-1} (A_up e): one FP64 V-cycle on a view of the mechanics hierarchy with its own FP64 work
@@ -303,17 +357,25 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     PS_TRY(ar.alloc(&aupe, h->nu));
     PS_TRY(ar.alloc(&h->rsl_w, h->nu));
     PS_TICK(); k_rsl_aupe<<<grid_for(h->nn, 256), 256, 0, st>>>(h->nn, J.uf_rp, J.uf_v, aupe);
-    Amg S = h->amg_u;
-    S.gexec = nullptr;
-    S.tail = nullptr;
-    for (auto& L : S.L) {
-      L.x = L.t = L.r = L.d = L.b = L.e = L.dsi = nullptr;
-      L.sv_f = nullptr;
-    }
     Arena tmp;
     tmp.stream = st;
-    ps_status rs = amg_alloc_work<double>(tmp, S, smooth_params(h->prm), st);
-    if (rs == PS_OK) rs = amg_vcycle_direct<double>(S, smooth_params(h->prm), aupe, h->rsl_w, st);
+    ps_status rs = PS_OK;
+    if (h->rbm) {
+      Rbm S = h->rbm_u;
+      S.gexec = nullptr;
+      rs = rbm_alloc_work<double>(tmp, S, st);
+      if (rs == PS_OK) rs = rbm_vcycle_direct<double>(S, smooth_params(h->prm), aupe, h->rsl_w, st);
+    } else {
+      Amg S = h->amg_u;
+      S.gexec = nullptr;
+      S.tail = nullptr;
+      for (auto& L : S.L) {
+        L.x = L.t = L.r = L.d = L.b = L.e = L.dsi = nullptr;
+        L.sv_f = nullptr;
+      }
+      rs = amg_alloc_work<double>(tmp, S, smooth_params(h->prm), st);
+      if (rs == PS_OK) rs = amg_vcycle_direct<double>(S, smooth_params(h->prm), aupe, h->rsl_w, st);
+    }
     cudaStreamSynchronize(st);
     tmp.free_all();
     ar.release(aupe);
@@ -390,7 +452,8 @@ void ps_params_default(ps_params* p) {
   p->ortho_sweep = 8;
   p->vcycle_tail = 0;
   p->pdl = 1;
-  p->ilu_scope = PS_ILU_GLOBAL;
+  p->ilu_scope = PS_ILU_LOCAL;
+  p->mech_amg = PS_MECH_SDC;
   p->local_stage = PS_LOCAL_ILU0;
   p->local_sweeps = 3;
 }
@@ -412,12 +475,18 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
     return PS_ERR_INVALID;
   if (params->solver != PS_SOLVER_FGMRES && params->solver != PS_SOLVER_RICHARDSON) return PS_ERR_INVALID;
   if (params->fs_mode != PS_FS_GIVEN && params->fs_mode != PS_FS_RSL) return PS_ERR_INVALID;
+  if (params->mech_amg != PS_MECH_SDC && params->mech_amg != PS_MECH_RBM) return PS_ERR_INVALID;
+  if (params->mech_amg == PS_MECH_RBM && params->smoother != PS_SMOOTH_CHEBYSHEV) {
+    set_reason("the rigid-body-mode mechanics hierarchy smooths with Chebyshev only");
+    return PS_ERR_INVALID;
+  }
   if (params->local_stage == PS_LOCAL_HBGS && (params->local_sweeps < 1 || params->local_sweeps > 64)) {
     set_reason("local_sweeps must be 1..64 for the block Gauss-Seidel local stage");
     return PS_ERR_INVALID;
   }
   ps_handle* h = new ps_handle();
   h->prm = *params;
+  h->rbm = params->mech_amg == PS_MECH_RBM;
   h->grid = *grid;
   h->st = (cudaStream_t)params->stream;
   h->ar.stream = h->st;
@@ -467,14 +536,11 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   }
   cudaStream_t st = h->st;
   bool host = h->prm.host_ptrs != 0;
-  auto kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  if (new_uu)
-    PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.uu_v), jac->A_uu.val, sizeof(double) * h->nnzb_uu * 9, kind, st));
-  if (new_uf)
-    PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.uf_v), jac->A_uf.val, sizeof(double) * h->nnzb_uf * 6, kind, st));
-  PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.fu_v), jac->A_fu.val, sizeof(double) * jac->A_fu.nnzb * 6, kind, st));
-  PS_CUDA(cudaMemcpyAsync(const_cast<double*>(h->J.ff_v), jac->A_ff.val, sizeof(double) * jac->A_ff.nnzb * 4, kind, st));
-  PS_CUDA(cudaMemcpyAsync(h->dfs, jac->d_fs, sizeof(double) * 2 * h->nc, kind, st));
+  if (new_uu) PS_TRY(copy_to(jac->A_uu.val, sizeof(double) * h->nnzb_uu * 9, const_cast<double*>(h->J.uu_v), host, st));
+  if (new_uf) PS_TRY(copy_to(jac->A_uf.val, sizeof(double) * h->nnzb_uf * 6, const_cast<double*>(h->J.uf_v), host, st));
+  PS_TRY(copy_to(jac->A_fu.val, sizeof(double) * jac->A_fu.nnzb * 6, const_cast<double*>(h->J.fu_v), host, st));
+  PS_TRY(copy_to(jac->A_ff.val, sizeof(double) * jac->A_ff.nnzb * 4, const_cast<double*>(h->J.ff_v), host, st));
+  PS_TRY(copy_to(jac->d_fs, sizeof(double) * 2 * h->nc, h->dfs, host, st));
   // the outer SpMV reads the stencil-indexed copies: refill them from the new values
   PS_TRY(jac_refresh_stencil(h->ar, h->J, (new_uu ? 1 : 0) | (new_uf ? 2 : 0) | 4 | 8, st));
   cudaStreamSynchronize(st);
@@ -487,6 +553,7 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   PS_TRY(build_flow(h));
   // the mechanics V-cycle graph holds the old flag's address: capture it again with the new one
   amg_release_graph(h->amg_u);
+  rbm_release_graph(h->rbm_u);
   h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
   h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
   h->amg_u.pdl = h->amg_p.pdl = h->prm.pdl ? 1 : 0;
@@ -522,7 +589,7 @@ ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double to
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  PS_TRY(copy_to(rhs, sizeof(double) * n, h->b, host, st));
   double* xk = h->x;
   double* z = h->Z;
   fill_zero(xk, n, st);
@@ -584,7 +651,7 @@ ps_status solve_richardson(ps_handle* h, const double* rhs, double* x, double to
   S.ms_setup_f = h->ms_setup_f;
   S.ms_copy_in = h->ms_copy_in;
   S.handle_bytes = h->ar.bytes + h->arf.bytes;
-  S.levels_u = int32_t(h->amg_u.L.size());
+  S.levels_u = int32_t(h->rbm ? h->rbm_u.L.size() : h->amg_u.L.size());
   S.levels_p = int32_t(h->amg_p.L.size());
   if (stats) *stats = S;
   return result;
@@ -627,7 +694,7 @@ struct FgmresRun {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
-    PS_CUDA(cudaMemcpyAsync(h->b, rhs, sizeof(double) * n, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    PS_TRY(copy_to(rhs, sizeof(double) * n, h->b, host, st));
     fill_zero(h->x, n, st);
     const int64_t ldv = h->ldv;
     if (ldv > n)  // padding rows of the basis (a failed solve may have left a NaN there)
@@ -775,7 +842,7 @@ struct FgmresRun {
     S.ms_copy_in = h->ms_copy_in;
   S.ms_copy_in = h->ms_copy_in;
     S.handle_bytes = h->ar.bytes + h->arf.bytes;
-    S.levels_u = int32_t(h->amg_u.L.size());
+    S.levels_u = int32_t(h->rbm ? h->rbm_u.L.size() : h->amg_u.L.size());
     S.levels_p = int32_t(h->amg_p.L.size());
     if (stats) *stats = S;
     return result;
@@ -856,6 +923,57 @@ ps_status ps_amg_level_copy(ps_handle* h, int32_t which, int32_t level, int64_t*
   return PS_OK;
 }
 
+int32_t ps_rbm_nlevels(ps_handle* h) { return h && h->rbm ? int32_t(h->rbm_u.L.size()) : 0; }
+
+ps_status ps_rbm_level_shape(ps_handle* h, int32_t level, int64_t* shape) {
+  if (!h || !h->rbm || !shape || level < 0 || level >= int32_t(h->rbm_u.L.size())) return PS_ERR_INVALID;
+  const RbmLevel& L = h->rbm_u.L[level];
+  shape[0] = L.n; shape[1] = L.b; shape[2] = L.nnzb; shape[3] = L.coarsest ? 0 : L.nagg;
+  shape[4] = L.coarsest ? 0 : L.pnnzb; shape[5] = L.coarsest ? 1 : 0;
+  return PS_OK;
+}
+
+namespace {
+ps_status copy_rowptr(ps_handle* h, const int32_t* rp, int64_t n, int64_t* out) {
+  int64_t* tmp;
+  PS_TRY(h->ar.alloc(&tmp, n + 1));
+  PS_TICK(); k_i32_to_i64<<<grid_for(n + 1, 256), 256, 0, h->st>>>(rp, tmp, n + 1);
+  PS_CUDA(cudaMemcpyAsync(out, tmp, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, h->st));
+  PS_CUDA(cudaStreamSynchronize(h->st));
+  h->ar.release(tmp);
+  return PS_OK;
+}
+}  // namespace
+
+ps_status ps_rbm_level_copy(ps_handle* h, int32_t level, int64_t* rowptr, int32_t* colind, double* val,
+                            int32_t* agg) {
+  if (!h || !h->rbm || level < 0 || level >= int32_t(h->rbm_u.L.size())) return PS_ERR_INVALID;
+  const RbmLevel& L = h->rbm_u.L[level];
+  cudaStream_t st = h->st;
+  if (rowptr) PS_TRY(copy_rowptr(h, L.rp, L.n, rowptr));
+  if (colind) PS_CUDA(cudaMemcpyAsync(colind, L.ci, sizeof(int32_t) * L.nnzb, cudaMemcpyDeviceToHost, st));
+  if (val) PS_CUDA(cudaMemcpyAsync(val, L.v, sizeof(double) * L.nnzb * L.b * L.b, cudaMemcpyDeviceToHost, st));
+  if (agg) {
+    if (L.agg && !L.coarsest) PS_CUDA(cudaMemcpyAsync(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, st));
+    else for (int64_t i = 0; i < L.n; ++i) agg[i] = -1;
+  }
+  PS_CUDA(cudaStreamSynchronize(st));
+  return PS_OK;
+}
+
+ps_status ps_rbm_prolongator_copy(ps_handle* h, int32_t level, int64_t* rowptr, int32_t* colind, double* val) {
+  if (!h || !h->rbm || level < 0 || level >= int32_t(h->rbm_u.L.size()) || h->rbm_u.L[level].coarsest)
+    return PS_ERR_INVALID;
+  const RbmLevel& L = h->rbm_u.L[level];
+  cudaStream_t st = h->st;
+  if (rowptr) PS_TRY(copy_rowptr(h, L.prp, L.n, rowptr));
+  if (colind) PS_CUDA(cudaMemcpyAsync(colind, L.pci, sizeof(int32_t) * L.pnnzb, cudaMemcpyDeviceToHost, st));
+  if (val)
+    PS_CUDA(cudaMemcpyAsync(val, L.pv, sizeof(double) * L.pnnzb * L.b * kRbmModes, cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  return PS_OK;
+}
+
 ps_status ps_flow_copy(ps_handle* h, double* spp, double* dinv) {
   if (!h) return PS_ERR_INVALID;
   if (spp) PS_CUDA(cudaMemcpyAsync(spp, h->F.spp, sizeof(double) * h->F.nnzb, cudaMemcpyDeviceToHost, h->st));
@@ -869,6 +987,7 @@ void ps_free(ps_handle* h) {
   cudaStreamSynchronize(h->st);
   amg_release_graph(h->amg_u);
   amg_release_graph(h->amg_p);
+  rbm_release_graph(h->rbm_u);
   h->arf.free_all();
   h->ar.free_all();
   cudaStreamSynchronize(h->st);

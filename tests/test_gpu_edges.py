@@ -60,7 +60,8 @@ def test_bounded_wait_times_out_and_handle_recovers(sysd):
     # a wavefront CTA that never publishes progress: its consumers give up after spin_limit polls,
     # the solve reports PS_ERR_TIMEOUT, and the same handle then solves normally
     osys, dev = sysd
-    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(spin_limit=20000, test_stall_wave=1))
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(spin_limit=20000, test_stall_wave=1,
+                                                             ilu_scope=ps.PS_ILU_GLOBAL))
     try:
         x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
         s, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8, raise_on_error=False)

@@ -121,17 +121,23 @@ def test_hierarchy_parity(cfg, kw, cm):
         ps.ps_free(h)
 
 
+# ILU(0) scope: (library scope, oracle subdomain tiles); the local scope is the default of both
+SCOPES = [(ps.PS_ILU_LOCAL, {}), (ps.PS_ILU_GLOBAL, dict(ilu_tile_y=0, ilu_tile_z=0))]
+
+
+@pytest.mark.parametrize("scope,otiles", SCOPES)
 @pytest.mark.parametrize("ilu", [ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH])
 @pytest.mark.parametrize("cfg,kw,cm", [(0, {}, 16), (0, {}, 500), (1, dict(nx=24, ny=20, nz=10), 500),
                                        (2, dict(nx=20, ny=44, nz=17), 500)])
-def test_apply_parity_fp64(cfg, kw, cm, ilu):
+def test_apply_parity_fp64(cfg, kw, cm, ilu, scope, otiles):
     # Algorithm 1 in FP64 against the oracle's Algorithm 1 on the same vector; the two larger grids have
     # multi-level hierarchies at the default coarse size (500)
     g = _gpu()
     osys = oracle.System(oracle.default_params(cfg, **kw))
-    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm, **otiles))
     dev = g.to_device(osys)
-    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm, ilu_mode=ilu))
+    h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(coarse_max_u=cm, coarse_max_p=cm, ilu_mode=ilu,
+                                                             ilu_scope=scope))
     try:
         for seed in range(3):
             vs = np.random.default_rng(seed).standard_normal(osys.n)
@@ -148,20 +154,21 @@ SOLVE_CASES = [(0, {}, 16), (0, {}, 500), (1, dict(nx=24, ny=20, nz=10), 60), (2
                (0, dict(nx=7, ny=3, nz=2), 500)]
 
 
+@pytest.mark.parametrize("scope,otiles", SCOPES)
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
 @pytest.mark.parametrize("cfg,kw,cm", SOLVE_CASES)
 @pytest.mark.parametrize("ilu", [ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH])
-def test_solve_parity(cfg, kw, cm, prec, ilu):
+def test_solve_parity(cfg, kw, cm, prec, ilu, scope, otiles):
     # true FP64 relres <= 1e-8 (recomputed by the oracle), solution within 1e-6 of the oracle
     # solved to 1e-12, iterations within 10% (+1) of the oracle's FGMRES at 1e-8
     g = _gpu()
     osys = oracle.System(oracle.default_params(cfg, **kw))
-    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=cm, coarse_max_p=cm, **otiles))
     xo, sto = P.fgmres(tol=1e-12)
     _, sto8 = P.fgmres(tol=1e-8)
     dev = g.to_device(osys)
     h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=cm, coarse_max_p=cm,
-                                                             ilu_mode=ilu))
+                                                             ilu_mode=ilu, ilu_scope=scope))
     try:
         x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
         _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
@@ -177,14 +184,15 @@ def test_solve_parity(cfg, kw, cm, prec, ilu):
 
 @pytest.mark.parametrize("prec,rtol", [(ps.PS_FP64, 1e-12), (ps.PS_MIXED_FP32, 2e-5)])
 def test_pencil_wavefront_matches_level_launch(prec, rtol):
-    # the sync-free pencil sweep (several CTAs along y and z) and the level-by-level sweep apply the
-    # same ILU(0) factors: Algorithm 1 outputs agree to rounding
+    # the sync-free pencil sweep of the global ILU(0) (several CTAs along y and z, exchanging tile faces)
+    # and the level-by-level sweep apply the same ILU(0) factors: Algorithm 1 outputs agree to rounding
     g = _gpu()
     osys = oracle.System(oracle.default_params(1, nx=12, ny=40, nz=20))
     dev = g.to_device(osys)
     out = []
     for ilu in (ps.PS_ILU_PENCIL, ps.PS_ILU_LEVEL_LAUNCH):
-        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, ilu_mode=ilu))
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, ilu_mode=ilu,
+                                                                 ilu_scope=ps.PS_ILU_GLOBAL))
         try:
             v = torch.from_numpy(np.random.default_rng(7).standard_normal(osys.n)).cuda()
             z = torch.empty_like(v)
