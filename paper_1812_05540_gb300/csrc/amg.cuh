@@ -120,6 +120,11 @@ ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t
 ps_status amg_aggregate_scalar(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
                                const double* v, double theta, int level, int32_t** agg, int64_t* nagg,
                                uint8_t** excl, cudaStream_t st);
+// sorted column pattern of the product X Y of two CSR patterns (n rows of X, m columns of Y), by the
+// SDC hierarchy's SpGEMM run on unit values; *crp (n + 1) and *cci are allocated in ar
+ps_status amg_spgemm_pattern(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int32_t* xci, int64_t xnnz,
+                             const int32_t* yrp, const int32_t* yci, int64_t ynnz, int32_t** crp, int32_t** cci,
+                             int64_t* cnnz, cudaStream_t st);
 // inverse of a dense n x n FP64 matrix by Gauss-Jordan with partial pivoting: M (row-major) is destroyed,
 // inv must hold the identity on entry
 ps_status amg_dense_inverse(Arena& ar, int64_t n, double* M, double* inv, cudaStream_t st);

@@ -835,22 +835,29 @@ __global__ void __launch_bounds__(256) k_gj_all(int64_t n, int nc, double* __res
       __syncthreads();
     }
     if (!grid_barrier(bar, ++phase * G, limit, err)) return;
-    const int64_t w2 = 2 * n, items = int64_t(nc) * n * w2;
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < items; t += int64_t(G) * blockDim.x) {
-      const int64_t j = t % w2, r = (t / w2) % n;
-      const int c = int(t / (w2 * n));
+    // elimination, one row of one component per CTA at a time.  Columns j < k of A are skipped: there the
+    // pivot row holds exact zeros (earlier pivots cleared them), so the update would leave the entry as it is.
+    for (int64_t rc = blockIdx.x; rc < int64_t(nc) * n; rc += int64_t(G)) {
+      const int c = int(rc / n);
+      const int64_t r = rc - int64_t(c) * n;
       if (r == k) continue;
       const double m = __ldcg(f + int64_t(c) * n + r);
       if (m == 0.0) continue;
       double* A = M + int64_t(c) * n * n;
       double* B = I + int64_t(c) * n * n;
-      if (j < n) A[r * n + j] = __ldcg(A + r * n + j) - m * __ldcg(A + k * n + j);
-      else B[r * n + j - n] = __ldcg(B + r * n + j - n) - m * __ldcg(B + k * n + j - n);
+      for (int64_t j = k + threadIdx.x; j < n; j += blockDim.x)
+        A[r * n + j] = __ldcg(A + r * n + j) - m * __ldcg(A + k * n + j);
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+        B[r * n + j] = __ldcg(B + r * n + j) - m * __ldcg(B + k * n + j);
     }
     if (!grid_barrier(bar, ++phase * G, limit, err)) return;
   }
 }
 
+__global__ void k_fill_one(double* __restrict__ a, int64_t n) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = 1.0;
+}
 __global__ void k_to_bf16(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < n) b[t] = __double2bfloat16(a[t]);
@@ -1270,6 +1277,29 @@ ps_status amg_aggregate_scalar(Arena& ar, int64_t n, int64_t nnz, const int32_t*
   PS_TRY(aggregate_impl<1>(ar, n, nnz, rp, ci, v, dgbar, *excl, theta, level, agg, nagg, st));
   ar.release(dgbar);
   ar.release(dg);
+  return PS_OK;
+}
+
+ps_status amg_spgemm_pattern(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int32_t* xci, int64_t xnnz,
+                             const int32_t* yrp, const int32_t* yci, int64_t ynnz, int32_t** crp, int32_t** cci,
+                             int64_t* cnnz, cudaStream_t st) {
+  double *xo, *yo, *cv;
+  int* d_err;
+  PS_TRY(ar.alloc(&xo, xnnz + 1));
+  PS_TRY(ar.alloc(&yo, ynnz + 1));
+  PS_TRY(ar.alloc(&d_err, 1));
+  PS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  PS_TICK(); k_fill_one<<<grid_for(xnnz + 1, 256), 256, 0, st>>>(xo, xnnz + 1);
+  PS_TICK(); k_fill_one<<<grid_for(ynnz + 1, 256), 256, 0, st>>>(yo, ynnz + 1);
+  PS_TRY(spgemm<1>(ar, n, m, xrp, xci, xo, yrp, yci, yo, crp, cci, &cv, cnnz, d_err, st));
+  int herr = 0;
+  PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  ar.release(xo); ar.release(yo); ar.release(cv); ar.release(d_err);
+  if (herr) {
+    set_reason("SpGEMM capacity exceeded in a block Galerkin product");
+    return PS_ERR_INVALID;
+  }
   return PS_OK;
 }
 

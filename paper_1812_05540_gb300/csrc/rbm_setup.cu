@@ -11,7 +11,6 @@ namespace ps_internal {
 namespace {
 
 constexpr int kMaxRowAgg = 512;    // distinct aggregates among the block columns of one row of A
-constexpr int kMaxRowC = 1024;     // block columns of one row of a Galerkin product
 
 // the six rigid-body modes at node I: translations along x, y, z and rotations about the axes through the
 // grid's centre, (0, -z, y), (z, 0, -x), (-y, x, 0), coordinates in cell widths; rows (x, y, z) of 6
@@ -237,81 +236,44 @@ __global__ void k_row_of(int64_t n, const int32_t* __restrict__ rp, int32_t* __r
   for (int32_t q = rp[i]; q < rp[i + 1]; ++q) rowof[q] = int32_t(i);
 }
 
-// block columns of row i of X Y, ascending; -1 when there are more than cap
-__device__ int prod_cols(int64_t i, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
-                         const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci, int32_t* list, int cap) {
-  int c = 0;
+// C = X Y with BR x BK blocks of X and BK x BC blocks of Y on C's given sorted pattern: block (i, j) sums
+// X_ik Y_kj over ascending k (the order of X's row), each entry of a product summing its inner index in
+// ascending order
+template <int BR, int BK, int BC>
+__global__ void k_bprod(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                        const double* __restrict__ xv, const int32_t* __restrict__ yrp,
+                        const int32_t* __restrict__ yci, const double* __restrict__ yv,
+                        const int32_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t c0 = crp[i], c1 = crp[i + 1];
+  for (int64_t e = int64_t(c0) * BR * BC; e < int64_t(c1) * BR * BC; ++e) cv[e] = 0.0;
   for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
     const int32_t k = xci[q];
+    double X[BR * BK];
+#pragma unroll
+    for (int e = 0; e < BR * BK; ++e) X[e] = xv[int64_t(q) * BR * BK + e];
     for (int32_t r = yrp[k]; r < yrp[k + 1]; ++r) {
       const int32_t j = yci[r];
-      int lo = 0, hi = c;
-      while (lo < hi) {
-        const int md = (lo + hi) >> 1;
-        if (list[md] < j) lo = md + 1;
-        else hi = md;
-      }
-      if (lo < c && list[lo] == j) continue;
-      if (c == cap) return -1;
-      for (int s = c; s > lo; --s) list[s] = list[s - 1];
-      list[lo] = j;
-      ++c;
-    }
-  }
-  return c;
-}
-
-__global__ void k_prod_count(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
-                             const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci, int32_t* __restrict__ cnt,
-                             int* __restrict__ err) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t list[kMaxRowC];
-  int c = prod_cols(i, xrp, xci, yrp, yci, list, kMaxRowC);
-  if (c < 0) {
-    atomicExch(err, 1);
-    c = 0;
-  }
-  cnt[i] = c;
-}
-
-// C = X Y with br x bk blocks of X and bk x bc blocks of Y: block (i, j) sums X_ik Y_kj over ascending k, each
-// entry of a product summing its inner index in ascending order
-__global__ void k_prod_fill(int64_t n, int br, int bk, int bc, const int32_t* __restrict__ xrp,
-                            const int32_t* __restrict__ xci, const double* __restrict__ xv,
-                            const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
-                            const double* __restrict__ yv, const int32_t* __restrict__ crp, int32_t* __restrict__ cci,
-                            double* __restrict__ cv) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t list[kMaxRowC];
-  const int c = prod_cols(i, xrp, xci, yrp, yci, list, kMaxRowC);
-  if (c != crp[i + 1] - crp[i]) return;  // overflow, reported by k_prod_count
-  for (int s = 0; s < c; ++s) {
-    const int32_t j = list[s];
-    double acc[36];
-    for (int e = 0; e < br * bc; ++e) acc[e] = 0.0;
-    for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
-      const int32_t k = xci[q];
-      int32_t lo = yrp[k], hi = yrp[k + 1];
+      int32_t lo = c0, hi = c1;
       while (lo < hi) {
         const int32_t md = (lo + hi) >> 1;
-        if (yci[md] < j) lo = md + 1;
+        if (cci[md] < j) lo = md + 1;
         else hi = md;
       }
-      if (lo == yrp[k + 1] || yci[lo] != j) continue;
-      const double* X = xv + int64_t(q) * br * bk;
-      const double* Y = yv + int64_t(lo) * bk * bc;
-      for (int a = 0; a < br; ++a)
-        for (int cc = 0; cc < bc; ++cc) {
+      if (lo >= c1) continue;  // not in the pattern: cannot happen for a pattern of X Y
+      double* C = cv + int64_t(lo) * BR * BC;
+      const double* Y = yv + int64_t(r) * BK * BC;
+#pragma unroll
+      for (int a = 0; a < BR; ++a)
+#pragma unroll
+        for (int c = 0; c < BC; ++c) {
           double p = 0.0;
-          for (int e = 0; e < bk; ++e) p = p + X[a * bk + e] * Y[e * bc + cc];
-          acc[a * bc + cc] = acc[a * bc + cc] + p;
+#pragma unroll
+          for (int e = 0; e < BK; ++e) p = p + X[a * BK + e] * Y[e * BC + c];
+          C[a * BC + c] = C[a * BC + c] + p;
         }
     }
-    const int64_t o = crp[i] + s;
-    cci[o] = j;
-    for (int e = 0; e < br * bc; ++e) cv[o * br * bc + e] = acc[e];
   }
 }
 
@@ -475,40 +437,40 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
     PS_CUDA(cudaGetLastError());
     ar.release(tc); ar.release(tcur); ar.release(src); ar.release(rowof);
     lev.rlane = lanes_for(double(pnnz) / double(na));
-    // A_c = R (A P)
-    int32_t *ac, *aprp, *apci;
+    // A_c = R (A P): patterns by the SDC hierarchy's SpGEMM, block values by k_bprod
+    int32_t *aprp, *apci;
+    int64_t apnnz = 0;
+    PS_TRY(amg_spgemm_pattern(ar, n, na, lev.rp, lev.ci, nnzb, lev.prp, lev.pci, pnnz, &aprp, &apci, &apnnz, st));
     double* apv;
-    PS_TRY(ar.alloc(&ac, n + 1));
-    PS_TRY(ar.alloc(&aprp, n + 1));
-    PS_TICK(); k_prod_count<<<grid_for(n, 64), 64, 0, st>>>(n, lev.rp, lev.ci, lev.prp, lev.pci, ac, err);
-    int32_t apnnz = 0;
-    PS_TRY(scan_i32(ar, ac, aprp, n, &apnnz, st));
-    PS_TRY(ar.alloc(&apci, size_t(apnnz) + 1));
     PS_TRY(ar.alloc(&apv, (size_t(apnnz) + 1) * b * kRbmModes));
-    PS_TICK(); k_prod_fill<<<grid_for(n, 64), 64, 0, st>>>(n, b, b, kRbmModes, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
-                                                            lev.pv, aprp, apci, apv);
-    ar.release(ac);
+    if (b == 3) {
+      PS_TICK(); k_bprod<3, 3, kRbmModes><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
+                                                                           lev.pv, aprp, apci, apv);
+    } else {
+      PS_TICK(); k_bprod<6, 6, kRbmModes><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
+                                                                           lev.pv, aprp, apci, apv);
+    }
     RbmLevel C;
     C.n = na; C.b = kRbmModes; C.B = Bc;
-    int32_t* cc;
-    PS_TRY(ar.alloc(&cc, na + 1));
-    PS_TRY(ar.alloc(&C.rp, na + 1));
-    PS_TICK(); k_prod_count<<<grid_for(na, 64), 64, 0, st>>>(na, lev.rrp, lev.rci, aprp, apci, cc, err);
-    int32_t cnnz = 0;
-    PS_TRY(scan_i32(ar, cc, C.rp, na, &cnnz, st));
+    int64_t cnnz = 0;
+    PS_TRY(amg_spgemm_pattern(ar, na, na, lev.rrp, lev.rci, pnnz, aprp, apci, apnnz, &C.rp, &C.ci, &cnnz, st));
     C.nnzb = cnnz;
-    PS_TRY(ar.alloc(&C.ci, size_t(cnnz) + 1));
     PS_TRY(ar.alloc(&C.v, (size_t(cnnz) + 1) * kRbmModes * kRbmModes));
-    PS_TICK(); k_prod_fill<<<grid_for(na, 64), 64, 0, st>>>(na, kRbmModes, b, kRbmModes, lev.rrp, lev.rci, lev.rv, aprp,
-                                                             apci, apv, C.rp, C.ci, C.v);
+    if (b == 3) {
+      PS_TICK(); k_bprod<kRbmModes, 3, kRbmModes><<<grid_for(na, 64), 64, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
+                                                                                   apci, apv, C.rp, C.ci, C.v);
+    } else {
+      PS_TICK(); k_bprod<kRbmModes, 6, kRbmModes><<<grid_for(na, 64), 64, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
+                                                                                   apci, apv, C.rp, C.ci, C.v);
+    }
     PS_TICK(); k_fix_diag<<<grid_for(na, 256), 256, 0, st>>>(na, kRbmModes, C.rp, C.ci, C.v);
     PS_CUDA(cudaGetLastError());
-    ar.release(cc); ar.release(aprp); ar.release(apci); ar.release(apv);
+    ar.release(aprp); ar.release(apci); ar.release(apv);
     int herr = 0;
     PS_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     if (herr) {
-      set_reason("rigid-body-mode hierarchy: a row of level %d has more block columns than the setup kernels hold", l);
+      set_reason("rigid-body-mode hierarchy: a row of level %d touches more aggregates than the setup kernels hold", l);
       return PS_ERR_INVALID;
     }
     if (mixed) {
