@@ -1468,7 +1468,8 @@ bool build_rbm(BAMG& H, BSR A0, vec B0, double theta0, int coarse_max, int max_l
     BLevel& lev = H.L[l];
     const int b = lev.b;
     const int64_t n = lev.A.nbr;
-    bool coarsest = n <= coarse_max || l + 1 >= max_levels;
+    // coarse_max counts nodes: a level is coarsest at 3 coarse_max unknowns, as many as coarse_max nodes carry
+    bool coarsest = n * b <= int64_t(3) * coarse_max || l + 1 >= max_levels;
     if (!coarsest) {
       Level sl;
       sl.A = block_strength(lev.A);

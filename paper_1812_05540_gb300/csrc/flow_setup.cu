@@ -123,6 +123,41 @@ __global__ void k_ilu_factor(const int32_t* __restrict__ cells, int32_t ncell_le
   inv22(D, &dinv[int64_t(i) * 4]);
 }
 
+// Processor-local ILU(0) factor in one launch: CTA t factors the cells of sweep tile t (its own subdomain) in
+// the forward sweep's wavefront order, thread (ly, lz) taking pencil position x = s - ly - lz at step s, so a
+// cell's lower neighbours in the tile were factored at earlier steps; one barrier per step.  Each cell runs
+// the arithmetic of k_ilu_factor with local != 0, so the factors are the same bits.
+__global__ void __launch_bounds__(kTY * kTZ) k_ilu_factor_tiles(int nx, int ny, int nz, const int32_t* __restrict__ rp,
+                                                                const int32_t* __restrict__ ci,
+                                                                const int32_t* __restrict__ diagpos,
+                                                                const double* __restrict__ sff, double* __restrict__ dinv) {
+  const int nby = (ny + kTY - 1) / kTY;
+  const int ly = threadIdx.x % kTY, lz = threadIdx.x / kTY;
+  const int yy = (blockIdx.x % nby) * kTY + ly, zz = (blockIdx.x / nby) * kTZ + lz;
+  const bool valid = yy < ny && zz < nz;
+  const int last = nx + kTY + kTZ - 3;
+  for (int s = 0; s <= last; ++s) {
+    const int x = s - ly - lz;
+    if (valid && x >= 0 && x < nx) {
+      const int32_t i = int32_t(x + int64_t(nx) * (yy + int64_t(ny) * zz));
+      const int32_t qd = diagpos[i];
+      double D[4] = {sff[int64_t(qd) * 4], sff[int64_t(qd) * 4 + 1], sff[int64_t(qd) * 4 + 2], sff[int64_t(qd) * 4 + 3]};
+      for (int32_t q = rp[i]; q < qd; ++q) {
+        const int32_t k = ci[q];
+        if (cross_tile(i, k, nx, ny)) continue;
+        double L[4], U[4];
+        mul22(&sff[int64_t(q) * 4], &dinv[int64_t(k) * 4], L);
+        int32_t qk = diagpos[k] + 1;
+        while (ci[qk] != i) ++qk;
+        mul22(L, &sff[int64_t(qk) * 4], U);
+        for (int e = 0; e < 4; ++e) D[e] -= U[e];
+      }
+      inv22(D, &dinv[int64_t(i) * 4]);
+    }
+    __syncthreads();
+  }
+}
+
 // S_ff^(FS) by stencil slot (the row of a 7-point pattern is z-1, y-1, x-1, self, x+1, y+1, z+1 with
 // the missing neighbours left out), 28 entries per cell
 __global__ void k_s28(int nx, int ny, int nz, const int32_t* __restrict__ rp, const double* __restrict__ sff,
@@ -284,10 +319,16 @@ ps_status flow_setup(Arena& ar, FlowStage& F, const int32_t* ff_rp, const int32_
   }
   PS_TICK(); k_sff_spp<<<grid_for(nc, 256), 256, 0, st>>>(nc, ff_rp, ff_ci, ff_v, d_fs, F.sff, F.spp, F.dss, F.dps, F.aps,
                                                F.diagpos, F.cpr == PS_CPR_TRUE_IMPES);
-  for (int l = 0; l < (F.local == PS_LOCAL_HBGS ? 0 : F.nlev); ++l) {
-    int32_t m = F.lev_off[l + 1] - F.lev_off[l];
-    PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos, F.sff,
-                                                   F.dinv, F.nx, F.ny, F.ilu_local);
+  if (F.local != PS_LOCAL_HBGS && F.ilu_local) {
+    // processor-local: the tiles are independent, one CTA each
+    PS_TICK(); k_ilu_factor_tiles<<<unsigned(sweep_tiles(F.ny, F.nz)), kTY * kTZ, 0, st>>>(F.nx, F.ny, F.nz, F.rp, F.ci,
+                                                                                         F.diagpos, F.sff, F.dinv);
+  } else {
+    for (int l = 0; l < (F.local == PS_LOCAL_HBGS ? 0 : F.nlev); ++l) {
+      int32_t m = F.lev_off[l + 1] - F.lev_off[l];
+      PS_TICK(); k_ilu_factor<<<grid_for(m, 128), 128, 0, st>>>(F.lev_cells + F.lev_off[l], m, F.rp, F.ci, F.diagpos,
+                                                                 F.sff, F.dinv, F.nx, F.ny, F.ilu_local);
+    }
   }
   PS_TICK(); k_s28<<<grid_for(nc, 256), 256, 0, st>>>(F.nx, F.ny, F.nz, F.rp, F.sff, F.s28);
   PS_CUDA(cudaGetLastError());

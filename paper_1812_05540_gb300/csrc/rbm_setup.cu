@@ -236,23 +236,26 @@ __global__ void k_row_of(int64_t n, const int32_t* __restrict__ rp, int32_t* __r
   for (int32_t q = rp[i]; q < rp[i + 1]; ++q) rowof[q] = int32_t(i);
 }
 
-// C = X Y with BR x BK blocks of X and BK x BC blocks of Y on C's given sorted pattern: block (i, j) sums
-// X_ik Y_kj over ascending k (the order of X's row), each entry of a product summing its inner index in
-// ascending order
+// C = X Y with BR x BK blocks of X and BK x BC blocks of Y on C's given sorted pattern, one warp per row of C:
+// block (i, j) sums X_ik Y_kj over ascending k (the order of X's row), each entry of a product summing its
+// inner index in ascending order.  The warp walks the row's products in that order; lane t owns the entries
+// t and t + 32 of the output block, so every entry is accumulated by one lane, in order.
 template <int BR, int BK, int BC>
-__global__ void k_bprod(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
-                        const double* __restrict__ xv, const int32_t* __restrict__ yrp,
-                        const int32_t* __restrict__ yci, const double* __restrict__ yv,
-                        const int32_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_bprod(int64_t n, const int32_t* __restrict__ xrp,
+                                               const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                                               const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                               const double* __restrict__ yv, const int32_t* __restrict__ crp,
+                                               const int32_t* __restrict__ cci, double* __restrict__ cv) {
+  constexpr int NE = BR * BC;
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= n) return;
   const int32_t c0 = crp[i], c1 = crp[i + 1];
-  for (int64_t e = int64_t(c0) * BR * BC; e < int64_t(c1) * BR * BC; ++e) cv[e] = 0.0;
+  for (int64_t e = int64_t(c0) * NE + lane; e < int64_t(c1) * NE; e += 32) cv[e] = 0.0;
+  __syncwarp();
   for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
     const int32_t k = xci[q];
-    double X[BR * BK];
-#pragma unroll
-    for (int e = 0; e < BR * BK; ++e) X[e] = xv[int64_t(q) * BR * BK + e];
+    const double* X = xv + int64_t(q) * BR * BK;
     for (int32_t r = yrp[k]; r < yrp[k + 1]; ++r) {
       const int32_t j = yci[r];
       int32_t lo = c0, hi = c1;
@@ -262,17 +265,16 @@ __global__ void k_bprod(int64_t n, const int32_t* __restrict__ xrp, const int32_
         else hi = md;
       }
       if (lo >= c1) continue;  // not in the pattern: cannot happen for a pattern of X Y
-      double* C = cv + int64_t(lo) * BR * BC;
+      double* C = cv + int64_t(lo) * NE;
       const double* Y = yv + int64_t(r) * BK * BC;
 #pragma unroll
-      for (int a = 0; a < BR; ++a)
+      for (int t = lane; t < NE; t += 32) {
+        const int a = t / BC, c = t % BC;
+        double p = 0.0;
 #pragma unroll
-        for (int c = 0; c < BC; ++c) {
-          double p = 0.0;
-#pragma unroll
-          for (int e = 0; e < BK; ++e) p = p + X[a * BK + e] * Y[e * BC + c];
-          C[a * BC + c] = C[a * BC + c] + p;
-        }
+        for (int e = 0; e < BK; ++e) p = p + X[a * BK + e] * Y[e * BC + c];
+        C[t] = C[t] + p;
+      }
     }
   }
 }
@@ -328,7 +330,8 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
     const int64_t n = lev.n, nnzb = lev.nnzb;
     const int b = lev.b;
     lev.lanes = lanes_for(double(nnzb) / double(n > 0 ? n : 1));
-    bool coarsest = n <= coarse_max || l + 1 >= max_levels;
+    // coarse_max counts nodes: a level is coarsest at 3 coarse_max unknowns, as many as coarse_max nodes carry
+    bool coarsest = n * b <= int64_t(3) * coarse_max || l + 1 >= max_levels;
     uint8_t* excl = nullptr;
     if (!coarsest) {
       double* s;
@@ -444,10 +447,10 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
     double* apv;
     PS_TRY(ar.alloc(&apv, (size_t(apnnz) + 1) * b * kRbmModes));
     if (b == 3) {
-      PS_TICK(); k_bprod<3, 3, kRbmModes><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
+      PS_TICK(); k_bprod<3, 3, kRbmModes><<<grid_for(n * 32, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
                                                                            lev.pv, aprp, apci, apv);
     } else {
-      PS_TICK(); k_bprod<6, 6, kRbmModes><<<grid_for(n, 128), 128, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
+      PS_TICK(); k_bprod<6, 6, kRbmModes><<<grid_for(n * 32, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.prp, lev.pci,
                                                                            lev.pv, aprp, apci, apv);
     }
     RbmLevel C;
@@ -457,10 +460,10 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
     C.nnzb = cnnz;
     PS_TRY(ar.alloc(&C.v, (size_t(cnnz) + 1) * kRbmModes * kRbmModes));
     if (b == 3) {
-      PS_TICK(); k_bprod<kRbmModes, 3, kRbmModes><<<grid_for(na, 64), 64, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
+      PS_TICK(); k_bprod<kRbmModes, 3, kRbmModes><<<grid_for(na * 32, 256), 256, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
                                                                                    apci, apv, C.rp, C.ci, C.v);
     } else {
-      PS_TICK(); k_bprod<kRbmModes, 6, kRbmModes><<<grid_for(na, 64), 64, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
+      PS_TICK(); k_bprod<kRbmModes, 6, kRbmModes><<<grid_for(na * 32, 256), 256, 0, st>>>(na, lev.rrp, lev.rci, lev.rv, aprp,
                                                                                    apci, apv, C.rp, C.ci, C.v);
     }
     PS_TICK(); k_fix_diag<<<grid_for(na, 256), 256, 0, st>>>(na, kRbmModes, C.rp, C.ci, C.v);
