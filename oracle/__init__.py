@@ -117,6 +117,7 @@ def lib(openmp=None):
         L = C.CDLL(build(openmp=openmp))
         L.or_num_threads.restype = C.c_int
         L.or_generate.argtypes = [C.POINTER(GenParams), C.POINTER(C.POINTER(_System))]
+        L.or_generate_at.argtypes = [C.POINTER(GenParams), _PD, C.POINTER(C.POINTER(_System))]
         L.or_system_free.argtypes = [C.POINTER(_System)]
         L.or_default_params.argtypes = [C.POINTER(GenParams), C.c_int]
         L.or_spmv.argtypes = [C.POINTER(_System), _PD, _PD]
@@ -207,10 +208,15 @@ def default_params(config=0, **kw):
 class System:
     """A generated Jacobian held as numpy arrays (copied out of the oracle)."""
 
-    def __init__(self, gp):
+    def __init__(self, gp, dx=None):
+        """dx: the Jacobian at the state base + dx (n values ordered as x); None: at the base state"""
         ptr = C.POINTER(_System)()
         self._L = lib()
-        rc = self._L.or_generate(C.byref(gp), C.byref(ptr))
+        if dx is None:
+            rc = self._L.or_generate(C.byref(gp), C.byref(ptr))
+        else:
+            dx = np.ascontiguousarray(dx, dtype=np.float64)
+            rc = self._L.or_generate_at(C.byref(gp), _d(dx), C.byref(ptr))
         if rc:
             raise RuntimeError("or_generate failed: %d" % rc)
         self._ptr = ptr

@@ -1638,12 +1638,19 @@ void or_default_params(or_gen_params* gp, int config) {
   gp->E0 = 1e10; gp->nu0 = 0.25; gp->kappa0 = 100.0 * kMilliDarcy; gp->phi0 = 0.2; gp->sw0 = 0.5;
 }
 
-int or_generate(const or_gen_params* gp, or_system** out) {
+// the Jacobian at the state base + dx (dx = NULL: the base state u = 0, s = S_w, p of the fields), the base
+// state being the previous time level
+static int generate_at(const or_gen_params* gp, const double* dx, or_system** out) {
   if (gp->nx < 1 || gp->ny < 1 || gp->nz < 1) return 1;
   Grid g{gp->nx, gp->ny, gp->nz, gp->h};
   Fields F = make_fields(*gp);
   State st;
   st.s = F.sw; st.p = F.p;
+  if (dx) {
+    const int64_t nu = 3 * g.nn();
+    st.u.assign(dx, dx + nu);
+    for (int64_t c = 0; c < g.ncell(); ++c) { st.s[c] += dx[nu + 2 * c]; st.p[c] += dx[nu + 2 * c + 1]; }
+  }
   Jac J;
   ExtraBC bc;
   assemble(*gp, g, F, st, bc, J);
@@ -1671,6 +1678,9 @@ int or_generate(const or_gen_params* gp, or_system** out) {
   *out = s;
   return 0;
 }
+
+int or_generate(const or_gen_params* gp, or_system** out) { return generate_at(gp, nullptr, out); }
+int or_generate_at(const or_gen_params* gp, const double* dx, or_system** out) { return generate_at(gp, dx, out); }
 
 void or_system_free(or_system* s) {
   if (!s) return;

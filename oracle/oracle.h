@@ -105,6 +105,11 @@ void or_spmv(const or_system* s, const double* x, double* y);
    IdN[8][3] = int dN_a/dx_d, INdN[8][8][3] = int N_a dN_b/dx_e */
 void or_ref_integrals(double h, double* G, double* IN, double* IdN, double* INdN);
 
+/* the system at the state base + dx (dx: n values ordered as x), the base state (u = 0, s = S_w, p of the
+   fields) taken as the previous time level: the Jacobian there, Dirichlet elimination and scaling as in
+   or_generate (alpha_u, alpha_f are that Jacobian's), rhs as in or_generate */
+int or_generate_at(const or_gen_params* gp, const double* dx, or_system** out);
+
 /* residual of the discrete weak form (§3, App. B) at x = state + dx, with the
    previous time level equal to the linearisation state (unscaled, no Dirichlet
    elimination).  Used for finite-difference checks of the Jacobian. */
