@@ -51,6 +51,19 @@ def build(force=False, openmp=False):
     return out
 
 
+class NewtonParams(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_newton", C.c_int32), ("forcing", C.c_int32), ("eta_fixed", C.c_double),
+                ("ew_gamma", C.c_double), ("ew_omega", C.c_double), ("ew_eta0", C.c_double),
+                ("ew_eta_max", C.c_double), ("max_backtracks", C.c_int32), ("restart", C.c_int32),
+                ("max_linear", C.c_int32)]
+
+
+class NewtonStats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("linear_iters", C.c_int32), ("backtracks", C.c_int32),
+                ("converged", C.c_int32), ("rnorm", C.c_double * 33), ("eta", C.c_double * 32),
+                ("lin_iters", C.c_int32 * 32)]
+
+
 class GenParams(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
                 ("seed", C.c_uint64), ("field_kind", C.c_int32), ("flags", C.c_uint32),
@@ -118,6 +131,11 @@ def lib(openmp=None):
         L.or_num_threads.restype = C.c_int
         L.or_generate.argtypes = [C.POINTER(GenParams), C.POINTER(C.POINTER(_System))]
         L.or_generate_at.argtypes = [C.POINTER(GenParams), _PD, C.POINTER(C.POINTER(_System))]
+        L.or_newton_params_default.argtypes = [C.POINTER(NewtonParams)]
+        L.or_newton.argtypes = [C.POINTER(GenParams), C.POINTER(PrecParams), C.POINTER(NewtonParams), _PD,
+                                C.POINTER(NewtonStats)]
+        L.or_ew_eta.argtypes = [C.POINTER(NewtonParams), C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.or_ew_eta.restype = C.c_double
         L.or_system_free.argtypes = [C.POINTER(_System)]
         L.or_default_params.argtypes = [C.POINTER(GenParams), C.c_int]
         L.or_spmv.argtypes = [C.POINTER(_System), _PD, _PD]
@@ -477,6 +495,35 @@ def correlated_field(seed, field, nx, ny, nz, Lx, Ly, Lz):
     out = np.empty(nx * ny * nz)
     lib().or_correlated_field(seed, field, nx, ny, nz, Lx, Ly, Lz, _d(out))
     return out.reshape(nz, ny, nx)
+
+
+FORCING_FIXED, FORCING_EW = 0, 1
+
+
+def default_newton_params(**kw):
+    np_ = NewtonParams()
+    lib().or_newton_params_default(C.byref(np_))
+    for k, v in kw.items():
+        setattr(np_, k, v)
+    return np_
+
+
+def newton(gp, pp=None, np_=None):
+    """Newton's method for one time step from the base state: (x relative to the base state, stats dict)"""
+    pp = pp or default_prec_params()
+    np_ = np_ or default_newton_params()
+    n = 3 * (gp.nx + 1) * (gp.ny + 1) * (gp.nz + 1) + 2 * gp.nx * gp.ny * gp.nz
+    x = np.zeros(n)
+    st = NewtonStats()
+    rc = lib().or_newton(C.byref(gp), C.byref(pp), C.byref(np_), _d(x), C.byref(st))
+    k = st.newton_iters
+    return x, dict(rc=rc, newton_iters=k, linear_iters=st.linear_iters, backtracks=st.backtracks,
+                   converged=bool(st.converged), rnorm=list(st.rnorm[:k + 1]), eta=list(st.eta[:k]),
+                   lin_iters=list(st.lin_iters[:k]))
+
+
+def ew_eta(np_, k, rk, rkm1, eta_prev, r0):
+    return lib().or_ew_eta(C.byref(np_), k, rk, rkm1, eta_prev, r0)
 
 
 def residual(gp, dx):

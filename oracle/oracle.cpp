@@ -2571,3 +2571,118 @@ int or_terzaghi(const or_terzaghi_params* tp, double* tout, double* pout, double
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Newton's method for one time step (§4 and its remarks on inexact Newton).  The previous time level is the
+// base state (u = 0, s = S_w, p of the fields) and is also the first iterate.  Each step evaluates the
+// residual at base + x (Dirichlet rows set to zero), assembles the Jacobian there (or_generate_at: rows
+// divided by that Jacobian's alpha_u, alpha_f, pressure unknowns in MPa), and solves J y = -R r by FGMRES
+// under the two-stage preconditioner to the relative tolerance eta_k, keeping the mechanics hierarchy of the
+// first step (§5.4); dx = C y.  Convergence is measured in the base state's row scaling R_0.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void or_newton_params_default(or_newton_params* np) {
+  std::memset(np, 0, sizeof(*np));
+  np->rtol = 1e-8;
+  np->max_newton = 12;
+  np->forcing = OR_FORCING_EW;
+  np->eta_fixed = 1e-6;
+  np->ew_gamma = 0.9;
+  np->ew_omega = 2.0;
+  np->ew_eta0 = 0.1;
+  np->ew_eta_max = 0.1;
+  np->max_backtracks = 4;
+  np->restart = 100;
+  np->max_linear = 1000;
+}
+
+// Krylov tolerance of Newton step k (Eisenstat and Walker's choice 2 with the safeguard the paper states,
+// capped at eta_max and floored so that the step does not solve beyond the nonlinear tolerance)
+double or_ew_eta(const or_newton_params* np, int k, double rk, double rkm1, double eta_prev, double r0) {
+  if (np->forcing == OR_FORCING_FIXED) return np->eta_fixed;
+  double eta;
+  if (k == 0) {
+    eta = np->ew_eta0;
+  } else {
+    eta = np->ew_gamma * std::pow(rk / rkm1, np->ew_omega);
+    const double safe = np->ew_gamma * std::pow(eta_prev, np->ew_omega);
+    if (safe > 0.1) eta = std::max(eta, safe);
+  }
+  eta = std::min(eta, np->ew_eta_max);
+  eta = std::max(eta, 0.5 * np->rtol * r0 / rk);
+  return eta;
+}
+
+int or_newton(const or_gen_params* gp, const or_prec_params* pp, const or_newton_params* np, double* x_out,
+              or_newton_stats* st) {
+  std::memset(st, 0, sizeof(*st));
+  or_system* s0 = nullptr;
+  if (generate_at(gp, nullptr, &s0)) return 1;
+  const int64_t n = s0->n, nu = s0->n_u;
+  const double au0 = s0->alpha_u, af0 = s0->alpha_f;
+  auto resid = [&](const vec& x, vec& r) {
+    r.assign(n, 0.0);
+    or_residual(gp, x.data(), r.data());
+    for (int64_t i = 0; i < nu; ++i)
+      if (s0->dirichlet[i]) r[i] = 0.0;
+  };
+  auto snorm = [&](const vec& r, double au, double af) {
+    double a = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double v = r[i] / (i < nu ? au : af);
+      a += v * v;
+    }
+    return std::sqrt(a);
+  };
+  vec x(n, 0.0), r, rt, y(n), rhs(n), xt(n);
+  resid(x, r);
+  double rk = snorm(r, au0, af0);
+  const double r0 = rk;
+  st->rnorm[0] = rk;
+  double rkm1 = rk, eta_prev = np->ew_eta0;
+  int rc = 0;
+  for (int k = 0; k < np->max_newton && k < 32; ++k) {
+    if (rk <= np->rtol * r0) { st->converged = 1; break; }
+    or_system* sk = nullptr;
+    if (generate_at(gp, x.data(), &sk)) { rc = 1; break; }
+    or_prec* P = nullptr;
+    if (or_prec_setup_reuse(sk, s0, pp, &P)) { or_system_free(sk); rc = 2; break; }
+    const double eta = or_ew_eta(np, k, rk, rkm1, eta_prev, r0);
+    for (int64_t i = 0; i < n; ++i) rhs[i] = -r[i] / (i < nu ? sk->alpha_u : sk->alpha_f);
+    or_stats ls;
+    std::fill(y.begin(), y.end(), 0.0);
+    or_fgmres(sk, P, rhs.data(), y.data(), eta, np->restart, np->max_linear, &ls);
+    or_prec_free(P);
+    or_system_free(sk);
+    st->eta[k] = eta;
+    st->lin_iters[k] = ls.iters;
+    st->linear_iters += ls.iters;
+    // dx = C y (pressure unknowns in MPa); backtracking on the R_0-scaled residual norm
+    double lam = 1.0, rt_norm = 0.0;
+    for (int bt = 0;; ++bt) {
+      for (int64_t i = 0; i < n; ++i) {
+        const bool pcol = i >= nu && ((i - nu) & 1);
+        xt[i] = x[i] + lam * (pcol ? 1e6 * y[i] : y[i]);
+      }
+      resid(xt, rt);
+      rt_norm = snorm(rt, au0, af0);
+      if (rt_norm <= (1.0 - 1e-4 * lam) * rk || bt >= np->max_backtracks) break;
+      lam *= 0.5;
+      ++st->backtracks;
+    }
+    x = xt;
+    r = rt;
+    rkm1 = rk;
+    rk = rt_norm;
+    eta_prev = eta;
+    st->newton_iters = k + 1;
+    st->rnorm[k + 1] = rk;
+  }
+  if (!rc && rk <= np->rtol * r0) st->converged = 1;
+  std::copy(x.begin(), x.end(), x_out);
+  or_system_free(s0);
+  return rc ? rc : (st->converged ? 0 : 4);
+}
+
+}  // extern "C"

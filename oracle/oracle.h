@@ -211,6 +211,32 @@ typedef struct {
 /* FGMRES(m) with right preconditioning (§4), x0 = 0 */
 int or_fgmres(const or_system* s, or_prec* p, const double* b, double* x, double tol,
               int restart, int max_iters, or_stats* st);
+/* Newton's method for one time step (§4 and its remarks on inexact Newton): the previous time level is the
+   base state and the first iterate; each step solves J y = -R r by FGMRES under the two-stage preconditioner
+   (mechanics hierarchy of the first step kept, §5.4) to the relative tolerance eta_k, with dx = C y
+   (pressure in MPa) and backtracking; converged when ||R_0 r_k|| <= rtol ||R_0 r_0||. */
+enum { OR_FORCING_FIXED = 0, OR_FORCING_EW = 1 };
+typedef struct {
+  double rtol;
+  int32_t max_newton;
+  int32_t forcing;         /* OR_FORCING_FIXED (eta_fixed) or OR_FORCING_EW (Eisenstat-Walker choice 2) */
+  double eta_fixed;
+  double ew_gamma, ew_omega, ew_eta0, ew_eta_max;
+  int32_t max_backtracks;
+  int32_t restart, max_linear;
+} or_newton_params;
+typedef struct {
+  int32_t newton_iters, linear_iters, backtracks, converged;
+  double rnorm[33];        /* ||R_0 r_k||, k = 0 .. newton_iters */
+  double eta[32];
+  int32_t lin_iters[32];
+} or_newton_stats;
+void or_newton_params_default(or_newton_params* np);
+double or_ew_eta(const or_newton_params* np, int k, double rk, double rkm1, double eta_prev, double r0);
+/* x_out: the converged x (u, then (s, p) per cell) relative to the base state */
+int or_newton(const or_gen_params* gp, const or_prec_params* pp, const or_newton_params* np, double* x_out,
+              or_newton_stats* st);
+
 /* sequential fixed-stress strategy (§5.4 remark): Richardson iteration x <- x + M^{-1}(b - A x) from x0 = 0
    until ||b - A x|| <= tol ||b|| or max_iters applications of M^{-1} */
 int or_richardson(const or_system* s, or_prec* p, const double* b, double* x, double tol, int max_iters,
