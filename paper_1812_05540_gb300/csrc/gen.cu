@@ -175,21 +175,24 @@ struct Phys {
   int fs_modulus;  // 0: K_dr in the fixed-stress diagonal, 1: uniaxial modulus K_dr + 4G/3
 };
 struct CellMat {
-  double lam, G, Kdr, dphidp, phi, rw, rnw, drho_deps, drho_dp, drho_ds;
+  double lam, G, Kdr, dphidp, phi, rw, rnw, rs, drho_deps, drho_dp, drho_ds;
 };
 
-__device__ inline CellMat cell_mat(const Phys& P, double E, double nu, double phi0, double s, double p) {
+// material state of a cell (App. B): moduli, porosity at mean volumetric strain ev, densities and their
+// derivatives
+__device__ inline CellMat cell_mat(const Phys& P, double E, double nu, double phi0, double s, double p,
+                                   double ev = 0.0) {
   CellMat m;
   m.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   m.G = E / (2.0 * (1.0 + nu));
   m.Kdr = E / (3.0 * (1.0 - 2.0 * nu));
   m.dphidp = (P.b - phi0) * (1.0 - P.b) / m.Kdr;
   double dp = p - P.p_ref;
-  m.phi = phi0 + P.b * 0.0 + m.dphidp * dp;
+  m.phi = phi0 + P.b * ev + m.dphidp * dp;
   m.rw = P.rho_w0 * (1.0 + P.c_w * dp);
   m.rnw = P.rho_nw0 * (1.0 + P.c_nw * dp);
-  double rs = P.rho_s0 * (1.0 + P.c_r * dp);
-  double B = -rs + s * m.rw + (1.0 - s) * m.rnw;
+  m.rs = P.rho_s0 * (1.0 + P.c_r * dp);
+  double B = -m.rs + s * m.rw + (1.0 - s) * m.rnw;
   m.drho_deps = B * P.b;
   m.drho_dp = B * m.dphidp + (1.0 - m.phi) * P.rho_s0 * P.c_r + s * m.phi * P.rho_w0 * P.c_w +
               (1.0 - s) * m.phi * P.rho_nw0 * P.c_nw;
@@ -216,8 +219,9 @@ __device__ inline void corey(const Phys& P, double s, double* krw, double* krnw,
   }
 }
 
-struct Ref {  // Q1 integrals on the cube of edge h
+struct Ref {  // Q1 integrals on the cube of edge h, and the shape functions at the 8 Gauss points
   double G[8][8][3][3], IN[8], IdN[8][3], INdN[8][8][3];
+  double gN[8][8], gdN[8][8][3], gw;  // [Gauss point][node]
 };
 
 // 2x2x2 Gauss on [0,h]^3; node a has coordinates ((a>>d)&1) h along axis d
@@ -239,6 +243,11 @@ void build_ref(double h, Ref* R) {
       dN[a][0] = df[0] * f[1] * f[2];
       dN[a][1] = f[0] * df[1] * f[2];
       dN[a][2] = f[0] * f[1] * df[2];
+    }
+    R->gw = w;
+    for (int a = 0; a < 8; ++a) {
+      R->gN[g][a] = N[a];
+      for (int d = 0; d < 3; ++d) R->gdN[g][a][d] = dN[a][d];
     }
     for (int a = 0; a < 8; ++a) {
       R->IN[a] += w * N[a];
@@ -320,9 +329,9 @@ __global__ void k_pattern_fill(Grid3 g, int kind, int64_t nrows, const int64_t* 
 // ---- material table per cell ----
 __global__ void k_material(Phys P, int64_t nc, const double* __restrict__ E, const double* __restrict__ nu,
                            const double* __restrict__ phi0, const double* __restrict__ sw,
-                           const double* __restrict__ p, CellMat* __restrict__ out) {
+                           const double* __restrict__ p, const double* __restrict__ ev, CellMat* __restrict__ out) {
   int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (c < nc) out[c] = cell_mat(P, E[c], nu[c], phi0[c], sw[c], p[c]);
+  if (c < nc) out[c] = cell_mat(P, E[c], nu[c], phi0[c], sw[c], p[c], ev ? ev[c] : 0.0);
 }
 
 // A_uu block (I, J): sum over the elements shared by nodes I and J (ascending
@@ -641,11 +650,124 @@ void ps_gen_default(ps_gen_params* gp, int32_t config) {
   gp->E0 = 1e10; gp->nu0 = 0.25; gp->kappa0 = 100.0 * kMD; gp->phi0 = 0.2; gp->sw0 = 0.5;
 }
 
+// Phys of the generator's parameters
+static Phys phys_of(const ps_gen_params* gp) {
+  Phys P;
+  P.dt = gp->dt; P.b = gp->biot; P.c_w = gp->c_w; P.c_nw = gp->c_nw; P.c_r = gp->c_r; P.mu_w = gp->mu_w;
+  P.mu_nw = gp->mu_nw; P.rho_w0 = gp->rho_w0; P.rho_nw0 = gp->rho_nw0; P.rho_s0 = gp->rho_s0; P.s_wr = gp->s_wr;
+  P.s_nwr = gp->s_nwr; P.grav = gp->grav; P.p_ref = gp->p_ref; P.corey = gp->corey; P.h = gp->h; P.flags = gp->flags;
+  P.fs_modulus = gp->fs_modulus;
+  return P;
+}
+
+// block patterns of the four Jacobian blocks and the Dirichlet flags (base nodes)
+static ps_status alloc_patterns(ps_system_impl* S, cudaStream_t st) {
+  Arena& ar = S->ar;
+  ps_system& o = S->pub;
+  Grid3 g{o.grid.nx, o.grid.ny, o.grid.nz};
+  const int64_t nn = o.n_nodes, nc = o.n_cells;
+  ps_bsr* blocks[4] = {&o.jac.A_uu, &o.jac.A_uf, &o.jac.A_fu, &o.jac.A_ff};
+  int64_t rows[4] = {nn, nn, nc, nc}, cols[4] = {nn, nc, nn, nc};
+  int br[4] = {3, 3, 2, 2}, bc[4] = {3, 2, 3, 2};
+  int32_t* cnt;
+  PS_TRY(ar.alloc(&cnt, nn > nc ? nn : nc));
+  for (int kind = 0; kind < 4; ++kind) {
+    ps_bsr& B = *blocks[kind];
+    int64_t* rp;
+    int32_t* ci;
+    double* v;
+    PS_TRY(ar.alloc(&rp, rows[kind] + 1));
+    PS_TICK(); k_pattern_count<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], cnt);
+    int64_t nnzb = 0;
+    PS_TRY(scan_i64(ar, cnt, rp, rows[kind], &nnzb, st));
+    PS_TRY(ar.alloc(&ci, nnzb));
+    PS_TRY(ar.alloc(&v, nnzb * br[kind] * bc[kind]));
+    PS_TICK(); k_pattern_fill<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], rp, ci);
+    B.n_brow = rows[kind]; B.n_bcol = cols[kind]; B.nnzb = nnzb; B.br = br[kind]; B.bc = bc[kind];
+    B.rowptr = rp; B.colind = ci; B.val = v;
+  }
+  ar.release(cnt);
+  double* dfs;
+  PS_TRY(ar.alloc(&dfs, 2 * nc));
+  o.jac.d_fs = dfs;
+  uint8_t* dir;
+  PS_TRY(ar.alloc(&dir, 3 * nn));
+  o.jac.dirichlet_u = dir;
+  return PS_OK;
+}
+
+// The Jacobian values of the system's patterns at the state (cell saturation s, pressure p, element-mean
+// volumetric strain ev; ev = NULL: zero strain): App. B blocks, Dirichlet elimination of the base nodes,
+// block-row scaling (alpha_u, alpha_f from these values; pressure columns in MPa), unit Dirichlet diagonal.
+static ps_status assemble_values(const ps_gen_params* gp, cudaStream_t st, ps_system_impl* S, const double* s_state,
+                                 const double* p_state, const double* ev) {
+  Arena& ar = S->ar;
+  ps_system& o = S->pub;
+  Grid3 g{o.grid.nx, o.grid.ny, o.grid.nz};
+  const int64_t nn = o.n_nodes, nc = o.n_cells;
+  const Phys P = phys_of(gp);
+  CellMat* M;
+  PS_TRY(ar.alloc(&M, nc));
+  PS_TICK(); k_material<<<grid_for(nc, 256), 256, 0, st>>>(P, nc, o.E, o.nu, o.phi0, s_state, p_state, ev, M);
+  Ref hR;
+  build_ref(gp->h, &hR);
+  Ref* dR;
+  PS_TRY(ar.alloc(&dR, 1));
+  PS_CUDA(cudaMemcpyAsync(dR, &hR, sizeof(Ref), cudaMemcpyHostToDevice, st));
+  double* vuu = const_cast<double*>(o.jac.A_uu.val);
+  double* vuf = const_cast<double*>(o.jac.A_uf.val);
+  double* vfu = const_cast<double*>(o.jac.A_fu.val);
+  double* vff = const_cast<double*>(o.jac.A_ff.val);
+  double* dfs = const_cast<double*>(o.jac.d_fs);
+  uint8_t* dir = const_cast<uint8_t*>(o.jac.dirichlet_u);
+  PS_TICK(); k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, vuu);
+  PS_TICK(); k_values_uf<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uf.rowptr, o.jac.A_uf.colind, nn, vuf);
+  PS_TICK(); k_values_fu<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, M, s_state, o.jac.A_fu.rowptr, o.jac.A_fu.colind,
+                                                         nc, vfu);
+  PS_TICK(); k_values_ff<<<grid_for(nc, 128), 128, 0, st>>>(g, P, M, s_state, p_state, o.kh, o.kv, o.jac.A_ff.rowptr,
+                                                         o.jac.A_ff.colind, nc, vff, dfs);
+  PS_CUDA(cudaGetLastError());
+  // Dirichlet elimination (base nodes)
+  PS_TICK(); k_dirichlet_flags<<<grid_for(nn, 256), 256, 0, st>>>(g, nn, dir, (gp->flags & PS_GEN_DIRICHLET) ? 1 : 0);
+  PS_TICK(); k_zero_uu<<<grid_for(nn, 128), 128, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
+  PS_TICK(); k_zero_uf<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uf.rowptr, nn, dir, vuf);
+  PS_TICK(); k_zero_fu<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, dir, vfu);
+  double* alpha;  // [alpha_u, alpha_f]
+  PS_TRY(ar.alloc(&alpha, 2));
+  double one2[2] = {1.0, 1.0};
+  PS_CUDA(cudaMemcpyAsync(alpha, one2, sizeof(one2), cudaMemcpyHostToDevice, st));
+  if (gp->flags & PS_GEN_SCALE) {
+    double *dv, *cv, *sums;
+    PS_TRY(ar.alloc(&dv, 3 * nn)); PS_TRY(ar.alloc(&cv, 3 * nn)); PS_TRY(ar.alloc(&sums, 3));
+    PS_TICK(); k_diag_uu<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu, dv, cv);
+    PS_TRY(sum_f64(ar, dv, 3 * nn, sums + 0, st));
+    PS_TRY(sum_f64(ar, cv, 3 * nn, sums + 1, st));
+    PS_TICK(); k_diag_pp<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc, vff, 1e6, dv);
+    PS_TRY(sum_f64(ar, dv, nc, sums + 2, st));
+    PS_TICK(); k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc));
+    const double pc = 1e6;
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_uu.nnzb * 9, 256), 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, 9, 0, pc, alpha, 0);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_uf.nnzb * 6, 256), 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, 2, 0x2, pc, alpha, 0);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_fu.nnzb * 6, 256), 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, 6, 0, pc, alpha, 1);
+    PS_TICK(); k_scale<<<grid_for(o.jac.A_ff.nnzb * 4, 256), 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, 2, 0x2, pc, alpha, 1);
+    PS_TICK(); k_scale<<<grid_for(2 * nc, 256), 256, 0, st>>>(dfs, 2 * nc, 1, 0x1, pc, alpha, 1);
+    PS_CUDA(cudaGetLastError());
+    ar.release(dv); ar.release(cv); ar.release(sums);
+  }
+  PS_TICK(); k_unit_diag<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
+  PS_CUDA(cudaGetLastError());
+  double ha[2];
+  PS_CUDA(cudaMemcpyAsync(ha, alpha, sizeof(ha), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  o.alpha_u = ha[0]; o.alpha_f = ha[1];
+  ar.release(M); ar.release(dR); ar.release(alpha);
+  return PS_OK;
+}
+
 static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_system_impl* S) {
   Arena& ar = S->ar;
   ar.stream = st;
   ps_system& o = S->pub;
-  Grid3 g{gp->nx, gp->ny, gp->nz};
   int64_t nn = int64_t(gp->nx + 1) * (gp->ny + 1) * (gp->nz + 1);
   int64_t nc = int64_t(gp->nx) * gp->ny * gp->nz;
   o.grid.nx = gp->nx; o.grid.ny = gp->ny; o.grid.nz = gp->nz;
@@ -689,96 +811,14 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   PS_TICK(); k_fields<<<grid_for(nc, 256), 256, 0, st>>>(fa, ghat, ksm, swsm, E, nu, kh, kv, phi, sw, p);
   PS_CUDA(cudaGetLastError());
   o.E = E; o.nu = nu; o.kh = kh; o.kv = kv; o.phi0 = phi; o.sw = sw; o.p = p;
-  // material table
-  Phys P;
-  P.dt = gp->dt; P.b = gp->biot; P.c_w = gp->c_w; P.c_nw = gp->c_nw; P.c_r = gp->c_r; P.mu_w = gp->mu_w;
-  P.mu_nw = gp->mu_nw; P.rho_w0 = gp->rho_w0; P.rho_nw0 = gp->rho_nw0; P.rho_s0 = gp->rho_s0; P.s_wr = gp->s_wr;
-  P.s_nwr = gp->s_nwr; P.grav = gp->grav; P.p_ref = gp->p_ref; P.corey = gp->corey; P.h = gp->h; P.flags = gp->flags;
-  P.fs_modulus = gp->fs_modulus;
-  CellMat* M;
-  PS_TRY(ar.alloc(&M, nc));
-  PS_TICK(); k_material<<<grid_for(nc, 256), 256, 0, st>>>(P, nc, E, nu, phi, sw, p, M);
-  Ref hR;
-  build_ref(gp->h, &hR);
-  Ref* dR;
-  PS_TRY(ar.alloc(&dR, 1));
-  PS_CUDA(cudaMemcpyAsync(dR, &hR, sizeof(Ref), cudaMemcpyHostToDevice, st));
-  // patterns
-  ps_bsr* blocks[4] = {&o.jac.A_uu, &o.jac.A_uf, &o.jac.A_fu, &o.jac.A_ff};
-  int64_t rows[4] = {nn, nn, nc, nc}, cols[4] = {nn, nc, nn, nc};
-  int br[4] = {3, 3, 2, 2}, bc[4] = {3, 2, 3, 2};
-  int32_t* cnt;
-  PS_TRY(ar.alloc(&cnt, nn > nc ? nn : nc));
-  for (int kind = 0; kind < 4; ++kind) {
-    ps_bsr& B = *blocks[kind];
-    int64_t* rp;
-    int32_t* ci;
-    double* v;
-    PS_TRY(ar.alloc(&rp, rows[kind] + 1));
-    PS_TICK(); k_pattern_count<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], cnt);
-    int64_t nnzb = 0;
-    PS_TRY(scan_i64(ar, cnt, rp, rows[kind], &nnzb, st));
-    PS_TRY(ar.alloc(&ci, nnzb));
-    PS_TRY(ar.alloc(&v, nnzb * br[kind] * bc[kind]));
-    PS_TICK(); k_pattern_fill<<<grid_for(rows[kind], 256), 256, 0, st>>>(g, kind, rows[kind], rp, ci);
-    B.n_brow = rows[kind]; B.n_bcol = cols[kind]; B.nnzb = nnzb; B.br = br[kind]; B.bc = bc[kind];
-    B.rowptr = rp; B.colind = ci; B.val = v;
-  }
-  ar.release(cnt);
-  double* vuu = const_cast<double*>(o.jac.A_uu.val);
-  double* vuf = const_cast<double*>(o.jac.A_uf.val);
-  double* vfu = const_cast<double*>(o.jac.A_fu.val);
-  double* vff = const_cast<double*>(o.jac.A_ff.val);
-  double* dfs;
-  PS_TRY(ar.alloc(&dfs, 2 * nc));
-  PS_TICK(); k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, vuu);
-  PS_TICK(); k_values_uf<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uf.rowptr, o.jac.A_uf.colind, nn, vuf);
-  PS_TICK(); k_values_fu<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, M, sw, o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, vfu);
-  PS_TICK(); k_values_ff<<<grid_for(nc, 128), 128, 0, st>>>(g, P, M, sw, p, kh, kv, o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc,
-                                                 vff, dfs);
-  PS_CUDA(cudaGetLastError());
-  o.jac.d_fs = dfs;
-  // Dirichlet elimination (base nodes)
-  uint8_t* dir;
-  PS_TRY(ar.alloc(&dir, 3 * nn));
-  PS_TICK(); k_dirichlet_flags<<<grid_for(nn, 256), 256, 0, st>>>(g, nn, dir, (gp->flags & PS_GEN_DIRICHLET) ? 1 : 0);
-  PS_TICK(); k_zero_uu<<<grid_for(nn, 128), 128, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
-  PS_TICK(); k_zero_uf<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uf.rowptr, nn, dir, vuf);
-  PS_TICK(); k_zero_fu<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, dir, vfu);
-  o.jac.dirichlet_u = dir;
-  double* alpha;  // [alpha_u, alpha_f]
-  PS_TRY(ar.alloc(&alpha, 2));
-  double one2[2] = {1.0, 1.0};
-  PS_CUDA(cudaMemcpyAsync(alpha, one2, sizeof(one2), cudaMemcpyHostToDevice, st));
-  if (gp->flags & PS_GEN_SCALE) {
-    double *dv, *cv, *sums;
-    PS_TRY(ar.alloc(&dv, 3 * nn)); PS_TRY(ar.alloc(&cv, 3 * nn)); PS_TRY(ar.alloc(&sums, 3));
-    PS_TICK(); k_diag_uu<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu, dv, cv);
-    PS_TRY(sum_f64(ar, dv, 3 * nn, sums + 0, st));
-    PS_TRY(sum_f64(ar, cv, 3 * nn, sums + 1, st));
-    PS_TICK(); k_diag_pp<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc, vff, 1e6, dv);
-    PS_TRY(sum_f64(ar, dv, nc, sums + 2, st));
-    PS_TICK(); k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc));
-    const double pc = 1e6;
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_uu.nnzb * 9, 256), 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, 9, 0, pc, alpha, 0);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_uf.nnzb * 6, 256), 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, 2, 0x2, pc, alpha, 0);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_fu.nnzb * 6, 256), 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, 6, 0, pc, alpha, 1);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_ff.nnzb * 4, 256), 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, 2, 0x2, pc, alpha, 1);
-    PS_TICK(); k_scale<<<grid_for(2 * nc, 256), 256, 0, st>>>(dfs, 2 * nc, 1, 0x1, pc, alpha, 1);
-    PS_CUDA(cudaGetLastError());
-    ar.release(dv); ar.release(cv); ar.release(sums);
-  }
-  PS_TICK(); k_unit_diag<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
+  PS_TRY(alloc_patterns(S, st));
+  PS_TRY(assemble_values(gp, st, S, sw, p, nullptr));
   double* rhs;
   PS_TRY(ar.alloc(&rhs, o.n));
-  PS_TICK(); k_rhs<<<grid_for(o.n, 256), 256, 0, st>>>(gp->seed, o.n, o.n_u, dir, rhs);
+  PS_TICK(); k_rhs<<<grid_for(o.n, 256), 256, 0, st>>>(gp->seed, o.n, o.n_u, o.jac.dirichlet_u, rhs);
   PS_CUDA(cudaGetLastError());
   o.rhs = rhs;
-  double ha[2];
-  PS_CUDA(cudaMemcpyAsync(ha, alpha, sizeof(ha), cudaMemcpyDeviceToHost, st));
-  PS_CUDA(cudaStreamSynchronize(st));
-  o.alpha_u = ha[0]; o.alpha_f = ha[1];
-  ar.release(M); ar.release(dR); ar.release(ghat); ar.release(alpha);
+  ar.release(ghat);
   if (ksm) ar.release(ksm);
   if (swsm) ar.release(swsm);
   PS_CUDA(cudaStreamSynchronize(st));
