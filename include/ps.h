@@ -377,6 +377,51 @@ void ps_gen_default(ps_gen_params* gp, int32_t config);
 ps_status ps_generate(const ps_gen_params* gp, void* stream, ps_system** out);
 void ps_system_free(ps_system* s);
 
+/* ---- the generated problem away from its linearisation point: Newton's method for one time step ----
+   The previous time level is the generator's base state (zero displacement, the saturation and pressure
+   fields sw and p) and x holds the unknowns relative to it (u; then (s, p) per cell; pressure in Pa).
+
+   ps_assemble_at: re-assembles sys's Jacobian values (App. B blocks, d_fs, Dirichlet elimination, scaling
+   with alpha_u, alpha_f recomputed, as ps_generate does at the base state) at base + dx, and writes the
+   unscaled residual of the discrete equations (§3 weak form and TPFA balances, App. B) there into r,
+   Dirichlet rows zero.  The porosity of the Jacobian's blocks uses the element-mean volumetric strain, the
+   residual the strain at each Gauss point.  dx, r: device arrays of sys->n doubles (r may be NULL); sys must
+   come from ps_generate(gp); the rhs and patterns are kept.  ps_residual_at: the residual alone. */
+ps_status ps_assemble_at(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, void* stream);
+ps_status ps_residual_at(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, void* stream);
+
+/* Newton's method (§4 and its remarks on inexact Newton): x_0 = 0; step k solves J_k y = -R_k r_k (R_k the
+   rows' scaling of J_k) by ps_solve under lin's preconditioner to the relative tolerance eta_k, keeping the
+   mechanics hierarchy of the first step (§5.4: ps_setup once, then ps_setup_flow), and sets
+   x_{k+1} = x_k + lambda C y (C: pressure unknowns from MPa to Pa), halving lambda up to max_backtracks times
+   while ||R_0 r|| > (1 - 1e-4 lambda) ||R_0 r_k||.  Converged when ||R_0 r_k|| <= rtol ||R_0 r_0||, R_0 the
+   base state's row scaling.  eta_k: eta_fixed (PS_FORCING_FIXED, the paper's runs use 1e-6) or Eisenstat
+   and Walker's choice gamma (||r_k|| / ||r_{k-1}||)^omega, eta_0 = ew_eta0, with the paper's safeguard
+   max(eta_k, gamma eta_{k-1}^omega) when gamma eta_{k-1}^omega > 0.1, capped at ew_eta_max and kept at or
+   above 0.5 rtol ||r_0|| / ||r_k|| (PS_FORCING_EW).  x: device array of n doubles (the final iterate). */
+enum { PS_FORCING_FIXED = 0, PS_FORCING_EW = 1 };
+typedef struct {
+  double rtol;              /* default 1e-8 */
+  int32_t max_newton;       /* default 12 (at most 32) */
+  int32_t forcing;          /* PS_FORCING_EW (default) or PS_FORCING_FIXED */
+  double eta_fixed;         /* default 1e-6 */
+  double ew_gamma, ew_omega, ew_eta0, ew_eta_max;  /* defaults 0.9, 2, 0.1, 0.1 (the paper's values) */
+  int32_t max_backtracks;   /* default 4 */
+} ps_newton_params;
+typedef struct {
+  int32_t newton_iters, linear_iters, backtracks, converged;
+  double rnorm[33];         /* ||R_0 r_k||, k = 0 .. newton_iters */
+  double eta[32];           /* Krylov tolerance of each step */
+  int32_t lin_iters[32];    /* FGMRES iterations of each step */
+  float ms_assemble, ms_linear, ms_total;  /* assembly (Jacobian and residuals), setup + solve, wall time */
+} ps_newton_stats;
+void ps_newton_params_default(ps_newton_params* np);
+/* eta_k of the rule above (k, ||r_k||, ||r_{k-1}||, eta_{k-1}, ||r_0||) */
+double ps_newton_eta(const ps_newton_params* np, int32_t k, double rk, double rkm1, double eta_prev, double r0);
+/* PS_ERR_NOT_CONVERGED when max_newton steps did not reach rtol (x and stats still filled) */
+ps_status ps_newton(const ps_gen_params* gp, const ps_params* lin, const ps_newton_params* np, double* x,
+                    ps_newton_stats* stats);
+
 const char* ps_strerror(ps_status s);
 
 /* Number of CUDA kernels this library has launched in the process so far

@@ -85,6 +85,22 @@ class ps_server_info(C.Structure):
                 ("max_inflight_requests", C.c_int64)]
 
 
+class ps_newton_params(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_newton", C.c_int32), ("forcing", C.c_int32), ("eta_fixed", C.c_double),
+                ("ew_gamma", C.c_double), ("ew_omega", C.c_double), ("ew_eta0", C.c_double),
+                ("ew_eta_max", C.c_double), ("max_backtracks", C.c_int32)]
+
+
+class ps_newton_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("linear_iters", C.c_int32), ("backtracks", C.c_int32),
+                ("converged", C.c_int32), ("rnorm", C.c_double * 33), ("eta", C.c_double * 32),
+                ("lin_iters", C.c_int32 * 32), ("ms_assemble", C.c_float), ("ms_linear", C.c_float),
+                ("ms_total", C.c_float)]
+
+
+PS_FORCING_FIXED, PS_FORCING_EW = 0, 1
+
+
 class ps_gen_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double),
                 ("seed", C.c_uint64), ("field_kind", C.c_int32), ("flags", C.c_uint32),
@@ -149,6 +165,17 @@ def lib():
         L.ps_generate.argtypes = [C.POINTER(ps_gen_params), C.c_void_p, C.POINTER(C.POINTER(ps_system))]
         L.ps_system_free.argtypes = [C.POINTER(ps_system)]
         L.ps_system_free.restype = None
+        L.ps_assemble_at.argtypes = [C.POINTER(ps_gen_params), C.POINTER(ps_system), C.c_void_p, C.c_void_p,
+                                     C.c_void_p]
+        L.ps_residual_at.argtypes = [C.POINTER(ps_gen_params), C.POINTER(ps_system), C.c_void_p, C.c_void_p,
+                                     C.c_void_p]
+        L.ps_newton_params_default.argtypes = [C.POINTER(ps_newton_params)]
+        L.ps_newton_params_default.restype = None
+        L.ps_newton_eta.argtypes = [C.POINTER(ps_newton_params), C.c_int32, C.c_double, C.c_double, C.c_double,
+                                    C.c_double]
+        L.ps_newton_eta.restype = C.c_double
+        L.ps_newton.argtypes = [C.POINTER(ps_gen_params), C.POINTER(ps_params), C.POINTER(ps_newton_params),
+                                C.c_void_p, C.POINTER(ps_newton_stats)]
         L.ps_residual_noalloc.argtypes = [C.POINTER(ps_jacobian), C.POINTER(ps_grid), C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
         S = C.c_void_p
@@ -230,6 +257,40 @@ def ps_generate(gp, stream=None):
 
 def ps_system_free(sys_ptr):
     lib().ps_system_free(sys_ptr)
+
+
+def ps_assemble_at(gp, sys_ptr, dx_ptr, r_ptr, stream=None):
+    """Jacobian values of the generated system (and the residual into r_ptr, may be 0) at base + dx"""
+    _check(lib().ps_assemble_at(C.byref(gp), sys_ptr, dx_ptr, r_ptr or None, stream), "ps_assemble_at")
+
+
+def ps_residual_at(gp, sys_ptr, dx_ptr, r_ptr, stream=None):
+    _check(lib().ps_residual_at(C.byref(gp), sys_ptr, dx_ptr, r_ptr, stream), "ps_residual_at")
+
+
+def ps_newton_params_default(**kw):
+    p = ps_newton_params()
+    lib().ps_newton_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def ps_newton_eta(np_, k, rk, rkm1, eta_prev, r0):
+    return lib().ps_newton_eta(C.byref(np_), k, rk, rkm1, eta_prev, r0)
+
+
+def ps_newton(gp, lin, np_, x_ptr, raise_on_error=True):
+    """Newton's method for one time step; returns (status, stats dict)"""
+    st = ps_newton_stats()
+    status = lib().ps_newton(C.byref(gp), C.byref(lin), C.byref(np_), x_ptr, C.byref(st))
+    if raise_on_error and status != PS_OK:
+        _check(status, "ps_newton")
+    k = st.newton_iters
+    return status, dict(newton_iters=k, linear_iters=st.linear_iters, backtracks=st.backtracks,
+                        converged=bool(st.converged), rnorm=list(st.rnorm[:k + 1]), eta=list(st.eta[:k]),
+                        lin_iters=list(st.lin_iters[:k]), ms_assemble=st.ms_assemble, ms_linear=st.ms_linear,
+                        ms_total=st.ms_total)
 
 
 def ps_setup(jac, grid, params):

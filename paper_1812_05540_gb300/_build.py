@@ -16,7 +16,7 @@ LIB = os.path.join(BUILD, "libps.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["util.cu", "gen.cu", "amg_setup.cu", "vcycle.cu", "flow_setup.cu", "flow_apply.cu", "krylov.cu",
-           "api.cu", "noalloc.cu", "serve.cu", "rbm_setup.cu", "rbm_apply.cu"]
+           "api.cu", "noalloc.cu", "serve.cu", "rbm_setup.cu", "rbm_apply.cu", "newton.cu"]
 NO_FMA = {"amg_setup.cu", "flow_setup.cu", "gen.cu", "rbm_setup.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

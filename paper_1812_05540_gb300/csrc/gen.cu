@@ -527,6 +527,164 @@ __global__ void k_values_ff(Grid3 g, Phys P, const CellMat* __restrict__ M, cons
   dfs[2 * c + 1] = V * P.b * P.b / Kfs * (1.0 - s) * m.rnw;
 }
 
+// ---- residual of the discrete equations at a state (§3, App. B), for Newton's method ----
+// Element-mean volumetric strain of each cell from the nodal displacements: (1/|K|) sum_a sum_d IdN_a,d u_a,d.
+__global__ void k_mean_epsv(Grid3 g, const Ref* __restrict__ R, const double* __restrict__ u, double h,
+                            double* __restrict__ ev) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nc = int64_t(g.nx) * g.ny * g.nz;
+  if (c >= nc) return;
+  const int i = int(c % g.nx), j = int((c / g.nx) % g.ny), k = int(c / (int64_t(g.nx) * g.ny));
+  double s = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    const int64_t I = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int d = 0; d < 3; ++d) s += R->IdN[a][d] * u[3 * I + d];
+  }
+  ev[c] = s / (h * h * h);
+}
+
+// Element part of the mechanics residual and the cell's flow accumulation.  Per cell: at each Gauss point the
+// displacement gradient, the effective stress lam eps_v I + G (grad u + grad u^T), the porosity and bulk
+// density at the pointwise strain, and the nodal terms int (sigma' : grad eta - b p div eta - rho g . eta),
+// summed over the Gauss points into er[c][a][d]; the accumulation change of both phases against the previous
+// time level (the base state: zero displacement, saturation s0, pressure p0) into rf[2 c], rf[2 c + 1].
+__global__ void k_res_elem(Grid3 g, Phys P, const Ref* __restrict__ R, const double* __restrict__ E,
+                           const double* __restrict__ nu, const double* __restrict__ phi0,
+                           const double* __restrict__ u, const double* __restrict__ s,
+                           const double* __restrict__ p, const double* __restrict__ s0,
+                           const double* __restrict__ p0, double* __restrict__ er, double* __restrict__ rf) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nc = int64_t(g.nx) * g.ny * g.nz;
+  if (c >= nc) return;
+  const int i = int(c % g.nx), j = int((c / g.nx) % g.ny), k = int(c / (int64_t(g.nx) * g.ny));
+  int64_t nodes[8];
+  for (int a = 0; a < 8; ++a) nodes[a] = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+  const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
+  const CellMat m0 = cell_mat(P, E[c], nu[c], phi0[c], s[c], p[c]);
+  const double sc = s[c], pc = p[c], b = P.b;
+  double acc[8][3];
+  for (int a = 0; a < 8; ++a)
+    for (int d = 0; d < 3; ++d) acc[a][d] = 0.0;
+  double int_ev = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    double gu[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 8; ++a)
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) gu[d][e] += u[3 * nodes[a] + d] * R->gdN[q][a][e];
+    const double ev = gu[0][0] + gu[1][1] + gu[2][2];
+    int_ev += R->gw * ev;
+    double sig[3][3];
+    for (int d = 0; d < 3; ++d)
+      for (int e = 0; e < 3; ++e) sig[d][e] = m0.lam * ev * (d == e) + m0.G * (gu[d][e] + gu[e][d]);
+    const double phi = phi0[c] + b * ev + m0.dphidp * (pc - P.p_ref);
+    const double rho = (1.0 - phi) * m0.rs + phi * (sc * m0.rw + (1.0 - sc) * m0.rnw);
+    for (int a = 0; a < 8; ++a)
+      for (int d = 0; d < 3; ++d) {
+        double v = 0.0;
+        for (int e = 0; e < 3; ++e) v += sig[d][e] * R->gdN[q][a][e];
+        v -= R->gdN[q][a][d] * b * pc;
+        const double gd = d == 2 ? -grav : 0.0;
+        v -= R->gN[q][a] * rho * gd;
+        acc[a][d] += R->gw * v;
+      }
+  }
+  for (int a = 0; a < 8; ++a)
+    for (int d = 0; d < 3; ++d) er[(c * 8 + a) * 3 + d] = acc[a][d];
+  double r0 = 0.0, r1 = 0.0;
+  if (P.flags & PS_GEN_ACCUM) {
+    const double V = P.h * P.h * P.h;
+    const double phiV = V * (phi0[c] + m0.dphidp * (pc - P.p_ref)) + b * int_ev;
+    const CellMat mp = cell_mat(P, E[c], nu[c], phi0[c], s0[c], p0[c]);
+    const double phiVp = V * (phi0[c] + mp.dphidp * (p0[c] - P.p_ref));
+    r0 = phiV * m0.rw * sc - phiVp * mp.rw * s0[c];
+    r1 = phiV * m0.rnw * (1.0 - sc) - phiVp * mp.rnw * (1.0 - s0[c]);
+  }
+  rf[2 * c] = r0;
+  rf[2 * c + 1] = r1;
+}
+
+// mass flux of one phase through the face K -> L (Eq. (8), Eq. (12)): face density, upwind mobility
+__device__ inline double face_value(const Phys& P, double Ups, double dz, int ph, double sK, double pK, double sL,
+                                    double pL) {
+  const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
+  const double r0 = ph == 0 ? P.rho_w0 : P.rho_nw0;
+  const double c = ph == 0 ? P.c_w : P.c_nw;
+  const double mu = ph == 0 ? P.mu_w : P.mu_nw;
+  const double rK = r0 * (1.0 + c * (pK - P.p_ref)), rL = r0 * (1.0 + c * (pL - P.p_ref));
+  const double aK = ph == 0 ? sK : 1.0 - sK, aL = ph == 0 ? sL : 1.0 - sL;
+  double vr;
+  if (aK > 0.0 && aL > 0.0) vr = 0.5 * (rK + rL);
+  else if (aK > 0.0) vr = rK;
+  else if (aL > 0.0) vr = rL;
+  else vr = 0.0;
+  const double Phi = Ups * ((pL - pK) + vr * grav * dz);
+  const bool upL = Phi > 0.0;
+  const double sU = upL ? sL : sK, pU = upL ? pL : pK;
+  double krw, krnw, dkrw, dkrnw;
+  corey(P, sU, &krw, &krnw, &dkrw, &dkrnw);
+  const double kr = ph == 0 ? krw : krnw;
+  const double rU = r0 * (1.0 + c * (pU - P.p_ref));
+  return rU * (kr / mu) * Phi;
+}
+
+// Residual rows: mechanics rows gather the element terms of the node's elements (ascending element id);
+// flow rows add the face fluxes to the accumulation in face order (below in z, y, x, then above in x, y, z),
+// -dt F on the lower cell and +dt F on the upper one.  Dirichlet rows are zero.
+__global__ void k_res_nodes(Grid3 g, const double* __restrict__ er, const uint8_t* __restrict__ dir,
+                            double* __restrict__ r) {
+  const int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nn = int64_t(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  if (I >= nn) return;
+  const int ix = int(I % (g.nx + 1)), iy = int((I / (g.nx + 1)) % (g.ny + 1)), iz = int(I / (int64_t(g.nx + 1) * (g.ny + 1)));
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int ez = max(iz - 1, 0); ez <= min(iz, g.nz - 1); ++ez)
+    for (int ey = max(iy - 1, 0); ey <= min(iy, g.ny - 1); ++ey)
+      for (int ex = max(ix - 1, 0); ex <= min(ix, g.nx - 1); ++ex) {
+        const int64_t c = g.cell(ex, ey, ez);
+        const int a = (ix - ex) | ((iy - ey) << 1) | ((iz - ez) << 2);
+        for (int d = 0; d < 3; ++d) v[d] += er[(c * 8 + a) * 3 + d];
+      }
+  for (int d = 0; d < 3; ++d) r[3 * I + d] = dir[3 * I + d] ? 0.0 : v[d];
+}
+
+__global__ void k_res_cells(Grid3 g, Phys P, const double* __restrict__ kh, const double* __restrict__ kv,
+                            const double* __restrict__ s, const double* __restrict__ p, const double* __restrict__ rf,
+                            double* __restrict__ r) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nc = int64_t(g.nx) * g.ny * g.nz;
+  if (c >= nc) return;
+  const int i = int(c % g.nx), j = int((c / g.nx) % g.ny), k = int(c / (int64_t(g.nx) * g.ny));
+  const int64_t nxy = int64_t(g.nx) * g.ny;
+  double v[2] = {rf[2 * c], rf[2 * c + 1]};
+  if (P.flags & PS_GEN_FLUX) {
+    for (int dir = 2; dir >= 0; --dir) {  // c is the upper cell L
+      if ((dir == 0 && i == 0) || (dir == 1 && j == 0) || (dir == 2 && k == 0)) continue;
+      const int64_t K = c - (dir == 0 ? 1 : dir == 1 ? g.nx : nxy);
+      const double Ups = dir == 2 ? face_ups(P.h, kv[K], kv[c]) : face_ups(P.h, kh[K], kh[c]);
+      const double dz = dir == 2 ? P.h : 0.0;
+      for (int ph = 0; ph < 2; ++ph) v[ph] += P.dt * face_value(P, Ups, dz, ph, s[K], p[K], s[c], p[c]);
+    }
+    for (int dir = 0; dir < 3; ++dir) {  // c is the lower cell K
+      if ((dir == 0 && i + 1 >= g.nx) || (dir == 1 && j + 1 >= g.ny) || (dir == 2 && k + 1 >= g.nz)) continue;
+      const int64_t L = c + (dir == 0 ? 1 : dir == 1 ? g.nx : nxy);
+      const double Ups = dir == 2 ? face_ups(P.h, kv[c], kv[L]) : face_ups(P.h, kh[c], kh[L]);
+      const double dz = dir == 2 ? P.h : 0.0;
+      for (int ph = 0; ph < 2; ++ph) v[ph] += -P.dt * face_value(P, Ups, dz, ph, s[c], p[c], s[L], p[L]);
+    }
+  }
+  r[2 * c] = v[0];
+  r[2 * c + 1] = v[1];
+}
+
+// state arrays of base + dx: s = s0 + dx_s, p = p0 + dx_p per cell
+__global__ void k_state(int64_t nc, int64_t nu, const double* __restrict__ dx, const double* __restrict__ s0,
+                        const double* __restrict__ p0, double* __restrict__ s, double* __restrict__ p) {
+  const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  s[c] = s0[c] + dx[nu + 2 * c];
+  p[c] = p0[c] + dx[nu + 2 * c + 1];
+}
+
 // ---- Dirichlet elimination and scaling ----
 __global__ void k_dirichlet_flags(Grid3 g, int64_t nn, uint8_t* __restrict__ dir, int on) {
   int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -840,6 +998,55 @@ ps_status ps_generate(const ps_gen_params* gp, void* stream, ps_system** out) {
   }
   *out = &S->pub;
   return PS_OK;
+}
+
+// residual (and with jac != 0 the Jacobian values) of a generated system at the state base + dx
+static ps_status state_impl(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, bool jac,
+                            cudaStream_t st) {
+  if (!gp || !sys || !dx || (!r && !jac)) return PS_ERR_INVALID;
+  ps_system_impl* S = reinterpret_cast<ps_system_impl*>(sys);
+  ps_system& o = S->pub;
+  if (o.grid.nx != gp->nx || o.grid.ny != gp->ny || o.grid.nz != gp->nz || o.grid.hx != gp->h) {
+    set_reason("ps_assemble_at: the system was not generated with these parameters");
+    return PS_ERR_INVALID;
+  }
+  Arena& ar = S->ar;
+  ar.stream = st;
+  const Grid3 g{o.grid.nx, o.grid.ny, o.grid.nz};
+  const int64_t nc = o.n_cells, nn = o.n_nodes;
+  double *s_st, *p_st, *ev;
+  PS_TRY(ar.alloc(&s_st, nc)); PS_TRY(ar.alloc(&p_st, nc)); PS_TRY(ar.alloc(&ev, nc));
+  Ref hR;
+  build_ref(gp->h, &hR);
+  Ref* dR;
+  PS_TRY(ar.alloc(&dR, 1));
+  PS_CUDA(cudaMemcpyAsync(dR, &hR, sizeof(Ref), cudaMemcpyHostToDevice, st));
+  PS_TICK(); k_state<<<grid_for(nc, 256), 256, 0, st>>>(nc, 3 * nn, dx, o.sw, o.p, s_st, p_st);
+  PS_TICK(); k_mean_epsv<<<grid_for(nc, 256), 256, 0, st>>>(g, dR, dx, gp->h, ev);
+  PS_CUDA(cudaGetLastError());
+  if (jac) PS_TRY(assemble_values(gp, st, S, s_st, p_st, ev));
+  if (r) {
+    const Phys P = phys_of(gp);
+    double *er, *rf;
+    PS_TRY(ar.alloc(&er, nc * 24)); PS_TRY(ar.alloc(&rf, 2 * nc));
+    PS_TICK(); k_res_elem<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, o.E, o.nu, o.phi0, dx, s_st, p_st, o.sw, o.p, er,
+                                                          rf);
+    PS_TICK(); k_res_nodes<<<grid_for(nn, 256), 256, 0, st>>>(g, er, o.jac.dirichlet_u, r);
+    PS_TICK(); k_res_cells<<<grid_for(nc, 256), 256, 0, st>>>(g, P, o.kh, o.kv, s_st, p_st, rf, r + 3 * nn);
+    PS_CUDA(cudaGetLastError());
+    ar.release(er); ar.release(rf);
+  }
+  ar.release(s_st); ar.release(p_st); ar.release(ev); ar.release(dR);
+  PS_CUDA(cudaStreamSynchronize(st));
+  return PS_OK;
+}
+
+ps_status ps_assemble_at(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, void* stream) {
+  return state_impl(gp, sys, dx, r, true, (cudaStream_t)stream);
+}
+
+ps_status ps_residual_at(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, void* stream) {
+  return state_impl(gp, sys, dx, r, false, (cudaStream_t)stream);
 }
 
 void ps_system_free(ps_system* s) {

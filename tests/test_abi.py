@@ -28,7 +28,8 @@ def test_binding_names_match_abi():
     import paper_1812_05540_gb300 as ps
     for n in ("ps_setup", "ps_setup_flow", "ps_solve", "ps_free", "ps_generate", "ps_system_free", "ps_spmv",
               "ps_apply_prec", "ps_strerror", "ps_params_default", "ps_gen_default", "ps_server_create",
-              "ps_server_submit", "ps_server_wait", "ps_server_destroy", "ps_setup_bytes_estimate"):
+              "ps_server_submit", "ps_server_wait", "ps_server_destroy", "ps_setup_bytes_estimate",
+              "ps_assemble_at", "ps_residual_at", "ps_newton", "ps_newton_params_default"):
         assert callable(getattr(ps, n))
 
 
@@ -41,9 +42,10 @@ def test_struct_layouts_match_header():
 #include <stdio.h>
 #include "ps.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ps_grid), sizeof(ps_bsr), sizeof(ps_jacobian),
-         sizeof(ps_params), sizeof(ps_stats), sizeof(ps_gen_params), sizeof(ps_system),
-         sizeof(ps_server_params), sizeof(ps_request_info), sizeof(ps_server_info));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ps_grid), sizeof(ps_bsr),
+         sizeof(ps_jacobian), sizeof(ps_params), sizeof(ps_stats), sizeof(ps_gen_params), sizeof(ps_system),
+         sizeof(ps_server_params), sizeof(ps_request_info), sizeof(ps_server_info), sizeof(ps_newton_params),
+         sizeof(ps_newton_stats));
   return 0;
 }
 '''
@@ -55,5 +57,5 @@ int main(void) {
         sizes = [int(v) for v in subprocess.check_output([exe]).split()]
     mine = [ctypes.sizeof(t) for t in (ps.ps_grid, ps.ps_bsr, ps.ps_jacobian, ps.ps_params, ps.ps_stats,
                                        ps.ps_gen_params, ps.ps_system, ps.ps_server_params, ps.ps_request_info,
-                                       ps.ps_server_info)]
+                                       ps.ps_server_info, ps.ps_newton_params, ps.ps_newton_stats)]
     assert sizes == mine

@@ -96,3 +96,15 @@ def test_forcing_term_hand_worked_values():
     assert oracle.ew_eta(np_, 3, 1e-7, 1e-2, 1e-4, 10.0) == pytest.approx(0.5 * 1e-8 * 10.0 / 1e-7)
     fixed = oracle.default_newton_params(forcing=oracle.FORCING_FIXED, eta_fixed=1e-6)
     assert oracle.ew_eta(fixed, 2, 1.0, 2.0, 0.1, 10.0) == 1e-6
+
+
+def test_library_forcing_term_equals_the_oracles():
+    # the library's host-side forcing rule (ps_newton_eta) against the oracle's on a spread of inputs
+    import itertools
+    import paper_1812_05540_gb300 as ps
+    for forcing in (oracle.FORCING_FIXED, oracle.FORCING_EW):
+        o = oracle.default_newton_params(forcing=forcing)
+        p = ps.ps_newton_params_default(forcing=forcing)
+        for k, rk, rkm1, eta_prev, r0 in itertools.product((0, 1, 4), (1e-7, 0.3, 2.0), (1e-3, 1.0, 5.0),
+                                                             (1e-4, 0.1, 0.6), (10.0,)):
+            assert ps.ps_newton_eta(p, k, rk, rkm1, eta_prev, r0) == oracle.ew_eta(o, k, rk, rkm1, eta_prev, r0)
