@@ -171,6 +171,7 @@ __global__ void k_fields(FieldArgs fa, const double* __restrict__ ghat, const do
 // App. B density derivatives) ----
 struct Phys {
   double dt, b, c_w, c_nw, c_r, mu_w, mu_nw, rho_w0, rho_nw0, rho_s0, s_wr, s_nwr, grav, p_ref, corey, h;
+  double inv_den, inv_mu_w, inv_mu_nw;  // 1 / (1 - s_wr - s_nwr), 1 / mu_w, 1 / mu_nw
   uint32_t flags;
   int fs_modulus;  // 0: K_dr in the fixed-stress diagonal, 1: uniaxial modulus K_dr + 4G/3
 };
@@ -202,17 +203,18 @@ __device__ inline CellMat cell_mat(const Phys& P, double E, double nu, double ph
 
 // Corey relative permeabilities of §6 (exponent P.corey) and their s-derivatives
 __device__ inline void corey(const Phys& P, double s, double* krw, double* krnw, double* dkrw, double* dkrnw) {
-  double den = 1.0 - P.s_wr - P.s_nwr;
+  // the scaled saturation is divided as written: whether it lies inside (0, 1) decides the derivatives
+  const double den = 1.0 - P.s_wr - P.s_nwr, rden = P.inv_den;
   double sh = (s - P.s_wr) / den;
   bool in = sh > 0.0 && sh < 1.0;
   sh = fmin(1.0, fmax(0.0, sh));
   double n = P.corey;
   if (n == 2.0) {
     *krw = sh * sh; *krnw = (1.0 - sh) * (1.0 - sh);
-    *dkrw = in ? 2.0 * sh / den : 0.0; *dkrnw = in ? -2.0 * (1.0 - sh) / den : 0.0;
+    *dkrw = in ? 2.0 * sh * rden : 0.0; *dkrnw = in ? -2.0 * (1.0 - sh) * rden : 0.0;
   } else if (n == 1.0) {
     *krw = sh; *krnw = 1.0 - sh;
-    *dkrw = in ? 1.0 / den : 0.0; *dkrnw = in ? -1.0 / den : 0.0;
+    *dkrw = in ? rden : 0.0; *dkrnw = in ? -rden : 0.0;
   } else {
     *krw = pow(sh, n); *krnw = pow(1.0 - sh, n);
     *dkrw = in ? n * pow(sh, n - 1.0) / den : 0.0; *dkrnw = in ? -n * pow(1.0 - sh, n - 1.0) / den : 0.0;
@@ -221,6 +223,8 @@ __device__ inline void corey(const Phys& P, double s, double* krw, double* krnw,
 
 struct Ref {  // Q1 integrals on the cube of edge h, and the shape functions at the 8 Gauss points
   double G[8][8][3][3], IN[8], IdN[8][3], INdN[8][8][3];
+  double H[8][8][3][3];  // the shear part of the element block: H_ab[d][e] = G_ab[e][d] + delta_de tr G_ab
+  double B1[2][2];       // 1-D linear shape functions at the two Gauss abscissae: B1[q][a]
   double gN[8][8], gdN[8][8][3], gw;  // [Gauss point][node]
 };
 
@@ -245,6 +249,10 @@ void build_ref(double h, Ref* R) {
       dN[a][2] = f[0] * f[1] * df[2];
     }
     R->gw = w;
+    for (int qq = 0; qq < 2; ++qq) {
+      R->B1[qq][0] = 1.0 - q[qq];
+      R->B1[qq][1] = q[qq];
+    }
     for (int a = 0; a < 8; ++a) {
       R->gN[g][a] = N[a];
       for (int d = 0; d < 3; ++d) R->gdN[g][a][d] = dN[a][d];
@@ -259,6 +267,12 @@ void build_ref(double h, Ref* R) {
         }
     }
   }
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      const double tr = R->G[a][b][0][0] + R->G[a][b][1][1] + R->G[a][b][2][2];
+      for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) R->H[a][b][d][e] = R->G[a][b][e][d] + (d == e ? tr : 0.0);
+    }
 }
 
 struct Grid3 {
@@ -334,39 +348,44 @@ __global__ void k_material(Phys P, int64_t nc, const double* __restrict__ E, con
   if (c < nc) out[c] = cell_mat(P, E[c], nu[c], phi0[c], sw[c], p[c], ev ? ev[c] : 0.0);
 }
 
-// A_uu block (I, J): sum over the elements shared by nodes I and J (ascending
-// element id) of the App. B element block: elasticity + gravity term.
+// A_uu block (I, J): sum over the elements shared by nodes I and J (ascending element id) of the App. B
+// element block, lam G_ab + mu H_ab (elasticity) plus the gravity term drho/deps_v g IN_a dN_b in the z row.
+// The neighbours J are walked in the pattern's order (27-point box, ascending id), so no column is decoded.
 __global__ void k_values_uu(Grid3 g, Phys P, const Ref* __restrict__ R, const CellMat* __restrict__ M,
-                            const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t nn,
-                            double* __restrict__ val) {
-  int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+                            const int64_t* __restrict__ rp, int64_t nn, double* __restrict__ val) {
+  const int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (I >= nn) return;
-  int ix = int(I % (g.nx + 1)), iy = int((I / (g.nx + 1)) % (g.ny + 1)), iz = int(I / (int64_t(g.nx + 1) * (g.ny + 1)));
-  double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
-  for (int64_t q = rp[I]; q < rp[I + 1]; ++q) {
-    int64_t J = ci[q];
-    int jx = int(J % (g.nx + 1)), jy = int((J / (g.nx + 1)) % (g.ny + 1)), jz = int(J / (int64_t(g.nx + 1) * (g.ny + 1)));
-    double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int ex0 = max(max(ix, jx) - 1, 0), ex1 = min(min(ix, jx), g.nx - 1);
-    int ey0 = max(max(iy, jy) - 1, 0), ey1 = min(min(iy, jy), g.ny - 1);
-    int ez0 = max(max(iz, jz) - 1, 0), ez1 = min(min(iz, jz), g.nz - 1);
-    for (int ez = ez0; ez <= ez1; ++ez)
-      for (int ey = ey0; ey <= ey1; ++ey)
-        for (int ex = ex0; ex <= ex1; ++ex) {
-          const CellMat& m = M[g.cell(ex, ey, ez)];
-          int a = (ix - ex) | ((iy - ey) << 1) | ((iz - ez) << 2);
-          int b = (jx - ex) | ((jy - ey) << 1) | ((jz - ez) << 2);
-          double trG = R->G[a][b][0][0] + R->G[a][b][1][1] + R->G[a][b][2][2];
-          for (int d = 0; d < 3; ++d)
-            for (int e = 0; e < 3; ++e) {
-              double kel = m.lam * R->G[a][b][d][e] + m.G * R->G[a][b][e][d] + (d == e ? m.G * trG : 0.0);
-              double gd = d == 2 ? -grav : 0.0;
-              double kg = -m.drho_deps * gd * R->INdN[a][b][e];
-              blk[d * 3 + e] += kel + kg;
+  const int ix = int(I % (g.nx + 1)), iy = int((I / (g.nx + 1)) % (g.ny + 1)),
+            iz = int(I / (int64_t(g.nx + 1) * (g.ny + 1)));
+  const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
+  int64_t q = rp[I];
+  for (int jz = max(iz - 1, 0); jz <= min(iz + 1, g.nz); ++jz)
+    for (int jy = max(iy - 1, 0); jy <= min(iy + 1, g.ny); ++jy)
+      for (int jx = max(ix - 1, 0); jx <= min(ix + 1, g.nx); ++jx, ++q) {
+        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        const int ex0 = max(max(ix, jx) - 1, 0), ex1 = min(min(ix, jx), g.nx - 1);
+        const int ey0 = max(max(iy, jy) - 1, 0), ey1 = min(min(iy, jy), g.ny - 1);
+        const int ez0 = max(max(iz, jz) - 1, 0), ez1 = min(min(iz, jz), g.nz - 1);
+        for (int ez = ez0; ez <= ez1; ++ez)
+          for (int ey = ey0; ey <= ey1; ++ey)
+            for (int ex = ex0; ex <= ex1; ++ex) {
+              const CellMat& m = M[g.cell(ex, ey, ez)];
+              const int a = (ix - ex) | ((iy - ey) << 1) | ((iz - ez) << 2);
+              const int b = (jx - ex) | ((jy - ey) << 1) | ((jz - ez) << 2);
+              const double lam = m.lam, mu = m.G;
+              const double* Gab = &R->G[a][b][0][0];
+              const double* Hab = &R->H[a][b][0][0];
+#pragma unroll
+              for (int t = 0; t < 9; ++t) blk[t] = fma(lam, Gab[t], fma(mu, Hab[t], blk[t]));
+              if (grav != 0.0) {
+                const double cg = m.drho_deps * grav;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) blk[6 + e] = fma(cg, R->INdN[a][b][e], blk[6 + e]);
+              }
             }
-        }
-    for (int t = 0; t < 9; ++t) val[q * 9 + t] = blk[t];
-  }
+#pragma unroll
+        for (int t = 0; t < 9; ++t) val[q * 9 + t] = blk[t];
+      }
 }
 
 // A_uf (node I, cell c) = [A_us A_up] and A_fu (cell c, node J) = [A_su; A_pu]
@@ -425,7 +444,7 @@ __device__ inline FaceD face_deriv(const Phys& P, double Ups, double dz, int ph,
   double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
   double r0 = ph == 0 ? P.rho_w0 : P.rho_nw0;
   double c = ph == 0 ? P.c_w : P.c_nw;
-  double mu = ph == 0 ? P.mu_w : P.mu_nw;
+  double rmu = ph == 0 ? P.inv_mu_w : P.inv_mu_nw;
   double rK = r0 * (1.0 + c * (pK - P.p_ref)), rL = r0 * (1.0 + c * (pL - P.p_ref));
   double aK = ph == 0 ? sK : 1.0 - sK, aL = ph == 0 ? sL : 1.0 - sL;
   double vr, dvK, dvL;
@@ -440,8 +459,8 @@ __device__ inline FaceD face_deriv(const Phys& P, double Ups, double dz, int ph,
   corey(P, sU, &krw, &krnw, &dkrw, &dkrnw);
   double kr = ph == 0 ? krw : krnw, dkr = ph == 0 ? dkrw : dkrnw;
   double rU = r0 * (1.0 + c * (pU - P.p_ref));
-  double lamU = kr / mu;
-  double dsU = rU / mu * Phi * dkr;
+  double lamU = kr * rmu;
+  double dsU = rU * rmu * Phi * dkr;
   FaceD f;
   bool sat = (P.flags & PS_GEN_FLUX_SAT) != 0;
   f.dsK = sat ? (upL ? 0.0 : dsU) : 0.0;
@@ -452,8 +471,9 @@ __device__ inline FaceD face_deriv(const Phys& P, double Ups, double dz, int ph,
   return f;
 }
 
+// harmonic mean of the two half transmissibilities |f| kappa / (h/2) = 2 h kappa (App. A)
 __device__ inline double face_ups(double h, double kK, double kL) {
-  double UK = h * h * kK / (0.5 * h), UL = h * h * kL / (0.5 * h);
+  const double UK = 2.0 * h * kK, UL = 2.0 * h * kL;
   return UK * UL / (UK + UL);
 }
 
@@ -543,57 +563,200 @@ __global__ void k_mean_epsv(Grid3 g, const Ref* __restrict__ R, const double* __
   ev[c] = s / (h * h * h);
 }
 
-// Element part of the mechanics residual and the cell's flow accumulation.  Per cell: at each Gauss point the
-// displacement gradient, the effective stress lam eps_v I + G (grad u + grad u^T), the porosity and bulk
-// density at the pointwise strain, and the nodal terms int (sigma' : grad eta - b p div eta - rho g . eta),
-// summed over the Gauss points into er[c][a][d]; the accumulation change of both phases against the previous
-// time level (the base state: zero displacement, saturation s0, pressure p0) into rf[2 c], rf[2 c + 1].
-__global__ void k_res_elem(Grid3 g, Phys P, const Ref* __restrict__ R, const double* __restrict__ E,
-                           const double* __restrict__ nu, const double* __restrict__ phi0,
-                           const double* __restrict__ u, const double* __restrict__ s,
-                           const double* __restrict__ p, const double* __restrict__ s0,
-                           const double* __restrict__ p0, double* __restrict__ er, double* __restrict__ rf) {
+// Two-axis tensor contractions of the trilinear element (node a = ax | ay << 1 | az << 2, Gauss point
+// q = qx | qy << 1 | qz << 2).  interp2: values at the 2 x 2 Gauss abscissae of a bilinear field given at the
+// 2 x 2 nodes, out[p][r] = sum_ij B[p][i] B[r][j] in[i][j]; project2 is its transpose,
+// out[i][j] = sum_pr B[p][i] B[r][j] in[p][r].
+__device__ __forceinline__ void interp2(const double (&B)[2][2], const double (&in)[2][2], double (&out)[2][2]) {
+  double t[2][2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) t[p][j] = fma(B[p][0], in[0][j], B[p][1] * in[1][j]);
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) out[p][r] = fma(B[r][0], t[p][0], B[r][1] * t[p][1]);
+}
+__device__ __forceinline__ void project2(const double (&B)[2][2], const double (&in)[2][2], double (&out)[2][2]) {
+  double t[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) t[i][r] = fma(B[0][i], in[0][r], B[1][i] * in[1][r]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) out[i][j] = fma(B[0][j], t[i][0], B[1][j] * t[i][1]);
+}
+
+// Element part of the mechanics residual and the cell's flow accumulation (App. B, Eq. (5) weak form, 2 x 2 x 2
+// Gauss).  Per cell: at each Gauss point the displacement gradient, the effective stress
+// lam eps_v I + G (grad u + grad u^T) and the bulk density at the pointwise strain; the nodal terms
+// int (sigma' : grad eta - b p div eta - rho g . eta) go to er[c][a][d].  The Q1 element is a tensor product,
+// so the gradients at the Gauss points and the projections onto the test functions are taken axis by axis
+// (sum factorisation): the x-derivative of a trilinear field is bilinear in (y, z) and the same at both x
+// abscissae, and so on.  The pressure term is b p times the integral of grad N_a; the density is affine in
+// the pointwise strain, rho = rho(phi_bar) + b (rho_f - rho_s) eps_v.  The accumulation change of both
+// phases against the previous time level (the base state: zero displacement, saturation s0, pressure p0)
+// goes to rf[2 c], rf[2 c + 1].
+__global__ void __launch_bounds__(128) k_res_elem(Grid3 g, Phys P, const Ref* __restrict__ R,
+                                                  const double* __restrict__ E, const double* __restrict__ nu,
+                                                  const double* __restrict__ phi0, const double* __restrict__ u,
+                                                  const double* __restrict__ s, const double* __restrict__ p,
+                                                  const double* __restrict__ s0, const double* __restrict__ p0,
+                                                  double* __restrict__ er, double* __restrict__ rf) {
   const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nc = int64_t(g.nx) * g.ny * g.nz;
   if (c >= nc) return;
   const int i = int(c % g.nx), j = int((c / g.nx) % g.ny), k = int(c / (int64_t(g.nx) * g.ny));
-  int64_t nodes[8];
-  for (int a = 0; a < 8; ++a) nodes[a] = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+  double B[2][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) B[q][a] = R->B1[q][a];
+  const double rh = 1.0 / P.h, w = R->gw;
+  // gradients at the Gauss points: gr[d][e][.][.] = d u_d / d x_e over the two abscissae of the other axes
+  // (e = x: [qy][qz], e = y: [qx][qz], e = z: [qx][qy])
+  double gr[3][3][2][2];
+  {
+    double un[3][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t I = g.node(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) un[d][a] = u[3 * I + d];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double dl[2][2];
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) dl[m][n] = (un[d][1 | (m << 1) | (n << 2)] - un[d][0 | (m << 1) | (n << 2)]) * rh;
+      interp2(B, dl, gr[d][0]);
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) dl[m][n] = (un[d][m | (1 << 1) | (n << 2)] - un[d][m | (0 << 1) | (n << 2)]) * rh;
+      interp2(B, dl, gr[d][1]);
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) dl[m][n] = (un[d][m | (n << 1) | (1 << 2)] - un[d][m | (n << 1) | (0 << 2)]) * rh;
+      interp2(B, dl, gr[d][2]);
+    }
+  }
   const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
   const CellMat m0 = cell_mat(P, E[c], nu[c], phi0[c], s[c], p[c]);
   const double sc = s[c], pc = p[c], b = P.b;
-  double acc[8][3];
-  for (int a = 0; a < 8; ++a)
-    for (int d = 0; d < 3; ++d) acc[a][d] = 0.0;
-  double int_ev = 0.0;
-  for (int q = 0; q < 8; ++q) {
-    double gu[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int a = 0; a < 8; ++a)
-      for (int d = 0; d < 3; ++d)
-        for (int e = 0; e < 3; ++e) gu[d][e] += u[3 * nodes[a] + d] * R->gdN[q][a][e];
-    const double ev = gu[0][0] + gu[1][1] + gu[2][2];
-    int_ev += R->gw * ev;
-    double sig[3][3];
-    for (int d = 0; d < 3; ++d)
-      for (int e = 0; e < 3; ++e) sig[d][e] = m0.lam * ev * (d == e) + m0.G * (gu[d][e] + gu[e][d]);
-    const double phi = phi0[c] + b * ev + m0.dphidp * (pc - P.p_ref);
-    const double rho = (1.0 - phi) * m0.rs + phi * (sc * m0.rw + (1.0 - sc) * m0.rnw);
-    for (int a = 0; a < 8; ++a)
-      for (int d = 0; d < 3; ++d) {
-        double v = 0.0;
-        for (int e = 0; e < 3; ++e) v += sig[d][e] * R->gdN[q][a][e];
-        v -= R->gdN[q][a][d] * b * pc;
-        const double gd = d == 2 ? -grav : 0.0;
-        v -= R->gN[q][a] * rho * gd;
-        acc[a][d] += R->gw * v;
+  const double lam = m0.lam, mu = m0.G;
+  // stresses summed over the abscissa of their derivative's axis: S[d][e][.][.] indexed like gr[d][e]
+  double S[3][3][2][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) S[d][e][m][n] = 0.0;
+  double evq[2][2][2];  // [qx][qy][qz]
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < 2; ++qx) {
+        double G[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          G[d][0] = gr[d][0][qy][qz];
+          G[d][1] = gr[d][1][qx][qz];
+          G[d][2] = gr[d][2][qx][qy];
+        }
+        const double ev = G[0][0] + G[1][1] + G[2][2];
+        evq[qx][qy][qz] = ev;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int e = 0; e < 3; ++e) {
+            const double sig = (d == e) ? fma(lam, ev, 2.0 * mu * G[d][d]) : mu * (G[d][e] + G[e][d]);
+            if (e == 0) S[d][0][qy][qz] += sig;
+            else if (e == 1) S[d][1][qx][qz] += sig;
+            else S[d][2][qx][qy] += sig;
+          }
       }
+  // projections onto the test-function gradients: f[a][d] = w sum_e D_e(a) (B B)^T S[d][e]
+  double f[8][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double T[2][2];
+    project2(B, S[d][0], T);  // T[ay][az]
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double v = w * rh * T[(a >> 1) & 1][(a >> 2) & 1];
+      f[a][d] = (a & 1) ? v : -v;
+    }
+    project2(B, S[d][1], T);  // T[ax][az]
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double v = w * rh * T[a & 1][(a >> 2) & 1];
+      f[a][d] += ((a >> 1) & 1) ? v : -v;
+    }
+    project2(B, S[d][2], T);  // T[ax][ay]
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double v = w * rh * T[a & 1][(a >> 1) & 1];
+      f[a][d] += ((a >> 2) & 1) ? v : -v;
+    }
   }
+  // pressure: - b p int dN_a / dx_d
+#pragma unroll
   for (int a = 0; a < 8; ++a)
-    for (int d = 0; d < 3; ++d) er[(c * 8 + a) * 3 + d] = acc[a][d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f[a][d] = fma(-b * pc, R->IdN[a][d], f[a][d]);
+  // integral of the strain and, for gravity, of N_a times the strain: w sum_q N_a(q) eps_v(q), axis by axis
+  double int_ev = 0.0;
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz)
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+      for (int qx = 0; qx < 2; ++qx) int_ev += evq[qx][qy][qz];
+  int_ev *= w;
+  const double phibar = phi0[c] + m0.dphidp * (pc - P.p_ref);
+  if (grav != 0.0) {
+    const double rf_ = sc * m0.rw + (1.0 - sc) * m0.rnw;
+    const double rho0 = m0.rs + phibar * (rf_ - m0.rs), kap = b * (rf_ - m0.rs);
+    double t1[2][2][2], t2[2][2][2];  // contract qx, then qy, then qz
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+      for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz) t1[ax][qy][qz] = fma(B[0][ax], evq[0][qy][qz], B[1][ax] * evq[1][qy][qz]);
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+      for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+        for (int qz = 0; qz < 2; ++qz) t2[ax][ay][qz] = fma(B[0][ay], t1[ax][0][qz], B[1][ay] * t1[ax][1][qz]);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+      const double Ne = w * fma(B[0][az], t2[ax][ay][0], B[1][az] * t2[ax][ay][1]);
+      f[a][2] = fma(grav, fma(rho0, R->IN[a], kap * Ne), f[a][2]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) er[(c * 8 + a) * 3 + d] = f[a][d];
   double r0 = 0.0, r1 = 0.0;
   if (P.flags & PS_GEN_ACCUM) {
     const double V = P.h * P.h * P.h;
-    const double phiV = V * (phi0[c] + m0.dphidp * (pc - P.p_ref)) + b * int_ev;
+    const double phiV = V * phibar + b * int_ev;
     const CellMat mp = cell_mat(P, E[c], nu[c], phi0[c], s0[c], p0[c]);
     const double phiVp = V * (phi0[c] + mp.dphidp * (p0[c] - P.p_ref));
     r0 = phiV * m0.rw * sc - phiVp * mp.rw * s0[c];
@@ -609,7 +772,7 @@ __device__ inline double face_value(const Phys& P, double Ups, double dz, int ph
   const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
   const double r0 = ph == 0 ? P.rho_w0 : P.rho_nw0;
   const double c = ph == 0 ? P.c_w : P.c_nw;
-  const double mu = ph == 0 ? P.mu_w : P.mu_nw;
+  const double rmu = ph == 0 ? P.inv_mu_w : P.inv_mu_nw;
   const double rK = r0 * (1.0 + c * (pK - P.p_ref)), rL = r0 * (1.0 + c * (pL - P.p_ref));
   const double aK = ph == 0 ? sK : 1.0 - sK, aL = ph == 0 ? sL : 1.0 - sL;
   double vr;
@@ -624,7 +787,7 @@ __device__ inline double face_value(const Phys& P, double Ups, double dz, int ph
   corey(P, sU, &krw, &krnw, &dkrw, &dkrnw);
   const double kr = ph == 0 ? krw : krnw;
   const double rU = r0 * (1.0 + c * (pU - P.p_ref));
-  return rU * (kr / mu) * Phi;
+  return rU * (kr * rmu) * Phi;
 }
 
 // Residual rows: mechanics rows gather the element terms of the node's elements (ascending element id);
@@ -747,14 +910,21 @@ __global__ void k_diag_pp(const int64_t* __restrict__ rp, const int32_t* __restr
   dv[c] = fabs(v[q * 4 + 3] * pcol);
 }
 
-// p-columns in MPa (x 1e6), then mechanics rows / alpha_u and flow rows / alpha_f
-__global__ void k_scale(double* __restrict__ v, int64_t nvals, int bs, int pcol_mask, double pcol,
-                        const double* __restrict__ alpha, int which) {
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= nvals) return;
-  double x = v[t];
-  if ((pcol_mask >> int(t % bs)) & 1) x = x * pcol;
-  v[t] = x / alpha[which];
+// p-columns in MPa (x 1e6), then mechanics rows / alpha_u and flow rows / alpha_f: each value is multiplied
+// once by the factor of its kind, fac[f_even] at even positions and fac[f_odd] at odd ones (every block's
+// row length is even where the two differ)
+__global__ void k_scale(double* __restrict__ v, int64_t nvals, const double* __restrict__ fac, int f_even,
+                        int f_odd) {
+  const double fe = fac[f_even], fo = fac[f_odd];
+  const int64_t npair = nvals >> 1;
+  double2* __restrict__ v2 = reinterpret_cast<double2*>(v);
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < npair; t += int64_t(gridDim.x) * blockDim.x) {
+    double2 x = v2[t];
+    x.x *= fe;
+    x.y *= fo;
+    v2[t] = x;
+  }
+  if ((nvals & 1) && blockIdx.x == 0 && threadIdx.x == 0) v[nvals - 1] *= fe;
 }
 
 __global__ void k_unit_diag(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t nn,
@@ -773,10 +943,15 @@ __global__ void k_rhs(uint64_t seed, int64_t n, int64_t nu, const uint8_t* __res
   b[r] = (r < nu && dir[r]) ? 0.0 : 2.0 * u01(seed, FRHS, 0, uint64_t(r)) - 1.0;
 }
 
-__global__ void k_alpha(const double* __restrict__ sums, double* __restrict__ alpha, double nc) {
-  // sums: [sum diag_u, count_u, sum |diag_pp|]
+__global__ void k_alpha(const double* __restrict__ sums, double* __restrict__ alpha, double nc, double pcol) {
+  // sums: [sum diag_u, count_u, sum |diag_pp|]; alpha[2..5]: the scaling factors 1/alpha_u, pcol/alpha_u,
+  // 1/alpha_f, pcol/alpha_f
   alpha[0] = sums[1] > 0.0 ? sums[0] / sums[1] : 1.0;
   alpha[1] = sums[2] / nc;
+  alpha[2] = 1.0 / alpha[0];
+  alpha[3] = pcol / alpha[0];
+  alpha[4] = 1.0 / alpha[1];
+  alpha[5] = pcol / alpha[1];
 }
 
 }  // namespace
@@ -809,12 +984,24 @@ void ps_gen_default(ps_gen_params* gp, int32_t config) {
 }
 
 // Phys of the generator's parameters
+// streaming multiprocessors of the current device (grid sizes of the grid-stride kernels)
+static int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    sms = 1;
+  return sms;
+}
+
 static Phys phys_of(const ps_gen_params* gp) {
   Phys P;
   P.dt = gp->dt; P.b = gp->biot; P.c_w = gp->c_w; P.c_nw = gp->c_nw; P.c_r = gp->c_r; P.mu_w = gp->mu_w;
   P.mu_nw = gp->mu_nw; P.rho_w0 = gp->rho_w0; P.rho_nw0 = gp->rho_nw0; P.rho_s0 = gp->rho_s0; P.s_wr = gp->s_wr;
   P.s_nwr = gp->s_nwr; P.grav = gp->grav; P.p_ref = gp->p_ref; P.corey = gp->corey; P.h = gp->h; P.flags = gp->flags;
   P.fs_modulus = gp->fs_modulus;
+  P.inv_den = 1.0 / (1.0 - gp->s_wr - gp->s_nwr);
+  P.inv_mu_w = 1.0 / gp->mu_w;
+  P.inv_mu_nw = 1.0 / gp->mu_nw;
   return P;
 }
 
@@ -878,7 +1065,7 @@ static ps_status assemble_values(const ps_gen_params* gp, cudaStream_t st, ps_sy
   double* vff = const_cast<double*>(o.jac.A_ff.val);
   double* dfs = const_cast<double*>(o.jac.d_fs);
   uint8_t* dir = const_cast<uint8_t*>(o.jac.dirichlet_u);
-  PS_TICK(); k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, vuu);
+  PS_TICK(); k_values_uu<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uu.rowptr, nn, vuu);
   PS_TICK(); k_values_uf<<<grid_for(nn, 128), 128, 0, st>>>(g, P, dR, M, o.jac.A_uf.rowptr, o.jac.A_uf.colind, nn, vuf);
   PS_TICK(); k_values_fu<<<grid_for(nc, 128), 128, 0, st>>>(g, P, dR, M, s_state, o.jac.A_fu.rowptr, o.jac.A_fu.colind,
                                                          nc, vfu);
@@ -890,8 +1077,8 @@ static ps_status assemble_values(const ps_gen_params* gp, cudaStream_t st, ps_sy
   PS_TICK(); k_zero_uu<<<grid_for(nn, 128), 128, 0, st>>>(o.jac.A_uu.rowptr, o.jac.A_uu.colind, nn, dir, vuu);
   PS_TICK(); k_zero_uf<<<grid_for(nn, 256), 256, 0, st>>>(o.jac.A_uf.rowptr, nn, dir, vuf);
   PS_TICK(); k_zero_fu<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_fu.rowptr, o.jac.A_fu.colind, nc, dir, vfu);
-  double* alpha;  // [alpha_u, alpha_f]
-  PS_TRY(ar.alloc(&alpha, 2));
+  double* alpha;  // [alpha_u, alpha_f, then the four scaling factors of k_alpha]
+  PS_TRY(ar.alloc(&alpha, 6));
   double one2[2] = {1.0, 1.0};
   PS_CUDA(cudaMemcpyAsync(alpha, one2, sizeof(one2), cudaMemcpyHostToDevice, st));
   if (gp->flags & PS_GEN_SCALE) {
@@ -902,13 +1089,15 @@ static ps_status assemble_values(const ps_gen_params* gp, cudaStream_t st, ps_sy
     PS_TRY(sum_f64(ar, cv, 3 * nn, sums + 1, st));
     PS_TICK(); k_diag_pp<<<grid_for(nc, 256), 256, 0, st>>>(o.jac.A_ff.rowptr, o.jac.A_ff.colind, nc, vff, 1e6, dv);
     PS_TRY(sum_f64(ar, dv, nc, sums + 2, st));
-    PS_TICK(); k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc));
-    const double pc = 1e6;
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_uu.nnzb * 9, 256), 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, 9, 0, pc, alpha, 0);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_uf.nnzb * 6, 256), 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, 2, 0x2, pc, alpha, 0);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_fu.nnzb * 6, 256), 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, 6, 0, pc, alpha, 1);
-    PS_TICK(); k_scale<<<grid_for(o.jac.A_ff.nnzb * 4, 256), 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, 2, 0x2, pc, alpha, 1);
-    PS_TICK(); k_scale<<<grid_for(2 * nc, 256), 256, 0, st>>>(dfs, 2 * nc, 1, 0x1, pc, alpha, 1);
+    PS_TICK(); k_alpha<<<1, 1, 0, st>>>(sums, alpha, double(nc), 1e6);
+    // A_uu: mechanics rows; A_uf: mechanics rows, columns (s, p); A_fu: flow rows; A_ff: flow rows, columns
+    // (s, p); d_fs: flow rows, p columns
+    const int sgrid = 4 * num_sms();
+    PS_TICK(); k_scale<<<sgrid, 256, 0, st>>>(vuu, o.jac.A_uu.nnzb * 9, alpha + 2, 0, 0);
+    PS_TICK(); k_scale<<<sgrid, 256, 0, st>>>(vuf, o.jac.A_uf.nnzb * 6, alpha + 2, 0, 1);
+    PS_TICK(); k_scale<<<sgrid, 256, 0, st>>>(vfu, o.jac.A_fu.nnzb * 6, alpha + 2, 2, 2);
+    PS_TICK(); k_scale<<<sgrid, 256, 0, st>>>(vff, o.jac.A_ff.nnzb * 4, alpha + 2, 2, 3);
+    PS_TICK(); k_scale<<<sgrid, 256, 0, st>>>(dfs, 2 * nc, alpha + 2, 3, 3);
     PS_CUDA(cudaGetLastError());
     ar.release(dv); ar.release(cv); ar.release(sums);
   }
