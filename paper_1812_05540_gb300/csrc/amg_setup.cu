@@ -69,7 +69,9 @@ __device__ __forceinline__ int32_t find_col(const int32_t* __restrict__ ci, int3
 }
 
 // symmetric strength graph: i~j if max(abar_ij, abar_ji) >= theta sqrt(abar_ii abar_jj); kStrLanes
-// threads per row, each entry decided on its own
+// threads per row.  Both entries of a pair get the same bits (max and the product under the root are
+// symmetric), so the entry above the diagonal decides the pair and writes its transposed entry as well;
+// an entry below the diagonal decides itself only when its transposed entry is missing.
 constexpr int kStrLanes = 8;
 template <int NC>
 __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -80,23 +82,32 @@ __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int3
   const int64_t i = t / kStrLanes;
   if (i >= n) return;
   for (int32_t q = rp[i] + int32_t(t % kStrLanes); q < rp[i + 1]; q += kStrLanes) {
-    int32_t j = ci[q];
+    const int32_t j = ci[q];
+    if (j == i || excl[i] || excl[j]) {
+      strong[q] = 0;
+      wgt[q] = 0.0;
+      continue;
+    }
+    const int32_t lo = rp[j], hi = rp[j + 1];
+    const int32_t qt = find_col(ci, lo, hi, int32_t(i));
+    const bool has_t = qt < hi && ci[qt] == i;
+    if (j < i && has_t) continue;  // the entry (j, i) above the diagonal writes this one
     uint8_t s = 0;
     double w = 0.0;
-    if (!excl[i] && j != i && !excl[j]) {
-      int32_t lo = rp[j], hi = rp[j + 1];
-      int32_t qt = find_col(ci, lo, hi, int32_t(i));
-      double aij = abar<NC>(v, q);
-      double aji = (qt < hi && ci[qt] == i) ? abar<NC>(v, qt) : 0.0;
-      double t = aij > aji ? aij : aji;
-      double den = sqrt(dgbar[i] * dgbar[j]);
-      if (t >= theta * den && t > 0.0) {
-        s = 1;
-        w = t / den;
-      }
+    const double aij = abar<NC>(v, q);
+    const double aji = has_t ? abar<NC>(v, qt) : 0.0;
+    const double tt = aij > aji ? aij : aji;
+    const double den = sqrt(dgbar[i] * dgbar[j]);
+    if (tt >= theta * den && tt > 0.0) {
+      s = 1;
+      w = tt / den;
     }
     strong[q] = s;
     wgt[q] = w;
+    if (has_t) {
+      strong[qt] = s;
+      wgt[qt] = w;
+    }
   }
 }
 
@@ -612,6 +623,97 @@ __global__ void k_spgemm_dense_fill(const int32_t* __restrict__ rows, int32_t nr
   }
 }
 
+// Dense path with few output columns (m <= kDenseMaxCols), one warp per row: the row's column set is a
+// bitmap and its accumulators a dense array, both in the warp's shared memory.  The count pass marks the
+// bitmap (in any order) and counts its bits.  The fill pass marks again, then adds the products one inner
+// index at a time in ascending order (lanes take the entries of that Y row, whose columns are distinct, so
+// no two lanes meet; a warp barrier separates consecutive inner indices), and emits the columns in
+// ascending order from the bitmap.
+__device__ __forceinline__ void dense_mark(int64_t i, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                                           const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                           uint32_t* bm, int32_t words, int lane) {
+  for (int t = lane; t < words; t += 32) bm[t] = 0u;
+  __syncwarp();
+  for_products(i, xrp, xci, yrp, lane, [&](bool valid, int, int32_t r, int32_t) {
+    if (valid) {
+      const int32_t j = yci[r];
+      atomicOr(&bm[j >> 5], 1u << (j & 31));
+    }
+  });
+  __syncwarp();
+}
+
+__global__ void k_spgemm_dense_count_w(const int32_t* __restrict__ rows, int32_t nrows,
+                                       const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                                       const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                       int32_t words, int32_t* __restrict__ cnt) {
+  extern __shared__ uint32_t bm_all[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (w >= nrows) return;
+  const int64_t i = rows[w];
+  uint32_t* bm = bm_all + int64_t(wib) * words;
+  dense_mark(i, xrp, xci, yrp, yci, bm, words, lane);
+  int c = 0;
+  for (int t = lane; t < words; t += 32) c += __popc(bm[t]);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[i] = c;
+}
+
+template <int NC>
+__global__ void k_spgemm_dense_fill_w(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                                      const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                                      const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                      const double* __restrict__ yv, int32_t m, int32_t words,
+                                      const int32_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                      double* __restrict__ cv) {
+  extern __shared__ double dsm[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (w >= nrows) return;
+  const int64_t i = rows[w];
+  const int64_t per = int64_t(m) * NC + (words + 1) / 2;  // doubles per warp: accumulators, then the bitmap
+  double* acc = dsm + int64_t(wib) * per;
+  uint32_t* bm = reinterpret_cast<uint32_t*>(acc + int64_t(m) * NC);
+  for (int64_t t = lane; t < int64_t(m) * NC; t += 32) acc[t] = 0.0;
+  dense_mark(i, xrp, xci, yrp, yci, bm, words, lane);
+  for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
+    const int32_t k = xci[q];
+    double x[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = xv[int64_t(q) * NC + c];
+    for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32) {
+      const int32_t j = yci[r];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[int64_t(j) * NC + c] = acc[int64_t(j) * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+    }
+    __syncwarp();
+  }
+  int32_t base = crp[i];
+  for (int32_t w0 = 0; w0 < words; w0 += 32) {
+    const int32_t t = w0 + lane;
+    uint32_t bits = t < words ? bm[t] : 0u;
+    const int32_t pc = __popc(bits);
+    int32_t inc = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    int32_t pos = base + inc - pc;
+    while (bits) {
+      const int b = __ffs(int(bits)) - 1;
+      bits &= bits - 1u;
+      const int32_t j = t * 32 + b;
+      cci[pos] = j;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) cv[int64_t(pos) * NC + c] = acc[int64_t(j) * NC + c];
+      ++pos;
+    }
+    base += __shfl_sync(0xffffffffu, inc, 31);
+  }
+}
+
 template <int NC, int C>
 __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
                               const int32_t* __restrict__ xci, const double* __restrict__ xv,
@@ -925,7 +1027,15 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   int32_t* stamp = nullptr;
   double* acc = nullptr;
   int64_t B = 0;
-  if (hl > 0) {
+  const int32_t words = int32_t((m + 31) / 32);
+  // warps per CTA of the shared-memory dense path (m <= kDenseMaxCols)
+  const size_t dense_per = (size_t(m) * NC + size_t(words + 1) / 2) * 8;
+  const int dense_wpb = int(std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / (dense_per > 0 ? dense_per : 1))));
+  if (hl > 0 && dense_ok) {
+    PS_TICK(); k_spgemm_dense_count_w<<<unsigned((hl + dense_wpb - 1) / dense_wpb), 32 * dense_wpb,
+                                        size_t(dense_wpb) * words * 4, st>>>(longrows, hl, xrp, xci, yrp, yci, words,
+                                                                             cnt);
+  } else if (hl > 0) {
     int64_t per = m * (4 + 8 * NC);
     B = (int64_t(256) << 20) / (per > 0 ? per : 1);
     if (B < 1) B = 1;
@@ -951,7 +1061,7 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   PS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, st));
   PS_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   PS_CUDA(cudaStreamSynchronize(st));
-  if (hl > B) {
+  if (!dense_ok && hl > B) {
     // more long rows than the count pass had: a larger batch of accumulators (tags are unique per
     // row, so fresh zeroed stamps serve any row)
     int64_t per = m * (4 + 8 * NC);
@@ -981,7 +1091,13 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     });
   }
   PS_CUDA(cudaGetLastError());
-  for (int64_t b0 = 0; b0 < hl; b0 += B) {
+  if (dense_ok && hl > 0) {
+    const size_t sm = size_t(dense_wpb) * dense_per;
+    cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    PS_TICK(); k_spgemm_dense_fill_w<NC><<<unsigned((hl + dense_wpb - 1) / dense_wpb), 32 * dense_wpb, sm, st>>>(
+        longrows, hl, xrp, xci, xv, yrp, yci, yv, int32_t(m), words, *crp, *cci, *cv);
+  }
+  for (int64_t b0 = 0; !dense_ok && b0 < hl; b0 += B) {
     int32_t nb = int32_t(hl - b0 < B ? hl - b0 : B);
     PS_TICK(); k_spgemm_dense_fill<NC><<<nb, 256, 0, st>>>(longrows + b0, nb, xrp, xci, xv, yrp, yci, yv, stamp, acc, m,
                                                            *crp, *cci, *cv);
@@ -990,6 +1106,127 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   if (stamp) { ar.release(stamp); ar.release(acc); }
   ar.release(cnt); ar.release(islong); ar.release(longrows); ar.release(nlong); ar.release(lists);
   ar.release(counts);
+  return PS_OK;
+}
+
+// ---- Galerkin product R (A P) with few coarse columns, against a dense copy of A P ----
+// A P (ny x m, m <= kDenseMaxCols) is scattered into a dense array Dn[k][j][c] that holds exact zeros off its
+// pattern, and into one pattern bitmap per row.  Row i of the product takes as its pattern the union of the
+// bitmaps of the A P rows that its R row touches, and each of its values is the sum over the R row, in
+// ascending order, of r_ik (A P)_kj: the terms off the pattern of A P are exact zeros, which leave a running
+// sum as it is, so the values equal those of the row-by-row sparse product.  All lanes work on outputs, where
+// the sparse product of such short, dense rows is bound by the latency of its chain of inner indices.
+__global__ void k_gal_densify(int64_t ny, int nc, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const double* __restrict__ v, int64_t m, int32_t words, double* __restrict__ Dn,
+                              uint32_t* __restrict__ YB) {
+  const int64_t k = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= ny) return;
+  for (int32_t q = rp[k] + lane; q < rp[k + 1]; q += 32) {
+    const int32_t j = ci[q];
+    for (int c = 0; c < nc; ++c) Dn[(k * m + j) * nc + c] = v[int64_t(q) * nc + c];
+    atomicOr(&YB[k * words + (j >> 5)], 1u << (j & 31));
+  }
+}
+
+__global__ void k_gal_count(int64_t n, const int32_t* __restrict__ xrp, const int32_t* __restrict__ xci,
+                            const uint32_t* __restrict__ YB, int32_t words, uint32_t* __restrict__ XB,
+                            int32_t* __restrict__ cnt) {
+  const int64_t i = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int c = 0;
+  for (int32_t w0 = 0; w0 < words; w0 += 32) {
+    const int32_t w = w0 + lane;
+    uint32_t b = 0u;
+    if (w < words)
+      for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) b |= YB[int64_t(xci[q]) * words + w];
+    if (w < words) XB[i * words + w] = b;
+    c += __popc(b);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[i] = c;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_gal_fill(int64_t n, const int32_t* __restrict__ xrp,
+                                                  const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                                                  const double* __restrict__ Dn, int64_t m, int32_t words,
+                                                  const uint32_t* __restrict__ XB, const int32_t* __restrict__ crp,
+                                                  int32_t* __restrict__ cci, double* __restrict__ cv) {
+  __shared__ int32_t cols[kDenseMaxCols];
+  __shared__ int32_t wbase[33];
+  const int64_t i = blockIdx.x;
+  if (i >= n) return;
+  // the row's columns in ascending order, from its bitmap (words <= 32: one warp scans the word counts)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const uint32_t b = lane < words ? XB[i * words + lane] : 0u;
+    const int32_t pc = __popc(b);
+    int32_t inc = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    wbase[lane] = inc - pc;
+    if (lane == 31) wbase[32] = inc;
+  }
+  __syncthreads();
+  for (int32_t w = threadIdx.x; w < words; w += blockDim.x) {
+    uint32_t b = XB[i * words + w];
+    int32_t pos = wbase[w];
+    while (b) {
+      const int t = __ffs(int(b)) - 1;
+      b &= b - 1u;
+      cols[pos++] = w * 32 + t;
+    }
+  }
+  __syncthreads();
+  const int32_t u = wbase[32], q0 = xrp[i], q1 = xrp[i + 1], o = crp[i];
+  for (int32_t idx = threadIdx.x; idx < u * NC; idx += blockDim.x) {
+    const int32_t slot = idx / NC, c = idx - slot * NC;
+    const int64_t j = cols[slot];
+    double acc = 0.0;
+#pragma unroll 4
+    for (int32_t q = q0; q < q1; ++q) acc = acc + xv[int64_t(q) * NC + c] * Dn[(int64_t(xci[q]) * m + j) * NC + c];
+    cv[int64_t(o + slot) * NC + c] = acc;
+    if (c == 0) cci[o + slot] = int32_t(j);
+  }
+}
+
+// C = X Y with Y of m <= kDenseMaxCols columns by the dense-copy kernels above; *used = false (nothing done)
+// when the dense copy of Y would exceed max_bytes
+template <int NC>
+ps_status galerkin_dense(Arena& ar, int64_t n, int64_t ny, int64_t m, const int32_t* xrp, const int32_t* xci,
+                         const double* xv, const int32_t* yrp, const int32_t* yci, const double* yv, int32_t** crp,
+                         int32_t** cci, double** cv, int64_t* cnnz, size_t max_bytes, bool* used, cudaStream_t st) {
+  *used = false;
+  const int32_t words = int32_t((m + 31) / 32);
+  const size_t dbytes = size_t(ny) * size_t(m) * NC * 8;
+  if (m > kDenseMaxCols || m < 1 || dbytes > max_bytes) return PS_OK;
+  double* Dn;
+  uint32_t *YB, *XB;
+  int32_t* cnt;
+  PS_TRY(ar.alloc(&Dn, size_t(ny) * m * NC));
+  PS_TRY(ar.alloc(&YB, size_t(ny) * words + 1));
+  PS_TRY(ar.alloc(&XB, size_t(n) * words + 1));
+  PS_TRY(ar.alloc(&cnt, n + 1));
+  PS_TRY(ar.alloc(crp, n + 1));
+  PS_CUDA(cudaMemsetAsync(Dn, 0, dbytes, st));
+  PS_CUDA(cudaMemsetAsync(YB, 0, sizeof(uint32_t) * (size_t(ny) * words + 1), st));
+  PS_TICK(); k_gal_densify<<<grid_for(ny * 32, 256), 256, 0, st>>>(ny, NC, yrp, yci, yv, m, words, Dn, YB);
+  PS_TICK(); k_gal_count<<<grid_for(n * 32, 256), 256, 0, st>>>(n, xrp, xci, YB, words, XB, cnt);
+  PS_CUDA(cudaGetLastError());
+  int32_t tot = 0;
+  PS_TRY(scan_i32(ar, cnt, *crp, n, &tot, st));
+  *cnnz = tot;
+  PS_TRY(ar.alloc(cci, size_t(tot) + 1));
+  PS_TRY(ar.alloc(cv, (size_t(tot) + 1) * NC));
+  PS_TICK(); k_gal_fill<NC><<<unsigned(n), 256, 0, st>>>(n, xrp, xci, xv, Dn, m, words, XB, *crp, *cci, *cv);
+  PS_CUDA(cudaGetLastError());
+  ar.release(Dn); ar.release(YB); ar.release(XB); ar.release(cnt);
+  *used = true;
   return PS_OK;
 }
 
@@ -1235,7 +1472,11 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     double *apv, *cv;
     int64_t apnnz = 0, cnnz = 0;
     PS_TRY(spgemm<NC>(ar, n, na, lev.rp, lev.ci, lev.v, lev.prp, lev.pci, lev.pv, &aprp, &apci, &apv, &apnnz, d_err, st));
-    PS_TRY(spgemm<NC>(ar, na, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz, d_err, st));
+    bool dense_rap = false;
+    PS_TRY(galerkin_dense<NC>(ar, na, n, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz,
+                              size_t(512) << 20, &dense_rap, st));
+    if (!dense_rap)
+      PS_TRY(spgemm<NC>(ar, na, na, lev.rrp, lev.rci, lev.rv, aprp, apci, apv, &crp, &cci, &cv, &cnnz, d_err, st));
     int herr = 0;
     PS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
