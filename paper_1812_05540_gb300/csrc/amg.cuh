@@ -84,6 +84,7 @@ struct AmgParams {
   int coarse_max, max_levels;
   bool mixed;
   bool bf16p;  // also keep BF16 copies of P and R (transfer operators read in BF16, summed in FP32)
+  bool l1 = true;  // form the l1 row norms (read only by the l1-Jacobi smoother)
 };
 
 // Build the hierarchy from the level-0 operator (rp/ci/v are adopted: the

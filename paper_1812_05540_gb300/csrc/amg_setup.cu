@@ -15,6 +15,8 @@
 #include "amg.cuh"
 #include "gridsync.cuh"
 
+#include <cooperative_groups.h>
+
 namespace ps_internal {
 namespace {
 
@@ -70,9 +72,35 @@ __device__ __forceinline__ int32_t find_col(const int32_t* __restrict__ ci, int3
 
 // symmetric strength graph: i~j if max(abar_ij, abar_ji) >= theta sqrt(abar_ii abar_jj); kStrLanes
 // threads per row.  Both entries of a pair get the same bits (max and the product under the root are
-// symmetric), so the entry above the diagonal decides the pair and writes its transposed entry as well;
-// an entry below the diagonal decides itself only when its transposed entry is missing.
+// symmetric), so the lanes of row i decide the pairs of its entries above the diagonal and write both entries;
+// an entry below the diagonal is decided by its own row only when its transposed entry is missing.  The
+// columns of a row are sorted, so its entries above the diagonal are contiguous and the lanes stay busy.
 constexpr int kStrLanes = 8;
+template <int NC>
+__device__ __forceinline__ void strength_pair(int64_t i, int32_t j, int32_t q, int32_t qt, bool has_t,
+                                              const double* __restrict__ v, const double* __restrict__ dgbar,
+                                              const uint8_t* __restrict__ excl, double theta,
+                                              uint8_t* __restrict__ strong, double* __restrict__ wgt) {
+  uint8_t s = 0;
+  double w = 0.0;
+  if (!excl[i] && !excl[j]) {
+    const double aij = abar<NC>(v, q);
+    const double aji = has_t ? abar<NC>(v, qt) : 0.0;
+    const double t = aij > aji ? aij : aji;
+    const double den = sqrt(dgbar[i] * dgbar[j]);
+    if (t >= theta * den && t > 0.0) {
+      s = 1;
+      w = t / den;
+    }
+  }
+  strong[q] = s;
+  wgt[q] = w;
+  if (has_t) {
+    strong[qt] = s;
+    wgt[qt] = w;
+  }
+}
+
 template <int NC>
 __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const double* __restrict__ v, const double* __restrict__ dgbar,
@@ -81,33 +109,25 @@ __global__ void k_strength(int64_t n, const int32_t* __restrict__ rp, const int3
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = t / kStrLanes;
   if (i >= n) return;
-  for (int32_t q = rp[i] + int32_t(t % kStrLanes); q < rp[i + 1]; q += kStrLanes) {
+  const int sub = int(t % kStrLanes);
+  const int32_t q0 = rp[i], q1 = rp[i + 1];
+  const int32_t qd = find_col(ci, q0, q1, int32_t(i));  // first entry with column >= i
+  const int32_t qu = (qd < q1 && ci[qd] == i) ? qd + 1 : qd;
+  if (sub == 0 && qu != qd) {
+    strong[qd] = 0;
+    wgt[qd] = 0.0;
+  }
+  for (int32_t q = qu + sub; q < q1; q += kStrLanes) {
     const int32_t j = ci[q];
-    if (j == i || excl[i] || excl[j]) {
-      strong[q] = 0;
-      wgt[q] = 0.0;
-      continue;
-    }
     const int32_t lo = rp[j], hi = rp[j + 1];
     const int32_t qt = find_col(ci, lo, hi, int32_t(i));
-    const bool has_t = qt < hi && ci[qt] == i;
-    if (j < i && has_t) continue;  // the entry (j, i) above the diagonal writes this one
-    uint8_t s = 0;
-    double w = 0.0;
-    const double aij = abar<NC>(v, q);
-    const double aji = has_t ? abar<NC>(v, qt) : 0.0;
-    const double tt = aij > aji ? aij : aji;
-    const double den = sqrt(dgbar[i] * dgbar[j]);
-    if (tt >= theta * den && tt > 0.0) {
-      s = 1;
-      w = tt / den;
-    }
-    strong[q] = s;
-    wgt[q] = w;
-    if (has_t) {
-      strong[qt] = s;
-      wgt[qt] = w;
-    }
+    strength_pair<NC>(i, j, q, qt, qt < hi && ci[qt] == i, v, dgbar, excl, theta, strong, wgt);
+  }
+  for (int32_t q = q0 + sub; q < qd; q += kStrLanes) {
+    const int32_t j = ci[q];
+    const int32_t lo = rp[j], hi = rp[j + 1];
+    const int32_t qt = find_col(ci, lo, hi, int32_t(i));
+    if (!(qt < hi && ci[qt] == i)) strength_pair<NC>(i, j, q, qt, false, v, dgbar, excl, theta, strong, wgt);
   }
 }
 
@@ -140,7 +160,10 @@ __device__ __forceinline__ bool group_any(bool b) {
   const int lane = int(threadIdx.x & 31);
   return ((m >> (lane & ~(kMisLanes - 1))) & ((1u << kMisLanes) - 1u)) != 0u;
 }
+// prev: the undecided flag of the previous round (null: none); a round after one that left no row
+// undecided changes nothing, so its kernels return at once
 #define MIS_ROW                                                      \
+  if (prev && *prev == 0) return;                                    \
   const int64_t t_ = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; \
   const int64_t i = t_ / kMisLanes;                                  \
   const int sub = int(t_ % kMisLanes);                               \
@@ -148,7 +171,7 @@ __device__ __forceinline__ bool group_any(bool b) {
 
 __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st, int level,
-                         int64_t* __restrict__ m1) {
+                         int64_t* __restrict__ m1, const int32_t* __restrict__ prev) {
   MIS_ROW
   int64_t m = -1;
   if (act) {
@@ -164,7 +187,7 @@ __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_
 }
 __global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const int64_t* __restrict__ m1, int level,
-                         uint8_t* __restrict__ st, uint8_t* __restrict__ nr) {
+                         uint8_t* __restrict__ st, uint8_t* __restrict__ nr, const int32_t* __restrict__ prev) {
   MIS_ROW
   int64_t m = -1;
   if (act) {
@@ -184,7 +207,7 @@ __global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_
 }
 __global__ void k_mis_c1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ nr,
-                         uint8_t* __restrict__ c1) {
+                         uint8_t* __restrict__ c1, const int32_t* __restrict__ prev) {
   MIS_ROW
   bool c = false;
   if (act) {
@@ -197,7 +220,7 @@ __global__ void k_mis_c1(int64_t n, const int32_t* __restrict__ rp, const int32_
 }
 __global__ void k_mis_c2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const uint8_t* __restrict__ strong, const uint8_t* __restrict__ c1,
-                         uint8_t* __restrict__ st, int32_t* __restrict__ undecided) {
+                         uint8_t* __restrict__ st, int32_t* __restrict__ undecided, const int32_t* __restrict__ prev) {
   MIS_ROW
   const bool undec = act && st[i] == 0;
   bool c = false;
@@ -1230,6 +1253,176 @@ ps_status galerkin_dense(Arena& ar, int64_t n, int64_t ny, int64_t m, const int3
   return PS_OK;
 }
 
+// The Gauss-Jordan inverse on one thread-block cluster per component, the matrix held in the cluster's
+// distributed shared memory: CTA `rank` keeps physical rows [rank R, rank R + R) of A and of the inverse.  Row
+// exchanges are a permutation (logical row r is physical row perm[r]).  The pivot is the largest |a| of
+// column k over the logical rows >= k (ties: the smaller logical row); its row is divided by the pivot, and
+// every other row subtracts its column-k entry times that row, with one fused multiply-add per entry.  In the
+// inverse only the columns of the rows pivoted so far (perm[0..k]) can be nonzero in the pivot row, so only
+// those are divided and updated.  Per pivot two hardware cluster barriers (no polling): one after the local
+// column maxima, one after the division; then each CTA copies the pivot row and updates its own rows.
+constexpr int kGjCluster = 16;
+__global__ void __launch_bounds__(256) k_gj_cluster(int64_t n, int R, const double* __restrict__ M,
+                                                    double* __restrict__ I) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double gsm[];
+  const int rank = int(cluster.block_rank());
+  const int CS = int(cluster.num_blocks());
+  const int c = int(blockIdx.x) / CS;
+  const int nn = int(n);
+  double* A = gsm;                         // [R][n]
+  double* B = A + int64_t(R) * n;          // [R][n]
+  double* prow = B + int64_t(R) * n;       // [2 n]: pivot row of A, then of B
+  double* fv = prow + 2 * n;               // [R]: column-k entries of the own rows
+  double* pval = fv + R;                   // [2]: local maximum, by pivot parity
+  int* pidx = reinterpret_cast<int*>(pval + 2);  // [2]
+  int* perm = pidx + 2;                    // [n]
+  int* iperm = perm + n;                   // [n]
+  __shared__ int sh_p;
+  const int ph0 = rank * R;
+  const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31, nwarp = int(blockDim.x) >> 5;
+  for (int lr = warp; lr < R; lr += nwarp) {
+    const int ph = ph0 + lr;
+    for (int j = lane; j < nn; j += 32) {
+      A[int64_t(lr) * n + j] = ph < nn ? M[(int64_t(c) * n + ph) * n + j] : 0.0;
+      B[int64_t(lr) * n + j] = (ph < nn && j == ph) ? 1.0 : 0.0;
+    }
+  }
+  for (int r = threadIdx.x; r < nn; r += blockDim.x) {
+    perm[r] = r;
+    iperm[r] = r;
+  }
+  cluster.sync();
+  for (int k = 0; k < nn; ++k) {
+    const int par = k & 1;
+    if (warp == 0) {
+      double best = -1.0;
+      int arg = INT_MAX;
+      for (int lr = lane; lr < R; lr += 32) {
+        const int ph = ph0 + lr;
+        if (ph < nn && iperm[ph] >= k) {
+          const double a = fabs(A[int64_t(lr) * n + k]);
+          const int li = iperm[ph];
+          if (a > best || (a == best && li < arg)) { best = a; arg = li; }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+      }
+      if (lane == 0) { pval[par] = best; pidx[par] = arg; }
+    }
+    cluster.sync();
+    if (warp == 0) {
+      double best = -1.0;
+      int arg = INT_MAX;
+      if (lane < CS) {
+        best = *cluster.map_shared_rank(pval + par, lane);
+        arg = *cluster.map_shared_rank(pidx + par, lane);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+      }
+      if (lane == 0) {
+        const int p = arg == INT_MAX ? k : arg;
+        const int rk = perm[k], rp = perm[p];
+        perm[k] = rp; perm[p] = rk;
+        iperm[rp] = k; iperm[rk] = p;
+        sh_p = rp;
+      }
+    }
+    __syncthreads();
+    const int php = sh_p;  // physical row of the pivot
+    const int owner = php / R, lp = php - owner * R;
+    if (rank == owner) {
+      const double piv = A[int64_t(lp) * n + k];
+      __syncthreads();
+      for (int j = k + threadIdx.x; j < nn; j += blockDim.x) A[int64_t(lp) * n + j] = A[int64_t(lp) * n + j] / piv;
+      for (int jj = threadIdx.x; jj <= k; jj += blockDim.x) {
+        const int j = perm[jj];
+        B[int64_t(lp) * n + j] = B[int64_t(lp) * n + j] / piv;
+      }
+    }
+    cluster.sync();
+    {
+      const double* rA = cluster.map_shared_rank(A, owner) + int64_t(lp) * n;
+      const double* rB = cluster.map_shared_rank(B, owner) + int64_t(lp) * n;
+      for (int j = k + threadIdx.x; j < nn; j += blockDim.x) prow[j] = rA[j];
+      for (int jj = threadIdx.x; jj <= k; jj += blockDim.x) {
+        const int j = perm[jj];
+        prow[n + j] = rB[j];
+      }
+      for (int lr = threadIdx.x; lr < R; lr += blockDim.x) fv[lr] = A[int64_t(lr) * n + k];
+    }
+    __syncthreads();
+    for (int lr = warp; lr < R; lr += nwarp) {
+      const int ph = ph0 + lr;
+      const double m = fv[lr];
+      if (ph >= nn || ph == php || m == 0.0) continue;
+      double* a = A + int64_t(lr) * n;
+      double* b = B + int64_t(lr) * n;
+      for (int j = k + lane; j < nn; j += 32) a[j] = fma(-m, prow[j], a[j]);
+      for (int jj = lane; jj <= k; jj += 32) {
+        const int j = perm[jj];
+        b[j] = fma(-m, prow[n + j], b[j]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int lr = warp; lr < R; lr += nwarp) {
+    const int ph = ph0 + lr;
+    if (ph >= nn) continue;
+    const int r = iperm[ph];
+    for (int j = lane; j < nn; j += 32) I[(int64_t(c) * n + r) * n + j] = B[int64_t(lr) * n + j];
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// k_gj_cluster when the rows fit the clusters' shared memory: true when done
+bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) {
+  int dev = 0, maxsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (int cs : {kGjCluster, 8}) {
+    const int R = int((n + cs - 1) / cs);
+    const size_t smem = (size_t(2) * R * n + 2 * n + R + 2) * 8 + size_t(2 + 2 * n) * 4;
+    if (smem > size_t(maxsm) - 1024) continue;
+    if (cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(cs * nc));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(cs);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_gj_cluster, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    PS_TICK();
+    if (cudaLaunchKernelEx(&cfg, k_gj_cluster, n, R, M, I) == cudaSuccess) return true;
+    cudaGetLastError();
+  }
+  return false;
+}
+
 // The coarsest inverse by k_gj_all: 0 done, 1 not launched (no cooperative launch; the caller runs the
 // launch-per-step path), 2 a grid barrier wait gave up (the inverse is incomplete)
 int gj_cooperative(int64_t n, int nc, double* M, double* I, double* f, Arena& ar, cudaStream_t st) {
@@ -1266,8 +1459,13 @@ int gj_cooperative(int64_t n, int nc, double* M, double* I, double* f, Arena& ar
 }
 
 // Gauss-Jordan inverses of nc dense n x n matrices (M is overwritten, inv starts as the identity): one
-// cooperative launch, else one launch pair per pivot
+// thread-block cluster per component when its rows fit the cluster's shared memory, else one cooperative
+// launch, else one launch pair per pivot
 ps_status gj_inverse(int64_t n, int nc, double* M, double* inv, double* f, Arena& ar, cudaStream_t st) {
+  if (gj_cluster(n, nc, M, inv, st)) {
+    PS_CUDA(cudaGetLastError());
+    return PS_OK;
+  }
   const int gj = gj_cooperative(n, nc, M, inv, f, ar, st);
   if (gj == 2) {
     set_reason("a bounded grid barrier wait of the coarsest-level Gauss-Jordan inverse gave up");
@@ -1301,16 +1499,21 @@ ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, c
   int64_t* m1;
   uint8_t *nr, *c1;
   int32_t* und;
-  PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, 1));
+  // rounds go in batches of kMisBatch between host checks; und[b] is the undecided flag of round b of a batch
+  constexpr int kMisBatch = 4;
+  PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, kMisBatch));
   PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, rp, strong, excl, stt);
-  for (int round = 0;; ++round) {
-    PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t), st));
-    PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, l, m1);
-    PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, l, stt, nr);
-    PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, nr, c1);
-    PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, c1, stt, und);
+  for (int round = 0;; round += kMisBatch) {
+    PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t) * kMisBatch, st));
+    for (int b = 0; b < kMisBatch; ++b) {
+      const int32_t* prev = b > 0 ? und + b - 1 : nullptr;
+      PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, l, m1, prev);
+      PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, l, stt, nr, prev);
+      PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, nr, c1, prev);
+      PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, c1, stt, und + b, prev);
+    }
     int32_t h_und = 0;
-    PS_CUDA(cudaMemcpyAsync(&h_und, und, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&h_und, und + kMisBatch - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     if (h_und == 0) break;
     if (round > 100000) {
@@ -1401,11 +1604,13 @@ ps_status build_impl(Arena& ar, Amg& H, int64_t n0, int64_t nnz0, int32_t* rp0, 
     double om[3] = {0, 0, 0};
     for (int c = 0; c < NC; ++c) om[c] = (4.0 / 3.0) / lev.lam[c];
     // l1 row norms for the l1-Jacobi smoother
-    PS_TRY(ar.alloc(&lev.dl1, n * NC));
-    PS_TICK(); k_l1<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.v, lev.dl1);
-    if (prm.mixed) {
-      PS_TRY(ar.alloc(&lev.dl1f, n * NC));
-      PS_TICK(); k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
+    if (prm.l1) {
+      PS_TRY(ar.alloc(&lev.dl1, n * NC));
+      PS_TICK(); k_l1<NC><<<grid_for(n, 256), 256, 0, st>>>(n, lev.rp, lev.v, lev.dl1);
+      if (prm.mixed) {
+        PS_TRY(ar.alloc(&lev.dl1f, n * NC));
+        PS_TICK(); k_to_f32<<<grid_for(n * NC, 256), 256, 0, st>>>(lev.dl1, lev.dl1f, n * NC);
+      }
     }
     // prolongator: T = A P_tent by the deterministic SpGEMM, then P = P_tent - omega D^{-1} T
     int64_t na = lev.nagg;

@@ -277,6 +277,7 @@ ps_status build_flow(ps_handle* h) {
   ap.theta = h->prm.theta_p; ap.coarse_max = h->prm.coarse_max_p; ap.max_levels = h->prm.max_levels;
   ap.mixed = h->mixed;
   ap.bf16p = h->bf16p;
+  ap.l1 = h->prm.smoother == PS_SMOOTH_L1JACOBI;
   PS_TRY(amg_build(ar, h->amg_p, 1, h->nc, F.nnzb, F.rp, F.ci, F.spp, ap, st));
   bool sp_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_p, h->grid.nx, h->grid.ny, h->grid.nz, 7, h->mixed, &sp_ok, st));
@@ -340,6 +341,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     ap.theta = h->prm.theta_u; ap.coarse_max = h->prm.coarse_max_u; ap.max_levels = h->prm.max_levels;
     ap.mixed = h->mixed;
     ap.bf16p = h->bf16p;
+    ap.l1 = h->prm.smoother == PS_SMOOTH_L1JACOBI;
     PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
     bool su_ok = false;
     PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
