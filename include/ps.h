@@ -401,11 +401,11 @@ ps_status ps_residual_at(const ps_gen_params* gp, ps_system* sys, const double* 
    above 0.5 rtol ||r_0|| / ||r_k|| (PS_FORCING_EW).  x: device array of n doubles (the final iterate). */
 enum { PS_FORCING_FIXED = 0, PS_FORCING_EW = 1 };
 typedef struct {
-  double rtol;              /* default 1e-8 */
+  double rtol;              /* default 1e-5 (the paper's Newton tolerance, Table 1) */
   int32_t max_newton;       /* default 12 (at most 32) */
   int32_t forcing;          /* PS_FORCING_EW (default) or PS_FORCING_FIXED */
   double eta_fixed;         /* default 1e-6 */
-  double ew_gamma, ew_omega, ew_eta0, ew_eta_max;  /* defaults 0.9, 2, 0.1, 0.1 (the paper's values) */
+  double ew_gamma, ew_omega, ew_eta0, ew_eta_max;  /* defaults 0.9, 2, 0.1 (the paper's values), 0.1 */
   int32_t max_backtracks;   /* default 4 */
 } ps_newton_params;
 typedef struct {

@@ -73,8 +73,8 @@ def test_newton_converges_to_a_root(cfg, kw):
 
 def test_fixed_tolerance_and_eisenstat_walker_reach_the_same_state():
     gp = oracle.default_params(1, nx=12, ny=10, nz=6)
-    xf, sf = oracle.newton(gp, np_=oracle.default_newton_params(forcing=oracle.FORCING_FIXED))
-    xe, se = oracle.newton(gp, np_=oracle.default_newton_params(forcing=oracle.FORCING_EW))
+    xf, sf = oracle.newton(gp, np_=oracle.default_newton_params(forcing=oracle.FORCING_FIXED, rtol=1e-8))
+    xe, se = oracle.newton(gp, np_=oracle.default_newton_params(forcing=oracle.FORCING_EW, rtol=1e-8))
     assert sf["converged"] and se["converged"]
     nu = 3 * (gp.nx + 1) * (gp.ny + 1) * (gp.nz + 1)
     for part in (slice(0, nu), slice(nu, None, 2), slice(nu + 1, None, 2)):
@@ -84,18 +84,25 @@ def test_fixed_tolerance_and_eisenstat_walker_reach_the_same_state():
 
 
 def test_forcing_term_hand_worked_values():
-    np_ = oracle.default_newton_params()  # gamma 0.9, omega 2, eta0 0.1, eta_max 0.1, rtol 1e-8
+    np_ = oracle.default_newton_params(rtol=1e-8)  # gamma 0.9, omega 2, eta0 0.1, eta_max 0.1
     assert oracle.ew_eta(np_, 0, 5.0, 5.0, 0.1, 10.0) == pytest.approx(0.1)
     # gamma (r_k / r_{k-1})^omega = 0.9 * 0.01 = 0.009; safeguard 0.9 * 0.1^2 = 0.009 is not above 0.1
     assert oracle.ew_eta(np_, 1, 1.0, 10.0, 0.1, 10.0) == pytest.approx(0.009)
     # the safeguard: gamma eta_prev^omega = 0.9 * 0.5^2 = 0.225 > 0.1 lifts eta to 0.225, then the cap 0.1
-    big = oracle.default_newton_params(ew_eta_max=1.0)
+    big = oracle.default_newton_params(ew_eta_max=1.0, rtol=1e-8)
     assert oracle.ew_eta(big, 1, 1.0, 10.0, 0.5, 10.0) == pytest.approx(0.225)
     assert oracle.ew_eta(np_, 1, 1.0, 10.0, 0.5, 10.0) == pytest.approx(0.1)
     # the floor: no tighter than half the nonlinear tolerance relative to the current residual
     assert oracle.ew_eta(np_, 3, 1e-7, 1e-2, 1e-4, 10.0) == pytest.approx(0.5 * 1e-8 * 10.0 / 1e-7)
-    fixed = oracle.default_newton_params(forcing=oracle.FORCING_FIXED, eta_fixed=1e-6)
+    fixed = oracle.default_newton_params(forcing=oracle.FORCING_FIXED, eta_fixed=1e-6, rtol=1e-8)
     assert oracle.ew_eta(fixed, 2, 1.0, 2.0, 0.1, 10.0) == 1e-6
+
+
+def test_default_tolerances_are_the_papers():
+    # Table 1: Newton tolerance 1e-5, Krylov tolerance 1e-6; the forcing parameters of the §4 remark
+    np_ = oracle.default_newton_params()
+    assert np_.rtol == 1e-5 and np_.eta_fixed == 1e-6
+    assert (np_.ew_gamma, np_.ew_omega, np_.ew_eta0) == (0.9, 2.0, 0.1)
 
 
 def test_library_forcing_term_equals_the_oracles():
