@@ -783,7 +783,7 @@ CSR transpose(const CSR& A) {
 }
 
 // C = X Y (row-wise Gustavson).  For each output entry the products are added
-// in ascending order of the inner index k, starting from 0.
+// in ascending order of the inner index k, starting from 0, each by one fused multiply-add.
 CSR spgemm(const CSR& X, const CSR& Y) {
   CSR C; C.n = X.n; C.m = Y.m; C.nc = X.nc;
   C.rp.assign(C.n + 1, 0);
@@ -805,7 +805,7 @@ CSR spgemm(const CSR& X, const CSR& Y) {
             cols.push_back(int32_t(j));
             for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = 0.0;
           }
-          for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = acc[j * X.nc + c] + X.v[q * X.nc + c] * Y.v[r * X.nc + c];
+          for (int c = 0; c < X.nc; ++c) acc[j * X.nc + c] = std::fma(X.v[q * X.nc + c], Y.v[r * X.nc + c], acc[j * X.nc + c]);
         }
       }
       std::sort(cols.begin(), cols.end());
@@ -1247,7 +1247,8 @@ BSR bsr_transpose(const BSR& A) {
 }
 
 // C = X Y with block products.  For each output block the block products X_ik Y_kj are added in ascending
-// order of k, starting from zero; each entry of a block product sums its inner index in ascending order.
+// order of k, starting from zero; each entry of a block product sums its inner index in ascending order, one
+// fused multiply-add per term.
 BSR bsr_spgemm(const BSR& X, const BSR& Y) {
   BSR C; C.nbr = X.nbr; C.nbc = Y.nbc; C.br = X.br; C.bc = Y.bc;
   const int br = X.br, bk = X.bc, bc = Y.bc, bs = br * bc;
@@ -1275,7 +1276,7 @@ BSR bsr_spgemm(const BSR& X, const BSR& Y) {
           for (int a = 0; a < br; ++a)
             for (int c = 0; c < bc; ++c) {
               double p = 0.0;
-              for (int e = 0; e < bk; ++e) p = p + xb[a * bk + e] * yb[e * bc + c];
+              for (int e = 0; e < bk; ++e) p = std::fma(xb[a * bk + e], yb[e * bc + c], p);
               acc[j * bs + a * bc + c] = acc[j * bs + a * bc + c] + p;
             }
         }

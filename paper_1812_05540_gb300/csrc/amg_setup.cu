@@ -614,7 +614,7 @@ __global__ void k_spgemm_dense_fill(const int32_t* __restrict__ rows, int32_t nr
     for (int32_t r = yrp[k] + threadIdx.x; r < yrp[k + 1]; r += blockDim.x) {
       int32_t j = yci[r];
       for (int c = 0; c < NC; ++c)
-        acc[int64_t(j) * NC + c] = acc[int64_t(j) * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+        acc[int64_t(j) * NC + c] = fma(x[c], yv[int64_t(r) * NC + c], acc[int64_t(j) * NC + c]);
     }
     __syncthreads();
   }
@@ -708,7 +708,7 @@ __global__ void k_spgemm_dense_fill_w(const int32_t* __restrict__ rows, int32_t 
     for (int32_t r = yrp[k] + lane; r < yrp[k + 1]; r += 32) {
       const int32_t j = yci[r];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[int64_t(j) * NC + c] = acc[int64_t(j) * NC + c] + x[c] * yv[int64_t(r) * NC + c];
+      for (int c = 0; c < NC; ++c) acc[int64_t(j) * NC + c] = fma(x[c], yv[int64_t(r) * NC + c], acc[int64_t(j) * NC + c]);
     }
     __syncwarp();
   }
@@ -751,12 +751,12 @@ __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, c
   if (w >= nrows) return;
   int64_t i = rows[w];
   if (islong[i]) return;
-  constexpr size_t per = size_t(H) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 8;
+  constexpr size_t per = size_t(H) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 16;
   unsigned char* base = sraw + per * wib;
   int32_t* tab = reinterpret_cast<int32_t*>(base);
   int32_t* list = reinterpret_cast<int32_t*>(base + H * 4);
   double* acc = reinterpret_cast<double*>(base + H * 4 + C * 4);
-  double* stg = acc + C * NC;  // one product per lane, staged for the in-order fold
+  double* stg = acc + C * NC;  // the two factors of one product per lane, staged for the in-order fold
   int ovf = 0;
   int u = spgemm_collect<H>(i, xrp, xci, yrp, yci, tab, lane, &ovf);
   if (u > C || __any_sync(0xffffffffu, ovf)) {
@@ -815,7 +815,10 @@ __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, c
       }
       pos = lo;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) stg[lane * NC + c] = x[c] * yv[int64_t(r) * NC + c];
+      for (int c = 0; c < NC; ++c) {
+        stg[lane * 2 * NC + c] = x[c];
+        stg[lane * 2 * NC + NC + c] = yv[int64_t(r) * NC + c];
+      }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, valid ? pos : (1 << 30) + lane);
     __syncwarp();
@@ -823,7 +826,10 @@ __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, c
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         double a = acc[pos * NC + c];
-        for (unsigned m = peers; m; m &= m - 1) a = a + stg[(__ffs(m) - 1) * NC + c];
+        for (unsigned m = peers; m; m &= m - 1) {
+          const int pl = __ffs(m) - 1;
+          a = fma(stg[pl * 2 * NC + c], stg[pl * 2 * NC + NC + c], a);
+        }
         acc[pos * NC + c] = a;
       }
     }
@@ -1106,7 +1112,7 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     for_class(b, [&](auto cc) {
       constexpr int C = decltype(cc)::value;
       const int wpb = C <= 128 ? 8 : (C <= 512 ? 4 : 2);
-      size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 8;
+      size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 16;
       size_t sm = per * wpb;
       cudaFuncSetAttribute(k_spgemm_fill<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
       PS_TICK(); k_spgemm_fill<NC, C><<<unsigned((nr + wpb - 1) / wpb), 32 * wpb, sm, st>>>(
@@ -1212,7 +1218,7 @@ __global__ void __launch_bounds__(256) k_gal_fill(int64_t n, const int32_t* __re
     const int64_t j = cols[slot];
     double acc = 0.0;
 #pragma unroll 4
-    for (int32_t q = q0; q < q1; ++q) acc = acc + xv[int64_t(q) * NC + c] * Dn[(int64_t(xci[q]) * m + j) * NC + c];
+    for (int32_t q = q0; q < q1; ++q) acc = fma(xv[int64_t(q) * NC + c], Dn[(int64_t(xci[q]) * m + j) * NC + c], acc);
     cv[int64_t(o + slot) * NC + c] = acc;
     if (c == 0) cci[o + slot] = int32_t(j);
   }

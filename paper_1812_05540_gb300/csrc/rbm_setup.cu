@@ -238,8 +238,10 @@ __global__ void k_row_of(int64_t n, const int32_t* __restrict__ rp, int32_t* __r
 
 // C = X Y with BR x BK blocks of X and BK x BC blocks of Y on C's given sorted pattern, one warp per row of C:
 // block (i, j) sums X_ik Y_kj over ascending k (the order of X's row), each entry of a product summing its
-// inner index in ascending order.  The warp walks the row's products in that order; lane t owns the entries
-// t and t + 32 of the output block, so every entry is accumulated by one lane, in order.
+// inner index in ascending order by fused multiply-adds.  The warp walks the row's X entries in order; the
+// products of one X entry with its Y row go to distinct output blocks, so up to G of them run side by side,
+// the lanes taking their entries (G * BR * BC of them) in turn: every output entry is still accumulated by one
+// lane at a time, in order, and the lanes stay busy where one 6 x 6 product would leave 28 of 64 slots idle.
 template <int BR, int BK, int BC>
 __global__ void __launch_bounds__(256) k_bprod(int64_t n, const int32_t* __restrict__ xrp,
                                                const int32_t* __restrict__ xci, const double* __restrict__ xv,
@@ -247,34 +249,47 @@ __global__ void __launch_bounds__(256) k_bprod(int64_t n, const int32_t* __restr
                                                const double* __restrict__ yv, const int32_t* __restrict__ crp,
                                                const int32_t* __restrict__ cci, double* __restrict__ cv) {
   constexpr int NE = BR * BC;
+  constexpr int G = NE % 32 == 0 ? 1 : (32 % NE == 0 ? 32 / NE : 8);  // products side by side
   const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
+  __shared__ int32_t spos_all[8][G];  // output block of each product of a group, per warp (256 threads)
+  int32_t* spos = spos_all[(threadIdx.x >> 5) & 7];
   const int32_t c0 = crp[i], c1 = crp[i + 1];
   for (int64_t e = int64_t(c0) * NE + lane; e < int64_t(c1) * NE; e += 32) cv[e] = 0.0;
   __syncwarp();
   for (int32_t q = xrp[i]; q < xrp[i + 1]; ++q) {
     const int32_t k = xci[q];
     const double* X = xv + int64_t(q) * BR * BK;
-    for (int32_t r = yrp[k]; r < yrp[k + 1]; ++r) {
-      const int32_t j = yci[r];
-      int32_t lo = c0, hi = c1;
-      while (lo < hi) {
-        const int32_t md = (lo + hi) >> 1;
-        if (cci[md] < j) lo = md + 1;
-        else hi = md;
+    const int32_t r1 = yrp[k + 1];
+    for (int32_t r0 = yrp[k]; r0 < r1; r0 += G) {
+      // lane g < G finds the output block of product r0 + g
+      int32_t pos = -1;
+      if (lane < G && r0 + lane < r1) {
+        const int32_t j = yci[r0 + lane];
+        int32_t lo = c0, hi = c1;
+        while (lo < hi) {
+          const int32_t md = (lo + hi) >> 1;
+          if (cci[md] < j) lo = md + 1;
+          else hi = md;
+        }
+        pos = lo < c1 ? lo : -1;  // -1: not in the pattern (cannot happen for a pattern of X Y)
       }
-      if (lo >= c1) continue;  // not in the pattern: cannot happen for a pattern of X Y
-      double* C = cv + int64_t(lo) * NE;
-      const double* Y = yv + int64_t(r) * BK * BC;
-#pragma unroll
-      for (int t = lane; t < NE; t += 32) {
-        const int a = t / BC, c = t % BC;
+      if (lane < G) spos[lane] = pos;
+      __syncwarp();
+      for (int t = lane; t < G * NE; t += 32) {
+        const int g = t / NE, e = t - g * NE;
+        const int32_t pg = spos[g];
+        if (r0 + g >= r1 || pg < 0) continue;
+        const int a = e / BC, c = e % BC;
+        const double* Y = yv + int64_t(r0 + g) * BK * BC;
         double p = 0.0;
 #pragma unroll
-        for (int e = 0; e < BK; ++e) p = p + X[a * BK + e] * Y[e * BC + c];
-        C[t] = C[t] + p;
+        for (int f = 0; f < BK; ++f) p = fma(X[a * BK + f], Y[f * BC + c], p);
+        double* C = cv + int64_t(pg) * NE;
+        C[e] = C[e] + p;
       }
+      __syncwarp();
     }
   }
 }
