@@ -169,16 +169,21 @@ __device__ __forceinline__ bool group_any(bool b) {
   const int sub = int(t_ % kMisLanes);                               \
   const bool act = i < n;
 
+// the priority keys of a level, formed once per aggregation instead of per neighbour and round
+__global__ void k_mis_keys(int64_t n, int level, int64_t* __restrict__ key) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) key[i] = mis_key(i, level);
+}
 __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st, int level,
-                         int64_t* __restrict__ m1, const int32_t* __restrict__ prev) {
+                         const uint8_t* __restrict__ strong, const uint8_t* __restrict__ st,
+                         const int64_t* __restrict__ key, int64_t* __restrict__ m1, const int32_t* __restrict__ prev) {
   MIS_ROW
   int64_t m = -1;
   if (act) {
-    if (sub == 0 && st[i] == 0) m = mis_key(i, level);
+    if (sub == 0 && st[i] == 0) m = key[i];
     for (int32_t q = rp[i] + sub; q < rp[i + 1]; q += kMisLanes)
       if (strong[q] && st[ci[q]] == 0) {
-        int64_t k = mis_key(ci[q], level);
+        const int64_t k = key[ci[q]];
         m = k > m ? k : m;
       }
   }
@@ -186,8 +191,9 @@ __global__ void k_mis_m1(int64_t n, const int32_t* __restrict__ rp, const int32_
   if (act && sub == 0) m1[i] = m;
 }
 __global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const uint8_t* __restrict__ strong, const int64_t* __restrict__ m1, int level,
-                         uint8_t* __restrict__ st, uint8_t* __restrict__ nr, const int32_t* __restrict__ prev) {
+                         const uint8_t* __restrict__ strong, const int64_t* __restrict__ m1,
+                         const int64_t* __restrict__ key, uint8_t* __restrict__ st, uint8_t* __restrict__ nr,
+                         const int32_t* __restrict__ prev) {
   MIS_ROW
   int64_t m = -1;
   if (act) {
@@ -200,7 +206,7 @@ __global__ void k_mis_m2(int64_t n, const int32_t* __restrict__ rp, const int32_
   }
   m = group_max(m);
   if (act && sub == 0) {
-    uint8_t r = (st[i] == 0 && m == mis_key(i, level)) ? 1 : 0;
+    uint8_t r = (st[i] == 0 && m == key[i]) ? 1 : 0;
     nr[i] = r;
     if (r) st[i] = 1;
   }
@@ -1508,13 +1514,16 @@ ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, c
   // rounds go in batches of kMisBatch between host checks; und[b] is the undecided flag of round b of a batch
   constexpr int kMisBatch = 4;
   PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, kMisBatch));
+  int64_t* key;
+  PS_TRY(ar.alloc(&key, n));
+  PS_TICK(); k_mis_keys<<<grid_for(n, 256), 256, 0, st>>>(n, l, key);
   PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, rp, strong, excl, stt);
   for (int round = 0;; round += kMisBatch) {
     PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t) * kMisBatch, st));
     for (int b = 0; b < kMisBatch; ++b) {
       const int32_t* prev = b > 0 ? und + b - 1 : nullptr;
-      PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, l, m1, prev);
-      PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, l, stt, nr, prev);
+      PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, key, m1, prev);
+      PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, key, stt, nr, prev);
       PS_TICK(); k_mis_c1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, nr, c1, prev);
       PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, c1, stt, und + b, prev);
     }
@@ -1537,7 +1546,7 @@ ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, c
   PS_TICK(); k_agg_phase2<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, strong, wgt, stt, ph1, *agg);
   PS_CUDA(cudaGetLastError());
   *nagg = na;
-  ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(isr); ar.release(rscan);
+  ar.release(m1); ar.release(nr); ar.release(c1); ar.release(und); ar.release(key); ar.release(isr); ar.release(rscan);
   ar.release(ph1); ar.release(strong); ar.release(wgt); ar.release(stt);
   return PS_OK;
 }

@@ -205,6 +205,70 @@ __global__ void k_p_fill(int64_t n, int b, const int32_t* __restrict__ rp, const
   }
 }
 
+// The same prolongator with one warp per row and B x 6 blocks: lane 0 lists the row's aggregates into pci
+// (the pattern), then for each aggregate the lanes take the entries (r, k) of its block (two per lane where
+// B = 6) and sum the products of the row's block columns in that aggregate in ascending order, each block
+// product entry over its inner index in ascending order: the arithmetic and order of k_p_fill, with the
+// warp's lanes on the FP64 work instead of one thread per row.
+template <int B>
+__global__ void __launch_bounds__(256) k_p_fill_w(int64_t n, const int32_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                  const int32_t* __restrict__ agg, const uint8_t* __restrict__ excl,
+                                                  const double* __restrict__ Pt, const double* __restrict__ dg,
+                                                  double omega, const int32_t* __restrict__ prp,
+                                                  int32_t* __restrict__ pci, double* __restrict__ pv) {
+  constexpr int NE = B * kRbmModes;
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n || excl[i]) return;
+  const int32_t o0 = prp[i], c = prp[i + 1] - prp[i];
+  if (lane == 0) {
+    int32_t list[kMaxRowAgg];
+    const int cc = row_aggs(i, rp, ci, agg, list, kMaxRowAgg);
+    if (cc == c)
+      for (int s = 0; s < c; ++s) pci[o0 + s] = list[s];
+    else
+      for (int s = 0; s < c; ++s) pci[o0 + s] = -1;  // overflow, reported by k_p_count
+  }
+  __syncwarp();
+  const int32_t q0 = rp[i], q1 = rp[i + 1];
+  const int t0 = lane, t1 = lane + 32;
+  const int r0 = t0 / kRbmModes, k0 = t0 % kRbmModes, r1 = t1 / kRbmModes, k1 = t1 % kRbmModes;
+  const int ai = agg[i];
+  for (int s = 0; s < c; ++s) {
+    const int32_t a = pci[o0 + s];
+    if (a < 0) return;
+    double S0 = 0.0, S1 = 0.0;
+    for (int32_t q = q0; q < q1; ++q) {
+      const int64_t j = ci[q];
+      if (agg[j] != a) continue;  // the same for every lane
+      const double* vq = v + int64_t(q) * B * B;
+      const double* pj = Pt + j * B * kRbmModes;
+      if (t0 < NE) {
+        double p = 0.0;
+#pragma unroll
+        for (int e = 0; e < B; ++e) p = p + vq[r0 * B + e] * pj[e * kRbmModes + k0];
+        S0 = S0 + p;
+      }
+      if (t1 < NE) {
+        double p = 0.0;
+#pragma unroll
+        for (int e = 0; e < B; ++e) p = p + vq[r1 * B + e] * pj[e * kRbmModes + k1];
+        S1 = S1 + p;
+      }
+    }
+    const int64_t o = o0 + s;
+    if (t0 < NE) {
+      const double delta = a == ai ? Pt[(i * B + r0) * kRbmModes + k0] : 0.0;
+      pv[(o * B + r0) * kRbmModes + k0] = delta - (omega / dg[i * B + r0]) * S0;
+    }
+    if (t1 < NE) {
+      const double delta = a == ai ? Pt[(i * B + r1) * kRbmModes + k1] : 0.0;
+      pv[(o * B + r1) * kRbmModes + k1] = delta - (omega / dg[i * B + r1]) * S1;
+    }
+  }
+}
+
 // transpose of a block matrix: entries grouped by column (cursor from the column offsets), then ordered by
 // row within each column, then the transposed blocks written out
 __global__ void k_t_count(int64_t nnz, const int32_t* __restrict__ ci, int32_t* __restrict__ cnt) {
@@ -428,8 +492,17 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
     lev.pnnzb = pnnz;
     PS_TRY(ar.alloc(&lev.pci, size_t(pnnz) + 1));
     PS_TRY(ar.alloc(&lev.pv, (size_t(pnnz) + 1) * b * kRbmModes));
-    PS_TICK(); k_p_fill<<<grid_for(n, 128), 128, 0, st>>>(n, b, lev.rp, lev.ci, lev.v, lev.agg, bex, lev.Pt, lev.dg,
-                                                           omega, lev.prp, lev.pci, lev.pv);
+    if (b == 3) {
+      PS_TICK(); k_p_fill_w<3><<<grid_for(n * 32, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, bex, lev.Pt,
+                                                                     lev.dg, omega, lev.prp, lev.pci, lev.pv);
+    } else if (b == kRbmModes) {
+      PS_TICK(); k_p_fill_w<kRbmModes><<<grid_for(n * 32, 256), 256, 0, st>>>(n, lev.rp, lev.ci, lev.v, lev.agg, bex,
+                                                                             lev.Pt, lev.dg, omega, lev.prp, lev.pci,
+                                                                             lev.pv);
+    } else {
+      PS_TICK(); k_p_fill<<<grid_for(n, 128), 128, 0, st>>>(n, b, lev.rp, lev.ci, lev.v, lev.agg, bex, lev.Pt, lev.dg,
+                                                             omega, lev.prp, lev.pci, lev.pv);
+    }
     PS_CUDA(cudaGetLastError());
     ar.release(pc); ar.release(bex);
     if (excl) ar.release(excl);
