@@ -140,10 +140,12 @@ typedef struct {
   int32_t cpr_reduction;      /* PS_CPR_QUASI_IMPES (default) or PS_CPR_TRUE_IMPES */
   int32_t solver;             /* PS_SOLVER_FGMRES (default) or PS_SOLVER_RICHARDSON */
   int32_t fs_mode;            /* PS_FS_GIVEN (default) or PS_FS_RSL */
-  int32_t vcycle_tail;        /* 1: the V-cycle levels below the finest run as one cooperative launch with
-                                 bounded grid barriers between their steps (Chebyshev degree 2, FP32/FP64
-                                 transfer operators); 0 (default): one kernel per step, replayed as a CUDA
-                                 graph, which measured faster.  Same results either way. */
+  int32_t vcycle_tail;        /* 0 (default): one kernel per V-cycle step, replayed as a CUDA graph;
+                                 1: the levels below the finest as one cooperative launch with bounded grid
+                                 barriers between their steps; 2: the levels from the first one of at most
+                                 1024 rows as one launch of a 16-CTA thread-block cluster with hardware cluster
+                                 barriers (both: Chebyshev degree 2, FP32/FP64 transfer operators).  Same
+                                 results every way; other values PS_ERR_INVALID. */
   int32_t pdl;                /* 1 (default): each V-cycle kernel after the first is launched with
                                  programmatic dependent launch, so its CTAs are scheduled while the
                                  previous kernel drains and wait on the device for its completion;

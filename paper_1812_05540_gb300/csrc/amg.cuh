@@ -68,8 +68,10 @@ struct Amg {
   // the levels from tail_l0 down run as one cooperative launch with bounded grid barriers between their
   // steps (k_vcycle_tail), when set up: tail points to the device array of their descriptors, tail_bar to
   // the barrier counter (zeroed before every launch); err is the handle's bounded-wait error flag
+  // tail_mode: 0 none, 1 the cooperative launch from level 1, 2 one thread-block cluster from the first small
+  // level (tail_grid is then the cluster's CTA count)
   void* tail = nullptr;
-  int tail_l0 = 0, tail_levels = 0, tail_grid = 0;
+  int tail_mode = 0, tail_l0 = 0, tail_levels = 0, tail_grid = 0;
   unsigned long long* tail_bar = nullptr;
   int* err = nullptr;
   int64_t spin_limit = 2000000;

@@ -7,6 +7,7 @@
 // index), so the aggregates and coarse operators are reproducible bit for bit.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 
@@ -1128,7 +1129,12 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   PS_CUDA(cudaGetLastError());
   if (dense_ok && hl > 0) {
     const size_t sm = size_t(dense_wpb) * dense_per;
-    cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    // the largest allowed size, the same for every caller (setups on several host threads)
+    int dev = 0, maxsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         std::max(maxsm, int(sm)));
     PS_TICK(); k_spgemm_dense_fill_w<NC><<<unsigned((hl + dense_wpb - 1) / dense_wpb), 32 * dense_wpb, sm, st>>>(
         longrows, hl, xrp, xci, xv, yrp, yci, yv, int32_t(m), words, *crp, *cci, *cv);
   }
@@ -1406,7 +1412,9 @@ bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) 
     const int R = int((n + cs - 1) / cs);
     const size_t smem = (size_t(2) * R * n + 2 * n + R + 2) * 8 + size_t(2 + 2 * n) * 4;
     if (smem > size_t(maxsm) - 1024) continue;
-    if (cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess ||
+    // the largest allowed size, the same for every caller: setups on several host threads may launch the
+    // kernel at once with different sizes
+    if (cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess ||
         (cs > 8 && cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
       cudaGetLastError();
       continue;
@@ -1437,7 +1445,12 @@ bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) 
 
 // The coarsest inverse by k_gj_all: 0 done, 1 not launched (no cooperative launch; the caller runs the
 // launch-per-step path), 2 a grid barrier wait gave up (the inverse is incomplete)
+// Cooperative launches of the inverse from setups on several host threads run one at a time (each waits for
+// its kernel before releasing the lock): two grids that each wait for all their CTAs to be resident must not
+// share the GPU.
+std::mutex g_coop_gj;
 int gj_cooperative(int64_t n, int nc, double* M, double* I, double* f, Arena& ar, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_coop_gj);
   int dev = 0, coop = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

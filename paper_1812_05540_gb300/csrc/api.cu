@@ -224,9 +224,8 @@ bool bsr_ok(const ps_bsr& B, int64_t rows, int64_t cols, int br, int bc) {
          B.nnzb >= 0 && B.nnzb < (int64_t(1) << 31) / 9;
 }
 
-ps_status build_flow(ps_handle* h) {
+ps_status build_flow(ps_handle* h, cudaStream_t st) {
   Arena& ar = h->arf;
-  cudaStream_t st = h->st;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -281,6 +280,7 @@ ps_status build_flow(ps_handle* h) {
   PS_TRY(amg_build(ar, h->amg_p, 1, h->nc, F.nnzb, F.rp, F.ci, F.spp, ap, st));
   bool sp_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_p, h->grid.nx, h->grid.ny, h->grid.nz, 7, h->mixed, &sp_ok, st));
+  h->amg_p.tail_mode = h->prm.vcycle_tail;
   if (h->mixed) {
     PS_TRY(amg_alloc_work<float>(ar, h->amg_p, smooth_params(h->prm), st));
     PS_TRY(flow_alloc_work<float>(ar, F, h->w32));
@@ -295,6 +295,9 @@ ps_status build_flow(ps_handle* h) {
   cudaEventDestroy(e1);
   return PS_OK;
 }
+
+ps_status build_mechanics(ps_handle* h, int64_t nnzb, cudaEvent_t e0, cudaEvent_t e1);
+ps_status finish_setup(ps_handle* h);
 
 ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   cudaStream_t st = h->st;
@@ -326,6 +329,17 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     return PS_ERR_INVALID;
   }
   int64_t nnzb = jac->A_uu.nnzb;
+  PS_TRY(build_mechanics(h, nnzb, e0, e1));
+  // §5.3 flow stage
+  PS_TRY(build_flow(h, st));
+  return finish_setup(h);
+}
+
+// §5.2 mechanics preconditioner (and the row-sum-lumped fixed stress, which applies it), on the handle's stream
+ps_status build_mechanics(ps_handle* h, int64_t nnzb, cudaEvent_t e0, cudaEvent_t e1) {
+  cudaStream_t st = h->st;
+  Arena& ar = h->ar;
+  JacDev& J = h->J;
   if (h->rbm) {
     // rigid-body-mode smoothed aggregation on the full A_uu
     PS_TRY(rbm_build(ar, h->rbm_u, h->grid.nx, h->grid.ny, h->grid.nz, nnzb, J.uu_rp, J.uu_ci, J.uu_v,
@@ -345,6 +359,7 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
     PS_TRY(amg_build(ar, h->amg_u, 3, h->nn, nnzb, J.uu_rp, J.uu_ci, sdc, ap, st));
     bool su_ok = false;
     PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
+    h->amg_u.tail_mode = h->prm.vcycle_tail;
     if (h->mixed) PS_TRY(amg_alloc_work<float>(ar, h->amg_u, smooth_params(h->prm), st));
     else PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
   }
@@ -388,8 +403,13 @@ ps_status setup_impl(ps_handle* h, const ps_jacobian* jac) {
   cudaEventElapsedTime(&h->ms_setup_u, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // §5.3 flow stage
-  PS_TRY(build_flow(h));
+  return PS_OK;
+}
+
+// what follows both stages: the V-cycles' flags and launch options, the Krylov workspace
+ps_status finish_setup(ps_handle* h) {
+  cudaStream_t st = h->st;
+  Arena& ar = h->ar;
   // the V-cycles' bounded grid barriers report through the same flag as the wavefront waits
   h->amg_u.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
   h->amg_p.err = h->prm.vcycle_tail ? h->F.ilu_err : nullptr;
@@ -477,6 +497,7 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
     return PS_ERR_INVALID;
   if (params->solver != PS_SOLVER_FGMRES && params->solver != PS_SOLVER_RICHARDSON) return PS_ERR_INVALID;
   if (params->fs_mode != PS_FS_GIVEN && params->fs_mode != PS_FS_RSL) return PS_ERR_INVALID;
+  if (params->vcycle_tail < 0 || params->vcycle_tail > 2) return PS_ERR_INVALID;
   if (params->mech_amg != PS_MECH_SDC && params->mech_amg != PS_MECH_RBM) return PS_ERR_INVALID;
   if (params->mech_amg == PS_MECH_RBM && params->smoother != PS_SMOOTH_CHEBYSHEV) {
     set_reason("the rigid-body-mode mechanics hierarchy smooths with Chebyshev only");
@@ -552,7 +573,7 @@ ps_status ps_setup_flow(ps_handle* h, const ps_jacobian* jac) {
   h->amg_p = Amg();
   h->w32 = FlowWork<float>();
   h->w64 = FlowWork<double>();
-  PS_TRY(build_flow(h));
+  PS_TRY(build_flow(h, st));
   // the mechanics V-cycle graph holds the old flag's address: capture it again with the new one
   amg_release_graph(h->amg_u);
   rbm_release_graph(h->rbm_u);

@@ -12,6 +12,8 @@
 #include "amg.cuh"
 #include "gridsync.cuh"
 
+#include <cooperative_groups.h>
+
 namespace ps_internal {
 namespace {
 
@@ -267,15 +269,21 @@ __global__ void k_dense_solve(int64_t n, const double* __restrict__ inv, const T
 }
 
 // ---------------------------------------------------------------------------
-// The coarse end of the V-cycle in one cooperative launch.  Below the finest level every level is small
-// and its kernels are bound by launch and drain latency, not bandwidth: about five microseconds per kernel
-// on levels whose data moves in one.  k_vcycle_tail runs the steps of levels tail_l0 .. coarsest in order
-// (down: smoothing pair, residual, restriction; the dense coarsest solve; up: prolongation, two post
-// steps), each as a grid-stride loop over the level's rows, with a bounded grid barrier between steps.
-// Each step is the same arithmetic as its own kernel (same row split into lanes, same order of sums), so the
-// result is bit-identical to the kernel-per-step path.  Used for Chebyshev of degree 2 with FP32 or FP64
-// transfer operators; other schedules keep the kernel-per-step path.
+// The coarse end of the V-cycle in one launch.  Below the finest level every level is small and its kernels
+// are bound by launch and drain latency, not bandwidth: about five microseconds per kernel on levels whose
+// data moves in one.  k_vcycle_tail runs the steps of levels tail_l0 .. coarsest in order (down: smoothing
+// pair, residual, restriction; the dense coarsest solve; up: prolongation, two post steps), each as a
+// grid-stride loop over the level's rows, with a barrier between steps: a bounded grid barrier in a
+// cooperative launch over the whole GPU (CL = false, from level 1), or the hardware barrier of one
+// thread-block cluster (CL = true, from the first level of at most kClusterTailRows rows, where 16 SMs
+// stream a level's operator from L2 as fast as the whole GPU and a barrier costs a fraction of a launch).
+// Vectors written inside the launch are read through L2 (ld.global.cg).  Each step is the same arithmetic as
+// its own kernel (same row split into lanes, same order of sums), so the result is bit-identical to the
+// kernel-per-step path.  Used for Chebyshev of degree 2 with FP32 or FP64 transfer operators; other schedules
+// keep the kernel-per-step path.
 // ---------------------------------------------------------------------------
+constexpr int64_t kClusterTailRows = 1024;
+constexpr int kTailCluster = 16;
 template <class T>
 struct TailLevel {
   int64_t n, nnext;
@@ -313,12 +321,20 @@ __device__ __forceinline__ void by_lanes(int lanes, F&& f) {
   }
 }
 
-template <class T, int NC>
+template <class T, int NC, bool CL>
 __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restrict__ lv, int nl,
                                                      unsigned long long* bar, int64_t limit, int* err) {
   const unsigned long long G = gridDim.x;
   unsigned long long phase = 0;
-  auto sync = [&]() -> bool { ++phase; return grid_barrier(bar, phase * G, limit, err); };
+  auto sync = [&]() -> bool {
+    if constexpr (CL) {
+      cooperative_groups::this_cluster().sync();
+      return true;
+    } else {
+      ++phase;
+      return grid_barrier(bar, phase * G, limit, err);
+    }
+  };
   // down the levels
   for (int k = 0; k + 1 < nl; ++k) {
     const TailLevel<T> L = lv[k];
@@ -327,14 +343,14 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.lanes, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int64_t j, int c) { return L.b[j * NC + c] * L.dsi[j * NC + c]; };
+        auto xf = [&](int64_t j, int c) { return __ldcg(L.b + j * NC + c) * L.dsi[j * NC + c]; };
         T s[NC];
         CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
         if (active && sub == 0)
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const T x1 = L.b[i * NC + c] * L.dsi[i * NC + c];
-            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
+            const T x1 = __ldcg(L.b + i * NC + c) * L.dsi[i * NC + c];
+            const T r = (__ldcg(L.b + i * NC + c) - s[c]) / L.dg[i * NC + c];
             const T dn = mad(T(a1[c]), x1, T(a2[c]) * r);
             L.x[i * NC + c] = x1 + dn;
           }
@@ -345,12 +361,12 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.lanes, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int64_t j, int c) { return L.x[j * NC + c]; };
+        auto xf = [&](int64_t j, int c) { return __ldcg(L.x + j * NC + c); };
         T s[NC];
         CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
         if (active && sub == 0)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) L.r[i * NC + c] = L.b[i * NC + c] - s[c];
+          for (int c = 0; c < NC; ++c) L.r[i * NC + c] = __ldcg(L.b + i * NC + c) - s[c];
       });
     });
     if (!sync()) return;
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.rlane, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.nnext, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int32_t j, int c) { return L.r[int64_t(j) * NC + c]; };
+        auto xf = [&](int32_t j, int c) { return __ldcg(L.r + int64_t(j) * NC + c); };
         T s[NC];
         const int32_t q0 = active ? L.rrp[i] : 0, q1 = active ? L.rrp[i + 1] : 0;
         Row<T, NC, LANES>::dot(active, q0, q1, L.rci, L.rv, xf, sub, s);
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
       const int64_t i = w % L.n;
       const double* row = L.inv + (int64_t(c) * L.n + i) * L.n;
       double s = 0.0;
-      for (int64_t j = lane; j < L.n; j += 32) s += row[j] * double(L.b[j * NC + c]);
+      for (int64_t j = lane; j < L.n; j += 32) s += row[j] * double(__ldcg(L.b + j * NC + c));
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) L.e[i * NC + c] = T(s);
     }
@@ -398,13 +414,13 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.plane, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int32_t j, int c) { return ec[int64_t(j) * NC + c]; };
+        auto xf = [&](int32_t j, int c) { return __ldcg(ec + int64_t(j) * NC + c); };
         T s[NC];
         const int32_t q0 = active ? L.prp[i] : 0, q1 = active ? L.prp[i + 1] : 0;
         Row<T, NC, LANES>::dot(active, q0, q1, L.pci, L.pv, xf, sub, s);
         if (active && sub == 0)
 #pragma unroll
-          for (int c = 0; c < NC; ++c) L.x[i * NC + c] = L.x[i * NC + c] + s[c];
+          for (int c = 0; c < NC; ++c) L.x[i * NC + c] = __ldcg(L.x + i * NC + c) + s[c];
       });
     });
     if (!sync()) return;
@@ -412,15 +428,15 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.lanes, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int64_t j, int c) { return L.x[j * NC + c]; };
+        auto xf = [&](int64_t j, int c) { return __ldcg(L.x + j * NC + c); };
         T s[NC];
         CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
         if (active && sub == 0)
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
+            const T r = (__ldcg(L.b + i * NC + c) - s[c]) / L.dg[i * NC + c];
             const T dn = T(p2[c]) * r;
-            L.t[i * NC + c] = L.x[i * NC + c] + dn;
+            L.t[i * NC + c] = __ldcg(L.x + i * NC + c) + dn;
             L.d[i * NC + c] = dn;
           }
       });
@@ -430,20 +446,21 @@ __global__ void __launch_bounds__(256) k_vcycle_tail(const TailLevel<T>* __restr
     by_lanes(L.lanes, [&](auto LN) {
       constexpr int LANES = decltype(LN)::value;
       tail_rows<LANES>(L.n, [&](int64_t i, int sub, bool active) {
-        auto xf = [&](int64_t j, int c) { return L.t[j * NC + c]; };
+        auto xf = [&](int64_t j, int c) { return __ldcg(L.t + j * NC + c); };
         T s[NC];
         CsrRows<T, NC, LANES>{L.rp, L.ci, L.v}.dot(i, sub, active, xf, s);
         if (active && sub == 0)
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const T r = (L.b[i * NC + c] - s[c]) / L.dg[i * NC + c];
-            const T dn = mad(T(a1[c]), L.d[i * NC + c], T(a2[c]) * r);
-            L.e[i * NC + c] = L.t[i * NC + c] + dn;
+            const T r = (__ldcg(L.b + i * NC + c) - s[c]) / L.dg[i * NC + c];
+            const T dn = mad(T(a1[c]), __ldcg(L.d + i * NC + c), T(a2[c]) * r);
+            L.e[i * NC + c] = __ldcg(L.t + i * NC + c) + dn;
           }
       });
     });
     if (k > 0 && !sync()) return;
   }
+  if constexpr (CL) cooperative_groups::this_cluster().sync();  // no CTA leaves while another may still run
 }
 
 template <class T>
@@ -638,8 +655,8 @@ void spmv_lanes(int lanes, int64_t n, const int32_t* rp, const int32_t* ci, cons
   }
 }
 
-// the tail levels in one cooperative launch; false when the launch was not possible (the caller then runs
-// the kernel-per-step path)
+// the tail levels in one launch (one thread-block cluster, or a cooperative launch over the GPU); false when
+// the launch was not possible (the caller then runs the kernel-per-step path)
 template <class T, int NC>
 bool launch_tail(Amg& H, cudaStream_t st) {
   const TailLevel<T>* lv = static_cast<const TailLevel<T>*>(H.tail);
@@ -647,12 +664,31 @@ bool launch_tail(Amg& H, cudaStream_t st) {
   unsigned long long* bar = H.tail_bar;
   int64_t limit = H.spin_limit;
   int* err = H.err;
+  if (H.tail_mode == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(H.tail_grid));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(H.tail_grid);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_vcycle_tail<T, NC, true>, lv, nl, bar, limit, err) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    PS_TICK();
+    return true;
+  }
   if (cudaMemsetAsync(bar, 0, sizeof(unsigned long long), st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   void* args[] = {&lv, &nl, &bar, &limit, &err};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_vcycle_tail<T, NC>, H.tail_grid, 256, args, 0, st);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_vcycle_tail<T, NC, false>, H.tail_grid, 256, args, 0, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -666,8 +702,8 @@ void vcycle_level(Amg& H, int l, const SmoothParams& sp, const T* b, T* out, cud
   AmgLevel& L = H.L[l];
   LevelT<T> V = view<T>(L);
   int64_t n = L.n;
-  if (l >= 1 && l == H.tail_l0 && H.tail && H.err && b == static_cast<const T*>(L.b) && out == static_cast<T*>(L.e) &&
-      launch_tail<T, NC>(H, st))
+  if (l >= 1 && l == H.tail_l0 && H.tail && (H.tail_mode == 2 || (H.tail_mode == 1 && H.err)) &&
+      b == static_cast<const T*>(L.b) && out == static_cast<T*>(L.e) && launch_tail<T, NC>(H, st))
     return;
   if (L.coarsest) {
     PS_TICK(); vl(k_dense_solve<T, NC>, grid_for(n * NC * 32, 256), st, n, V.inv, b, out);
@@ -703,27 +739,62 @@ void vcycle_launch(Amg& H, const SmoothParams& sp, const T* b, T* x, cudaStream_
 
 }  // namespace
 
-// descriptors of the levels below the finest for k_vcycle_tail (Chebyshev degree 2, FP32 or FP64 transfer
-// operators, cooperative launch available); leaves H.tail null otherwise
+// descriptors of the tail levels for k_vcycle_tail (Chebyshev degree 2, FP32 or FP64 transfer operators):
+// tail_mode 1, the levels below the finest in a cooperative launch; tail_mode 2, the levels from the first
+// one of at most kClusterTailRows rows in one thread-block cluster.  Leaves H.tail null when the mode is 0
+// or the launch is not possible.
 template <class T>
 ps_status tail_setup(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st) {
   H.tail = nullptr;
   const int nlev = int(H.L.size());
-  if (sp.kind != PS_SMOOTH_CHEBYSHEV || sp.degree != 2 || nlev < 3) return PS_OK;
-  for (int l = 1; l < nlev; ++l) {
+  if (H.tail_mode == 0 || sp.kind != PS_SMOOTH_CHEBYSHEV || sp.degree != 2 || nlev < 3) return PS_OK;
+  int l0 = 1;
+  if (H.tail_mode == 2) {
+    while (l0 < nlev - 1 && H.L[l0].n > kClusterTailRows) ++l0;
+    if (l0 >= nlev - 1) return PS_OK;  // only the coarsest is small: nothing to merge
+  }
+  for (int l = l0; l < nlev; ++l) {
     const AmgLevel& L = H.L[l];
     if (l < nlev - 1 && (!L.dsi || L.coarsest || L.pvb || L.rvb || L.sv_f || L.sv_d)) return PS_OK;
   }
   if (!H.L[nlev - 1].coarsest) return PS_OK;
-  int dev = 0, coop = 0, sms = 0, occ = 0;
+  int dev = 0, coop = 0, sms = 0, occ = 0, grid = 0;
   PS_CUDA(cudaGetDevice(&dev));
-  PS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const void* fn = H.nc == 3 ? (const void*)k_vcycle_tail<T, 3> : (const void*)k_vcycle_tail<T, 1>;
-  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0));
-  if (!coop || occ < 1) return PS_OK;
+  if (H.tail_mode == 2) {
+    const void* fn = H.nc == 3 ? (const void*)k_vcycle_tail<T, 3, true> : (const void*)k_vcycle_tail<T, 1, true>;
+    for (int cs : {kTailCluster, 8}) {
+      if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(cs));
+      cfg.blockDim = dim3(256);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(cs);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) == cudaSuccess && ncl >= 1) {
+        grid = cs;
+        break;
+      }
+      cudaGetLastError();
+    }
+    if (grid == 0) return PS_OK;
+  } else {
+    PS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const void* fn = H.nc == 3 ? (const void*)k_vcycle_tail<T, 3, false> : (const void*)k_vcycle_tail<T, 1, false>;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0));
+    if (!coop || occ < 1) return PS_OK;
+    grid = sms * (occ < 2 ? occ : 2);
+  }
   std::vector<TailLevel<T>> tl;
-  for (int l = 1; l < nlev; ++l) {
+  for (int l = l0; l < nlev; ++l) {
     const AmgLevel& L = H.L[l];
     const LevelT<T> V = view<T>(L);
     TailLevel<T> t;
@@ -750,9 +821,9 @@ ps_status tail_setup(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st)
   PS_TRY(ar.alloc(&H.tail_bar, 1));
   PS_CUDA(cudaStreamSynchronize(st));
   H.tail = d;
-  H.tail_l0 = 1;
+  H.tail_l0 = l0;
   H.tail_levels = int(tl.size());
-  H.tail_grid = sms * (occ < 2 ? occ : 2);
+  H.tail_grid = grid;
   return PS_OK;
 }
 

@@ -283,16 +283,18 @@ def test_bf16_prolongator_variant(cfg, kw, cm):
 
 
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
-def test_vcycle_tail_matches_kernel_per_step(prec):
-    # the levels below the finest in one cooperative launch (bounded grid barriers between the steps) do the
-    # arithmetic of the kernel-per-step path in the same order: Algorithm 1 gives the same bits either way,
-    # on a grid whose hierarchies have four levels
+@pytest.mark.parametrize("cfg,kw", [(2, dict(nx=21, ny=44, nz=17)), (1, {})])
+def test_vcycle_tail_matches_kernel_per_step(prec, cfg, kw):
+    # the levels below the finest in one cooperative launch (bounded grid barriers between the steps), and the
+    # small levels in one thread-block cluster (hardware cluster barriers), do the arithmetic of the
+    # kernel-per-step path in the same order: Algorithm 1 gives the same bits every way, on a grid whose
+    # hierarchies have four levels (the cluster tail from level 1) and on the 64x64x32 grid (from level 2)
     g = _gpu()
-    osys = oracle.System(oracle.default_params(2, nx=21, ny=44, nz=17))
+    osys = oracle.System(oracle.default_params(cfg, **kw))
     dev = g.to_device(osys)
     out = []
     side = torch.cuda.Stream()  # a stream that can be captured, so the V-cycles run as CUDA graphs
-    for tail in (1, 0):
+    for tail in (1, 2, 0):
         h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, vcycle_tail=tail,
                                                                  stream=side.cuda_stream))
         try:
@@ -305,7 +307,15 @@ def test_vcycle_tail_matches_kernel_per_step(prec):
             out.append(z.cpu().numpy())
         finally:
             ps.ps_free(h)
-    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[2])
+
+
+def test_vcycle_tail_rejects_unknown_mode():
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(0))
+    dev = g.to_device(osys)
+    with pytest.raises(ps.PsError):
+        ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(vcycle_tail=3))
 
 
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
