@@ -346,7 +346,11 @@ enum { PS_FIELDS_LOGNORMAL = 0, PS_FIELDS_LAYERED = 1, PS_FIELDS_CHANNELS = 2,
 enum {
   PS_GEN_GRAVITY = 1 << 0, PS_GEN_DIRICHLET = 1 << 1, PS_GEN_SCALE = 1 << 2,
   PS_GEN_ACCUM = 1 << 3, PS_GEN_FLUX = 1 << 4, PS_GEN_FLUX_SAT = 1 << 5,
-  PS_GEN_COUPLING = 1 << 6, PS_GEN_ALL = 0x7f
+  PS_GEN_COUPLING = 1 << 6, PS_GEN_ALL = 0x7f,
+  /* option, not in PS_GEN_ALL: Peaceman wells under bottom-hole pressure control (§3 well model, Table 1): a
+     water injector in the cell column (0, 0) and a producer in (nx-1, ny-1), both perforating every layer,
+     bottom-hole pressures 5 MPa above and below the hydrostatic formation pressure at the top perforation */
+  PS_GEN_WELLS = 1 << 7
 };
 
 typedef struct {

@@ -23,6 +23,7 @@ _LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 OR_GRAVITY, OR_DIRICHLET, OR_SCALE, OR_ACCUM, OR_FLUX, OR_FLUX_SAT, OR_COUPLING = (1 << i for i in range(7))
 OR_ALL = 0x7F
+OR_WELLS = 1 << 7  # Peaceman wells (an option; not in OR_ALL)
 FIELDS_LOGNORMAL, FIELDS_LAYERED, FIELDS_CHANNELS, FIELDS_HOMOGENEOUS = range(4)
 MECH_AMG, MECH_EXACT, MECH_AMG_RBM = 0, 1, 2
 FLOW_CPR, FLOW_EXACT_FS, FLOW_EXACT_SCHUR = 0, 1, 2

@@ -502,6 +502,73 @@ FaceFlux face_flux(const or_gen_params& gp, double Ups, double dz, double g, int
 }
 
 // Jacobian blocks of App. B at the given state, before scaling and Dirichlet.
+// ---------------------------------------------------------------------------
+// Peaceman wells under bottom-hole pressure control (§3 well model: Eq. (peaceman), Eq. (well_index);
+// Table 1 well control).  Two vertical wells perforate every layer at opposite ends of the grid: the water
+// injector in the cell column (0, 0), the producer in the column (nx - 1, ny - 1); each perforation connects
+// the well to the centroid of its cell.  The bottom-hole pressure is referred to the top perforation's
+// centroid z_bh and set 5 MPa above (injector) or below (producer) the formation pressure there, the
+// hydrostatic part of the initial pressure field; well radius 0.1524 m, skin 0.  For the isotropic cube cell
+// of edge h, WI = 2 pi h kappa_h / (ln(r / r_w) + s_k) with r = 0.28 sqrt(2) h / 2.  Phase potential
+// Phi_l = WI [(p_bh - p_K) + rho_l g (z_bh - z_K)]; injector q^I_w = rho_w (lambda_w + lambda_nw) Phi_w and no
+// non-wetting injection; producer q^P_l = -rho_l lambda_l Phi_l for both phases.  The cell's mass balances
+// get -dt (q^I_l - q^P_l) and their derivatives (App. B, viscosities constant).
+// ---------------------------------------------------------------------------
+const double kWellRadius = 0.1524, kWellSkin = 0.0, kWellDeltaBHP = 5.0e6;
+
+// 1: injector, 2: producer, 0: no well in the cell column (i, j)
+int well_kind(const Grid& g, int i, int j) {
+  if (i == 0 && j == 0) return 1;
+  if (i == g.nx - 1 && j == g.ny - 1) return 2;
+  return 0;
+}
+
+struct WellTerm {
+  double r[2];     // residual terms of the wetting (s) and non-wetting (p) rows
+  double d[2][2];  // their derivatives by (s, p) of the cell
+};
+
+WellTerm well_term(const or_gen_params& gp, const Grid& g, const Fields& F, int kind, int64_t c, int k, double s,
+                   double p) {
+  WellTerm w;
+  std::memset(&w, 0, sizeof(w));
+  const double grav = (gp.flags & OR_GRAVITY) ? gp.grav : 0.0;
+  const double h = g.h;
+  const double ztop = g.nz * h, zbh = (g.nz - 0.5) * h, zK = (k + 0.5) * h;
+  const double pform = gp.p_ref + gp.rho_w0 * grav * (ztop - zbh);
+  const double pbh = kind == 1 ? pform + kWellDeltaBHP : pform - kWellDeltaBHP;
+  const double re = 0.28 * std::sqrt(2.0 * h * h) / 2.0;
+  const double WI = 2.0 * kPi * h * F.kh[c] / (std::log(re / kWellRadius) + kWellSkin);
+  double krw, krnw, dkrw, dkrnw;
+  relperm(gp, s, &krw, &krnw, &dkrw, &dkrnw);
+  const double lam[2] = {krw / gp.mu_w, krnw / gp.mu_nw}, dlam[2] = {dkrw / gp.mu_w, dkrnw / gp.mu_nw};
+  const double dp = p - gp.p_ref;
+  const double rho[2] = {gp.rho_w0 * (1.0 + gp.c_w * dp), gp.rho_nw0 * (1.0 + gp.c_nw * dp)};
+  const double drho[2] = {gp.rho_w0 * gp.c_w, gp.rho_nw0 * gp.c_nw};
+  for (int l = 0; l < 2; ++l) {
+    const double Phi = WI * ((pbh - p) + rho[l] * grav * (zbh - zK));
+    const double dPhi = WI * (-1.0 + drho[l] * grav * (zbh - zK));
+    double q = 0.0, dqs = 0.0, dqp = 0.0;  // q^I_l - q^P_l and its derivatives
+    if (kind == 1) {
+      if (l == 0) {
+        const double lt = lam[0] + lam[1];
+        q = rho[0] * lt * Phi;
+        dqs = rho[0] * (dlam[0] + dlam[1]) * Phi;
+        dqp = drho[0] * lt * Phi + rho[0] * lt * dPhi;
+      }
+    } else {
+      // -q^P_l = rho_l lambda_l Phi_l
+      q = rho[l] * lam[l] * Phi;
+      dqs = rho[l] * dlam[l] * Phi;
+      dqp = drho[l] * lam[l] * Phi + rho[l] * lam[l] * dPhi;
+    }
+    w.r[l] = -gp.dt * q;
+    w.d[l][0] = -gp.dt * dqs;
+    w.d[l][1] = -gp.dt * dqp;
+  }
+  return w;
+}
+
 void assemble(const or_gen_params& gp, const Grid& g, const Fields& F, const State& st,
               const ExtraBC& bc, Jac& J) {
   RefInt R = ref_integrals(g.h);
@@ -555,7 +622,7 @@ void assemble(const or_gen_params& gp, const Grid& g, const Fields& F, const Sta
             if (coupling) { blk2[0 * 3 + e] += su; blk2[1 * 3 + e] += pu; }
           }
         }
-        // accumulation (App. B element blocks A_ss, A_sp, A_ps, A_pp; no wells)
+        // accumulation (App. B element blocks A_ss, A_sp, A_ps, A_pp; the well terms follow the face loop)
         if (gp.flags & OR_ACCUM) {
           int64_t pos = J.ff.find(c, c);
           double* blk = &J.ff.v[pos * 4];
@@ -620,6 +687,19 @@ void assemble(const or_gen_params& gp, const Grid& g, const Fields& F, const Sta
         }
     }
   }
+  // wells: cell-diagonal terms
+  if (gp.flags & OR_WELLS)
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          const int kind = well_kind(g, i, j);
+          if (!kind) continue;
+          const int64_t K = g.cell(i, j, k);
+          const WellTerm w = well_term(gp, g, F, kind, K, k, st.s[K], st.p[K]);
+          const int64_t pKK = J.ff.find(K, K);
+          for (int l = 0; l < 2; ++l)
+            for (int e = 0; e < 2; ++e) J.ff.v[pKK * 4 + l * 2 + e] += w.d[l][e];
+        }
   // Dirichlet dofs
   int64_t nu = 3 * g.nn();
   J.dir.assign(nu, 0);
@@ -1827,6 +1907,17 @@ void residual(const or_gen_params& gp, const Grid& g, const Fields& F, const Sta
           }
         }
   }
+  if (gp.flags & OR_WELLS)
+    for (int k = 0; k < g.nz; ++k)
+      for (int j = 0; j < g.ny; ++j)
+        for (int i = 0; i < g.nx; ++i) {
+          const int kind = well_kind(g, i, j);
+          if (!kind) continue;
+          const int64_t K = g.cell(i, j, k);
+          const WellTerm w = well_term(gp, g, F, kind, K, k, x.s[K], x.p[K]);
+          r[3 * nn + 2 * K] += w.r[0];
+          r[3 * nn + 2 * K + 1] += w.r[1];
+        }
 }
 
 void full_dense(const or_system* s, vec& d) {

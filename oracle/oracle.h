@@ -36,7 +36,8 @@ enum {
   OR_FLUX = 1 << 4,       /* TPFA face terms */
   OR_FLUX_SAT = 1 << 5,   /* saturation derivatives of the face fluxes */
   OR_COUPLING = 1 << 6,   /* A_uf and A_fu blocks */
-  OR_ALL = 0x7f
+  OR_ALL = 0x7f,          /* everything above; the wells below are an option */
+  OR_WELLS = 1 << 7       /* Peaceman wells under bottom-hole pressure control (water injector, producer) */
 };
 
 /* field statistics */

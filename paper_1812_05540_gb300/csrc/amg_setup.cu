@@ -1121,7 +1121,10 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
       const int wpb = C <= 128 ? 8 : (C <= 512 ? 4 : 2);
       size_t per = size_t(2 * C) * 4 + size_t(C) * 4 + size_t(C) * NC * 8 + size_t(32) * NC * 16;
       size_t sm = per * wpb;
-      cudaFuncSetAttribute(k_spgemm_fill<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      static std::once_flag once;  // one size per instance: set once per process
+      std::call_once(once, [sm]() {
+        cudaFuncSetAttribute(k_spgemm_fill<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+      });
       PS_TICK(); k_spgemm_fill<NC, C><<<unsigned((nr + wpb - 1) / wpb), 32 * wpb, sm, st>>>(
           rows, nr, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, islong, d_err);
     });
@@ -1129,12 +1132,14 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
   PS_CUDA(cudaGetLastError());
   if (dense_ok && hl > 0) {
     const size_t sm = size_t(dense_wpb) * dense_per;
-    // the largest allowed size, the same for every caller (setups on several host threads)
-    int dev = 0, maxsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         std::max(maxsm, int(sm)));
+    // the largest allowed size, set once, the same for every caller (setups on several host threads)
+    static std::once_flag once;
+    std::call_once(once, []() {
+      int dev = 0, maxsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+    });
     PS_TICK(); k_spgemm_dense_fill_w<NC><<<unsigned((hl + dense_wpb - 1) / dense_wpb), 32 * dense_wpb, sm, st>>>(
         longrows, hl, xrp, xci, xv, yrp, yci, yv, int32_t(m), words, *crp, *cci, *cv);
   }
@@ -1402,23 +1407,49 @@ __global__ void __launch_bounds__(256) k_gj_cluster(int64_t n, int R, const doub
 
 // k_gj_cluster when the rows fit the clusters' shared memory: true when done
 bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) {
-  int dev = 0, maxsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+  // device limits, kernel attributes and cluster feasibility, set up once per process: the attributes take
+  // the largest allowed shared-memory size (the same for every caller, so that setups on several host threads
+  // may launch at once), and with at most that much per CTA one CTA fits an SM, so whether a cluster of cs
+  // CTAs can be resident depends on cs alone
+  static std::once_flag once;
+  static int maxsm = 0, fits[2] = {0, 0};  // fits[0]: clusters of kGjCluster CTAs, fits[1]: of 8
+  std::call_once(once, []() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess) {
+      cudaGetLastError();
+      maxsm = 0;
+      return;
+    }
+    const bool np = cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     cudaGetLastError();
-    return false;
-  }
-  for (int cs : {kGjCluster, 8}) {
+    for (int t = 0; t < 2; ++t) {
+      const int cs = t == 0 ? kGjCluster : 8;
+      if (cs > 8 && !np) continue;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(cs));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = size_t(maxsm) - 1024;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = unsigned(cs);
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      fits[t] = cudaOccupancyMaxActiveClusters(&ncl, k_gj_cluster, &cfg) == cudaSuccess && ncl >= 1;
+      cudaGetLastError();
+    }
+  });
+  if (maxsm == 0) return false;
+  for (int t = 0; t < 2; ++t) {
+    if (!fits[t]) continue;
+    const int cs = t == 0 ? kGjCluster : 8;
     const int R = int((n + cs - 1) / cs);
     const size_t smem = (size_t(2) * R * n + 2 * n + R + 2) * 8 + size_t(2 + 2 * n) * 4;
     if (smem > size_t(maxsm) - 1024) continue;
-    // the largest allowed size, the same for every caller: setups on several host threads may launch the
-    // kernel at once with different sizes
-    if (cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess ||
-        (cs > 8 && cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
-      cudaGetLastError();
-      continue;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(cs * nc));
     cfg.blockDim = dim3(256);
@@ -1431,11 +1462,6 @@ bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_gj_cluster, &cfg) != cudaSuccess || ncl < 1) {
-      cudaGetLastError();
-      continue;
-    }
     PS_TICK();
     if (cudaLaunchKernelEx(&cfg, k_gj_cluster, n, R, M, I) == cudaSuccess) return true;
     cudaGetLastError();

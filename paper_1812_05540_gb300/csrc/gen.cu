@@ -477,6 +477,55 @@ __device__ inline double face_ups(double h, double kK, double kL) {
   return UK * UL / (UK + UL);
 }
 
+// Peaceman well of the cell column (i, j) under bottom-hole pressure control (§3 well model, Eq. (peaceman),
+// Eq. (well_index); Table 1): 1 the water injector (column (0, 0)), 2 the producer (column (nx-1, ny-1)), 0 none.
+// Both perforate every layer; the bottom-hole pressure is referred to the top perforation's centroid and set
+// 5 MPa above (injector) or below (producer) the hydrostatic formation pressure there.  For the cube cell of
+// edge h, WI = 2 pi h kappa_h / ln(r / r_w), r = 0.28 sqrt(2) h / 2, r_w = 0.1524 m, no skin.  The cell's
+// mass-balance rows get -dt (q^I_l - q^P_l): injector q^I_w = rho_w (lambda_w + lambda_nw) Phi_w (no
+// non-wetting injection), producer q^P_l = -rho_l lambda_l Phi_l, Phi_l = WI [(p_bh - p) + rho_l g (z_bh - z)];
+// wr gets the two terms and wd their (s, p) derivatives.
+__device__ inline int well_kind(const Grid3& g, int i, int j) {
+  if (i == 0 && j == 0) return 1;
+  if (i == g.nx - 1 && j == g.ny - 1) return 2;
+  return 0;
+}
+__device__ void well_terms(const Phys& P, const Grid3& g, int kind, int k, double kh, double s, double p,
+                           double wr[2], double wd[2][2]) {
+  const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
+  const double h = P.h, zbh = (g.nz - 0.5) * h, zK = (k + 0.5) * h;
+  const double pform = P.p_ref + P.rho_w0 * grav * (g.nz * h - zbh);
+  const double pbh = kind == 1 ? pform + 5.0e6 : pform - 5.0e6;
+  const double WI = 2.0 * kPiG * h * kh / log(0.28 * sqrt(2.0) * h / 2.0 / 0.1524);
+  double krw, krnw, dkrw, dkrnw;
+  corey(P, s, &krw, &krnw, &dkrw, &dkrnw);
+  const double lam[2] = {krw * P.inv_mu_w, krnw * P.inv_mu_nw};
+  const double dlam[2] = {dkrw * P.inv_mu_w, dkrnw * P.inv_mu_nw};
+  const double dp = p - P.p_ref;
+  const double rho[2] = {P.rho_w0 * (1.0 + P.c_w * dp), P.rho_nw0 * (1.0 + P.c_nw * dp)};
+  const double drho[2] = {P.rho_w0 * P.c_w, P.rho_nw0 * P.c_nw};
+  for (int l = 0; l < 2; ++l) {
+    const double Phi = WI * ((pbh - p) + rho[l] * grav * (zbh - zK));
+    const double dPhi = WI * (-1.0 + drho[l] * grav * (zbh - zK));
+    double q = 0.0, dqs = 0.0, dqp = 0.0;
+    if (kind == 1) {
+      if (l == 0) {
+        const double lt = lam[0] + lam[1];
+        q = rho[0] * lt * Phi;
+        dqs = rho[0] * (dlam[0] + dlam[1]) * Phi;
+        dqp = drho[0] * lt * Phi + rho[0] * lt * dPhi;
+      }
+    } else {
+      q = rho[l] * lam[l] * Phi;
+      dqs = rho[l] * dlam[l] * Phi;
+      dqp = drho[l] * lam[l] * Phi + rho[l] * lam[l] * dPhi;
+    }
+    wr[l] = -P.dt * q;
+    wd[l][0] = -P.dt * dqs;
+    wd[l][1] = -P.dt * dqp;
+  }
+}
+
 // A_ff row of cell c: accumulation (App. B element blocks), then the faces in
 // which c is the upper cell L (lower cells ascending), then those in which c is
 // the lower cell K (x, y, z).  Row K gets -dt dF, row L gets +dt dF.
@@ -538,6 +587,15 @@ __global__ void k_values_ff(Grid3 g, Phys P, const CellMat* __restrict__ M, cons
         val[qL * 4 + ph * 2 + 0] = 0.0 + -P.dt * f.dsL;
         val[qL * 4 + ph * 2 + 1] = 0.0 + -P.dt * f.dpL;
       }
+    }
+  }
+  if (P.flags & PS_GEN_WELLS) {
+    const int kind = well_kind(g, i, j);
+    if (kind) {
+      double wr[2], wd[2][2];
+      well_terms(P, g, kind, k, kh[c], s, p[c], wr, wd);
+      for (int l = 0; l < 2; ++l)
+        for (int e = 0; e < 2; ++e) dg[l * 2 + e] += wd[l][e];
     }
   }
   for (int t = 0; t < 4; ++t) val[qd * 4 + t] = dg[t];
@@ -833,6 +891,15 @@ __global__ void k_res_cells(Grid3 g, Phys P, const double* __restrict__ kh, cons
       const double Ups = dir == 2 ? face_ups(P.h, kv[c], kv[L]) : face_ups(P.h, kh[c], kh[L]);
       const double dz = dir == 2 ? P.h : 0.0;
       for (int ph = 0; ph < 2; ++ph) v[ph] += -P.dt * face_value(P, Ups, dz, ph, s[c], p[c], s[L], p[L]);
+    }
+  }
+  if (P.flags & PS_GEN_WELLS) {
+    const int kind = well_kind(g, i, j);
+    if (kind) {
+      double wr[2], wd[2][2];
+      well_terms(P, g, kind, k, kh[c], s[c], p[c], wr, wd);
+      v[0] += wr[0];
+      v[1] += wr[1];
     }
   }
   r[2 * c] = v[0];

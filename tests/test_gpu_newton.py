@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CASES = [(0, {}), (1, dict(nx=12, ny=10, nz=6))]
+WELLS = (1, dict(nx=12, ny=10, nz=6, flags=oracle.OR_ALL | oracle.OR_WELLS))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,7 +42,7 @@ def _offset(s0, seed):
     return dx
 
 
-@pytest.mark.parametrize("cfg,kw", CASES)
+@pytest.mark.parametrize("cfg,kw", CASES + [WELLS])
 def test_assemble_at_matches_oracle(cfg, kw):
     from tests.test_gpu_parity import _rows_close
     g = _g()
@@ -83,7 +84,7 @@ def test_assemble_at_matches_oracle(cfg, kw):
 
 @pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
 @pytest.mark.parametrize("forcing", [ps.PS_FORCING_FIXED, ps.PS_FORCING_EW])
-@pytest.mark.parametrize("cfg,kw", CASES)
+@pytest.mark.parametrize("cfg,kw", CASES + [WELLS])
 def test_newton_matches_oracle(cfg, kw, forcing, prec):
     ogp = oracle.default_params(cfg, **kw)
     ggp = _g().gen_params_like(ogp)

@@ -39,7 +39,8 @@ def _rows_close(a, b, bs, rp, rtol):
 GEN_CASES = [(0, {}), (1, dict(nx=24, ny=20, nz=10)), (2, dict(nx=30, ny=44, nz=17)),
              (0, dict(nx=5, ny=3, nz=2, flags=oracle.OR_ALL & ~oracle.OR_SCALE)),
              (3, dict(field_kind=oracle.FIELDS_HOMOGENEOUS, nx=4, ny=4, nz=3, dp_amp=0.0)),
-             (1, dict(nx=12, ny=10, nz=6, fs_modulus=1))]
+             (1, dict(nx=12, ny=10, nz=6, fs_modulus=1)),
+             (2, dict(nx=20, ny=24, nz=9, flags=oracle.OR_ALL | oracle.OR_WELLS))]
 
 
 @pytest.mark.parametrize("cfg,kw", GEN_CASES)

@@ -115,3 +115,49 @@ def test_library_forcing_term_equals_the_oracles():
         for k, rk, rkm1, eta_prev, r0 in itertools.product((0, 1, 4), (1e-7, 0.3, 2.0), (1e-3, 1.0, 5.0),
                                                              (1e-4, 0.1, 0.6), (10.0,)):
             assert ps.ps_newton_eta(p, k, rk, rkm1, eta_prev, r0) == oracle.ew_eta(o, k, rk, rkm1, eta_prev, r0)
+
+
+def test_well_jacobian_is_the_residual_derivative():
+    # the Peaceman well terms (§3 well model) of the Jacobian at an offset state are the derivatives of the
+    # residual's well sources: central differences on the well cells' columns; a planted sign or density
+    # mistake in either side fails it
+    gp = oracle.default_params(0, nx=4, ny=3, nz=3, flags=oracle.OR_ALL | oracle.OR_WELLS)
+    s0 = oracle.System(gp)
+    rng = np.random.default_rng(5)
+    dx = np.zeros(s0.n)
+    dx[s0.n_u::2] = 0.02 * rng.standard_normal(s0.n_cells)
+    dx[s0.n_u + 1::2] = 2e5 * rng.standard_normal(s0.n_cells)
+    s = oracle.System(gp, dx)
+    J = s.dense()
+    nx, ny, nz = gp.nx, gp.ny, gp.nz
+    wells = [i + nx * (j + ny * k) for k in range(nz) for (i, j) in ((0, 0), (nx - 1, ny - 1))]
+    for c in wells:
+        for comp, h in ((0, 1e-6), (1, 1.0)):
+            col = s0.n_u + 2 * c + comp
+            e = np.zeros(s0.n)
+            e[col] = h
+            d = (oracle.residual(gp, dx + e) - oracle.residual(gp, dx - e)) / (2 * h)
+            if comp == 1:
+                d = d * 1e6
+            fd = _scaled_rows(s, d)[s0.n_u:]
+            jc = J[s0.n_u:, col]
+            assert np.linalg.norm(fd - jc) <= 1e-5 * max(np.linalg.norm(jc), 1e-12), (c, comp)
+
+
+def test_wells_inject_water_and_produce_both_phases():
+    # at the base state the injector column gains wetting-phase mass only and the producer column loses mass of
+    # both phases (the 5 MPa bottom-hole offsets of Table 1 set the signs): the residual's well sources
+    gp = oracle.default_params(0, nx=4, ny=3, nz=3)
+    gw = oracle.default_params(0, nx=4, ny=3, nz=3, flags=oracle.OR_ALL | oracle.OR_WELLS)
+    s0 = oracle.System(gp)
+    x = np.zeros(s0.n)
+    dr = oracle.residual(gw, x) - oracle.residual(gp, x)
+    nx, ny, nz = gp.nx, gp.ny, gp.nz
+    nu = s0.n_u
+    inj = [i for i in range(s0.n_cells) if i % nx == 0 and (i // nx) % ny == 0]
+    prod = [i for i in range(s0.n_cells) if i % nx == nx - 1 and (i // nx) % ny == ny - 1]
+    other = [c for c in range(s0.n_cells) if c not in inj and c not in prod]
+    assert np.all(dr[:nu] == 0.0)
+    assert all(dr[nu + 2 * c] < 0 and dr[nu + 2 * c + 1] == 0.0 for c in inj)  # -dt q^I_w < 0
+    assert all(dr[nu + 2 * c] > 0 and dr[nu + 2 * c + 1] > 0 for c in prod)  # +dt q^P_l > 0
+    assert all(dr[nu + 2 * c] == 0.0 and dr[nu + 2 * c + 1] == 0.0 for c in other)
