@@ -555,9 +555,13 @@ def run_ours(args):
         if not args.no_newton:
             nw = {}
             xn = torch.zeros(n, dtype=torch.float64, device="cuda")
-            for fname, forcing in (("eisenstat_walker", ps.PS_FORCING_EW), ("fixed_1e-6", ps.PS_FORCING_FIXED)):
+            gpw = ps.ps_gen_default(args.config)
+            gpw.flags = gpw.flags | ps.PS_GEN_WELLS
+            for fname, forcing, gpn in (("eisenstat_walker", ps.PS_FORCING_EW, gp),
+                                        ("fixed_1e-6", ps.PS_FORCING_FIXED, gp),
+                                        ("eisenstat_walker_with_wells", ps.PS_FORCING_EW, gpw)):
                 torch.cuda.synchronize()
-                nst, nstats = ps.ps_newton(gp, ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr),
+                nst, nstats = ps.ps_newton(gpn, ps.ps_params_default(precision=ps.PS_MIXED_FP32, stream=sptr),
                                            ps.ps_newton_params_default(forcing=forcing), xn.data_ptr(),
                                            raise_on_error=False)
                 k = nstats["newton_iters"]
@@ -570,7 +574,8 @@ def run_ours(args):
             del xn
             nw["note"] = ("one time step from the previous level, mixed precision, to ||R r_k|| <= %g ||R r_0|| "
                           "(the paper's Newton tolerance); linear_s includes the setups (mechanics once, flow per "
-                          "Newton step)" % ps.ps_newton_params_default().rtol)
+                          "Newton step); with_wells: the Peaceman injector/producer pair of PS_GEN_WELLS under "
+                          "bottom-hole pressure control" % ps.ps_newton_params_default().rtol)
         per_mx = t_mx / args.steps
         per_64 = t_64 / args.steps
 

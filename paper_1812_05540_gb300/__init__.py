@@ -30,6 +30,7 @@ PS_FIELDS_LOGNORMAL, PS_FIELDS_LAYERED, PS_FIELDS_CHANNELS, PS_FIELDS_HOMOGENEOU
 PS_GEN_GRAVITY, PS_GEN_DIRICHLET, PS_GEN_SCALE, PS_GEN_ACCUM, PS_GEN_FLUX, PS_GEN_FLUX_SAT, PS_GEN_COUPLING = \
     (1 << i for i in range(7))
 PS_GEN_ALL = 0x7F
+PS_GEN_WELLS = 1 << 7  # Peaceman wells (an option; not in PS_GEN_ALL)
 
 
 class ps_grid(C.Structure):
