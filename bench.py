@@ -557,6 +557,7 @@ def run_ours(args):
             xn = torch.zeros(n, dtype=torch.float64, device="cuda")
             gpw = ps.ps_gen_default(args.config)
             gpw.flags = gpw.flags | ps.PS_GEN_WELLS
+            gpw.dt = 8640.0  # the first step of the paper's runs: 0.1 day (Table 1), a tenth of the BHP build-up
             for fname, forcing, gpn in (("eisenstat_walker", ps.PS_FORCING_EW, gp),
                                         ("fixed_1e-6", ps.PS_FORCING_FIXED, gp),
                                         ("eisenstat_walker_with_wells", ps.PS_FORCING_EW, gpw)):
@@ -575,7 +576,7 @@ def run_ours(args):
             nw["note"] = ("one time step from the previous level, mixed precision, to ||R r_k|| <= %g ||R r_0|| "
                           "(the paper's Newton tolerance); linear_s includes the setups (mechanics once, flow per "
                           "Newton step); with_wells: the Peaceman injector/producer pair of PS_GEN_WELLS under "
-                          "bottom-hole pressure control" % ps.ps_newton_params_default().rtol)
+                          "bottom-hole pressure control, first step of 0.1 day" % ps.ps_newton_params_default().rtol)
         per_mx = t_mx / args.steps
         per_64 = t_64 / args.steps
 

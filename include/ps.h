@@ -159,6 +159,12 @@ typedef struct {
                                  rigid-body modes as near-nullspace, 6 x 6 blocks on the aggregates below,
                                  QR-based tentative prolongator, Jacobi-smoothed P, Galerkin levels;
                                  Chebyshev smoothing only (PS_ERR_INVALID otherwise) */
+  int32_t autotune;           /* 1: at setup, time the CSR row kernels of every coarse level (operator, P, R)
+                                 with half, the same and twice the lanes per row that the mean row length
+                                 gives, and keep the fastest (within 3 %% the default stays); choices are cached
+                                 per process by level shape, so equal hierarchies get equal schedules.  The
+                                 lanes change only the order of a row's FP32/FP64 sums.  0 (default): lanes
+                                 from the mean row length alone. */
 } ps_params;
 
 typedef struct {
@@ -349,7 +355,8 @@ enum {
   PS_GEN_COUPLING = 1 << 6, PS_GEN_ALL = 0x7f,
   /* option, not in PS_GEN_ALL: Peaceman wells under bottom-hole pressure control (§3 well model, Table 1): a
      water injector in the cell column (0, 0) and a producer in (nx-1, ny-1), both perforating every layer,
-     bottom-hole pressures 5 MPa above and below the hydrostatic formation pressure at the top perforation */
+     bottom-hole pressures 5 MPa above and below the hydrostatic formation pressure at the top perforation,
+     built up linearly over one day (a step of dt reaches the fraction min(dt / 1 day, 1)) */
   PS_GEN_WELLS = 1 << 7
 };
 

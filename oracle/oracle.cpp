@@ -508,7 +508,8 @@ FaceFlux face_flux(const or_gen_params& gp, double Ups, double dz, double g, int
 // injector in the cell column (0, 0), the producer in the column (nx - 1, ny - 1); each perforation connects
 // the well to the centroid of its cell.  The bottom-hole pressure is referred to the top perforation's
 // centroid z_bh and set 5 MPa above (injector) or below (producer) the formation pressure there, the
-// hydrostatic part of the initial pressure field; well radius 0.1524 m, skin 0.  For the isotropic cube cell
+// hydrostatic part of the initial pressure field, after a linear build-up over one day (a step of dt from the
+// start reaches the fraction min(dt / 1 day, 1) of it); well radius 0.1524 m, skin 0.  For the isotropic cube cell
 // of edge h, WI = 2 pi h kappa_h / (ln(r / r_w) + s_k) with r = 0.28 sqrt(2) h / 2.  Phase potential
 // Phi_l = WI [(p_bh - p_K) + rho_l g (z_bh - z_K)]; injector q^I_w = rho_w (lambda_w + lambda_nw) Phi_w and no
 // non-wetting injection; producer q^P_l = -rho_l lambda_l Phi_l for both phases.  The cell's mass balances
@@ -536,7 +537,9 @@ WellTerm well_term(const or_gen_params& gp, const Grid& g, const Fields& F, int 
   const double h = g.h;
   const double ztop = g.nz * h, zbh = (g.nz - 0.5) * h, zK = (k + 0.5) * h;
   const double pform = gp.p_ref + gp.rho_w0 * grav * (ztop - zbh);
-  const double pbh = kind == 1 ? pform + kWellDeltaBHP : pform - kWellDeltaBHP;
+  // the offsets build up linearly over one day (Table 1 ramp time): at the end of a step of dt from the start
+  const double dbhp = kWellDeltaBHP * std::min(gp.dt / 86400.0, 1.0);
+  const double pbh = kind == 1 ? pform + dbhp : pform - dbhp;
   const double re = 0.28 * std::sqrt(2.0 * h * h) / 2.0;
   const double WI = 2.0 * kPi * h * F.kh[c] / (std::log(re / kWellRadius) + kWellSkin);
   double krw, krnw, dkrw, dkrnw;

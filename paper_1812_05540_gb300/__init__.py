@@ -58,7 +58,7 @@ class ps_params(C.Structure):
                 ("ortho", C.c_int32), ("test_stall_gs", C.c_int32), ("ortho_sweep", C.c_int32),
                 ("local_stage", C.c_int32), ("local_sweeps", C.c_int32), ("cpr_reduction", C.c_int32),
                 ("solver", C.c_int32), ("fs_mode", C.c_int32), ("vcycle_tail", C.c_int32),
-                ("pdl", C.c_int32), ("ilu_scope", C.c_int32), ("mech_amg", C.c_int32)]
+                ("pdl", C.c_int32), ("ilu_scope", C.c_int32), ("mech_amg", C.c_int32), ("autotune", C.c_int32)]
 
 
 class ps_stats(C.Structure):

@@ -72,6 +72,8 @@ struct Amg {
   // level (tail_grid is then the cluster's CTA count)
   void* tail = nullptr;
   int tail_mode = 0, tail_l0 = 0, tail_levels = 0, tail_grid = 0;
+  // 1: the lanes per row of the coarse levels' CSR kernels are picked by timing (amg_alloc_work)
+  int autotune = 0;
   unsigned long long* tail_bar = nullptr;
   int* err = nullptr;
   int64_t spin_limit = 2000000;

@@ -281,6 +281,7 @@ ps_status build_flow(ps_handle* h, cudaStream_t st) {
   bool sp_ok = false;
   PS_TRY(amg_stencil(ar, h->amg_p, h->grid.nx, h->grid.ny, h->grid.nz, 7, h->mixed, &sp_ok, st));
   h->amg_p.tail_mode = h->prm.vcycle_tail;
+  h->amg_p.autotune = h->prm.autotune;
   if (h->mixed) {
     PS_TRY(amg_alloc_work<float>(ar, h->amg_p, smooth_params(h->prm), st));
     PS_TRY(flow_alloc_work<float>(ar, F, h->w32));
@@ -360,6 +361,7 @@ ps_status build_mechanics(ps_handle* h, int64_t nnzb, cudaEvent_t e0, cudaEvent_
     bool su_ok = false;
     PS_TRY(amg_stencil(ar, h->amg_u, h->grid.nx + 1, h->grid.ny + 1, h->grid.nz + 1, 27, h->mixed, &su_ok, st));
     h->amg_u.tail_mode = h->prm.vcycle_tail;
+    h->amg_u.autotune = h->prm.autotune;
     if (h->mixed) PS_TRY(amg_alloc_work<float>(ar, h->amg_u, smooth_params(h->prm), st));
     else PS_TRY(amg_alloc_work<double>(ar, h->amg_u, smooth_params(h->prm), st));
   }
@@ -498,6 +500,7 @@ ps_status ps_setup(const ps_jacobian* jac, const ps_grid* grid, const ps_params*
   if (params->solver != PS_SOLVER_FGMRES && params->solver != PS_SOLVER_RICHARDSON) return PS_ERR_INVALID;
   if (params->fs_mode != PS_FS_GIVEN && params->fs_mode != PS_FS_RSL) return PS_ERR_INVALID;
   if (params->vcycle_tail < 0 || params->vcycle_tail > 2) return PS_ERR_INVALID;
+  if (params->autotune < 0 || params->autotune > 1) return PS_ERR_INVALID;
   if (params->mech_amg != PS_MECH_SDC && params->mech_amg != PS_MECH_RBM) return PS_ERR_INVALID;
   if (params->mech_amg == PS_MECH_RBM && params->smoother != PS_SMOOTH_CHEBYSHEV) {
     set_reason("the rigid-body-mode mechanics hierarchy smooths with Chebyshev only");

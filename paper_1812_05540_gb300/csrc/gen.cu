@@ -480,7 +480,8 @@ __device__ inline double face_ups(double h, double kK, double kL) {
 // Peaceman well of the cell column (i, j) under bottom-hole pressure control (§3 well model, Eq. (peaceman),
 // Eq. (well_index); Table 1): 1 the water injector (column (0, 0)), 2 the producer (column (nx-1, ny-1)), 0 none.
 // Both perforate every layer; the bottom-hole pressure is referred to the top perforation's centroid and set
-// 5 MPa above (injector) or below (producer) the hydrostatic formation pressure there.  For the cube cell of
+// 5 MPa above (injector) or below (producer) the hydrostatic formation pressure there, built up linearly over
+// one day (a step of dt from the start reaches the fraction min(dt / 1 day, 1)).  For the cube cell of
 // edge h, WI = 2 pi h kappa_h / ln(r / r_w), r = 0.28 sqrt(2) h / 2, r_w = 0.1524 m, no skin.  The cell's
 // mass-balance rows get -dt (q^I_l - q^P_l): injector q^I_w = rho_w (lambda_w + lambda_nw) Phi_w (no
 // non-wetting injection), producer q^P_l = -rho_l lambda_l Phi_l, Phi_l = WI [(p_bh - p) + rho_l g (z_bh - z)];
@@ -495,7 +496,8 @@ __device__ void well_terms(const Phys& P, const Grid3& g, int kind, int k, doubl
   const double grav = (P.flags & PS_GEN_GRAVITY) ? P.grav : 0.0;
   const double h = P.h, zbh = (g.nz - 0.5) * h, zK = (k + 0.5) * h;
   const double pform = P.p_ref + P.rho_w0 * grav * (g.nz * h - zbh);
-  const double pbh = kind == 1 ? pform + 5.0e6 : pform - 5.0e6;
+  const double dbhp = 5.0e6 * fmin(P.dt / 86400.0, 1.0);  // one-day linear build-up of the offsets
+  const double pbh = kind == 1 ? pform + dbhp : pform - dbhp;
   const double WI = 2.0 * kPiG * h * kh / log(0.28 * sqrt(2.0) * h / 2.0 / 0.1524);
   double krw, krnw, dkrw, dkrnw;
   corey(P, s, &krw, &krnw, &dkrw, &dkrnw);

@@ -13,6 +13,9 @@
 #include "gridsync.cuh"
 
 #include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace ps_internal {
 namespace {
@@ -827,6 +830,88 @@ ps_status tail_setup(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st)
   return PS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Lanes-per-row autotuner for the CSR kernels of the coarse levels.  For each level below the finest (the
+// finest is stencil-indexed on the structured grid, or tuned too when it is not) it times the residual kernel
+// of the level operator, and for every level the prolongation and restriction products, with half, the same
+// and twice the lanes that the mean row length gives (3 launches each after one warm-up, CUDA events on the
+// setup stream), and keeps the fastest; a candidate must beat the default by 3 % to replace it.  The choice
+// is cached per process by (value type, components, kind, rows, entries), so equal hierarchies get equal
+// schedules.  The lanes change only the order in which a row's products are summed.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune;
+
+template <class F>
+int tune_lanes(int kind, int tsize, int nc, int64_t n, int64_t nnz, int def, cudaStream_t st, F&& run) {
+  const auto key = std::make_tuple(tsize, nc, kind, n, nnz);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return def;
+  }
+  const int cand[3] = {def > 1 ? def / 2 : def, def, def < 32 ? def * 2 : def};
+  float best_ms = 0.0f, def_ms = 0.0f;
+  int best = def;
+  for (int t = 0; t < 3; ++t) {
+    const int L = cand[t];
+    if (t != 1 && L == def) continue;
+    run(L);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) run(L);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (L == def) def_ms = ms;
+    if (t == 0 || ms < best_ms) { best_ms = ms; best = L; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (best != def && best_ms > 0.97f * def_ms) best = def;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto ins = g_tune.emplace(key, best);
+  return ins.first->second;
+}
+
+template <class T, int NC>
+void autotune_levels(Amg& H, cudaStream_t st) {
+  const int nlev = int(H.L.size());
+  for (int l = 0; l + 1 < nlev; ++l) {
+    AmgLevel& L = H.L[l];
+    AmgLevel& C = H.L[l + 1];
+    LevelT<T> V = view<T>(L);
+    const T* b = static_cast<const T*>(L.b);
+    T* x = static_cast<T*>(L.x);
+    T* r = static_cast<T*>(L.r);
+    const int64_t n = L.n;
+    if (!V.sv) {
+      L.lanes = tune_lanes(0, int(sizeof(T)), NC, n, L.nnz, L.lanes, st, [&](int lanes) {
+        AmgLevel Lt = L;
+        Lt.lanes = lanes;
+        with_rows<T, NC>(Lt, V, [&](auto a) {
+          using A = decltype(a);
+          PS_TICK(); k_resid<T, NC, A><<<rows_grid<A>(n), 256, 0, st>>>(a, n, b, x, r);
+        });
+      });
+    }
+    if (!L.pvb) {
+      L.plane = tune_lanes(1, int(sizeof(T)), NC, n, L.pnnz, L.plane, st, [&](int lanes) {
+        spmv_lanes<T, NC>(lanes, n, L.prp, L.pci, V.pv, static_cast<const T*>(C.e), x, 0, st);
+      });
+      L.rlane = tune_lanes(2, int(sizeof(T)), NC, C.n, L.pnnz, L.rlane, st, [&](int lanes) {
+        spmv_lanes<T, NC>(lanes, C.n, L.rrp, L.rci, V.rv, r, static_cast<T*>(C.b), 0, st);
+      });
+    }
+  }
+}
+
 template <class T>
 ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t st) {
   for (auto& L : H.L) {
@@ -846,6 +931,11 @@ ps_status amg_alloc_work(Arena& ar, Amg& H, const SmoothParams& sp, cudaStream_t
     }
   }
   PS_CUDA(cudaGetLastError());
+  if (H.autotune) {
+    if (H.nc == 3) autotune_levels<T, 3>(H, st);
+    else autotune_levels<T, 1>(H, st);
+    PS_CUDA(cudaGetLastError());
+  }
   return tail_setup<T>(ar, H, sp, st);
 }
 

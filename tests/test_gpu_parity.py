@@ -348,3 +348,35 @@ def test_vcycle_programmatic_launch_same_bits(prec):
     if prec == ps.PS_FP64:
         zo = oracle.Prec(osys).apply(vs)
         assert np.linalg.norm(out[0] - zo) <= 1e-10 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("prec", [ps.PS_FP64, ps.PS_MIXED_FP32])
+def test_autotuned_lanes_solve_and_repeat(prec):
+    # lanes per row picked by timing at setup change only the order of a row's sums: the solve still meets the
+    # spec tolerances against the oracle, and a second handle of the same hierarchy reuses the cached
+    # choices, so Algorithm 1 gives it the same bits
+    g = _gpu()
+    osys = oracle.System(oracle.default_params(1, nx=24, ny=20, nz=10))
+    P = oracle.Prec(osys, oracle.default_prec_params(coarse_max_u=60, coarse_max_p=60))
+    xo, _ = P.fgmres(tol=1e-12)
+    _, sto = P.fgmres(tol=1e-8)
+    dev = g.to_device(osys)
+    zs = []
+    for rep in range(2):
+        h = ps.ps_setup(dev.jac, dev.grid, ps.ps_params_default(precision=prec, coarse_max_u=60, coarse_max_p=60,
+                                                                 autotune=1))
+        try:
+            v = torch.from_numpy(np.random.default_rng(4).standard_normal(osys.n)).cuda()
+            z = torch.empty_like(v)
+            ps.ps_apply_prec(h, v.data_ptr(), z.data_ptr())
+            zs.append(z.cpu().numpy())
+            x = torch.zeros(osys.n, dtype=torch.float64, device="cuda")
+            _, st = ps.ps_solve(h, dev.rhs.data_ptr(), x.data_ptr(), 1e-8)
+        finally:
+            ps.ps_free(h)
+        xs = x.cpu().numpy()
+        relres = np.linalg.norm(osys.rhs - osys.spmv(xs)) / np.linalg.norm(osys.rhs)
+        assert relres <= 1e-8
+        assert np.linalg.norm(xs - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert abs(st.iters - sto.iters) <= max(1, int(0.1 * sto.iters) + 1)
+    assert np.array_equal(zs[0], zs[1])
