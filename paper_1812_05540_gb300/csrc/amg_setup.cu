@@ -744,6 +744,164 @@ __global__ void k_spgemm_dense_fill_w(const int32_t* __restrict__ rows, int32_t 
   }
 }
 
+// ---- class-0 rows (at most 32 distinct columns) two to a warp ----
+// The fill of a short row keeps few lanes busy in the in-order folds of same-column products, and on GB300 a
+// warp's FP64 instruction costs the pipe a full issue whatever its active lanes.  Here each half-warp (16
+// lanes) takes one row, so the folds of two rows share each instruction.  The two halves run the same
+// sequence of warp-wide steps (loop counts are the larger of the two), and every result is formed as in
+// k_spgemm_fill: products of a row in (q, r) order, a column's products folded in that order by fused
+// multiply-adds, columns emitted sorted.
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ int half_max(int v) { return max(v, __shfl_xor_sync(kFull, v, 16)); }
+
+template <class F>
+__device__ __forceinline__ void for_products_h(int64_t i, const int32_t* __restrict__ xrp,
+                                               const int32_t* __restrict__ xci, const int32_t* __restrict__ yrp,
+                                               int hl, F&& f) {
+  const int32_t q0 = i >= 0 ? xrp[i] : 0, q1 = i >= 0 ? xrp[i + 1] : 0;
+  const int nch = half_max((q1 - q0 + 15) / 16);
+  for (int ch = 0; ch < nch; ++ch) {
+    const int32_t qc = q0 + ch * 16;
+    const int32_t q = qc + hl;
+    const bool v = q < q1;
+    const int32_t k = v ? xci[q] : 0;
+    const int32_t lo = v ? yrp[k] : 0;
+    const int32_t len = v ? yrp[k + 1] - lo : 0;
+    int32_t inc = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      const int32_t t = __shfl_up_sync(kFull, inc, o, 16);
+      if (hl >= o) inc += t;
+    }
+    const int32_t total = __shfl_sync(kFull, inc, 15, 16);
+    const int32_t excl = inc - len;
+    const int nr = half_max((total + 15) / 16);
+    for (int rr = 0; rr < nr; ++rr) {
+      const int32_t p = rr * 16 + hl;
+      int e = 0;
+#pragma unroll
+      for (int stp = 8; stp > 0; stp >>= 1) {
+        const int32_t ex = __shfl_sync(kFull, excl, e + stp, 16);
+        if (ex <= p) e += stp;
+      }
+      const int32_t lo_e = __shfl_sync(kFull, lo, e, 16);
+      const int32_t ex_e = __shfl_sync(kFull, excl, e, 16);
+      f(p < total, e, lo_e + (p - ex_e), qc);
+    }
+  }
+}
+
+template <int NC>
+__global__ void k_spgemm_fill_h(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
+                                const int32_t* __restrict__ xci, const double* __restrict__ xv,
+                                const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
+                                const double* __restrict__ yv, const int32_t* __restrict__ crp,
+                                int32_t* __restrict__ cci, double* __restrict__ cv,
+                                const uint8_t* __restrict__ islong, int* __restrict__ err) {
+  constexpr int C = 32, H = 2 * C;
+  constexpr int PER = H * 4 + C * 4 + C * NC * 8 + 16 * 2 * NC * 8;  // bytes per half-warp
+  extern __shared__ unsigned char sraw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + wib;
+  if (w * 2 >= nrows) return;  // the whole warp
+  const int64_t slot = w * 2 + half;
+  int64_t i = slot < nrows ? rows[slot] : -1;
+  if (i >= 0 && islong[i]) i = -1;
+  unsigned char* base = sraw + size_t(PER) * (wib * 2 + half);
+  int32_t* tab = reinterpret_cast<int32_t*>(base);
+  int32_t* list = reinterpret_cast<int32_t*>(base + H * 4);
+  double* acc = reinterpret_cast<double*>(base + H * 4 + C * 4);
+  double* stg = acc + C * NC;
+  // distinct columns into this half's hash table
+  for (int t = hl; t < H; t += 16) tab[t] = kEmpty;
+  __syncwarp();
+  int ovf = 0, cnt = 0;
+  for_products_h(i, xrp, xci, yrp, hl, [&](bool valid, int, int32_t r, int32_t) {
+    if (valid && hash_insert<H>(tab, yci[r], &ovf)) ++cnt;
+  });
+  __syncwarp();
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o, 16);
+  const int u = cnt;
+  const int bad = __any_sync(kFull, ovf != 0 || u > C);
+  if (bad) {
+    if (lane == 0) atomicExch(err, 1);
+    return;
+  }
+  // compact this half's table into list[0..u)
+  int pos = 0;
+  for (int t0 = 0; t0 < H; t0 += 16) {
+    const int32_t key = tab[t0 + hl];
+    const bool f = key != kEmpty;
+    const unsigned mk = (__ballot_sync(kFull, f) >> (half * 16)) & 0xffffu;
+    if (f) list[pos + __popc(mk & ((1u << hl) - 1u))] = key;
+    pos += __popc(mk);
+  }
+  __syncwarp();
+  // bitonic sort of list[0..P), P the next power of two >= u over both halves (padding INT_MAX)
+  int P = 1;
+  while (P < u) P <<= 1;
+  P = half_max(P);
+  for (int t = u + hl; t < P; t += 16) list[t] = 0x7fffffff;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = hl; t < P; t += 16) {
+        const int q = t ^ j;
+        if (q > t) {
+          const int32_t a = list[t], b = list[q];
+          const bool up = (t & k) == 0;
+          if ((a > b) == up) { list[t] = b; list[q] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  for (int t = hl; t < u * NC; t += 16) acc[t] = 0.0;
+  __syncwarp();
+  // numeric: a column's products folded in (q, r) order by the lowest lane of each same-column group
+  const int32_t q1 = i >= 0 ? xrp[i + 1] : 0;
+  for_products_h(i, xrp, xci, yrp, hl, [&](bool valid, int e, int32_t r, int32_t qc) {
+    int pp = 0;
+    if (valid) {
+      const int32_t jj = yci[r];
+      int lo = 0, hi = u;
+      while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (list[m] < jj) lo = m + 1;
+        else hi = m;
+      }
+      pp = lo;
+      const int32_t qe = qc + e;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        stg[hl * 2 * NC + c] = qe < q1 ? xv[int64_t(qe) * NC + c] : 0.0;
+        stg[hl * 2 * NC + NC + c] = yv[int64_t(r) * NC + c];
+      }
+    }
+    const unsigned peers = __match_any_sync(kFull, valid ? ((half << 30) | pp) : int(0x7fff0000 + lane));
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        double a = acc[pp * NC + c];
+        for (unsigned m = peers; m; m &= m - 1) {
+          const int pl = (__ffs(m) - 1) & 15;
+          a = fma(stg[pl * 2 * NC + c], stg[pl * 2 * NC + NC + c], a);
+        }
+        acc[pp * NC + c] = a;
+      }
+    }
+    __syncwarp();
+  });
+  if (i < 0) return;
+  const int32_t o = crp[i];
+  for (int t = hl; t < u; t += 16) {
+    cci[o + t] = list[t];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cv[int64_t(o + t) * NC + c] = acc[t * NC + c];
+  }
+}
+
 template <int NC, int C>
 __global__ void k_spgemm_fill(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
                               const int32_t* __restrict__ xci, const double* __restrict__ xv,
@@ -1116,6 +1274,14 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     int32_t nr = hc[kClasses + b];
     if (nr == 0) continue;
     const int32_t* rows = lists + int64_t(b) * n;
+    if (b == 0) {
+      // rows of at most 32 columns: two to a warp
+      constexpr int wpb = 8;
+      constexpr size_t per = size_t(2) * (64 * 4 + 32 * 4 + 32 * NC * 8 + 16 * 2 * NC * 8);
+      PS_TICK(); k_spgemm_fill_h<NC><<<unsigned((nr + 2 * wpb - 1) / (2 * wpb)), 32 * wpb, per * wpb, st>>>(
+          rows, nr, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, islong, d_err);
+      continue;
+    }
     for_class(b, [&](auto cc) {
       constexpr int C = decltype(cc)::value;
       const int wpb = C <= 128 ? 8 : (C <= 512 ? 4 : 2);
