@@ -744,7 +744,7 @@ __global__ void k_spgemm_dense_fill_w(const int32_t* __restrict__ rows, int32_t 
   }
 }
 
-// ---- class-0 rows (at most 32 distinct columns) two to a warp ----
+// ---- rows of the smallest class (at most 32 distinct columns) two to a warp ----
 // The fill of a short row keeps few lanes busy in the in-order folds of same-column products, and on GB300 a
 // warp's FP64 instruction costs the pipe a full issue whatever its active lanes.  Here each half-warp (16
 // lanes) takes one row, so the folds of two rows share each instruction.  The two halves run the same
@@ -791,14 +791,14 @@ __device__ __forceinline__ void for_products_h(int64_t i, const int32_t* __restr
   }
 }
 
-template <int NC>
+template <int NC, int C>
 __global__ void k_spgemm_fill_h(const int32_t* __restrict__ rows, int32_t nrows, const int32_t* __restrict__ xrp,
                                 const int32_t* __restrict__ xci, const double* __restrict__ xv,
                                 const int32_t* __restrict__ yrp, const int32_t* __restrict__ yci,
                                 const double* __restrict__ yv, const int32_t* __restrict__ crp,
                                 int32_t* __restrict__ cci, double* __restrict__ cv,
                                 const uint8_t* __restrict__ islong, int* __restrict__ err) {
-  constexpr int C = 32, H = 2 * C;
+  constexpr int H = 2 * C;
   constexpr int PER = H * 4 + C * 4 + C * NC * 8 + 16 * 2 * NC * 8;  // bytes per half-warp
   extern __shared__ unsigned char sraw[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
@@ -838,7 +838,7 @@ __global__ void k_spgemm_fill_h(const int32_t* __restrict__ rows, int32_t nrows,
     pos += __popc(mk);
   }
   __syncwarp();
-  // bitonic sort of list[0..P), P the next power of two >= u over both halves (padding INT_MAX)
+  // bitonic sort of list[0..P), P the larger of the two halves' next powers of two >= u (padding INT_MAX)
   int P = 1;
   while (P < u) P <<= 1;
   P = half_max(P);
@@ -1275,11 +1275,19 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     if (nr == 0) continue;
     const int32_t* rows = lists + int64_t(b) * n;
     if (b == 0) {
-      // rows of at most 32 columns: two to a warp
-      constexpr int wpb = 8;
-      constexpr size_t per = size_t(2) * (64 * 4 + 32 * 4 + 32 * NC * 8 + 16 * 2 * NC * 8);
-      PS_TICK(); k_spgemm_fill_h<NC><<<unsigned((nr + 2 * wpb - 1) / (2 * wpb)), 32 * wpb, per * wpb, st>>>(
-          rows, nr, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, islong, d_err);
+      // rows of at most 32 columns: two to a warp (the 128-column class measured slower this way: its rows
+      // have enough products per round to keep the lanes busy, and half the lanes doubled its rounds)
+      for_class(b, [&](auto cc) {
+        constexpr int C = decltype(cc)::value;
+        constexpr int wpb = 8;
+        constexpr size_t per = size_t(2) * (2 * C * 4 + C * 4 + C * NC * 8 + 16 * 2 * NC * 8);
+        static std::once_flag once;  // one size per instance: set once per process
+        std::call_once(once, []() {
+          cudaFuncSetAttribute(k_spgemm_fill_h<NC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(per * wpb));
+        });
+        PS_TICK(); k_spgemm_fill_h<NC, C><<<unsigned((nr + 2 * wpb - 1) / (2 * wpb)), 32 * wpb, per * wpb, st>>>(
+            rows, nr, xrp, xci, xv, yrp, yci, yv, *crp, *cci, *cv, islong, d_err);
+      });
       continue;
     }
     for_class(b, [&](auto cc) {
