@@ -6,6 +6,7 @@
 // every floating-point sum is taken in a fixed order (ascending column / inner
 // index), so the aggregates and coarse operators are reproducible bit for bit.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <mutex>
 #include <cmath>
@@ -1310,9 +1311,12 @@ ps_status spgemm(Arena& ar, int64_t n, int64_t m, const int32_t* xrp, const int3
     static std::once_flag once;
     std::call_once(once, []() {
       int dev = 0, maxsm = 0;
+      cudaFuncAttributes fa;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (cudaFuncGetAttributes(&fa, k_spgemm_dense_fill_w<NC>) == cudaSuccess) maxsm -= int(fa.sharedSizeBytes);
       cudaFuncSetAttribute(k_spgemm_dense_fill_w<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+      cudaGetLastError();
     });
     PS_TICK(); k_spgemm_dense_fill_w<NC><<<unsigned((hl + dense_wpb - 1) / dense_wpb), 32 * dense_wpb, sm, st>>>(
         longrows, hl, xrp, xci, xv, yrp, yci, yv, int32_t(m), words, *crp, *cci, *cv);
@@ -1581,53 +1585,40 @@ __global__ void __launch_bounds__(256) k_gj_cluster(int64_t n, int R, const doub
 
 // k_gj_cluster when the rows fit the clusters' shared memory: true when done
 bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) {
-  // device limits, kernel attributes and cluster feasibility, set up once per process: the attributes take
-  // the largest allowed shared-memory size (the same for every caller, so that setups on several host threads
-  // may launch at once), and with at most that much per CTA one CTA fits an SM, so whether a cluster of cs
-  // CTAs can be resident depends on cs alone
+  // device limits and kernel attributes, set once per process: the attributes take the largest allowed
+  // shared-memory size, the same for every caller, so that setups on several host threads may launch at once
   static std::once_flag once;
-  static int maxsm = 0, fits[2] = {0, 0};  // fits[0]: clusters of kGjCluster CTAs, fits[1]: of 8
+  static int maxsm = 0;
+  static bool nonportable = false;
   std::call_once(once, []() {
     int dev = 0;
+    cudaFuncAttributes fa;
+    // the dynamic limit is the opt-in maximum less the kernel's static shared memory
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_gj_cluster) != cudaSuccess ||
+        (maxsm -= int(fa.sharedSizeBytes)) <= 0 ||
         cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess) {
       cudaGetLastError();
       maxsm = 0;
       return;
     }
-    const bool np = cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    nonportable = cudaFuncSetAttribute(k_gj_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     cudaGetLastError();
-    for (int t = 0; t < 2; ++t) {
-      const int cs = t == 0 ? kGjCluster : 8;
-      if (cs > 8 && !np) continue;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(unsigned(cs));
-      cfg.blockDim = dim3(256);
-      cfg.dynamicSmemBytes = size_t(maxsm) - 1024;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = unsigned(cs);
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int ncl = 0;
-      fits[t] = cudaOccupancyMaxActiveClusters(&ncl, k_gj_cluster, &cfg) == cudaSuccess && ncl >= 1;
-      cudaGetLastError();
-    }
   });
   if (maxsm == 0) return false;
+  // whether a cluster of cs CTAs with this much shared memory each can be resident: asked once per
+  // (cluster size, 8 KB step of the size), the size rounded up
+  static std::atomic<int8_t> fits[2][32];  // 0 unknown, 1 fits, 2 does not
   for (int t = 0; t < 2; ++t) {
-    if (!fits[t]) continue;
     const int cs = t == 0 ? kGjCluster : 8;
+    if (cs > 8 && !nonportable) continue;
     const int R = int((n + cs - 1) / cs);
     const size_t smem = (size_t(2) * R * n + 2 * n + R + 2) * 8 + size_t(2 + 2 * n) * 4;
     if (smem > size_t(maxsm) - 1024) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(cs * nc));
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1636,6 +1627,19 @@ bool gj_cluster(int64_t n, int nc, const double* M, double* I, cudaStream_t st) 
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    const int step = int(std::min<size_t>(31, (smem + 8191) / 8192));
+    int8_t f = fits[t][step].load();
+    if (f == 0) {
+      cfg.dynamicSmemBytes = std::min<size_t>(size_t(step) * 8192, size_t(maxsm) - 1024);
+      cfg.gridDim = dim3(unsigned(cs));
+      int ncl = 0;
+      f = (cudaOccupancyMaxActiveClusters(&ncl, k_gj_cluster, &cfg) == cudaSuccess && ncl >= 1) ? 1 : 2;
+      cudaGetLastError();
+      fits[t][step].store(f);
+      cfg.gridDim = dim3(unsigned(cs * nc));
+    }
+    if (f != 1) continue;
+    cfg.dynamicSmemBytes = smem;
     PS_TICK();
     if (cudaLaunchKernelEx(&cfg, k_gj_cluster, n, R, M, I) == cudaSuccess) return true;
     cudaGetLastError();
