@@ -169,47 +169,11 @@ __global__ void k_p_count(int64_t n, const int32_t* __restrict__ rp, const int32
   cnt[i] = c;
 }
 
-// P = (I - omega D^{-1} A) P_tent: block (i, a) = [a == agg(i)] P_tent(i) - (omega / d_i) S, with S the sum
-// over the row's block columns j in aggregate a (ascending) of A_ij P_tent(j)
-__global__ void k_p_fill(int64_t n, int b, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const double* __restrict__ v, const int32_t* __restrict__ agg, const uint8_t* __restrict__ excl,
-                         const double* __restrict__ Pt, const double* __restrict__ dg, double omega,
-                         const int32_t* __restrict__ prp, int32_t* __restrict__ pci, double* __restrict__ pv) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n || excl[i]) return;
-  int32_t list[kMaxRowAgg];
-  const int c = row_aggs(i, rp, ci, agg, list, kMaxRowAgg);
-  if (c != prp[i + 1] - prp[i]) return;  // overflow, reported by k_p_count
-  for (int s = 0; s < c; ++s) {
-    const int32_t a = list[s];
-    double S[6][kRbmModes];
-    for (int r = 0; r < b; ++r)
-      for (int k = 0; k < kRbmModes; ++k) S[r][k] = 0.0;
-    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
-      const int64_t j = ci[q];
-      if (agg[j] != a) continue;
-      for (int r = 0; r < b; ++r)
-        for (int k = 0; k < kRbmModes; ++k) {
-          double p = 0.0;
-          for (int e = 0; e < b; ++e) p = p + v[(int64_t(q) * b + r) * b + e] * Pt[(j * b + e) * kRbmModes + k];
-          S[r][k] = S[r][k] + p;
-        }
-    }
-    const int64_t o = prp[i] + s;
-    pci[o] = a;
-    for (int r = 0; r < b; ++r)
-      for (int k = 0; k < kRbmModes; ++k) {
-        const double delta = a == agg[i] ? Pt[(i * b + r) * kRbmModes + k] : 0.0;
-        pv[(o * b + r) * kRbmModes + k] = delta - (omega / dg[i * b + r]) * S[r][k];
-      }
-  }
-}
-
-// The same prolongator with one warp per row and B x 6 blocks: lane 0 lists the row's aggregates into pci
-// (the pattern), then for each aggregate the lanes take the entries (r, k) of its block (two per lane where
-// B = 6) and sum the products of the row's block columns in that aggregate in ascending order, each block
-// product entry over its inner index in ascending order: the arithmetic and order of k_p_fill, with the
-// warp's lanes on the FP64 work instead of one thread per row.
+// P = (I - omega D^{-1} A) P_tent with B x 6 blocks, one warp per row: block (i, a) = [a == agg(i)] P_tent(i)
+// - (omega / d_i) S, with S the sum over the row's block columns j in aggregate a (ascending) of A_ij P_tent(j).
+// Lane 0 lists the row's aggregates into pci (the pattern); then for each aggregate the lanes take the entries
+// (r, k) of its block (two per lane where B = 6), each block-product entry summed over its inner index in
+// ascending order.
 template <int B>
 __global__ void __launch_bounds__(256) k_p_fill_w(int64_t n, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ ci, const double* __restrict__ v,
@@ -500,8 +464,8 @@ ps_status rbm_build(Arena& ar, Rbm& H, int nx, int ny, int nz, int64_t nnzb0, co
                                                                              lev.Pt, lev.dg, omega, lev.prp, lev.pci,
                                                                              lev.pv);
     } else {
-      PS_TICK(); k_p_fill<<<grid_for(n, 128), 128, 0, st>>>(n, b, lev.rp, lev.ci, lev.v, lev.agg, bex, lev.Pt, lev.dg,
-                                                             omega, lev.prp, lev.pci, lev.pv);
+      set_reason("rigid-body-mode level with %d x %d blocks", b, b);
+      return PS_ERR_INVALID;
     }
     PS_CUDA(cudaGetLastError());
     ar.release(pc); ar.release(bex);
