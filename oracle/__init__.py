@@ -530,7 +530,8 @@ def ew_eta(np_, k, rk, rkm1, eta_prev, r0):
 def residual(gp, dx):
     dx = np.ascontiguousarray(dx, dtype=np.float64)
     r = np.empty_like(dx)
-    lib().or_residual(C.byref(gp), _d(dx), _d(r))
+    if lib().or_residual(C.byref(gp), _d(dx), _d(r)) != 0:
+        raise ValueError("or_residual: invalid parameters")
     return r
 
 

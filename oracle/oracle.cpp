@@ -517,6 +517,11 @@ FaceFlux face_flux(const or_gen_params& gp, double Ups, double dz, double g, int
 // ---------------------------------------------------------------------------
 const double kWellRadius = 0.1524, kWellSkin = 0.0, kWellDeltaBHP = 5.0e6;
 
+// the well index needs a cell wider than the wellbore: Peaceman's radius r = 0.28 sqrt(2) h / 2 above r_w
+bool wells_ok(const or_gen_params& gp) {
+  return !(gp.flags & OR_WELLS) || 0.28 * std::sqrt(2.0) * gp.h / 2.0 > kWellRadius;
+}
+
 // 1: injector, 2: producer, 0: no well in the cell column (i, j)
 int well_kind(const Grid& g, int i, int j) {
   if (i == 0 && j == 0) return 1;
@@ -1725,7 +1730,7 @@ void or_default_params(or_gen_params* gp, int config) {
 // the Jacobian at the state base + dx (dx = NULL: the base state u = 0, s = S_w, p of the fields), the base
 // state being the previous time level
 static int generate_at(const or_gen_params* gp, const double* dx, or_system** out) {
-  if (gp->nx < 1 || gp->ny < 1 || gp->nz < 1) return 1;
+  if (gp->nx < 1 || gp->ny < 1 || gp->nz < 1 || !wells_ok(*gp)) return 1;
   Grid g{gp->nx, gp->ny, gp->nz, gp->h};
   Fields F = make_fields(*gp);
   State st;
@@ -2015,6 +2020,7 @@ void fgmres(int64_t n, const Op& A, const Op& M, const double* b, double* x, dou
 extern "C" {
 
 int or_residual(const or_gen_params* gp, const double* dx, double* r) {
+  if (!wells_ok(*gp)) return 1;
   Grid g{gp->nx, gp->ny, gp->nz, gp->h};
   Fields F = make_fields(*gp);
   State prev;

@@ -1241,8 +1241,16 @@ static ps_status generate_impl(const ps_gen_params* gp, cudaStream_t st, ps_syst
   return PS_OK;
 }
 
+// the well index needs a cell wider than the wellbore: Peaceman's radius 0.28 sqrt(2) h / 2 above 0.1524 m
+static bool wells_ok(const ps_gen_params* gp) {
+  if (!(gp->flags & PS_GEN_WELLS) || 0.28 * std::sqrt(2.0) * gp->h / 2.0 > 0.1524) return true;
+  set_reason("Peaceman wells need cells wider than the wellbore (h > 0.77 m), h = %g", gp->h);
+  return false;
+}
+
 ps_status ps_generate(const ps_gen_params* gp, void* stream, ps_system** out) {
   if (!gp || !out || gp->nx < 1 || gp->ny < 1 || gp->nz < 1 || !(gp->h > 0.0)) return PS_ERR_INVALID;
+  if (!wells_ok(gp)) return PS_ERR_INVALID;
   if (int64_t(gp->nx + 1) * (gp->ny + 1) * (gp->nz + 1) * 27 >= (int64_t(1) << 31)) return PS_ERR_INVALID;
   ps_system_impl* S = new ps_system_impl();
   std::memset(&S->pub, 0, sizeof(S->pub));
@@ -1262,6 +1270,7 @@ ps_status ps_generate(const ps_gen_params* gp, void* stream, ps_system** out) {
 static ps_status state_impl(const ps_gen_params* gp, ps_system* sys, const double* dx, double* r, bool jac,
                             cudaStream_t st) {
   if (!gp || !sys || !dx || (!r && !jac)) return PS_ERR_INVALID;
+  if (!wells_ok(gp)) return PS_ERR_INVALID;
   ps_system_impl* S = reinterpret_cast<ps_system_impl*>(sys);
   ps_system& o = S->pub;
   if (o.grid.nx != gp->nx || o.grid.ny != gp->ny || o.grid.nz != gp->nz || o.grid.hx != gp->h) {

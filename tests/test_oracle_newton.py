@@ -161,3 +161,21 @@ def test_wells_inject_water_and_produce_both_phases():
     assert all(dr[nu + 2 * c] < 0 and dr[nu + 2 * c + 1] == 0.0 for c in inj)  # -dt q^I_w < 0
     assert all(dr[nu + 2 * c] > 0 and dr[nu + 2 * c + 1] > 0 for c in prod)  # +dt q^P_l > 0
     assert all(dr[nu + 2 * c] == 0.0 and dr[nu + 2 * c + 1] == 0.0 for c in other)
+
+
+def test_wells_need_cells_wider_than_the_wellbore():
+    # Eq. (well_index) needs Peaceman's radius 0.28 sqrt(2) h / 2 above the well radius 0.1524 m: both the
+    # oracle and the library refuse wells on cells of 0.5 m (the library before touching the device)
+    import ctypes
+    import paper_1812_05540_gb300 as ps
+    gp = oracle.default_params(0, nx=4, ny=3, nz=3, h=0.5, flags=oracle.OR_ALL | oracle.OR_WELLS)
+    with pytest.raises(ValueError):
+        oracle.residual(gp, np.zeros(3 * 5 * 4 * 4 + 2 * 36))
+    with pytest.raises(RuntimeError):
+        oracle.System(gp)
+    g = ps.ps_gen_default(0)
+    g.nx, g.ny, g.nz, g.h = 4, 3, 3, 0.5
+    g.flags = ps.PS_GEN_ALL | ps.PS_GEN_WELLS
+    out = ctypes.POINTER(ps.ps_system)()
+    assert ps.lib().ps_generate(ctypes.byref(g), None, ctypes.byref(out)) == ps.PS_ERR_INVALID
+    assert not out
