@@ -1728,16 +1728,17 @@ ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, c
   int64_t* m1;
   uint8_t *nr, *c1;
   int32_t* und;
-  // rounds go in batches of kMisBatch between host checks; und[b] is the undecided flag of round b of a batch
+  // rounds go in batches between host checks, two then kMisBatch (small levels often finish within two
+  // rounds); und[b] is the undecided flag of round b of a batch
   constexpr int kMisBatch = 4;
   PS_TRY(ar.alloc(&m1, n)); PS_TRY(ar.alloc(&nr, n)); PS_TRY(ar.alloc(&c1, n)); PS_TRY(ar.alloc(&und, kMisBatch));
   int64_t* key;
   PS_TRY(ar.alloc(&key, n));
   PS_TICK(); k_mis_keys<<<grid_for(n, 256), 256, 0, st>>>(n, l, key);
   PS_TICK(); k_mis_init<<<grid_for(n, 256), 256, 0, st>>>(n, rp, strong, excl, stt);
-  for (int round = 0;; round += kMisBatch) {
+  for (int round = 0, nbat = 2;; round += nbat, nbat = kMisBatch) {
     PS_CUDA(cudaMemsetAsync(und, 0, sizeof(int32_t) * kMisBatch, st));
-    for (int b = 0; b < kMisBatch; ++b) {
+    for (int b = 0; b < nbat; ++b) {
       const int32_t* prev = b > 0 ? und + b - 1 : nullptr;
       PS_TICK(); k_mis_m1<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, stt, key, m1, prev);
       PS_TICK(); k_mis_m2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, m1, key, stt, nr, prev);
@@ -1745,7 +1746,7 @@ ps_status aggregate_impl(Arena& ar, int64_t n, int64_t nnz, const int32_t* rp, c
       PS_TICK(); k_mis_c2<<<grid_for(n * kMisLanes, 256), 256, 0, st>>>(n, rp, ci, strong, c1, stt, und + b, prev);
     }
     int32_t h_und = 0;
-    PS_CUDA(cudaMemcpyAsync(&h_und, und + kMisBatch - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(&h_und, und + nbat - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     if (h_und == 0) break;
     if (round > 100000) {
